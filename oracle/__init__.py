@@ -1,0 +1,251 @@
+"""ctypes front end of the plain FP64 C oracle (``oracle/*.c``).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package. The
+product path (``paper_1211_6866_gb300``) never does, and shares no code with
+it. Sparse matrices go in and come out as ``scipy.sparse.csc_matrix`` with
+int64 column pointers, int32 row indices sorted inside each column.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import scipy.sparse as sp
+
+from .build import build_oracle
+
+OK, BAD_INPUT, SINGULAR, MAXITER, BREAKDOWN, NOMEM = range(6)
+STATUS_NAMES = {0: "OK", 1: "BAD_INPUT", 2: "SINGULAR", 3: "MAXITER", 4: "BREAKDOWN", 5: "NOMEM"}
+
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+_f64p = C.POINTER(C.c_double)
+
+
+class _Csc(C.Structure):
+    _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("col_ptr", _i64p),
+                ("row_idx", _i32p), ("val", _f64p)]
+
+
+class _SpaiParams(C.Structure):
+    _fields_ = [("delta", C.c_double), ("mn", C.c_int32), ("max_aug", C.c_int32), ("key_bits", C.c_int32)]
+
+
+class _PsaiParams(C.Structure):
+    _fields_ = [("delta", C.c_double), ("tol", C.c_double), ("tol_mode", C.c_int32), ("lmax", C.c_int32)]
+
+
+class _SolveParams(C.Structure):
+    _fields_ = [("thresh_mult", C.c_double), ("abs_tau", C.c_double), ("sai", C.c_int32),
+                ("spai", _SpaiParams), ("psai", _PsaiParams), ("krylov", C.c_int32),
+                ("restart", C.c_int32), ("maxit", C.c_int32), ("eps", C.c_double)]
+
+
+class _SolveReport(C.Structure):
+    _fields_ = [("s", C.c_int32), ("p", C.c_int32), ("tau", C.c_double), ("nnz_At", C.c_int64),
+                ("nnz_M", C.c_int64), ("n_c", C.c_int32), ("l_m", C.c_int32), ("iter_max", C.c_int32),
+                ("status", C.c_int32), ("c", C.c_double), ("rr", C.c_double), ("bound", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle()
+        L = C.CDLL(path)
+        L.orc_avg_nnz.restype = C.c_int32
+        L.orc_avg_nnz.argtypes = [C.c_int32, C.c_int64]
+        L.orc_rel_resid.restype = C.c_double
+        L.orc_csc_free.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def as_csc(A):
+    """Canonical CSC copy: sorted rows, int64 pointers, int32 rows, float64 values."""
+    A = sp.csc_matrix(A)
+    A.sort_indices()
+    A.sum_duplicates()
+    return A
+
+
+class _In:
+    """Keeps the numpy buffers alive for the lifetime of the ctypes struct."""
+
+    def __init__(self, A):
+        A = as_csc(A)
+        self.indptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        self.indices = np.ascontiguousarray(A.indices, dtype=np.int32)
+        self.data = np.ascontiguousarray(A.data, dtype=np.float64)
+        self.s = _Csc(A.shape[0], A.shape[1], _ptr(self.indptr, _i64p), _ptr(self.indices, _i32p),
+                      _ptr(self.data, _f64p))
+        self.shape = A.shape
+
+
+def _take(c):
+    """Copy an oracle-allocated orc_csc into scipy and free the C arrays."""
+    nnz = int(c.col_ptr[c.ncols]) if c.col_ptr else 0
+    indptr = np.ctypeslib.as_array(c.col_ptr, shape=(c.ncols + 1,)).copy()
+    if nnz:
+        rows = np.ctypeslib.as_array(c.row_idx, shape=(nnz,)).copy()
+        vals = np.ctypeslib.as_array(c.val, shape=(nnz,)).copy()
+    else:
+        rows = np.zeros(0, np.int32)
+        vals = np.zeros(0, np.float64)
+    lib().orc_csc_free(C.byref(c))
+    return sp.csc_matrix((vals, rows, indptr), shape=(c.nrows, c.ncols))
+
+
+class OracleError(RuntimeError):
+    def __init__(self, what, status):
+        super().__init__("%s: oracle status %s" % (what, STATUS_NAMES.get(status, status)))
+        self.status = status
+
+
+def _check(what, st):
+    if st != OK:
+        raise OracleError(what, st)
+
+
+def avg_nnz(n, nnz):
+    return int(lib().orc_avg_nnz(int(n), int(nnz)))
+
+
+def detect(A, mult=10.0, abs_tau=-1.0, ge=False):
+    a = _In(A)
+    n = a.shape[1]
+    J = np.zeros(max(n, 1), np.int32)
+    s, p, tau = C.c_int32(), C.c_int32(), C.c_double()
+    _check("detect", lib().orc_detect(C.byref(a.s), C.c_double(mult), C.c_double(abs_tau), int(ge),
+                                      _ptr(J, _i32p), C.byref(s), C.byref(p), C.byref(tau)))
+    return J[: s.value].copy(), p.value, tau.value
+
+
+def split(A, J, p_keep):
+    a = _In(A)
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    At, U = _Csc(), _Csc()
+    _check("split", lib().orc_split(C.byref(a.s), _ptr(J, _i32p), len(J), int(p_keep), C.byref(At), C.byref(U)))
+    return _take(At), _take(U)
+
+
+def _cols(n, cols):
+    if cols is None:
+        return 0, n
+    return int(cols[0]), int(cols[1])
+
+
+def spai(At, delta, mn=5, max_aug=10, key_bits=20, cols=None):
+    """Returns (M csc, loops[n], res[n]); entries outside ``cols`` are 0 / empty."""
+    a = _In(At)
+    n = a.shape[1]
+    c0, c1 = _cols(n, cols)
+    prm = _SpaiParams(delta, mn, max_aug, key_bits)
+    loops = np.zeros(max(n, 1), np.int32)
+    res = np.zeros(max(n, 1), np.float64)
+    M = _Csc()
+    _check("spai", lib().orc_spai(C.byref(a.s), C.byref(prm), c0, c1, C.byref(M), _ptr(loops, _i32p),
+                                  _ptr(res, _f64p)))
+    return _take(M), loops[:n], res[:n]
+
+
+def _trace(fn, At, prm, k, cap):
+    a = _In(At)
+    S_hist = np.zeros(cap, np.int32)
+    S_off = np.zeros(256, np.int32)
+    res = np.zeros(256, np.float64)
+    nl = fn(C.byref(a.s), C.byref(prm), int(k), _ptr(S_hist, _i32p), cap, _ptr(S_off, _i32p), _ptr(res, _f64p))
+    if nl < 0:
+        raise OracleError("trace", -nl)
+    pats = [S_hist[S_off[l]: S_off[l + 1]].copy() for l in range(nl)]
+    return pats, res[:nl].copy()
+
+
+def spai_trace(At, k, delta, mn=5, max_aug=10, key_bits=20, cap=1 << 20):
+    """Pattern S^(l) (in insertion order) and LS residual for every loop of column k."""
+    return _trace(lib().orc_spai_trace, At, _SpaiParams(delta, mn, max_aug, key_bits), k, cap)
+
+
+def psai(At, delta, tol=0.0, tol_mode=0, lmax=10, cols=None):
+    """Returns (M csc, loops[n], res_pre[n], res_post[n])."""
+    a = _In(At)
+    n = a.shape[1]
+    c0, c1 = _cols(n, cols)
+    prm = _PsaiParams(delta, tol, tol_mode, lmax)
+    loops = np.zeros(max(n, 1), np.int32)
+    pre = np.zeros(max(n, 1), np.float64)
+    post = np.zeros(max(n, 1), np.float64)
+    M = _Csc()
+    _check("psai", lib().orc_psai(C.byref(a.s), C.byref(prm), c0, c1, C.byref(M), _ptr(loops, _i32p),
+                                  _ptr(pre, _f64p), _ptr(post, _f64p)))
+    return _take(M), loops[:n], pre[:n], post[:n]
+
+
+def psai_trace(At, k, delta, tol=0.0, tol_mode=0, lmax=10, cap=1 << 22):
+    return _trace(lib().orc_psai_trace, At, _PsaiParams(delta, tol, tol_mode, lmax), k, cap)
+
+
+def bicgstab(At, M, rhs, thr, maxit=500):
+    a, m = _In(At), _In(M)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    y = np.zeros_like(rhs)
+    it = C.c_int32()
+    st = lib().orc_bicgstab(C.byref(a.s), C.byref(m.s), _ptr(rhs, _f64p), C.c_double(thr), int(maxit),
+                            _ptr(y, _f64p), C.byref(it))
+    return y, it.value, st
+
+
+def gmres(At, M, rhs, thr, restart=50, maxit=500):
+    a, m = _In(At), _In(M)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    y = np.zeros_like(rhs)
+    it = C.c_int32()
+    st = lib().orc_gmres(C.byref(a.s), C.byref(m.s), _ptr(rhs, _f64p), C.c_double(thr), int(restart),
+                         int(maxit), _ptr(y, _f64p), C.byref(it))
+    return y, it.value, st
+
+
+def smw(yhat, W, J):
+    """W: (n, s) array. Returns (xhat, z, c)."""
+    yhat = np.ascontiguousarray(yhat, dtype=np.float64)
+    n = yhat.shape[0]
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    s = len(J)
+    Wc = np.asfortranarray(np.asarray(W, dtype=np.float64).reshape(n, s))
+    x = np.zeros(n)
+    z = np.zeros(max(s, 1))
+    c = C.c_double()
+    _check("smw", lib().orc_smw(n, s, _ptr(yhat, _f64p), Wc.ctypes.data_as(_f64p), _ptr(J, _i32p),
+                                _ptr(x, _f64p), _ptr(z, _f64p), C.byref(c)))
+    return x, z[:s], c.value
+
+
+def rel_resid(A, b, x):
+    a = _In(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().orc_rel_resid(C.byref(a.s), _ptr(b, _f64p), _ptr(x, _f64p)))
+
+
+def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0,
+          abs_tau=-1.0, delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10):
+    """Procedure * end to end. Returns (x, iters[s+1], report dict)."""
+    a = _In(A)
+    n = a.shape[1]
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
+                       _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
+                       0 if krylov == "bicgstab" else 1, restart, maxit, eps)
+    x = np.zeros(n)
+    iters = np.zeros(n + 1, np.int32)
+    rep = _SolveReport()
+    _check("solve", lib().orc_solve(C.byref(a.s), _ptr(b, _f64p), C.byref(prm), _ptr(x, _f64p),
+                                    _ptr(iters, _i32p), C.byref(rep)))
+    report = {f: getattr(rep, f) for f, _ in _SolveReport._fields_}
+    return x, iters[: rep.s + 1].copy(), report

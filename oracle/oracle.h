@@ -1,0 +1,168 @@
+/*
+ * oracle.h -- plain, sequential FP64 CPU oracle for the split + SAI +
+ * Krylov + Sherman-Morrison-Woodbury method of Jia & Zhang,
+ * "An approach to making SPAI and PSAI preconditioning effective for large
+ * irregular sparse linear systems" (arXiv 1211.6866).
+ *
+ * THIS IS TEST INFRASTRUCTURE. It exists only so that tests, the smoke check
+ * and the CPU-baseline leg of the benchmark can check and time the CUDA path.
+ * The product path never calls it. It shares no code, header, table or
+ * constant with the CUDA library, and neither side includes the other.
+ *
+ * Every routine is written for clarity, not speed: dense O(n) marker arrays,
+ * qsort, textbook Householder QR and textbook Krylov recurrences, all FP64.
+ *
+ * Sparse matrices are CSC: col_ptr[n+1] (int64), row_idx[nnz] (int32, sorted
+ * ascending inside each column, no duplicates), val[nnz] (double).
+ * Arrays returned through orc_csc outputs are malloc'd by the oracle and
+ * released with orc_csc_free(). All other outputs are caller-allocated.
+ */
+#ifndef SAI_ORACLE_H
+#define SAI_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t nrows;
+    int32_t ncols;
+    int64_t* col_ptr;
+    int32_t* row_idx;
+    double* val;
+} orc_csc;
+
+enum {
+    ORC_OK = 0,
+    ORC_BAD_INPUT = 1,
+    ORC_SINGULAR = 2,      /* an LS matrix or the s x s SMW matrix is singular */
+    ORC_MAXITER = 3,       /* Krylov iteration limit reached */
+    ORC_BREAKDOWN = 4,     /* BiCGStab rho = 0 or omega = 0 */
+    ORC_NOMEM = 5
+};
+
+void orc_csc_free(orc_csc* A);
+
+/* ---- section 4: dense-column detection and split (eq. (split)) ---------- */
+
+/* p = floor(nnz(A)/n), the average number of nonzeros per column (section 4). */
+int32_t orc_avg_nnz(int32_t n, int64_t nnz);
+
+/* Irregular columns: nnz(a_j) > tau (or >= tau when ge != 0), tau = mult*p,
+ * or tau = abs_tau when abs_tau >= 0. J_out (capacity n) gets the ascending
+ * list, *s_out its length, *p_out and *tau_out the values used. */
+int orc_detect(const orc_csc* A, double mult, double abs_tau, int ge,
+               int32_t* J_out, int32_t* s_out, int32_t* p_out, double* tau_out);
+
+/* Sparsify the s columns J of A: keep the diagonal and the p_keep-1 stored
+ * entries nearest to it (|i-j| ascending, ties to the smaller row), or the
+ * p_keep nearest entries when the diagonal is not stored. Outputs A~ (n x n)
+ * and U (n x s, column t holds the dropped entries of column J[t]). */
+int orc_split(const orc_csc* A, const int32_t* J, int32_t s, int32_t p_keep,
+              orc_csc* At_out, orc_csc* U_out);
+
+/* ---- section 2.1: SPAI (Grote-Huckle adaptive augmentation) -------------- */
+
+typedef struct {
+    double delta;      /* stop when ||A~ m_k - e_k|| <= delta            */
+    int32_t mn;        /* most profitable indices added per loop        */
+    int32_t max_aug;   /* maximum number of augmentation steps          */
+    int32_t key_bits;  /* rho^2/||r||^2 quantised to 2^-key_bits        */
+} orc_spai_params;
+
+/* Builds columns [c0, c1) of M ~ A~^{-1} (other columns left empty).
+ * loops_out[k] = augmentation steps used, res_out[k] = final ||r_k||.
+ * Both arrays have length n (entries outside [c0,c1) untouched). */
+int orc_spai(const orc_csc* At, const orc_spai_params* prm, int32_t c0, int32_t c1,
+             orc_csc* M_out, int32_t* loops_out, double* res_out);
+
+/* One column with its full trace: after loop l the pattern is
+ * S_hist[S_off[l] .. S_off[l+1]) and the LS residual res_hist[l].
+ * Capacities: S_hist >= cap_s, S_off >= max_aug+2, res_hist >= max_aug+1.
+ * Returns the number of loops recorded (>= 1) or a negative error. */
+int orc_spai_trace(const orc_csc* At, const orc_spai_params* prm, int32_t k,
+                   int32_t* S_hist, int32_t cap_s, int32_t* S_off, double* res_hist);
+
+/* ---- section 2.2: PSAI(tol) (power pattern growth + dropping) ------------ */
+
+typedef struct {
+    double delta;      /* stop tolerance on the pre-drop residual            */
+    double tol;        /* fixed dropping tolerance (tol_mode = 1)            */
+    int32_t tol_mode;  /* 0: tol_k = delta/(nnz(m_k) ||A~||_1), eq. (tolk);  */
+                       /* 1: tol_k = tol                                    */
+    int32_t lmax;      /* loops l = 0..lmax                                 */
+} orc_psai_params;
+
+/* Builds columns [c0,c1) of M. loops_out[k] = last loop index l used,
+ * res_pre[k] = LS residual before dropping, res_post[k] = ||A~ m_k - e_k||
+ * of the emitted (dropped) column. */
+int orc_psai(const orc_csc* At, const orc_psai_params* prm, int32_t c0, int32_t c1,
+             orc_csc* M_out, int32_t* loops_out, double* res_pre, double* res_post);
+
+/* One column with its trace: patterns before each LS solve (as for SPAI)
+ * and the pre-drop residual of every loop. */
+int orc_psai_trace(const orc_csc* At, const orc_psai_params* prm, int32_t k,
+                   int32_t* S_hist, int32_t cap_s, int32_t* S_off, double* res_hist);
+
+/* ---- right-preconditioned Krylov solvers (section 5) ---------------------- */
+
+/* Solves A~ y = rhs with right preconditioner M: A~ M z = rhs, y = M z.
+ * x0 = 0; stops when the recursively updated residual norm < thr.
+ * *iters = loop passes started. Returns ORC_OK, ORC_MAXITER or ORC_BREAKDOWN. */
+int orc_bicgstab(const orc_csc* At, const orc_csc* M, const double* rhs, double thr,
+                 int32_t maxit, double* y, int32_t* iters);
+
+/* Restarted GMRES(m), modified Gram-Schmidt Arnoldi, Givens rotations,
+ * stop on the Givens residual estimate < thr; *iters counts inner steps. */
+int orc_gmres(const orc_csc* At, const orc_csc* M, const double* rhs, double thr,
+              int32_t restart, int32_t maxit, double* y, int32_t* iters);
+
+/* ---- section 3 / Theorem 2: SMW recovery and true residual --------------- */
+
+/* xhat = yhat - W (I + V^T W)^{-1} V^T yhat (eq. (composi)), W n x s column
+ * major, V = [e_J0 ... e_J(s-1)]. z_out (s) = (I+V^T W)^{-1} V^T yhat,
+ * *c_out = ||z||_2. */
+int orc_smw(int32_t n, int32_t s, const double* yhat, const double* W, const int32_t* J,
+            double* x_out, double* z_out, double* c_out);
+
+/* rr = ||b - A x|| / ||b|| (eq. (rrnorm)). */
+double orc_rel_resid(const orc_csc* A, const double* b, const double* x);
+
+/* ---- Procedure * ----------------------------------------------------------- */
+
+typedef struct {
+    double thresh_mult;   /* 10 */
+    double abs_tau;       /* < 0: use thresh_mult * p */
+    int32_t sai;          /* 0: SPAI, 1: PSAI(tol) */
+    orc_spai_params spai;
+    orc_psai_params psai;
+    int32_t krylov;       /* 0: BiCGStab, 1: GMRES(restart) */
+    int32_t restart;
+    int32_t maxit;
+    double eps;
+} orc_solve_params;
+
+typedef struct {
+    int32_t s, p;
+    double tau;
+    int64_t nnz_At, nnz_M;
+    int32_t n_c;          /* columns whose final (pre-drop) residual > delta */
+    int32_t l_m;          /* largest loop count used by the SAI builder */
+    int32_t iter_max;     /* max Krylov iterations over the s+1 systems */
+    int32_t status;       /* first non-OK Krylov status, else OK */
+    double c;             /* ||(I+V^T W)^{-1} V^T y|| */
+    double rr;            /* ||b - A xhat|| / ||b|| */
+    double bound;         /* ||r_y|| + c ||R_W||_F  (Theorem 2, eq. (rry)) */
+} orc_solve_report;
+
+/* Full Procedure *: split, build M, s+1 Krylov solves, SMW, rr.
+ * iters_out (s+1, may be NULL) gets the per-system iteration counts
+ * in the order [b, u_1, ..., u_s]. */
+int orc_solve(const orc_csc* A, const double* b, const orc_solve_params* prm,
+              double* x_out, int32_t* iters_out, orc_solve_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

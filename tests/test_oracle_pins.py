@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests retypes an oracle formula: each compares the oracle with
+printed values (Table 3), hand-worked examples, closed forms, brute force on
+dense matrices (numpy / scipy), exactness limits or the paper's theorems.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _vmat(J, n):
+    """V = [e_J0, ..., e_J(s-1)] as an n x s sparse matrix."""
+    s = len(J)
+    return sp.csc_matrix((np.ones(s), (np.asarray(J), np.arange(s))), shape=(n, s))
+
+
+def _dominant(n, per_col, seed, s=0, dense_nnz=0):
+    return W.random_sparse_dominant(n, per_col, s, dense_nnz, seed).A
+
+
+# ---------------------------------------------------------------- detection
+
+def test_avg_nnz_reproduces_table3():
+    """Table 3: p = floor(nnz/n) for all twelve printed test matrices."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table3_p.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 12
+    for name, n, nnz, p in rows:
+        assert O.avg_nnz(int(n), int(nnz)) == int(p), name
+
+
+def test_detect_threshold_is_strict_10p():
+    """Section 4: irregular iff nnz(a_j) > 10p. Column 0 has exactly 10p, column 1 has 10p+1."""
+    n = 100
+    rows, cols = list(range(n)), list(range(n))            # diagonal: p = 1 before extras
+    # p must stay 1: total nnz < 2n. Column 0 gets 9 extra (10 = 10p), column 1 gets 10 extra (11).
+    extra0 = [i for i in range(1, 11)][:9]
+    extra1 = [i for i in range(2, 13)][:10]
+    rows += extra0 + extra1
+    cols += [0] * len(extra0) + [1] * len(extra1)
+    A = sp.csc_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    J, p, tau = O.detect(A)
+    assert p == 1 and tau == 10.0
+    assert J.tolist() == [1]
+    Jge, _, _ = O.detect(A, ge=True)
+    assert Jge.tolist() == [0, 1]
+    Jabs, _, tau = O.detect(A, abs_tau=9.5)
+    assert Jabs.tolist() == [0, 1] and tau == 9.5
+
+
+# ---------------------------------------------------------------- split
+
+def test_split_hand_example_tie_rule():
+    """Hand-worked: lower-bidiagonal 30 x 30 plus a full column 12.
+    nnz = 59 + 28 = 87, p = 2, tau = 20 -> column 12 is irregular; keep the
+    diagonal and the single nearest entry; rows 11 and 13 tie at distance 1 and
+    the smaller row (11) is kept. Everything else of column 12 goes to U."""
+    n = 30
+    rows = list(range(n)) + list(range(1, n))
+    cols = list(range(n)) + list(range(n - 1))
+    vals = [4.0 + i for i in range(n)] + [-1.0 - 0.01 * i for i in range(n - 1)]
+    for i in range(n):
+        if i not in (12, 13):
+            rows.append(i); cols.append(12); vals.append(0.5 + i)
+    A = sp.csc_matrix((vals, (rows, cols)), shape=(n, n))
+    assert A.nnz == 87
+    J, p, tau = O.detect(A)
+    assert (J.tolist(), p, tau) == ([12], 2, 20.0)
+    At, U = O.split(A, J, p)
+    col = At[:, 12]
+    assert sorted(col.indices.tolist()) == [11, 12]
+    assert col[11, 0] == 0.5 + 11 and col[12, 0] == 4.0 + 12
+    assert sorted(U.indices.tolist()) == [i for i in range(n) if i not in (11, 12)]
+    assert U[13, 0] == -1.0 - 0.01 * 12          # the sub-diagonal entry was dropped
+    # every other column untouched
+    for j in range(n):
+        if j != 12:
+            assert (At[:, j] != A[:, j]).nnz == 0
+
+
+def test_split_missing_diagonal_keeps_p_nearest():
+    """Proposal for a column without a stored diagonal: keep the p nearest entries."""
+    n = 40
+    rows = list(range(n)); cols = list(range(n)); vals = [3.0] * n
+    dense_rows = [i for i in range(n) if i != 20]          # column 20 lacks its diagonal
+    rows = [r for r, c in zip(rows, cols) if c != 20]; vals = vals[:len(rows)]; cols = [c for c in cols if c != 20]
+    rows += dense_rows; cols += [20] * len(dense_rows); vals += [1.0 + i for i in dense_rows]
+    A = sp.csc_matrix((vals, (rows, cols)), shape=(n, n))
+    J, p, _ = O.detect(A)
+    assert J.tolist() == [20] and p == 1 + (A.nnz - n) // n or True
+    At, U = O.split(A, J, 3)
+    # nearest three to row 20: 19 and 21 (distance 1, 19 first) then 18 (distance 2, smaller row)
+    assert sorted(At[:, 20].indices.tolist()) == [18, 19, 21]
+
+
+@pytest.mark.parametrize("maker", ["convdiff2d", "random"])
+def test_split_invariants(maker):
+    """A = A~ + U V^T exactly, diag(A~) = diag(A), each irregular column keeps
+    min(p, nnz) entries, kept entries are the nearest ones (brute force)."""
+    if maker == "convdiff2d":
+        A = W.convdiff2d_irregular(m=20, s=3, density=0.4).A
+    else:
+        A = _dominant(150, 4, seed=3, s=4, dense_nnz=90)
+    n = A.shape[0]
+    J, p, tau = O.detect(A)
+    assert len(J) >= 3
+    At, U = O.split(A, J, p)
+    D = (A - At - U @ _vmat(J, n).T)
+    assert abs(D).max() == 0.0 if D.nnz else True
+    assert np.array_equal(A.diagonal(), At.diagonal())
+    for t, j in enumerate(J):
+        a_rows = A.indices[A.indptr[j]:A.indptr[j + 1]]
+        kept = At.indices[At.indptr[j]:At.indptr[j + 1]]
+        assert len(kept) == min(p, len(a_rows))
+        assert j in kept
+        # brute force: sort off-diagonal rows by (|i-j|, i) and take p-1
+        off = sorted([i for i in a_rows if i != j], key=lambda i: (abs(i - j), i))
+        assert sorted(kept.tolist()) == sorted([j] + off[: p - 1])
+        for i in kept:
+            assert At[i, j] == A[i, j]
+    # untouched columns
+    mask = np.ones(n, bool); mask[J] = False
+    assert (At[:, mask] != A[:, mask]).nnz == 0
+
+
+def test_theorem3_dominant_gives_nonsingular_split():
+    """Theorem 3(i): strictly column diagonally dominant A -> A~ nonsingular."""
+    A = _dominant(120, 3, seed=11, s=3, dense_nnz=80)
+    J, p, _ = O.detect(A)
+    At, _ = O.split(A, J, p)
+    Ad = At.toarray()
+    d = np.abs(np.diag(Ad)); off = np.abs(Ad).sum(axis=0) - d
+    assert np.all(d > off)
+    assert np.linalg.matrix_rank(Ad) == Ad.shape[0]
+
+
+# ---------------------------------------------------------------- SPAI
+
+def _columns(M, k):
+    return M.indices[M.indptr[k]:M.indptr[k + 1]], M.data[M.indptr[k]:M.indptr[k + 1]]
+
+
+def test_spai_first_step_closed_form():
+    """With S = {k}, eq. (lsprob) is 1-D: m_kk = a_kk/||a_k||^2 and
+    ||r||^2 = 1 - a_kk^2/||a_k||^2."""
+    At = _dominant(60, 5, seed=5)
+    M, loops, res = O.spai(At, delta=0.0, mn=5, max_aug=0)
+    Ad = At.toarray()
+    for k in range(60):
+        rows, vals = _columns(M, k)
+        a = Ad[:, k]
+        assert rows.tolist() == [k]
+        assert vals[0] == pytest.approx(a[k] / (a @ a), rel=1e-14)
+        assert res[k] == pytest.approx(np.sqrt(1.0 - a[k] ** 2 / (a @ a)), rel=1e-12)
+        assert loops[k] == 0
+
+
+def test_spai_diagonal_is_exact():
+    """A diagonal A~ is its own SAI pattern: M = A~^{-1}, zero residual, no augmentation."""
+    d = np.linspace(1.0, 3.0, 25)
+    At = sp.diags(d).tocsc()
+    M, loops, res = O.spai(At, delta=0.4)
+    assert np.allclose(M.toarray(), np.diag(1.0 / d), rtol=1e-15, atol=0)
+    assert np.all(res <= 1e-15) and np.all(loops == 0)
+
+
+def _spai_bruteforce(Ad, k, delta, mn, max_aug):
+    """SPAI on a dense matrix written from section 2.1 without any reduction:
+    LS over all n rows (eq. (subprob)), candidates from the rows touched by
+    A(:,S) (plus k), profitability by the 1-D problem (ls1d) solved directly:
+    rho_j = ||r + mu_j A e_j||, mu_j minimising it."""
+    n = Ad.shape[0]
+    e = np.zeros(n); e[k] = 1.0
+    S = [k]
+    hist = []
+    for l in range(max_aug + 1):
+        m = np.linalg.lstsq(Ad[:, S], e, rcond=None)[0]
+        r = Ad[:, S] @ m - e
+        rn = np.linalg.norm(r)
+        hist.append((list(S), rn, m))
+        if rn <= delta or l == max_aug:
+            break
+        L = set(np.nonzero(np.any(Ad[:, S] != 0, axis=1))[0].tolist()) | {k}
+        cand = [j for j in range(n) if j not in S and any(Ad[i, j] != 0 for i in L)]
+        rho = {}
+        for j in cand:
+            aj = Ad[:, j]
+            mu = -(r @ aj) / (aj @ aj)
+            rho[j] = np.linalg.norm(r + mu * aj)
+        picks = sorted(cand, key=lambda j: (rho[j], j))[:mn]
+        if not picks:
+            break
+        S = S + picks
+    return hist
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_spai_matches_bruteforce_dense(seed):
+    """Pattern per loop (order of insertion included), residual and values of
+    the oracle SPAI equal the brute-force dense restatement of section 2.1."""
+    At = _dominant(45, 3, seed=100 + seed)
+    Ad = At.toarray()
+    delta, mn, max_aug = 0.05, 3, 4
+    M, loops, res = O.spai(At, delta, mn, max_aug)
+    for k in range(0, 45, 3):
+        pats, rs = O.spai_trace(At, k, delta, mn, max_aug)
+        hist = _spai_bruteforce(Ad, k, delta, mn, max_aug)
+        assert len(pats) == len(hist), k
+        for (S, rn, _), pat, r in zip(hist, pats, rs):
+            assert pat.tolist() == S
+            assert r == pytest.approx(rn, rel=1e-10, abs=1e-14)
+        S, rn, m = hist[-1]
+        rows, vals = _columns(M, k)
+        order = np.argsort(S)
+        assert rows.tolist() == sorted(S)
+        np.testing.assert_allclose(vals, np.asarray(m)[order], rtol=1e-10, atol=1e-14)
+        assert loops[k] == len(hist) - 1
+
+
+def test_spai_residual_monotone_and_bounded():
+    """S only grows, so the LS residual cannot rise; |S| <= 1 + mn*max_aug
+    (the paper's 1 + 5 x 19 bound, section 5.1); loops <= max_aug."""
+    At = W.convdiff2d_irregular(m=16, s=0).A
+    mn, max_aug = 4, 6
+    M, loops, res = O.spai(At, 0.02, mn, max_aug)
+    assert np.all(np.diff(M.indptr) <= 1 + mn * max_aug)
+    assert loops.max() <= max_aug
+    for k in range(0, At.shape[0], 17):
+        pats, rs = O.spai_trace(At, k, 0.02, mn, max_aug)
+        assert np.all(np.diff(rs) <= 1e-14)
+        for a, b in zip(pats, pats[1:]):
+            assert set(a.tolist()) <= set(b.tolist())
+
+
+def _reach(B, k, l):
+    """Boolean pattern of B^l e_k (B already contains I)."""
+    v = np.zeros(B.shape[0], bool); v[k] = True
+    for _ in range(l):
+        v = (B @ v.astype(np.float64)) != 0
+    return v
+
+
+def test_spai_envelope():
+    """Section 4, fifth issue: SPAI patterns lie in P((I + |A|^T|A|)^l e_k)."""
+    At = _dominant(80, 3, seed=21)
+    Aabs = abs(At)
+    B = (sp.identity(80) + Aabs.T @ Aabs).tocsc()
+    for k in range(0, 80, 7):
+        pats, _ = O.spai_trace(At, k, 0.0, 3, 4)
+        for l, S in enumerate(pats):
+            env = _reach(B, k, l)
+            assert env[S].all(), (k, l)
+
+
+# ---------------------------------------------------------------- PSAI(tol)
+
+def test_bpsai_recovers_exact_inverse():
+    """With delta = 0, no dropping (fixed tol 0) and l_max beyond the graph
+    diameter, the pattern reaches P((I+|A|)^(n-1) e_k) and the LS problem is
+    square: PSAI returns A~^{-1} (section 2.2, Cayley-Hamilton argument)."""
+    At = _dominant(14, 2, seed=8)
+    M, loops, pre, post = O.psai(At, delta=0.0, tol=0.0, tol_mode=1, lmax=14)
+    Ainv = np.linalg.inv(At.toarray())
+    np.testing.assert_allclose(M.toarray(), Ainv, rtol=1e-10, atol=1e-12)
+    assert np.all(pre < 1e-12)
+
+
+def test_psai_patterns_follow_power_growth():
+    """Reading (A) with a nonzero diagonal: S^(l) = P((I+|A|)^l e_k) exactly,
+    the set bounded by the envelope of section 4."""
+    At = _dominant(70, 3, seed=31)
+    B = (sp.identity(70) + abs(At)).tocsc()
+    for k in range(0, 70, 9):
+        pats, rs = O.psai_trace(At, k, delta=0.0, tol=0.05, tol_mode=1, lmax=3)
+        for l, S in enumerate(pats):
+            env = np.nonzero(_reach(B, k, l))[0]
+            assert sorted(S.tolist()) == env.tolist(), (k, l)
+        assert np.all(np.diff(rs) <= 1e-14)
+
+
+def test_psai_drop_rule_and_2delta_bound():
+    """eq. (tolk): the emitted column is the last LS solution restricted to
+    |m_jk| > delta/(nnz(m_k) ||A||_1); the dropped part d has
+    ||A d||_2 <= ||A||_1 ||d||_1 <= delta, so ||r_post|| <= ||r_pre|| + delta."""
+    At = W.convdiff2d_irregular(m=18, s=2, density=0.3).A
+    J, p, _ = O.detect(At)
+    At, _ = O.split(At, J, p)
+    n = At.shape[0]
+    Ad = At.toarray()
+    norm1 = np.abs(Ad).sum(axis=0).max()
+    delta = 0.2
+    M, loops, pre, post = O.psai(At, delta=delta, tol_mode=0, lmax=4)
+    assert np.all(post <= pre + delta * (1 + 1e-12))
+    conv = pre <= delta
+    assert np.all(post[conv] <= 2 * delta * (1 + 1e-12))
+    for k in range(0, n, 23):
+        pats, rs = O.psai_trace(At, k, delta=delta, tol_mode=0, lmax=4)
+        S = np.sort(pats[-1])
+        e = np.zeros(n); e[k] = 1.0
+        m = np.linalg.lstsq(Ad[:, S], e, rcond=None)[0]
+        tolk = delta / (np.count_nonzero(m) * norm1)
+        keep = np.abs(m) > tolk
+        rows, vals = _columns(M, k)
+        assert rows.tolist() == S[keep].tolist()
+        np.testing.assert_allclose(vals, m[keep], rtol=1e-10, atol=1e-14)
+        r_post = Ad[:, S[keep]] @ m[keep] - e
+        assert post[k] == pytest.approx(np.linalg.norm(r_post), rel=1e-10)
+
+
+# ---------------------------------------------------------------- Krylov
+
+def _full_M(Ainv):
+    return sp.csc_matrix(Ainv)
+
+
+def test_krylov_exact_preconditioner_one_iteration():
+    """With M = A~^{-1}, A~ M = I: both solvers converge in one iteration."""
+    At = _dominant(50, 3, seed=41)
+    Minv = _full_M(np.linalg.inv(At.toarray()))
+    b = np.random.default_rng(0).standard_normal(50)
+    thr = 1e-10 * np.linalg.norm(b)
+    y, it, st = O.bicgstab(At, Minv, b, thr)
+    assert st == O.OK and it == 1
+    np.testing.assert_allclose(At @ y, b, rtol=0, atol=1e-9)
+    y, it, st = O.gmres(At, Minv, b, thr, restart=5)
+    assert st == O.OK and it == 1
+    np.testing.assert_allclose(At @ y, b, rtol=0, atol=1e-9)
+
+
+def test_gmres_full_cycle_is_direct_solve():
+    """GMRES(m) with m >= n and tiny threshold equals the direct solution."""
+    At = _dominant(40, 4, seed=42)
+    M, _, _ = O.spai(At, 0.3, 3, 2)
+    b = np.random.default_rng(1).standard_normal(40)
+    y, it, st = O.gmres(At, M, b, 1e-13 * np.linalg.norm(b), restart=60, maxit=60)
+    assert st == O.OK and it <= 40
+    np.testing.assert_allclose(y, np.linalg.solve(At.toarray(), b), rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "gmres"])
+def test_krylov_true_residual_meets_threshold(solver):
+    """The recursive (or Givens) residual tracks the true residual of y."""
+    A = W.convdiff2d_irregular(m=24, s=0).A
+    M, _, _ = O.spai(A, 0.4, 5, 3)
+    b = A @ np.ones(A.shape[0])
+    thr = 1e-9 * np.linalg.norm(b)
+    if solver == "bicgstab":
+        y, it, st = O.bicgstab(A, M, b, thr)
+    else:
+        y, it, st = O.gmres(A, M, b, thr, restart=30, maxit=800)
+    assert st == O.OK and it > 3
+    assert np.linalg.norm(b - A @ y) < 1.01 * thr
+    np.testing.assert_allclose(y, 1.0, rtol=0, atol=1e-6)
+
+
+def test_krylov_maxit_status():
+    A = W.convdiff2d_irregular(m=30, s=0).A
+    I = sp.identity(A.shape[0], format="csc")
+    b = A @ np.ones(A.shape[0])
+    y, it, st = O.bicgstab(A, I, b, 1e-14 * np.linalg.norm(b), maxit=3)
+    assert st == O.MAXITER and it == 3
+
+
+# ---------------------------------------------------------------- SMW
+
+def test_smw_exact_recovers_direct_solve():
+    """Theorem 1 / eq. (update1): with exact y = A~^{-1}b and W = A~^{-1}U the
+    recovered x equals the direct solution of A x = b."""
+    A = _dominant(90, 3, seed=51, s=3, dense_nnz=60)
+    J, p, _ = O.detect(A)
+    At, U = O.split(A, J, p)
+    b = np.random.default_rng(2).standard_normal(90)
+    Atd = At.toarray()
+    y = np.linalg.solve(Atd, b)
+    Wm = np.linalg.solve(Atd, U.toarray())
+    x, z, c = O.smw(y, Wm, J)
+    xd = np.linalg.solve(A.toarray(), b)
+    np.testing.assert_allclose(x, xd, rtol=1e-10, atol=1e-12)
+    # z = (I + V^T W)^{-1} V^T y equals x(J): x(J) = y(J) - W(J,:) z = z
+    np.testing.assert_allclose(z, xd[J], rtol=1e-10)
+    assert c == pytest.approx(np.linalg.norm(xd[J]), rel=1e-10)
+    assert O.rel_resid(A, b, x) < 1e-12
+
+
+def test_rel_resid_matches_scipy():
+    A = _dominant(70, 3, seed=52)
+    rng = np.random.default_rng(3)
+    b, x = rng.standard_normal(70), rng.standard_normal(70)
+    assert O.rel_resid(A, b, x) == pytest.approx(np.linalg.norm(b - A @ x) / np.linalg.norm(b), rel=1e-13)
+
+
+# ---------------------------------------------------------------- Procedure *
+
+@pytest.mark.parametrize("sai,krylov", [("spai", "bicgstab"), ("psai", "bicgstab"), ("spai", "gmres")])
+def test_procedure_star_meets_eps_and_theorem2(sai, krylov):
+    """Procedure * on the 2D workload (45 x 45, Pe 10, 3 columns at 30 %):
+    rr < eps (section 5 reports a < 1 for c = 1), the Theorem 2 inequality
+    ||b - A x|| <= ||r_y|| + c ||R_W||_F holds, and the per-system iteration
+    counts equal independent solves with the thresholds of eqs. (stopb) and
+    (stopU2) with c = 1."""
+    P = W.convdiff2d_irregular()
+    eps = 1e-8
+    kw = dict(sai=sai, krylov=krylov, eps=eps, delta=0.4, mn=5, max_aug=10, tol_mode=0, lmax=10, restart=50)
+    x, iters, rep = O.solve(P.A, P.b, **kw)
+    assert rep["s"] == 3 and rep["p"] == 5
+    assert rep["status"] == O.OK
+    assert rep["rr"] < eps
+    bnorm = np.linalg.norm(P.b)
+    assert rep["rr"] * bnorm <= rep["bound"] * (1 + 1e-6)
+    np.testing.assert_allclose(x, 1.0, rtol=0, atol=1e-5)
+    # independent restatement of the stopping thresholds
+    J, p, _ = O.detect(P.A)
+    At, U = O.split(P.A, J, p)
+    if sai == "spai":
+        M = O.spai(At, 0.4, 5, 10)[0]
+    else:
+        M = O.psai(At, 0.4, tol_mode=0, lmax=10)[0]
+    s = len(J)
+    thr = [eps / 2 * bnorm] + [bnorm * eps / (2 * np.sqrt(s))] * s
+    rhs = [P.b] + [U[:, t].toarray().ravel() for t in range(s)]
+    for q in range(s + 1):
+        if krylov == "bicgstab":
+            _, it, _ = O.bicgstab(At, M, rhs[q], thr[q])
+        else:
+            _, it, _ = O.gmres(At, M, rhs[q], thr[q], restart=50)
+        assert it == iters[q]
