@@ -1,0 +1,231 @@
+/*
+ * saismw.h -- C ABI of the GB300 (sm_103a) implementation of Jia & Zhang's
+ * approach for irregular sparse systems A x = b (arXiv 1211.6866):
+ *
+ *   1. split A = A~ + U V^T              (section 3, eq. (split); section 4)
+ *   2. build M ~ A~^{-1} by SPAI or PSAI  (section 2.1, section 2.2)
+ *   3. solve the s+1 systems A~ y = b, A~ w_j = u_j with right
+ *      preconditioner M                   (eqs. (regprob), (auxi); section 5)
+ *   4. recover x = y - W (I + V^T W)^{-1} V^T y        (eq. (composi))
+ *      with the stopping rules of Theorem 2, eqs. (stopb), (stopU2), c = 1.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers unless the comment says "host".
+ *    The caller owns them; the library never frees or keeps them beyond the
+ *    call (except where a handle documents a copy).
+ *  - Sparse inputs are CSC: col_ptr[n+1] int64 (col_ptr[0] = 0), row_idx[nnz]
+ *    int32 strictly ascending inside each column, val[nnz] double.
+ *  - Dense multi-right-hand-side blocks are n x k ROW-MAJOR (the k values of a
+ *    row are contiguous, element (i,c) at [i*k + c]).
+ *  - Handles own their device buffers and release them in *_destroy.
+ *  - All work is enqueued on `stream`. Calls that return sizes or reports to
+ *    the host synchronise the stream before returning.
+ *  - Errors: the first error is returned; no C++ exception crosses the ABI;
+ *    outputs are unspecified unless SAI_OK is returned, except that
+ *    SAI_MAXITER still returns the last iterates and a filled report.
+ *  - One CUDA device: the device current at the call.
+ */
+#ifndef SAISMW_H
+#define SAISMW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sai_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    SAI_OK = 0,
+    SAI_INVALID_ARG = 1,       /* bad size, NULL pointer, unsorted rows, ... */
+    SAI_CUDA_ERROR = 2,        /* a CUDA runtime call failed */
+    SAI_OOM = 3,               /* device allocation failed */
+    SAI_PATTERN_OVERFLOW = 4,  /* an SAI column outgrew the largest workspace tier */
+    SAI_MAXITER = 5,           /* a Krylov system hit maxit (iterates still returned) */
+    SAI_BREAKDOWN = 6,         /* BiCGStab rho = 0 / omega = 0, GMRES zero pivot */
+    SAI_SINGULAR = 7,          /* singular LS matrix A^_k or singular I + V^T W */
+    SAI_NOT_IMPLEMENTED = 8
+} sai_status;
+
+/* Returns a static, NUL-terminated name for a status code. */
+const char* sai_status_string(sai_status st);
+
+/* View of a caller-owned square CSC matrix on the device. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int64_t* col_ptr;
+    const int32_t* row_idx;
+    const double* val;
+} sai_csc_view;
+
+/* ----------------------------------------------------------------------
+ * Step 1: split (section 4, first dropping approach; eq. (split)).
+ * p = floor(nnz(A)/n). Column j is irregular when nnz(a_j) > tau with
+ * tau = thresh_mult * p (paper: 10, "8p to 15p work as well"), or
+ * tau = abs_tau when abs_tau >= 0; ge != 0 uses >= instead of > (the
+ * "10p or more" wording of section 1). Each irregular column keeps its
+ * diagonal and the p_keep-1 stored entries nearest to it (|i-j| ascending,
+ * ties to the smaller row; p_keep nearest when no diagonal is stored);
+ * p_keep <= 0 means p_keep = p (the paper's choice p^ = p). Dropped entries
+ * form U (n x s), V = [e_J0 ... e_J(s-1)] with J ascending.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double thresh_mult;
+    double abs_tau;
+    int32_t ge;
+    int32_t p_keep;
+} sai_split_params;
+
+typedef struct sai_split_s* sai_split;
+
+typedef struct {
+    int32_t n, s, p, p_keep;
+    double tau;
+    int64_t nnz_At, nnz_U;
+    double norm1_At;  /* ||A~||_1 = max_j sum_i |a~_ij| (used by eq. (tolk)) */
+} sai_split_info;
+
+/* Builds A~ (CSC and CSR), U (CSC) and J on the device from A.
+ * The handle keeps its own copies; A may be freed after the call returns.
+ * Rows must be strictly ascending per column (SAI_INVALID_ARG otherwise). */
+sai_status sai_split_create(const sai_csc_view* A, const sai_split_params* prm,
+                            sai_stream_t stream, sai_split* out);
+sai_status sai_split_get_info(sai_split h, sai_split_info* info);
+/* Copies the split to caller buffers sized from sai_split_get_info
+ * (At: n+1, nnz_At, nnz_At; U: s+1, nnz_U, nnz_U; J: s). NULL pointers are
+ * skipped. */
+sai_status sai_split_copy_out(sai_split h, int64_t* At_col_ptr, int32_t* At_row_idx, double* At_val,
+                              int64_t* U_col_ptr, int32_t* U_row_idx, double* U_val, int32_t* J,
+                              sai_stream_t stream);
+void sai_split_destroy(sai_split h);
+
+/* ----------------------------------------------------------------------
+ * Step 2: sparse approximate inverse M ~ A~^{-1}, min ||A~ M - I||_F,
+ * decoupled into n independent problems min ||A~ m_k - e_k|| (eq. (subprob))
+ * solved through the reduced problems (lsprob) by Householder QR, updated
+ * incrementally as the pattern grows. Initial pattern S_k^(0) = {k}.
+ * The reduced row set L_k always contains k.
+ * ---------------------------------------------------------------------- */
+typedef enum { SAI_FP64 = 0, SAI_FP32_REFINE64 = 1 } sai_precision;
+
+/* SPAI (section 2.1, eqs. (candi), (ls1d), (muj), (rhoj)). Loop: solve,
+ * stop when ||r_k|| <= delta or max_aug augmentation steps were made,
+ * otherwise add the mn candidates j in N \ S (N = columns touching the rows
+ * of L_k) with the smallest keys (floor(rho_j^2/||r_k||^2 * 2^key_bits), j).
+ * key_bits in [1, 31]; 20 is the default reading. */
+typedef struct {
+    double delta;      /* paper: 0.4 (section 5.1) */
+    int32_t mn;        /* paper: 5, at most 8 here */
+    int32_t max_aug;   /* paper: l_max = 20 loops, i.e. 19 augmentations */
+    int32_t key_bits;
+    int32_t precision; /* sai_precision; only SAI_FP64 in this version */
+} sai_spai_params;
+
+/* PSAI(tol) (section 2.2). Loop l = 0..lmax: solve on S^(l), drop
+ * |m_jk| <= tol_k with tol_k = delta/(nnz(m_k) ||A~||_1) (tol_mode 0,
+ * eq. (tolk)) or tol_k = tol (tol_mode 1); stop when the pre-drop residual
+ * <= delta or l = lmax and emit the kept entries of that solution; else
+ * S^(l+1) = P(|A~| a^(l)) u S_kept^(l) with a^(0) = e_k. */
+typedef struct {
+    double delta;      /* paper: 0.4 */
+    double tol;
+    int32_t tol_mode;
+    int32_t lmax;      /* paper: 10 */
+    int32_t precision;
+} sai_psai_params;
+
+typedef struct sai_precond_s* sai_precond;
+
+typedef struct {
+    int32_t n;
+    int64_t nnz_M;
+    int32_t n_c;        /* columns whose final (pre-drop) residual > delta */
+    int32_t l_m;        /* largest loop index used over all columns */
+    int32_t n_tier[3];  /* columns finished per workspace tier */
+    double build_ms;    /* device time of the build, CUDA events */
+} sai_precond_info;
+
+sai_status sai_build_spai(sai_split h, const sai_spai_params* prm, sai_stream_t stream, sai_precond* out);
+sai_status sai_build_psai(sai_split h, const sai_psai_params* prm, sai_stream_t stream, sai_precond* out);
+sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info);
+/* M as CSC (rows ascending per column): col_ptr n+1, row_idx/val nnz_M.
+ * loops[n]: augmentation steps (SPAI) or last loop index (PSAI).
+ * res[n]: final LS residual (pre-drop for PSAI). res_post[n] (PSAI only,
+ * else zeros): ||A~ m_k - e_k|| of the emitted column. NULLs skipped. */
+sai_status sai_precond_copy_out(sai_precond P, int64_t* col_ptr, int32_t* row_idx, double* val,
+                                int32_t* loops, double* res, double* res_post, sai_stream_t stream);
+void sai_precond_destroy(sai_precond P);
+
+/* ----------------------------------------------------------------------
+ * Step 3: k systems A~ X(:,c) = B(:,c) solved together, right
+ * preconditioned (A~ M z = b, x = M z), x0 = 0, one SpMM with A~ and one
+ * with M per operator application for all right-hand sides at once.
+ * System c stops when its residual norm < thr[c] (host array); converged
+ * systems are frozen. BiCGStab tests after the half and the full step (a
+ * half-step exit counts a full iteration); GMRES(restart) tests the Givens
+ * residual estimate and restarts from the true residual.
+ * ---------------------------------------------------------------------- */
+typedef enum { SAI_BICGSTAB = 0, SAI_GMRES = 1 } sai_krylov_method;
+
+typedef struct {
+    int32_t method;
+    int32_t restart;   /* GMRES(m); ignored by BiCGStab */
+    int32_t maxit;     /* paper: 500 */
+} sai_krylov_params;
+
+/* B, X: n x k row-major device blocks. thr, iters, status: host arrays of k.
+ * Returns SAI_OK, SAI_MAXITER or SAI_BREAKDOWN (the first non-OK system
+ * status), or an error. Synchronises the stream. */
+sai_status sai_krylov_solve(sai_split h, sai_precond P, int32_t k, const double* B, const double* thr,
+                            const sai_krylov_params* prm, double* X, int32_t* iters, int32_t* status,
+                            sai_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * Step 4: SMW recovery, eq. (composi):
+ *   xhat = yhat - What (I + V^T What)^{-1} (V^T yhat)
+ * Y: n x (s+1) row-major, column 0 = yhat, columns 1..s = What.
+ * x: n. c_out (host, may be NULL): c = ||(I + V^T What)^{-1} V^T yhat||.
+ * Gaussian elimination with partial pivoting on the s x s matrix.
+ * ---------------------------------------------------------------------- */
+sai_status sai_smw_recover(sai_split h, const double* Y, double* x, double* c_out, sai_stream_t stream);
+
+/* rr = ||b - A x|| / ||b|| (eq. (rrnorm)) for a caller CSC matrix;
+ * rr_out is a host pointer. Synchronises the stream. */
+sai_status sai_rel_resid(const sai_csc_view* A, const double* b, const double* x, double* rr_out,
+                         sai_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * Procedure *: split, build M, the s+1 solves with the Theorem 2
+ * thresholds ||r_y|| < (eps/2)||b|| and ||r_wj|| < eps ||b|| / (2 sqrt(s)),
+ * SMW recovery and rr. b, x: device n-vectors.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    sai_split_params split;
+    int32_t sai;                  /* 0: SPAI, 1: PSAI(tol) */
+    sai_spai_params spai;
+    sai_psai_params psai;
+    sai_krylov_params krylov;
+    double eps;                   /* paper: 1e-8 */
+} sai_solve_params;
+
+typedef struct {
+    sai_split_info split;
+    sai_precond_info precond;
+    int32_t status;               /* worst Krylov status (sai_status) */
+    int32_t iter_max;             /* max iterations over the s+1 systems */
+    double c;
+    double rr;                    /* ||b - A xhat|| / ||b|| */
+    double ms_split, ms_build, ms_krylov, ms_smw;  /* device time per step */
+} sai_solve_report;
+
+/* iters (host, may be NULL): s+1 iteration counts in the order [b, u_1..u_s];
+ * pass capacity in iters_cap (counts beyond it are not written). */
+sai_status sai_solve(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
+                     int32_t* iters, int32_t iters_cap, sai_solve_report* rep, sai_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAISMW_H */

@@ -1,0 +1,305 @@
+"""Python binding of ``libsaismw.so`` (C ABI in ``include/saismw.h``).
+
+Argument marshalling only: every step of split, SAI build, Krylov solves,
+SMW recovery and residual check runs in the library's CUDA kernels. PyTorch
+provides device memory and the current CUDA stream. There is no CPU fallback:
+if the compiled library cannot be loaded or no CUDA device is present, the
+calls raise.
+
+Layouts (see the header): sparse matrices are CSC with int64 column pointers,
+int32 row indices ascending per column, float64 values; multi-right-hand-side
+blocks are n x k row-major float64 tensors.
+"""
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+__all__ = ["CscMatrix", "SaiError", "split", "build_spai", "build_psai", "krylov_solve", "smw_recover",
+           "rel_resid", "solve", "library_path", "load"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libsaismw.so")
+
+SAI_OK, SAI_INVALID_ARG, SAI_CUDA_ERROR, SAI_OOM, SAI_PATTERN_OVERFLOW, SAI_MAXITER, SAI_BREAKDOWN, \
+    SAI_SINGULAR, SAI_NOT_IMPLEMENTED = range(9)
+BICGSTAB, GMRES = 0, 1
+
+
+class SaiError(RuntimeError):
+    def __init__(self, what, status):
+        name = _lib.sai_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__("%s failed: %s" % (what, name))
+        self.status = status
+
+
+# ---------------------------------------------------------------- ctypes mirror of saismw.h
+class _CscView(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class _SplitParams(C.Structure):
+    _fields_ = [("thresh_mult", C.c_double), ("abs_tau", C.c_double), ("ge", C.c_int32), ("p_keep", C.c_int32)]
+
+
+class _SplitInfo(C.Structure):
+    _fields_ = [("n", C.c_int32), ("s", C.c_int32), ("p", C.c_int32), ("p_keep", C.c_int32), ("tau", C.c_double),
+                ("nnz_At", C.c_int64), ("nnz_U", C.c_int64), ("norm1_At", C.c_double)]
+
+
+class _SpaiParams(C.Structure):
+    _fields_ = [("delta", C.c_double), ("mn", C.c_int32), ("max_aug", C.c_int32), ("key_bits", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+class _PsaiParams(C.Structure):
+    _fields_ = [("delta", C.c_double), ("tol", C.c_double), ("tol_mode", C.c_int32), ("lmax", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+class _PrecondInfo(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz_M", C.c_int64), ("n_c", C.c_int32), ("l_m", C.c_int32),
+                ("n_tier", C.c_int32 * 3), ("build_ms", C.c_double)]
+
+
+class _KrylovParams(C.Structure):
+    _fields_ = [("method", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32)]
+
+
+class _SolveParams(C.Structure):
+    _fields_ = [("split", _SplitParams), ("sai", C.c_int32), ("spai", _SpaiParams), ("psai", _PsaiParams),
+                ("krylov", _KrylovParams), ("eps", C.c_double)]
+
+
+class _SolveReport(C.Structure):
+    _fields_ = [("split", _SplitInfo), ("precond", _PrecondInfo), ("status", C.c_int32), ("iter_max", C.c_int32),
+                ("c", C.c_double), ("rr", C.c_double), ("ms_split", C.c_double), ("ms_build", C.c_double),
+                ("ms_krylov", C.c_double), ("ms_smw", C.c_double)]
+
+
+_lib = None
+
+
+def library_path():
+    return _LIBPATH
+
+
+def load():
+    """Load libsaismw.so (it must have been built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise ImportError("libsaismw.so not built: run __graft_entry__.build() (no CPU fallback exists)")
+    L = C.CDLL(_LIBPATH)
+    vp, i32, dp = C.c_void_p, C.c_int32, C.c_void_p
+    L.sai_status_string.restype = C.c_char_p
+    L.sai_status_string.argtypes = [C.c_int]
+    L.sai_split_create.argtypes = [C.POINTER(_CscView), C.POINTER(_SplitParams), vp, C.POINTER(vp)]
+    L.sai_split_get_info.argtypes = [vp, C.POINTER(_SplitInfo)]
+    L.sai_split_copy_out.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, vp]
+    L.sai_split_destroy.argtypes = [vp]
+    L.sai_split_destroy.restype = None
+    L.sai_build_spai.argtypes = [vp, C.POINTER(_SpaiParams), vp, C.POINTER(vp)]
+    L.sai_build_psai.argtypes = [vp, C.POINTER(_PsaiParams), vp, C.POINTER(vp)]
+    L.sai_precond_get_info.argtypes = [vp, C.POINTER(_PrecondInfo)]
+    L.sai_precond_copy_out.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
+    L.sai_precond_destroy.argtypes = [vp]
+    L.sai_precond_destroy.restype = None
+    L.sai_krylov_solve.argtypes = [vp, vp, i32, dp, C.POINTER(C.c_double), C.POINTER(_KrylovParams), dp,
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp]
+    L.sai_smw_recover.argtypes = [vp, dp, dp, C.POINTER(C.c_double), vp]
+    L.sai_rel_resid.argtypes = [C.POINTER(_CscView), dp, dp, C.POINTER(C.c_double), vp]
+    L.sai_solve.argtypes = [C.POINTER(_CscView), dp, C.POINTER(_SolveParams), dp, C.POINTER(C.c_int32), i32,
+                            C.POINTER(_SolveReport), vp]
+    for f in ("sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
+              "sai_precond_get_info", "sai_precond_copy_out", "sai_krylov_solve", "sai_smw_recover",
+              "sai_rel_resid", "sai_solve"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _stream():
+    if not torch.cuda.is_available():
+        raise RuntimeError("saismw needs a CUDA device; there is no CPU fallback")
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(what, st, allow=()):
+    if st != SAI_OK and st not in allow:
+        raise SaiError(what, st)
+    return st
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+@dataclass
+class CscMatrix:
+    """Square CSC matrix on the device (int64 col_ptr, int32 row_idx, float64 val)."""
+    n: int
+    col_ptr: torch.Tensor
+    row_idx: torch.Tensor
+    val: torch.Tensor
+
+    @staticmethod
+    def from_arrays(indptr, indices, data, n, device="cuda"):
+        return CscMatrix(int(n), torch.as_tensor(indptr, dtype=torch.int64).to(device).contiguous(),
+                         torch.as_tensor(indices, dtype=torch.int32).to(device).contiguous(),
+                         torch.as_tensor(data, dtype=torch.float64).to(device).contiguous())
+
+    @property
+    def nnz(self):
+        return int(self.row_idx.numel())
+
+    def view(self):
+        return _CscView(self.n, self.nnz, _p(self.col_ptr).value, _p(self.row_idx).value, _p(self.val).value)
+
+
+class Split:
+    """Handle of a split A = A~ + U V^T held on the device."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+        info = _SplitInfo()
+        _check("sai_split_get_info", load().sai_split_get_info(self._h, C.byref(info)))
+        self.n, self.s, self.p, self.p_keep = info.n, info.s, info.p, info.p_keep
+        self.tau, self.nnz_At, self.nnz_U, self.norm1_At = info.tau, info.nnz_At, info.nnz_U, info.norm1_At
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.sai_split_destroy(self._h)
+            self._h = None
+
+    def arrays(self):
+        """(At: CscMatrix, U: (col_ptr, row_idx, val), J) as device tensors."""
+        dev = "cuda"
+        at = (torch.empty(self.n + 1, dtype=torch.int64, device=dev),
+              torch.empty(self.nnz_At, dtype=torch.int32, device=dev),
+              torch.empty(self.nnz_At, dtype=torch.float64, device=dev))
+        u = (torch.empty(self.s + 1, dtype=torch.int64, device=dev),
+             torch.empty(self.nnz_U, dtype=torch.int32, device=dev),
+             torch.empty(self.nnz_U, dtype=torch.float64, device=dev))
+        J = torch.empty(self.s, dtype=torch.int32, device=dev)
+        _check("sai_split_copy_out", load().sai_split_copy_out(self._h, *[_p(t) for t in at + u], _p(J), _stream()))
+        torch.cuda.current_stream().synchronize()
+        return CscMatrix(self.n, *at), u, J
+
+
+class Precond:
+    """Handle of a sparse approximate inverse M held on the device."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+        info = _PrecondInfo()
+        _check("sai_precond_get_info", load().sai_precond_get_info(self._h, C.byref(info)))
+        self.n, self.nnz, self.n_c, self.l_m = info.n, info.nnz_M, info.n_c, info.l_m
+        self.n_tier = list(info.n_tier)
+        self.build_ms = info.build_ms
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.sai_precond_destroy(self._h)
+            self._h = None
+
+    def arrays(self):
+        """(M: CscMatrix, loops, res, res_post) as device tensors."""
+        dev = "cuda"
+        cp = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        ri = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        v = torch.empty(self.nnz, dtype=torch.float64, device=dev)
+        loops = torch.empty(self.n, dtype=torch.int32, device=dev)
+        res = torch.empty(self.n, dtype=torch.float64, device=dev)
+        post = torch.empty(self.n, dtype=torch.float64, device=dev)
+        _check("sai_precond_copy_out", load().sai_precond_copy_out(self._h, _p(cp), _p(ri), _p(v), _p(loops),
+                                                                   _p(res), _p(post), _stream()))
+        torch.cuda.current_stream().synchronize()
+        return CscMatrix(self.n, cp, ri, v), loops, res, post
+
+
+def split(A, thresh_mult=10.0, abs_tau=-1.0, ge=False, p_keep=0):
+    """Step 1 of Procedure *: detect the irregular columns and split A = A~ + U V^T."""
+    L = load()
+    h = C.c_void_p()
+    v = A.view()
+    prm = _SplitParams(thresh_mult, abs_tau, int(ge), int(p_keep))
+    _check("sai_split_create", L.sai_split_create(C.byref(v), C.byref(prm), _stream(), C.byref(h)))
+    return Split(h.value)
+
+
+def build_spai(sp, delta=0.4, mn=5, max_aug=10, key_bits=20):
+    L = load()
+    h = C.c_void_p()
+    prm = _SpaiParams(delta, mn, max_aug, key_bits, 0)
+    _check("sai_build_spai", L.sai_build_spai(sp._h, C.byref(prm), _stream(), C.byref(h)))
+    return Precond(h.value)
+
+
+def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10):
+    L = load()
+    h = C.c_void_p()
+    prm = _PsaiParams(delta, tol, tol_mode, lmax, 0)
+    _check("sai_build_psai", L.sai_build_psai(sp._h, C.byref(prm), _stream(), C.byref(h)))
+    return Precond(h.value)
+
+
+def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500):
+    """Solves A~ X = B (n x k, row-major, device) with right preconditioner M.
+    Returns (X, iters list, status list, overall status)."""
+    L = load()
+    B = B.contiguous()
+    n, k = B.shape
+    X = torch.empty_like(B)
+    thr_a = (C.c_double * k)(*[float(t) for t in thr])
+    it = (C.c_int32 * k)()
+    stt = (C.c_int32 * k)()
+    prm = _KrylovParams(method, restart, maxit)
+    st = _check("sai_krylov_solve", L.sai_krylov_solve(sp._h, P._h, k, _p(B), thr_a, C.byref(prm), _p(X), it, stt,
+                                                       _stream()), allow=(SAI_MAXITER, SAI_BREAKDOWN))
+    return X, list(it), list(stt), st
+
+
+def smw_recover(sp, Y):
+    """x = y - W (I + V^T W)^{-1} V^T y with Y = [y, W] (n x (s+1) row-major). Returns (x, c)."""
+    L = load()
+    Y = Y.contiguous()
+    x = torch.empty(Y.shape[0], dtype=torch.float64, device=Y.device)
+    c = C.c_double()
+    _check("sai_smw_recover", L.sai_smw_recover(sp._h, _p(Y), _p(x), C.byref(c), _stream()))
+    return x, c.value
+
+
+def rel_resid(A, b, x):
+    L = load()
+    rr = C.c_double()
+    v = A.view()
+    _check("sai_rel_resid", L.sai_rel_resid(C.byref(v), _p(b), _p(x), C.byref(rr), _stream()))
+    return rr.value
+
+
+def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0, abs_tau=-1.0,
+          delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, x=None):
+    """Procedure * on the device. Returns (x, iters list, report dict)."""
+    L = load()
+    if x is None:
+        x = torch.empty(A.n, dtype=torch.float64, device=b.device)
+    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0), 0 if sai == "spai" else 1,
+                       _SpaiParams(delta, mn, max_aug, key_bits, 0), _PsaiParams(delta, tol, tol_mode, lmax, 0),
+                       _KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit), eps)
+    cap = A.n + 1
+    iters = (C.c_int32 * cap)()
+    rep = _SolveReport()
+    v = A.view()
+    st = _check("sai_solve", L.sai_solve(C.byref(v), _p(b), C.byref(prm), _p(x), iters, cap, C.byref(rep),
+                                         _stream()), allow=(SAI_MAXITER, SAI_BREAKDOWN))
+    s = rep.split.s
+    report = dict(s=s, p=rep.split.p, tau=rep.split.tau, nnz_At=rep.split.nnz_At, nnz_U=rep.split.nnz_U,
+                  nnz_M=rep.precond.nnz_M, n_c=rep.precond.n_c, l_m=rep.precond.l_m,
+                  n_tier=list(rep.precond.n_tier), status=st, iter_max=rep.iter_max, c=rep.c, rr=rep.rr,
+                  ms_split=rep.ms_split, ms_build=rep.ms_build, ms_krylov=rep.ms_krylov, ms_smw=rep.ms_smw,
+                  build_ms=rep.precond.build_ms)
+    return x, list(iters[: s + 1]), report

@@ -1,0 +1,330 @@
+// api.cu -- extern "C" entry points declared in include/saismw.h.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <new>
+
+#include "internal.h"
+
+void sai_internal_note_cuda_error(cudaError_t e, const char* what, const char* file, int line)
+{
+    if (getenv("SAISMW_VERBOSE"))
+        fprintf(stderr, "saismw: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+}
+
+// The stream-ordered pool keeps freed blocks for reuse instead of returning
+// them to the driver after every synchronisation.
+void sai_pool_init_once()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (done_dev == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done_dev = dev;
+}
+
+static inline cudaStream_t S(sai_stream_t s) { return (cudaStream_t)s; }
+
+extern "C" {
+
+const char* sai_status_string(sai_status st)
+{
+    switch (st) {
+    case SAI_OK: return "SAI_OK";
+    case SAI_INVALID_ARG: return "SAI_INVALID_ARG";
+    case SAI_CUDA_ERROR: return "SAI_CUDA_ERROR";
+    case SAI_OOM: return "SAI_OOM";
+    case SAI_PATTERN_OVERFLOW: return "SAI_PATTERN_OVERFLOW";
+    case SAI_MAXITER: return "SAI_MAXITER";
+    case SAI_BREAKDOWN: return "SAI_BREAKDOWN";
+    case SAI_SINGULAR: return "SAI_SINGULAR";
+    case SAI_NOT_IMPLEMENTED: return "SAI_NOT_IMPLEMENTED";
+    }
+    return "SAI_UNKNOWN";
+}
+
+sai_status sai_split_create(const sai_csc_view* A, const sai_split_params* prm, sai_stream_t stream, sai_split* out)
+{
+    if (!out) return SAI_INVALID_ARG;
+    *out = nullptr;
+    sai_pool_init_once();
+    sai_split_s* h = new (std::nothrow) sai_split_s();
+    if (!h) return SAI_OOM;
+    sai_status st = sai_split_build(A, prm, S(stream), false, h);
+    if (st != SAI_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return SAI_OK;
+}
+
+sai_status sai_split_get_info(sai_split h, sai_split_info* info)
+{
+    if (!h || !info) return SAI_INVALID_ARG;
+    info->n = h->n;
+    info->s = h->s;
+    info->p = h->p;
+    info->p_keep = h->p_keep;
+    info->tau = h->tau;
+    info->nnz_At = h->nnz_At;
+    info->nnz_U = h->nnz_U;
+    info->norm1_At = h->norm1;
+    return SAI_OK;
+}
+
+sai_status sai_split_copy_out(sai_split h, int64_t* At_col_ptr, int32_t* At_row_idx, double* At_val,
+                              int64_t* U_col_ptr, int32_t* U_row_idx, double* U_val, int32_t* J,
+                              sai_stream_t stream)
+{
+    if (!h) return SAI_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    const cudaMemcpyKind D = cudaMemcpyDeviceToDevice;
+    if (At_col_ptr) SAI_CUDA(cudaMemcpyAsync(At_col_ptr, h->At_cp.p, sizeof(int64_t) * (h->n + 1), D, st));
+    if (At_row_idx && h->nnz_At) SAI_CUDA(cudaMemcpyAsync(At_row_idx, h->At_ri.p, sizeof(int32_t) * h->nnz_At, D, st));
+    if (At_val && h->nnz_At) SAI_CUDA(cudaMemcpyAsync(At_val, h->At_v.p, sizeof(double) * h->nnz_At, D, st));
+    if (U_col_ptr) SAI_CUDA(cudaMemcpyAsync(U_col_ptr, h->U_cp.p, sizeof(int64_t) * (h->s + 1), D, st));
+    if (U_row_idx && h->nnz_U) SAI_CUDA(cudaMemcpyAsync(U_row_idx, h->U_ri.p, sizeof(int32_t) * h->nnz_U, D, st));
+    if (U_val && h->nnz_U) SAI_CUDA(cudaMemcpyAsync(U_val, h->U_v.p, sizeof(double) * h->nnz_U, D, st));
+    if (J && h->s) SAI_CUDA(cudaMemcpyAsync(J, h->J.p, sizeof(int32_t) * h->s, D, st));
+    return SAI_OK;
+}
+
+void sai_split_destroy(sai_split h) { delete h; }
+
+sai_status sai_build_spai(sai_split h, const sai_spai_params* prm, sai_stream_t stream, sai_precond* out)
+{
+    if (!out) return SAI_INVALID_ARG;
+    *out = nullptr;
+    sai_pool_init_once();
+    sai_precond_s* P = new (std::nothrow) sai_precond_s();
+    if (!P) return SAI_OOM;
+    sai_status st = sai_spai_build(h, prm, S(stream), false, P);
+    if (st != SAI_OK) {
+        delete P;
+        return st;
+    }
+    *out = P;
+    return SAI_OK;
+}
+
+sai_status sai_build_psai(sai_split h, const sai_psai_params* prm, sai_stream_t stream, sai_precond* out)
+{
+    if (!out) return SAI_INVALID_ARG;
+    *out = nullptr;
+    sai_pool_init_once();
+    sai_precond_s* P = new (std::nothrow) sai_precond_s();
+    if (!P) return SAI_OOM;
+    sai_status st = sai_psai_build(h, prm, S(stream), false, P);
+    if (st != SAI_OK) {
+        delete P;
+        return st;
+    }
+    *out = P;
+    return SAI_OK;
+}
+
+sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info)
+{
+    if (!P || !info) return SAI_INVALID_ARG;
+    info->n = P->n;
+    info->nnz_M = P->nnz;
+    info->n_c = P->n_c;
+    info->l_m = P->l_m;
+    for (int q = 0; q < 3; ++q) info->n_tier[q] = P->n_tier[q];
+    info->build_ms = P->ms;
+    return SAI_OK;
+}
+
+sai_status sai_precond_copy_out(sai_precond P, int64_t* col_ptr, int32_t* row_idx, double* val, int32_t* loops,
+                                double* res, double* res_post, sai_stream_t stream)
+{
+    if (!P) return SAI_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    const cudaMemcpyKind D = cudaMemcpyDeviceToDevice;
+    if (col_ptr) SAI_CUDA(cudaMemcpyAsync(col_ptr, P->M_cp.p, sizeof(int64_t) * (P->n + 1), D, st));
+    if (row_idx && P->nnz) SAI_CUDA(cudaMemcpyAsync(row_idx, P->M_ri.p, sizeof(int32_t) * P->nnz, D, st));
+    if (val && P->nnz) SAI_CUDA(cudaMemcpyAsync(val, P->M_v.p, sizeof(double) * P->nnz, D, st));
+    if (loops && P->n) SAI_CUDA(cudaMemcpyAsync(loops, P->loops.p, sizeof(int32_t) * P->n, D, st));
+    if (res && P->n) SAI_CUDA(cudaMemcpyAsync(res, P->res.p, sizeof(double) * P->n, D, st));
+    if (res_post && P->n) SAI_CUDA(cudaMemcpyAsync(res_post, P->res_post.p, sizeof(double) * P->n, D, st));
+    return SAI_OK;
+}
+
+void sai_precond_destroy(sai_precond P) { delete P; }
+
+sai_status sai_krylov_solve(sai_split h, sai_precond P, int32_t k, const double* B, const double* thr,
+                            const sai_krylov_params* prm, double* X, int32_t* iters, int32_t* status,
+                            sai_stream_t stream)
+{
+    sai_pool_init_once();
+    return sai_krylov_run(h, P, k, B, thr, prm, X, iters, status, S(stream));
+}
+
+sai_status sai_smw_recover(sai_split h, const double* Y, double* x, double* c_out, sai_stream_t stream)
+{
+    sai_pool_init_once();
+    return sai_smw_run(h, Y, x, c_out, S(stream));
+}
+
+sai_status sai_rel_resid(const sai_csc_view* A, const double* b, const double* x, double* rr_out,
+                         sai_stream_t stream)
+{
+    if (!A || !rr_out || A->n < 0 || (A->n > 0 && (!b || !x || !A->col_ptr))) return SAI_INVALID_ARG;
+    sai_pool_init_once();
+    double nn[2] = {0.0, 0.0};
+    SAI_TRY(sai_csc_residual_norms(A->n, A->col_ptr, A->row_idx, A->val, b, x, nn, S(stream)));
+    *rr_out = nn[1] > 0.0 ? sqrt(nn[0] / nn[1]) : sqrt(nn[0]);
+    return SAI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- Procedure *
+namespace {
+
+// B = [b, u_1 .. u_s] as an n x (s+1) row-major block
+__global__ void k_fill_rhs(int32_t n, int32_t s, const double* b, const int64_t* Ucp, const int32_t* Uri,
+                           const double* Uv, double* B)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ld = (int64_t)s + 1;
+    if (i < n) {
+        B[i * ld] = b[i];
+        for (int t = 0; t < s; ++t) B[i * ld + 1 + t] = 0.0;
+    }
+}
+
+__global__ void k_scatter_U(int32_t s, const int64_t* Ucp, const int32_t* Uri, const double* Uv, double* B)
+{
+    const int t = blockIdx.x;
+    const int64_t ld = (int64_t)s + 1;
+    for (int64_t q = Ucp[t] + threadIdx.x; q < Ucp[t + 1]; q += blockDim.x) B[(int64_t)Uri[q] * ld + 1 + t] = Uv[q];
+}
+
+__global__ void k_sumsq(int32_t n, const double* b, double* out)
+{
+    __shared__ double sh[1024];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += b[i] * b[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)blockDim.x; ++q) t += sh[q];
+        *out = t;
+    }
+}
+
+struct Ev {
+    cudaEvent_t e = nullptr;
+    Ev() { cudaEventCreate(&e); }
+    ~Ev() { cudaEventDestroy(e); }
+};
+
+sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
+                      int32_t* iters, int32_t iters_cap, sai_solve_report* rep, cudaStream_t st)
+{
+    if (!A || !prm || !rep || (A->n > 0 && (!b || !x))) return SAI_INVALID_ARG;
+    *rep = sai_solve_report{};
+    Ev e0, e1, e2, e3, e4;
+    SAI_CUDA(cudaEventRecord(e0.e, st));
+    sai_split_s h;
+    SAI_TRY(sai_split_build(A, &prm->split, st, true, &h));
+    SAI_CUDA(cudaEventRecord(e1.e, st));
+    sai_precond_s P;
+    if (prm->sai == 0) SAI_TRY(sai_spai_build(&h, &prm->spai, st, true, &P));
+    else SAI_TRY(sai_psai_build(&h, &prm->psai, st, true, &P));
+    SAI_CUDA(cudaEventRecord(e2.e, st));
+    const int32_t n = h.n, s = h.s, k = s + 1;
+    Buf Bb, Yb, nb;
+    SAI_TRY(Bb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+    SAI_TRY(Yb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+    SAI_TRY(nb.alloc(sizeof(double), st, true));
+    if (n > 0) k_fill_rhs<<<sai_div_up(n, 256), 256, 0, st>>>(n, s, b, nullptr, nullptr, nullptr, Bb.as<double>());
+    if (s > 0)
+        k_scatter_U<<<s, 256, 0, st>>>(s, h.U_cp.as<int64_t>(), h.U_ri.as<int32_t>(), h.U_v.as<double>(),
+                                       Bb.as<double>());
+    k_sumsq<<<1, 1024, 0, st>>>(n, b, nb.as<double>());
+    SAI_CUDA(cudaGetLastError());
+    double bb = 0.0;
+    SAI_CUDA(cudaMemcpyAsync(&bb, nb.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    const double bnorm = sqrt(bb);
+    // Theorem 2 with c = 1: eqs. (stopb) and (stopU2)
+    double* thr = (double*)malloc(sizeof(double) * k);
+    int32_t* it = (int32_t*)malloc(sizeof(int32_t) * k);
+    int32_t* stt = (int32_t*)malloc(sizeof(int32_t) * k);
+    if (!thr || !it || !stt) {
+        free(thr);
+        free(it);
+        free(stt);
+        return SAI_OOM;
+    }
+    thr[0] = 0.5 * prm->eps * bnorm;
+    for (int t = 1; t < k; ++t) thr[t] = prm->eps * bnorm / (2.0 * sqrt((double)s));
+    sai_status kst = sai_krylov_run(&h, &P, k, Bb.as<double>(), thr, &prm->krylov, Yb.as<double>(), it, stt, st);
+    SAI_CUDA(cudaEventRecord(e3.e, st));
+    if (kst != SAI_OK && kst != SAI_MAXITER && kst != SAI_BREAKDOWN) {
+        free(thr);
+        free(it);
+        free(stt);
+        return kst;
+    }
+    int imax = 0;
+    for (int t = 0; t < k; ++t) {
+        if (it[t] > imax) imax = it[t];
+        if (iters && t < iters_cap) iters[t] = it[t];
+    }
+    free(thr);
+    free(it);
+    free(stt);
+    double c = 0.0;
+    SAI_TRY(sai_smw_run(&h, Yb.as<double>(), x, &c, st));
+    SAI_CUDA(cudaEventRecord(e4.e, st));
+    double nn[2] = {0.0, 0.0};
+    SAI_TRY(sai_csc_residual_norms(A->n, A->col_ptr, A->row_idx, A->val, b, x, nn, st));
+    rep->split.n = h.n;
+    rep->split.s = h.s;
+    rep->split.p = h.p;
+    rep->split.p_keep = h.p_keep;
+    rep->split.tau = h.tau;
+    rep->split.nnz_At = h.nnz_At;
+    rep->split.nnz_U = h.nnz_U;
+    rep->split.norm1_At = h.norm1;
+    rep->precond.n = P.n;
+    rep->precond.nnz_M = P.nnz;
+    rep->precond.n_c = P.n_c;
+    rep->precond.l_m = P.l_m;
+    for (int q = 0; q < 3; ++q) rep->precond.n_tier[q] = P.n_tier[q];
+    rep->precond.build_ms = P.ms;
+    rep->status = kst;
+    rep->iter_max = imax;
+    rep->c = c;
+    rep->rr = nn[1] > 0.0 ? sqrt(nn[0] / nn[1]) : sqrt(nn[0]);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0.e, e1.e);
+    rep->ms_split = ms;
+    cudaEventElapsedTime(&ms, e1.e, e2.e);
+    rep->ms_build = ms;
+    cudaEventElapsedTime(&ms, e2.e, e3.e);
+    rep->ms_krylov = ms;
+    cudaEventElapsedTime(&ms, e3.e, e4.e);
+    rep->ms_smw = ms;
+    return kst;
+}
+
+}  // namespace
+
+extern "C" sai_status sai_solve(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
+                                int32_t* iters, int32_t iters_cap, sai_solve_report* rep, sai_stream_t stream)
+{
+    sai_pool_init_once();
+    return solve_impl(A, b, prm, x, iters, iters_cap, rep, S(stream));
+}

@@ -1,0 +1,835 @@
+// sai.cu -- construction of the sparse approximate inverse M ~ A~^{-1}
+// (section 2 of the paper): n independent problems min ||A~ m_k - e_k||
+// (eq. (subprob)) reduced to min ||A^_k m^_k - e^_k|| (eq. (lsprob)) and solved
+// by Householder QR, one warp per column.
+//
+// Per column k the warp keeps, in a private workspace:
+//   S      the pattern (insertion order), |S| <= SCAP
+//   L      the rows of A~(:,S) plus k (row k always at local position 0),
+//          with a hash row -> local position, |L| <= LCAP
+//   Q      A^ = A~(L,S) factored in place: Householder vectors below and on
+//          the diagonal, R above it (column-major, leading dimension LCAP),
+//          rdiag = diag(R), beta = 2/(v^T v)
+//   cv     Q^T e^,   m  the LS solution,   r  the residual A^ m - e^ on L
+// When S grows, only the new columns are gathered: the old reflectors are
+// applied to them and the trailing block is factored ("updating m^_k instead of
+// resolving it", section 2.1). New rows are zero in the old columns because L
+// already holds every nonzero row of A~(:,S_old).
+//
+// SPAI (section 2.1): candidates N \ S from the rows of L (CSR of A~),
+// rho_j^2 = ||r||^2 - (r^T A~e_j)^2/||A~e_j||^2 (eq. (rhoj)), ranked by the key
+// (floor(rho_j^2/||r||^2 * 2^key_bits) << 32 | j) and the mn smallest added.
+// PSAI(tol) (section 2.2): drop |m_jk| <= tol_k (eq. (tolk)); grow
+// S^(l+1) = P(|A~| a^(l)) u S_kept.
+//
+// Workspace tiers: tier 0 lives in shared memory (most columns of regular
+// sparse matrices); a column that outgrows it is queued and restarted in the
+// global-memory tiers 1 and 2. Restarting reproduces the same arithmetic, so
+// the result does not depend on the tier that finished a column.
+#include <float.h>
+
+#include "internal.h"
+
+namespace {
+
+enum { ST_DONE = 0, ST_OVERFLOW = 1, ST_SINGULAR = 2 };
+constexpr int MNMAX = 8;
+
+struct SaiMat {
+    int32_t n;
+    const int64_t* __restrict__ cp;  // CSC of A~
+    const int32_t* __restrict__ ri;
+    const double* __restrict__ cv;
+    const int64_t* __restrict__ rp;  // CSR pattern of A~
+    const int32_t* __restrict__ rc;
+    const double* __restrict__ colnorm2;
+    double norm1;
+};
+
+struct SpaiArgs {
+    double delta;
+    double scale;  // 2^key_bits
+    int mn, max_aug;
+};
+
+struct PsaiArgs {
+    double delta, tol;
+    int tol_mode, lmax;
+};
+
+struct Out {
+    int32_t smax;      // output slots per column
+    int32_t* cnt;      // [n]
+    int32_t* rows;     // [n * smax]
+    double* vals;      // [n * smax]
+    int32_t* loops;    // [n]
+    double* res;       // [n]
+    double* res_post;  // [n] (PSAI)
+    int32_t* tier;     // [n] tier that finished the column
+};
+
+constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int LCAP_, int SCAP_, int HL_, int HC_>
+struct Tier {
+    static constexpr int LCAP = LCAP_, SCAP = SCAP_, HL = HL_, HC = HC_;
+    static constexpr size_t OFF_Q = 0;
+    static constexpr size_t OFF_CV = OFF_Q + 8ull * LCAP * SCAP;
+    static constexpr size_t OFF_R = OFF_CV + 8ull * LCAP;
+    static constexpr size_t OFF_M = OFF_R + 8ull * LCAP;
+    static constexpr size_t OFF_BETA = OFF_M + 8ull * SCAP;
+    static constexpr size_t OFF_RD = OFF_BETA + 8ull * SCAP;
+    static constexpr size_t OFF_LROW = OFF_RD + 8ull * SCAP;
+    static constexpr size_t OFF_HK = OFF_LROW + 4ull * LCAP;
+    static constexpr size_t OFF_HV = OFF_HK + 4ull * HL;
+    static constexpr size_t OFF_S = OFF_HV + 4ull * HL;
+    static constexpr size_t OFF_A0 = OFF_S + 4ull * SCAP;
+    static constexpr size_t OFF_A1 = OFF_A0 + 4ull * SCAP;
+    static constexpr size_t OFF_CK = OFF_A1 + 4ull * SCAP;
+    static constexpr size_t OFF_CF = OFF_CK + 4ull * HC;
+    static constexpr size_t OFF_KP = OFF_CF + (size_t)HC;
+    static constexpr size_t BYTES = a16(OFF_KP + (size_t)SCAP);
+    static_assert(HL >= 2 * LCAP && (HL & (HL - 1)) == 0, "row hash");
+    static_assert(HC >= 2 * SCAP && (HC & (HC - 1)) == 0, "candidate hash");
+};
+
+using Tier0 = Tier<64, 16, 128, 512>;      // shared memory, ~13.6 KB per warp
+using Tier1 = Tier<256, 64, 512, 2048>;    // global memory, ~150 KB per warp
+using Tier2 = Tier<1024, 128, 2048, 8192>; // global memory, ~1.1 MB per warp
+
+struct Ws {
+    double *Q, *cv, *r, *m, *beta, *rd;
+    int32_t *Lrow, *hk, *hv, *S, *a0, *a1, *ck;
+    uint8_t *cf, *kp;
+};
+
+template <class T>
+__device__ __forceinline__ Ws bind_ws(char* b)
+{
+    Ws w;
+    w.Q = (double*)(b + T::OFF_Q);
+    w.cv = (double*)(b + T::OFF_CV);
+    w.r = (double*)(b + T::OFF_R);
+    w.m = (double*)(b + T::OFF_M);
+    w.beta = (double*)(b + T::OFF_BETA);
+    w.rd = (double*)(b + T::OFF_RD);
+    w.Lrow = (int32_t*)(b + T::OFF_LROW);
+    w.hk = (int32_t*)(b + T::OFF_HK);
+    w.hv = (int32_t*)(b + T::OFF_HV);
+    w.S = (int32_t*)(b + T::OFF_S);
+    w.a0 = (int32_t*)(b + T::OFF_A0);
+    w.a1 = (int32_t*)(b + T::OFF_A1);
+    w.ck = (int32_t*)(b + T::OFF_CK);
+    w.cf = (uint8_t*)(b + T::OFF_CF);
+    w.kp = (uint8_t*)(b + T::OFF_KP);
+    return w;
+}
+
+__device__ __forceinline__ uint32_t hmix(int32_t key)
+{
+    uint32_t h = (uint32_t)key;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Lookup in an open-addressing table (keys -1 = empty). Returns the value or -1.
+template <int H>
+__device__ __forceinline__ int32_t hfind(const int32_t* hk, const int32_t* hv, int32_t key)
+{
+    uint32_t s = hmix(key) & (H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+        int32_t k = hk[s];
+        if (k == key) return hv[s];
+        if (k == -1) return -1;
+        s = (s + 1) & (H - 1);
+    }
+    return -1;
+}
+
+// Slot of key (inserting it if absent); -1 if the table is full.
+template <int H>
+__device__ __forceinline__ int hinsert(int32_t* hk, int32_t key, bool& inserted)
+{
+    uint32_t s = hmix(key) & (H - 1);
+    inserted = false;
+    for (int probe = 0; probe < H; ++probe) {
+        int32_t k = *((volatile int32_t*)&hk[s]);
+        if (k == key) return (int)s;
+        if (k == -1) {
+            int32_t old = atomicCAS(&hk[s], -1, key);
+            if (old == -1) {
+                inserted = true;
+                return (int)s;
+            }
+            if (old == key) return (int)s;
+        }
+        s = (s + 1) & (H - 1);
+    }
+    return -1;
+}
+
+template <int H>
+__device__ __forceinline__ int hslot(const int32_t* hk, int32_t key)
+{
+    uint32_t s = hmix(key) & (H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+        int32_t k = hk[s];
+        if (k == key) return (int)s;
+        if (k == -1) return -1;
+        s = (s + 1) & (H - 1);
+    }
+    return -1;
+}
+
+// Adds the rows of column j of A~ to L. New rows get consecutive positions in
+// entry order, so L's order does not depend on scheduling. False on overflow.
+template <class T>
+__device__ bool add_rows(const Ws& w, const SaiMat& A, int32_t j, int& nL)
+{
+    const int lane = lane_id();
+    const int64_t b = A.cp[j], e = A.cp[j + 1];
+    for (int64_t base = b; base < e; base += 32) {
+        const int64_t q = base + lane;
+        bool isnew = false;
+        int slot = 0;
+        int32_t i = -1;
+        if (q < e) {
+            i = A.ri[q];
+            slot = hinsert<T::HL>(w.hk, i, isnew);
+        }
+        if (__any_sync(SAI_FULL, slot < 0)) return false;
+        const unsigned mask = __ballot_sync(SAI_FULL, isnew);
+        const int cnt = __popc(mask);
+        if (nL + cnt > T::LCAP) return false;
+        if (isnew) {
+            const int pos = nL + __popc(mask & ((1u << lane) - 1u));
+            w.hv[slot] = pos;
+            w.Lrow[pos] = i;
+        }
+        nL += cnt;
+        __syncwarp();
+    }
+    return true;
+}
+
+// Resets the per-column state to S = {k}, L = {k}, cv = e^.
+template <class T>
+__device__ void col_init(const Ws& w, int32_t k, int& nL, int& nS, int& nfact)
+{
+    const int lane = lane_id();
+    for (int q = lane; q < T::HL; q += 32) w.hk[q] = -1;
+    __syncwarp();
+    if (lane == 0) {
+        bool ins;
+        int sl = hinsert<T::HL>(w.hk, k, ins);
+        w.hv[sl] = 0;
+        w.Lrow[0] = k;
+        w.cv[0] = 1.0;
+    }
+    __syncwarp();
+    nL = 1;
+    nS = 1;
+    nfact = 0;
+}
+
+// Gathers the new columns S[nfact..nS), updates the QR factorisation and
+// solves R m = (Q^T e^)(0:nS). Returns ST_DONE, ST_OVERFLOW or ST_SINGULAR.
+template <class T>
+__device__ int ls_update(const Ws& w, const SaiMat& A, int& nL, int nS, int& nfact)
+{
+    const int lane = lane_id();
+    const int nL_old = nL;
+    for (int t = nfact; t < nS; ++t)
+        if (!add_rows<T>(w, A, w.S[t], nL)) return ST_OVERFLOW;
+    // zero the new rows of the old columns and of cv, and the new columns
+    for (int t = 0; t < nS; ++t) {
+        double* col = w.Q + (size_t)t * T::LCAP;
+        for (int i = (t < nfact ? nL_old : 0) + lane; i < nL; i += 32) col[i] = 0.0;
+    }
+    for (int i = nL_old + lane; i < nL; i += 32) w.cv[i] = 0.0;
+    __syncwarp();
+    for (int t = nfact; t < nS; ++t) {
+        const int32_t j = w.S[t];
+        double* col = w.Q + (size_t)t * T::LCAP;
+        for (int64_t q = A.cp[j] + lane; q < A.cp[j + 1]; q += 32) {
+            const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
+            if (pos >= 0) col[pos] = A.cv[q];
+        }
+    }
+    __syncwarp();
+    // old reflectors on the new columns
+    for (int jr = 0; jr < nfact; ++jr) {
+        const double* v = w.Q + (size_t)jr * T::LCAP;
+        const double bj = w.beta[jr];
+        for (int t = nfact; t < nS; ++t) {
+            double* col = w.Q + (size_t)t * T::LCAP;
+            double d = 0.0;
+            for (int i = jr + lane; i < nL; i += 32) d = fma(v[i], col[i], d);
+            d = warp_sum(d);
+            const double f = bj * d;
+            for (int i = jr + lane; i < nL; i += 32) col[i] = fma(-f, v[i], col[i]);
+            __syncwarp();
+        }
+    }
+    // factor the trailing block column by column
+    for (int t = nfact; t < nS; ++t) {
+        double* col = w.Q + (size_t)t * T::LCAP;
+        double s2 = 0.0;
+        for (int i = t + lane; i < nL; i += 32) s2 = fma(col[i], col[i], s2);
+        s2 = warp_sum(s2);
+        if (!(s2 > 0.0)) return ST_SINGULAR;
+        const double nrm = sqrt(s2);
+        const double x0 = col[t];
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;
+        const double bt = 1.0 / (nrm * (nrm + fabs(x0)));  // 2/(v^T v), v^T v = 2 nrm (nrm + |x0|)
+        __syncwarp();
+        if (lane == 0) {
+            col[t] = x0 - alpha;
+            w.rd[t] = alpha;
+            w.beta[t] = bt;
+        }
+        __syncwarp();
+        for (int t2 = t + 1; t2 <= nS; ++t2) {
+            double* c2 = t2 < nS ? w.Q + (size_t)t2 * T::LCAP : w.cv;
+            double d = 0.0;
+            for (int i = t + lane; i < nL; i += 32) d = fma(col[i], c2[i], d);
+            d = warp_sum(d);
+            const double f = bt * d;
+            for (int i = t + lane; i < nL; i += 32) c2[i] = fma(-f, col[i], c2[i]);
+            __syncwarp();
+        }
+    }
+    nfact = nS;
+    // back substitution
+    for (int i = lane; i < nS; i += 32) w.m[i] = w.cv[i];
+    __syncwarp();
+    for (int t = nS - 1; t >= 0; --t) {
+        const double mt = w.m[t] / w.rd[t];
+        __syncwarp();
+        if (lane == 0) w.m[t] = mt;
+        const double* col = w.Q + (size_t)t * T::LCAP;
+        for (int i = lane; i < t; i += 32) w.m[i] = fma(-col[i], mt, w.m[i]);
+        __syncwarp();
+    }
+    return ST_DONE;
+}
+
+// r = A~(L,S) m - e^ on L (only the columns with use[t] != 0 when use given);
+// returns ||r||^2.
+template <class T>
+__device__ double residual(const Ws& w, const SaiMat& A, int nL, int nS, const uint8_t* use)
+{
+    const int lane = lane_id();
+    for (int i = lane; i < nL; i += 32) w.r[i] = (i == 0) ? -1.0 : 0.0;
+    __syncwarp();
+    for (int t = 0; t < nS; ++t) {
+        if (use && !use[t]) continue;
+        const int32_t j = w.S[t];
+        const double mt = w.m[t];
+        for (int64_t q = A.cp[j] + lane; q < A.cp[j + 1]; q += 32) {
+            const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
+            if (pos >= 0) w.r[pos] = fma(A.cv[q], mt, w.r[pos]);
+        }
+        __syncwarp();
+    }
+    double s = 0.0;
+    for (int i = lane; i < nL; i += 32) s = fma(w.r[i], w.r[i], s);
+    return warp_sum(s);
+}
+
+template <class T>
+__device__ int spai_column(const Ws& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out, int& l_out,
+                           double& rn_out)
+{
+    const int lane = lane_id();
+    int nL, nS, nfact;
+    col_init<T>(w, k, nL, nS, nfact);
+    if (lane == 0) w.S[0] = k;
+    __syncwarp();
+    int l = 0;
+    double rn = 0.0;
+    for (;;) {
+        int st = ls_update<T>(w, A, nL, nS, nfact);
+        if (st != ST_DONE) return st;
+        const double rn2 = residual<T>(w, A, nL, nS, nullptr);
+        rn = sqrt(rn2);
+        if (rn <= a.delta || l >= a.max_aug) break;
+        // candidate set N \ S from the rows of L
+        for (int q = lane; q < T::HC; q += 32) {
+            w.ck[q] = -1;
+            w.cf[q] = 0;
+        }
+        __syncwarp();
+        bool ovf = false;
+        for (int t = lane; t < nS; t += 32) {
+            bool ins;
+            int sl = hinsert<T::HC>(w.ck, w.S[t], ins);
+            if (sl < 0) ovf = true;
+            else w.cf[sl] = 1;
+        }
+        __syncwarp();
+        int ncand = 0;
+        for (int idx = lane; idx < nL; idx += 32) {
+            const int32_t i = w.Lrow[idx];
+            for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+                bool ins;
+                int sl = hinsert<T::HC>(w.ck, A.rc[q], ins);
+                if (sl < 0) ovf = true;
+                ncand += ins;
+            }
+        }
+        ncand = warp_sum_int(ncand);
+        if (__any_sync(SAI_FULL, ovf) || ncand + nS > T::HC / 2) return ST_OVERFLOW;
+        __syncwarp();
+        // profitability keys and a per-lane sorted top list
+        unsigned long long top[MNMAX];
+#pragma unroll
+        for (int q = 0; q < MNMAX; ++q) top[q] = ULLONG_MAX;
+        for (int sl = lane; sl < T::HC; sl += 32) {
+            const int32_t j = w.ck[sl];
+            if (j < 0 || w.cf[sl]) continue;
+            const double nj = A.colnorm2[j];
+            if (!(nj > 0.0)) continue;
+            double d = 0.0;
+            for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+                const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
+                if (pos >= 0) d = fma(w.r[pos], A.cv[q], d);
+            }
+            const double rho2 = rn2 - d * d / nj;
+            double tq = rho2 / rn2;
+            tq = fmin(fmax(tq, 0.0), 1.0);
+            unsigned long long x = ((unsigned long long)floor(tq * a.scale) << 32) | (unsigned)j;
+#pragma unroll
+            for (int q = 0; q < MNMAX; ++q) {
+                const unsigned long long lo = top[q] < x ? top[q] : x;
+                x = top[q] < x ? x : top[q];
+                top[q] = lo;
+            }
+        }
+        int added = 0;
+        for (int sel = 0; sel < a.mn; ++sel) {
+            const unsigned long long best = warp_min_u64(top[0]);
+            if (best == ULLONG_MAX) break;
+            if (top[0] == best) {
+#pragma unroll
+                for (int q = 0; q < MNMAX - 1; ++q) top[q] = top[q + 1];
+                top[MNMAX - 1] = ULLONG_MAX;
+            }
+            if (nS + added >= T::SCAP) return ST_OVERFLOW;
+            if (lane == 0) w.S[nS + added] = (int32_t)(best & 0xffffffffull);
+            ++added;
+        }
+        __syncwarp();
+        if (added == 0) break;
+        nS += added;
+        ++l;
+    }
+    nS_out = nS;
+    l_out = l;
+    rn_out = rn;
+    return ST_DONE;
+}
+
+// PSAI(tol), reading (A): S^(l+1) = P(a^(l+1)) u S_kept^(l), a^(l+1) = |A~| a^(l).
+template <class T>
+__device__ int psai_column(const Ws& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out, int& l_out,
+                           double& rn_pre, double& rn_post)
+{
+    const int lane = lane_id();
+    int nL, nS, nfact;
+    col_init<T>(w, k, nL, nS, nfact);
+    if (lane == 0) {
+        w.S[0] = k;
+        w.a0[0] = k;
+    }
+    __syncwarp();
+    int na = 1;
+    int32_t* apat = w.a0;
+    int32_t* anew = w.a1;
+    int l = 0;
+    for (;;) {
+        int st = ls_update<T>(w, A, nL, nS, nfact);
+        if (st != ST_DONE) return st;
+        const double rn = sqrt(residual<T>(w, A, nL, nS, nullptr));
+        double tolk = a.tol;
+        if (a.tol_mode == 0) {
+            int nz = 0;
+            for (int t = lane; t < nS; t += 32) nz += (w.m[t] != 0.0);
+            nz = warp_sum_int(nz);
+            tolk = (nz > 0 && A.norm1 > 0.0) ? a.delta / ((double)nz * A.norm1) : 0.0;
+        }
+        // keep flags: kp[t] = |m_t| > tol_k
+        for (int t = lane; t < nS; t += 32) w.kp[t] = (uint8_t)(fabs(w.m[t]) > tolk);
+        __syncwarp();
+        if (rn <= a.delta || l >= a.lmax) {
+            rn_pre = rn;
+            rn_post = sqrt(residual<T>(w, A, nL, nS, w.kp));
+            // compact the kept entries to the front of S / m (order preserved)
+            int q = 0;
+            if (lane == 0) {
+                for (int t = 0; t < nS; ++t)
+                    if (w.kp[t]) {
+                        w.S[q] = w.S[t];
+                        w.m[q] = w.m[t];
+                        ++q;
+                    }
+            }
+            nS_out = __shfl_sync(SAI_FULL, q, 0);
+            __syncwarp();
+            l_out = l;
+            return ST_DONE;
+        }
+        // a^(l+1): union of the column patterns of a^(l); positions in entry order
+        for (int q = lane; q < T::HC; q += 32) {
+            w.ck[q] = -1;
+            w.cf[q] = 0;
+        }
+        __syncwarp();
+        int nb = 0;
+        for (int t = 0; t < na; ++t) {
+            const int32_t j = apat[t];
+            const int64_t b = A.cp[j], e = A.cp[j + 1];
+            for (int64_t base = b; base < e; base += 32) {
+                const int64_t q = base + lane;
+                bool isnew = false;
+                int slot = 0;
+                int32_t i = -1;
+                if (q < e) {
+                    i = A.ri[q];
+                    slot = hinsert<T::HC>(w.ck, i, isnew);
+                }
+                if (__any_sync(SAI_FULL, slot < 0)) return ST_OVERFLOW;
+                const unsigned mask = __ballot_sync(SAI_FULL, isnew);
+                const int cnt = __popc(mask);
+                if (nb + cnt > T::SCAP) return ST_OVERFLOW;
+                if (isnew) anew[nb + __popc(mask & ((1u << lane) - 1u))] = i;
+                nb += cnt;
+                __syncwarp();
+            }
+        }
+        // cf = 1 marks members of S^(l) inside a^(l+1); a dropped member that is
+        // not in a^(l+1) leaves the pattern (S shrinks)
+        bool shrink = false;
+        for (int t = lane; t < nS; t += 32) {
+            const int sl = hslot<T::HC>(w.ck, w.S[t]);
+            if (sl >= 0) w.cf[sl] = 1;
+            else if (!w.kp[t]) shrink = true;
+        }
+        shrink = __any_sync(SAI_FULL, shrink);
+        __syncwarp();
+        if (!shrink) {
+            // pure growth: append the members of a^(l+1) not in S, in list order
+            int add = 0;
+            for (int base = 0; base < nb; base += 32) {
+                const int t = base + lane;
+                bool fresh = false;
+                int32_t j = -1;
+                if (t < nb) {
+                    j = anew[t];
+                    fresh = w.cf[hslot<T::HC>(w.ck, j)] == 0;
+                }
+                const unsigned mask = __ballot_sync(SAI_FULL, fresh);
+                if (nS + add + __popc(mask) > T::SCAP) return ST_OVERFLOW;
+                if (fresh) w.S[nS + add + __popc(mask & ((1u << lane) - 1u))] = j;
+                add += __popc(mask);
+            }
+            __syncwarp();
+            nS += add;
+        } else {
+            // rebuild from scratch with S = a^(l+1), then the kept members of
+            // S^(l) outside a^(l+1)
+            int q2 = nb;
+            if (lane == 0) {
+                for (int t = 0; t < nS; ++t)
+                    if (w.kp[t] && hslot<T::HC>(w.ck, w.S[t]) < 0) {
+                        if (q2 < T::SCAP) apat[q2 - nb] = w.S[t];
+                        ++q2;
+                    }
+            }
+            q2 = __shfl_sync(SAI_FULL, q2, 0);
+            __syncwarp();
+            if (q2 > T::SCAP) return ST_OVERFLOW;
+            // apat (old a^(l)) is free now: it holds the extra kept members
+            for (int t = lane; t < q2; t += 32) w.S[t] = t < nb ? anew[t] : apat[t - nb];
+            __syncwarp();
+            col_init<T>(w, k, nL, nS, nfact);
+            nS = q2;
+        }
+        // a^(l+1) becomes current
+        int32_t* sw = apat;
+        apat = anew;
+        anew = sw;
+        na = nb;
+        ++l;
+    }
+}
+
+template <class T, bool SMEM, bool PSAI>
+__global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa, const int32_t* __restrict__ work,
+                                             int32_t nwork, int* next, char* gscratch, Out out, int32_t* ovf_list,
+                                             int* ovf_cnt, int* err, int tier_id)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    char* base = SMEM ? smem + (size_t)wib * T::BYTES
+                      : gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * T::BYTES;
+    const Ws w = bind_ws<T>(base);
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(next, 1);
+        item = __shfl_sync(SAI_FULL, item, 0);
+        if (item >= nwork) break;
+        const int32_t k = work ? work[item] : item;
+        int nS = 0, l = 0;
+        double rn = 0.0, rpost = 0.0;
+        int st = PSAI ? psai_column<T>(w, A, k, pa, nS, l, rn, rpost) : spai_column<T>(w, A, k, sa, nS, l, rn);
+        if (st == ST_DONE) {
+            if (nS > out.smax) st = ST_OVERFLOW;
+        }
+        if (st == ST_DONE) {
+            const size_t o = (size_t)k * out.smax;
+            for (int t = lane; t < nS; t += 32) {
+                out.rows[o + t] = w.S[t];
+                out.vals[o + t] = w.m[t];
+            }
+            if (lane == 0) {
+                out.cnt[k] = nS;
+                out.loops[k] = l;
+                out.res[k] = rn;
+                if (out.res_post) out.res_post[k] = rpost;
+                out.tier[k] = tier_id;
+            }
+        } else if (st == ST_OVERFLOW) {
+            if (lane == 0) {
+                if (ovf_list) {
+                    int p = atomicAdd(ovf_cnt, 1);
+                    ovf_list[p] = k;
+                } else {
+                    atomicOr(err, 1);
+                }
+            }
+        } else {
+            if (lane == 0) atomicOr(err, 2);
+        }
+        __syncwarp();
+    }
+}
+
+// One warp per column: rank-sort the column's slots by row into CSC.
+__global__ void k_assemble(int32_t n, int32_t smax, const int32_t* cnt, const int32_t* rows, const double* vals,
+                           const int64_t* cp, int32_t* ri, double* v)
+{
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    const int c = cnt[k];
+    const size_t o = (size_t)k * smax;
+    for (int t = lane; t < c; t += 32) {
+        const int32_t r = rows[o + t];
+        int rank = 0;
+        for (int u = 0; u < c; ++u) rank += rows[o + u] < r;
+        ri[cp[k] + rank] = r;
+        v[cp[k] + rank] = vals[o + t];
+    }
+}
+
+__global__ void k_stats(int32_t n, const int32_t* loops, const double* res, double delta, int* out)
+{
+    int nc = 0, lm = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        nc += res[k] > delta;
+        lm = max(lm, loops[k]);
+    }
+    nc = warp_sum_int(nc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(SAI_FULL, lm, o));
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], nc);
+        atomicMax(&out[1], lm);
+    }
+}
+
+__global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&out[2 + tier[k]], 1);
+}
+
+int g_num_sms = 0;
+
+template <class T, bool SMEM, bool PSAI>
+sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, const int32_t* work, int32_t nwork,
+                       int* next, const Out& out, int32_t* ovf_list, int* ovf_cnt, int* err, int tier_id,
+                       cudaStream_t st)
+{
+    if (nwork <= 0) return SAI_OK;
+    const int warps_per_block = 8;
+    const int threads = 32 * warps_per_block;
+    int blocks;
+    Buf scratch;
+    size_t smem = 0;
+    if (SMEM) {
+        smem = T::BYTES * warps_per_block;
+        SAI_CUDA(cudaFuncSetAttribute(k_sai<T, SMEM, PSAI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sai<T, SMEM, PSAI>, threads, smem));
+        if (per_sm < 1) per_sm = 1;
+        blocks = g_num_sms * per_sm;
+    } else {
+        blocks = g_num_sms * 2;
+        const int need = (nwork + warps_per_block - 1) / warps_per_block;
+        if (blocks > need) blocks = need;
+        SAI_TRY(scratch.alloc(T::BYTES * (size_t)warps_per_block * blocks, st, true));
+    }
+    SAI_CUDA(cudaMemsetAsync(next, 0, sizeof(int), st));
+    k_sai<T, SMEM, PSAI><<<blocks, threads, smem, st>>>(A, sa, pa, work, nwork, next, scratch.as<char>(), out,
+                                                        ovf_list, ovf_cnt, err, tier_id);
+    SAI_CUDA(cudaGetLastError());
+    return SAI_OK;
+}
+
+template <bool PSAI>
+sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs& pa, int32_t smax, double delta,
+                        cudaStream_t st, bool async, sai_precond_s* P)
+{
+    if (g_num_sms == 0) {
+        int dev = 0;
+        SAI_CUDA(cudaGetDevice(&dev));
+        SAI_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int32_t n = h->n;
+    P->n = n;
+    cudaEvent_t e0, e1;
+    SAI_CUDA(cudaEventCreate(&e0));
+    SAI_CUDA(cudaEventCreate(&e1));
+    SAI_CUDA(cudaEventRecord(e0, st));
+    SaiMat A;
+    A.n = n;
+    A.cp = h->At_cp.as<int64_t>();
+    A.ri = h->At_ri.as<int32_t>();
+    A.cv = h->At_v.as<double>();
+    A.rp = h->Atr_rp.as<int64_t>();
+    A.rc = h->Atr_ci.as<int32_t>();
+    A.colnorm2 = h->colnorm2.as<double>();
+    A.norm1 = h->norm1;
+
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    Buf cnt, rows, vals, tier, ctr, ovf0, ovf1;
+    SAI_TRY(cnt.alloc(sizeof(int32_t) * nn, st, true));
+    SAI_TRY(rows.alloc(sizeof(int32_t) * nn * smax, st, true));
+    SAI_TRY(vals.alloc(sizeof(double) * nn * smax, st, true));
+    SAI_TRY(tier.alloc(sizeof(int32_t) * nn, st, true));
+    SAI_TRY(P->loops.alloc(sizeof(int32_t) * nn, st, async));
+    SAI_TRY(P->res.alloc(sizeof(double) * nn, st, async));
+    SAI_TRY(P->res_post.alloc(sizeof(double) * nn, st, async));
+    SAI_TRY(ctr.alloc(sizeof(int) * 16, st, true));
+    SAI_TRY(ovf0.alloc(sizeof(int32_t) * nn, st, true));
+    SAI_TRY(ovf1.alloc(sizeof(int32_t) * nn, st, true));
+    SAI_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(int) * 16, st));
+    SAI_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * nn, st));
+    SAI_CUDA(cudaMemsetAsync(P->res_post.p, 0, sizeof(double) * nn, st));
+    int* c = ctr.as<int>();  // [0] next, [1] ovf count t0, [2] ovf count t1, [3] err, [4..] stats
+    Out out;
+    out.smax = smax;
+    out.cnt = cnt.as<int32_t>();
+    out.rows = rows.as<int32_t>();
+    out.vals = vals.as<double>();
+    out.loops = P->loops.as<int32_t>();
+    out.res = P->res.as<double>();
+    out.res_post = PSAI ? P->res_post.as<double>() : nullptr;
+    out.tier = tier.as<int32_t>();
+
+    SAI_TRY((launch_tier<Tier0, true, PSAI>(A, sa, pa, nullptr, n, c + 0, out, ovf0.as<int32_t>(), c + 1, c + 3, 0,
+                                            st)));
+    int hc[4];
+    SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    if (hc[1] > 0) {
+        SAI_TRY((launch_tier<Tier1, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), hc[1], c + 0, out, ovf1.as<int32_t>(),
+                                                 c + 2, c + 3, 1, st)));
+        SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaStreamSynchronize(st));
+        if (hc[2] > 0)
+            SAI_TRY((launch_tier<Tier2, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out, nullptr,
+                                                     nullptr, c + 3, 2, st)));
+    }
+    // assemble M (CSC, rows ascending) and its CSR copy
+    SAI_TRY(P->M_cp.alloc(sizeof(int64_t) * (nn + 1), st, async));
+    SAI_TRY(sai_scan_counts_i32(cnt.as<int32_t>(), P->M_cp.as<int64_t>(), n, st));
+    int64_t nnzM = 0;
+    SAI_CUDA(cudaMemcpyAsync(&nnzM, P->M_cp.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    if (hc[3] & 2) return SAI_SINGULAR;
+    if (hc[3] & 1) return SAI_PATTERN_OVERFLOW;
+    P->nnz = nnzM;
+    SAI_TRY(P->M_ri.alloc(sizeof(int32_t) * (size_t)(nnzM > 0 ? nnzM : 1), st, async));
+    SAI_TRY(P->M_v.alloc(sizeof(double) * (size_t)(nnzM > 0 ? nnzM : 1), st, async));
+    if (n > 0)
+        k_assemble<<<sai_div_up((int64_t)n * 32, 256), 256, 0, st>>>(n, smax, cnt.as<int32_t>(), rows.as<int32_t>(),
+                                                                     vals.as<double>(), P->M_cp.as<int64_t>(),
+                                                                     P->M_ri.as<int32_t>(), P->M_v.as<double>());
+    SAI_CUDA(cudaGetLastError());
+    SAI_TRY(sai_csc_to_csr(n, n, nnzM, P->M_cp.as<int64_t>(), P->M_ri.as<int32_t>(), P->M_v.as<double>(), P->Mr_rp,
+                           P->Mr_ci, P->Mr_v, st, async));
+    SAI_CUDA(cudaEventRecord(e1, st));
+    if (n > 0) {
+        k_stats<<<g_num_sms * 2, 256, 0, st>>>(n, P->loops.as<int32_t>(), P->res.as<double>(), delta, c + 4);
+        k_tier_count<<<g_num_sms * 2, 256, 0, st>>>(n, tier.as<int32_t>(), c + 4);
+    }
+    SAI_CUDA(cudaGetLastError());
+    int hs[5];
+    SAI_CUDA(cudaMemcpyAsync(hs, c + 4, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    P->n_c = hs[0];
+    P->l_m = hs[1];
+    P->n_tier[0] = hs[2];
+    P->n_tier[1] = hs[3];
+    P->n_tier[2] = hs[4];
+    SAI_CUDA(cudaEventElapsedTime(&P->ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return SAI_OK;
+}
+
+}  // namespace
+
+sai_status sai_spai_build(const sai_split_s* h, const sai_spai_params* prm, cudaStream_t st, bool async,
+                          sai_precond_s* P)
+{
+    if (!h || !prm || !P) return SAI_INVALID_ARG;
+    if (prm->mn < 1 || prm->mn > MNMAX || prm->max_aug < 0 || prm->key_bits < 1 || prm->key_bits > 31 ||
+        !(prm->delta >= 0.0))
+        return SAI_INVALID_ARG;
+    if (prm->precision != SAI_FP64) return SAI_NOT_IMPLEMENTED;
+    SpaiArgs sa;
+    sa.delta = prm->delta;
+    sa.scale = ldexp(1.0, prm->key_bits);
+    sa.mn = prm->mn;
+    sa.max_aug = prm->max_aug;
+    PsaiArgs pa = {};
+    long long bound = 1 + (long long)prm->mn * prm->max_aug;
+    int32_t smax = (int32_t)(bound < Tier2::SCAP ? bound : Tier2::SCAP);
+    return build_common<false>(h, sa, pa, smax, prm->delta, st, async, P);
+}
+
+sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cudaStream_t st, bool async,
+                          sai_precond_s* P)
+{
+    if (!h || !prm || !P) return SAI_INVALID_ARG;
+    if (prm->lmax < 0 || (prm->tol_mode != 0 && prm->tol_mode != 1) || !(prm->delta >= 0.0) || !(prm->tol >= 0.0))
+        return SAI_INVALID_ARG;
+    if (prm->precision != SAI_FP64) return SAI_NOT_IMPLEMENTED;
+    SpaiArgs sa = {};
+    PsaiArgs pa;
+    pa.delta = prm->delta;
+    pa.tol = prm->tol;
+    pa.tol_mode = prm->tol_mode;
+    pa.lmax = prm->lmax;
+    return build_common<true>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
+}

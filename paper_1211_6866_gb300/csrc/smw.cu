@@ -1,0 +1,146 @@
+// smw.cu -- Sherman-Morrison-Woodbury recovery of x (Theorem 1; eq.
+// (composi)): xhat = yhat - What (I + V^T What)^{-1} (V^T yhat), with
+// V = [e_J0 .. e_J(s-1)], so V^T What is What(J,:) and V^T yhat is yhat(J).
+//   k_smw_gather   C = I + What(J,:) (column-major s x s), g = yhat(J)
+//   k_lu_solve     Gaussian elimination with partial pivoting (first largest
+//                  |pivot| wins), one block; z = C^{-1} g, c = ||z||
+//   k_smw_update   xhat(i) = yhat(i) - sum_t What(i,t) z_t, one thread per row
+#include <math.h>
+
+#include "internal.h"
+
+namespace {
+
+__global__ void k_smw_gather(int32_t n, int32_t s, const int32_t* J, const double* Y, double* C, double* g)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)s * s) return;
+    const int col = (int)(t / s), row = (int)(t - (int64_t)col * s);  // C(row, col)
+    const int64_t ld = (int64_t)s + 1;
+    C[(int64_t)col * s + row] = (row == col ? 1.0 : 0.0) + Y[(int64_t)J[row] * ld + 1 + col];
+    if (col == 0) g[row] = Y[(int64_t)J[row] * ld];
+}
+
+__global__ void k_lu_solve(int32_t s, double* C, double* g, double* z, double* c_out, int* err)
+{
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    __shared__ int piv_s;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = 0; k < s; ++k) {
+        double best = -1.0;
+        int bidx = s;
+        for (int i = k + tid; i < s; i += nt) {
+            const double a = fabs(C[(int64_t)k * s + i]);
+            if (a > best) {
+                best = a;
+                bidx = i;
+            }
+        }
+        bv[tid] = best;
+        bi[tid] = bidx;
+        __syncthreads();
+        for (int w = nt >> 1; w > 0; w >>= 1) {
+            if (tid < w) {
+                const double ov = bv[tid + w];
+                const int oi = bi[tid + w];
+                if (ov > bv[tid] || (ov == bv[tid] && oi < bi[tid])) {
+                    bv[tid] = ov;
+                    bi[tid] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        if (tid == 0) piv_s = (bv[0] > 0.0) ? bi[0] : -1;
+        __syncthreads();
+        const int piv = piv_s;
+        if (piv < 0) {
+            if (tid == 0) *err = 1;
+            return;
+        }
+        if (piv != k) {
+            for (int j = tid; j < s; j += nt) {
+                const double tmp = C[(int64_t)j * s + k];
+                C[(int64_t)j * s + k] = C[(int64_t)j * s + piv];
+                C[(int64_t)j * s + piv] = tmp;
+            }
+            if (tid == 0) {
+                const double tmp = g[k];
+                g[k] = g[piv];
+                g[piv] = tmp;
+            }
+        }
+        __syncthreads();
+        const double akk = C[(int64_t)k * s + k];
+        const double gk = g[k];
+        for (int i = k + 1 + tid; i < s; i += nt) {
+            const double l = C[(int64_t)k * s + i] / akk;
+            C[(int64_t)k * s + i] = l;
+            for (int j = k + 1; j < s; ++j) C[(int64_t)j * s + i] -= l * C[(int64_t)j * s + k];
+            g[i] -= l * gk;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < s; i += nt) z[i] = g[i];
+    __syncthreads();
+    for (int j = s - 1; j >= 0; --j) {
+        if (tid == 0) z[j] = z[j] / C[(int64_t)j * s + j];
+        __syncthreads();
+        const double zj = z[j];
+        for (int i = tid; i < j; i += nt) z[i] -= C[(int64_t)j * s + i] * zj;
+        __syncthreads();
+    }
+    double acc = 0.0;
+    for (int i = tid; i < s; i += nt) acc += z[i] * z[i];
+    bv[tid] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < nt; ++q) t += bv[q];
+        *c_out = sqrt(t);
+    }
+}
+
+__global__ void k_smw_update(int32_t n, int32_t s, const double* Y, const double* z, double* x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t ld = (int64_t)s + 1;
+    const double* row = Y + i * ld;
+    double v = row[0];
+    for (int t = 0; t < s; ++t) v = fma(-row[1 + t], z[t], v);
+    x[i] = v;
+}
+
+}  // namespace
+
+sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st)
+{
+    if (!h || (h->n > 0 && (!Y || !x))) return SAI_INVALID_ARG;
+    const int32_t n = h->n, s = h->s;
+    const size_t ss = (size_t)(s > 0 ? s : 1);
+    Buf C, g, z, cbuf, err;
+    SAI_TRY(C.alloc(sizeof(double) * ss * ss, st, true));
+    SAI_TRY(g.alloc(sizeof(double) * ss, st, true));
+    SAI_TRY(z.alloc(sizeof(double) * ss, st, true));
+    SAI_TRY(cbuf.alloc(sizeof(double), st, true));
+    SAI_TRY(err.alloc(sizeof(int), st, true));
+    SAI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    SAI_CUDA(cudaMemsetAsync(cbuf.p, 0, sizeof(double), st));
+    if (s > 0) {
+        k_smw_gather<<<sai_div_up((int64_t)s * s, 256), 256, 0, st>>>(n, s, h->J.as<int32_t>(), Y, C.as<double>(),
+                                                                    g.as<double>());
+        k_lu_solve<<<1, 1024, 0, st>>>(s, C.as<double>(), g.as<double>(), z.as<double>(), cbuf.as<double>(),
+                                       err.as<int>());
+    }
+    if (n > 0) k_smw_update<<<sai_div_up(n, 256), 256, 0, st>>>(n, s, Y, z.as<double>(), x);
+    SAI_CUDA(cudaGetLastError());
+    int herr = 0;
+    double hc = 0.0;
+    SAI_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaMemcpyAsync(&hc, cbuf.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    if (herr) return SAI_SINGULAR;
+    if (c_out) *c_out = hc;
+    return SAI_OK;
+}

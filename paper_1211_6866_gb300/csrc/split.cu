@@ -1,0 +1,215 @@
+// split.cu -- dense-column detection and sparsification (section 4 of the
+// paper; eq. (split) A = A~ + U V^T).
+//
+// Kernels:
+//   k_flag_dense    nnz(a_j) = col_ptr[j+1]-col_ptr[j] > tau      (one thread / column)
+//   k_compact_J     J = ascending list of flagged columns           (scan + scatter)
+//   k_window        for each irregular column: the kept entries are a contiguous
+//                   window of its sorted rows around the diagonal (diagonal plus the
+//                   p_keep-1 nearest, ties to the smaller row)      (one thread / column)
+//   k_copy_split    copies A into A~ (window only for irregular columns) and U
+//                   (the rest)                                      (one warp / column)
+//   k_colstats      ||a~_j||^2 and sum_i |a~_ij| per column, max -> ||A~||_1
+#include "internal.h"
+
+__global__ void k_flag_dense(int32_t n, const int64_t* cp, double tau, int ge, int32_t* flag)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double c = (double)(cp[j + 1] - cp[j]);
+    flag[j] = ge ? (c >= tau) : (c > tau);
+}
+
+__global__ void k_compact_J(int32_t n, const int32_t* flag, const int64_t* pos, int32_t* J)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (flag[j]) J[pos[j]] = (int32_t)j;
+}
+
+// Two-pointer walk outwards from the diagonal: the kept set of an irregular
+// column is [w0, w1) in its sorted entry range.
+__global__ void k_window(int32_t s, const int32_t* J, const int64_t* cp, const int32_t* ri, int32_t p_keep,
+                         int64_t* w0, int64_t* w1)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= s) return;
+    int32_t j = J[t];
+    int64_t b = cp[j], e = cp[j + 1];
+    int64_t lo = b, hi = e;  // binary search: first row >= j
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (ri[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    int64_t mid = lo;
+    int64_t left = mid - 1, right = mid;  // next candidates on each side
+    int32_t kept = 0;
+    int64_t a0 = mid, a1 = mid;           // window [a0, a1)
+    if (mid < e && ri[mid] == j) {
+        kept = 1;
+        right = mid + 1;
+        a1 = mid + 1;
+    }
+    while (kept < p_keep && (left >= b || right < e)) {
+        bool take_left;
+        if (left < b) take_left = false;
+        else if (right >= e) take_left = true;
+        else take_left = ((int64_t)j - ri[left]) <= ((int64_t)ri[right] - j);
+        if (take_left) {
+            a0 = left;
+            --left;
+        } else {
+            a1 = right + 1;
+            ++right;
+        }
+        ++kept;
+    }
+    w0[t] = a0;
+    w1[t] = a1;
+}
+
+__global__ void k_count_split(int32_t n, const int64_t* cp, const int32_t* flag, const int64_t* pos,
+                              const int64_t* w0, const int64_t* w1, int64_t* cnt_At, int64_t* cnt_U)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int64_t c = cp[j + 1] - cp[j];
+    if (flag[j]) {
+        int64_t t = pos[j];
+        int64_t kept = w1[t] - w0[t];
+        cnt_At[j] = kept;
+        cnt_U[t] = c - kept;
+    } else {
+        cnt_At[j] = c;
+    }
+}
+
+__global__ void k_copy_split(int32_t n, const int64_t* cp, const int32_t* ri, const double* v,
+                             const int32_t* flag, const int64_t* pos, const int64_t* w0, const int64_t* w1,
+                             const int64_t* At_cp, int32_t* At_ri, double* At_v, const int64_t* U_cp,
+                             int32_t* U_ri, double* U_v)
+{
+    int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    int64_t b = cp[j], e = cp[j + 1];
+    int64_t oa = At_cp[j];
+    if (!flag[j]) {
+        for (int64_t q = b + lane; q < e; q += 32) {
+            At_ri[oa + (q - b)] = ri[q];
+            At_v[oa + (q - b)] = v[q];
+        }
+        return;
+    }
+    int64_t t = pos[j];
+    int64_t a0 = w0[t], a1 = w1[t];
+    int64_t ou = U_cp[t];
+    for (int64_t q = b + lane; q < e; q += 32) {
+        if (q >= a0 && q < a1) {
+            At_ri[oa + (q - a0)] = ri[q];
+            At_v[oa + (q - a0)] = v[q];
+        } else {
+            int64_t d = q < a0 ? (q - b) : (q - b) - (a1 - a0);
+            U_ri[ou + d] = ri[q];
+            U_v[ou + d] = v[q];
+        }
+    }
+}
+
+__global__ void k_colstats(int32_t n, const int64_t* cp, const double* v, double* colnorm2,
+                           unsigned long long* norm1_bits)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s2 = 0.0, s1 = 0.0;
+    for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
+        s2 += v[q] * v[q];
+        s1 += fabs(v[q]);
+    }
+    colnorm2[j] = s2;
+    // non-negative doubles order like their bit patterns
+    atomicMax(norm1_bits, (unsigned long long)__double_as_longlong(s1));
+}
+
+sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, cudaStream_t st, bool async,
+                           sai_split_s* h)
+{
+    if (!A || !prm || !h || A->n < 0 || A->nnz < 0) return SAI_INVALID_ARG;
+    if (A->n > 0 && (!A->col_ptr || (A->nnz > 0 && (!A->row_idx || !A->val)))) return SAI_INVALID_ARG;
+    const int32_t n = A->n;
+    const int64_t nnz = A->nnz;
+    SAI_TRY(sai_validate_csc(n, n, nnz, A->col_ptr, A->row_idx, st));
+    cudaEvent_t e0, e1;
+    SAI_CUDA(cudaEventCreate(&e0));
+    SAI_CUDA(cudaEventCreate(&e1));
+    SAI_CUDA(cudaEventRecord(e0, st));
+
+    h->n = n;
+    h->p = n > 0 ? (int32_t)(nnz / n) : 0;
+    h->tau = prm->abs_tau >= 0.0 ? prm->abs_tau : prm->thresh_mult * (double)h->p;
+    h->p_keep = prm->p_keep > 0 ? prm->p_keep : (h->p > 0 ? h->p : 1);
+    const unsigned gb = sai_div_up(n > 0 ? n : 1, 256);
+
+    Buf flag, pos;
+    SAI_TRY(flag.alloc(sizeof(int32_t) * (size_t)(n + 1), st, true));
+    SAI_TRY(pos.alloc(sizeof(int64_t) * (size_t)(n + 1), st, true));
+    if (n > 0) k_flag_dense<<<gb, 256, 0, st>>>(n, A->col_ptr, h->tau, prm->ge, flag.as<int32_t>());
+    SAI_TRY(sai_scan_counts_i32(flag.as<int32_t>(), pos.as<int64_t>(), n, st));
+    int64_t s64 = 0;
+    SAI_CUDA(cudaMemcpyAsync(&s64, pos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    h->s = (int32_t)s64;
+    const int32_t s = h->s;
+
+    SAI_TRY(h->J.alloc(sizeof(int32_t) * (size_t)(s > 0 ? s : 1), st, async));
+    if (n > 0) k_compact_J<<<gb, 256, 0, st>>>(n, flag.as<int32_t>(), pos.as<int64_t>(), h->J.as<int32_t>());
+    Buf w0, w1, cntA, cntU;
+    SAI_TRY(w0.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
+    SAI_TRY(w1.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
+    SAI_TRY(cntA.alloc(sizeof(int64_t) * (size_t)(n + 1), st, true));
+    SAI_TRY(cntU.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
+    if (s > 0)
+        k_window<<<sai_div_up(s, 128), 128, 0, st>>>(s, h->J.as<int32_t>(), A->col_ptr, A->row_idx, h->p_keep,
+                                                     w0.as<int64_t>(), w1.as<int64_t>());
+    if (n > 0)
+        k_count_split<<<gb, 256, 0, st>>>(n, A->col_ptr, flag.as<int32_t>(), pos.as<int64_t>(), w0.as<int64_t>(),
+                                          w1.as<int64_t>(), cntA.as<int64_t>(), cntU.as<int64_t>());
+    SAI_TRY(h->At_cp.alloc(sizeof(int64_t) * (size_t)(n + 1), st, async));
+    SAI_TRY(h->U_cp.alloc(sizeof(int64_t) * (size_t)(s + 1), st, async));
+    SAI_TRY(sai_scan_counts_i64(cntA.as<int64_t>(), h->At_cp.as<int64_t>(), n, st));
+    SAI_TRY(sai_scan_counts_i64(cntU.as<int64_t>(), h->U_cp.as<int64_t>(), s, st));
+    int64_t tot[2] = {0, 0};
+    SAI_CUDA(cudaMemcpyAsync(&tot[0], h->At_cp.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaMemcpyAsync(&tot[1], h->U_cp.as<int64_t>() + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    h->nnz_At = tot[0];
+    h->nnz_U = tot[1];
+    SAI_TRY(h->At_ri.alloc(sizeof(int32_t) * (size_t)(h->nnz_At > 0 ? h->nnz_At : 1), st, async));
+    SAI_TRY(h->At_v.alloc(sizeof(double) * (size_t)(h->nnz_At > 0 ? h->nnz_At : 1), st, async));
+    SAI_TRY(h->U_ri.alloc(sizeof(int32_t) * (size_t)(h->nnz_U > 0 ? h->nnz_U : 1), st, async));
+    SAI_TRY(h->U_v.alloc(sizeof(double) * (size_t)(h->nnz_U > 0 ? h->nnz_U : 1), st, async));
+    if (n > 0)
+        k_copy_split<<<sai_div_up((int64_t)n * 32, 256), 256, 0, st>>>(
+            n, A->col_ptr, A->row_idx, A->val, flag.as<int32_t>(), pos.as<int64_t>(), w0.as<int64_t>(),
+            w1.as<int64_t>(), h->At_cp.as<int64_t>(), h->At_ri.as<int32_t>(), h->At_v.as<double>(),
+            h->U_cp.as<int64_t>(), h->U_ri.as<int32_t>(), h->U_v.as<double>());
+    SAI_CUDA(cudaGetLastError());
+    SAI_TRY(sai_csc_to_csr(n, n, h->nnz_At, h->At_cp.as<int64_t>(), h->At_ri.as<int32_t>(), h->At_v.as<double>(),
+                           h->Atr_rp, h->Atr_ci, h->Atr_v, st, async));
+    SAI_TRY(h->colnorm2.alloc(sizeof(double) * (size_t)(n > 0 ? n : 1), st, async));
+    Buf n1;
+    SAI_TRY(n1.alloc(sizeof(unsigned long long), st, true));
+    SAI_CUDA(cudaMemsetAsync(n1.p, 0, sizeof(unsigned long long), st));
+    if (n > 0)
+        k_colstats<<<gb, 256, 0, st>>>(n, h->At_cp.as<int64_t>(), h->At_v.as<double>(), h->colnorm2.as<double>(),
+                                       n1.as<unsigned long long>());
+    SAI_CUDA(cudaGetLastError());
+    SAI_CUDA(cudaMemcpyAsync(&h->norm1, n1.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaEventRecord(e1, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    SAI_CUDA(cudaEventElapsedTime(&h->ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return SAI_OK;
+}
