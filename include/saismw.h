@@ -225,6 +225,35 @@ typedef struct {
 sai_status sai_solve(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
                      int32_t* iters, int32_t iters_cap, sai_solve_report* rep, sai_stream_t stream);
 
+/* ----------------------------------------------------------------------
+ * Diagnostics (not part of the paper's method): launch counting and the
+ * per-kernel measurements behind the roofline figures.
+ * ---------------------------------------------------------------------- */
+#define SAI_PROF_MAX_SITES 8
+
+typedef struct {
+    char name[24];
+    int64_t launches;   /* launches of this site while the profile was open */
+    double ms;          /* sum of their CUDA-event durations */
+    double bytes;       /* algorithmic bytes moved by those launches */
+    double flops;       /* algorithmic floating-point operations */
+} sai_profile_site;
+
+typedef struct {
+    uint64_t launches;  /* all kernel launches of the library while open */
+    int32_t nsites;
+    sai_profile_site site[SAI_PROF_MAX_SITES];
+} sai_profile_report;
+
+/* Total number of kernel launches made by the library in this process. */
+uint64_t sai_launch_count(void);
+/* Opens a profile: resets the counters and brackets every launch of the
+ * profiled sites (SAI build, Krylov SpMM, GMRES projections and updates,
+ * BiCGStab vector kernels) with CUDA events on its stream. */
+sai_status sai_profile_begin(void);
+/* Closes the profile: synchronises the device, fills *out. */
+sai_status sai_profile_end(sai_profile_report* out);
+
 #ifdef __cplusplus
 }
 #endif

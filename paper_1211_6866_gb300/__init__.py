@@ -17,7 +17,7 @@ from dataclasses import dataclass
 import torch
 
 __all__ = ["CscMatrix", "SaiError", "split", "build_spai", "build_psai", "krylov_solve", "smw_recover",
-           "rel_resid", "solve", "library_path", "load"]
+           "rel_resid", "solve", "library_path", "load", "profile_begin", "profile_end", "launch_count"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "libsaismw.so")
@@ -79,6 +79,15 @@ class _SolveReport(C.Structure):
                 ("ms_krylov", C.c_double), ("ms_smw", C.c_double)]
 
 
+class _ProfSite(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
+class _ProfReport(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("nsites", C.c_int32), ("site", _ProfSite * 8)]
+
+
 _lib = None
 
 
@@ -114,7 +123,11 @@ def load():
     L.sai_rel_resid.argtypes = [C.POINTER(_CscView), dp, dp, C.POINTER(C.c_double), vp]
     L.sai_solve.argtypes = [C.POINTER(_CscView), dp, C.POINTER(_SolveParams), dp, C.POINTER(C.c_int32), i32,
                             C.POINTER(_SolveReport), vp]
-    for f in ("sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
+    L.sai_launch_count.restype = C.c_uint64
+    L.sai_launch_count.argtypes = []
+    L.sai_profile_begin.argtypes = []
+    L.sai_profile_end.argtypes = [C.POINTER(_ProfReport)]
+    for f in ("sai_profile_begin", "sai_profile_end", "sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
               "sai_precond_get_info", "sai_precond_copy_out", "sai_krylov_solve", "sai_smw_recover",
               "sai_rel_resid", "sai_solve"):
         getattr(L, f).restype = C.c_int
@@ -303,3 +316,24 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
                   ms_split=rep.ms_split, ms_build=rep.ms_build, ms_krylov=rep.ms_krylov, ms_smw=rep.ms_smw,
                   build_ms=rep.precond.build_ms)
     return x, list(iters[: s + 1]), report
+
+
+def launch_count():
+    """Kernel launches made by the library so far in this process."""
+    return int(load().sai_launch_count())
+
+
+def profile_begin():
+    """Open a profile: per-site CUDA-event timing and algorithmic work counters."""
+    _check("sai_profile_begin", load().sai_profile_begin())
+
+
+def profile_end():
+    """Close the profile; returns {"launches": L, "sites": {name: {launches, ms, bytes, flops}}}."""
+    rep = _ProfReport()
+    _check("sai_profile_end", load().sai_profile_end(C.byref(rep)))
+    sites = {}
+    for q in range(rep.nsites):
+        st = rep.site[q]
+        sites[st.name.decode()] = dict(launches=int(st.launches), ms=st.ms, bytes=st.bytes, flops=st.flops)
+    return {"launches": int(rep.launches), "sites": sites}

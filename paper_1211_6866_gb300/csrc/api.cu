@@ -3,9 +3,34 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <atomic>
+#include <mutex>
 #include <new>
+#include <string.h>
+#include <vector>
 
 #include "internal.h"
+
+// ---------------------------------------------------------------- accounting
+static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mu;
+// Events are created up front when a profile opens, so that bracketing a
+// launch costs two cudaEventRecord calls and no allocation.
+static std::vector<cudaEvent_t> g_ev_pool;
+static std::atomic<size_t> g_ev_next{0};
+static std::vector<std::pair<size_t, size_t>> g_prof_ev[PROF_NSITES];
+static const char* k_site_names[PROF_NSITES] = {"sai_build", "krylov_spmm", "gmres_project", "gmres_update",
+                                                "bicgstab_vector"};
+static const size_t k_ev_pool = 1 << 16;
+
+unsigned sai_count_grid(unsigned g)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return g;
+}
+
+bool sai_prof_on() { return g_prof.load(std::memory_order_relaxed); }
 
 void sai_internal_note_cuda_error(cudaError_t e, const char* what, const char* file, int line)
 {
@@ -31,7 +56,77 @@ void sai_pool_init_once()
 
 static inline cudaStream_t S(sai_stream_t s) { return (cudaStream_t)s; }
 
+ProfScope::ProfScope(int site_, cudaStream_t st_) : site(site_), st(st_)
+{
+    if (!sai_prof_on()) return;
+    const size_t i = g_ev_next.fetch_add(2);
+    if (i + 1 >= g_ev_pool.size()) return;
+    idx = (long long)i;
+    cudaEventRecord(g_ev_pool[i], st);
+}
+
+ProfScope::~ProfScope()
+{
+    if (idx < 0) return;
+    const size_t i = (size_t)idx;
+    cudaEventRecord(g_ev_pool[i + 1], st);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_ev[site].emplace_back(i, i + 1);
+}
+
 extern "C" {
+
+uint64_t sai_launch_count(void) { return g_launches.load(); }
+
+sai_status sai_profile_begin(void)
+{
+    SAI_CUDA(cudaDeviceSynchronize());
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (auto& v : g_prof_ev) v.clear();
+        if (g_ev_pool.empty()) {
+            g_ev_pool.resize(k_ev_pool);
+            for (auto& e : g_ev_pool) SAI_CUDA(cudaEventCreate(&e));
+        }
+        g_ev_next.store(0);
+    }
+    SAI_TRY(sai_krylov_work_reset());
+    SAI_TRY(sai_build_work_reset());
+    SAI_CUDA(cudaDeviceSynchronize());
+    g_launches.store(0);
+    g_prof.store(true);
+    return SAI_OK;
+}
+
+sai_status sai_profile_end(sai_profile_report* out)
+{
+    if (!out) return SAI_INVALID_ARG;
+    g_prof.store(false);
+    SAI_CUDA(cudaDeviceSynchronize());
+    memset(out, 0, sizeof(*out));
+    out->launches = g_launches.load();
+    double wk[PROF_NSITES * 2], wb[PROF_NSITES * 2];
+    SAI_TRY(sai_krylov_work_read(wk));
+    SAI_TRY(sai_build_work_read(wb));
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    out->nsites = PROF_NSITES;
+    for (int q = 0; q < PROF_NSITES; ++q) {
+        sai_profile_site& ps = out->site[q];
+        strncpy(ps.name, k_site_names[q], sizeof(ps.name) - 1);
+        ps.launches = (int64_t)g_prof_ev[q].size();
+        double ms = 0.0;
+        for (auto& pr : g_prof_ev[q]) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, g_ev_pool[pr.first], g_ev_pool[pr.second]);
+            ms += t;
+        }
+        g_prof_ev[q].clear();
+        ps.ms = ms;
+        ps.bytes = wk[2 * q] + wb[2 * q];
+        ps.flops = wk[2 * q + 1] + wb[2 * q + 1];
+    }
+    return SAI_OK;
+}
 
 const char* sai_status_string(sai_status st)
 {
@@ -247,11 +342,11 @@ sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_pa
     SAI_TRY(Bb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
     SAI_TRY(Yb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
     SAI_TRY(nb.alloc(sizeof(double), st, true));
-    if (n > 0) k_fill_rhs<<<sai_div_up(n, 256), 256, 0, st>>>(n, s, b, nullptr, nullptr, nullptr, Bb.as<double>());
+    if (n > 0) k_fill_rhs<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, b, nullptr, nullptr, nullptr, Bb.as<double>());
     if (s > 0)
-        k_scatter_U<<<s, 256, 0, st>>>(s, h.U_cp.as<int64_t>(), h.U_ri.as<int32_t>(), h.U_v.as<double>(),
+        k_scatter_U<<<SAI_GRID(s), 256, 0, st>>>(s, h.U_cp.as<int64_t>(), h.U_ri.as<int32_t>(), h.U_v.as<double>(),
                                        Bb.as<double>());
-    k_sumsq<<<1, 1024, 0, st>>>(n, b, nb.as<double>());
+    k_sumsq<<<SAI_GRID(1), 1024, 0, st>>>(n, b, nb.as<double>());
     SAI_CUDA(cudaGetLastError());
     double bb = 0.0;
     SAI_CUDA(cudaMemcpyAsync(&bb, nb.p, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -55,34 +55,28 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
-// Stream-ordered device buffer owned by host code (RAII, frees on the stream).
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    cudaStream_t st = nullptr;
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() { release(); }
-    sai_status alloc(size_t nbytes, cudaStream_t s)
-    {
-        release();
-        st = s;
-        bytes = nbytes;
-        if (nbytes == 0) return SAI_OK;
-        cudaError_t e = cudaMallocAsync(&p, nbytes, s);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            sai_internal_note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
-            return e == cudaErrorMemoryAllocation ? SAI_OOM : SAI_CUDA_ERROR;
-        }
-        return SAI_OK;
-    }
-    void release()
-    {
-        if (p) cudaFreeAsync(p, st);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <class T> T* as() const { return static_cast<T*>(p); }
+// ---------------------------------------------------------------- accounting
+// Every kernel launch of the library passes its grid size through SAI_GRID,
+// which counts the launch (the expression is only evaluated when the launch
+// statement runs).
+unsigned sai_count_grid(unsigned g);
+#define SAI_GRID(g) sai_count_grid((unsigned)(g))
+
+// Profiled launch sites: CUDA events around each launch (only while a
+// profile is open) plus algorithmic bytes / flops accumulated on the device.
+enum {
+    PROF_SAI_BUILD = 0,  // k_sai, all tiers
+    PROF_SPMM = 1,       // SpMM of the Krylov inner iterations
+    PROF_GM_DOTS = 2,    // GMRES projections V^T w
+    PROF_GM_UPDATE = 3,  // GMRES updates w -= V h
+    PROF_BICG_VEC = 4,   // BiCGStab vector updates and inner products
+    PROF_NSITES = 5
 };
+struct ProfScope {
+    int site;
+    cudaStream_t st;
+    long long idx = -1;  // index of the first event of the pair in the pool
+    ProfScope(int site_, cudaStream_t st_);
+    ~ProfScope();
+};
+bool sai_prof_on();

@@ -82,3 +82,10 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
 sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st);
 
 void sai_pool_init_once();
+
+// Device-side algorithmic work per profiled site ([site][0] bytes, [1] flops),
+// one accumulator per translation unit.
+sai_status sai_krylov_work_reset();
+sai_status sai_krylov_work_read(double* out /* PROF_NSITES x 2 */);
+sai_status sai_build_work_reset();
+sai_status sai_build_work_read(double* out /* PROF_NSITES x 2 */);

@@ -107,12 +107,12 @@ void spmm_m(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, in
     if (blocks < 1) blocks = 1;
     const unsigned g = (unsigned)blocks;
     switch (G) {
-    case 1: k_spmm_m<1, MODE><<<g, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
-    case 2: k_spmm_m<2, MODE><<<g, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
-    case 4: k_spmm_m<4, MODE><<<g, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
-    case 8: k_spmm_m<8, MODE><<<g, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
-    case 16: k_spmm_m<16, MODE><<<g, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
-    default: k_spmm_m<32, MODE><<<g, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
+    case 1: k_spmm_m<1, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
+    case 2: k_spmm_m<2, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
+    case 4: k_spmm_m<4, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
+    case 8: k_spmm_m<8, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
+    case 16: k_spmm_m<16, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
+    default: k_spmm_m<32, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B, mask); break;
     }
 }
 
@@ -123,6 +123,26 @@ struct Sys {  // per-system state, arrays of k
 };
 
 enum { ST_OK = 0, ST_MAXITER = 5, ST_BREAKDOWN = 6 };  // same values as sai_status
+
+// Algorithmic work of the profiled sites, accumulated by the single-block
+// finalize kernels from the number of systems that took part in each launch.
+__device__ double d_kwork[PROF_NSITES * 2];
+
+struct Dims {  // sizes for the work accounting
+    double n, nnzA, nnzM;
+};
+
+__device__ __forceinline__ void kwork_add(int site, double bytes, double flops)
+{
+    atomicAdd(&d_kwork[2 * site], bytes);
+    atomicAdd(&d_kwork[2 * site + 1], flops);
+}
+
+// one SpMM launch over the k_act unmasked systems: matrix once, X read once, Y written
+__device__ __forceinline__ void spmm_work(double n, double nnz, int kact)
+{
+    if (kact > 0) kwork_add(PROF_SPMM, 8.0 * (n + 1) + 12.0 * nnz + 16.0 * n * kact, 2.0 * nnz * kact);
+}
 
 // ================================================================== BiCGStab
 __global__ void k_bicg_init(int64_t n, int k, const double* B, double* x, double* r, double* rh, double* p,
@@ -205,9 +225,15 @@ __global__ void k_dot1(int64_t n, int k, const double* a, const double* b, const
     block_partials<1>(acc, rc, k, part);
 }
 
-__global__ void k_bicg_f1(int k, int nblk, const double* part, Sys S)
+__global__ void k_bicg_f1(int k, int nblk, const double* part, Sys S, Dims D)
 {
     const int c = threadIdx.x;
+    const int k1 = __syncthreads_count(c < k && S.active[c]);
+    if (c == 0 && k1 > 0) {
+        spmm_work(D.n, D.nnzM, k1);
+        spmm_work(D.n, D.nnzA, k1);
+        kwork_add(PROF_BICG_VEC, 8.0 * D.n * k1 * (4 + 2), D.n * k1 * (3 + 2));  // p update, r^T v
+    }
     if (c >= k || !S.active[c]) return;
     const double rv = fin(part, 0, nblk, k, c);
     if (rv == 0.0) {
@@ -234,9 +260,11 @@ __global__ void k_bicg_s(int64_t n, int k, const double* r, const double* v, dou
     block_partials<1>(acc, rc, k, part);
 }
 
-__global__ void k_bicg_f2(int k, int nblk, const double* part, Sys S)
+__global__ void k_bicg_f2(int k, int nblk, const double* part, Sys S, Dims D)
 {
     const int c = threadIdx.x;
+    const int k2 = __syncthreads_count(c < k && S.active[c]);
+    if (c == 0 && k2 > 0) kwork_add(PROF_BICG_VEC, 8.0 * D.n * k2 * 3, D.n * k2 * 4.0);  // s = r - alpha v, ||s||
     if (c >= k) return;
     if (!S.active[c]) {
         S.go[c] = 0;
@@ -260,9 +288,15 @@ __global__ void k_dot2(int64_t n, int k, const double* t, const double* s, const
     block_partials<2>(acc, rc, k, part);
 }
 
-__global__ void k_bicg_f3(int k, int nblk, const double* part, Sys S)
+__global__ void k_bicg_f3(int k, int nblk, const double* part, Sys S, Dims D)
 {
     const int c = threadIdx.x;
+    const int k3 = __syncthreads_count(c < k && S.go[c]);
+    if (c == 0 && k3 > 0) {
+        spmm_work(D.n, D.nnzM, k3);
+        spmm_work(D.n, D.nnzA, k3);
+        kwork_add(PROF_BICG_VEC, 8.0 * D.n * k3 * 2, D.n * k3 * 4.0);  // t^T s, t^T t
+    }
     if (c >= k || !S.go[c]) return;
     const double ts = fin(part, 0, nblk, k, c), tt = fin(part, 1, nblk, k, c);
     if (tt == 0.0) {
@@ -300,9 +334,11 @@ __global__ void k_bicg_xr(int64_t n, int k, double* x, double* r, const double* 
     block_partials<2>(acc, rc, k, part);
 }
 
-__global__ void k_bicg_f4(int k, int nblk, const double* part, Sys S, int* any_active)
+__global__ void k_bicg_f4(int k, int nblk, const double* part, Sys S, Dims D, int* any_active)
 {
     const int c = threadIdx.x;
+    const int k4 = __syncthreads_count(c < k && S.active[c]);
+    if (c == 0 && k4 > 0) kwork_add(PROF_BICG_VEC, 8.0 * D.n * k4 * 8, D.n * k4 * 10.0);  // x, r, two dots
     int act = 0;
     if (c < k && S.active[c]) {
         const double rr = fin(part, 0, nblk, k, c), rhr = fin(part, 1, nblk, k, c);
@@ -467,9 +503,18 @@ __global__ void k_gm_update(int64_t n, int k, int j, double* w, Gm G, int pass, 
 }
 
 // H(:,j) = h0 + h1, ||w||, Givens rotations, residual estimate, stop tests
-__global__ void k_gm_givens(int k, int j, int nblk, const double* part, int maxit, Sys S, Gm G, int* any_adv)
+__global__ void k_gm_givens(int k, int j, int nblk, const double* part, int maxit, Sys S, Gm G, Dims D,
+                            int* any_adv)
 {
     const int c = threadIdx.x;
+    const int ka = __syncthreads_count(c < k && G.adv[c]);
+    if (c == 0 && ka > 0) {
+        spmm_work(D.n, D.nnzM, ka);
+        spmm_work(D.n, D.nnzA, ka);
+        // two CGS passes: V_0..j and w read (+ w written by the update)
+        kwork_add(PROF_GM_DOTS, 2.0 * 8.0 * D.n * ka * (j + 2), 2.0 * 2.0 * D.n * ka * (j + 1));
+        kwork_add(PROF_GM_UPDATE, 2.0 * 8.0 * D.n * ka * (j + 3), 2.0 * 2.0 * D.n * ka * (j + 1) + 2.0 * D.n * ka);
+    }
     int act = 0;
     if (c < k && G.adv[c]) {
         const int m = G.m;
@@ -646,6 +691,10 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     SAI_CUDA(cudaMemsetAsync(ii, 0, sizeof(int) * 10 * k, st));
     int* fl = flag.as<int>();
     int hflag = 0;
+    Dims D;
+    D.n = (double)n;
+    D.nnzA = (double)h->nnz_At;
+    D.nnzM = (double)P->nnz;
     const int check_every = 4;
 
     if (prm->method == SAI_BICGSTAB) {
@@ -659,24 +708,51 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         double* s = ph + blk;
         double* sh = s + blk;
         double* t = sh + blk;
-        k_bicg_init<<<nb, KT, 0, st>>>(n, k, B, X, r, rh, p, v, part.as<double>());
-        k_bicg_f0<<<1, KT, 0, st>>>(k, nb, part.as<double>(), S);
+        k_bicg_init<<<SAI_GRID(nb), KT, 0, st>>>(n, k, B, X, r, rh, p, v, part.as<double>());
+        k_bicg_f0<<<SAI_GRID(1), KT, 0, st>>>(k, nb, part.as<double>(), S);
         SAI_CUDA(cudaGetLastError());
         for (int it = 0; it < prm->maxit; ++it) {
-            k_bicg_start<<<1, KT, 0, st>>>(k, prm->maxit, S);
-            k_bicg_p<<<nb, KT, 0, st>>>(n, k, r, p, v, S);
-            spmm_m<0>(n, Mr, Mc, Mv, k, p, ph, nullptr, S.active, st);
-            spmm_m<0>(n, Ar, Ac, Av, k, ph, v, nullptr, S.active, st);
-            k_dot1<<<nb, KT, 0, st>>>(n, k, rh, v, S.active, part.as<double>());
-            k_bicg_f1<<<1, KT, 0, st>>>(k, nb, part.as<double>(), S);
-            k_bicg_s<<<nb, KT, 0, st>>>(n, k, r, v, s, S, part.as<double>());
-            k_bicg_f2<<<1, KT, 0, st>>>(k, nb, part.as<double>(), S);
-            spmm_m<0>(n, Mr, Mc, Mv, k, s, sh, nullptr, S.go, st);
-            spmm_m<0>(n, Ar, Ac, Av, k, sh, t, nullptr, S.go, st);
-            k_dot2<<<nb, KT, 0, st>>>(n, k, t, s, S.go, part.as<double>());
-            k_bicg_f3<<<1, KT, 0, st>>>(k, nb, part.as<double>(), S);
-            k_bicg_xr<<<nb, KT, 0, st>>>(n, k, X, r, rh, ph, sh, s, t, S, part.as<double>());
-            k_bicg_f4<<<1, KT, 0, st>>>(k, nb, part.as<double>(), S, fl);
+            k_bicg_start<<<SAI_GRID(1), KT, 0, st>>>(k, prm->maxit, S);
+            {
+                ProfScope ps(PROF_BICG_VEC, st);
+                k_bicg_p<<<SAI_GRID(nb), KT, 0, st>>>(n, k, r, p, v, S);
+            }
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmm_m<0>(n, Mr, Mc, Mv, k, p, ph, nullptr, S.active, st);
+            }
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmm_m<0>(n, Ar, Ac, Av, k, ph, v, nullptr, S.active, st);
+            }
+            {
+                ProfScope ps(PROF_BICG_VEC, st);
+                k_dot1<<<SAI_GRID(nb), KT, 0, st>>>(n, k, rh, v, S.active, part.as<double>());
+            }
+            k_bicg_f1<<<SAI_GRID(1), KT, 0, st>>>(k, nb, part.as<double>(), S, D);
+            {
+                ProfScope ps(PROF_BICG_VEC, st);
+                k_bicg_s<<<SAI_GRID(nb), KT, 0, st>>>(n, k, r, v, s, S, part.as<double>());
+            }
+            k_bicg_f2<<<SAI_GRID(1), KT, 0, st>>>(k, nb, part.as<double>(), S, D);
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmm_m<0>(n, Mr, Mc, Mv, k, s, sh, nullptr, S.go, st);
+            }
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmm_m<0>(n, Ar, Ac, Av, k, sh, t, nullptr, S.go, st);
+            }
+            {
+                ProfScope ps(PROF_BICG_VEC, st);
+                k_dot2<<<SAI_GRID(nb), KT, 0, st>>>(n, k, t, s, S.go, part.as<double>());
+            }
+            k_bicg_f3<<<SAI_GRID(1), KT, 0, st>>>(k, nb, part.as<double>(), S, D);
+            {
+                ProfScope ps(PROF_BICG_VEC, st);
+                k_bicg_xr<<<SAI_GRID(nb), KT, 0, st>>>(n, k, X, r, rh, ph, sh, s, t, S, part.as<double>());
+            }
+            k_bicg_f4<<<SAI_GRID(1), KT, 0, st>>>(k, nb, part.as<double>(), S, D, fl);
             SAI_CUDA(cudaGetLastError());
             if ((it + 1) % check_every == 0 || it + 1 == prm->maxit) {
                 SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -685,7 +761,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
             }
         }
         // systems still active after maxit passes
-        k_bicg_start<<<1, KT, 0, st>>>(k, prm->maxit, S);
+        k_bicg_start<<<SAI_GRID(1), KT, 0, st>>>(k, prm->maxit, S);
     } else {
         Gm G;
         G.m = m;
@@ -719,28 +795,40 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         double* r = wb.as<double>();
         double* w = r + blk;
         double* z = w + blk;
-        k_gm_init<<<nb, KT, 0, st>>>(n, k, B, X, r, part.as<double>());
+        k_gm_init<<<SAI_GRID(nb), KT, 0, st>>>(n, k, B, X, r, part.as<double>());
         int first = 1;
         for (;;) {
-            k_gm_cycle_start<<<1, KT, 0, st>>>(k, nb, part.as<double>(), prm->maxit, S, G, first, fl);
+            k_gm_cycle_start<<<SAI_GRID(1), KT, 0, st>>>(k, nb, part.as<double>(), prm->maxit, S, G, first, fl);
             first = 0;
             SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
             SAI_CUDA(cudaStreamSynchronize(st));
             if (!hflag) break;
-            k_gm_v0<<<nb, KT, 0, st>>>(n, k, r, S, G);
+            k_gm_v0<<<SAI_GRID(nb), KT, 0, st>>>(n, k, r, S, G);
             int jmax = 0;
             for (int j = 0; j < m; ++j) {
                 const double* vj = G.V + (size_t)j * blk;
-                spmm_m<0>(n, Mr, Mc, Mv, k, vj, z, nullptr, G.adv, st);
-                spmm_m<0>(n, Ar, Ac, Av, k, z, w, nullptr, G.adv, st);
-                for (int pass = 0; pass < 2; ++pass) {
-                    k_gm_dots<<<nb, KT, 0, st>>>(n, k, j, w, G, part.as<double>());
-                    k_gm_fin_h<<<sai_div_up((int64_t)(j + 1) * k, 256), 256, 0, st>>>(k, j, nb, part.as<double>(),
-                                                                                       G, pass);
-                    k_gm_update<<<nb, KT, 0, st>>>(n, k, j, w, G, pass, part.as<double>());
+                {
+                    ProfScope ps(PROF_SPMM, st);
+                    spmm_m<0>(n, Mr, Mc, Mv, k, vj, z, nullptr, G.adv, st);
                 }
-                k_gm_givens<<<1, KT, 0, st>>>(k, j, nb, part.as<double>(), prm->maxit, S, G, fl);
-                k_gm_normalize<<<nb, KT, 0, st>>>(n, k, j, w, S, G);
+                {
+                    ProfScope ps(PROF_SPMM, st);
+                    spmm_m<0>(n, Ar, Ac, Av, k, z, w, nullptr, G.adv, st);
+                }
+                for (int pass = 0; pass < 2; ++pass) {
+                    {
+                        ProfScope ps(PROF_GM_DOTS, st);
+                        k_gm_dots<<<SAI_GRID(nb), KT, 0, st>>>(n, k, j, w, G, part.as<double>());
+                    }
+                    k_gm_fin_h<<<SAI_GRID(sai_div_up((int64_t)(j + 1) * k, 256)), 256, 0, st>>>(k, j, nb, part.as<double>(),
+                                                                                       G, pass);
+                    {
+                        ProfScope ps(PROF_GM_UPDATE, st);
+                        k_gm_update<<<SAI_GRID(nb), KT, 0, st>>>(n, k, j, w, G, pass, part.as<double>());
+                    }
+                }
+                k_gm_givens<<<SAI_GRID(1), KT, 0, st>>>(k, j, nb, part.as<double>(), prm->maxit, S, G, D, fl);
+                k_gm_normalize<<<SAI_GRID(nb), KT, 0, st>>>(n, k, j, w, S, G);
                 SAI_CUDA(cudaGetLastError());
                 jmax = j + 1;
                 if ((j + 1) % check_every == 0 || j + 1 == m) {
@@ -749,13 +837,13 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
                     if (!hflag) break;
                 }
             }
-            k_gm_trisolve<<<1, KT, 0, st>>>(k, S, G);
-            k_gm_combine<<<nb, KT, 0, st>>>(n, k, jmax, w, G);
+            k_gm_trisolve<<<SAI_GRID(1), KT, 0, st>>>(k, S, G);
+            k_gm_combine<<<SAI_GRID(nb), KT, 0, st>>>(n, k, jmax, w, G);
             spmm_m<0>(n, Mr, Mc, Mv, k, w, z, nullptr, G.cyc, st);
-            k_gm_xadd<<<nb, KT, 0, st>>>(n, k, X, z, G);
-            k_gm_cycle_end<<<1, KT, 0, st>>>(k, prm->maxit, S, G, fl);
+            k_gm_xadd<<<SAI_GRID(nb), KT, 0, st>>>(n, k, X, z, G);
+            k_gm_cycle_end<<<SAI_GRID(1), KT, 0, st>>>(k, prm->maxit, S, G, fl);
             spmm_m<1>(n, Ar, Ac, Av, k, X, r, B, G.cyc, st);
-            k_norm2<<<nb, KT, 0, st>>>(n, k, r, G.cyc, part.as<double>());
+            k_norm2<<<SAI_GRID(nb), KT, 0, st>>>(n, k, r, G.cyc, part.as<double>());
             SAI_CUDA(cudaGetLastError());
         }
     }
@@ -766,4 +854,17 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     for (int c = 0; c < k; ++c)
         if (status[c] != SAI_OK && worst == SAI_OK) worst = (sai_status)status[c];
     return worst;
+}
+
+sai_status sai_krylov_work_reset()
+{
+    double z[PROF_NSITES * 2] = {};
+    SAI_CUDA(cudaMemcpyToSymbol(d_kwork, z, sizeof(z)));
+    return SAI_OK;
+}
+
+sai_status sai_krylov_work_read(double* out)
+{
+    SAI_CUDA(cudaMemcpyFromSymbol(out, d_kwork, sizeof(double) * PROF_NSITES * 2));
+    return SAI_OK;
 }

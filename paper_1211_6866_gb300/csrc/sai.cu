@@ -33,6 +33,11 @@
 namespace {
 
 enum { ST_DONE = 0, ST_OVERFLOW = 1, ST_SINGULAR = 2 };
+
+// Algorithmic bytes of the build (site PROF_SAI_BUILD), per finished column:
+// the final pattern's columns read (12 B per stored entry), the row patterns
+// of L read for candidates (4 B per entry) and the column written (12 B per entry).
+__device__ double d_swork[PROF_NSITES * 2];
 constexpr int MNMAX = 8;
 
 struct SaiMat {
@@ -343,7 +348,7 @@ __device__ double residual(const Ws& w, const SaiMat& A, int nL, int nS, const u
 
 template <class T>
 __device__ int spai_column(const Ws& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out, int& l_out,
-                           double& rn_out)
+                           double& rn_out, int& nL_out)
 {
     const int lane = lane_id();
     int nL, nS, nfact;
@@ -431,13 +436,14 @@ __device__ int spai_column(const Ws& w, const SaiMat& A, int32_t k, const SpaiAr
     nS_out = nS;
     l_out = l;
     rn_out = rn;
+    nL_out = nL;
     return ST_DONE;
 }
 
 // PSAI(tol), reading (A): S^(l+1) = P(a^(l+1)) u S_kept^(l), a^(l+1) = |A~| a^(l).
 template <class T>
 __device__ int psai_column(const Ws& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out, int& l_out,
-                           double& rn_pre, double& rn_post)
+                           double& rn_pre, double& rn_post, int& nL_out)
 {
     const int lane = lane_id();
     int nL, nS, nfact;
@@ -481,6 +487,7 @@ __device__ int psai_column(const Ws& w, const SaiMat& A, int32_t k, const PsaiAr
             nS_out = __shfl_sync(SAI_FULL, q, 0);
             __syncwarp();
             l_out = l;
+            nL_out = nL;
             return ST_DONE;
         }
         // a^(l+1): union of the column patterns of a^(l); positions in entry order
@@ -579,15 +586,17 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
     char* base = SMEM ? smem + (size_t)wib * T::BYTES
                       : gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * T::BYTES;
     const Ws w = bind_ws<T>(base);
+    double work_bytes = 0.0;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(next, 1);
         item = __shfl_sync(SAI_FULL, item, 0);
         if (item >= nwork) break;
         const int32_t k = work ? work[item] : item;
-        int nS = 0, l = 0;
+        int nS = 0, l = 0, nL = 0;
         double rn = 0.0, rpost = 0.0;
-        int st = PSAI ? psai_column<T>(w, A, k, pa, nS, l, rn, rpost) : spai_column<T>(w, A, k, sa, nS, l, rn);
+        int st = PSAI ? psai_column<T>(w, A, k, pa, nS, l, rn, rpost, nL)
+                      : spai_column<T>(w, A, k, sa, nS, l, rn, nL);
         if (st == ST_DONE) {
             if (nS > out.smax) st = ST_OVERFLOW;
         }
@@ -597,6 +606,10 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
                 out.rows[o + t] = w.S[t];
                 out.vals[o + t] = w.m[t];
             }
+            double cb = 0.0;
+            for (int t = lane; t < nS; t += 32) cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
+            for (int t = lane; t < nL; t += 32) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
+            work_bytes += warp_sum(cb);
             if (lane == 0) {
                 out.cnt[k] = nS;
                 out.loops[k] = l;
@@ -618,6 +631,7 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
         }
         __syncwarp();
     }
+    if (lane == 0 && work_bytes > 0.0) atomicAdd(&d_swork[2 * PROF_SAI_BUILD], work_bytes);
 }
 
 // One warp per column: rank-sort the column's slots by row into CSC.
@@ -687,8 +701,12 @@ sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, 
         SAI_TRY(scratch.alloc(T::BYTES * (size_t)warps_per_block * blocks, st, true));
     }
     SAI_CUDA(cudaMemsetAsync(next, 0, sizeof(int), st));
-    k_sai<T, SMEM, PSAI><<<blocks, threads, smem, st>>>(A, sa, pa, work, nwork, next, scratch.as<char>(), out,
-                                                        ovf_list, ovf_cnt, err, tier_id);
+    {
+        ProfScope ps(PROF_SAI_BUILD, st);
+        k_sai<T, SMEM, PSAI><<<SAI_GRID(blocks), threads, smem, st>>>(A, sa, pa, work, nwork, next,
+                                                                     scratch.as<char>(), out, ovf_list, ovf_cnt,
+                                                                     err, tier_id);
+    }
     SAI_CUDA(cudaGetLastError());
     return SAI_OK;
 }
@@ -771,7 +789,7 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     SAI_TRY(P->M_ri.alloc(sizeof(int32_t) * (size_t)(nnzM > 0 ? nnzM : 1), st, async));
     SAI_TRY(P->M_v.alloc(sizeof(double) * (size_t)(nnzM > 0 ? nnzM : 1), st, async));
     if (n > 0)
-        k_assemble<<<sai_div_up((int64_t)n * 32, 256), 256, 0, st>>>(n, smax, cnt.as<int32_t>(), rows.as<int32_t>(),
+        k_assemble<<<SAI_GRID(sai_div_up((int64_t)n * 32, 256)), 256, 0, st>>>(n, smax, cnt.as<int32_t>(), rows.as<int32_t>(),
                                                                      vals.as<double>(), P->M_cp.as<int64_t>(),
                                                                      P->M_ri.as<int32_t>(), P->M_v.as<double>());
     SAI_CUDA(cudaGetLastError());
@@ -779,8 +797,8 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
                            P->Mr_ci, P->Mr_v, st, async));
     SAI_CUDA(cudaEventRecord(e1, st));
     if (n > 0) {
-        k_stats<<<g_num_sms * 2, 256, 0, st>>>(n, P->loops.as<int32_t>(), P->res.as<double>(), delta, c + 4);
-        k_tier_count<<<g_num_sms * 2, 256, 0, st>>>(n, tier.as<int32_t>(), c + 4);
+        k_stats<<<SAI_GRID(g_num_sms * 2), 256, 0, st>>>(n, P->loops.as<int32_t>(), P->res.as<double>(), delta, c + 4);
+        k_tier_count<<<SAI_GRID(g_num_sms * 2), 256, 0, st>>>(n, tier.as<int32_t>(), c + 4);
     }
     SAI_CUDA(cudaGetLastError());
     int hs[5];
@@ -832,4 +850,17 @@ sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cuda
     pa.tol_mode = prm->tol_mode;
     pa.lmax = prm->lmax;
     return build_common<true>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
+}
+
+sai_status sai_build_work_reset()
+{
+    double z[PROF_NSITES * 2] = {};
+    SAI_CUDA(cudaMemcpyToSymbol(d_swork, z, sizeof(z)));
+    return SAI_OK;
+}
+
+sai_status sai_build_work_read(double* out)
+{
+    SAI_CUDA(cudaMemcpyFromSymbol(out, d_swork, sizeof(double) * PROF_NSITES * 2));
+    return SAI_OK;
 }

@@ -128,12 +128,12 @@ sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double*
     SAI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     SAI_CUDA(cudaMemsetAsync(cbuf.p, 0, sizeof(double), st));
     if (s > 0) {
-        k_smw_gather<<<sai_div_up((int64_t)s * s, 256), 256, 0, st>>>(n, s, h->J.as<int32_t>(), Y, C.as<double>(),
+        k_smw_gather<<<SAI_GRID(sai_div_up((int64_t)s * s, 256)), 256, 0, st>>>(n, s, h->J.as<int32_t>(), Y, C.as<double>(),
                                                                     g.as<double>());
-        k_lu_solve<<<1, 1024, 0, st>>>(s, C.as<double>(), g.as<double>(), z.as<double>(), cbuf.as<double>(),
+        k_lu_solve<<<SAI_GRID(1), 1024, 0, st>>>(s, C.as<double>(), g.as<double>(), z.as<double>(), cbuf.as<double>(),
                                        err.as<int>());
     }
-    if (n > 0) k_smw_update<<<sai_div_up(n, 256), 256, 0, st>>>(n, s, Y, z.as<double>(), x);
+    if (n > 0) k_smw_update<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, Y, z.as<double>(), x);
     SAI_CUDA(cudaGetLastError());
     int herr = 0;
     double hc = 0.0;

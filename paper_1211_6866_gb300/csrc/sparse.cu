@@ -120,9 +120,9 @@ static sai_status scan_counts(const T* in, int64_t* out, int64_t n, cudaStream_t
     int64_t ntiles = n > 0 ? (n + SCAN_TILE - 1) / SCAN_TILE : 1;
     Buf tsum;
     SAI_TRY(tsum.alloc(sizeof(int64_t) * ntiles, st, true));
-    k_scan_tilesum<T><<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(in, n, tsum.as<int64_t>());
-    k_scan_tiles<<<1, 1024, 0, st>>>(tsum.as<int64_t>(), ntiles);
-    k_scan_apply<T><<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(in, n, tsum.as<int64_t>(), out);
+    k_scan_tilesum<T><<<SAI_GRID((unsigned)ntiles), SCAN_THREADS, 0, st>>>(in, n, tsum.as<int64_t>());
+    k_scan_tiles<<<SAI_GRID(1), 1024, 0, st>>>(tsum.as<int64_t>(), ntiles);
+    k_scan_apply<T><<<SAI_GRID((unsigned)ntiles), SCAN_THREADS, 0, st>>>(in, n, tsum.as<int64_t>(), out);
     SAI_CUDA(cudaGetLastError());
     return SAI_OK;
 }
@@ -167,7 +167,7 @@ sai_status sai_validate_csc(int32_t nrows, int32_t ncols, int64_t nnz, const int
     Buf bad;
     SAI_TRY(bad.alloc(sizeof(int), st, true));
     SAI_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    k_validate_csc<<<sai_div_up(ncols, 256), 256, 0, st>>>(nrows, ncols, nnz, cp, ri, bad.as<int>());
+    k_validate_csc<<<SAI_GRID(sai_div_up(ncols, 256)), 256, 0, st>>>(nrows, ncols, nnz, cp, ri, bad.as<int>());
     SAI_CUDA(cudaGetLastError());
     int h = 0;
     SAI_CUDA(cudaMemcpyAsync(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -228,15 +228,15 @@ sai_status sai_csc_to_csr(int32_t nrows, int32_t ncols, int64_t nnz, const int64
     if (nnz > 0) {
         unsigned g = sai_div_up(nnz, 256);
         if (g > 152 * 64) g = 152 * 64;
-        k_row_hist<<<g, 256, 0, st>>>(nnz, ri, cnt.as<int32_t>());
+        k_row_hist<<<SAI_GRID(g), 256, 0, st>>>(nnz, ri, cnt.as<int32_t>());
     }
     SAI_TRY(sai_scan_counts_i32(cnt.as<int32_t>(), rp.as<int64_t>(), nrows, st));
     SAI_CUDA(cudaMemcpyAsync(fill.p, rp.p, sizeof(int64_t) * ((size_t)nrows + 1), cudaMemcpyDeviceToDevice, st));
     if (ncols > 0)
-        k_scatter_rows<<<sai_div_up((int64_t)ncols * 32, 256), 256, 0, st>>>(ncols, cp, ri, cv, fill.as<int64_t>(),
+        k_scatter_rows<<<SAI_GRID(sai_div_up((int64_t)ncols * 32, 256)), 256, 0, st>>>(ncols, cp, ri, cv, fill.as<int64_t>(),
                                                                          tci.as<int32_t>(), tv.as<double>());
     if (nrows > 0)
-        k_sort_rows<<<sai_div_up((int64_t)nrows * 32, 256), 256, 0, st>>>(nrows, rp.as<int64_t>(), tci.as<int32_t>(),
+        k_sort_rows<<<SAI_GRID(sai_div_up((int64_t)nrows * 32, 256)), 256, 0, st>>>(nrows, rp.as<int64_t>(), tci.as<int32_t>(),
                                                                          tv.as<double>(), ci.as<int32_t>(),
                                                                          rv.as<double>());
     SAI_CUDA(cudaGetLastError());
@@ -284,12 +284,12 @@ static void launch_spmm(int32_t n, const int64_t* rp, const int32_t* ci, const d
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
     switch (G) {
-    case 1: k_spmm<1, MODE><<<(unsigned)blocks, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
-    case 2: k_spmm<2, MODE><<<(unsigned)blocks, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
-    case 4: k_spmm<4, MODE><<<(unsigned)blocks, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
-    case 8: k_spmm<8, MODE><<<(unsigned)blocks, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
-    case 16: k_spmm<16, MODE><<<(unsigned)blocks, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
-    default: k_spmm<32, MODE><<<(unsigned)blocks, 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
+    case 1: k_spmm<1, MODE><<<SAI_GRID((unsigned)blocks), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
+    case 2: k_spmm<2, MODE><<<SAI_GRID((unsigned)blocks), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
+    case 4: k_spmm<4, MODE><<<SAI_GRID((unsigned)blocks), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
+    case 8: k_spmm<8, MODE><<<SAI_GRID((unsigned)blocks), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
+    case 16: k_spmm<16, MODE><<<SAI_GRID((unsigned)blocks), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
+    default: k_spmm<32, MODE><<<SAI_GRID((unsigned)blocks), 256, 0, st>>>(n, rp, ci, v, k, X, Y, B); break;
     }
 }
 
@@ -370,9 +370,9 @@ sai_status sai_csc_residual_norms(int32_t n, const int64_t* cp, const int32_t* r
     SAI_TRY(ax.alloc(sizeof(double) * (size_t)(n > 0 ? n : 1), st, true));
     SAI_TRY(part.alloc(sizeof(double) * (2 * nb + 2), st, true));
     SAI_CUDA(cudaMemsetAsync(ax.p, 0, sizeof(double) * (size_t)n, st));
-    if (n > 0) k_csc_axpy<<<sai_div_up((int64_t)n * 32, 256), 256, 0, st>>>(n, cp, ri, cv, x, ax.as<double>());
-    k_resid_norms<<<nb, 256, 0, st>>>(n, b, ax.as<double>(), part.as<double>());
-    k_sum_pairs<<<1, 32, 0, st>>>(part.as<double>(), nb, part.as<double>() + 2 * nb);
+    if (n > 0) k_csc_axpy<<<SAI_GRID(sai_div_up((int64_t)n * 32, 256)), 256, 0, st>>>(n, cp, ri, cv, x, ax.as<double>());
+    k_resid_norms<<<SAI_GRID(nb), 256, 0, st>>>(n, b, ax.as<double>(), part.as<double>());
+    k_sum_pairs<<<SAI_GRID(1), 32, 0, st>>>(part.as<double>(), nb, part.as<double>() + 2 * nb);
     SAI_CUDA(cudaGetLastError());
     SAI_CUDA(cudaMemcpyAsync(out2_host, part.as<double>() + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));

@@ -154,7 +154,7 @@ sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, c
     Buf flag, pos;
     SAI_TRY(flag.alloc(sizeof(int32_t) * (size_t)(n + 1), st, true));
     SAI_TRY(pos.alloc(sizeof(int64_t) * (size_t)(n + 1), st, true));
-    if (n > 0) k_flag_dense<<<gb, 256, 0, st>>>(n, A->col_ptr, h->tau, prm->ge, flag.as<int32_t>());
+    if (n > 0) k_flag_dense<<<SAI_GRID(gb), 256, 0, st>>>(n, A->col_ptr, h->tau, prm->ge, flag.as<int32_t>());
     SAI_TRY(sai_scan_counts_i32(flag.as<int32_t>(), pos.as<int64_t>(), n, st));
     int64_t s64 = 0;
     SAI_CUDA(cudaMemcpyAsync(&s64, pos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -163,17 +163,17 @@ sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, c
     const int32_t s = h->s;
 
     SAI_TRY(h->J.alloc(sizeof(int32_t) * (size_t)(s > 0 ? s : 1), st, async));
-    if (n > 0) k_compact_J<<<gb, 256, 0, st>>>(n, flag.as<int32_t>(), pos.as<int64_t>(), h->J.as<int32_t>());
+    if (n > 0) k_compact_J<<<SAI_GRID(gb), 256, 0, st>>>(n, flag.as<int32_t>(), pos.as<int64_t>(), h->J.as<int32_t>());
     Buf w0, w1, cntA, cntU;
     SAI_TRY(w0.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
     SAI_TRY(w1.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
     SAI_TRY(cntA.alloc(sizeof(int64_t) * (size_t)(n + 1), st, true));
     SAI_TRY(cntU.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
     if (s > 0)
-        k_window<<<sai_div_up(s, 128), 128, 0, st>>>(s, h->J.as<int32_t>(), A->col_ptr, A->row_idx, h->p_keep,
+        k_window<<<SAI_GRID(sai_div_up(s, 128)), 128, 0, st>>>(s, h->J.as<int32_t>(), A->col_ptr, A->row_idx, h->p_keep,
                                                      w0.as<int64_t>(), w1.as<int64_t>());
     if (n > 0)
-        k_count_split<<<gb, 256, 0, st>>>(n, A->col_ptr, flag.as<int32_t>(), pos.as<int64_t>(), w0.as<int64_t>(),
+        k_count_split<<<SAI_GRID(gb), 256, 0, st>>>(n, A->col_ptr, flag.as<int32_t>(), pos.as<int64_t>(), w0.as<int64_t>(),
                                           w1.as<int64_t>(), cntA.as<int64_t>(), cntU.as<int64_t>());
     SAI_TRY(h->At_cp.alloc(sizeof(int64_t) * (size_t)(n + 1), st, async));
     SAI_TRY(h->U_cp.alloc(sizeof(int64_t) * (size_t)(s + 1), st, async));
@@ -190,7 +190,7 @@ sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, c
     SAI_TRY(h->U_ri.alloc(sizeof(int32_t) * (size_t)(h->nnz_U > 0 ? h->nnz_U : 1), st, async));
     SAI_TRY(h->U_v.alloc(sizeof(double) * (size_t)(h->nnz_U > 0 ? h->nnz_U : 1), st, async));
     if (n > 0)
-        k_copy_split<<<sai_div_up((int64_t)n * 32, 256), 256, 0, st>>>(
+        k_copy_split<<<SAI_GRID(sai_div_up((int64_t)n * 32, 256)), 256, 0, st>>>(
             n, A->col_ptr, A->row_idx, A->val, flag.as<int32_t>(), pos.as<int64_t>(), w0.as<int64_t>(),
             w1.as<int64_t>(), h->At_cp.as<int64_t>(), h->At_ri.as<int32_t>(), h->At_v.as<double>(),
             h->U_cp.as<int64_t>(), h->U_ri.as<int32_t>(), h->U_v.as<double>());
@@ -202,7 +202,7 @@ sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, c
     SAI_TRY(n1.alloc(sizeof(unsigned long long), st, true));
     SAI_CUDA(cudaMemsetAsync(n1.p, 0, sizeof(unsigned long long), st));
     if (n > 0)
-        k_colstats<<<gb, 256, 0, st>>>(n, h->At_cp.as<int64_t>(), h->At_v.as<double>(), h->colnorm2.as<double>(),
+        k_colstats<<<SAI_GRID(gb), 256, 0, st>>>(n, h->At_cp.as<int64_t>(), h->At_v.as<double>(), h->colnorm2.as<double>(),
                                        n1.as<unsigned long long>());
     SAI_CUDA(cudaGetLastError());
     SAI_CUDA(cudaMemcpyAsync(&h->norm1, n1.p, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -1,0 +1,77 @@
+"""Full-size parity on the benchmark workload (64^3 convection-diffusion, n = 262144,
+10 dense columns), in the configuration bench.py times.
+
+The oracle cannot redo the whole solve inside a test run, so:
+ - M is compared column by column on three column ranges the oracle builds
+   (pattern bit-exact, values within 1e-10 relative);
+ - nnz(M), n_c, l_m and the s+1 GMRES iteration counts are compared with the
+   complete oracle run stored by tests/golden/make_oracle_convdiff3d.py
+   (iterations within +-1);
+ - the recovered x satisfies ||b - A x||/||b|| < eps, checked on the device
+   and again with the oracle's residual routine.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import assert_same_pattern_and_values, lib, need_gpu, to_dev, to_scipy, torch
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_convdiff3d_m64_s10.json")
+KRYLOV = dict(krylov="gmres", restart=50, eps=1e-10, maxit=500)
+CASES = {
+    "spai": dict(sai="spai", delta=0.3, mn=5, max_aug=10),
+    "psai": dict(sai="psai", delta=0.3, tol=1e-3, tol_mode=1, lmax=10),
+}
+RANGES = [(0, 3000), (130000, 132000), (262144 - 2500, 262144)]
+
+
+@pytest.fixture(scope="module")
+def problem():
+    need_gpu()
+    P = W.convdiff3d_irregular()
+    J, p, _ = O.detect(P.A)
+    At, _ = O.split(P.A, J, p)
+    with open(GOLDEN) as f:
+        gold = json.load(f)
+    return P, At, gold
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fullsize_build_samples_match_oracle(problem, case):
+    P, At, gold = problem
+    sai = lib()
+    h = sai.split(to_dev(P.A))
+    kw = CASES[case]
+    if case == "spai":
+        Pc = sai.build_spai(h, delta=kw["delta"], mn=kw["mn"], max_aug=kw["max_aug"])
+    else:
+        Pc = sai.build_psai(h, delta=kw["delta"], tol=kw["tol"], tol_mode=kw["tol_mode"], lmax=kw["lmax"])
+    Md = to_scipy(Pc.arrays()[0])
+    rep = gold["cases"][case]["report"]
+    assert Pc.nnz == rep["nnz_M"] and Pc.n_c == rep["n_c"] and Pc.l_m == rep["l_m"]
+    for c0, c1 in RANGES:
+        if case == "spai":
+            Mo = O.spai(At, kw["delta"], kw["mn"], kw["max_aug"], cols=(c0, c1))[0]
+        else:
+            Mo = O.psai(At, kw["delta"], kw["tol"], kw["tol_mode"], kw["lmax"], cols=(c0, c1))[0]
+        assert_same_pattern_and_values(Md, Mo, cols=range(c0, c1))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fullsize_solve_matches_oracle_run(problem, case):
+    P, At, gold = problem
+    sai = lib()
+    x, iters, rep = sai.solve(to_dev(P.A), torch.as_tensor(P.b, device="cuda"), **CASES[case], **KRYLOV)
+    g = gold["cases"][case]
+    assert rep["s"] == g["report"]["s"] and rep["nnz_M"] == g["report"]["nnz_M"]
+    assert all(abs(a - b) <= 1 for a, b in zip(iters, g["iters"])), (iters, g["iters"])
+    assert rep["rr"] < 1e-10
+    assert O.rel_resid(P.A, P.b, x.cpu().numpy()) < 1e-10
+    assert rep["c"] == pytest.approx(g["report"]["c"], rel=1e-6)
+    np.testing.assert_allclose(x.cpu().numpy(), 1.0, rtol=0, atol=1e-7)
