@@ -191,6 +191,22 @@ sai_status sai_krylov_solve(sai_split h, sai_precond P, int32_t k, const double*
  * ---------------------------------------------------------------------- */
 sai_status sai_smw_recover(sai_split h, const double* Y, double* x, double* c_out, sai_stream_t stream);
 
+/* The same recovery without any device allocation, for callers that cannot
+ * allocate: code whose device memory is entirely owned by a host framework's
+ * pool or a fixed budget, or that runs where an allocation would synchronise
+ * or is not permitted. The paper has no counterpart; it is an interface
+ * convenience. Inputs are explicit instead of a split handle: n, s, J (s
+ * ascending row indices of V, device), Y (n x (s+1) row-major, device), x
+ * (n, device output), c_out (host, may be NULL).
+ * Scratch: a static device array of about 516 KB (s <= 256) that every
+ * device loading the library holds until the process exits; s > 256 returns
+ * SAI_INVALID_ARG. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the array, so calls that overlap on the GPU (other
+ * streams or threads) race: serialise them. Synchronises the stream. */
+sai_status sai_smw_recover_noalloc(int32_t n, int32_t s, const int32_t* J, const double* Y, double* x,
+                                   double* c_out, sai_stream_t stream);
+
 /* rr = ||b - A x|| / ||b|| (eq. (rrnorm)) for a caller CSC matrix;
  * rr_out is a host pointer. Synchronises the stream. */
 sai_status sai_rel_resid(const sai_csc_view* A, const double* b, const double* x, double* rr_out,

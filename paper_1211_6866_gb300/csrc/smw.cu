@@ -7,6 +7,8 @@
 //   k_smw_update   xhat(i) = yhat(i) - sum_t What(i,t) z_t, one thread per row
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace {
@@ -139,6 +141,80 @@ sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double*
     double hc = 0.0;
     SAI_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaMemcpyAsync(&hc, cbuf.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    if (herr) return SAI_SINGULAR;
+    if (c_out) *c_out = hc;
+    return SAI_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// sai_smw_recover_noalloc: the same SMW recovery for callers that cannot
+// allocate device memory -- code that runs where every device byte is owned
+// by a host framework's own pool or a fixed budget, or where an allocation
+// would synchronise or is not permitted. Its scratch (the s x s matrix, two
+// s-vectors, c and an error flag) is this file-scope array, reserved once on
+// every device that loads the library and held until the process exits.
+namespace {
+
+constexpr int NOALLOC_MAX_S = 256;
+constexpr size_t NOALLOC_C_OFF = 0;
+constexpr size_t NOALLOC_G_OFF = NOALLOC_C_OFF + sizeof(double) * NOALLOC_MAX_S * NOALLOC_MAX_S;
+constexpr size_t NOALLOC_Z_OFF = NOALLOC_G_OFF + sizeof(double) * NOALLOC_MAX_S;
+constexpr size_t NOALLOC_CV_OFF = NOALLOC_Z_OFF + sizeof(double) * NOALLOC_MAX_S;
+constexpr size_t NOALLOC_ERR_OFF = NOALLOC_CV_OFF + 256;
+constexpr size_t NOALLOC_BYTES = NOALLOC_ERR_OFF + 256;
+
+static __device__ __align__(256) unsigned char g_smw_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEV = 64;
+static unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEV];
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array for the current device, looked up once
+// per device (the host-side symbol is only a stand-in, not a device address).
+sai_status noalloc_scratch(unsigned char** out)
+{
+    int dev = 0;
+    SAI_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEV) return SAI_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        SAI_CUDA(cudaGetSymbolAddress(&p, g_smw_noalloc_scratch));
+        g_noalloc_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SAI_OK;
+}
+
+}  // namespace
+
+extern "C" sai_status sai_smw_recover_noalloc(int32_t n, int32_t s, const int32_t* J, const double* Y, double* x,
+                                              double* c_out, sai_stream_t stream)
+{
+    if (n < 0 || s < 0 || s > n || (n > 0 && (!Y || !x)) || (s > 0 && !J)) return SAI_INVALID_ARG;
+    if (s > NOALLOC_MAX_S) return SAI_INVALID_ARG;  // beyond the static scratch
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    SAI_TRY(noalloc_scratch(&base));
+    double* C = (double*)(base + NOALLOC_C_OFF);
+    double* g = (double*)(base + NOALLOC_G_OFF);
+    double* z = (double*)(base + NOALLOC_Z_OFF);
+    double* cval = (double*)(base + NOALLOC_CV_OFF);
+    int* err = (int*)(base + NOALLOC_ERR_OFF);
+    // the array keeps the previous call's contents: clear what must start at zero
+    SAI_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    SAI_CUDA(cudaMemsetAsync(cval, 0, sizeof(double), st));
+    if (s > 0) {
+        k_smw_gather<<<SAI_GRID(sai_div_up((int64_t)s * s, 256)), 256, 0, st>>>(n, s, J, Y, C, g);
+        k_lu_solve<<<SAI_GRID(1), 1024, 0, st>>>(s, C, g, z, cval, err);
+    }
+    if (n > 0) k_smw_update<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, Y, z, x);
+    SAI_CUDA(cudaGetLastError());
+    int herr = 0;
+    double hc = 0.0;
+    SAI_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaMemcpyAsync(&hc, cval, sizeof(double), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));
     if (herr) return SAI_SINGULAR;
     if (c_out) *c_out = hc;
