@@ -41,6 +41,8 @@ UNIT = "columns/s"
 SPAI_KW = dict(sai="spai", delta=0.3, mn=5, max_aug=10)
 PSAI_KW = dict(sai="psai", delta=0.3, tol=1e-3, tol_mode=1, lmax=10)
 KRYLOV_KW = dict(krylov="gmres", restart=50, eps=1e-10, maxit=500)
+OPT_KW = dict(krylov_precision=1)    # FP32 inner GMRES refined in FP64
+PLAIN_KW = dict(krylov_precision=0)  # plain FP64 GPU form
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_convdiff3d_m64_s10.json")
 
 
@@ -124,6 +126,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline
 FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 
 def roofline(prof, peaks):
@@ -136,13 +139,15 @@ def roofline(prof, peaks):
     bytes_l = s["bytes"] / s["launches"]
     flops_l = s["flops"] / s["launches"]
     hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    fp32 = name.endswith("_fp32")
+    alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
     t_hbm = bytes_l / (hbm * 1e9)
-    t_alu = flops_l / (FP64_PEAK_TFLOPS * 1e12)
+    t_alu = flops_l / (alu_peak * 1e12)
     if flops_l > 0 and t_alu > t_hbm:
         ach = flops_l / avg_s / 1e12
-        r = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-             "frac": ach / FP64_PEAK_TFLOPS,
-             "peak_source": "FP64 ALU nominal from unit counts and clocks (probe measured 1.20)"}
+        r = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+             "frac": ach / alu_peak,
+             "peak_source": ("FP32" if fp32 else "FP64") + " ALU nominal from unit counts and clocks"}
     else:
         ach = bytes_l / avg_s / 1e9
         r = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
@@ -238,42 +243,49 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step(form):
         out = []
         for kw in (SPAI_KW, PSAI_KW):
-            x, iters, rep = sai.solve(dA, b, **kw, **KRYLOV_KW)
+            x, iters, rep = sai.solve(dA, b, **kw, **KRYLOV_KW, **form)
             out.append((x, iters, rep))
         return out
 
     for _ in range(args.warmup):
-        step()
+        step(OPT_KW)
+    step(PLAIN_KW)
     torch.cuda.synchronize()
+
+    def timed(form, nsteps, profile):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            sai.profile_begin()
+        ms, reps = [], []
+        for _ in range(nsteps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step(form)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            reps.append(res)
+        torch.cuda.synchronize()
+        prof = sai.profile_end() if profile else None
+        total = float(np.sum(ms))
+        if dist:
+            t = torch.tensor([total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+            dist.barrier()
+        return total / nsteps, reps, prof
+
     clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    sai.profile_begin()
-    step_ms, reps = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        reps.append(res)
-    torch.cuda.synchronize()
-    prof = sai.profile_end()
+    ms_step, reps, prof = timed(OPT_KW, args.steps, True)
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    ms_step = total_ms / args.steps
+    ms_plain, reps_plain, _ = timed(PLAIN_KW, max(1, min(args.steps, 3)), False)
     value = ws * 2 * n / (ms_step / 1e3)
 
     # e2e: public API from pinned host buffers, copies inside the timing
@@ -290,7 +302,7 @@ def run_ours(args):
         cp, ri, va, bb = (t.to("cuda", non_blocking=True) for t in hA)
         M = sai.CscMatrix(n, cp, ri, va)
         for kw, xh in zip((SPAI_KW, PSAI_KW), hx):
-            x, _, _ = sai.solve(M, bb, **kw, **KRYLOV_KW)
+            x, _, _ = sai.solve(M, bb, **kw, **KRYLOV_KW, **OPT_KW)
             xh.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
@@ -304,7 +316,7 @@ def run_ours(args):
     peaks = load_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
         "data": "synthetic", "config": workload_config(P),
         "full_solve_ms": {"spai": last[0][2]["ms_split"] + last[0][2]["ms_build"] + last[0][2]["ms_krylov"] +
                           last[0][2]["ms_smw"],
@@ -316,8 +328,12 @@ def run_ours(args):
         "iters": {k: r[1] for k, r in zip(("spai", "psai"), last)},
         "rr": {k: r[2]["rr"] for k, r in zip(("spai", "psai"), last)},
         "nnz_M": {k: r[2]["nnz_M"] for k, r in zip(("spai", "psai"), last)},
-        "form": "plain FP64 GPU (the comparison form itself); vs_plain_fp64 = 1",
-        "vs_plain_fp64": 1.0,
+        "form": "SAI build FP64; s+1 GMRES(50) solves with FP32 inner iterations refined in FP64 (FP64 residual "
+                "b - A~x, correction and every stop test); SMW and rr FP64",
+        "plain_fp64": {"ms_per_step": ms_plain, "value": ws * 2 * n / (ms_plain / 1e3),
+                       "iters": {k: r[1] for k, r in zip(("spai", "psai"), reps_plain[-1])},
+                       "rr": {k: r[2]["rr"] for k, r in zip(("spai", "psai"), reps_plain[-1])}},
+        "vs_plain_fp64": ms_plain / ms_step,
         "roofline": roofline(prof, peaks),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": float(np.mean(e2e_ms))},

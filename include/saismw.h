@@ -173,6 +173,11 @@ typedef struct {
     int32_t method;
     int32_t restart;   /* GMRES(m); ignored by BiCGStab */
     int32_t maxit;     /* paper: 500 */
+    int32_t precision; /* SAI_FP64, or SAI_FP32_REFINE64 (GMRES only): FP32 inner
+                          GMRES solves of A~ d = r/||r|| refined in FP64 --
+                          r = b - A~ x, x += ||r|| d and every stop test in FP64;
+                          maxit then bounds the total inner iterations */
+    double inner_tol;  /* relative inner tolerance of the refined form; <= 0 -> 1e-4 */
 } sai_krylov_params;
 
 /* B, X: n x k row-major device blocks. thr, iters, status: host arrays of k.
@@ -245,7 +250,7 @@ sai_status sai_solve(const sai_csc_view* A, const double* b, const sai_solve_par
  * Diagnostics (not part of the paper's method): launch counting and the
  * per-kernel measurements behind the roofline figures.
  * ---------------------------------------------------------------------- */
-#define SAI_PROF_MAX_SITES 8
+#define SAI_PROF_MAX_SITES 12
 
 typedef struct {
     char name[24];

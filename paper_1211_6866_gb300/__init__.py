@@ -65,7 +65,8 @@ class _PrecondInfo(C.Structure):
 
 
 class _KrylovParams(C.Structure):
-    _fields_ = [("method", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32)]
+    _fields_ = [("method", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32), ("precision", C.c_int32),
+                ("inner_tol", C.c_double)]
 
 
 class _SolveParams(C.Structure):
@@ -85,7 +86,7 @@ class _ProfSite(C.Structure):
 
 
 class _ProfReport(C.Structure):
-    _fields_ = [("launches", C.c_uint64), ("nsites", C.c_int32), ("site", _ProfSite * 8)]
+    _fields_ = [("launches", C.c_uint64), ("nsites", C.c_int32), ("site", _ProfSite * 12)]
 
 
 _lib = None
@@ -260,8 +261,9 @@ def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10):
     return Precond(h.value)
 
 
-def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500):
+def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500, precision=0, inner_tol=0.0):
     """Solves A~ X = B (n x k, row-major, device) with right preconditioner M.
+    precision 1 (GMRES only): FP32 inner solves refined in FP64.
     Returns (X, iters list, status list, overall status)."""
     L = load()
     B = B.contiguous()
@@ -270,7 +272,7 @@ def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500):
     thr_a = (C.c_double * k)(*[float(t) for t in thr])
     it = (C.c_int32 * k)()
     stt = (C.c_int32 * k)()
-    prm = _KrylovParams(method, restart, maxit)
+    prm = _KrylovParams(method, restart, maxit, precision, inner_tol)
     st = _check("sai_krylov_solve", L.sai_krylov_solve(sp._h, P._h, k, _p(B), thr_a, C.byref(prm), _p(X), it, stt,
                                                        _stream()), allow=(SAI_MAXITER, SAI_BREAKDOWN))
     return X, list(it), list(stt), st
@@ -295,14 +297,19 @@ def rel_resid(A, b, x):
 
 
 def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0, abs_tau=-1.0,
-          delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, x=None):
-    """Procedure * on the device. Returns (x, iters list, report dict)."""
+          delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, x=None, krylov_precision=0,
+          inner_tol=0.0, sai_precision=0):
+    """Procedure * on the device. krylov_precision=1 selects the FP32-inner /
+    FP64-refined GMRES; sai_precision=1 the FP32 QR + FP64 refinement build.
+    Returns (x, iters list, report dict)."""
     L = load()
     if x is None:
         x = torch.empty(A.n, dtype=torch.float64, device=b.device)
     prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0), 0 if sai == "spai" else 1,
-                       _SpaiParams(delta, mn, max_aug, key_bits, 0), _PsaiParams(delta, tol, tol_mode, lmax, 0),
-                       _KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit), eps)
+                       _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
+                       _PsaiParams(delta, tol, tol_mode, lmax, sai_precision),
+                       _KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit, krylov_precision,
+                                     inner_tol), eps)
     cap = A.n + 1
     iters = (C.c_int32 * cap)()
     rep = _SolveReport()

@@ -20,8 +20,9 @@ static std::mutex g_prof_mu;
 static std::vector<cudaEvent_t> g_ev_pool;
 static std::atomic<size_t> g_ev_next{0};
 static std::vector<std::pair<size_t, size_t>> g_prof_ev[PROF_NSITES];
-static const char* k_site_names[PROF_NSITES] = {"sai_build", "krylov_spmm", "gmres_project", "gmres_update",
-                                                "bicgstab_vector"};
+static const char* k_site_names[PROF_NSITES] = {"sai_build",          "krylov_spmm",     "gmres_project",
+                                                "gmres_update",       "bicgstab_vector", "krylov_spmm_fp32",
+                                                "gmres_project_fp32", "gmres_update_fp32"};
 static const size_t k_ev_pool = 1 << 16;
 
 unsigned sai_count_grid(unsigned g)

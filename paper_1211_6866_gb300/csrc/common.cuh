@@ -36,6 +36,19 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SAI_FULL, v, o);
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v)
+{
+    return warp_sum(v);
+}
+
 __device__ __forceinline__ int warp_sum_int(int v)
 {
 #pragma unroll
@@ -70,7 +83,10 @@ enum {
     PROF_GM_DOTS = 2,    // GMRES projections V^T w
     PROF_GM_UPDATE = 3,  // GMRES updates w -= V h
     PROF_BICG_VEC = 4,   // BiCGStab vector updates and inner products
-    PROF_NSITES = 5
+    PROF_SPMM32 = 5,     // FP32 SpMV of the refined GMRES inner solves
+    PROF_GM_DOTS32 = 6,  // FP32 projections
+    PROF_GM_UPDATE32 = 7,// FP32 updates
+    PROF_NSITES = 8
 };
 struct ProfScope {
     int site;

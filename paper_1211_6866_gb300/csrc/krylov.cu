@@ -29,8 +29,8 @@ namespace {
 constexpr int CTRL = 256;      // threads of the single-block control kernels (>= k)
 constexpr int CHUNK = 1024;    // rows per (system, chunk) reduction item (one warp)
 constexpr int TILE = 256;      // rows per SpMV item (one block)
-constexpr int PJ = 32;         // basis vectors per register-tiled projection pass
-constexpr int IT_WARPS = 8;    // warps per block of the item kernels
+constexpr int PJ = 16;         // basis vectors per register-tiled projection pass
+constexpr int IT_WARPS = 4;    // warps per block of the item kernels (small blocks: finer occupancy)
 
 enum { ST_OK = 0, ST_MAXITER = 5, ST_BREAKDOWN = 6 };  // same values as sai_status
 
@@ -41,6 +41,8 @@ __device__ double d_kwork[PROF_NSITES * 2];
 
 struct Dims {
     double n, nnzA, nnzM;
+    double esz;                           // bytes per vector / matrix value
+    int site_spmm, site_dots, site_upd;   // profile sites of this precision
 };
 
 __device__ __forceinline__ void kwork_add(int site, double bytes, double flops)
@@ -50,9 +52,10 @@ __device__ __forceinline__ void kwork_add(int site, double bytes, double flops)
 }
 
 // one SpMV launch over k_act systems: matrix once, x read once, y written
-__device__ __forceinline__ void spmm_work(double n, double nnz, int kact)
+__device__ __forceinline__ void spmm_work(const Dims& D, double nnz, int kact)
 {
-    if (kact > 0) kwork_add(PROF_SPMM, 8.0 * (n + 1) + 12.0 * nnz + 16.0 * n * kact, 2.0 * nnz * kact);
+    if (kact > 0)
+        kwork_add(D.site_spmm, 8.0 * (D.n + 1) + (4.0 + D.esz) * nnz + 2.0 * D.esz * D.n * kact, 2.0 * nnz * kact);
 }
 
 // ---------------------------------------------------------------- lists
@@ -86,14 +89,15 @@ __global__ void k_from_soa(int64_t n, int k, int64_t ld, const double* __restric
 }
 
 // ---------------------------------------------------------------- SpMV over a list
-// Y[c] = A X[c] (mode 0) or B[c] - A X[c] (mode 1) for the systems in list.
+// Y[c] = A X[c] (mode 0) or B[c] - A X[c] (mode 1) for the systems in list, in
+// the value type T (FP64, or FP32 for the inner solves of the refined GMRES).
 // Items are (row tile, system), tile-major, so the systems of a tile reuse
 // the tile's matrix rows from cache. One thread per row (CSR).
-template <int MODE>
+template <class T, int MODE>
 __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int64_t* __restrict__ rp,
-                                               const int32_t* __restrict__ ci, const double* __restrict__ v,
-                                               const double* __restrict__ X, double* __restrict__ Y,
-                                               const double* __restrict__ B, const int* __restrict__ list)
+                                               const int32_t* __restrict__ ci, const T* __restrict__ v,
+                                               const T* __restrict__ X, T* __restrict__ Y,
+                                               const T* __restrict__ B, const int* __restrict__ list)
 {
     const int cnt = list[0];
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
@@ -102,8 +106,8 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
         const int c = list[1 + (int)(it - tile * cnt)];
         const int64_t row = tile * TILE + threadIdx.x;
         if (row >= n) continue;
-        const double* xc = X + (int64_t)c * ld;
-        double acc = 0.0;
+        const T* xc = X + (int64_t)c * ld;
+        T acc = 0;
         const int64_t b = rp[row], e = rp[row + 1];
         for (int64_t t = b; t < e; ++t) acc = fma(v[t], xc[ci[t]], acc);
         if (MODE == 0) Y[(int64_t)c * ld + row] = acc;
@@ -111,17 +115,24 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
     }
 }
 
-template <int MODE>
-void spmv(int32_t n, int64_t ld, const int64_t* rp, const int32_t* ci, const double* v, int k, const double* X,
-          double* Y, const double* B, const int* list, cudaStream_t st)
+template <class T, int MODE>
+void spmv(int32_t n, int64_t ld, const int64_t* rp, const int32_t* ci, const T* v, int k, const T* X, T* Y,
+          const T* B, const int* list, cudaStream_t st)
 {
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
     int64_t g = tiles * k;
     const int64_t cap = (int64_t)g_sms * 8;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    k_spmv<MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, rp, ci, v, X, Y, B, list);
+    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, rp, ci, v, X, Y, B, list);
 }
+
+template <class T>
+struct Ops {  // A~ and M in CSR with values of type T
+    const int64_t *Ar, *Mr;
+    const int32_t *Ac, *Mc;
+    const T *Av, *Mv;
+};
 
 // ---------------------------------------------------------------- item kernels
 // An item is (system in list, row chunk of CHUNK rows) handled by one warp.
@@ -280,8 +291,8 @@ __global__ void k_bicg_f1(int k, int nch, const double* part, Sys S, Dims D)
     const int c = threadIdx.x;
     const int k1 = S.lact[0];
     if (c == 0 && k1 > 0) {
-        spmm_work(D.n, D.nnzM, k1);
-        spmm_work(D.n, D.nnzA, k1);
+        spmm_work(D, D.nnzM, k1);
+        spmm_work(D, D.nnzA, k1);
         kwork_add(PROF_BICG_VEC, 8.0 * D.n * k1 * (4 + 2), D.n * k1 * (3 + 2));  // p update, rhat^T v
     }
     if (c < k && S.active[c]) {
@@ -338,8 +349,8 @@ __global__ void k_bicg_f3(int k, int nch, const double* part, Sys S, Dims D)
     const int c = threadIdx.x;
     const int k3 = S.lgo[0];
     if (c == 0 && k3 > 0) {
-        spmm_work(D.n, D.nnzM, k3);
-        spmm_work(D.n, D.nnzA, k3);
+        spmm_work(D, D.nnzM, k3);
+        spmm_work(D, D.nnzA, k3);
         kwork_add(PROF_BICG_VEC, 8.0 * D.n * k3 * 2, D.n * k3 * 4.0);  // t^T s, t^T t
     }
     if (c < k && S.go[c]) {
@@ -413,55 +424,171 @@ __global__ void k_bicg_f4(int k, int nch, const double* part, Sys S, Dims D, int
     }
 }
 
+
+sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const double* Bsd, double* Xsd, Sys& S,
+                        double* pt, int* fl, int maxit, const Dims& D, cudaStream_t st)
+{
+    const int32_t n = I.n;
+    const int64_t ld = I.ld;
+    const size_t blk = (size_t)ld * k;
+    const int ib = item_blocks(n > 0 ? n : 1, k);
+    const int nch = I.nch;
+    const int check_every = 4;
+    int hflag = 0;
+    Buf vecs;
+    SAI_TRY(vecs.alloc(sizeof(double) * blk * 8 + 8, st, true));
+    SAI_CUDA(cudaMemsetAsync(vecs.p, 0, sizeof(double) * blk * 8, st));
+    double* r = vecs.as<double>();
+    double* rh = r + blk;
+    double* p = rh + blk;
+    double* v = p + blk;
+    double* ph = v + blk;
+    double* s = ph + blk;
+    double* sh = s + blk;
+    double* t = sh + blk;
+    k_bicg_init<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r, rh, p, v, S.lall, pt);
+    k_bicg_f0<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S);
+    SAI_CUDA(cudaGetLastError());
+    for (int it = 0; it < maxit; ++it) {
+        k_bicg_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, maxit, S);
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_bicg_p<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, p, v, S);
+        }
+        {
+            ProfScope ps(PROF_SPMM, st);
+            spmv<double, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, p, ph, nullptr, S.lact, st);
+        }
+        {
+            ProfScope ps(PROF_SPMM, st);
+            spmv<double, 0>(n, ld, A.Ar, A.Ac, A.Av, k, ph, v, nullptr, S.lact, st);
+        }
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_dots<1><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, rh, v, nullptr, nullptr, S.lact, pt);
+        }
+        k_bicg_f1<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_bicg_s<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, v, s, S, pt);
+        }
+        k_bicg_f2<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
+        {
+            ProfScope ps(PROF_SPMM, st);
+            spmv<double, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, s, sh, nullptr, S.lgo, st);
+        }
+        {
+            ProfScope ps(PROF_SPMM, st);
+            spmv<double, 0>(n, ld, A.Ar, A.Ac, A.Av, k, sh, t, nullptr, S.lgo, st);
+        }
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_dots<2><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, t, s, t, t, S.lgo, pt);
+        }
+        k_bicg_f3<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_bicg_xr<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Xsd, r, rh, ph, sh, s, t, S, pt);
+        }
+        k_bicg_f4<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D, fl);
+        SAI_CUDA(cudaGetLastError());
+        if ((it + 1) % check_every == 0 || it + 1 == maxit) {
+            SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            if (!hflag) break;
+        }
+    }
+    // systems still active after maxit passes
+    k_bicg_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, maxit, S);
+    SAI_CUDA(cudaGetLastError());
+    return SAI_OK;
+}
+
 // ================================================================== GMRES(m)
+// Control state (FP64 scalars and flags), shared by the FP64 and FP32 engines.
 struct Gm {
     int m;
-    int64_t vstride;  // k * ld: distance between basis vectors V_i
-    double* V;        // (m+1) blocks of k systems
-    double* H;        // k x m x (m+1): column j of system c at H[(c*m + j)*(m+1)]
-    double* cs;       // k x m
-    double* sn;       // k x m
-    double* g;        // k x (m+1)
-    double* h;        // 2 x (m+1) x k  (projection passes)
-    double* u;        // k x m
-    double* ww;       // k: ||w||^2 before the projection
-    double* hn2;      // k: ||w||^2 after it
+    double* H;   // k x m x (m+1): column j of system c at H[(c*m + j)*(m+1)]
+    double* cs;  // k x m
+    double* sn;  // k x m
+    double* g;   // k x (m+1)
+    double* h;   // 2 x (m+1) x k  (projection passes)
+    double* u;   // k x m
+    double* ww;  // k: ||w||^2 before the projection
+    double* hn2; // k: ||w||^2 after it
     int *cyc, *adv, *jd, *done, *conv, *reo;
     int *lcyc, *ladv, *lreo;  // lists
 };
 
-__global__ void k_gm_init(Items I, int k, const double* __restrict__ Bs, double* x, double* r, const int* list,
-                          double* part)
+// Krylov basis: m+1 system-major blocks of k vectors in the value type T.
+template <class T>
+struct Basis {
+    T* V;
+    int64_t vs;  // distance between V_i and V_{i+1}
+};
+
+// 16-byte vectors of T (double2 / float4) for the streaming kernels; every
+// system vector starts on a 256-byte boundary (ld is a multiple of 32) and its
+// padding rows [n, ld) are zero, so whole vectors can be read past n.
+template <class T>
+struct Vec;
+template <>
+struct Vec<double> {
+    using type = double2;
+    static constexpr int W = 2;
+    __device__ static double dot(const double2& a, const double2& b) { return fma(a.x, b.x, a.y * b.y); }
+    __device__ static double2 axpy(double a, const double2& x, const double2& y)
+    {
+        return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+    }
+};
+template <>
+struct Vec<float> {
+    using type = float4;
+    static constexpr int W = 4;
+    __device__ static float dot(const float4& a, const float4& b)
+    {
+        return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+    }
+    __device__ static float4 axpy(float a, const float4& x, const float4& y)
+    {
+        return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+    }
+};
+
+template <class T>
+__global__ void k_gm_init(Items I, int k, const T* __restrict__ Bs, T* x, T* r, const int* list, double* part)
 {
     FOR_ITEMS(I, list, c, r0, r1)
     {
-        double acc = 0.0;
+        T acc = 0;
         const int64_t o = (int64_t)c * I.ld;
         for (int64_t i = r0 + lane_; i < r1; i += 32) {
-            const double b = Bs[o + i];
-            x[o + i] = 0.0;
+            const T b = Bs[o + i];
+            x[o + i] = 0;
             r[o + i] = b;
             acc = fma(b, b, acc);
         }
-        acc = warp_sum(acc);
-        if (lane_ == 0) part[pidx(0, c, q_, k, I.nch)] = acc;
+        acc = warp_sum_t(acc);
+        if (lane_ == 0) part[pidx(0, c, q_, k, I.nch)] = (double)acc;
     }
 }
 
-__global__ void k_norm2(Items I, int k, const double* __restrict__ r, const int* list, double* part)
+template <class T>
+__global__ void k_norm2(Items I, int k, const T* __restrict__ r, const int* list, double* part)
 {
     FOR_ITEMS(I, list, c, r0, r1)
     {
-        double acc = 0.0;
+        T acc = 0;
         const int64_t o = (int64_t)c * I.ld;
         for (int64_t i = r0 + lane_; i < r1; i += 32) acc = fma(r[o + i], r[o + i], acc);
-        acc = warp_sum(acc);
-        if (lane_ == 0) part[pidx(0, c, q_, k, I.nch)] = acc;
+        acc = warp_sum_t(acc);
+        if (lane_ == 0) part[pidx(0, c, q_, k, I.nch)] = (double)acc;
     }
 }
 
 // cycle start: true residual norm, stop tests, g = beta e_1
-__global__ void k_gm_cycle_start(int k, int nch, const double* part, int maxit, Sys S, Gm G, int first,
+__global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* cap, Sys S, Gm G, int first,
                                  int* any_cyc)
 {
     const int c = threadIdx.x;
@@ -481,7 +608,7 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, int maxit, 
             if (beta < S.thr[c]) {
                 G.done[c] = 1;
                 S.status[c] = ST_OK;
-            } else if (S.iters[c] >= maxit) {
+            } else if (S.iters[c] >= cap[c]) {
                 G.done[c] = 1;
                 S.status[c] = ST_MAXITER;
             } else {
@@ -502,46 +629,54 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, int maxit, 
     }
 }
 
-__global__ void k_gm_v0(Items I, const double* __restrict__ r, Sys S, Gm G)
+template <class T>
+__global__ void k_gm_v0(Items I, const T* __restrict__ r, Sys S, Gm G, Basis<T> Bv)
 {
     FOR_ITEMS(I, G.lcyc, c, r0, r1)
     {
-        const double inv = 1.0 / S.beta[c];
+        const T inv = (T)(1.0 / S.beta[c]);
         const int64_t o = (int64_t)c * I.ld;
-        for (int64_t i = r0 + lane_; i < r1; i += 32) G.V[o + i] = r[o + i] * inv;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) Bv.V[o + i] = r[o + i] * inv;
     }
 }
 
 // Projection h_i = V_i^T w (i in [i0, i0+ni)) and ||w||^2 for the systems of
 // list: each warp item keeps NI+1 accumulators in registers and streams its
 // chunk of w and of the ni basis vectors once.
-template <int NI>
+template <class T, int NI>
 __global__ void __launch_bounds__(IT_WARPS * 32) k_gm_proj(Items I, int k, int i0, int ni,
-                                                          const double* __restrict__ w, Gm G, const int* list,
+                                                          const T* __restrict__ w, Basis<T> Bv, const int* list,
                                                           double* __restrict__ part)
 {
+    using VT = typename Vec<T>::type;
+    constexpr int VW = Vec<T>::W;
     FOR_ITEMS(I, list, c, r0, r1)
     {
-        double acc[NI + 1];
+        T acc[NI + 1];
 #pragma unroll
-        for (int i = 0; i <= NI; ++i) acc[i] = 0.0;
+        for (int i = 0; i <= NI; ++i) acc[i] = 0;
         const int64_t o = (int64_t)c * I.ld;
-        const double* Vp = G.V + (int64_t)i0 * G.vstride + o;
-        for (int64_t row = r0 + lane_; row < r1; row += 32) {
-            const double wv = w[o + row];
+        const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
+        const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
+        for (int64_t row = r0 + (int64_t)lane_ * VW; row < r1v; row += 32 * VW) {
+            const VT wv = *reinterpret_cast<const VT*>(w + o + row);
+            VT vv[NI];
 #pragma unroll
             for (int i = 0; i < NI; ++i)
-                if (i < ni) acc[i] = fma(Vp[(int64_t)i * G.vstride + row], wv, acc[i]);
-            acc[NI] = fma(wv, wv, acc[NI]);
+                if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+                if (i < ni) acc[i] += Vec<T>::dot(vv[i], wv);
+            acc[NI] += Vec<T>::dot(wv, wv);
         }
 #pragma unroll
-        for (int i = 0; i <= NI; ++i) acc[i] = warp_sum(acc[i]);
+        for (int i = 0; i <= NI; ++i) acc[i] = warp_sum_t(acc[i]);
         if (lane_ == 0) {
             double* pp = part + ((size_t)c * I.nch + q_) * (PJ + 1);
 #pragma unroll
             for (int i = 0; i < NI; ++i)
-                if (i < ni) pp[i] = acc[i];
-            pp[PJ] = acc[NI];
+                if (i < ni) pp[i] = (double)acc[i];
+            pp[PJ] = (double)acc[NI];
         }
     }
 }
@@ -569,30 +704,37 @@ __global__ void k_gm_fin(int k, int nch, int i0, int ni, const double* __restric
 
 // w -= sum_{i in chunk} V_i h_i for the systems of list; the last chunk also
 // writes ||w||^2 partials (one per item)
-template <int NI>
-__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, int i0, int ni, double* __restrict__ w,
-                                                         Gm G, const double* __restrict__ h, const int* list,
+template <class T, int NI>
+__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, int i0, int ni, T* __restrict__ w,
+                                                         Basis<T> Bv, const double* __restrict__ h, const int* list,
                                                          int last, double* __restrict__ part)
 {
+    using VT = typename Vec<T>::type;
+    constexpr int VW = Vec<T>::W;
     FOR_ITEMS(I, list, c, r0, r1)
     {
-        double hc[NI];
+        T hc[NI];
 #pragma unroll
-        for (int i = 0; i < NI; ++i) hc[i] = i < ni ? h[(size_t)(i0 + i) * k + c] : 0.0;
+        for (int i = 0; i < NI; ++i) hc[i] = i < ni ? (T)(-h[(size_t)(i0 + i) * k + c]) : (T)0;
         const int64_t o = (int64_t)c * I.ld;
-        const double* Vp = G.V + (int64_t)i0 * G.vstride + o;
-        double acc = 0.0;
-        for (int64_t row = r0 + lane_; row < r1; row += 32) {
-            double wv = w[o + row];
+        const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
+        const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
+        T acc = 0;
+        for (int64_t row = r0 + (int64_t)lane_ * VW; row < r1v; row += 32 * VW) {
+            VT wv = *reinterpret_cast<const VT*>(w + o + row);
+            VT vv[NI];
 #pragma unroll
             for (int i = 0; i < NI; ++i)
-                if (i < ni) wv = fma(-Vp[(int64_t)i * G.vstride + row], hc[i], wv);
-            w[o + row] = wv;
-            acc = fma(wv, wv, acc);
+                if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+                if (i < ni) wv = Vec<T>::axpy(hc[i], vv[i], wv);
+            *reinterpret_cast<VT*>(w + o + row) = wv;
+            acc += Vec<T>::dot(wv, wv);
         }
         if (last) {
-            acc = warp_sum(acc);
-            if (lane_ == 0) part[(size_t)c * I.nch + q_] = acc;
+            acc = warp_sum_t(acc);
+            if (lane_ == 0) part[(size_t)c * I.nch + q_] = (double)acc;
         }
     }
 }
@@ -626,17 +768,17 @@ __global__ void k_gm_finnorm(int k, int nch, const double* __restrict__ part, Gm
 }
 
 // H(:,j) = h0 (+ h1), ||w||, Givens rotations, residual estimate, stop tests
-__global__ void k_gm_givens(int k, int j, int maxit, Sys S, Gm G, Dims D, int* any_adv)
+__global__ void k_gm_givens(int k, int j, const int* cap, Sys S, Gm G, Dims D, int* any_adv)
 {
     const int c = threadIdx.x;
     if (c == 0) {
         const int ka = G.ladv[0], kr = G.lreo[0];
         if (ka > 0) {
-            spmm_work(D.n, D.nnzM, ka);
-            spmm_work(D.n, D.nnzA, ka);
+            spmm_work(D, D.nnzM, ka);
+            spmm_work(D, D.nnzA, ka);
             const double p = (double)(ka + kr);  // projection passes
-            kwork_add(PROF_GM_DOTS, 8.0 * D.n * p * (j + 2), D.n * p * (2.0 * (j + 1) + 2.0));
-            kwork_add(PROF_GM_UPDATE, 8.0 * D.n * p * (j + 3), D.n * p * (2.0 * (j + 1) + 2.0));
+            kwork_add(D.site_dots, D.esz * D.n * p * (j + 2), D.n * p * (2.0 * (j + 1) + 2.0));
+            kwork_add(D.site_upd, D.esz * D.n * p * (j + 3), D.n * p * (2.0 * (j + 1) + 2.0));
         }
     }
     if (c < k && G.adv[c]) {
@@ -674,7 +816,7 @@ __global__ void k_gm_givens(int k, int j, int maxit, Sys S, Gm G, Dims D, int* a
         if (fabs(gc[j + 1]) < S.thr[c]) {
             G.adv[c] = 0;
             G.conv[c] = 1;
-        } else if (S.iters[c] >= maxit) {
+        } else if (S.iters[c] >= cap[c]) {
             G.adv[c] = 0;
         }
     }
@@ -687,14 +829,15 @@ __global__ void k_gm_givens(int k, int j, int maxit, Sys S, Gm G, Dims D, int* a
     }
 }
 
-__global__ void k_gm_normalize(Items I, int j, const double* __restrict__ w, Sys S, Gm G)
+template <class T>
+__global__ void k_gm_normalize(Items I, int j, const T* __restrict__ w, Sys S, Gm G, Basis<T> Bv)
 {
     FOR_ITEMS(I, G.ladv, c, r0, r1)
     {
         const double hn = S.hn[c];
-        const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+        const T inv = (T)(hn > 0.0 ? 1.0 / hn : 0.0);
         const int64_t o = (int64_t)c * I.ld;
-        double* Vn = G.V + (int64_t)(j + 1) * G.vstride + o;
+        T* Vn = Bv.V + (int64_t)(j + 1) * Bv.vs + o;
         for (int64_t i = r0 + lane_; i < r1; i += 32) Vn[i] = w[o + i] * inv;
     }
 }
@@ -727,7 +870,8 @@ __global__ void k_gm_trisolve(int k, Sys S, Gm G)
 }
 
 // w = V u per system (the caller forms z = M w and x += z)
-__global__ void k_gm_combine(Items I, double* w, Gm G)
+template <class T>
+__global__ void k_gm_combine(Items I, T* w, Gm G, Basis<T> Bv)
 {
     FOR_ITEMS(I, G.lcyc, c, r0, r1)
     {
@@ -735,14 +879,15 @@ __global__ void k_gm_combine(Items I, double* w, Gm G)
         const double* uc = G.u + (size_t)c * G.m;
         const int64_t o = (int64_t)c * I.ld;
         for (int64_t i = r0 + lane_; i < r1; i += 32) {
-            double s = 0.0;
-            for (int q = 0; q < jd; ++q) s = fma(G.V[(int64_t)q * G.vstride + o + i], uc[q], s);
+            T s = 0;
+            for (int q = 0; q < jd; ++q) s = fma(Bv.V[(int64_t)q * Bv.vs + o + i], (T)uc[q], s);
             w[o + i] = s;
         }
     }
 }
 
-__global__ void k_gm_xadd(Items I, double* x, const double* __restrict__ z, Gm G)
+template <class T>
+__global__ void k_gm_xadd(Items I, T* x, const T* __restrict__ z, Gm G)
 {
     FOR_ITEMS(I, G.lcyc, c, r0, r1)
     {
@@ -753,14 +898,14 @@ __global__ void k_gm_xadd(Items I, double* x, const double* __restrict__ z, Gm G
 
 // end of a cycle: converged systems are done; a system that used its last
 // iteration inside the cycle ends with MAXITER; the rest need a residual
-__global__ void k_gm_cycle_end(int k, int maxit, Sys S, Gm G, int* any_left)
+__global__ void k_gm_cycle_end(int k, const int* cap, Sys S, Gm G, int* any_left)
 {
     const int c = threadIdx.x;
     if (c < k) {
         if (G.cyc[c] && G.conv[c]) {
             G.done[c] = 1;
             S.status[c] = ST_OK;
-        } else if (G.cyc[c] && S.iters[c] >= maxit) {
+        } else if (G.cyc[c] && S.iters[c] >= cap[c]) {
             G.done[c] = 1;
             S.status[c] = ST_MAXITER;
         }
@@ -781,33 +926,122 @@ __global__ void k_list_all(int k, int* list)
     }
 }
 
-// ---------------------------------------------------------------- host helpers
-template <int NI>
-void proj_t(const Items& I, int k, int i0, int ni, const double* w, const Gm& G, const int* list, double* part,
-            cudaStream_t st)
+__global__ void k_fill_int(int k, int* a, int v)
 {
-    k_gm_proj<NI><<<SAI_GRID(item_blocks(I.n, k)), IT_WARPS * 32, 0, st>>>(I, k, i0, ni, w, G, list, part);
+    for (int c = threadIdx.x; c < k; c += blockDim.x) a[c] = v;
 }
 
-template <int NI>
-void upd_t(const Items& I, int k, int i0, int ni, double* w, const Gm& G, const double* h, const int* list, int last,
-           double* part, cudaStream_t st)
+__global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b)
 {
-    k_gm_upd<NI><<<SAI_GRID(item_blocks(I.n, k)), IT_WARPS * 32, 0, st>>>(I, k, i0, ni, w, G, h, list, last, part);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------- iterative refinement (FP64 outer)
+// Outer step check: beta_c = ||b_c - A~ x_c|| (FP64). Stops a system when
+// beta_c < thr_c (the FP64 stopping test) or when its inner iterations
+// reach maxit; otherwise sets the inner tolerance on the normalised residual
+// thr_in_c = max(tau, 0.3 thr_c / beta_c) and the inner iteration cap.
+__global__ void k_ir_check(int k, int nch, const double* part, const double* thr, double tau, int maxit,
+                           const int* tot, int* done, int* status, double* beta, double* thr_in, int* cap,
+                           int* lir, int* any)
+{
+    const int c = threadIdx.x;
+    if (c < k && !done[c]) {
+        const double b = sqrt(sum_chunks(part, 0, c, k, nch));
+        beta[c] = b;
+        if (b < thr[c]) {
+            done[c] = 1;
+            status[c] = ST_OK;
+        } else if (tot[c] >= maxit) {
+            done[c] = 1;
+            status[c] = ST_MAXITER;
+        } else {
+            thr_in[c] = fmax(tau, 0.3 * thr[c] / b);
+            cap[c] = maxit - tot[c];
+        }
+    }
+    if (c < k && done[c]) {
+        thr_in[c] = INFINITY;  // a finished system takes no inner iteration
+        cap[c] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int q = 0;
+        for (int s = 0; s < k; ++s)
+            if (!done[s]) lir[1 + q++] = s;
+        lir[0] = q;
+        *any = q > 0;
+    }
+}
+
+// r32 = r64 / beta for the refined systems, 0 for the others
+__global__ void k_ir_scale(Items I, int k, const double* __restrict__ r64, const double* beta, const int* done,
+                           float* __restrict__ r32, const int* lall)
+{
+    FOR_ITEMS(I, lall, c, r0, r1)
+    {
+        const int64_t o = (int64_t)c * I.ld;
+        const double s = done[c] ? 0.0 : 1.0 / beta[c];
+        for (int64_t i = r0 + lane_; i < r1; i += 32) r32[o + i] = (float)(r64[o + i] * s);
+    }
+}
+
+// x64 += beta * d32 for the refined systems; tot += inner iterations
+__global__ void k_ir_update(Items I, double* __restrict__ x64, const float* __restrict__ d32, const double* beta,
+                            const int* lir)
+{
+    FOR_ITEMS(I, lir, c, r0, r1)
+    {
+        const int64_t o = (int64_t)c * I.ld;
+        const double b = beta[c];
+        for (int64_t i = r0 + lane_; i < r1; i += 32) x64[o + i] = fma(b, (double)d32[o + i], x64[o + i]);
+    }
+}
+
+__global__ void k_ir_total(int k, const int* lir, const int* it_in, int* tot)
+{
+    if (threadIdx.x == 0)
+        for (int s = 0; s < lir[0]; ++s) tot[lir[1 + s]] += it_in[lir[1 + s]];
+}
+
+// final report of the refined solve: outer status and total inner iterations
+__global__ void k_ir_finish(int k, const int* done, const int* status64, const int* tot, int* status, int* iters)
+{
+    const int c = threadIdx.x;
+    if (c < k) {
+        status[c] = done[c] ? status64[c] : ST_MAXITER;
+        iters[c] = tot[c];
+    }
+}
+
+// ---------------------------------------------------------------- GMRES engine
+template <class T, int NI>
+void proj_t(const Items& I, int k, int i0, int ni, const T* w, const Basis<T>& B, const int* list, double* part,
+            cudaStream_t st)
+{
+    k_gm_proj<T, NI><<<SAI_GRID(item_blocks(I.n, k)), IT_WARPS * 32, 0, st>>>(I, k, i0, ni, w, B, list, part);
+}
+
+template <class T, int NI>
+void upd_t(const Items& I, int k, int i0, int ni, T* w, const Basis<T>& B, const double* h, const int* list,
+           int last, double* part, cudaStream_t st)
+{
+    k_gm_upd<T, NI><<<SAI_GRID(item_blocks(I.n, k)), IT_WARPS * 32, 0, st>>>(I, k, i0, ni, w, B, h, list, last, part);
 }
 
 // One classical Gram-Schmidt pass of w against V_0..V_j for the systems of list.
-void cgs_pass(const Items& I, int k, int j, int pass, double* w, const Gm& G, const int* list, double* part,
-              double* part2, cudaStream_t st)
+template <class T>
+void cgs_pass(const Items& I, int k, int j, int pass, T* w, const Basis<T>& B, const Gm& G, const int* list,
+              double* part, double* part2, const Dims& D, cudaStream_t st)
 {
     double* h = G.h + (size_t)pass * (G.m + 1) * k;
     for (int i0 = 0; i0 <= j; i0 += PJ) {
         const int ni = (j + 1 - i0) < PJ ? (j + 1 - i0) : PJ;
         {
-            ProfScope ps(PROF_GM_DOTS, st);
-            if (ni <= 8) proj_t<8>(I, k, i0, ni, w, G, list, part, st);
-            else if (ni <= 16) proj_t<16>(I, k, i0, ni, w, G, list, part, st);
-            else proj_t<32>(I, k, i0, ni, w, G, list, part, st);
+            ProfScope ps(D.site_dots, st);
+            if (ni <= 8) proj_t<T, 8>(I, k, i0, ni, w, B, list, part, st);
+            else proj_t<T, 16>(I, k, i0, ni, w, B, list, part, st);
         }
         const int64_t warps = (int64_t)k * (ni + 1);
         k_gm_fin<<<SAI_GRID(sai_div_up(warps * 32, 256)), 256, 0, st>>>(k, I.nch, i0, ni, part, list, h,
@@ -816,12 +1050,129 @@ void cgs_pass(const Items& I, int k, int j, int pass, double* w, const Gm& G, co
     for (int i0 = 0; i0 <= j; i0 += PJ) {
         const int ni = (j + 1 - i0) < PJ ? (j + 1 - i0) : PJ;
         const int last = (i0 + PJ > j) ? 1 : 0;
-        ProfScope ps(PROF_GM_UPDATE, st);
-        if (ni <= 8) upd_t<8>(I, k, i0, ni, w, G, h, list, last, part2, st);
-        else if (ni <= 16) upd_t<16>(I, k, i0, ni, w, G, h, list, last, part2, st);
-        else upd_t<32>(I, k, i0, ni, w, G, h, list, last, part2, st);
+        ProfScope ps(D.site_upd, st);
+        if (ni <= 8) upd_t<T, 8>(I, k, i0, ni, w, B, h, list, last, part2, st);
+        else upd_t<T, 16>(I, k, i0, ni, w, B, h, list, last, part2, st);
     }
     k_gm_finnorm<<<SAI_GRID(1), 1024, 0, st>>>(k, I.nch, part2, G, pass);
+}
+
+template <class T>
+struct GmWork {  // device buffers of one GMRES engine
+    Basis<T> B;
+    T *r, *w, *z;
+};
+
+// Restarted GMRES on the systems with finite thresholds: X = 0 start,
+// per-system iteration caps, S.iters counts the inner steps of this call.
+template <class T>
+sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs, T* Xs, const GmWork<T>& Wk, Sys& S,
+                     Gm& G, const int* cap, double* pt, double* pt2, int* fl, const Dims& D, cudaStream_t st)
+{
+    const int32_t n = I.n;
+    const int64_t ld = I.ld;
+    const int ib = item_blocks(n > 0 ? n : 1, k);
+    const int check_every = 4;
+    int hflag = 0;
+    T* r = Wk.r;
+    T* w = Wk.w;
+    T* z = Wk.z;
+    k_gm_init<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bs, Xs, r, S.lall, pt2);
+    int first = 1;
+    for (;;) {
+        k_gm_cycle_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, I.nch, pt2, cap, S, G, first, fl);
+        first = 0;
+        SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaStreamSynchronize(st));
+        if (!hflag) break;
+        k_gm_v0<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, S, G, Wk.B);
+        for (int j = 0; j < m; ++j) {
+            const T* vj = Wk.B.V + (size_t)j * Wk.B.vs;
+            {
+                ProfScope ps(D.site_spmm, st);
+                spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, vj, z, nullptr, G.ladv, st);
+            }
+            {
+                ProfScope ps(D.site_spmm, st);
+                spmv<T, 0>(n, ld, A.Ar, A.Ac, A.Av, k, z, w, nullptr, G.ladv, st);
+            }
+            cgs_pass<T>(I, k, j, 0, w, Wk.B, G, G.ladv, pt, pt2, D, st);
+            cgs_pass<T>(I, k, j, 1, w, Wk.B, G, G.lreo, pt, pt2, D, st);
+            k_gm_givens<<<SAI_GRID(1), CTRL, 0, st>>>(k, j, cap, S, G, D, fl);
+            k_gm_normalize<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, j, w, S, G, Wk.B);
+            SAI_CUDA(cudaGetLastError());
+            if ((j + 1) % check_every == 0 || j + 1 == m) {
+                SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+                SAI_CUDA(cudaStreamSynchronize(st));
+                if (!hflag) break;
+            }
+        }
+        k_gm_trisolve<<<SAI_GRID(1), CTRL, 0, st>>>(k, S, G);
+        k_gm_combine<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, w, G, Wk.B);
+        spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, w, z, nullptr, G.lcyc, st);
+        k_gm_xadd<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, Xs, z, G);
+        k_gm_cycle_end<<<SAI_GRID(1), CTRL, 0, st>>>(k, cap, S, G, fl);
+        spmv<T, 1>(n, ld, A.Ar, A.Ac, A.Av, k, Xs, r, Bs, G.lcyc, st);
+        k_norm2<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, G.lcyc, pt2);
+        SAI_CUDA(cudaGetLastError());
+    }
+    return SAI_OK;
+}
+
+// Carves the control state of GMRES(m) for k systems out of one double and
+// one int buffer.
+sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
+{
+    G.m = m;
+    const size_t hsz = (size_t)k * (m + 1) * m + 2 * (size_t)k * m + (size_t)k * (m + 1) + 2 * (size_t)(m + 1) * k +
+                       (size_t)k * m + 2 * (size_t)k;
+    SAI_TRY(hb.alloc(sizeof(double) * hsz, st, true));
+    SAI_TRY(ib.alloc(sizeof(int) * (6 * k + 3 * (k + 1)), st, true));
+    SAI_CUDA(cudaMemsetAsync(hb.p, 0, sizeof(double) * hsz, st));
+    SAI_CUDA(cudaMemsetAsync(ib.p, 0, sizeof(int) * (6 * k + 3 * (k + 1)), st));
+    double* hp = hb.as<double>();
+    G.H = hp;
+    hp += (size_t)k * (m + 1) * m;
+    G.cs = hp;
+    hp += (size_t)k * m;
+    G.sn = hp;
+    hp += (size_t)k * m;
+    G.g = hp;
+    hp += (size_t)k * (m + 1);
+    G.h = hp;
+    hp += 2 * (size_t)(m + 1) * k;
+    G.u = hp;
+    hp += (size_t)k * m;
+    G.ww = hp;
+    G.hn2 = hp + k;
+    int* ip = ib.as<int>();
+    G.cyc = ip;
+    G.adv = ip + k;
+    G.jd = ip + 2 * k;
+    G.done = ip + 3 * k;
+    G.conv = ip + 4 * k;
+    G.reo = ip + 5 * k;
+    G.lcyc = ip + 6 * k;
+    G.ladv = G.lcyc + (k + 1);
+    G.lreo = G.ladv + (k + 1);
+    return SAI_OK;
+}
+
+template <class T>
+sai_status gm_work_alloc(size_t blk, int64_t n, int64_t ld, int m, Buf& vb, Buf& wb, GmWork<T>& Wk, cudaStream_t st)
+{
+    SAI_TRY(vb.alloc(sizeof(T) * blk * (m + 1) + 16, st, true));
+    SAI_TRY(wb.alloc(sizeof(T) * blk * 3 + 16, st, true));
+    SAI_CUDA(cudaMemsetAsync(wb.p, 0, sizeof(T) * blk * 3, st));
+    // the padding rows [n, ld) of every basis vector stay zero
+    if (ld > n)
+        SAI_CUDA(cudaMemset2DAsync(vb.as<T>() + n, sizeof(T) * ld, 0, sizeof(T) * (ld - n), blk / ld * (m + 1), st));
+    Wk.B.V = vb.as<T>();
+    Wk.B.vs = (int64_t)blk;
+    Wk.r = wb.as<T>();
+    Wk.w = Wk.r + blk;
+    Wk.z = Wk.w + blk;
+    return SAI_OK;
 }
 
 }  // namespace
@@ -833,6 +1184,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     if (!h || !P || !prm || !thr || !iters || !status || k < 1 || k > CTRL) return SAI_INVALID_ARG;
     if (prm->maxit < 0 || (prm->method == SAI_GMRES && prm->restart < 1)) return SAI_INVALID_ARG;
     if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES) return SAI_INVALID_ARG;
+    if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
+    if (prm->precision == SAI_FP32_REFINE64 && prm->method != SAI_GMRES) return SAI_NOT_IMPLEMENTED;
     const int32_t n = h->n;
     if (n > 0 && (!B || !X)) return SAI_INVALID_ARG;
     if (g_sms == 0) {
@@ -847,17 +1200,18 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     I.ld = ld;
     I.nch = nchunks(n > 0 ? n : 1);
     const int ib = item_blocks(n > 0 ? n : 1, k);
-    const int64_t* Ar = h->Atr_rp.as<int64_t>();
-    const int32_t* Ac = h->Atr_ci.as<int32_t>();
-    const double* Av = h->Atr_v.as<double>();
-    const int64_t* Mr = P->Mr_rp.as<int64_t>();
-    const int32_t* Mc = P->Mr_ci.as<int32_t>();
-    const double* Mv = P->Mr_v.as<double>();
+    Ops<double> A64;
+    A64.Ar = h->Atr_rp.as<int64_t>();
+    A64.Ac = h->Atr_ci.as<int32_t>();
+    A64.Av = h->Atr_v.as<double>();
+    A64.Mr = P->Mr_rp.as<int64_t>();
+    A64.Mc = P->Mr_ci.as<int32_t>();
+    A64.Mv = P->Mr_v.as<double>();
     int64_t tg = sai_div_up((int64_t)n * k > 0 ? (int64_t)n * k : 1, 256);
     if (tg > (int64_t)g_sms * 8) tg = (int64_t)g_sms * 8;
     const int tgrid = (int)tg;
 
-    Buf sysd, sysi, part, part2, flag, Bs, Xs;
+    Buf sysd, sysi, part, part2, flag, Bs, Xs, capb;
     SAI_TRY(sysd.alloc(sizeof(double) * 7 * k, st, true));
     SAI_TRY(sysi.alloc(sizeof(int) * (5 * k + 3 * (k + 1)), st, true));
     SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * (PJ + 1), st, true));
@@ -865,6 +1219,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     SAI_TRY(flag.alloc(sizeof(int) * 4, st, true));
     SAI_TRY(Bs.alloc(sizeof(double) * blk + 8, st, true));
     SAI_TRY(Xs.alloc(sizeof(double) * blk + 8, st, true));
+    SAI_TRY(capb.alloc(sizeof(int) * k, st, true));
     Sys S;
     double* d = sysd.as<double>();
     S.thr = d;
@@ -893,166 +1248,94 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     D.n = (double)n;
     D.nnzA = (double)h->nnz_At;
     D.nnzM = (double)P->nnz;
-    const int check_every = 4;
+    D.esz = 8.0;
+    D.site_spmm = PROF_SPMM;
+    D.site_dots = PROF_GM_DOTS;
+    D.site_upd = PROF_GM_UPDATE;
     double* Bsd = Bs.as<double>();
     double* Xsd = Xs.as<double>();
+    double* pt = part.as<double>();
+    double* pt2 = part2.as<double>();
+    int* cap = capb.as<int>();
     if (n > 0) k_to_soa<<<SAI_GRID(tgrid), 256, 0, st>>>(n, k, ld, B, Bsd);
     k_list_all<<<SAI_GRID(1), 32, 0, st>>>(k, S.lall);
+    k_fill_int<<<SAI_GRID(1), 256, 0, st>>>(k, cap, prm->maxit);
     SAI_CUDA(cudaGetLastError());
 
     if (prm->method == SAI_BICGSTAB) {
-        Buf vecs;
-        SAI_TRY(vecs.alloc(sizeof(double) * blk * 8 + 8, st, true));
-        SAI_CUDA(cudaMemsetAsync(vecs.p, 0, sizeof(double) * blk * 8, st));
-        double* r = vecs.as<double>();
-        double* rh = r + blk;
-        double* p = rh + blk;
-        double* v = p + blk;
-        double* ph = v + blk;
-        double* s = ph + blk;
-        double* sh = s + blk;
-        double* t = sh + blk;
-        double* pt = part.as<double>();
-        const int nch = I.nch;
-        k_bicg_init<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r, rh, p, v, S.lall, pt);
-        k_bicg_f0<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S);
-        SAI_CUDA(cudaGetLastError());
-        for (int it = 0; it < prm->maxit; ++it) {
-            k_bicg_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, prm->maxit, S);
-            {
-                ProfScope ps(PROF_BICG_VEC, st);
-                k_bicg_p<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, p, v, S);
-            }
-            {
-                ProfScope ps(PROF_SPMM, st);
-                spmv<0>(n, ld, Mr, Mc, Mv, k, p, ph, nullptr, S.lact, st);
-            }
-            {
-                ProfScope ps(PROF_SPMM, st);
-                spmv<0>(n, ld, Ar, Ac, Av, k, ph, v, nullptr, S.lact, st);
-            }
-            {
-                ProfScope ps(PROF_BICG_VEC, st);
-                k_dots<1><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, rh, v, nullptr, nullptr, S.lact, pt);
-            }
-            k_bicg_f1<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
-            {
-                ProfScope ps(PROF_BICG_VEC, st);
-                k_bicg_s<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, v, s, S, pt);
-            }
-            k_bicg_f2<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
-            {
-                ProfScope ps(PROF_SPMM, st);
-                spmv<0>(n, ld, Mr, Mc, Mv, k, s, sh, nullptr, S.lgo, st);
-            }
-            {
-                ProfScope ps(PROF_SPMM, st);
-                spmv<0>(n, ld, Ar, Ac, Av, k, sh, t, nullptr, S.lgo, st);
-            }
-            {
-                ProfScope ps(PROF_BICG_VEC, st);
-                k_dots<2><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, t, s, t, t, S.lgo, pt);
-            }
-            k_bicg_f3<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
-            {
-                ProfScope ps(PROF_BICG_VEC, st);
-                k_bicg_xr<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Xsd, r, rh, ph, sh, s, t, S, pt);
-            }
-            k_bicg_f4<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D, fl);
-            SAI_CUDA(cudaGetLastError());
-            if ((it + 1) % check_every == 0 || it + 1 == prm->maxit) {
-                SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
-                SAI_CUDA(cudaStreamSynchronize(st));
-                if (!hflag) break;
-            }
-        }
-        // systems still active after maxit passes
-        k_bicg_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, prm->maxit, S);
-    } else {
-        const int m = prm->restart;
+        SAI_TRY(bicgstab_run(I, k, A64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
+    } else if (prm->precision == SAI_FP64) {
         Gm G;
-        G.m = m;
-        G.vstride = (int64_t)blk;
-        Buf vb, hb, ibuf, wb;
-        SAI_TRY(vb.alloc(sizeof(double) * blk * (m + 1) + 8, st, true));
-        SAI_TRY(wb.alloc(sizeof(double) * blk * 3 + 8, st, true));
-        SAI_CUDA(cudaMemsetAsync(wb.p, 0, sizeof(double) * blk * 3, st));
-        const size_t hsz = (size_t)k * (m + 1) * m + 2 * (size_t)k * m + (size_t)k * (m + 1) +
-                           2 * (size_t)(m + 1) * k + (size_t)k * m + 2 * (size_t)k;
-        SAI_TRY(hb.alloc(sizeof(double) * hsz, st, true));
-        SAI_TRY(ibuf.alloc(sizeof(int) * (6 * k + 3 * (k + 1)), st, true));
-        SAI_CUDA(cudaMemsetAsync(hb.p, 0, sizeof(double) * hsz, st));
-        G.V = vb.as<double>();
-        double* hp = hb.as<double>();
-        G.H = hp;
-        hp += (size_t)k * (m + 1) * m;
-        G.cs = hp;
-        hp += (size_t)k * m;
-        G.sn = hp;
-        hp += (size_t)k * m;
-        G.g = hp;
-        hp += (size_t)k * (m + 1);
-        G.h = hp;
-        hp += 2 * (size_t)(m + 1) * k;
-        G.u = hp;
-        hp += (size_t)k * m;
-        G.ww = hp;
-        G.hn2 = hp + k;
-        int* ip = ibuf.as<int>();
-        G.cyc = ip;
-        G.adv = ip + k;
-        G.jd = ip + 2 * k;
-        G.done = ip + 3 * k;
-        G.conv = ip + 4 * k;
-        G.reo = ip + 5 * k;
-        G.lcyc = ip + 6 * k;
-        G.ladv = G.lcyc + (k + 1);
-        G.lreo = G.ladv + (k + 1);
-        SAI_CUDA(cudaMemsetAsync(ip, 0, sizeof(int) * (6 * k + 3 * (k + 1)), st));
-        double* r = wb.as<double>();
-        double* w = r + blk;
-        double* z = w + blk;
-        double* pt = part.as<double>();
-        double* pt2 = part2.as<double>();
-        k_gm_init<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r, S.lall, pt2);
-        int first = 1;
-        for (;;) {
-            k_gm_cycle_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, I.nch, pt2, prm->maxit, S, G, first, fl);
-            first = 0;
+        Buf hb, ibuf, vb, wb;
+        GmWork<double> Wk;
+        SAI_TRY(gm_alloc(k, prm->restart, hb, ibuf, G, st));
+        SAI_TRY(gm_work_alloc<double>(blk, n, ld, prm->restart, vb, wb, Wk, st));
+        SAI_TRY(gmres_run<double>(I, k, prm->restart, A64, Bsd, Xsd, Wk, S, G, cap, pt, pt2, fl, D, st));
+    } else {
+        // GMRES with iterative refinement: FP64 residual, correction and stop
+        // tests outside; the inner solves run entirely in FP32.
+        const double tau = prm->inner_tol > 0.0 ? prm->inner_tol : 1e-4;
+        Gm G;
+        Buf hb, ibuf, vb, wb, a32, m32, r64b, v32b, irb, ird;
+        GmWork<float> Wk;
+        SAI_TRY(gm_alloc(k, prm->restart, hb, ibuf, G, st));
+        SAI_TRY(gm_work_alloc<float>(blk, n, ld, prm->restart, vb, wb, Wk, st));
+        SAI_TRY(a32.alloc(sizeof(float) * (size_t)(h->nnz_At > 0 ? h->nnz_At : 1), st, true));
+        SAI_TRY(m32.alloc(sizeof(float) * (size_t)(P->nnz > 0 ? P->nnz : 1), st, true));
+        SAI_TRY(r64b.alloc(sizeof(double) * blk + 8, st, true));
+        SAI_TRY(v32b.alloc(sizeof(float) * blk * 2 + 16, st, true));
+        SAI_TRY(irb.alloc(sizeof(int) * (4 * k + (k + 1)), st, true));
+        SAI_TRY(ird.alloc(sizeof(double) * 3 * k, st, true));
+        SAI_CUDA(cudaMemsetAsync(v32b.p, 0, sizeof(float) * blk * 2, st));
+        SAI_CUDA(cudaMemsetAsync(irb.p, 0, sizeof(int) * (4 * k + (k + 1)), st));
+        int64_t cg = sai_div_up(h->nnz_At > P->nnz ? h->nnz_At : P->nnz, 256);
+        if (cg > (int64_t)g_sms * 8) cg = (int64_t)g_sms * 8;
+        if (cg < 1) cg = 1;
+        if (h->nnz_At > 0) k_cast_f32<<<SAI_GRID(cg), 256, 0, st>>>(h->nnz_At, A64.Av, a32.as<float>());
+        if (P->nnz > 0) k_cast_f32<<<SAI_GRID(cg), 256, 0, st>>>(P->nnz, A64.Mv, m32.as<float>());
+        Ops<float> A32;
+        A32.Ar = A64.Ar;
+        A32.Ac = A64.Ac;
+        A32.Av = a32.as<float>();
+        A32.Mr = A64.Mr;
+        A32.Mc = A64.Mc;
+        A32.Mv = m32.as<float>();
+        double* r64 = r64b.as<double>();
+        float* r32 = v32b.as<float>();
+        float* d32 = r32 + blk;
+        int* done = irb.as<int>();
+        int* status64 = done + k;
+        int* tot = done + 2 * k;
+        int* lir = done + 4 * k;
+        double* beta = ird.as<double>();
+        double* thr64 = beta + k;
+        double* thr_in = S.thr;
+        SAI_CUDA(cudaMemcpyAsync(thr64, thr, sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        Dims D32 = D;
+        D32.esz = 4.0;
+        D32.site_spmm = PROF_SPMM32;
+        D32.site_dots = PROF_GM_DOTS32;
+        D32.site_upd = PROF_GM_UPDATE32;
+        // r64 = B, x64 = 0 and ||B||^2 partials
+        k_gm_init<double><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r64, S.lall, pt2);
+        const int max_outer = 40;
+        for (int outer = 0; outer < max_outer; ++outer) {
+            k_ir_check<<<SAI_GRID(1), CTRL, 0, st>>>(k, I.nch, pt2, thr64, tau, prm->maxit, tot, done, status64, beta,
+                                                     thr_in, cap, lir, fl);
             SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
             SAI_CUDA(cudaStreamSynchronize(st));
             if (!hflag) break;
-            k_gm_v0<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, S, G);
-            for (int j = 0; j < m; ++j) {
-                const double* vj = G.V + (size_t)j * blk;
-                {
-                    ProfScope ps(PROF_SPMM, st);
-                    spmv<0>(n, ld, Mr, Mc, Mv, k, vj, z, nullptr, G.ladv, st);
-                }
-                {
-                    ProfScope ps(PROF_SPMM, st);
-                    spmv<0>(n, ld, Ar, Ac, Av, k, z, w, nullptr, G.ladv, st);
-                }
-                cgs_pass(I, k, j, 0, w, G, G.ladv, pt, pt2, st);
-                cgs_pass(I, k, j, 1, w, G, G.lreo, pt, pt2, st);
-                k_gm_givens<<<SAI_GRID(1), CTRL, 0, st>>>(k, j, prm->maxit, S, G, D, fl);
-                k_gm_normalize<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, j, w, S, G);
-                SAI_CUDA(cudaGetLastError());
-                if ((j + 1) % check_every == 0 || j + 1 == m) {
-                    SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
-                    SAI_CUDA(cudaStreamSynchronize(st));
-                    if (!hflag) break;
-                }
-            }
-            k_gm_trisolve<<<SAI_GRID(1), CTRL, 0, st>>>(k, S, G);
-            k_gm_combine<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, w, G);
-            spmv<0>(n, ld, Mr, Mc, Mv, k, w, z, nullptr, G.lcyc, st);
-            k_gm_xadd<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, Xsd, z, G);
-            k_gm_cycle_end<<<SAI_GRID(1), CTRL, 0, st>>>(k, prm->maxit, S, G, fl);
-            spmv<1>(n, ld, Ar, Ac, Av, k, Xsd, r, Bsd, G.lcyc, st);
-            k_norm2<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, G.lcyc, pt2);
+            k_ir_scale<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r64, beta, done, r32, S.lall);
+            SAI_TRY(gmres_run<float>(I, k, prm->restart, A32, r32, d32, Wk, S, G, cap, pt, pt2, fl, D32, st));
+            k_ir_update<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, Xsd, d32, beta, lir);
+            k_ir_total<<<SAI_GRID(1), 32, 0, st>>>(k, lir, S.iters, tot);
+            spmv<double, 1>(n, ld, A64.Ar, A64.Ac, A64.Av, k, Xsd, r64, Bsd, lir, st);
+            k_norm2<double><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r64, lir, pt2);
             SAI_CUDA(cudaGetLastError());
         }
+        // report the outer status and the total inner iterations
+        k_ir_finish<<<SAI_GRID(1), CTRL, 0, st>>>(k, done, status64, tot, S.status, S.iters);
+        SAI_CUDA(cudaGetLastError());
     }
     if (n > 0) k_from_soa<<<SAI_GRID(tgrid), 256, 0, st>>>(n, k, ld, Xsd, X);
     SAI_CUDA(cudaGetLastError());
