@@ -255,9 +255,10 @@ sai_status sai_solve(const sai_csc_view* A, const double* b, const sai_solve_par
 typedef struct {
     char name[24];
     int64_t launches;   /* launches of this site while the profile was open */
-    double ms;          /* sum of their CUDA-event durations */
-    double bytes;       /* algorithmic bytes moved by those launches */
-    double flops;       /* algorithmic floating-point operations */
+    int64_t timed;      /* launches bracketed by CUDA events (every 7th) */
+    double ms;          /* device time of all launches: mean timed duration x launches */
+    double bytes;       /* algorithmic bytes moved by all launches */
+    double flops;       /* algorithmic floating-point operations of all launches */
 } sai_profile_site;
 
 typedef struct {
@@ -268,9 +269,10 @@ typedef struct {
 
 /* Total number of kernel launches made by the library in this process. */
 uint64_t sai_launch_count(void);
-/* Opens a profile: resets the counters and brackets every launch of the
- * profiled sites (SAI build, Krylov SpMM, GMRES projections and updates,
- * BiCGStab vector kernels) with CUDA events on its stream. */
+/* Opens a profile: resets the counters, counts every launch of the profiled
+ * sites (SAI build, Krylov SpMV, GMRES projections and updates, BiCGStab
+ * vector kernels) and brackets one launch in seven of each site with CUDA
+ * events on its stream. */
 sai_status sai_profile_begin(void);
 /* Closes the profile: synchronises the device, fills *out. */
 sai_status sai_profile_end(sai_profile_report* out);

@@ -81,8 +81,8 @@ class _SolveReport(C.Structure):
 
 
 class _ProfSite(C.Structure):
-    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double),
-                ("flops", C.c_double)]
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("timed", C.c_int64), ("ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
 
 
 class _ProfReport(C.Structure):
@@ -342,5 +342,6 @@ def profile_end():
     sites = {}
     for q in range(rep.nsites):
         st = rep.site[q]
-        sites[st.name.decode()] = dict(launches=int(st.launches), ms=st.ms, bytes=st.bytes, flops=st.flops)
+        sites[st.name.decode()] = dict(launches=int(st.launches), timed=int(st.timed), ms=st.ms, bytes=st.bytes,
+                                       flops=st.flops)
     return {"launches": int(rep.launches), "sites": sites}

@@ -31,6 +31,8 @@ unsigned sai_count_grid(unsigned g)
     return g;
 }
 
+void sai_count_grid_add(long long d) { g_launches.fetch_add((unsigned long long)d, std::memory_order_relaxed); }
+
 bool sai_prof_on() { return g_prof.load(std::memory_order_relaxed); }
 
 void sai_internal_note_cuda_error(cudaError_t e, const char* what, const char* file, int line)
@@ -57,9 +59,28 @@ void sai_pool_init_once()
 
 static inline cudaStream_t S(sai_stream_t s) { return (cudaStream_t)s; }
 
+cudaStream_t sai_aux_stream()
+{
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+        streams[dev] = nullptr;
+    return streams[dev];
+}
+
+// Every launch of a profiled site is counted; one in k_prof_stride is timed
+// with a pair of events (a uniform subsample of the site's launches), which
+// keeps the event overhead out of the timed region.
+static const long long k_prof_stride = 7;
+static std::atomic<long long> g_site_calls[PROF_NSITES];
+
 ProfScope::ProfScope(int site_, cudaStream_t st_) : site(site_), st(st_)
 {
     if (!sai_prof_on()) return;
+    if (g_site_calls[site].fetch_add(1) % k_prof_stride != 0) return;
     const size_t i = g_ev_next.fetch_add(2);
     if (i + 1 >= g_ev_pool.size()) return;
     idx = (long long)i;
@@ -85,6 +106,7 @@ sai_status sai_profile_begin(void)
     {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         for (auto& v : g_prof_ev) v.clear();
+        for (auto& c : g_site_calls) c.store(0);
         if (g_ev_pool.empty()) {
             g_ev_pool.resize(k_ev_pool);
             for (auto& e : g_ev_pool) SAI_CUDA(cudaEventCreate(&e));
@@ -114,15 +136,18 @@ sai_status sai_profile_end(sai_profile_report* out)
     for (int q = 0; q < PROF_NSITES; ++q) {
         sai_profile_site& ps = out->site[q];
         strncpy(ps.name, k_site_names[q], sizeof(ps.name) - 1);
-        ps.launches = (int64_t)g_prof_ev[q].size();
+        ps.launches = (int64_t)g_site_calls[q].load();
         double ms = 0.0;
         for (auto& pr : g_prof_ev[q]) {
             float t = 0.f;
             cudaEventElapsedTime(&t, g_ev_pool[pr.first], g_ev_pool[pr.second]);
             ms += t;
         }
+        // scale the timed subsample to all launches of the site
+        const size_t timed = g_prof_ev[q].size();
+        ps.ms = timed ? ms * (double)ps.launches / (double)timed : 0.0;
+        ps.timed = (int64_t)timed;
         g_prof_ev[q].clear();
-        ps.ms = ms;
         ps.bytes = wk[2 * q] + wb[2 * q];
         ps.flops = wk[2 * q + 1] + wb[2 * q + 1];
     }

@@ -74,6 +74,9 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 // statement runs).
 unsigned sai_count_grid(unsigned g);
 #define SAI_GRID(g) sai_count_grid((unsigned)(g))
+// Adjusts the count for launches replayed from a CUDA graph (counted at
+// replay) or captured into one (not run at capture).
+void sai_count_grid_add(long long d);
 
 // Profiled launch sites: CUDA events around each launch (only while a
 // profile is open) plus algorithmic bytes / flops accumulated on the device.

@@ -82,6 +82,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
 sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st);
 
 void sai_pool_init_once();
+// Library-owned non-blocking stream of the current device (for graph capture), or nullptr.
+cudaStream_t sai_aux_stream();
 
 // Device-side algorithmic work per profiled site ([site][0] bytes, [1] flops),
 // one accumulator per translation unit.

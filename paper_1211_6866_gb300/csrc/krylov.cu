@@ -97,9 +97,11 @@ template <class T, int MODE>
 __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const T* __restrict__ v,
                                                const T* __restrict__ X, T* __restrict__ Y,
-                                               const T* __restrict__ B, const int* __restrict__ list)
+                                               const T* __restrict__ B, const int* __restrict__ list,
+                                               const int* __restrict__ xidx, int64_t xstride)
 {
     const int cnt = list[0];
+    if (xidx) X += (int64_t)(*xidx) * xstride;  // X = block number *xidx of a basis
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
     for (int64_t it = blockIdx.x; it < tiles * cnt; it += gridDim.x) {
         const int64_t tile = it / cnt;
@@ -117,14 +119,14 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
 
 template <class T, int MODE>
 void spmv(int32_t n, int64_t ld, const int64_t* rp, const int32_t* ci, const T* v, int k, const T* X, T* Y,
-          const T* B, const int* list, cudaStream_t st)
+          const T* B, const int* list, cudaStream_t st, const int* xidx = nullptr, int64_t xstride = 0)
 {
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
     int64_t g = tiles * k;
     const int64_t cap = (int64_t)g_sms * 8;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, rp, ci, v, X, Y, B, list);
+    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, rp, ci, v, X, Y, B, list, xidx, xstride);
 }
 
 template <class T>
@@ -518,7 +520,10 @@ struct Gm {
     double* hn2; // k: ||w||^2 after it
     int *cyc, *adv, *jd, *done, *conv, *reo;
     int *lcyc, *ladv, *lreo;  // lists
+    int* jdev;                // inner index j of the current Arnoldi step
 };
+
+constexpr int GM_MAXM = 128;  // largest restart length
 
 // Krylov basis: m+1 system-major blocks of k vectors in the value type T.
 template <class T>
@@ -625,6 +630,7 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* 
         build_list(k, G.cyc, G.lcyc);
         build_list(k, G.adv, G.ladv);
         G.lreo[0] = 0;
+        *G.jdev = 0;
         *any_cyc = G.lcyc[0] > 0;
     }
 }
@@ -640,102 +646,117 @@ __global__ void k_gm_v0(Items I, const T* __restrict__ r, Sys S, Gm G, Basis<T> 
     }
 }
 
-// Projection h_i = V_i^T w (i in [i0, i0+ni)) and ||w||^2 for the systems of
-// list: each warp item keeps NI+1 accumulators in registers and streams its
-// chunk of w and of the ni basis vectors once.
-template <class T, int NI>
-__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_proj(Items I, int k, int i0, int ni,
-                                                          const T* __restrict__ w, Basis<T> Bv, const int* list,
+// Projection h_i = V_i^T w (i = 0..j, j = *jdev) and ||w||^2 for the systems
+// of list: each warp item streams its chunk of w and of the basis once per
+// group of PJ vectors, with PJ accumulators in registers. Partials: slot i of
+// item (c, q) at part[(c*nch + q)*(GM_MAXM+2) + i], slot GM_MAXM+1 = ||w||^2.
+template <class T>
+__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_proj(Items I, int k, const T* __restrict__ w, Basis<T> Bv,
+                                                          const int* list, const int* jdev,
                                                           double* __restrict__ part)
 {
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
+    const int j = *jdev;
     FOR_ITEMS(I, list, c, r0, r1)
     {
-        T acc[NI + 1];
-#pragma unroll
-        for (int i = 0; i <= NI; ++i) acc[i] = 0;
         const int64_t o = (int64_t)c * I.ld;
-        const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
-        for (int64_t row = r0 + (int64_t)lane_ * VW; row < r1v; row += 32 * VW) {
-            const VT wv = *reinterpret_cast<const VT*>(w + o + row);
-            VT vv[NI];
+        double* pp = part + ((size_t)c * I.nch + q_) * (GM_MAXM + 2);
+        for (int i0 = 0; i0 <= j; i0 += PJ) {
+            const int ni = min(PJ, j + 1 - i0);
+            const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
+            T acc[PJ];
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
+            for (int i = 0; i < PJ; ++i) acc[i] = 0;
+            T aw = 0;
+            for (int64_t row = r0 + (int64_t)lane_ * VW; row < r1v; row += 32 * VW) {
+                const VT wv = *reinterpret_cast<const VT*>(w + o + row);
+                VT vv[PJ];
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (i < ni) acc[i] += Vec<T>::dot(vv[i], wv);
-            acc[NI] += Vec<T>::dot(wv, wv);
-        }
+                for (int i = 0; i < PJ; ++i)
+                    if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
 #pragma unroll
-        for (int i = 0; i <= NI; ++i) acc[i] = warp_sum_t(acc[i]);
-        if (lane_ == 0) {
-            double* pp = part + ((size_t)c * I.nch + q_) * (PJ + 1);
+                for (int i = 0; i < PJ; ++i)
+                    if (i < ni) acc[i] += Vec<T>::dot(vv[i], wv);
+                if (i0 == 0) aw += Vec<T>::dot(wv, wv);
+            }
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (i < ni) pp[i] = (double)acc[i];
-            pp[PJ] = (double)acc[NI];
+            for (int i = 0; i < PJ; ++i) acc[i] = warp_sum_t(acc[i]);
+            if (lane_ == 0) {
+#pragma unroll
+                for (int i = 0; i < PJ; ++i)
+                    if (i < ni) pp[i0 + i] = (double)acc[i];
+            }
+            if (i0 == 0) {
+                aw = warp_sum_t(aw);
+                if (lane_ == 0) pp[GM_MAXM + 1] = (double)aw;
+            }
         }
     }
 }
 
-// h[pass][i0+i][c] for i < ni and ww[c] from the chunk partials; one warp per
-// (listed system, i); slot PJ is ||w||^2
-__global__ void k_gm_fin(int k, int nch, int i0, int ni, const double* __restrict__ part, const int* list,
+// h[i][c] for i <= j and ww[c] from the chunk partials; one warp per
+// (listed system, slot); launched with k*(GM_MAXM+2) warps at most
+__global__ void k_gm_fin(int k, int nch, const double* __restrict__ part, const int* list, const int* jdev,
                          double* __restrict__ h, double* __restrict__ ww)
 {
+    const int j = *jdev;
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int cnt = list[0];
-    if (q >= (int64_t)cnt * (ni + 1)) return;
-    const int s = (int)(q / (ni + 1)), i = (int)(q - (int64_t)s * (ni + 1));
+    if (q >= (int64_t)cnt * (j + 2)) return;
+    const int s = (int)(q / (j + 2)), i = (int)(q - (int64_t)s * (j + 2));
     const int c = list[1 + s];
-    const int slot = i < ni ? i : PJ;
+    const int slot = i <= j ? i : GM_MAXM + 1;
     double sum = 0.0;
-    for (int b = lane; b < nch; b += 32) sum += part[((size_t)c * nch + b) * (PJ + 1) + slot];
+    for (int b = lane; b < nch; b += 32) sum += part[((size_t)c * nch + b) * (GM_MAXM + 2) + slot];
     sum = warp_sum(sum);
     if (lane == 0) {
-        if (i < ni) h[(size_t)(i0 + i) * k + c] = sum;
+        if (i <= j) h[(size_t)i * k + c] = sum;
         else if (ww) ww[c] = sum;
     }
 }
 
-// w -= sum_{i in chunk} V_i h_i for the systems of list; the last chunk also
-// writes ||w||^2 partials (one per item)
-template <class T, int NI>
-__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, int i0, int ni, T* __restrict__ w,
-                                                         Basis<T> Bv, const double* __restrict__ h, const int* list,
-                                                         int last, double* __restrict__ part)
+// w -= sum_{i<=j} V_i h_i for the systems of list, one pass over w; writes
+// ||w||^2 partials (one per item). h of the warp's system is staged in
+// shared memory.
+template <class T>
+__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, T* __restrict__ w, Basis<T> Bv,
+                                                         const double* __restrict__ h, const int* list,
+                                                         const int* jdev, double* __restrict__ part)
 {
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
+    __shared__ T hs[IT_WARPS][GM_MAXM];
+    const int j = *jdev;
+    const int wid = threadIdx.x >> 5;
     FOR_ITEMS(I, list, c, r0, r1)
     {
-        T hc[NI];
-#pragma unroll
-        for (int i = 0; i < NI; ++i) hc[i] = i < ni ? (T)(-h[(size_t)(i0 + i) * k + c]) : (T)0;
+        for (int i = lane_; i <= j; i += 32) hs[wid][i] = (T)(-h[(size_t)i * k + c]);
+        __syncwarp();
         const int64_t o = (int64_t)c * I.ld;
-        const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
         T acc = 0;
         for (int64_t row = r0 + (int64_t)lane_ * VW; row < r1v; row += 32 * VW) {
             VT wv = *reinterpret_cast<const VT*>(w + o + row);
-            VT vv[NI];
+            for (int i0 = 0; i0 <= j; i0 += PJ) {
+                const int ni = min(PJ, j + 1 - i0);
+                const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o + row;
+                VT vv[PJ];
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
+                for (int i = 0; i < PJ; ++i)
+                    if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs);
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (i < ni) wv = Vec<T>::axpy(hc[i], vv[i], wv);
+                for (int i = 0; i < PJ; ++i)
+                    if (i < ni) wv = Vec<T>::axpy(hs[wid][i0 + i], vv[i], wv);
+            }
             *reinterpret_cast<VT*>(w + o + row) = wv;
             acc += Vec<T>::dot(wv, wv);
         }
-        if (last) {
-            acc = warp_sum_t(acc);
-            if (lane_ == 0) part[(size_t)c * I.nch + q_] = (double)acc;
-        }
+        acc = warp_sum_t(acc);
+        if (lane_ == 0) part[(size_t)c * I.nch + q_] = (double)acc;
+        __syncwarp();
     }
 }
 
@@ -768,9 +789,10 @@ __global__ void k_gm_finnorm(int k, int nch, const double* __restrict__ part, Gm
 }
 
 // H(:,j) = h0 (+ h1), ||w||, Givens rotations, residual estimate, stop tests
-__global__ void k_gm_givens(int k, int j, const int* cap, Sys S, Gm G, Dims D, int* any_adv)
+__global__ void k_gm_givens(int k, const int* cap, Sys S, Gm G, Dims D, int* any_adv)
 {
     const int c = threadIdx.x;
+    const int j = *G.jdev;
     if (c == 0) {
         const int ka = G.ladv[0], kr = G.lreo[0];
         if (ka > 0) {
@@ -816,22 +838,25 @@ __global__ void k_gm_givens(int k, int j, const int* cap, Sys S, Gm G, Dims D, i
         if (fabs(gc[j + 1]) < S.thr[c]) {
             G.adv[c] = 0;
             G.conv[c] = 1;
-        } else if (S.iters[c] >= cap[c]) {
-            G.adv[c] = 0;
+        } else if (S.iters[c] >= cap[c] || j + 1 >= G.m) {
+            G.adv[c] = 0;  // iteration cap, or the cycle is full: restart
         }
     }
     __syncthreads();
     if (c < k) G.reo[c] = 0;
     if (threadIdx.x == 0) {
+        const int had = G.ladv[0];
         build_list(k, G.adv, G.ladv);
         G.lreo[0] = 0;
+        if (had > 0) *G.jdev = j + 1;
         *any_adv = G.ladv[0] > 0;
     }
 }
 
 template <class T>
-__global__ void k_gm_normalize(Items I, int j, const T* __restrict__ w, Sys S, Gm G, Basis<T> Bv)
+__global__ void k_gm_normalize(Items I, const T* __restrict__ w, Sys S, Gm G, Basis<T> Bv)
 {
+    const int j = *G.jdev - 1;  // givens has advanced the index: write V_{j+1}
     FOR_ITEMS(I, G.ladv, c, r0, r1)
     {
         const double hn = S.hn[c];
@@ -1016,43 +1041,23 @@ __global__ void k_ir_finish(int k, const int* done, const int* status64, const i
 }
 
 // ---------------------------------------------------------------- GMRES engine
-template <class T, int NI>
-void proj_t(const Items& I, int k, int i0, int ni, const T* w, const Basis<T>& B, const int* list, double* part,
-            cudaStream_t st)
-{
-    k_gm_proj<T, NI><<<SAI_GRID(item_blocks(I.n, k)), IT_WARPS * 32, 0, st>>>(I, k, i0, ni, w, B, list, part);
-}
-
-template <class T, int NI>
-void upd_t(const Items& I, int k, int i0, int ni, T* w, const Basis<T>& B, const double* h, const int* list,
-           int last, double* part, cudaStream_t st)
-{
-    k_gm_upd<T, NI><<<SAI_GRID(item_blocks(I.n, k)), IT_WARPS * 32, 0, st>>>(I, k, i0, ni, w, B, h, list, last, part);
-}
-
 // One classical Gram-Schmidt pass of w against V_0..V_j for the systems of list.
 template <class T>
-void cgs_pass(const Items& I, int k, int j, int pass, T* w, const Basis<T>& B, const Gm& G, const int* list,
-              double* part, double* part2, const Dims& D, cudaStream_t st)
+void cgs_pass(const Items& I, int k, int pass, T* w, const Basis<T>& B, const Gm& G, const int* list, double* part,
+              double* part2, const Dims& D, cudaStream_t st)
 {
     double* h = G.h + (size_t)pass * (G.m + 1) * k;
-    for (int i0 = 0; i0 <= j; i0 += PJ) {
-        const int ni = (j + 1 - i0) < PJ ? (j + 1 - i0) : PJ;
-        {
-            ProfScope ps(D.site_dots, st);
-            if (ni <= 8) proj_t<T, 8>(I, k, i0, ni, w, B, list, part, st);
-            else proj_t<T, 16>(I, k, i0, ni, w, B, list, part, st);
-        }
-        const int64_t warps = (int64_t)k * (ni + 1);
-        k_gm_fin<<<SAI_GRID(sai_div_up(warps * 32, 256)), 256, 0, st>>>(k, I.nch, i0, ni, part, list, h,
-                                                                       (i0 == 0 && pass == 0) ? G.ww : nullptr);
+    const int ib = item_blocks(I.n, k);
+    {
+        ProfScope ps(D.site_dots, st);
+        k_gm_proj<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, w, B, list, G.jdev, part);
     }
-    for (int i0 = 0; i0 <= j; i0 += PJ) {
-        const int ni = (j + 1 - i0) < PJ ? (j + 1 - i0) : PJ;
-        const int last = (i0 + PJ > j) ? 1 : 0;
+    const int64_t warps = (int64_t)k * (G.m + 2);
+    k_gm_fin<<<SAI_GRID(sai_div_up(warps * 32, 256)), 256, 0, st>>>(k, I.nch, part, list, G.jdev, h,
+                                                                   pass == 0 ? G.ww : nullptr);
+    {
         ProfScope ps(D.site_upd, st);
-        if (ni <= 8) upd_t<T, 8>(I, k, i0, ni, w, B, h, list, last, part2, st);
-        else upd_t<T, 16>(I, k, i0, ni, w, B, h, list, last, part2, st);
+        k_gm_upd<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, w, B, h, list, G.jdev, part2);
     }
     k_gm_finnorm<<<SAI_GRID(1), 1024, 0, st>>>(k, I.nch, part2, G, pass);
 }
@@ -1065,6 +1070,34 @@ struct GmWork {  // device buffers of one GMRES engine
 
 // Restarted GMRES on the systems with finite thresholds: X = 0 start,
 // per-system iteration caps, S.iters counts the inner steps of this call.
+// One Arnoldi step for the advancing systems (inner index j on the device).
+template <class T>
+void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, Sys& S, Gm& G, const int* cap,
+                  double* pt, double* pt2, int* fl, const Dims& D, cudaStream_t st)
+{
+    const int32_t n = I.n;
+    const int64_t ld = I.ld;
+    {
+        ProfScope ps(D.site_spmm, st);
+        spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, Wk.B.V, Wk.z, nullptr, G.ladv, st, G.jdev, Wk.B.vs);
+    }
+    {
+        ProfScope ps(D.site_spmm, st);
+        spmv<T, 0>(n, ld, A.Ar, A.Ac, A.Av, k, Wk.z, Wk.w, nullptr, G.ladv, st);
+    }
+    cgs_pass<T>(I, k, 0, Wk.w, Wk.B, G, G.ladv, pt, pt2, D, st);
+    cgs_pass<T>(I, k, 1, Wk.w, Wk.B, G, G.lreo, pt, pt2, D, st);
+    k_gm_givens<<<SAI_GRID(1), CTRL, 0, st>>>(k, cap, S, G, D, fl);
+    k_gm_normalize<T><<<SAI_GRID(item_blocks(n > 0 ? n : 1, k)), IT_WARPS * 32, 0, st>>>(I, Wk.w, S, G, Wk.B);
+}
+
+constexpr int GM_STEPS_PER_CHECK = 4;  // Arnoldi steps between host checks (one graph)
+constexpr int GM_LAUNCHES_PER_STEP = 12;
+
+// Restarted GMRES on the systems with finite thresholds: X = 0 start,
+// per-system iteration caps, S.iters counts the inner steps of this call.
+// Unless a profile is open, each group of GM_STEPS_PER_CHECK Arnoldi steps
+// runs as one captured CUDA graph.
 template <class T>
 sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs, T* Xs, const GmWork<T>& Wk, Sys& S,
                      Gm& G, const int* cap, double* pt, double* pt2, int* fl, const Dims& D, cudaStream_t st)
@@ -1072,13 +1105,47 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
     const int32_t n = I.n;
     const int64_t ld = I.ld;
     const int ib = item_blocks(n > 0 ? n : 1, k);
-    const int check_every = 4;
     int hflag = 0;
     T* r = Wk.r;
     T* w = Wk.w;
     T* z = Wk.z;
+    // Graphs are captured and replayed on a library stream ordered after the
+    // caller's stream (the legacy default stream cannot be captured).
+    const bool use_graph = !sai_prof_on();
+    cudaStream_t caller = st;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    if (use_graph) {
+        cudaStream_t aux = sai_aux_stream();
+        if (aux) {
+            SAI_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+            SAI_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+            SAI_CUDA(cudaEventRecord(ev_in, caller));
+            SAI_CUDA(cudaStreamWaitEvent(aux, ev_in, 0));
+            st = aux;
+        }
+    }
+    cudaGraphExec_t gexec = nullptr;
+    if (use_graph && st != caller) {
+        cudaStreamCaptureStatus cs;
+        SAI_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            cudaGraph_t graph = nullptr;
+            SAI_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            for (int q = 0; q < GM_STEPS_PER_CHECK; ++q) arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, pt2, fl, D, st);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                gexec = nullptr;
+                (void)cudaGetLastError();
+            }
+            // the captured launches ran no kernel yet: count them at replay
+            sai_count_grid_add(-(long long)GM_STEPS_PER_CHECK * GM_LAUNCHES_PER_STEP);
+        }
+    }
     k_gm_init<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bs, Xs, r, S.lall, pt2);
     int first = 1;
+    sai_status status = SAI_OK;
     for (;;) {
         k_gm_cycle_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, I.nch, pt2, cap, S, G, first, fl);
         first = 0;
@@ -1086,27 +1153,24 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         SAI_CUDA(cudaStreamSynchronize(st));
         if (!hflag) break;
         k_gm_v0<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, S, G, Wk.B);
-        for (int j = 0; j < m; ++j) {
-            const T* vj = Wk.B.V + (size_t)j * Wk.B.vs;
-            {
-                ProfScope ps(D.site_spmm, st);
-                spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, vj, z, nullptr, G.ladv, st);
+        for (int j0 = 0; j0 < m; j0 += GM_STEPS_PER_CHECK) {
+            if (gexec) {
+                cudaError_t e = cudaGraphLaunch(gexec, st);
+                if (e != cudaSuccess) {
+                    status = SAI_CUDA_ERROR;
+                    break;
+                }
+                sai_count_grid_add((long long)GM_STEPS_PER_CHECK * GM_LAUNCHES_PER_STEP);
+            } else {
+                for (int q = 0; q < GM_STEPS_PER_CHECK; ++q)
+                    arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, pt2, fl, D, st);
             }
-            {
-                ProfScope ps(D.site_spmm, st);
-                spmv<T, 0>(n, ld, A.Ar, A.Ac, A.Av, k, z, w, nullptr, G.ladv, st);
-            }
-            cgs_pass<T>(I, k, j, 0, w, Wk.B, G, G.ladv, pt, pt2, D, st);
-            cgs_pass<T>(I, k, j, 1, w, Wk.B, G, G.lreo, pt, pt2, D, st);
-            k_gm_givens<<<SAI_GRID(1), CTRL, 0, st>>>(k, j, cap, S, G, D, fl);
-            k_gm_normalize<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, j, w, S, G, Wk.B);
             SAI_CUDA(cudaGetLastError());
-            if ((j + 1) % check_every == 0 || j + 1 == m) {
-                SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
-                SAI_CUDA(cudaStreamSynchronize(st));
-                if (!hflag) break;
-            }
+            SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            if (!hflag) break;
         }
+        if (status != SAI_OK) break;
         k_gm_trisolve<<<SAI_GRID(1), CTRL, 0, st>>>(k, S, G);
         k_gm_combine<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, w, G, Wk.B);
         spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, w, z, nullptr, G.lcyc, st);
@@ -1116,7 +1180,14 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         k_norm2<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, G.lcyc, pt2);
         SAI_CUDA(cudaGetLastError());
     }
-    return SAI_OK;
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (ev_in) {
+        cudaEventRecord(ev_out, st);
+        cudaStreamWaitEvent(caller, ev_out, 0);
+        cudaEventDestroy(ev_in);
+        cudaEventDestroy(ev_out);
+    }
+    return status;
 }
 
 // Carves the control state of GMRES(m) for k systems out of one double and
@@ -1127,9 +1198,9 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
     const size_t hsz = (size_t)k * (m + 1) * m + 2 * (size_t)k * m + (size_t)k * (m + 1) + 2 * (size_t)(m + 1) * k +
                        (size_t)k * m + 2 * (size_t)k;
     SAI_TRY(hb.alloc(sizeof(double) * hsz, st, true));
-    SAI_TRY(ib.alloc(sizeof(int) * (6 * k + 3 * (k + 1)), st, true));
+    SAI_TRY(ib.alloc(sizeof(int) * (6 * k + 3 * (k + 1) + 1), st, true));
     SAI_CUDA(cudaMemsetAsync(hb.p, 0, sizeof(double) * hsz, st));
-    SAI_CUDA(cudaMemsetAsync(ib.p, 0, sizeof(int) * (6 * k + 3 * (k + 1)), st));
+    SAI_CUDA(cudaMemsetAsync(ib.p, 0, sizeof(int) * (6 * k + 3 * (k + 1) + 1), st));
     double* hp = hb.as<double>();
     G.H = hp;
     hp += (size_t)k * (m + 1) * m;
@@ -1155,6 +1226,7 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
     G.lcyc = ip + 6 * k;
     G.ladv = G.lcyc + (k + 1);
     G.lreo = G.ladv + (k + 1);
+    G.jdev = G.lreo + (k + 1);
     return SAI_OK;
 }
 
@@ -1182,7 +1254,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
                           int32_t* status, cudaStream_t st)
 {
     if (!h || !P || !prm || !thr || !iters || !status || k < 1 || k > CTRL) return SAI_INVALID_ARG;
-    if (prm->maxit < 0 || (prm->method == SAI_GMRES && prm->restart < 1)) return SAI_INVALID_ARG;
+    if (prm->maxit < 0 || (prm->method == SAI_GMRES && (prm->restart < 1 || prm->restart >= GM_MAXM)))
+        return SAI_INVALID_ARG;
     if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES) return SAI_INVALID_ARG;
     if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     if (prm->precision == SAI_FP32_REFINE64 && prm->method != SAI_GMRES) return SAI_NOT_IMPLEMENTED;
@@ -1214,7 +1287,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     Buf sysd, sysi, part, part2, flag, Bs, Xs, capb;
     SAI_TRY(sysd.alloc(sizeof(double) * 7 * k, st, true));
     SAI_TRY(sysi.alloc(sizeof(int) * (5 * k + 3 * (k + 1)), st, true));
-    SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * (PJ + 1), st, true));
+    SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * (GM_MAXM + 2), st, true));
     SAI_TRY(part2.alloc(sizeof(double) * (size_t)k * I.nch * 2, st, true));
     SAI_TRY(flag.alloc(sizeof(int) * 4, st, true));
     SAI_TRY(Bs.alloc(sizeof(double) * blk + 8, st, true));
