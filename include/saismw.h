@@ -120,7 +120,11 @@ typedef struct {
     int32_t mn;        /* paper: 5, at most 8 here */
     int32_t max_aug;   /* paper: l_max = 20 loops, i.e. 19 augmentations */
     int32_t key_bits;
-    int32_t precision; /* sai_precision; only SAI_FP64 in this version */
+    int32_t precision; /* SAI_FP64, or SAI_FP32_REFINE64: Householder QR of the
+                          reduced problems in FP32, then per loop one FP64
+                          refinement step by the corrected semi-normal
+                          equations; residuals, stop tests and SPAI keys use
+                          the refined solution in FP64 */
 } sai_spai_params;
 
 /* PSAI(tol) (section 2.2). Loop l = 0..lmax: solve on S^(l), drop
@@ -133,7 +137,7 @@ typedef struct {
     double tol;
     int32_t tol_mode;
     int32_t lmax;      /* paper: 10 */
-    int32_t precision;
+    int32_t precision; /* as for SPAI; the drop test uses the refined solution */
 } sai_psai_params;
 
 typedef struct sai_precond_s* sai_precond;

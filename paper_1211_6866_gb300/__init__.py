@@ -245,18 +245,20 @@ def split(A, thresh_mult=10.0, abs_tau=-1.0, ge=False, p_keep=0):
     return Split(h.value)
 
 
-def build_spai(sp, delta=0.4, mn=5, max_aug=10, key_bits=20):
+def build_spai(sp, delta=0.4, mn=5, max_aug=10, key_bits=20, precision=0):
+    """precision 1: FP32 QR with one FP64 refinement step per loop."""
     L = load()
     h = C.c_void_p()
-    prm = _SpaiParams(delta, mn, max_aug, key_bits, 0)
+    prm = _SpaiParams(delta, mn, max_aug, key_bits, precision)
     _check("sai_build_spai", L.sai_build_spai(sp._h, C.byref(prm), _stream(), C.byref(h)))
     return Precond(h.value)
 
 
-def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10):
+def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10, precision=0):
+    """precision 1: FP32 QR with one FP64 refinement step per loop."""
     L = load()
     h = C.c_void_p()
-    prm = _PsaiParams(delta, tol, tol_mode, lmax, 0)
+    prm = _PsaiParams(delta, tol, tol_mode, lmax, precision)
     _check("sai_build_psai", L.sai_build_psai(sp._h, C.byref(prm), _stream(), C.byref(h)))
     return Precond(h.value)
 

@@ -75,16 +75,18 @@ struct Out {
 
 constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <int LCAP_, int SCAP_, int HL_, int HC_>
+template <int LCAP_, int SCAP_, int HL_, int HC_, class TQ_ = double>
 struct Tier {
+    using TQ = TQ_;  // scalar of the QR factors (double, or float for the refined form)
     static constexpr int LCAP = LCAP_, SCAP = SCAP_, HL = HL_, HC = HC_;
     static constexpr size_t OFF_Q = 0;
-    static constexpr size_t OFF_CV = OFF_Q + 8ull * LCAP * SCAP;
-    static constexpr size_t OFF_R = OFF_CV + 8ull * LCAP;
+    static constexpr size_t OFF_CV = OFF_Q + sizeof(TQ) * LCAP * SCAP;
+    static constexpr size_t OFF_R = a16(OFF_CV + sizeof(TQ) * LCAP);
     static constexpr size_t OFF_M = OFF_R + 8ull * LCAP;
-    static constexpr size_t OFF_BETA = OFF_M + 8ull * SCAP;
-    static constexpr size_t OFF_RD = OFF_BETA + 8ull * SCAP;
-    static constexpr size_t OFF_LROW = OFF_RD + 8ull * SCAP;
+    static constexpr size_t OFF_G = OFF_M + 8ull * SCAP;
+    static constexpr size_t OFF_BETA = OFF_G + 8ull * SCAP;
+    static constexpr size_t OFF_RD = OFF_BETA + sizeof(TQ) * SCAP;
+    static constexpr size_t OFF_LROW = a16(OFF_RD + sizeof(TQ) * SCAP);
     static constexpr size_t OFF_HK = OFF_LROW + 4ull * LCAP;
     static constexpr size_t OFF_HV = OFF_HK + 4ull * HL;
     static constexpr size_t OFF_S = OFF_HV + 4ull * HL;
@@ -98,26 +100,33 @@ struct Tier {
     static_assert(HC >= 2 * SCAP && (HC & (HC - 1)) == 0, "candidate hash");
 };
 
-using Tier0 = Tier<64, 16, 128, 512>;      // shared memory, ~13.6 KB per warp
+using Tier0 = Tier<64, 16, 128, 512>;      // shared memory, ~13.7 KB per warp
 using Tier1 = Tier<256, 64, 512, 2048>;    // global memory, ~150 KB per warp
 using Tier2 = Tier<1024, 128, 2048, 8192>; // global memory, ~1.1 MB per warp
+using Tier0F = Tier<64, 16, 128, 512, float>;
+using Tier1F = Tier<256, 64, 512, 2048, float>;
+using Tier2F = Tier<1024, 128, 2048, 8192, float>;
 
-struct Ws {
-    double *Q, *cv, *r, *m, *beta, *rd;
+template <class TQ>
+struct WsT {
+    TQ *Q, *cv, *beta, *rd;  // QR factors, Q^T e^, 2/(v^T v), diag(R)
+    double *r, *m, *g;       // FP64 residual, solution, refinement scratch
     int32_t *Lrow, *hk, *hv, *S, *a0, *a1, *ck;
     uint8_t *cf, *kp;
 };
 
 template <class T>
-__device__ __forceinline__ Ws bind_ws(char* b)
+__device__ __forceinline__ WsT<typename T::TQ> bind_ws(char* b)
 {
-    Ws w;
-    w.Q = (double*)(b + T::OFF_Q);
-    w.cv = (double*)(b + T::OFF_CV);
+    using TQ = typename T::TQ;
+    WsT<TQ> w;
+    w.Q = (TQ*)(b + T::OFF_Q);
+    w.cv = (TQ*)(b + T::OFF_CV);
     w.r = (double*)(b + T::OFF_R);
     w.m = (double*)(b + T::OFF_M);
-    w.beta = (double*)(b + T::OFF_BETA);
-    w.rd = (double*)(b + T::OFF_RD);
+    w.g = (double*)(b + T::OFF_G);
+    w.beta = (TQ*)(b + T::OFF_BETA);
+    w.rd = (TQ*)(b + T::OFF_RD);
     w.Lrow = (int32_t*)(b + T::OFF_LROW);
     w.hk = (int32_t*)(b + T::OFF_HK);
     w.hv = (int32_t*)(b + T::OFF_HV);
@@ -193,7 +202,7 @@ __device__ __forceinline__ int hslot(const int32_t* hk, int32_t key)
 // Adds the rows of column j of A~ to L. New rows get consecutive positions in
 // entry order, so L's order does not depend on scheduling. False on overflow.
 template <class T>
-__device__ bool add_rows(const Ws& w, const SaiMat& A, int32_t j, int& nL)
+__device__ bool add_rows(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t j, int& nL)
 {
     const int lane = lane_id();
     const int64_t b = A.cp[j], e = A.cp[j + 1];
@@ -223,7 +232,7 @@ __device__ bool add_rows(const Ws& w, const SaiMat& A, int32_t j, int& nL)
 
 // Resets the per-column state to S = {k}, L = {k}, cv = e^.
 template <class T>
-__device__ void col_init(const Ws& w, int32_t k, int& nL, int& nS, int& nfact)
+__device__ void col_init(const WsT<typename T::TQ>& w, int32_t k, int& nL, int& nS, int& nfact)
 {
     const int lane = lane_id();
     for (int q = lane; q < T::HL; q += 32) w.hk[q] = -1;
@@ -233,7 +242,7 @@ __device__ void col_init(const Ws& w, int32_t k, int& nL, int& nS, int& nfact)
         int sl = hinsert<T::HL>(w.hk, k, ins);
         w.hv[sl] = 0;
         w.Lrow[0] = k;
-        w.cv[0] = 1.0;
+        w.cv[0] = 1;
     }
     __syncwarp();
     nL = 1;
@@ -244,53 +253,54 @@ __device__ void col_init(const Ws& w, int32_t k, int& nL, int& nS, int& nfact)
 // Gathers the new columns S[nfact..nS), updates the QR factorisation and
 // solves R m = (Q^T e^)(0:nS). Returns ST_DONE, ST_OVERFLOW or ST_SINGULAR.
 template <class T>
-__device__ int ls_update(const Ws& w, const SaiMat& A, int& nL, int nS, int& nfact)
+__device__ int ls_update(const WsT<typename T::TQ>& w, const SaiMat& A, int& nL, int nS, int& nfact)
 {
+    using TQ = typename T::TQ;
     const int lane = lane_id();
     const int nL_old = nL;
     for (int t = nfact; t < nS; ++t)
         if (!add_rows<T>(w, A, w.S[t], nL)) return ST_OVERFLOW;
     // zero the new rows of the old columns and of cv, and the new columns
     for (int t = 0; t < nS; ++t) {
-        double* col = w.Q + (size_t)t * T::LCAP;
-        for (int i = (t < nfact ? nL_old : 0) + lane; i < nL; i += 32) col[i] = 0.0;
+        TQ* col = w.Q + (size_t)t * T::LCAP;
+        for (int i = (t < nfact ? nL_old : 0) + lane; i < nL; i += 32) col[i] = 0;
     }
-    for (int i = nL_old + lane; i < nL; i += 32) w.cv[i] = 0.0;
+    for (int i = nL_old + lane; i < nL; i += 32) w.cv[i] = 0;
     __syncwarp();
     for (int t = nfact; t < nS; ++t) {
         const int32_t j = w.S[t];
-        double* col = w.Q + (size_t)t * T::LCAP;
+        TQ* col = w.Q + (size_t)t * T::LCAP;
         for (int64_t q = A.cp[j] + lane; q < A.cp[j + 1]; q += 32) {
             const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
-            if (pos >= 0) col[pos] = A.cv[q];
+            if (pos >= 0) col[pos] = (TQ)A.cv[q];
         }
     }
     __syncwarp();
     // old reflectors on the new columns
     for (int jr = 0; jr < nfact; ++jr) {
-        const double* v = w.Q + (size_t)jr * T::LCAP;
-        const double bj = w.beta[jr];
+        const TQ* v = w.Q + (size_t)jr * T::LCAP;
+        const TQ bj = w.beta[jr];
         for (int t = nfact; t < nS; ++t) {
-            double* col = w.Q + (size_t)t * T::LCAP;
-            double d = 0.0;
+            TQ* col = w.Q + (size_t)t * T::LCAP;
+            TQ d = 0;
             for (int i = jr + lane; i < nL; i += 32) d = fma(v[i], col[i], d);
-            d = warp_sum(d);
-            const double f = bj * d;
+            d = warp_sum_t(d);
+            const TQ f = bj * d;
             for (int i = jr + lane; i < nL; i += 32) col[i] = fma(-f, v[i], col[i]);
             __syncwarp();
         }
     }
     // factor the trailing block column by column
     for (int t = nfact; t < nS; ++t) {
-        double* col = w.Q + (size_t)t * T::LCAP;
-        double s2 = 0.0;
+        TQ* col = w.Q + (size_t)t * T::LCAP;
+        TQ s2 = 0;
         for (int i = t + lane; i < nL; i += 32) s2 = fma(col[i], col[i], s2);
-        s2 = warp_sum(s2);
-        if (!(s2 > 0.0)) return ST_SINGULAR;
-        const double nrm = sqrt(s2);
-        const double x0 = col[t];
-        const double alpha = x0 >= 0.0 ? -nrm : nrm;
-        const double bt = 1.0 / (nrm * (nrm + fabs(x0)));  // 2/(v^T v), v^T v = 2 nrm (nrm + |x0|)
+        s2 = warp_sum_t(s2);
+        if (!(s2 > (TQ)0)) return ST_SINGULAR;
+        const TQ nrm = sqrt(s2);
+        const TQ x0 = col[t];
+        const TQ alpha = x0 >= (TQ)0 ? -nrm : nrm;
+        const TQ bt = (TQ)1 / (nrm * (nrm + fabs(x0)));  // 2/(v^T v), v^T v = 2 nrm (nrm + |x0|)
         __syncwarp();
         if (lane == 0) {
             col[t] = x0 - alpha;
@@ -299,25 +309,25 @@ __device__ int ls_update(const Ws& w, const SaiMat& A, int& nL, int nS, int& nfa
         }
         __syncwarp();
         for (int t2 = t + 1; t2 <= nS; ++t2) {
-            double* c2 = t2 < nS ? w.Q + (size_t)t2 * T::LCAP : w.cv;
-            double d = 0.0;
+            TQ* c2 = t2 < nS ? w.Q + (size_t)t2 * T::LCAP : w.cv;
+            TQ d = 0;
             for (int i = t + lane; i < nL; i += 32) d = fma(col[i], c2[i], d);
-            d = warp_sum(d);
-            const double f = bt * d;
+            d = warp_sum_t(d);
+            const TQ f = bt * d;
             for (int i = t + lane; i < nL; i += 32) c2[i] = fma(-f, col[i], c2[i]);
             __syncwarp();
         }
     }
     nfact = nS;
-    // back substitution
-    for (int i = lane; i < nS; i += 32) w.m[i] = w.cv[i];
+    // back substitution (FP64 arithmetic on the stored factors)
+    for (int i = lane; i < nS; i += 32) w.m[i] = (double)w.cv[i];
     __syncwarp();
     for (int t = nS - 1; t >= 0; --t) {
-        const double mt = w.m[t] / w.rd[t];
+        const double mt = w.m[t] / (double)w.rd[t];
         __syncwarp();
         if (lane == 0) w.m[t] = mt;
-        const double* col = w.Q + (size_t)t * T::LCAP;
-        for (int i = lane; i < t; i += 32) w.m[i] = fma(-col[i], mt, w.m[i]);
+        const TQ* col = w.Q + (size_t)t * T::LCAP;
+        for (int i = lane; i < t; i += 32) w.m[i] = fma(-(double)col[i], mt, w.m[i]);
         __syncwarp();
     }
     return ST_DONE;
@@ -326,7 +336,7 @@ __device__ int ls_update(const Ws& w, const SaiMat& A, int& nL, int nS, int& nfa
 // r = A~(L,S) m - e^ on L (only the columns with use[t] != 0 when use given);
 // returns ||r||^2.
 template <class T>
-__device__ double residual(const Ws& w, const SaiMat& A, int nL, int nS, const uint8_t* use)
+__device__ double residual(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, int nS, const uint8_t* use)
 {
     const int lane = lane_id();
     for (int i = lane; i < nL; i += 32) w.r[i] = (i == 0) ? -1.0 : 0.0;
@@ -346,8 +356,46 @@ __device__ double residual(const Ws& w, const SaiMat& A, int nL, int nS, const u
     return warp_sum(s);
 }
 
+// One FP64 refinement step of the LS solution by the corrected semi-normal
+// equations: m += R^{-1} R^{-T} A^^T (e^ - A^ m), with the residual and
+// A^^T r formed in FP64 from the FP64 values of A~ and R from the (FP32) QR.
 template <class T>
-__device__ int spai_column(const Ws& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out, int& l_out,
+__device__ void refine(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, int nS)
+{
+    const int lane = lane_id();
+    residual<T>(w, A, nL, nS, nullptr);  // r = A^ m - e^
+    for (int t = lane; t < nS; t += 32) {
+        const int32_t j = w.S[t];
+        double g = 0.0;
+        for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+            const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
+            if (pos >= 0) g = fma(-A.cv[q], w.r[pos], g);
+        }
+        w.g[t] = g;  // A^^T (e^ - A^ m)
+    }
+    __syncwarp();
+    // R^T y = g (forward), R(t,i) = Q[i][t] for i > t
+    for (int t = 0; t < nS; ++t) {
+        const double yt = w.g[t] / (double)w.rd[t];
+        __syncwarp();
+        if (lane == 0) w.g[t] = yt;
+        for (int i = t + 1 + lane; i < nS; i += 32) w.g[i] = fma(-(double)w.Q[(size_t)i * T::LCAP + t], yt, w.g[i]);
+        __syncwarp();
+    }
+    // R d = y (backward)
+    for (int t = nS - 1; t >= 0; --t) {
+        const double dt = w.g[t] / (double)w.rd[t];
+        __syncwarp();
+        if (lane == 0) w.g[t] = dt;
+        for (int i = lane; i < t; i += 32) w.g[i] = fma(-(double)w.Q[(size_t)t * T::LCAP + i], dt, w.g[i]);
+        __syncwarp();
+    }
+    for (int t = lane; t < nS; t += 32) w.m[t] += w.g[t];
+    __syncwarp();
+}
+
+template <class T>
+__device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out, int& l_out,
                            double& rn_out, int& nL_out)
 {
     const int lane = lane_id();
@@ -360,6 +408,7 @@ __device__ int spai_column(const Ws& w, const SaiMat& A, int32_t k, const SpaiAr
     for (;;) {
         int st = ls_update<T>(w, A, nL, nS, nfact);
         if (st != ST_DONE) return st;
+        if (sizeof(typename T::TQ) < sizeof(double)) refine<T>(w, A, nL, nS);
         const double rn2 = residual<T>(w, A, nL, nS, nullptr);
         rn = sqrt(rn2);
         if (rn <= a.delta || l >= a.max_aug) break;
@@ -442,7 +491,7 @@ __device__ int spai_column(const Ws& w, const SaiMat& A, int32_t k, const SpaiAr
 
 // PSAI(tol), reading (A): S^(l+1) = P(a^(l+1)) u S_kept^(l), a^(l+1) = |A~| a^(l).
 template <class T>
-__device__ int psai_column(const Ws& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out, int& l_out,
+__device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out, int& l_out,
                            double& rn_pre, double& rn_post, int& nL_out)
 {
     const int lane = lane_id();
@@ -460,6 +509,7 @@ __device__ int psai_column(const Ws& w, const SaiMat& A, int32_t k, const PsaiAr
     for (;;) {
         int st = ls_update<T>(w, A, nL, nS, nfact);
         if (st != ST_DONE) return st;
+        if (sizeof(typename T::TQ) < sizeof(double)) refine<T>(w, A, nL, nS);
         const double rn = sqrt(residual<T>(w, A, nL, nS, nullptr));
         double tolk = a.tol;
         if (a.tol_mode == 0) {
@@ -585,7 +635,7 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
     const int wib = threadIdx.x >> 5;
     char* base = SMEM ? smem + (size_t)wib * T::BYTES
                       : gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * T::BYTES;
-    const Ws w = bind_ws<T>(base);
+    const WsT<typename T::TQ> w = bind_ws<T>(base);
     double work_bytes = 0.0;
     for (;;) {
         int item = 0;
@@ -711,7 +761,22 @@ sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, 
     return SAI_OK;
 }
 
-template <bool PSAI>
+template <class TQ>
+struct Tiers;
+template <>
+struct Tiers<double> {
+    using T0 = Tier0;
+    using T1 = Tier1;
+    using T2 = Tier2;
+};
+template <>
+struct Tiers<float> {
+    using T0 = Tier0F;
+    using T1 = Tier1F;
+    using T2 = Tier2F;
+};
+
+template <bool PSAI, class TQ>
 sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs& pa, int32_t smax, double delta,
                         cudaStream_t st, bool async, sai_precond_s* P)
 {
@@ -762,18 +827,21 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     out.res_post = PSAI ? P->res_post.as<double>() : nullptr;
     out.tier = tier.as<int32_t>();
 
-    SAI_TRY((launch_tier<Tier0, true, PSAI>(A, sa, pa, nullptr, n, c + 0, out, ovf0.as<int32_t>(), c + 1, c + 3, 0,
+    using T0 = typename Tiers<TQ>::T0;
+    using T1 = typename Tiers<TQ>::T1;
+    using T2 = typename Tiers<TQ>::T2;
+    SAI_TRY((launch_tier<T0, true, PSAI>(A, sa, pa, nullptr, n, c + 0, out, ovf0.as<int32_t>(), c + 1, c + 3, 0,
                                             st)));
     int hc[4];
     SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));
     if (hc[1] > 0) {
-        SAI_TRY((launch_tier<Tier1, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), hc[1], c + 0, out, ovf1.as<int32_t>(),
+        SAI_TRY((launch_tier<T1, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), hc[1], c + 0, out, ovf1.as<int32_t>(),
                                                  c + 2, c + 3, 1, st)));
         SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
         SAI_CUDA(cudaStreamSynchronize(st));
         if (hc[2] > 0)
-            SAI_TRY((launch_tier<Tier2, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out, nullptr,
+            SAI_TRY((launch_tier<T2, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out, nullptr,
                                                      nullptr, c + 3, 2, st)));
     }
     // assemble M (CSC, rows ascending) and its CSR copy
@@ -824,7 +892,7 @@ sai_status sai_spai_build(const sai_split_s* h, const sai_spai_params* prm, cuda
     if (prm->mn < 1 || prm->mn > MNMAX || prm->max_aug < 0 || prm->key_bits < 1 || prm->key_bits > 31 ||
         !(prm->delta >= 0.0))
         return SAI_INVALID_ARG;
-    if (prm->precision != SAI_FP64) return SAI_NOT_IMPLEMENTED;
+    if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     SpaiArgs sa;
     sa.delta = prm->delta;
     sa.scale = ldexp(1.0, prm->key_bits);
@@ -833,7 +901,8 @@ sai_status sai_spai_build(const sai_split_s* h, const sai_spai_params* prm, cuda
     PsaiArgs pa = {};
     long long bound = 1 + (long long)prm->mn * prm->max_aug;
     int32_t smax = (int32_t)(bound < Tier2::SCAP ? bound : Tier2::SCAP);
-    return build_common<false>(h, sa, pa, smax, prm->delta, st, async, P);
+    if (prm->precision == SAI_FP32_REFINE64) return build_common<false, float>(h, sa, pa, smax, prm->delta, st, async, P);
+    return build_common<false, double>(h, sa, pa, smax, prm->delta, st, async, P);
 }
 
 sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cudaStream_t st, bool async,
@@ -842,14 +911,16 @@ sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cuda
     if (!h || !prm || !P) return SAI_INVALID_ARG;
     if (prm->lmax < 0 || (prm->tol_mode != 0 && prm->tol_mode != 1) || !(prm->delta >= 0.0) || !(prm->tol >= 0.0))
         return SAI_INVALID_ARG;
-    if (prm->precision != SAI_FP64) return SAI_NOT_IMPLEMENTED;
+    if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     SpaiArgs sa = {};
     PsaiArgs pa;
     pa.delta = prm->delta;
     pa.tol = prm->tol;
     pa.tol_mode = prm->tol_mode;
     pa.lmax = prm->lmax;
-    return build_common<true>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
+    if (prm->precision == SAI_FP32_REFINE64)
+        return build_common<true, float>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
+    return build_common<true, double>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
 }
 
 sai_status sai_build_work_reset()
