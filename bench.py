@@ -41,7 +41,7 @@ UNIT = "columns/s"
 SPAI_KW = dict(sai="spai", delta=0.3, mn=5, max_aug=10)
 PSAI_KW = dict(sai="psai", delta=0.3, tol=1e-3, tol_mode=1, lmax=10)
 KRYLOV_KW = dict(krylov="gmres", restart=50, eps=1e-10, maxit=500)
-OPT_KW = dict(krylov_precision=1)    # FP32 inner GMRES refined in FP64
+OPT_KW = dict(krylov_precision=1, sai_precision=1)  # FP32 QR + FP64 refinement; FP32 inner GMRES refined in FP64
 PLAIN_KW = dict(krylov_precision=0)  # plain FP64 GPU form
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_convdiff3d_m64_s10.json")
 
@@ -335,7 +335,8 @@ def run_ours(args):
         "iters": {k: r[1] for k, r in zip(("spai", "psai"), last)},
         "rr": {k: r[2]["rr"] for k, r in zip(("spai", "psai"), last)},
         "nnz_M": {k: r[2]["nnz_M"] for k, r in zip(("spai", "psai"), last)},
-        "form": "SAI build FP64; s+1 GMRES(50) solves with FP32 inner iterations refined in FP64 (FP64 residual "
+        "form": "SAI build with FP32 Householder QR and one FP64 refinement step per loop (FP64 residuals, stop "
+                "tests and SPAI keys); s+1 GMRES(50) solves with FP32 inner iterations refined in FP64 (FP64 residual "
                 "b - A~x, correction and every stop test); SMW and rr FP64",
         "plain_fp64": {"ms_per_step": ms_plain, "value": ws * 2 * n / (ms_plain / 1e3),
                        "iters": {k: r[1] for k, r in zip(("spai", "psai"), reps_plain[-1])},

@@ -28,6 +28,7 @@ namespace {
 
 constexpr int CTRL = 256;      // threads of the single-block control kernels (>= k)
 constexpr int CHUNK = 1024;    // rows per (system, chunk) reduction item (one warp)
+constexpr int CHUNK_U = 256;   // rows per item of the GMRES update (no per-vector reduction)
 constexpr int TILE = 256;      // rows per SpMV item (one block)
 constexpr int PJ = 16;         // basis vectors per register-tiled projection pass
 constexpr int IT_WARPS = 4;    // warps per block of the item kernels (small blocks: finer occupancy)
@@ -35,6 +36,8 @@ constexpr int IT_WARPS = 4;    // warps per block of the item kernels (small blo
 enum { ST_OK = 0, ST_MAXITER = 5, ST_BREAKDOWN = 6 };  // same values as sai_status
 
 int g_sms = 0;
+// resident blocks per SM of the projection / update kernels, [0] double, [1] float
+int g_res_proj[2] = {1, 1}, g_res_upd[2] = {1, 1};
 
 // ---------------------------------------------------------------- accounting
 __device__ double d_kwork[PROF_NSITES * 2];
@@ -100,20 +103,38 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
                                                const T* __restrict__ B, const int* __restrict__ list,
                                                const int* __restrict__ xidx, int64_t xstride)
 {
+    constexpr int CT = 4;  // systems per thread: each matrix entry is loaded once for CT gathers
     const int cnt = list[0];
     if (xidx) X += (int64_t)(*xidx) * xstride;  // X = block number *xidx of a basis
+    const int groups = (cnt + CT - 1) / CT;
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
-    for (int64_t it = blockIdx.x; it < tiles * cnt; it += gridDim.x) {
-        const int64_t tile = it / cnt;
-        const int c = list[1 + (int)(it - tile * cnt)];
+    for (int64_t it = blockIdx.x; it < tiles * groups; it += gridDim.x) {
+        const int64_t tile = it / groups;
+        const int g0 = (int)(it - tile * groups) * CT;
+        const int ng = min(CT, cnt - g0);
         const int64_t row = tile * TILE + threadIdx.x;
         if (row >= n) continue;
-        const T* xc = X + (int64_t)c * ld;
-        T acc = 0;
+        int64_t off[CT];
+#pragma unroll
+        for (int t = 0; t < CT; ++t) off[t] = t < ng ? (int64_t)list[1 + g0 + t] * ld : 0;
+        T acc[CT];
+#pragma unroll
+        for (int t = 0; t < CT; ++t) acc[t] = 0;
         const int64_t b = rp[row], e = rp[row + 1];
-        for (int64_t t = b; t < e; ++t) acc = fma(v[t], xc[ci[t]], acc);
-        if (MODE == 0) Y[(int64_t)c * ld + row] = acc;
-        else Y[(int64_t)c * ld + row] = B[(int64_t)c * ld + row] - acc;
+        for (int64_t q = b; q < e; ++q) {
+            const T a = v[q];
+            const int32_t col = ci[q];
+#pragma unroll
+            for (int t = 0; t < CT; ++t)
+                if (t < ng) acc[t] = fma(a, X[off[t] + col], acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < CT; ++t) {
+            if (t < ng) {
+                if (MODE == 0) Y[off[t] + row] = acc[t];
+                else Y[off[t] + row] = B[off[t] + row] - acc[t];
+            }
+        }
     }
 }
 
@@ -122,7 +143,7 @@ void spmv(int32_t n, int64_t ld, const int64_t* rp, const int32_t* ci, const T* 
           const T* B, const int* list, cudaStream_t st, const int* xidx = nullptr, int64_t xstride = 0)
 {
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
-    int64_t g = tiles * k;
+    int64_t g = tiles * ((k + 3) / 4);
     const int64_t cap = (int64_t)g_sms * 8;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
@@ -141,7 +162,8 @@ struct Ops {  // A~ and M in CSR with values of type T
 struct Items {
     int32_t n;
     int64_t ld;
-    int nch;  // chunks per system
+    int nch;   // CHUNK-row chunks per system
+    int nchu;  // CHUNK_U-row chunks per system (GMRES update)
 };
 
 __host__ __device__ __forceinline__ int nchunks(int64_t n) { return (int)((n + CHUNK - 1) / CHUNK); }
@@ -658,40 +680,50 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_gm_proj(Items I, int k, const
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
     const int j = *jdev;
-    FOR_ITEMS(I, list, c, r0, r1)
-    {
+    const int ng = j / PJ + 1;  // groups of PJ basis vectors
+    const int cnt = list[0];
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // items: (chunk q, system, basis group g), g fastest so that the items of
+    // one (system, chunk) read their chunk of w from cache
+    for (int64_t it = w0; it < (int64_t)cnt * I.nch * ng; it += nw) {
+        const int g = (int)(it % ng);
+        const int64_t rest = it / ng;
+        const int c = list[1 + (int)(rest % cnt)];
+        const int q = (int)(rest / cnt);
+        const int i0 = g * PJ;
+        const int ni = min(PJ, j + 1 - i0);
+        const int64_t r0 = (int64_t)q * CHUNK, r1 = min((int64_t)I.n, r0 + CHUNK);
         const int64_t o = (int64_t)c * I.ld;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
-        double* pp = part + ((size_t)c * I.nch + q_) * (GM_MAXM + 2);
-        for (int i0 = 0; i0 <= j; i0 += PJ) {
-            const int ni = min(PJ, j + 1 - i0);
-            const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
-            T acc[PJ];
+        const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
+        T acc[PJ];
 #pragma unroll
-            for (int i = 0; i < PJ; ++i) acc[i] = 0;
-            T aw = 0;
-            for (int64_t row = r0 + (int64_t)lane_ * VW; row < r1v; row += 32 * VW) {
-                const VT wv = *reinterpret_cast<const VT*>(w + o + row);
-                VT vv[PJ];
+        for (int i = 0; i < PJ; ++i) acc[i] = 0;
+        T aw = 0;
+        for (int64_t row = r0 + (int64_t)lane * VW; row < r1v; row += 32 * VW) {
+            const VT wv = *reinterpret_cast<const VT*>(w + o + row);
+            VT vv[PJ];
 #pragma unroll
-                for (int i = 0; i < PJ; ++i)
-                    if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
+            for (int i = 0; i < PJ; ++i)
+                if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
 #pragma unroll
-                for (int i = 0; i < PJ; ++i)
-                    if (i < ni) acc[i] += Vec<T>::dot(vv[i], wv);
-                if (i0 == 0) aw += Vec<T>::dot(wv, wv);
-            }
+            for (int i = 0; i < PJ; ++i)
+                if (i < ni) acc[i] += Vec<T>::dot(vv[i], wv);
+            if (g == 0) aw += Vec<T>::dot(wv, wv);
+        }
 #pragma unroll
-            for (int i = 0; i < PJ; ++i) acc[i] = warp_sum_t(acc[i]);
-            if (lane_ == 0) {
+        for (int i = 0; i < PJ; ++i) acc[i] = warp_sum_t(acc[i]);
+        double* pp = part + ((size_t)c * I.nch + q) * (GM_MAXM + 2);
+        if (lane == 0) {
 #pragma unroll
-                for (int i = 0; i < PJ; ++i)
-                    if (i < ni) pp[i0 + i] = (double)acc[i];
-            }
-            if (i0 == 0) {
-                aw = warp_sum_t(aw);
-                if (lane_ == 0) pp[GM_MAXM + 1] = (double)aw;
-            }
+            for (int i = 0; i < PJ; ++i)
+                if (i < ni) pp[i0 + i] = (double)acc[i];
+        }
+        if (g == 0) {
+            aw = warp_sum_t(aw);
+            if (lane == 0) pp[GM_MAXM + 1] = (double)aw;
         }
     }
 }
@@ -730,15 +762,20 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, T* __r
     constexpr int VW = Vec<T>::W;
     __shared__ T hs[IT_WARPS][GM_MAXM];
     const int j = *jdev;
-    const int wid = threadIdx.x >> 5;
-    FOR_ITEMS(I, list, c, r0, r1)
-    {
-        for (int i = lane_; i <= j; i += 32) hs[wid][i] = (T)(-h[(size_t)i * k + c]);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cnt = list[0];
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = w0; it < (int64_t)cnt * I.nchu; it += nw) {
+        const int c = list[1 + (int)(it % cnt)];
+        const int q = (int)(it / cnt);
+        for (int i = lane; i <= j; i += 32) hs[wid][i] = (T)(-h[(size_t)i * k + c]);
         __syncwarp();
+        const int64_t r0 = (int64_t)q * CHUNK_U, r1 = min((int64_t)I.n, r0 + CHUNK_U);
         const int64_t o = (int64_t)c * I.ld;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
         T acc = 0;
-        for (int64_t row = r0 + (int64_t)lane_ * VW; row < r1v; row += 32 * VW) {
+        for (int64_t row = r0 + (int64_t)lane * VW; row < r1v; row += 32 * VW) {
             VT wv = *reinterpret_cast<const VT*>(w + o + row);
             for (int i0 = 0; i0 <= j; i0 += PJ) {
                 const int ni = min(PJ, j + 1 - i0);
@@ -755,7 +792,7 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, T* __r
             acc += Vec<T>::dot(wv, wv);
         }
         acc = warp_sum_t(acc);
-        if (lane_ == 0) part[(size_t)c * I.nch + q_] = (double)acc;
+        if (lane == 0) part[(size_t)c * I.nchu + q] = (double)acc;
         __syncwarp();
     }
 }
@@ -1047,19 +1084,25 @@ void cgs_pass(const Items& I, int k, int pass, T* w, const Basis<T>& B, const Gm
               double* part2, const Dims& D, cudaStream_t st)
 {
     double* h = G.h + (size_t)pass * (G.m + 1) * k;
-    const int ib = item_blocks(I.n, k);
+    // one wave of resident blocks: the grid-stride item loops then end together
+    const int fp = sizeof(T) == 4;
+    const int64_t pcap = (int64_t)g_sms * g_res_proj[fp], ucap = (int64_t)g_sms * g_res_upd[fp];
+    int64_t pb = ((int64_t)I.nch * k * ((G.m - 1) / PJ + 1) + IT_WARPS - 1) / IT_WARPS;
+    int64_t ub = ((int64_t)I.nchu * k + IT_WARPS - 1) / IT_WARPS;
+    pb = pb < pcap ? pb : pcap;
+    ub = ub < ucap ? ub : ucap;
     {
         ProfScope ps(D.site_dots, st);
-        k_gm_proj<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, w, B, list, G.jdev, part);
+        k_gm_proj<T><<<SAI_GRID(pb), IT_WARPS * 32, 0, st>>>(I, k, w, B, list, G.jdev, part);
     }
     const int64_t warps = (int64_t)k * (G.m + 2);
     k_gm_fin<<<SAI_GRID(sai_div_up(warps * 32, 256)), 256, 0, st>>>(k, I.nch, part, list, G.jdev, h,
                                                                    pass == 0 ? G.ww : nullptr);
     {
         ProfScope ps(D.site_upd, st);
-        k_gm_upd<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, w, B, h, list, G.jdev, part2);
+        k_gm_upd<T><<<SAI_GRID(ub), IT_WARPS * 32, 0, st>>>(I, k, w, B, h, list, G.jdev, part2);
     }
-    k_gm_finnorm<<<SAI_GRID(1), 1024, 0, st>>>(k, I.nch, part2, G, pass);
+    k_gm_finnorm<<<SAI_GRID(1), 1024, 0, st>>>(k, I.nchu, part2, G, pass);
 }
 
 template <class T>
@@ -1233,14 +1276,18 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
 template <class T>
 sai_status gm_work_alloc(size_t blk, int64_t n, int64_t ld, int m, Buf& vb, Buf& wb, GmWork<T>& Wk, cudaStream_t st)
 {
-    SAI_TRY(vb.alloc(sizeof(T) * blk * (m + 1) + 16, st, true));
+    // basis blocks are vs = blk + 96 values apart (keeps the blocks off a
+    // common power-of-two stride); the whole basis starts zeroed so the
+    // padding rows [n, ld) of every vector stay zero
+    const int64_t vs = (int64_t)blk + 96;
+    SAI_TRY(vb.alloc(sizeof(T) * (size_t)vs * (m + 1) + 16, st, true));
     SAI_TRY(wb.alloc(sizeof(T) * blk * 3 + 16, st, true));
     SAI_CUDA(cudaMemsetAsync(wb.p, 0, sizeof(T) * blk * 3, st));
-    // the padding rows [n, ld) of every basis vector stay zero
-    if (ld > n)
-        SAI_CUDA(cudaMemset2DAsync(vb.as<T>() + n, sizeof(T) * ld, 0, sizeof(T) * (ld - n), blk / ld * (m + 1), st));
+    SAI_CUDA(cudaMemsetAsync(vb.p, 0, sizeof(T) * (size_t)vs * (m + 1), st));
+    (void)n;
+    (void)ld;
     Wk.B.V = vb.as<T>();
-    Wk.B.vs = (int64_t)blk;
+    Wk.B.vs = vs;
     Wk.r = wb.as<T>();
     Wk.w = Wk.r + blk;
     Wk.z = Wk.w + blk;
@@ -1265,13 +1312,24 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         int dev = 0;
         SAI_CUDA(cudaGetDevice(&dev));
         SAI_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_proj[0], k_gm_proj<double>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_proj[1], k_gm_proj<float>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[0], k_gm_upd<double>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[1], k_gm_upd<float>, IT_WARPS * 32, 0));
+        for (int i = 0; i < 2; ++i) {
+            if (g_res_proj[i] < 1) g_res_proj[i] = 1;
+            if (g_res_upd[i] < 1) g_res_upd[i] = 1;
+        }
     }
-    const int64_t ld = ((int64_t)n + 31) / 32 * 32;
+    // leading dimension: n rounded up to 32, plus 32 so that the k system
+    // vectors of a block do not all start on the same large power of two
+    const int64_t ld = ((int64_t)n + 31) / 32 * 32 + 32;
     const size_t blk = (size_t)ld * k;  // one system-major block of k vectors
     Items I;
     I.n = n;
     I.ld = ld;
     I.nch = nchunks(n > 0 ? n : 1);
+    I.nchu = (int)(((int64_t)(n > 0 ? n : 1) + CHUNK_U - 1) / CHUNK_U);
     const int ib = item_blocks(n > 0 ? n : 1, k);
     Ops<double> A64;
     A64.Ar = h->Atr_rp.as<int64_t>();
@@ -1288,7 +1346,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     SAI_TRY(sysd.alloc(sizeof(double) * 7 * k, st, true));
     SAI_TRY(sysi.alloc(sizeof(int) * (5 * k + 3 * (k + 1)), st, true));
     SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * (GM_MAXM + 2), st, true));
-    SAI_TRY(part2.alloc(sizeof(double) * (size_t)k * I.nch * 2, st, true));
+    SAI_TRY(part2.alloc(sizeof(double) * (size_t)k * (I.nchu > 2 * I.nch ? I.nchu : 2 * I.nch), st, true));
     SAI_TRY(flag.alloc(sizeof(int) * 4, st, true));
     SAI_TRY(Bs.alloc(sizeof(double) * blk + 8, st, true));
     SAI_TRY(Xs.alloc(sizeof(double) * blk + 8, st, true));
