@@ -8,7 +8,8 @@
 //
 // Work distribution: device-side lists of the systems that take part in a
 // step (list[0] = count, list[1..] = system indices, ascending) are rebuilt
-// by the single-block control kernels; data-parallel kernels loop over the
+// by the control kernels (single-block, or one block per system with the
+// last block to arrive rebuilding the list); data-parallel kernels loop over the
 // items (system in the list) x (row tile or row chunk), so converged systems
 // cost nothing and the host never needs to know which systems are active.
 // Inner products are formed per (system, row chunk) by one warp and summed
@@ -16,10 +17,11 @@
 //
 // BiCGStab: van der Vorst's recurrence on A~ M z = b with y = M z updated
 // directly; stop tests after the half step (s) and the full step (r).
-// GMRES(m): Arnoldi with classical Gram-Schmidt, re-applied for a system
-// only when its norm falls below 1/sqrt(2) of the pre-projection norm (the
-// Daniel-Gragg-Kaufman-Stewart criterion); Givens rotations; stop on the
-// rotated residual |g_{j+1}|; restart from the true residual b - A~ y.
+// GMRES(m): Arnoldi with classical Gram-Schmidt applied twice, the second
+// pass delayed by one step and fused with the next step's reduction (one
+// reduction and one update pass over the basis per step); Givens rotations;
+// stop on the rotated residual |g_{j+1}|; restart from the true residual
+// b - A~ y.
 #include <math.h>
 
 #include "internal.h"
@@ -36,8 +38,8 @@ constexpr int IT_WARPS = 4;    // warps per block of the item kernels (small blo
 enum { ST_OK = 0, ST_MAXITER = 5, ST_BREAKDOWN = 6 };  // same values as sai_status
 
 int g_sms = 0;
-// resident blocks per SM of the projection / update kernels, [0] double, [1] float
-int g_res_proj[2] = {1, 1}, g_res_upd[2] = {1, 1};
+// resident blocks per SM of the GMRES dot / update kernels, [0] double, [1] float
+int g_res_dots[2] = {1, 1}, g_res_upd[2] = {1, 1};
 
 // ---------------------------------------------------------------- accounting
 __device__ double d_kwork[PROF_NSITES * 2];
@@ -92,7 +94,7 @@ __global__ void k_from_soa(int64_t n, int k, int64_t ld, const double* __restric
 }
 
 // ---------------------------------------------------------------- SpMV over a list
-// Y[c] = A X[c] (mode 0) or B[c] - A X[c] (mode 1) for the systems in list, in
+// Y[c] = A X[c] (mode 0), B[c] - A X[c] (mode 1) or Y[c] + A X[c] (mode 2) for the systems in list, in
 // the value type T (FP64, or FP32 for the inner solves of the refined GMRES).
 // Items are (row tile, system), tile-major, so the systems of a tile reuse
 // the tile's matrix rows from cache. One thread per row (CSR).
@@ -101,11 +103,11 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
                                                const int32_t* __restrict__ ci, const T* __restrict__ v,
                                                const T* __restrict__ X, T* __restrict__ Y,
                                                const T* __restrict__ B, const int* __restrict__ list,
-                                               const int* __restrict__ xidx, int64_t xstride)
+                                               const int* __restrict__ jstop, int jmax)
 {
     constexpr int CT = 4;  // systems per thread: each matrix entry is loaded once for CT gathers
+    if (jstop && *jstop >= jmax) return;  // the step needs no operator application
     const int cnt = list[0];
-    if (xidx) X += (int64_t)(*xidx) * xstride;  // X = block number *xidx of a basis
     const int groups = (cnt + CT - 1) / CT;
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
     for (int64_t it = blockIdx.x; it < tiles * groups; it += gridDim.x) {
@@ -132,7 +134,8 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
         for (int t = 0; t < CT; ++t) {
             if (t < ng) {
                 if (MODE == 0) Y[off[t] + row] = acc[t];
-                else Y[off[t] + row] = B[off[t] + row] - acc[t];
+                else if (MODE == 1) Y[off[t] + row] = B[off[t] + row] - acc[t];
+                else Y[off[t] + row] += acc[t];
             }
         }
     }
@@ -140,14 +143,14 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
 
 template <class T, int MODE>
 void spmv(int32_t n, int64_t ld, const int64_t* rp, const int32_t* ci, const T* v, int k, const T* X, T* Y,
-          const T* B, const int* list, cudaStream_t st, const int* xidx = nullptr, int64_t xstride = 0)
+          const T* B, const int* list, cudaStream_t st, const int* jstop = nullptr, int jmax = 0)
 {
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
     int64_t g = tiles * ((k + 3) / 4);
     const int64_t cap = (int64_t)g_sms * 8;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, rp, ci, v, X, Y, B, list, xidx, xstride);
+    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, rp, ci, v, X, Y, B, list, jstop, jmax);
 }
 
 template <class T>
@@ -532,20 +535,27 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
 // Control state (FP64 scalars and flags), shared by the FP64 and FP32 engines.
 struct Gm {
     int m;
-    double* H;   // k x m x (m+1): column j of system c at H[(c*m + j)*(m+1)]
-    double* cs;  // k x m
-    double* sn;  // k x m
-    double* g;   // k x (m+1)
-    double* h;   // 2 x (m+1) x k  (projection passes)
-    double* u;   // k x m
-    double* ww;  // k: ||w||^2 before the projection
-    double* hn2; // k: ||w||^2 after it
-    int *cyc, *adv, *jd, *done, *conv, *reo;
-    int *lcyc, *ladv, *lreo;  // lists
-    int* jdev;                // inner index j of the current Arnoldi step
+    double* H;      // rotated columns (the triangle R): column j of system c at H[(c*m + j)*(m+1)]
+    double* Hu;     // the same columns before rotation (the Hessenberg matrix of the Arnoldi relation)
+    double* cs;     // k x m
+    double* sn;     // k x m
+    double* g;      // k x (m+1)
+    double* hp;     // k x (m+1): first-pass coefficients of the newest column
+    double* sco;    // k x (m+1): s = V^T u of the current step
+    double* cco;    // k x (m+1): c = V^T z of the current step
+    double* y;      // k x m: least-squares solution at the end of a cycle
+    double* alpha;  // k: norm of u - V s
+    double* dco;    // k: v_j^T (A M v_j)-part of z, see k_dc_step
+    int *cyc, *adv, *jd, *done, *conv;
+    int *lcyc, *ladv;  // lists
+    int* jdev;         // number of finished basis vectors in the current cycle
+    int* bcnt;         // arrival counter of the multi-block control kernels
 };
 
-constexpr int GM_MAXM = 128;  // largest restart length
+constexpr int GM_MAXM = 128;             // largest restart length
+constexpr int PD = 8;                    // basis vectors per pass of the fused dot kernel
+constexpr int PS = 2 * GM_MAXM + 2;      // partial slots per (system, chunk)
+constexpr int STEP_THREADS = 1024;       // threads of the per-system control kernels
 
 // Krylov basis: m+1 system-major blocks of k vectors in the value type T.
 template <class T>
@@ -568,6 +578,13 @@ struct Vec<double> {
     {
         return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
     }
+    __device__ static double2 lin(double a, const double2& x, double b, const double2& y)  // a x + b y
+    {
+        return make_double2(fma(a, x.x, b * y.x), fma(a, x.y, b * y.y));
+    }
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double2 sub(const double2& a, const double2& b) { return make_double2(a.x - b.x, a.y - b.y); }
+    __device__ static double2 scale(double s, const double2& a) { return make_double2(s * a.x, s * a.y); }
 };
 template <>
 struct Vec<float> {
@@ -581,6 +598,12 @@ struct Vec<float> {
     {
         return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
     }
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static float4 sub(const float4& a, const float4& b)
+    {
+        return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    }
+    __device__ static float4 scale(float s, const float4& a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
 };
 
 template <class T>
@@ -629,7 +652,6 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* 
         G.adv[c] = 0;
         G.conv[c] = 0;
         G.jd[c] = 0;
-        G.reo[c] = 0;
         if (!G.done[c]) {
             const double beta = sqrt(sum_chunks(part, 0, c, k, nch));
             if (beta < S.thr[c]) {
@@ -651,134 +673,306 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* 
     if (threadIdx.x == 0) {
         build_list(k, G.cyc, G.lcyc);
         build_list(k, G.adv, G.ladv);
-        G.lreo[0] = 0;
         *G.jdev = 0;
+        *G.bcnt = 0;
         *any_cyc = G.lcyc[0] > 0;
     }
 }
 
-template <class T>
-__global__ void k_gm_v0(Items I, const T* __restrict__ r, Sys S, Gm G, Basis<T> Bv)
-{
-    FOR_ITEMS(I, G.lcyc, c, r0, r1)
-    {
-        const T inv = (T)(1.0 / S.beta[c]);
-        const int64_t o = (int64_t)c * I.ld;
-        for (int64_t i = r0 + lane_; i < r1; i += 32) Bv.V[o + i] = r[o + i] * inv;
-    }
-}
+// ------------------------------------------------ Arnoldi with delayed re-orthogonalisation
+// Classical Gram-Schmidt applied twice, with the second pass of each vector
+// delayed by one step and merged into the next step's single reduction
+// (the "DCGS2" Arnoldi of Swirydowicz et al. 2020 / Bielich et al. 2022).
+//
+// At step j the basis v_0..v_{j-1} is final and u is the candidate for v_j:
+// the remainder of A M v_{j-1} after one projection (for j = 0, u = r0).
+// With z = A M u, one pass over the rows forms
+//     s = V^T u,  c = V^T z,  uu = u^T u,  uz = u^T z            (k_dc_dots)
+// from which (k_dc_step)
+//     alpha = sqrt(uu - s^T s),   v_j = (u - V s) / alpha,
+//     column j-1 of the Hessenberg matrix = hp + s, with subdiagonal alpha,
+//     d = (uz - s^T c) / alpha  (= v_j^T z),
+//     hp(new)_i = ([c; d]_i - (Hbar s)_i) / alpha,  i = 0..j,
+// using A M V_j = V_{j+1} Hbar_j, so that A M v_j = (z - V_{j+1} Hbar_j s)/alpha.
+// A second pass over the rows (k_dc_update) then writes
+//     v_j = (u - V s) / alpha   and   u <- (z - V c - d v_j) / alpha,
+// the first-pass remainder of A M v_j against v_0..v_j. The column of the
+// Hessenberg matrix, its Givens rotation and the stop test therefore run one
+// step behind the operator application; a cycle of m columns takes m + 1
+// steps, the last without an operator application.
+// In exact arithmetic the basis, the Hessenberg matrix and the iterates are
+// those of Arnoldi with modified Gram-Schmidt (Sec. 4.3's GMRES).
 
-// Projection h_i = V_i^T w (i = 0..j, j = *jdev) and ||w||^2 for the systems
-// of list: each warp item streams its chunk of w and of the basis once per
-// group of PJ vectors, with PJ accumulators in registers. Partials: slot i of
-// item (c, q) at part[(c*nch + q)*(GM_MAXM+2) + i], slot GM_MAXM+1 = ||w||^2.
+// Partials: slot 2i = v_i^T u, 2i+1 = v_i^T z (i < j), 2*GM_MAXM = u^T u,
+// 2*GM_MAXM+1 = u^T z, stored at part[((c*PS) + slot)*nch + q] for chunk q.
 template <class T>
-__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_proj(Items I, int k, const T* __restrict__ w, Basis<T> Bv,
-                                                          const int* list, const int* jdev,
+__global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __restrict__ u, const T* __restrict__ z,
+                                                          Basis<T> Bv, const int* list, const int* jdev,
                                                           double* __restrict__ part)
 {
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
     const int j = *jdev;
-    const int ng = j / PJ + 1;  // groups of PJ basis vectors
+    const int ng = j > 0 ? (j + PD - 1) / PD : 1;  // groups of PD basis vectors
     const int cnt = list[0];
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // items: (chunk q, system, basis group g), g fastest so that the items of
-    // one (system, chunk) read their chunk of w from cache
+    // items (chunk q, system, group g), g fastest: the items of one chunk read
+    // its rows of u and z from cache
     for (int64_t it = w0; it < (int64_t)cnt * I.nch * ng; it += nw) {
         const int g = (int)(it % ng);
         const int64_t rest = it / ng;
         const int c = list[1 + (int)(rest % cnt)];
         const int q = (int)(rest / cnt);
-        const int i0 = g * PJ;
-        const int ni = min(PJ, j + 1 - i0);
+        const int i0 = g * PD;
+        const int ni = min(PD, j - i0);
         const int64_t r0 = (int64_t)q * CHUNK, r1 = min((int64_t)I.n, r0 + CHUNK);
         const int64_t o = (int64_t)c * I.ld;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
         const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
-        T acc[PJ];
+        T as[PD], ac[PD];
 #pragma unroll
-        for (int i = 0; i < PJ; ++i) acc[i] = 0;
-        T aw = 0;
+        for (int i = 0; i < PD; ++i) as[i] = ac[i] = 0;
+        T uu = 0, uz = 0;
         for (int64_t row = r0 + (int64_t)lane * VW; row < r1v; row += 32 * VW) {
-            const VT wv = *reinterpret_cast<const VT*>(w + o + row);
-            VT vv[PJ];
+            const VT uv = *reinterpret_cast<const VT*>(u + o + row);
+            const VT zv = *reinterpret_cast<const VT*>(z + o + row);
+            VT vv[PD];
 #pragma unroll
-            for (int i = 0; i < PJ; ++i)
+            for (int i = 0; i < PD; ++i)
                 if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs + row);
 #pragma unroll
-            for (int i = 0; i < PJ; ++i)
-                if (i < ni) acc[i] += Vec<T>::dot(vv[i], wv);
-            if (g == 0) aw += Vec<T>::dot(wv, wv);
+            for (int i = 0; i < PD; ++i)
+                if (i < ni) {
+                    as[i] += Vec<T>::dot(vv[i], uv);
+                    ac[i] += Vec<T>::dot(vv[i], zv);
+                }
+            if (g == 0) {
+                uu += Vec<T>::dot(uv, uv);
+                uz += Vec<T>::dot(uv, zv);
+            }
         }
 #pragma unroll
-        for (int i = 0; i < PJ; ++i) acc[i] = warp_sum_t(acc[i]);
-        double* pp = part + ((size_t)c * I.nch + q) * (GM_MAXM + 2);
+        for (int i = 0; i < PD; ++i) {
+            as[i] = warp_sum_t(as[i]);
+            ac[i] = warp_sum_t(ac[i]);
+        }
+        uu = warp_sum_t(uu);
+        uz = warp_sum_t(uz);
         if (lane == 0) {
+            double* pc = part + (size_t)c * PS * I.nch + q;
 #pragma unroll
-            for (int i = 0; i < PJ; ++i)
-                if (i < ni) pp[i0 + i] = (double)acc[i];
-        }
-        if (g == 0) {
-            aw = warp_sum_t(aw);
-            if (lane == 0) pp[GM_MAXM + 1] = (double)aw;
+            for (int i = 0; i < PD; ++i)
+                if (i < ni) {
+                    pc[(size_t)(2 * (i0 + i)) * I.nch] = (double)as[i];
+                    pc[(size_t)(2 * (i0 + i) + 1) * I.nch] = (double)ac[i];
+                }
+            if (g == 0) {
+                pc[(size_t)(2 * GM_MAXM) * I.nch] = (double)uu;
+                pc[(size_t)(2 * GM_MAXM + 1) * I.nch] = (double)uz;
+            }
         }
     }
 }
 
-// h[i][c] for i <= j and ww[c] from the chunk partials; one warp per
-// (listed system, slot); launched with k*(GM_MAXM+2) warps at most
-__global__ void k_gm_fin(int k, int nch, const double* __restrict__ part, const int* list, const int* jdev,
-                         double* __restrict__ h, double* __restrict__ ww)
+// Arrival of one block of a multi-block control kernel: true in exactly one
+// block, the last to arrive, after every other block's writes are visible.
+// No block waits for another.
+__device__ __forceinline__ bool last_block_arrives(int* bcnt)
 {
-    const int j = *jdev;
-    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int cnt = list[0];
-    if (q >= (int64_t)cnt * (j + 2)) return;
-    const int s = (int)(q / (j + 2)), i = (int)(q - (int64_t)s * (j + 2));
-    const int c = list[1 + s];
-    const int slot = i <= j ? i : GM_MAXM + 1;
-    double sum = 0.0;
-    for (int b = lane; b < nch; b += 32) sum += part[((size_t)c * nch + b) * (GM_MAXM + 2) + slot];
-    sum = warp_sum(sum);
-    if (lane == 0) {
-        if (i <= j) h[(size_t)i * k + c] = sum;
-        else if (ww) ww[c] = sum;
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(bcnt, 1) == (int)gridDim.x - 1;
+        if (last) __threadfence();
+    }
+    __syncthreads();
+    return last != 0;
+}
+
+__device__ __forceinline__ void rebuild_list(int k, const int* mask, int* list)
+{
+    const volatile int* vm = mask;
+    int q = 0;
+    for (int c = 0; c < k; ++c)
+        if (vm[c]) list[1 + q++] = c;
+    list[0] = q;
+}
+
+// Step j for the system of block b of list ladv (grid = k blocks): reduces
+// the chunk partials, finishes column j-1 (Givens rotation, residual
+// estimate |g_j|, stop tests) and forms the coefficients of k_dc_update.
+// tiny: relative floor of alpha^2 below which u counts as lying in span(V).
+__global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const double* __restrict__ part,
+                                                         const int* cap, Sys S, Gm G, Dims D, double tiny,
+                                                         int* any_adv)
+{
+    __shared__ double red[PS];
+    __shared__ double rc[GM_MAXM + 1];
+    __shared__ double csS[GM_MAXM], snS[GM_MAXM];
+    __shared__ double sh[2];
+    __shared__ int stop;
+    const int j = *G.jdev;
+    const int cnt = G.ladv[0];
+    const int m = G.m;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
+    if ((int)blockIdx.x < cnt) {
+        const int c = G.ladv[1 + blockIdx.x];
+        const int ns = 2 * j + 2;
+        for (int t = wid; t < ns; t += nwarp) {
+            const int slot = t < 2 * j ? t : 2 * GM_MAXM + (t - 2 * j);
+            const double* p = part + ((size_t)c * PS + slot) * nch;
+            double sum = 0.0;
+            for (int q = lane; q < nch; q += 32) sum += p[q];
+            sum = warp_sum(sum);
+            if (lane == 0) red[t] = sum;
+        }
+        __syncthreads();
+        // red[2i] = s_i, red[2i+1] = c_i (i < j), red[2j] = u^T u, red[2j+1] = u^T z
+        if (wid == 0) {
+            double ss = 0.0, sc = 0.0;
+            for (int i = lane; i < j; i += 32) {
+                ss = fma(red[2 * i], red[2 * i], ss);
+                sc = fma(red[2 * i], red[2 * i + 1], sc);
+            }
+            ss = warp_sum(ss);
+            sc = warp_sum(sc);
+            if (lane == 0) {
+                const double uu = red[2 * j], uz = red[2 * j + 1];
+                const double a2 = uu - ss;
+                const double al = a2 > tiny * uu ? sqrt(a2) : 0.0;
+                sh[0] = al;
+                sh[1] = al > 0.0 ? (uz - sc) / al : 0.0;
+                stop = 0;
+            }
+        }
+        __syncthreads();
+        const double al = sh[0], d = sh[1];
+        double* Huc = G.Hu + (size_t)c * m * (m + 1);
+        double* Hc = G.H + (size_t)c * m * (m + 1);
+        if (j >= 1) {
+            // column j-1: first-pass coefficients + s, subdiagonal alpha
+            const double* hpc = G.hp + (size_t)c * (m + 1);
+            for (int i = tid; i <= j; i += blockDim.x) {
+                const double v = i < j ? hpc[i] + red[2 * i] : al;
+                Huc[(size_t)(j - 1) * (m + 1) + i] = v;
+                rc[i] = v;
+            }
+            for (int i = tid; i < j - 1; i += blockDim.x) {
+                csS[i] = G.cs[(size_t)c * m + i];
+                snS[i] = G.sn[(size_t)c * m + i];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                for (int i = 0; i < j - 1; ++i) {
+                    const double a = rc[i], b = rc[i + 1];
+                    rc[i] = csS[i] * a + snS[i] * b;
+                    rc[i + 1] = -snS[i] * a + csS[i] * b;
+                }
+                const double a = rc[j - 1], b = rc[j];
+                const double den = sqrt(a * a + b * b);
+                const double cn = den == 0.0 ? 1.0 : a / den, sn = den == 0.0 ? 0.0 : b / den;
+                G.cs[(size_t)c * m + j - 1] = cn;
+                G.sn[(size_t)c * m + j - 1] = sn;
+                rc[j - 1] = cn * a + sn * b;
+                rc[j] = 0.0;
+                double* gc = G.g + (size_t)c * (m + 1);
+                gc[j] = -sn * gc[j - 1];
+                gc[j - 1] = cn * gc[j - 1];
+                S.iters[c] += 1;
+                G.jd[c] = j;
+                if (fabs(gc[j]) < S.thr[c]) {
+                    G.conv[c] = 1;
+                    stop = 1;
+                } else if (al == 0.0 || S.iters[c] >= cap[c] || j >= m) {
+                    stop = 1;  // breakdown, iteration cap, or the cycle is full: restart
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i <= j; i += blockDim.x) Hc[(size_t)(j - 1) * (m + 1) + i] = rc[i];
+        } else if (tid == 0) {
+            // v_0 = r0 / alpha: the right-hand side of the small problem is alpha e_1
+            G.g[(size_t)c * (m + 1)] = al;
+            if (al == 0.0) {
+                G.conv[c] = 1;
+                stop = 1;
+            }
+        }
+        __syncthreads();
+        if (!stop) {
+            // first-pass coefficients of column j and the update coefficients;
+            // (Hbar s)_i = sum_{q >= max(i-1,0)} Hbar(i,q) s_q over the final columns q < j
+            double* hpc = G.hp + (size_t)c * (m + 1);
+            for (int i = tid; i <= j; i += blockDim.x) {
+                double hs = 0.0;
+                for (int q = i > 0 ? i - 1 : 0; q < j; ++q) hs = fma(Huc[(size_t)q * (m + 1) + i], red[2 * q], hs);
+                const double cz = i < j ? red[2 * i + 1] : d;
+                hpc[i] = (cz - hs) / al;
+                if (i < j) {
+                    G.sco[(size_t)c * (m + 1) + i] = red[2 * i];
+                    G.cco[(size_t)c * (m + 1) + i] = red[2 * i + 1];
+                }
+            }
+            if (tid == 0) {
+                G.alpha[c] = al;
+                G.dco[c] = d;
+            }
+        } else if (tid == 0) {
+            G.adv[c] = 0;
+        }
+    }
+    if (last_block_arrives(G.bcnt) && tid == 0) {
+        rebuild_list(k, G.adv, G.ladv);
+        const int ku = G.ladv[0];
+        if (cnt > 0) {
+            if (j < m) {
+                spmm_work(D, D.nnzM, cnt);
+                spmm_work(D, D.nnzA, cnt);
+            }
+            kwork_add(D.site_dots, D.esz * D.n * cnt * (j + 2), D.n * cnt * (4.0 * j + 4.0));
+            if (ku > 0) kwork_add(D.site_upd, D.esz * D.n * ku * (j + 4), D.n * ku * (4.0 * j + 6.0));
+            *G.jdev = j + 1;
+        }
+        *any_adv = ku > 0;
+        *G.bcnt = 0;
     }
 }
 
-// w -= sum_{i<=j} V_i h_i for the systems of list, one pass over w; writes
-// ||w||^2 partials (one per item). h of the warp's system is staged in
-// shared memory.
+// v_j = (u - V s)/alpha and u <- (z - V c - d v_j)/alpha for the systems of
+// list; one pass over the rows, PJ basis vectors per register tile.
 template <class T>
-__global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, T* __restrict__ w, Basis<T> Bv,
-                                                         const double* __restrict__ h, const int* list,
-                                                         const int* jdev, double* __restrict__ part)
+__global__ void __launch_bounds__(IT_WARPS * 32) k_dc_update(Items I, T* __restrict__ u, const T* __restrict__ z,
+                                                            Basis<T> Bv, Gm G, const int* list, const int* jdev)
 {
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
-    __shared__ T hs[IT_WARPS][GM_MAXM];
-    const int j = *jdev;
+    __shared__ T hs[IT_WARPS][GM_MAXM], hc[IT_WARPS][GM_MAXM];
+    const int j = *jdev - 1;  // k_dc_step has advanced the index: write V_j
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cnt = list[0];
+    const int m1 = G.m + 1;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = w0; it < (int64_t)cnt * I.nchu; it += nw) {
         const int c = list[1 + (int)(it % cnt)];
         const int q = (int)(it / cnt);
-        for (int i = lane; i <= j; i += 32) hs[wid][i] = (T)(-h[(size_t)i * k + c]);
+        for (int i = lane; i < j; i += 32) {
+            hs[wid][i] = (T)G.sco[(size_t)c * m1 + i];
+            hc[wid][i] = (T)G.cco[(size_t)c * m1 + i];
+        }
+        const T ia = (T)(1.0 / G.alpha[c]);
+        const T dd = (T)G.dco[c];
         __syncwarp();
         const int64_t r0 = (int64_t)q * CHUNK_U, r1 = min((int64_t)I.n, r0 + CHUNK_U);
         const int64_t o = (int64_t)c * I.ld;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
-        T acc = 0;
+        T* Vj = Bv.V + (int64_t)j * Bv.vs + o;
         for (int64_t row = r0 + (int64_t)lane * VW; row < r1v; row += 32 * VW) {
-            VT wv = *reinterpret_cast<const VT*>(w + o + row);
-            for (int i0 = 0; i0 <= j; i0 += PJ) {
-                const int ni = min(PJ, j + 1 - i0);
+            VT a_s = Vec<T>::zero(), a_c = Vec<T>::zero();
+            for (int i0 = 0; i0 < j; i0 += PJ) {
+                const int ni = min(PJ, j - i0);
                 const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o + row;
                 VT vv[PJ];
 #pragma unroll
@@ -786,175 +980,105 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_gm_upd(Items I, int k, T* __r
                     if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs);
 #pragma unroll
                 for (int i = 0; i < PJ; ++i)
-                    if (i < ni) wv = Vec<T>::axpy(hs[wid][i0 + i], vv[i], wv);
+                    if (i < ni) {
+                        a_s = Vec<T>::axpy(hs[wid][i0 + i], vv[i], a_s);
+                        a_c = Vec<T>::axpy(hc[wid][i0 + i], vv[i], a_c);
+                    }
             }
-            *reinterpret_cast<VT*>(w + o + row) = wv;
-            acc += Vec<T>::dot(wv, wv);
+            const VT uv = *reinterpret_cast<const VT*>(u + o + row);
+            const VT zv = *reinterpret_cast<const VT*>(z + o + row);
+            const VT v = Vec<T>::scale(ia, Vec<T>::sub(uv, a_s));
+            const VT un = Vec<T>::scale(ia, Vec<T>::axpy(-dd, v, Vec<T>::sub(zv, a_c)));
+            *reinterpret_cast<VT*>(Vj + row) = v;
+            *reinterpret_cast<VT*>(u + o + row) = un;
         }
-        acc = warp_sum_t(acc);
-        if (lane == 0) part[(size_t)c * I.nchu + q] = (double)acc;
         __syncwarp();
     }
 }
 
-// ||w||^2 after a projection pass (one warp per listed system). Pass 0 marks
-// the systems that need a second pass: ||w_after||^2 < ||w_before||^2 / 2.
-__global__ void k_gm_finnorm(int k, int nch, const double* __restrict__ part, Gm G, int pass)
+// y = R(0:jd,0:jd)^{-1} g(0:jd) per system of the cycle (R upper triangular),
+// by column-oriented back substitution from shared memory; grid = k blocks,
+// dynamic shared memory (m*(m+1) + m) doubles.
+__global__ void k_dc_trisolve(int k, Sys S, Gm G)
 {
-    const int* list = pass == 0 ? G.ladv : G.lreo;
-    const int cnt = list[0];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int s = wid; s < cnt; s += blockDim.x >> 5) {
-        const int c = list[1 + s];
-        double sum = 0.0;
-        for (int b = lane; b < nch; b += 32) sum += part[(size_t)c * nch + b];
-        sum = warp_sum(sum);
-        if (lane == 0) {
-            G.hn2[c] = sum;
-            if (pass == 0) G.reo[c] = sum < 0.5 * G.ww[c];
-        }
-    }
-    __syncthreads();
-    if (pass == 0 && threadIdx.x == 0) {
-        int q = 0;
-        for (int s = 0; s < cnt; ++s) {
-            const int c = list[1 + s];
-            if (G.reo[c]) G.lreo[1 + q++] = c;
-        }
-        G.lreo[0] = q;
-    }
-}
-
-// H(:,j) = h0 (+ h1), ||w||, Givens rotations, residual estimate, stop tests
-__global__ void k_gm_givens(int k, const int* cap, Sys S, Gm G, Dims D, int* any_adv)
-{
-    const int c = threadIdx.x;
-    const int j = *G.jdev;
-    if (c == 0) {
-        const int ka = G.ladv[0], kr = G.lreo[0];
-        if (ka > 0) {
-            spmm_work(D, D.nnzM, ka);
-            spmm_work(D, D.nnzA, ka);
-            const double p = (double)(ka + kr);  // projection passes
-            kwork_add(D.site_dots, D.esz * D.n * p * (j + 2), D.n * p * (2.0 * (j + 1) + 2.0));
-            kwork_add(D.site_upd, D.esz * D.n * p * (j + 3), D.n * p * (2.0 * (j + 1) + 2.0));
-        }
-    }
-    if (c < k && G.adv[c]) {
-        const int m = G.m;
-        double* Hc = G.H + ((size_t)c * m + j) * (m + 1);
-        const bool two = G.reo[c] != 0;
-        for (int i = 0; i <= j; ++i)
-            Hc[i] = G.h[(size_t)i * k + c] + (two ? G.h[((size_t)(m + 1) + i) * k + c] : 0.0);
-        const double hn = sqrt(G.hn2[c]);
-        Hc[j + 1] = hn;
-        S.hn[c] = hn;
-        double* csc = G.cs + (size_t)c * m;
-        double* snc = G.sn + (size_t)c * m;
-        for (int i = 0; i < j; ++i) {
-            const double a = Hc[i], b = Hc[i + 1];
-            Hc[i] = csc[i] * a + snc[i] * b;
-            Hc[i + 1] = -snc[i] * a + csc[i] * b;
-        }
-        const double a = Hc[j], b = Hc[j + 1];
-        const double den = sqrt(a * a + b * b);
-        if (den == 0.0) {
-            csc[j] = 1.0;
-            snc[j] = 0.0;
-        } else {
-            csc[j] = a / den;
-            snc[j] = b / den;
-        }
-        Hc[j] = csc[j] * a + snc[j] * b;
-        Hc[j + 1] = 0.0;
-        double* gc = G.g + (size_t)c * (m + 1);
-        gc[j + 1] = -snc[j] * gc[j];
-        gc[j] = csc[j] * gc[j];
-        S.iters[c] += 1;
-        G.jd[c] = j + 1;
-        if (fabs(gc[j + 1]) < S.thr[c]) {
-            G.adv[c] = 0;
-            G.conv[c] = 1;
-        } else if (S.iters[c] >= cap[c] || j + 1 >= G.m) {
-            G.adv[c] = 0;  // iteration cap, or the cycle is full: restart
-        }
-    }
-    __syncthreads();
-    if (c < k) G.reo[c] = 0;
-    if (threadIdx.x == 0) {
-        const int had = G.ladv[0];
-        build_list(k, G.adv, G.ladv);
-        G.lreo[0] = 0;
-        if (had > 0) *G.jdev = j + 1;
-        *any_adv = G.ladv[0] > 0;
-    }
-}
-
-template <class T>
-__global__ void k_gm_normalize(Items I, const T* __restrict__ w, Sys S, Gm G, Basis<T> Bv)
-{
-    const int j = *G.jdev - 1;  // givens has advanced the index: write V_{j+1}
-    FOR_ITEMS(I, G.ladv, c, r0, r1)
-    {
-        const double hn = S.hn[c];
-        const T inv = (T)(hn > 0.0 ? 1.0 / hn : 0.0);
-        const int64_t o = (int64_t)c * I.ld;
-        T* Vn = Bv.V + (int64_t)(j + 1) * Bv.vs + o;
-        for (int64_t i = r0 + lane_; i < r1; i += 32) Vn[i] = w[o + i] * inv;
-    }
-}
-
-// u = H(0:jd,0:jd)^{-1} g(0:jd) per system (upper triangular)
-__global__ void k_gm_trisolve(int k, Sys S, Gm G)
-{
-    const int c = threadIdx.x;
-    if (c < k && G.cyc[c]) {
-        const int m = G.m, jd = G.jd[c];
-        const double* gc = G.g + (size_t)c * (m + 1);
-        double* uc = G.u + (size_t)c * m;
-        for (int i = 0; i < m; ++i) uc[i] = 0.0;
+    extern __shared__ double sm[];
+    __shared__ int bad;
+    const int m = G.m;
+    double* Rs = sm;                      // column q at Rs[q*(m+1)]
+    double* t = sm + (size_t)m * (m + 1);
+    const int cnt = G.lcyc[0];
+    if ((int)blockIdx.x < cnt) {
+        const int c = G.lcyc[1 + blockIdx.x];
+        const int jd = G.jd[c];
+        const double* Hc = G.H + (size_t)c * m * (m + 1);
+        for (int e = threadIdx.x; e < jd * (m + 1); e += blockDim.x) Rs[e] = Hc[e];
+        for (int i = threadIdx.x; i < jd; i += blockDim.x) t[i] = G.g[(size_t)c * (m + 1) + i];
+        if (threadIdx.x == 0) bad = 0;
+        __syncthreads();
         for (int i = jd - 1; i >= 0; --i) {
-            double t = gc[i];
-            for (int q = i + 1; q < jd; ++q) t -= G.H[((size_t)c * m + q) * (m + 1) + i] * uc[q];
-            const double d = G.H[((size_t)c * m + i) * (m + 1) + i];
-            if (d == 0.0) {
-                S.status[c] = ST_BREAKDOWN;
-                G.done[c] = 1;
-                G.cyc[c] = 0;
-                for (int q = 0; q < m; ++q) uc[q] = 0.0;
+            const double dg = Rs[(size_t)i * (m + 1) + i];
+            if (dg == 0.0) {
+                if (threadIdx.x == 0) bad = 1;
                 break;
             }
-            uc[i] = t / d;
+            const double yi = t[i] / dg;
+            __syncthreads();
+            for (int r = threadIdx.x; r < i; r += blockDim.x) t[r] = fma(-Rs[(size_t)i * (m + 1) + r], yi, t[r]);
+            if (threadIdx.x == 0) t[i] = yi;
+            __syncthreads();
+        }
+        __syncthreads();
+        double* yc = G.y + (size_t)c * m;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) yc[i] = (bad || i >= jd) ? 0.0 : t[i];
+        if (bad && threadIdx.x == 0) {
+            S.status[c] = ST_BREAKDOWN;
+            G.done[c] = 1;
+            G.cyc[c] = 0;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) build_list(k, G.cyc, G.lcyc);
+    if (last_block_arrives(G.bcnt) && threadIdx.x == 0) {
+        rebuild_list(k, G.cyc, G.lcyc);
+        *G.bcnt = 0;
+    }
 }
 
-// w = V u per system (the caller forms z = M w and x += z)
+// w = V y per system of the cycle (the caller adds M w to x)
 template <class T>
-__global__ void k_gm_combine(Items I, T* w, Gm G, Basis<T> Bv)
+__global__ void __launch_bounds__(IT_WARPS * 32) k_dc_combine(Items I, T* __restrict__ w, Basis<T> Bv, Gm G)
 {
-    FOR_ITEMS(I, G.lcyc, c, r0, r1)
-    {
+    using VT = typename Vec<T>::type;
+    constexpr int VW = Vec<T>::W;
+    __shared__ T ys[IT_WARPS][GM_MAXM];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int* list = G.lcyc;
+    const int cnt = list[0];
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = w0; it < (int64_t)cnt * I.nchu; it += nw) {
+        const int c = list[1 + (int)(it % cnt)];
+        const int q = (int)(it / cnt);
         const int jd = G.jd[c];
-        const double* uc = G.u + (size_t)c * G.m;
+        for (int i = lane; i < jd; i += 32) ys[wid][i] = (T)G.y[(size_t)c * G.m + i];
+        __syncwarp();
+        const int64_t r0 = (int64_t)q * CHUNK_U, r1 = min((int64_t)I.n, r0 + CHUNK_U);
         const int64_t o = (int64_t)c * I.ld;
-        for (int64_t i = r0 + lane_; i < r1; i += 32) {
-            T s = 0;
-            for (int q = 0; q < jd; ++q) s = fma(Bv.V[(int64_t)q * Bv.vs + o + i], (T)uc[q], s);
-            w[o + i] = s;
+        const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
+        for (int64_t row = r0 + (int64_t)lane * VW; row < r1v; row += 32 * VW) {
+            VT acc = Vec<T>::zero();
+            for (int i0 = 0; i0 < jd; i0 += PJ) {
+                const int ni = min(PJ, jd - i0);
+                const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o + row;
+                VT vv[PJ];
+#pragma unroll
+                for (int i = 0; i < PJ; ++i)
+                    if (i < ni) vv[i] = *reinterpret_cast<const VT*>(Vp + (int64_t)i * Bv.vs);
+#pragma unroll
+                for (int i = 0; i < PJ; ++i)
+                    if (i < ni) acc = Vec<T>::axpy(ys[wid][i0 + i], vv[i], acc);
+            }
+            *reinterpret_cast<VT*>(w + o + row) = acc;
         }
-    }
-}
-
-template <class T>
-__global__ void k_gm_xadd(Items I, T* x, const T* __restrict__ z, Gm G)
-{
-    FOR_ITEMS(I, G.lcyc, c, r0, r1)
-    {
-        const int64_t o = (int64_t)c * I.ld;
-        for (int64_t i = r0 + lane_; i < r1; i += 32) x[o + i] += z[o + i];
+        __syncwarp();
     }
 }
 
@@ -1078,64 +1202,47 @@ __global__ void k_ir_finish(int k, const int* done, const int* status64, const i
 }
 
 // ---------------------------------------------------------------- GMRES engine
-// One classical Gram-Schmidt pass of w against V_0..V_j for the systems of list.
 template <class T>
-void cgs_pass(const Items& I, int k, int pass, T* w, const Basis<T>& B, const Gm& G, const int* list, double* part,
-              double* part2, const Dims& D, cudaStream_t st)
+struct GmWork {  // device buffers of one GMRES engine
+    Basis<T> B;
+    T *r, *t, *z, *w;  // r: residual, then the candidate u of each step; t = M u; z = A~ t; w = V y
+};
+
+// One Arnoldi step (5 launches) for the advancing systems, index j on the device.
+template <class T>
+void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, Sys& S, Gm& G, const int* cap,
+                  double* pt, int* fl, const Dims& D, double tiny, cudaStream_t st)
 {
-    double* h = G.h + (size_t)pass * (G.m + 1) * k;
-    // one wave of resident blocks: the grid-stride item loops then end together
+    const int32_t n = I.n;
+    const int64_t ld = I.ld;
+    // the last step of a cycle (j = m) needs no operator application
+    {
+        ProfScope ps(D.site_spmm, st);
+        spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, Wk.r, Wk.t, nullptr, G.ladv, st, G.jdev, G.m);
+    }
+    {
+        ProfScope ps(D.site_spmm, st);
+        spmv<T, 0>(n, ld, A.Ar, A.Ac, A.Av, k, Wk.t, Wk.z, nullptr, G.ladv, st, G.jdev, G.m);
+    }
     const int fp = sizeof(T) == 4;
-    const int64_t pcap = (int64_t)g_sms * g_res_proj[fp], ucap = (int64_t)g_sms * g_res_upd[fp];
-    int64_t pb = ((int64_t)I.nch * k * ((G.m - 1) / PJ + 1) + IT_WARPS - 1) / IT_WARPS;
+    const int64_t pcap = (int64_t)g_sms * g_res_dots[fp], ucap = (int64_t)g_sms * g_res_upd[fp];
+    int64_t pb = ((int64_t)I.nch * k * ((G.m - 1) / PD + 1) + IT_WARPS - 1) / IT_WARPS;
     int64_t ub = ((int64_t)I.nchu * k + IT_WARPS - 1) / IT_WARPS;
     pb = pb < pcap ? pb : pcap;
     ub = ub < ucap ? ub : ucap;
     {
         ProfScope ps(D.site_dots, st);
-        k_gm_proj<T><<<SAI_GRID(pb), IT_WARPS * 32, 0, st>>>(I, k, w, B, list, G.jdev, part);
+        k_dc_dots<T><<<SAI_GRID(pb), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G.ladv, G.jdev, pt);
     }
-    const int64_t warps = (int64_t)k * (G.m + 2);
-    k_gm_fin<<<SAI_GRID(sai_div_up(warps * 32, 256)), 256, 0, st>>>(k, I.nch, part, list, G.jdev, h,
-                                                                   pass == 0 ? G.ww : nullptr);
+    k_dc_step<<<SAI_GRID(k), STEP_THREADS, 0, st>>>(k, I.nch, pt, cap, S, G, D, tiny, fl);
     {
         ProfScope ps(D.site_upd, st);
-        k_gm_upd<T><<<SAI_GRID(ub), IT_WARPS * 32, 0, st>>>(I, k, w, B, h, list, G.jdev, part2);
+        k_dc_update<T><<<SAI_GRID(ub), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G, G.ladv, G.jdev);
     }
-    k_gm_finnorm<<<SAI_GRID(1), 1024, 0, st>>>(k, I.nchu, part2, G, pass);
-}
-
-template <class T>
-struct GmWork {  // device buffers of one GMRES engine
-    Basis<T> B;
-    T *r, *w, *z;
-};
-
-// Restarted GMRES on the systems with finite thresholds: X = 0 start,
-// per-system iteration caps, S.iters counts the inner steps of this call.
-// One Arnoldi step for the advancing systems (inner index j on the device).
-template <class T>
-void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, Sys& S, Gm& G, const int* cap,
-                  double* pt, double* pt2, int* fl, const Dims& D, cudaStream_t st)
-{
-    const int32_t n = I.n;
-    const int64_t ld = I.ld;
-    {
-        ProfScope ps(D.site_spmm, st);
-        spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, Wk.B.V, Wk.z, nullptr, G.ladv, st, G.jdev, Wk.B.vs);
-    }
-    {
-        ProfScope ps(D.site_spmm, st);
-        spmv<T, 0>(n, ld, A.Ar, A.Ac, A.Av, k, Wk.z, Wk.w, nullptr, G.ladv, st);
-    }
-    cgs_pass<T>(I, k, 0, Wk.w, Wk.B, G, G.ladv, pt, pt2, D, st);
-    cgs_pass<T>(I, k, 1, Wk.w, Wk.B, G, G.lreo, pt, pt2, D, st);
-    k_gm_givens<<<SAI_GRID(1), CTRL, 0, st>>>(k, cap, S, G, D, fl);
-    k_gm_normalize<T><<<SAI_GRID(item_blocks(n > 0 ? n : 1, k)), IT_WARPS * 32, 0, st>>>(I, Wk.w, S, G, Wk.B);
 }
 
 constexpr int GM_STEPS_PER_CHECK = 4;  // Arnoldi steps between host checks (one graph)
-constexpr int GM_LAUNCHES_PER_STEP = 12;
+constexpr int GM_LAUNCHES_PER_STEP = 5;
 
 // Restarted GMRES on the systems with finite thresholds: X = 0 start,
 // per-system iteration caps, S.iters counts the inner steps of this call.
@@ -1148,10 +1255,16 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
     const int32_t n = I.n;
     const int64_t ld = I.ld;
     const int ib = item_blocks(n > 0 ? n : 1, k);
+    int64_t cb = ((int64_t)I.nchu * k + IT_WARPS - 1) / IT_WARPS;
+    if (cb > (int64_t)g_sms * 8) cb = (int64_t)g_sms * 8;
+    // alpha^2 below 64 unit roundoffs of u^T u: u lies in span(V) to working accuracy
+    const double tiny = 64.0 * (sizeof(T) == 4 ? 5.96e-8 : 1.11e-16);
+    const size_t tri_smem = sizeof(double) * ((size_t)m * (m + 1) + m);
+    if (tri_smem > 48 * 1024)
+        SAI_CUDA(cudaFuncSetAttribute(k_dc_trisolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
     int hflag = 0;
     T* r = Wk.r;
     T* w = Wk.w;
-    T* z = Wk.z;
     // Graphs are captured and replayed on a library stream ordered after the
     // caller's stream (the legacy default stream cannot be captured).
     const bool use_graph = !sai_prof_on();
@@ -1174,7 +1287,7 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         if (cs == cudaStreamCaptureStatusNone) {
             cudaGraph_t graph = nullptr;
             SAI_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            for (int q = 0; q < GM_STEPS_PER_CHECK; ++q) arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, pt2, fl, D, st);
+            for (int q = 0; q < GM_STEPS_PER_CHECK; ++q) arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, fl, D, tiny, st);
             cudaError_t e = cudaStreamEndCapture(st, &graph);
             if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
             if (graph) cudaGraphDestroy(graph);
@@ -1195,8 +1308,8 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
         SAI_CUDA(cudaStreamSynchronize(st));
         if (!hflag) break;
-        k_gm_v0<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, S, G, Wk.B);
-        for (int j0 = 0; j0 < m; j0 += GM_STEPS_PER_CHECK) {
+        // steps 0..m: every system of the cycle stops by step m
+        for (int j0 = 0; j0 <= m; j0 += GM_STEPS_PER_CHECK) {
             if (gexec) {
                 cudaError_t e = cudaGraphLaunch(gexec, st);
                 if (e != cudaSuccess) {
@@ -1206,7 +1319,7 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
                 sai_count_grid_add((long long)GM_STEPS_PER_CHECK * GM_LAUNCHES_PER_STEP);
             } else {
                 for (int q = 0; q < GM_STEPS_PER_CHECK; ++q)
-                    arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, pt2, fl, D, st);
+                    arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, fl, D, tiny, st);
             }
             SAI_CUDA(cudaGetLastError());
             SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1214,10 +1327,9 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
             if (!hflag) break;
         }
         if (status != SAI_OK) break;
-        k_gm_trisolve<<<SAI_GRID(1), CTRL, 0, st>>>(k, S, G);
-        k_gm_combine<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, w, G, Wk.B);
-        spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, w, z, nullptr, G.lcyc, st);
-        k_gm_xadd<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, Xs, z, G);
+        k_dc_trisolve<<<SAI_GRID(k), 128, tri_smem, st>>>(k, S, G);
+        k_dc_combine<T><<<SAI_GRID(cb), IT_WARPS * 32, 0, st>>>(I, w, Wk.B, G);
+        spmv<T, 2>(n, ld, A.Mr, A.Mc, A.Mv, k, w, Xs, nullptr, G.lcyc, st);  // x += M V y
         k_gm_cycle_end<<<SAI_GRID(1), CTRL, 0, st>>>(k, cap, S, G, fl);
         spmv<T, 1>(n, ld, A.Ar, A.Ac, A.Av, k, Xs, r, Bs, G.lcyc, st);
         k_norm2<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, G.lcyc, pt2);
@@ -1238,59 +1350,64 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
 sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
 {
     G.m = m;
-    const size_t hsz = (size_t)k * (m + 1) * m + 2 * (size_t)k * m + (size_t)k * (m + 1) + 2 * (size_t)(m + 1) * k +
-                       (size_t)k * m + 2 * (size_t)k;
+    const size_t km1 = (size_t)k * (m + 1);
+    const size_t hsz = 2 * (size_t)k * (m + 1) * m + 2 * (size_t)k * m + 4 * km1 + (size_t)k * m + 2 * (size_t)k;
+    const size_t isz = 5 * (size_t)k + 2 * (size_t)(k + 1) + 2;
     SAI_TRY(hb.alloc(sizeof(double) * hsz, st, true));
-    SAI_TRY(ib.alloc(sizeof(int) * (6 * k + 3 * (k + 1) + 1), st, true));
+    SAI_TRY(ib.alloc(sizeof(int) * isz, st, true));
     SAI_CUDA(cudaMemsetAsync(hb.p, 0, sizeof(double) * hsz, st));
-    SAI_CUDA(cudaMemsetAsync(ib.p, 0, sizeof(int) * (6 * k + 3 * (k + 1) + 1), st));
+    SAI_CUDA(cudaMemsetAsync(ib.p, 0, sizeof(int) * isz, st));
     double* hp = hb.as<double>();
     G.H = hp;
+    hp += (size_t)k * (m + 1) * m;
+    G.Hu = hp;
     hp += (size_t)k * (m + 1) * m;
     G.cs = hp;
     hp += (size_t)k * m;
     G.sn = hp;
     hp += (size_t)k * m;
     G.g = hp;
-    hp += (size_t)k * (m + 1);
-    G.h = hp;
-    hp += 2 * (size_t)(m + 1) * k;
-    G.u = hp;
+    hp += km1;
+    G.hp = hp;
+    hp += km1;
+    G.sco = hp;
+    hp += km1;
+    G.cco = hp;
+    hp += km1;
+    G.y = hp;
     hp += (size_t)k * m;
-    G.ww = hp;
-    G.hn2 = hp + k;
+    G.alpha = hp;
+    G.dco = hp + k;
     int* ip = ib.as<int>();
     G.cyc = ip;
     G.adv = ip + k;
     G.jd = ip + 2 * k;
     G.done = ip + 3 * k;
     G.conv = ip + 4 * k;
-    G.reo = ip + 5 * k;
-    G.lcyc = ip + 6 * k;
+    G.lcyc = ip + 5 * k;
     G.ladv = G.lcyc + (k + 1);
-    G.lreo = G.ladv + (k + 1);
-    G.jdev = G.lreo + (k + 1);
+    G.jdev = G.ladv + (k + 1);
+    G.bcnt = G.jdev + 1;
     return SAI_OK;
 }
 
 template <class T>
-sai_status gm_work_alloc(size_t blk, int64_t n, int64_t ld, int m, Buf& vb, Buf& wb, GmWork<T>& Wk, cudaStream_t st)
+sai_status gm_work_alloc(size_t blk, int m, Buf& vb, Buf& wb, GmWork<T>& Wk, cudaStream_t st)
 {
     // basis blocks are vs = blk + 96 values apart (keeps the blocks off a
-    // common power-of-two stride); the whole basis starts zeroed so the
-    // padding rows [n, ld) of every vector stay zero
+    // common power-of-two stride); everything starts zeroed so the padding
+    // rows [n, ld) of every vector stay zero
     const int64_t vs = (int64_t)blk + 96;
     SAI_TRY(vb.alloc(sizeof(T) * (size_t)vs * (m + 1) + 16, st, true));
-    SAI_TRY(wb.alloc(sizeof(T) * blk * 3 + 16, st, true));
-    SAI_CUDA(cudaMemsetAsync(wb.p, 0, sizeof(T) * blk * 3, st));
+    SAI_TRY(wb.alloc(sizeof(T) * blk * 4 + 16, st, true));
+    SAI_CUDA(cudaMemsetAsync(wb.p, 0, sizeof(T) * blk * 4, st));
     SAI_CUDA(cudaMemsetAsync(vb.p, 0, sizeof(T) * (size_t)vs * (m + 1), st));
-    (void)n;
-    (void)ld;
     Wk.B.V = vb.as<T>();
     Wk.B.vs = vs;
     Wk.r = wb.as<T>();
-    Wk.w = Wk.r + blk;
-    Wk.z = Wk.w + blk;
+    Wk.t = Wk.r + blk;
+    Wk.z = Wk.t + blk;
+    Wk.w = Wk.z + blk;
     return SAI_OK;
 }
 
@@ -1312,12 +1429,12 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         int dev = 0;
         SAI_CUDA(cudaGetDevice(&dev));
         SAI_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
-        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_proj[0], k_gm_proj<double>, IT_WARPS * 32, 0));
-        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_proj[1], k_gm_proj<float>, IT_WARPS * 32, 0));
-        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[0], k_gm_upd<double>, IT_WARPS * 32, 0));
-        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[1], k_gm_upd<float>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_dots[0], k_dc_dots<double>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_dots[1], k_dc_dots<float>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[0], k_dc_update<double>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[1], k_dc_update<float>, IT_WARPS * 32, 0));
         for (int i = 0; i < 2; ++i) {
-            if (g_res_proj[i] < 1) g_res_proj[i] = 1;
+            if (g_res_dots[i] < 1) g_res_dots[i] = 1;
             if (g_res_upd[i] < 1) g_res_upd[i] = 1;
         }
     }
@@ -1345,8 +1462,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     Buf sysd, sysi, part, part2, flag, Bs, Xs, capb;
     SAI_TRY(sysd.alloc(sizeof(double) * 7 * k, st, true));
     SAI_TRY(sysi.alloc(sizeof(int) * (5 * k + 3 * (k + 1)), st, true));
-    SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * (GM_MAXM + 2), st, true));
-    SAI_TRY(part2.alloc(sizeof(double) * (size_t)k * (I.nchu > 2 * I.nch ? I.nchu : 2 * I.nch), st, true));
+    SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * (PS > 2 ? PS : 2), st, true));
+    SAI_TRY(part2.alloc(sizeof(double) * (size_t)k * I.nch * 2, st, true));
     SAI_TRY(flag.alloc(sizeof(int) * 4, st, true));
     SAI_TRY(Bs.alloc(sizeof(double) * blk + 8, st, true));
     SAI_TRY(Xs.alloc(sizeof(double) * blk + 8, st, true));
@@ -1400,7 +1517,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         Buf hb, ibuf, vb, wb;
         GmWork<double> Wk;
         SAI_TRY(gm_alloc(k, prm->restart, hb, ibuf, G, st));
-        SAI_TRY(gm_work_alloc<double>(blk, n, ld, prm->restart, vb, wb, Wk, st));
+        SAI_TRY(gm_work_alloc<double>(blk, prm->restart, vb, wb, Wk, st));
         SAI_TRY(gmres_run<double>(I, k, prm->restart, A64, Bsd, Xsd, Wk, S, G, cap, pt, pt2, fl, D, st));
     } else {
         // GMRES with iterative refinement: FP64 residual, correction and stop
@@ -1410,7 +1527,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         Buf hb, ibuf, vb, wb, a32, m32, r64b, v32b, irb, ird;
         GmWork<float> Wk;
         SAI_TRY(gm_alloc(k, prm->restart, hb, ibuf, G, st));
-        SAI_TRY(gm_work_alloc<float>(blk, n, ld, prm->restart, vb, wb, Wk, st));
+        SAI_TRY(gm_work_alloc<float>(blk, prm->restart, vb, wb, Wk, st));
         SAI_TRY(a32.alloc(sizeof(float) * (size_t)(h->nnz_At > 0 ? h->nnz_At : 1), st, true));
         SAI_TRY(m32.alloc(sizeof(float) * (size_t)(P->nnz > 0 ? P->nnz : 1), st, true));
         SAI_TRY(r64b.alloc(sizeof(double) * blk + 8, st, true));
