@@ -224,6 +224,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def nvtx(torch, label):
+    """Opens (label) or closes (None) an NVTX range; a build without NVTX skips it."""
+    try:
+        if label:
+            torch.cuda.nvtx.range_push(label)
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def run_ours(args):
     import torch
     import paper_1211_6866_gb300 as sai
@@ -257,12 +268,14 @@ def run_ours(args):
     step(PLAIN_KW)
     torch.cuda.synchronize()
 
-    def timed(form, nsteps, profile):
+    def timed(form, nsteps, profile, label=None):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         if profile:
             sai.profile_begin()
+        if label:  # NVTX range: lets ncu --nvtx-include select exactly the timed launches
+            nvtx(torch, label)
         ms, reps = [], []
         for _ in range(nsteps):
             flush.zero_()
@@ -274,6 +287,8 @@ def run_ours(args):
             ms.append(e0.elapsed_time(e1))
             reps.append(res)
         torch.cuda.synchronize()
+        if label:
+            nvtx(torch, None)
         prof = sai.profile_end() if profile else None
         total = float(np.sum(ms))
         if dist:
@@ -286,7 +301,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = sai.launch_count()
-    ms_step, reps, _ = timed(OPT_KW, args.steps, False)
+    ms_step, reps, _ = timed(OPT_KW, args.steps, False, "bench_timed")
     launches = sai.launch_count() - l0
     clk = clocks.stop()
     # per-kernel durations: one more step with the library's event profile

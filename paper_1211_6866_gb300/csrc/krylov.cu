@@ -705,6 +705,10 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* 
 
 // Partials: slot 2i = v_i^T u, 2i+1 = v_i^T z (i < j), 2*GM_MAXM = u^T u,
 // 2*GM_MAXM+1 = u^T z, stored at part[((c*PS) + slot)*nch + q] for chunk q.
+// One block per item (chunk q, system, group g of PD basis vectors), g
+// fastest so the items of one chunk read its rows of u and z from cache; the
+// block's IT_WARPS warps take interleaved 16-byte row vectors of the chunk and
+// their sums are combined in warp order through shared memory.
 template <class T>
 __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __restrict__ u, const T* __restrict__ z,
                                                           Basis<T> Bv, const int* list, const int* jdev,
@@ -712,15 +716,13 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __r
 {
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
+    constexpr int NR = 2 * PD + 2;
+    __shared__ T red[IT_WARPS][NR];
     const int j = *jdev;
     const int ng = j > 0 ? (j + PD - 1) / PD : 1;  // groups of PD basis vectors
     const int cnt = list[0];
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // items (chunk q, system, group g), g fastest: the items of one chunk read
-    // its rows of u and z from cache
-    for (int64_t it = w0; it < (int64_t)cnt * I.nch * ng; it += nw) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < (int64_t)cnt * I.nch * ng; it += gridDim.x) {
         const int g = (int)(it % ng);
         const int64_t rest = it / ng;
         const int c = list[1 + (int)(rest % cnt)];
@@ -735,7 +737,7 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __r
 #pragma unroll
         for (int i = 0; i < PD; ++i) as[i] = ac[i] = 0;
         T uu = 0, uz = 0;
-        for (int64_t row = r0 + (int64_t)lane * VW; row < r1v; row += 32 * VW) {
+        for (int64_t row = r0 + (int64_t)threadIdx.x * VW; row < r1v; row += IT_WARPS * 32 * VW) {
             const VT uv = *reinterpret_cast<const VT*>(u + o + row);
             const VT zv = *reinterpret_cast<const VT*>(z + o + row);
             VT vv[PD];
@@ -761,18 +763,26 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __r
         uu = warp_sum_t(uu);
         uz = warp_sum_t(uz);
         if (lane == 0) {
-            double* pc = part + (size_t)c * PS * I.nch + q;
 #pragma unroll
-            for (int i = 0; i < PD; ++i)
-                if (i < ni) {
-                    pc[(size_t)(2 * (i0 + i)) * I.nch] = (double)as[i];
-                    pc[(size_t)(2 * (i0 + i) + 1) * I.nch] = (double)ac[i];
-                }
-            if (g == 0) {
-                pc[(size_t)(2 * GM_MAXM) * I.nch] = (double)uu;
-                pc[(size_t)(2 * GM_MAXM + 1) * I.nch] = (double)uz;
+            for (int i = 0; i < PD; ++i) {
+                red[wid][2 * i] = as[i];
+                red[wid][2 * i + 1] = ac[i];
             }
+            red[wid][2 * PD] = uu;
+            red[wid][2 * PD + 1] = uz;
         }
+        __syncthreads();
+        const int nsl = 2 * ni + (g == 0 ? 2 : 0);
+        if ((int)threadIdx.x < nsl) {
+            const int t = threadIdx.x;
+            const int widx = t < 2 * ni ? t : 2 * PD + (t - 2 * ni);
+            const int slot = t < 2 * ni ? 2 * i0 + t : 2 * GM_MAXM + (t - 2 * ni);
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < IT_WARPS; ++w) sum += (double)red[w][widx];
+            part[((size_t)c * PS + slot) * I.nch + q] = sum;
+        }
+        __syncthreads();
     }
 }
 
@@ -824,8 +834,18 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         for (int t = wid; t < ns; t += nwarp) {
             const int slot = t < 2 * j ? t : 2 * GM_MAXM + (t - 2 * j);
             const double* p = part + ((size_t)c * PS + slot) * nch;
-            double sum = 0.0;
-            for (int q = lane; q < nch; q += 32) sum += p[q];
+            // eight independent loads in flight per lane, summed in a fixed order
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = 0.0;
+            for (int q0 = 0; q0 < nch; q0 += 8 * 32) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = q0 + u * 32 + lane;
+                    if (q < nch) v[u] += p[q];
+                }
+            }
+            double sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
             sum = warp_sum(sum);
             if (lane == 0) red[t] = sum;
         }
@@ -903,17 +923,22 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         __syncthreads();
         if (!stop) {
             // first-pass coefficients of column j and the update coefficients;
-            // (Hbar s)_i = sum_{q >= max(i-1,0)} Hbar(i,q) s_q over the final columns q < j
+            // (Hbar s)_i = sum_{q >= max(i-1,0)} Hbar(i,q) s_q over the final columns q < j,
+            // one warp per row i, lanes over q
             double* hpc = G.hp + (size_t)c * (m + 1);
-            for (int i = tid; i <= j; i += blockDim.x) {
+            for (int i = wid; i <= j; i += nwarp) {
                 double hs = 0.0;
-                for (int q = i > 0 ? i - 1 : 0; q < j; ++q) hs = fma(Huc[(size_t)q * (m + 1) + i], red[2 * q], hs);
-                const double cz = i < j ? red[2 * i + 1] : d;
-                hpc[i] = (cz - hs) / al;
-                if (i < j) {
-                    G.sco[(size_t)c * (m + 1) + i] = red[2 * i];
-                    G.cco[(size_t)c * (m + 1) + i] = red[2 * i + 1];
+                for (int q = (i > 0 ? i - 1 : 0) + lane; q < j; q += 32)
+                    hs = fma(Huc[(size_t)q * (m + 1) + i], red[2 * q], hs);
+                hs = warp_sum(hs);
+                if (lane == 0) {
+                    const double cz = i < j ? red[2 * i + 1] : d;
+                    hpc[i] = (cz - hs) / al;
                 }
+            }
+            for (int i = tid; i < j; i += blockDim.x) {
+                G.sco[(size_t)c * (m + 1) + i] = red[2 * i];
+                G.cco[(size_t)c * (m + 1) + i] = red[2 * i + 1];
             }
             if (tid == 0) {
                 G.alpha[c] = al;
@@ -970,6 +995,9 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_update(Items I, T* __restr
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
         T* Vj = Bv.V + (int64_t)j * Bv.vs + o;
         for (int64_t row = r0 + (int64_t)lane * VW; row < r1v; row += 32 * VW) {
+            // u and z first: their loads overlap the basis loop
+            const VT uv = *reinterpret_cast<const VT*>(u + o + row);
+            const VT zv = *reinterpret_cast<const VT*>(z + o + row);
             VT a_s = Vec<T>::zero(), a_c = Vec<T>::zero();
             for (int i0 = 0; i0 < j; i0 += PJ) {
                 const int ni = min(PJ, j - i0);
@@ -985,8 +1013,6 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_update(Items I, T* __restr
                         a_c = Vec<T>::axpy(hc[wid][i0 + i], vv[i], a_c);
                     }
             }
-            const VT uv = *reinterpret_cast<const VT*>(u + o + row);
-            const VT zv = *reinterpret_cast<const VT*>(z + o + row);
             const VT v = Vec<T>::scale(ia, Vec<T>::sub(uv, a_s));
             const VT un = Vec<T>::scale(ia, Vec<T>::axpy(-dd, v, Vec<T>::sub(zv, a_c)));
             *reinterpret_cast<VT*>(Vj + row) = v;
@@ -1226,7 +1252,7 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
     }
     const int fp = sizeof(T) == 4;
     const int64_t pcap = (int64_t)g_sms * g_res_dots[fp], ucap = (int64_t)g_sms * g_res_upd[fp];
-    int64_t pb = ((int64_t)I.nch * k * ((G.m - 1) / PD + 1) + IT_WARPS - 1) / IT_WARPS;
+    int64_t pb = (int64_t)I.nch * k * ((G.m - 1) / PD + 1);
     int64_t ub = ((int64_t)I.nchu * k + IT_WARPS - 1) / IT_WARPS;
     pb = pb < pcap ? pb : pcap;
     ub = ub < ucap ? ub : ucap;
