@@ -182,6 +182,9 @@ typedef struct {
                           r = b - A~ x, x += ||r|| d and every stop test in FP64;
                           maxit then bounds the total inner iterations */
     double inner_tol;  /* relative inner tolerance of the refined form; <= 0 -> 1e-4 */
+    int32_t transpose; /* 0: solve A~ y = b with right preconditioner M (Procedure *);
+                          1: solve A~^T y = b with right preconditioner M^T (the
+                          adjoint solves of sai_backward) */
 } sai_krylov_params;
 
 /* B, X: n x k row-major device blocks. thr, iters, status: host arrays of k.
@@ -249,6 +252,43 @@ typedef struct {
  * pass capacity in iters_cap (counts beyond it are not written). */
 sai_status sai_solve(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
                      int32_t* iters, int32_t iters_cap, sai_solve_report* rep, sai_stream_t stream);
+
+/* ----------------------------------------------------------------------
+ * Steps 3-5 of Procedure * on an existing split and preconditioner (one
+ * split and one M serve any number of right-hand sides), and the backward
+ * pass of x = A^{-1} b.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    sai_krylov_params krylov;
+    double eps;                   /* Theorem 2 thresholds as in sai_solve_params */
+} sai_stage_params;
+
+/* x = A^{-1} b from the s+1 solves with h's A~ and P's M, the Theorem 2
+ * thresholds (from ||b||), SMW recovery and rr. A: the matrix h was split
+ * from (device CSC, used for rr only). b, x: device n-vectors. rep: split and
+ * precond fields from the handles, ms_split = ms_build = 0. iters: as in
+ * sai_solve. */
+sai_status sai_solve_with(const sai_csc_view* A, sai_split h, sai_precond P, const double* b,
+                          const sai_stage_params* prm, double* x, int32_t* iters, int32_t iters_cap,
+                          sai_solve_report* rep, sai_stream_t stream);
+
+/* Backward pass of x = A^{-1} b for a loss L with g = dL/dx. Not in the
+ * paper: the adjoint of Procedure * built from the same pieces. With
+ * A^T = A~^T + V U^T, lambda = A^{-T} g is recovered by Theorem 1 applied to
+ * A^T:
+ *   [yhat, What] = A~^{-T} [g, e_J1 .. e_Js]      (s+1 solves, preconditioner M^T)
+ *   lambda = yhat - What (I + U^T What)^{-1} (U^T yhat)
+ * with the Theorem 2 thresholds taken from ||g||. Outputs (device):
+ *   lambda     n      = dL/db
+ *   grad_vals  nnz(A) = dL/dA on A's stored pattern, aligned with A->val:
+ *                       -lambda_i x_j for the entry (i, j)
+ * A: the matrix h was split from (device CSC); x: the forward solution
+ * (device n-vector). rep->rr = ||g - A^T lambda|| / ||g||, rep->c = ||z||,
+ * rep->status / iter_max / ms_krylov / ms_smw as in sai_solve; iters: the
+ * s+1 adjoint iteration counts. grad_vals may be NULL (skipped). */
+sai_status sai_backward(const sai_csc_view* A, sai_split h, sai_precond P, const double* x, const double* g,
+                        const sai_stage_params* prm, double* lambda, double* grad_vals, int32_t* iters,
+                        int32_t iters_cap, sai_solve_report* rep, sai_stream_t stream);
 
 /* ----------------------------------------------------------------------
  * Diagnostics (not part of the paper's method): launch counting and the

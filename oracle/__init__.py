@@ -86,6 +86,7 @@ class _In:
         self.s = _Csc(A.shape[0], A.shape[1], _ptr(self.indptr, _i64p), _ptr(self.indices, _i32p),
                       _ptr(self.data, _f64p))
         self.shape = A.shape
+        self.nnz = int(A.nnz)
 
 
 def _take(c):
@@ -249,3 +250,58 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
                                     _ptr(iters, _i32p), C.byref(rep)))
     report = {f: getattr(rep, f) for f, _ in _SolveReport._fields_}
     return x, iters[: rep.s + 1].copy(), report
+
+
+def csc_transpose(A):
+    """A^T as a canonical CSC (the oracle's own transpose)."""
+    a = _In(A)
+    out = _Csc()
+    _check("csc_transpose", lib().orc_csc_transpose(C.byref(a.s), C.byref(out)))
+    return _take(out)
+
+
+def smw_adjoint(yhat, W, U):
+    """Theorem 1 on A^T = A~^T + V U^T. W: (n, s) array, U: n x s CSC.
+    Returns (lambda, z, c)."""
+    yhat = np.ascontiguousarray(yhat, dtype=np.float64)
+    n = yhat.shape[0]
+    u = _In(U)
+    s = u.shape[1]
+    Wc = np.asfortranarray(np.asarray(W, dtype=np.float64).reshape(n, s))
+    lam = np.zeros(n)
+    z = np.zeros(max(s, 1))
+    c = C.c_double()
+    _check("smw_adjoint", lib().orc_smw_adjoint(n, s, _ptr(yhat, _f64p), Wc.ctypes.data_as(_f64p), C.byref(u.s),
+                                                _ptr(lam, _f64p), _ptr(z, _f64p), C.byref(c)))
+    return lam, z[:s], c.value
+
+
+def backward(A, x, g, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0,
+             abs_tau=-1.0, delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10):
+    """Backward pass of x = A^{-1} b (adjoint of Procedure *).
+    Returns (lambda = dL/db, grad_vals aligned with A's CSC values, iters[s+1], report)."""
+    a = _In(A)
+    n = a.shape[1]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
+                       _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
+                       0 if krylov == "bicgstab" else 1, restart, maxit, eps)
+    lam = np.zeros(n)
+    gv = np.zeros(a.nnz)
+    iters = np.zeros(n + 1, np.int32)
+    rep = _SolveReport()
+    _check("backward", lib().orc_backward(C.byref(a.s), _ptr(x, _f64p), _ptr(g, _f64p), C.byref(prm),
+                                          _ptr(lam, _f64p), _ptr(gv, _f64p), _ptr(iters, _i32p), C.byref(rep)))
+    report = {f: getattr(rep, f) for f, _ in _SolveReport._fields_}
+    return lam, gv, iters[: rep.s + 1].copy(), report
+
+
+def backward_dense(A, x, g):
+    """The plain definition, small n only: lambda = A^{-T} g by dense LU
+    (numpy.linalg.solve), dL/dA_ij = -lambda_i x_j on A's stored pattern.
+    Returns (lambda, grad_vals aligned with A's canonical CSC values)."""
+    Ac = as_csc(A)
+    lam = np.linalg.solve(Ac.toarray().T, np.asarray(g, dtype=np.float64))
+    cols = np.repeat(np.arange(Ac.shape[1]), np.diff(Ac.indptr))
+    return lam, -lam[Ac.indices] * np.asarray(x, dtype=np.float64)[cols]

@@ -9,7 +9,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["oracle_core.c", "oracle_split.c", "oracle_sai.c", "oracle_krylov.c", "oracle_smw.c"]
+SOURCES = ["oracle_core.c", "oracle_split.c", "oracle_sai.c", "oracle_krylov.c", "oracle_smw.c", "oracle_backward.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -162,6 +162,24 @@ typedef struct {
 int orc_solve(const orc_csc* A, const double* b, const orc_solve_params* prm,
               double* x_out, int32_t* iters_out, orc_solve_report* rep);
 
+/* ---- backward pass (not in the paper: the adjoint of Procedure *) ------- */
+
+/* B = A^T in CSC (arrays malloc'd, free with orc_csc_free). */
+int orc_csc_transpose(const orc_csc* A, orc_csc* B);
+
+/* Theorem 1 on A^T = A~^T + V U^T:
+ * lambda = yhat - W (I + U^T W)^{-1} (U^T yhat); W n x s column-major, U n x s CSC. */
+int orc_smw_adjoint(int32_t n, int32_t s, const double* yhat, const double* W, const orc_csc* U,
+                    double* lambda_out, double* z_out, double* c_out);
+
+/* Backward pass of x = A^{-1} b for g = dL/dx: split and M as in orc_solve,
+ * [yhat, W] = A~^{-T}[g, e_J] by the s+1 solves with right preconditioner
+ * M^T and the Theorem 2 thresholds from ||g||, lambda by orc_smw_adjoint,
+ * grad_vals[q] = -lambda_i x_j for A's stored entry q = (i, j) (may be NULL).
+ * rep->rr = ||g - A^T lambda|| / ||g||, rep->c = ||z||. */
+int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_solve_params* prm,
+                 double* lambda_out, double* grad_vals, int32_t* iters_out, orc_solve_report* rep);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,7 +66,11 @@ class _PrecondInfo(C.Structure):
 
 class _KrylovParams(C.Structure):
     _fields_ = [("method", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32), ("precision", C.c_int32),
-                ("inner_tol", C.c_double)]
+                ("inner_tol", C.c_double), ("transpose", C.c_int32)]
+
+
+class _StageParams(C.Structure):
+    _fields_ = [("krylov", _KrylovParams), ("eps", C.c_double)]
 
 
 class _SolveParams(C.Structure):
@@ -124,13 +128,17 @@ def load():
     L.sai_rel_resid.argtypes = [C.POINTER(_CscView), dp, dp, C.POINTER(C.c_double), vp]
     L.sai_solve.argtypes = [C.POINTER(_CscView), dp, C.POINTER(_SolveParams), dp, C.POINTER(C.c_int32), i32,
                             C.POINTER(_SolveReport), vp]
+    L.sai_solve_with.argtypes = [C.POINTER(_CscView), vp, vp, dp, C.POINTER(_StageParams), dp,
+                                 C.POINTER(C.c_int32), i32, C.POINTER(_SolveReport), vp]
+    L.sai_backward.argtypes = [C.POINTER(_CscView), vp, vp, dp, dp, C.POINTER(_StageParams), dp, dp,
+                               C.POINTER(C.c_int32), i32, C.POINTER(_SolveReport), vp]
     L.sai_launch_count.restype = C.c_uint64
     L.sai_launch_count.argtypes = []
     L.sai_profile_begin.argtypes = []
     L.sai_profile_end.argtypes = [C.POINTER(_ProfReport)]
     for f in ("sai_profile_begin", "sai_profile_end", "sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
               "sai_precond_get_info", "sai_precond_copy_out", "sai_krylov_solve", "sai_smw_recover",
-              "sai_rel_resid", "sai_solve"):
+              "sai_rel_resid", "sai_solve", "sai_solve_with", "sai_backward"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -263,8 +271,10 @@ def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10, precision=0):
     return Precond(h.value)
 
 
-def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500, precision=0, inner_tol=0.0):
-    """Solves A~ X = B (n x k, row-major, device) with right preconditioner M.
+def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500, precision=0, inner_tol=0.0,
+                 transpose=False):
+    """Solves A~ X = B (n x k, row-major, device) with right preconditioner M,
+    or A~^T X = B with M^T when transpose is set.
     precision 1 (GMRES only): FP32 inner solves refined in FP64.
     Returns (X, iters list, status list, overall status)."""
     L = load()
@@ -274,7 +284,7 @@ def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500, precisio
     thr_a = (C.c_double * k)(*[float(t) for t in thr])
     it = (C.c_int32 * k)()
     stt = (C.c_int32 * k)()
-    prm = _KrylovParams(method, restart, maxit, precision, inner_tol)
+    prm = _KrylovParams(method, restart, maxit, precision, inner_tol, int(bool(transpose)))
     st = _check("sai_krylov_solve", L.sai_krylov_solve(sp._h, P._h, k, _p(B), thr_a, C.byref(prm), _p(X), it, stt,
                                                        _stream()), allow=(SAI_MAXITER, SAI_BREAKDOWN))
     return X, list(it), list(stt), st
@@ -311,7 +321,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
                        _PsaiParams(delta, tol, tol_mode, lmax, sai_precision),
                        _KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit, krylov_precision,
-                                     inner_tol), eps)
+                                     inner_tol, 0), eps)
     cap = A.n + 1
     iters = (C.c_int32 * cap)()
     rep = _SolveReport()
@@ -325,6 +335,86 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
                   ms_split=rep.ms_split, ms_build=rep.ms_build, ms_krylov=rep.ms_krylov, ms_smw=rep.ms_smw,
                   build_ms=rep.precond.build_ms)
     return x, list(iters[: s + 1]), report
+
+
+def _report(rep, st):
+    return dict(s=rep.split.s, p=rep.split.p, tau=rep.split.tau, nnz_At=rep.split.nnz_At, nnz_U=rep.split.nnz_U,
+                nnz_M=rep.precond.nnz_M, n_c=rep.precond.n_c, l_m=rep.precond.l_m, n_tier=list(rep.precond.n_tier),
+                status=st, iter_max=rep.iter_max, c=rep.c, rr=rep.rr, ms_split=rep.ms_split, ms_build=rep.ms_build,
+                ms_krylov=rep.ms_krylov, ms_smw=rep.ms_smw, build_ms=rep.precond.build_ms)
+
+
+def _stage(krylov, eps, maxit, restart, krylov_precision, inner_tol):
+    return _StageParams(_KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit, krylov_precision,
+                                      inner_tol, 0), eps)
+
+
+def solve_with(A, sp, P, b, krylov="bicgstab", eps=1e-8, maxit=500, restart=50, krylov_precision=0, inner_tol=0.0,
+               x=None):
+    """Steps 3-5 of Procedure * on an existing split sp of A and preconditioner P.
+    Returns (x, iters list, report dict)."""
+    L = load()
+    if x is None:
+        x = torch.empty(A.n, dtype=torch.float64, device=b.device)
+    prm = _stage(krylov, eps, maxit, restart, krylov_precision, inner_tol)
+    cap = sp.s + 1
+    iters = (C.c_int32 * cap)()
+    rep = _SolveReport()
+    v = A.view()
+    st = _check("sai_solve_with", L.sai_solve_with(C.byref(v), sp._h, P._h, _p(b), C.byref(prm), _p(x), iters, cap,
+                                                   C.byref(rep), _stream()), allow=(SAI_MAXITER, SAI_BREAKDOWN))
+    return x, list(iters[:cap]), _report(rep, st)
+
+
+def backward(A, sp, P, x, g, krylov="bicgstab", eps=1e-8, maxit=500, restart=50, krylov_precision=0,
+             inner_tol=0.0, grad_vals=True):
+    """Backward pass of x = A^{-1} b for g = dL/dx: the s+1 transposed solves
+    with M^T and Theorem 1 on A^T = A~^T + V U^T. Returns
+    (lambda = dL/db, dL/dA values on A's pattern or None, iters list, report);
+    report["rr"] = ||g - A^T lambda|| / ||g||."""
+    L = load()
+    lam = torch.empty(A.n, dtype=torch.float64, device=g.device)
+    gv = torch.empty(A.nnz, dtype=torch.float64, device=g.device) if grad_vals else None
+    prm = _stage(krylov, eps, maxit, restart, krylov_precision, inner_tol)
+    cap = sp.s + 1
+    iters = (C.c_int32 * cap)()
+    rep = _SolveReport()
+    v = A.view()
+    st = _check("sai_backward", L.sai_backward(C.byref(v), sp._h, P._h, _p(x), _p(g.contiguous()), C.byref(prm),
+                                               _p(lam), _p(gv), iters, cap, C.byref(rep), _stream()),
+                allow=(SAI_MAXITER, SAI_BREAKDOWN))
+    return lam, gv, list(iters[:cap]), _report(rep, st)
+
+
+class SparseSolve(torch.autograd.Function):
+    """x = A^{-1} b through Procedure * with gradients for A's stored values
+    and for b. forward(col_ptr, row_idx, val, b, opts): opts is a dict of
+    split / build / solve keywords (sai, delta, mn, max_aug, tol, tol_mode,
+    lmax, krylov, eps, maxit, restart, thresh_mult, abs_tau)."""
+
+    @staticmethod
+    def forward(ctx, col_ptr, row_idx, val, b, opts):
+        o = dict(opts)
+        A = CscMatrix(b.numel(), col_ptr, row_idx, val.detach().contiguous())
+        sp = split(A, thresh_mult=o.get("thresh_mult", 10.0), abs_tau=o.get("abs_tau", -1.0))
+        if o.get("sai", "spai") == "spai":
+            P = build_spai(sp, delta=o.get("delta", 0.4), mn=o.get("mn", 5), max_aug=o.get("max_aug", 10))
+        else:
+            P = build_psai(sp, delta=o.get("delta", 0.4), tol=o.get("tol", 0.0), tol_mode=o.get("tol_mode", 0),
+                           lmax=o.get("lmax", 10))
+        kw = dict(krylov=o.get("krylov", "bicgstab"), eps=o.get("eps", 1e-8), maxit=o.get("maxit", 500),
+                  restart=o.get("restart", 50))
+        x, _, rep = solve_with(A, sp, P, b.detach().contiguous(), **kw)
+        ctx.state = (A, sp, P, kw)
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        A, sp, P, kw = ctx.state
+        lam, gv, _, _ = backward(A, sp, P, x, gx.contiguous(), grad_vals=ctx.needs_input_grad[2], **kw)
+        return None, None, gv, lam, None
 
 
 def launch_count():

@@ -349,68 +349,59 @@ struct Ev {
     ~Ev() { cudaEventDestroy(e); }
 };
 
-sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
-                      int32_t* iters, int32_t iters_cap, sai_solve_report* rep, cudaStream_t st)
+// B = [g, e_J1 .. e_Js]: right-hand sides of the adjoint solves (V's columns)
+__global__ void k_set_units(int32_t s, const int32_t* J, double* B)
 {
-    if (!A || !prm || !rep || (A->n > 0 && (!b || !x))) return SAI_INVALID_ARG;
-    *rep = sai_solve_report{};
-    Ev e0, e1, e2, e3, e4;
-    SAI_CUDA(cudaEventRecord(e0.e, st));
-    sai_split_s h;
-    SAI_TRY(sai_split_build(A, &prm->split, st, true, &h));
-    SAI_CUDA(cudaEventRecord(e1.e, st));
-    sai_precond_s P;
-    if (prm->sai == 0) SAI_TRY(sai_spai_build(&h, &prm->spai, st, true, &P));
-    else SAI_TRY(sai_psai_build(&h, &prm->psai, st, true, &P));
-    SAI_CUDA(cudaEventRecord(e2.e, st));
-    const int32_t n = h.n, s = h.s, k = s + 1;
-    Buf Bb, Yb, nb;
-    SAI_TRY(Bb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
-    SAI_TRY(Yb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
-    SAI_TRY(nb.alloc(sizeof(double), st, true));
-    if (n > 0) k_fill_rhs<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, b, nullptr, nullptr, nullptr, Bb.as<double>());
-    if (s > 0)
-        k_scatter_U<<<SAI_GRID(s), 256, 0, st>>>(s, h.U_cp.as<int64_t>(), h.U_ri.as<int32_t>(), h.U_v.as<double>(),
-                                       Bb.as<double>());
-    k_sumsq<<<SAI_GRID(1), 1024, 0, st>>>(n, b, nb.as<double>());
-    SAI_CUDA(cudaGetLastError());
-    double bb = 0.0;
-    SAI_CUDA(cudaMemcpyAsync(&bb, nb.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-    SAI_CUDA(cudaStreamSynchronize(st));
-    const double bnorm = sqrt(bb);
-    // Theorem 2 with c = 1: eqs. (stopb) and (stopU2)
-    double* thr = (double*)malloc(sizeof(double) * k);
-    int32_t* it = (int32_t*)malloc(sizeof(int32_t) * k);
-    int32_t* stt = (int32_t*)malloc(sizeof(int32_t) * k);
-    if (!thr || !it || !stt) {
-        free(thr);
-        free(it);
-        free(stt);
-        return SAI_OOM;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < s) B[(int64_t)J[t] * (s + 1) + 1 + t] = 1.0;
+}
+
+// Per block: sum over its columns j of (g_j - (A^T lambda)_j)^2, one warp per
+// column, warps summed in order.
+__global__ void k_adj_resid(int32_t n, const int64_t* cp, const int32_t* ri, const double* v, const double* lam,
+                            const double* g, double* partial)
+{
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double mine = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * nw + wid; j < n; j += (int64_t)gridDim.x * nw) {
+        double acc = 0.0;
+        for (int64_t q = cp[j] + lane; q < cp[j + 1]; q += 32) acc = fma(v[q], lam[ri[q]], acc);
+        acc = warp_sum(acc);
+        const double r = g[j] - acc;
+        mine = fma(r, r, mine);
     }
-    thr[0] = 0.5 * prm->eps * bnorm;
-    for (int t = 1; t < k; ++t) thr[t] = prm->eps * bnorm / (2.0 * sqrt((double)s));
-    sai_status kst = sai_krylov_run(&h, &P, k, Bb.as<double>(), thr, &prm->krylov, Yb.as<double>(), it, stt, st);
-    SAI_CUDA(cudaEventRecord(e3.e, st));
-    if (kst != SAI_OK && kst != SAI_MAXITER && kst != SAI_BREAKDOWN) {
-        free(thr);
-        free(it);
-        free(stt);
-        return kst;
+    if (lane == 0) sh[wid] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh[w];
+        partial[blockIdx.x] = t;
     }
-    int imax = 0;
-    for (int t = 0; t < k; ++t) {
-        if (it[t] > imax) imax = it[t];
-        if (iters && t < iters_cap) iters[t] = it[t];
+}
+
+__global__ void k_sum_in_order(int32_t m, const double* a, double* out)
+{
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < m; ++i) t += a[i];
+        *out = t;
     }
-    free(thr);
-    free(it);
-    free(stt);
-    double c = 0.0;
-    SAI_TRY(sai_smw_run(&h, Yb.as<double>(), x, &c, st));
-    SAI_CUDA(cudaEventRecord(e4.e, st));
-    double nn[2] = {0.0, 0.0};
-    SAI_TRY(sai_csc_residual_norms(A->n, A->col_ptr, A->row_idx, A->val, b, x, nn, st));
+}
+
+// dL/dA(i,j) = -lambda_i x_j on A's stored pattern, one warp per column
+__global__ void k_grad_vals(int32_t n, const int64_t* cp, const int32_t* ri, const double* lam, const double* x,
+                            double* gv)
+{
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const double xj = x[j];
+    for (int64_t q = cp[j] + lane; q < cp[j + 1]; q += 32) gv[q] = -lam[ri[q]] * xj;
+}
+
+void report_handles(const sai_split_s& h, const sai_precond_s& P, sai_solve_report* rep)
+{
     rep->split.n = h.n;
     rep->split.s = h.s;
     rep->split.p = h.p;
@@ -425,19 +416,193 @@ sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_pa
     rep->precond.l_m = P.l_m;
     for (int q = 0; q < 3; ++q) rep->precond.n_tier[q] = P.n_tier[q];
     rep->precond.build_ms = P.ms;
+}
+
+// ||v||_2 of a device n-vector, read back to the host
+sai_status host_norm(int32_t n, const double* v, double* out, cudaStream_t st)
+{
+    Buf nb;
+    SAI_TRY(nb.alloc(sizeof(double), st, true));
+    k_sumsq<<<SAI_GRID(1), 1024, 0, st>>>(n, v, nb.as<double>());
+    SAI_CUDA(cudaGetLastError());
+    double vv = 0.0;
+    SAI_CUDA(cudaMemcpyAsync(&vv, nb.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    *out = sqrt(vv);
+    return SAI_OK;
+}
+
+// The s+1 solves with the Theorem 2 thresholds (c = 1) of eqs. (stopb) and
+// (stopU2), taken from rnorm = ||b|| (or ||g|| for the adjoint solves).
+// Returns an error, or SAI_OK with *kst the worst system status.
+sai_status stage_solves(const sai_split_s& h, const sai_precond_s& P, const double* B, double rnorm,
+                        const sai_krylov_params& kp, double eps, double* Y, int32_t* iters, int32_t iters_cap,
+                        int32_t* imax, sai_status* kst, cudaStream_t st)
+{
+    const int32_t s = h.s, k = s + 1;
+    double* thr = (double*)malloc(sizeof(double) * k);
+    int32_t* it = (int32_t*)malloc(sizeof(int32_t) * k);
+    int32_t* stt = (int32_t*)malloc(sizeof(int32_t) * k);
+    if (!thr || !it || !stt) {
+        free(thr);
+        free(it);
+        free(stt);
+        return SAI_OOM;
+    }
+    thr[0] = 0.5 * eps * rnorm;
+    for (int t = 1; t < k; ++t) thr[t] = eps * rnorm / (2.0 * sqrt((double)s));
+    const sai_status r = sai_krylov_run(&h, &P, k, B, thr, &kp, Y, it, stt, st);
+    if (r == SAI_OK || r == SAI_MAXITER || r == SAI_BREAKDOWN) {
+        int m = 0;
+        for (int t = 0; t < k; ++t) {
+            if (it[t] > m) m = it[t];
+            if (iters && t < iters_cap) iters[t] = it[t];
+        }
+        *imax = m;
+        *kst = r;
+    }
+    free(thr);
+    free(it);
+    free(stt);
+    return (r == SAI_OK || r == SAI_MAXITER || r == SAI_BREAKDOWN) ? SAI_OK : r;
+}
+
+// Steps 3-5 of Procedure * on the handles: B = [b, u_1..u_s], the solves,
+// SMW recovery, rr.
+sai_status solve_steps(const sai_csc_view* A, const sai_split_s& h, const sai_precond_s& P, const double* b,
+                       const sai_krylov_params& kp, double eps, double* x, int32_t* iters, int32_t iters_cap,
+                       sai_solve_report* rep, cudaEvent_t e_solve, cudaEvent_t e_smw, cudaEvent_t e_end,
+                       cudaStream_t st)
+{
+    const int32_t n = h.n, s = h.s, k = s + 1;
+    Buf Bb, Yb;
+    SAI_TRY(Bb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+    SAI_TRY(Yb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+    if (n > 0) k_fill_rhs<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, b, nullptr, nullptr, nullptr, Bb.as<double>());
+    if (s > 0)
+        k_scatter_U<<<SAI_GRID(s), 256, 0, st>>>(s, h.U_cp.as<int64_t>(), h.U_ri.as<int32_t>(), h.U_v.as<double>(),
+                                       Bb.as<double>());
+    SAI_CUDA(cudaGetLastError());
+    double bnorm = 0.0;
+    SAI_TRY(host_norm(n, b, &bnorm, st));
+    SAI_CUDA(cudaEventRecord(e_solve, st));
+    int32_t imax = 0;
+    sai_status kst = SAI_OK;
+    SAI_TRY(stage_solves(h, P, Bb.as<double>(), bnorm, kp, eps, Yb.as<double>(), iters, iters_cap, &imax, &kst, st));
+    SAI_CUDA(cudaEventRecord(e_smw, st));
+    double c = 0.0;
+    SAI_TRY(sai_smw_run(&h, Yb.as<double>(), x, &c, st));
+    SAI_CUDA(cudaEventRecord(e_end, st));
+    double nn[2] = {0.0, 0.0};
+    SAI_TRY(sai_csc_residual_norms(A->n, A->col_ptr, A->row_idx, A->val, b, x, nn, st));
+    report_handles(h, P, rep);
     rep->status = kst;
     rep->iter_max = imax;
     rep->c = c;
     rep->rr = nn[1] > 0.0 ? sqrt(nn[0] / nn[1]) : sqrt(nn[0]);
+    return kst;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b)
+{
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0.e, e1.e);
-    rep->ms_split = ms;
-    cudaEventElapsedTime(&ms, e1.e, e2.e);
-    rep->ms_build = ms;
-    cudaEventElapsedTime(&ms, e2.e, e3.e);
-    rep->ms_krylov = ms;
-    cudaEventElapsedTime(&ms, e3.e, e4.e);
-    rep->ms_smw = ms;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
+                      int32_t* iters, int32_t iters_cap, sai_solve_report* rep, cudaStream_t st)
+{
+    if (!A || !prm || !rep || (A->n > 0 && (!b || !x))) return SAI_INVALID_ARG;
+    *rep = sai_solve_report{};
+    Ev e0, e1, e2, e3, e4, e5;
+    SAI_CUDA(cudaEventRecord(e0.e, st));
+    sai_split_s h;
+    SAI_TRY(sai_split_build(A, &prm->split, st, true, &h));
+    SAI_CUDA(cudaEventRecord(e1.e, st));
+    sai_precond_s P;
+    if (prm->sai == 0) SAI_TRY(sai_spai_build(&h, &prm->spai, st, true, &P));
+    else SAI_TRY(sai_psai_build(&h, &prm->psai, st, true, &P));
+    SAI_CUDA(cudaEventRecord(e2.e, st));
+    const sai_status r =
+        solve_steps(A, h, P, b, prm->krylov, prm->eps, x, iters, iters_cap, rep, e3.e, e4.e, e5.e, st);
+    if (r != SAI_OK && r != SAI_MAXITER && r != SAI_BREAKDOWN) return r;
+    rep->ms_split = elapsed(e0.e, e1.e);
+    rep->ms_build = elapsed(e1.e, e2.e);
+    rep->ms_krylov = elapsed(e2.e, e4.e);  // includes forming B and ||b||
+    rep->ms_smw = elapsed(e4.e, e5.e);
+    return r;
+}
+
+sai_status solve_with_impl(const sai_csc_view* A, const sai_split_s* h, const sai_precond_s* P, const double* b,
+                           const sai_stage_params* prm, double* x, int32_t* iters, int32_t iters_cap,
+                           sai_solve_report* rep, cudaStream_t st)
+{
+    if (!A || !h || !P || !prm || !rep || A->n != h->n || P->n != h->n || (h->n > 0 && (!b || !x)))
+        return SAI_INVALID_ARG;
+    *rep = sai_solve_report{};
+    Ev e0, e1, e2, e3;
+    SAI_CUDA(cudaEventRecord(e0.e, st));
+    const sai_status r = solve_steps(A, *h, *P, b, prm->krylov, prm->eps, x, iters, iters_cap, rep, e1.e, e2.e,
+                                     e3.e, st);
+    if (r != SAI_OK && r != SAI_MAXITER && r != SAI_BREAKDOWN) return r;
+    rep->ms_krylov = elapsed(e0.e, e2.e);
+    rep->ms_smw = elapsed(e2.e, e3.e);
+    return r;
+}
+
+// Backward pass: Theorem 1 on A^T = A~^T + V U^T (see saismw.h).
+sai_status backward_impl(const sai_csc_view* A, const sai_split_s* h, const sai_precond_s* P, const double* x,
+                         const double* g, const sai_stage_params* prm, double* lambda, double* grad_vals,
+                         int32_t* iters, int32_t iters_cap, sai_solve_report* rep, cudaStream_t st)
+{
+    if (!A || !h || !P || !prm || !rep || A->n != h->n || P->n != h->n ||
+        (h->n > 0 && (!x || !g || !lambda || !A->col_ptr)))
+        return SAI_INVALID_ARG;
+    *rep = sai_solve_report{};
+    const int32_t n = h->n, s = h->s, k = s + 1;
+    Ev e0, e1, e2;
+    SAI_CUDA(cudaEventRecord(e0.e, st));
+    Buf Bb, Yb;
+    SAI_TRY(Bb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+    SAI_TRY(Yb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+    if (n > 0) k_fill_rhs<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, g, nullptr, nullptr, nullptr, Bb.as<double>());
+    if (s > 0) k_set_units<<<SAI_GRID(sai_div_up(s, 256)), 256, 0, st>>>(s, h->J.as<int32_t>(), Bb.as<double>());
+    SAI_CUDA(cudaGetLastError());
+    double gnorm = 0.0;
+    SAI_TRY(host_norm(n, g, &gnorm, st));
+    sai_krylov_params kp = prm->krylov;
+    kp.transpose = 1;
+    int32_t imax = 0;
+    sai_status kst = SAI_OK;
+    SAI_TRY(stage_solves(*h, *P, Bb.as<double>(), gnorm, kp, prm->eps, Yb.as<double>(), iters, iters_cap, &imax,
+                         &kst, st));
+    SAI_CUDA(cudaEventRecord(e1.e, st));
+    double c = 0.0;
+    SAI_TRY(sai_smw_adj_run(h, Yb.as<double>(), lambda, &c, st));
+    if (grad_vals && n > 0)
+        k_grad_vals<<<SAI_GRID(sai_div_up((int64_t)n * 32, 256)), 256, 0, st>>>(n, A->col_ptr, A->row_idx, lambda, x,
+                                                                            grad_vals);
+    SAI_CUDA(cudaEventRecord(e2.e, st));
+    // adjoint residual ||g - A^T lambda|| / ||g||
+    int64_t rb = sai_div_up((int64_t)(n > 0 ? n : 1) * 32, 256);
+    if (rb > 1024) rb = 1024;
+    Buf part, out;
+    SAI_TRY(part.alloc(sizeof(double) * (size_t)rb, st, true));
+    SAI_TRY(out.alloc(sizeof(double), st, true));
+    k_adj_resid<<<SAI_GRID(rb), 256, 0, st>>>(n, A->col_ptr, A->row_idx, A->val, lambda, g, part.as<double>());
+    k_sum_in_order<<<SAI_GRID(1), 32, 0, st>>>((int32_t)rb, part.as<double>(), out.as<double>());
+    SAI_CUDA(cudaGetLastError());
+    double rr2 = 0.0;
+    SAI_CUDA(cudaMemcpyAsync(&rr2, out.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    report_handles(*h, *P, rep);
+    rep->status = kst;
+    rep->iter_max = imax;
+    rep->c = c;
+    rep->rr = gnorm > 0.0 ? sqrt(rr2) / gnorm : sqrt(rr2);
+    rep->ms_krylov = elapsed(e0.e, e1.e);
+    rep->ms_smw = elapsed(e1.e, e2.e);
     return kst;
 }
 
@@ -448,4 +613,20 @@ extern "C" sai_status sai_solve(const sai_csc_view* A, const double* b, const sa
 {
     sai_pool_init_once();
     return solve_impl(A, b, prm, x, iters, iters_cap, rep, S(stream));
+}
+
+extern "C" sai_status sai_solve_with(const sai_csc_view* A, sai_split h, sai_precond P, const double* b,
+                                     const sai_stage_params* prm, double* x, int32_t* iters, int32_t iters_cap,
+                                     sai_solve_report* rep, sai_stream_t stream)
+{
+    sai_pool_init_once();
+    return solve_with_impl(A, h, P, b, prm, x, iters, iters_cap, rep, S(stream));
+}
+
+extern "C" sai_status sai_backward(const sai_csc_view* A, sai_split h, sai_precond P, const double* x,
+                                   const double* g, const sai_stage_params* prm, double* lambda, double* grad_vals,
+                                   int32_t* iters, int32_t iters_cap, sai_solve_report* rep, sai_stream_t stream)
+{
+    sai_pool_init_once();
+    return backward_impl(A, h, P, x, g, prm, lambda, grad_vals, iters, iters_cap, rep, S(stream));
 }

@@ -80,6 +80,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
                           const double* thr, const sai_krylov_params* prm, double* X, int32_t* iters,
                           int32_t* status, cudaStream_t st);
 sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st);
+// Theorem 1 for A^T = A~^T + V U^T: x = yhat - What (I + U^T What)^{-1} (U^T yhat)
+sai_status sai_smw_adj_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st);
 
 void sai_pool_init_once();
 // Library-owned non-blocking stream of the current device (for graph capture), or nullptr.

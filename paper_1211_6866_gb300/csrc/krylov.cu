@@ -1,5 +1,6 @@
 // krylov.cu -- the s+1 right-preconditioned Krylov solves of Procedure *
-// (A~ y = b, A~ w_j = u_j, eqs. (regprob), (auxi)) for k systems at once.
+// (A~ y = b, A~ w_j = u_j, eqs. (regprob), (auxi)) for k systems at once, and
+// the transposed solves A~^T y = rhs with preconditioner M^T of the backward pass.
 //
 // Layout: inside the solver every block of k vectors is stored system-major
 // (system c's vector is contiguous, leading dimension ld = n rounded up to 32),
@@ -1448,6 +1449,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         return SAI_INVALID_ARG;
     if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES) return SAI_INVALID_ARG;
     if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
+    if (prm->transpose != 0 && prm->transpose != 1) return SAI_INVALID_ARG;
     if (prm->precision == SAI_FP32_REFINE64 && prm->method != SAI_GMRES) return SAI_NOT_IMPLEMENTED;
     const int32_t n = h->n;
     if (n > 0 && (!B || !X)) return SAI_INVALID_ARG;
@@ -1474,13 +1476,24 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     I.nch = nchunks(n > 0 ? n : 1);
     I.nchu = (int)(((int64_t)(n > 0 ? n : 1) + CHUNK_U - 1) / CHUNK_U);
     const int ib = item_blocks(n > 0 ? n : 1, k);
+    // CSR of A~ and M, or for the transposed solves CSR of A~^T and M^T,
+    // which are the CSC arrays of A~ and M
     Ops<double> A64;
-    A64.Ar = h->Atr_rp.as<int64_t>();
-    A64.Ac = h->Atr_ci.as<int32_t>();
-    A64.Av = h->Atr_v.as<double>();
-    A64.Mr = P->Mr_rp.as<int64_t>();
-    A64.Mc = P->Mr_ci.as<int32_t>();
-    A64.Mv = P->Mr_v.as<double>();
+    if (!prm->transpose) {
+        A64.Ar = h->Atr_rp.as<int64_t>();
+        A64.Ac = h->Atr_ci.as<int32_t>();
+        A64.Av = h->Atr_v.as<double>();
+        A64.Mr = P->Mr_rp.as<int64_t>();
+        A64.Mc = P->Mr_ci.as<int32_t>();
+        A64.Mv = P->Mr_v.as<double>();
+    } else {
+        A64.Ar = h->At_cp.as<int64_t>();
+        A64.Ac = h->At_ri.as<int32_t>();
+        A64.Av = h->At_v.as<double>();
+        A64.Mr = P->M_cp.as<int64_t>();
+        A64.Mc = P->M_ri.as<int32_t>();
+        A64.Mv = P->M_v.as<double>();
+    }
     int64_t tg = sai_div_up((int64_t)n * k > 0 ? (int64_t)n * k : 1, 256);
     if (tg > (int64_t)g_sms * 8) tg = (int64_t)g_sms * 8;
     const int tgrid = (int)tg;

@@ -5,6 +5,8 @@
 //   k_lu_solve     Gaussian elimination with partial pivoting (first largest
 //                  |pivot| wins), one block; z = C^{-1} g, c = ||z||
 //   k_smw_update   xhat(i) = yhat(i) - sum_t What(i,t) z_t, one thread per row
+// and its adjoint for A^T = A~^T + V U^T (the backward pass), where the small
+// system is C = I + U^T What, g = U^T yhat (k_smw_gather_adj).
 #include <math.h>
 
 #include <mutex>
@@ -21,6 +23,25 @@ __global__ void k_smw_gather(int32_t n, int32_t s, const int32_t* J, const doubl
     const int64_t ld = (int64_t)s + 1;
     C[(int64_t)col * s + row] = (row == col ? 1.0 : 0.0) + Y[(int64_t)J[row] * ld + 1 + col];
     if (col == 0) g[row] = Y[(int64_t)J[row] * ld];
+}
+
+// Adjoint form (A^T = A~^T + V U^T): C = I + U^T What (column-major s x s),
+// g = U^T yhat. One warp per (row a of U^T, column b of Y), b = 0 is yhat.
+__global__ void k_smw_gather_adj(int32_t s, const int64_t* Ucp, const int32_t* Uri, const double* Uv,
+                                 const double* Y, double* C, double* g)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)s * (s + 1)) return;
+    const int a = (int)(w % s), b = (int)(w / s);
+    const int64_t ld = (int64_t)s + 1;
+    double acc = 0.0;
+    for (int64_t q = Ucp[a] + lane; q < Ucp[a + 1]; q += 32) acc = fma(Uv[q], Y[(int64_t)Uri[q] * ld + b], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        if (b == 0) g[a] = acc;
+        else C[(int64_t)(b - 1) * s + a] = (a == b - 1 ? 1.0 : 0.0) + acc;
+    }
 }
 
 __global__ void k_lu_solve(int32_t s, double* C, double* g, double* z, double* c_out, int* err)
@@ -116,7 +137,9 @@ __global__ void k_smw_update(int32_t n, int32_t s, const double* Y, const double
 
 }  // namespace
 
-sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st)
+namespace {
+
+sai_status smw_common(const sai_split_s* h, const double* Y, double* x, double* c_out, bool adjoint, cudaStream_t st)
 {
     if (!h || (h->n > 0 && (!Y || !x))) return SAI_INVALID_ARG;
     const int32_t n = h->n, s = h->s;
@@ -130,8 +153,13 @@ sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double*
     SAI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     SAI_CUDA(cudaMemsetAsync(cbuf.p, 0, sizeof(double), st));
     if (s > 0) {
-        k_smw_gather<<<SAI_GRID(sai_div_up((int64_t)s * s, 256)), 256, 0, st>>>(n, s, h->J.as<int32_t>(), Y, C.as<double>(),
-                                                                    g.as<double>());
+        if (!adjoint)
+            k_smw_gather<<<SAI_GRID(sai_div_up((int64_t)s * s, 256)), 256, 0, st>>>(n, s, h->J.as<int32_t>(), Y,
+                                                                                   C.as<double>(), g.as<double>());
+        else
+            k_smw_gather_adj<<<SAI_GRID(sai_div_up((int64_t)s * (s + 1) * 32, 256)), 256, 0, st>>>(
+                s, h->U_cp.as<int64_t>(), h->U_ri.as<int32_t>(), h->U_v.as<double>(), Y, C.as<double>(),
+                g.as<double>());
         k_lu_solve<<<SAI_GRID(1), 1024, 0, st>>>(s, C.as<double>(), g.as<double>(), z.as<double>(), cbuf.as<double>(),
                                        err.as<int>());
     }
@@ -145,6 +173,18 @@ sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double*
     if (herr) return SAI_SINGULAR;
     if (c_out) *c_out = hc;
     return SAI_OK;
+}
+
+}  // namespace
+
+sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st)
+{
+    return smw_common(h, Y, x, c_out, false, st);
+}
+
+sai_status sai_smw_adj_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st)
+{
+    return smw_common(h, Y, x, c_out, true, st);
 }
 
 // ---------------------------------------------------------------- allocation-free variant

@@ -432,3 +432,110 @@ def test_procedure_star_meets_eps_and_theorem2(sai, krylov):
         else:
             _, it, _ = O.gmres(At, M, rhs[q], thr[q], restart=50)
         assert it == iters[q]
+
+
+# ---------------------------------------------------------------- backward pass (O8)
+def test_backward_dense_matches_central_differences():
+    """The dense adjoint (lambda = A^{-T} g, dL/dA_ij = -lambda_i x_j) against
+    central differences of L = g^T A^{-1} b at h = 1e-6, each perturbed
+    system solved by a dense LU (scipy), over b and a sample of A's stored
+    entries including the dense columns'."""
+    P = W.random_sparse_dominant(40, 3, 2, 15, seed=31)
+    A = O.as_csc(P.A)
+    rng = np.random.default_rng(3)
+    g = rng.standard_normal(A.shape[0])
+    b = rng.standard_normal(A.shape[0])
+    x = sla.solve(A.toarray(), b)
+    lam, gv = O.backward_dense(A, x, g)
+    h = 1e-6
+
+    def loss(Ad, bb):
+        return float(g @ sla.solve(Ad, bb))
+
+    Ad = A.toarray()
+    for i in rng.choice(A.shape[0], 8, replace=False):
+        e = np.zeros_like(b)
+        e[i] = h
+        fd = (loss(Ad, b + e) - loss(Ad, b - e)) / (2 * h)
+        assert fd == pytest.approx(lam[i], rel=1e-6, abs=1e-9)
+    cols = np.repeat(np.arange(A.shape[1]), np.diff(A.indptr))
+    for q in rng.choice(A.nnz, 25, replace=False):
+        i, j = A.indices[q], cols[q]
+        Ap, Am = Ad.copy(), Ad.copy()
+        Ap[i, j] += h
+        Am[i, j] -= h
+        fd = (loss(Ap, b) - loss(Am, b)) / (2 * h)
+        assert fd == pytest.approx(gv[q], rel=1e-6, abs=1e-9)
+
+
+def test_smw_adjoint_with_exact_solves_is_the_dense_adjoint():
+    """Theorem 1 applied to A^T = A~^T + V U^T: with yhat, W from exact dense
+    solves of A~^T, the oracle's adjoint recovery equals A^{-T} g."""
+    P = W.random_sparse_dominant(80, 3, 3, 70, seed=32)
+    A = O.as_csc(P.A)
+    J, p, _ = O.detect(A)
+    assert len(J) == 3
+    At, U = O.split(A, J, p)
+    n = A.shape[0]
+    g = np.random.default_rng(4).standard_normal(n)
+    rhs = np.column_stack([g, _vmat(J, n).toarray()])
+    Y = sla.solve(At.toarray().T, rhs)
+    lam, z, c = O.smw_adjoint(Y[:, 0], Y[:, 1:], U)
+    lam_d = sla.solve(A.toarray().T, g)
+    np.testing.assert_allclose(lam, lam_d, rtol=1e-10, atol=1e-12)
+    assert c == pytest.approx(np.linalg.norm(z))
+
+
+def test_csc_transpose_is_the_transpose():
+    A = O.as_csc(_dominant(50, 4, 33, s=2, dense_nnz=20))
+    T = O.csc_transpose(A)
+    assert (T != A.T.tocsc()).nnz == 0
+    assert np.all(np.diff(T.indptr) >= 0)
+
+
+@pytest.mark.parametrize("krylov", ["bicgstab", "gmres"])
+def test_oracle_backward_meets_the_adjoint_thresholds(krylov):
+    """The sparse adjoint pipeline (split, M, s+1 transposed solves with M^T,
+    adjoint SMW) meets the Theorem 2 bound on ||g - A^T lambda|| on the 2D
+    workload, agrees with the dense adjoint, and its iteration counts equal independent
+    solves of A~^T with M^T at the Theorem 2 thresholds taken from ||g||."""
+    P = W.convdiff2d_irregular()
+    A = O.as_csc(P.A)
+    eps = 1e-10
+    x = O.solve(A, P.b, krylov=krylov, eps=eps)[0]
+    g = np.random.default_rng(5).standard_normal(A.shape[0])
+    lam, gv, iters, rep = O.backward(A, x, g, krylov=krylov, eps=eps)
+    assert rep["status"] == O.OK and rep["s"] == 3
+    # Theorem 2 on A^T: ||g - A^T lambda|| <= ||r_y|| + c ||R_W||_F, with the
+    # thresholds eps||g||/2 and eps||g||/(2 sqrt(s)) per system
+    assert rep["rr"] <= eps * (1 + rep["c"]) / 2 * 1.05
+    lam_d, gv_d = O.backward_dense(A, x, g)
+    np.testing.assert_allclose(lam, lam_d, rtol=0, atol=1e-7 * np.abs(lam_d).max())
+    np.testing.assert_allclose(gv, gv_d, rtol=0, atol=1e-7 * np.abs(gv_d).max())
+    J, p, _ = O.detect(A)
+    At, U = O.split(A, J, p)
+    M = O.spai(At, 0.4, 5, 10)[0]
+    gn = np.linalg.norm(g)
+    s = len(J)
+    thr = [eps / 2 * gn] + [gn * eps / (2 * np.sqrt(s))] * s
+    rhs = [g] + [np.eye(A.shape[0])[:, j] for j in J]
+    for q in range(s + 1):
+        if krylov == "bicgstab":
+            _, it, _ = O.bicgstab(At.T.tocsc(), M.T.tocsc(), rhs[q], thr[q])
+        else:
+            _, it, _ = O.gmres(At.T.tocsc(), M.T.tocsc(), rhs[q], thr[q], restart=50)
+        assert it == iters[q]
+
+
+def test_zipf_workload_structure():
+    """The heavy-tailed generator: counts capped, strict column dominance,
+    irregular columns found above the absolute threshold 200."""
+    P = W.zipf_columns(n=1500)
+    A = O.as_csc(P.A)
+    cnt = np.diff(A.indptr)
+    assert cnt.max() <= 750 + 1
+    d = A.diagonal()
+    off = np.asarray(abs(A).sum(axis=0)).ravel() - np.abs(d)
+    assert np.all(np.abs(d) > 1.19 * off)
+    J, p, tau = O.detect(A, abs_tau=200.0)
+    assert tau == 200.0 and len(J) == int((cnt > 200).sum()) and len(J) > 10

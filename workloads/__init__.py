@@ -144,3 +144,27 @@ def random_sparse_dominant(n, nnz_per_col, s, dense_nnz, seed, dominance=1.2):
         vals += [v, [dominance * np.abs(v).sum() + 1.0]]
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
     return _finish("random_n%d" % n, A, dict(n=n, s=s, dense_cols=dense.tolist(), seed=seed))
+
+
+def zipf_columns(n=2000, alpha=1.5, cap=None, dominance=1.2, seed=SEED_BASE + 5):
+    """Heavy-tailed irregular matrix (the Zipf-count workload): column j holds
+    min(Zipf(alpha), cap) off-diagonal entries at distinct random rows with
+    N(0,1) values, and a diagonal a_jj = dominance * sum_{i != j} |a_ij|
+    (strict column dominance, so A~ stays nonsingular by Theorem 3(i)).
+    Irregular columns are those above the absolute threshold tau = 200.
+    The recipe is that of a 1e5-column system scaled to n; cap defaults to
+    min(5000, n // 2)."""
+    rng = np.random.default_rng(seed)
+    cap = min(5000, n // 2) if cap is None else cap
+    counts = np.minimum(rng.zipf(alpha, size=n), cap)
+    rows, cols, vals = [], [], []
+    for j in range(n):
+        k = int(counts[j])
+        r = rng.choice(n - 1, size=k, replace=False)
+        r = r + (r >= j)  # skip the diagonal
+        v = rng.standard_normal(k)
+        rows += [r, [j]]
+        cols += [np.full(k, j), [j]]
+        vals += [v, [dominance * np.abs(v).sum() + 1e-3]]
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    return _finish("zipf_n%d" % n, A, dict(n=n, alpha=alpha, cap=cap, abs_tau=200.0, seed=seed))
