@@ -129,12 +129,8 @@ FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nomi
 FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 
-def roofline(prof, peaks):
-    """Dominant profiled site (largest device time): achieved vs its binding peak."""
-    sites = {k: v for k, v in prof["sites"].items() if v["launches"] > 0 and v["ms"] > 0}
-    if not sites:
-        return None
-    name, s = max(sites.items(), key=lambda kv: kv[1]["ms"])
+def site_roofline(name, s, peaks):
+    """Binding peak and achieved rate of one profiled site (per-launch averages)."""
     avg_s = s["ms"] / s["launches"] / 1e3
     bytes_l = s["bytes"] / s["launches"]
     flops_l = s["flops"] / s["launches"]
@@ -145,19 +141,32 @@ def roofline(prof, peaks):
     t_alu = flops_l / (alu_peak * 1e12)
     if flops_l > 0 and t_alu > t_hbm:
         ach = flops_l / avg_s / 1e12
-        r = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-             "frac": ach / alu_peak,
+        r = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
              "peak_source": ("FP32" if fp32 else "FP64") + " ALU nominal from unit counts and clocks"}
     else:
         ach = bytes_l / avg_s / 1e9
         r = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
              "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback"}
-    r.update({"kernel": name, "launches": s["launches"], "avg_launch_us": avg_s * 1e6,
-              "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
-              "traffic": None, "timed_launches": s.get("timed", s["launches"]),
-              "measured": "CUDA events on every 7th launch of the site, one profiled step after the timed steps",
-              "sites": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
-                        for k, v in prof["sites"].items() if v["launches"]}})
+    r.update({"launches": s["launches"], "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": bytes_l,
+              "algorithmic_flops_per_launch": flops_l, "timed_launches": s.get("timed", s["launches"])})
+    return r
+
+
+def roofline(prof, peaks):
+    """Dominant profiled site (largest device time): achieved vs its binding peak;
+    every site's figures under "sites"."""
+    sites = {k: v for k, v in prof["sites"].items() if v["launches"] > 0 and v["ms"] > 0}
+    if not sites:
+        return None
+    name = max(sites, key=lambda k: sites[k]["ms"])
+    r = site_roofline(name, sites[name], peaks)
+    r.update({"kernel": name, "traffic": None,
+              "measured": "CUDA events on the first 16 launches of each site and every 7th after, "
+                          "one profiled step after the timed steps",
+              "sites": {k: dict(ms=round(v["ms"], 3), **{q: (round(x, 4) if isinstance(x, float) else x)
+                                                         for q, x in site_roofline(k, v, peaks).items()
+                                                         if q in ("bound", "achieved", "unit", "frac", "launches")})
+                        for k, v in sites.items()}})
     return r
 
 

@@ -19,7 +19,11 @@ static std::mutex g_prof_mu;
 // launch costs two cudaEventRecord calls and no allocation.
 static std::vector<cudaEvent_t> g_ev_pool;
 static std::atomic<size_t> g_ev_next{0};
-static std::vector<std::pair<size_t, size_t>> g_prof_ev[PROF_NSITES];
+struct ProfPair {
+    size_t a, b;  // event pair in the pool
+    bool all;     // from the fully timed head of the site's launches
+};
+static std::vector<ProfPair> g_prof_ev[PROF_NSITES];
 static const char* k_site_names[PROF_NSITES] = {"sai_build",          "krylov_spmm",     "gmres_project",
                                                 "gmres_update",       "bicgstab_vector", "krylov_spmm_fp32",
                                                 "gmres_project_fp32", "gmres_update_fp32"};
@@ -71,16 +75,20 @@ cudaStream_t sai_aux_stream()
     return streams[dev];
 }
 
-// Every launch of a profiled site is counted; one in k_prof_stride is timed
-// with a pair of events (a uniform subsample of the site's launches), which
-// keeps the event overhead out of the timed region.
+// Every launch of a profiled site is counted; the first k_prof_all launches
+// of a site and then one in k_prof_stride are timed with a pair of events (a
+// uniform subsample of the frequent sites' launches, every launch of the rare
+// ones), which keeps the event overhead out of the timed region.
 static const long long k_prof_stride = 7;
+static const long long k_prof_all = 16;
 static std::atomic<long long> g_site_calls[PROF_NSITES];
 
 ProfScope::ProfScope(int site_, cudaStream_t st_) : site(site_), st(st_)
 {
     if (!sai_prof_on()) return;
-    if (g_site_calls[site].fetch_add(1) % k_prof_stride != 0) return;
+    const long long c = g_site_calls[site].fetch_add(1);
+    if (c >= k_prof_all && c % k_prof_stride != 0) return;
+    all = c < k_prof_all;
     const size_t i = g_ev_next.fetch_add(2);
     if (i + 1 >= g_ev_pool.size()) return;
     idx = (long long)i;
@@ -93,7 +101,7 @@ ProfScope::~ProfScope()
     const size_t i = (size_t)idx;
     cudaEventRecord(g_ev_pool[i + 1], st);
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof_ev[site].emplace_back(i, i + 1);
+    g_prof_ev[site].push_back(ProfPair{i, i + 1, all});
 }
 
 extern "C" {
@@ -137,15 +145,24 @@ sai_status sai_profile_end(sai_profile_report* out)
         sai_profile_site& ps = out->site[q];
         strncpy(ps.name, k_site_names[q], sizeof(ps.name) - 1);
         ps.launches = (int64_t)g_site_calls[q].load();
-        double ms = 0.0;
+        // the head launches are all timed; the rest are a 1-in-k_prof_stride
+        // sample scaled to the launches after the head
+        double ms_head = 0.0, ms_tail = 0.0;
+        size_t n_head = 0, n_tail = 0;
         for (auto& pr : g_prof_ev[q]) {
             float t = 0.f;
-            cudaEventElapsedTime(&t, g_ev_pool[pr.first], g_ev_pool[pr.second]);
-            ms += t;
+            cudaEventElapsedTime(&t, g_ev_pool[pr.a], g_ev_pool[pr.b]);
+            if (pr.all) {
+                ms_head += t;
+                ++n_head;
+            } else {
+                ms_tail += t;
+                ++n_tail;
+            }
         }
-        // scale the timed subsample to all launches of the site
-        const size_t timed = g_prof_ev[q].size();
-        ps.ms = timed ? ms * (double)ps.launches / (double)timed : 0.0;
+        const double rest = (double)ps.launches - (double)n_head;
+        ps.ms = ms_head + (n_tail ? ms_tail * rest / (double)n_tail : 0.0);
+        const size_t timed = n_head + n_tail;
         ps.timed = (int64_t)timed;
         g_prof_ev[q].clear();
         ps.bytes = wk[2 * q] + wb[2 * q];

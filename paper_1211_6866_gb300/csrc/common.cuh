@@ -95,6 +95,7 @@ struct ProfScope {
     int site;
     cudaStream_t st;
     long long idx = -1;  // index of the first event of the pair in the pool
+    bool all = false;    // one of the site's first launches, all of which are timed
     ProfScope(int site_, cudaStream_t st_);
     ~ProfScope();
 };

@@ -394,9 +394,31 @@ __device__ void refine(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, in
     __syncwarp();
 }
 
+// Algorithmic flops of one ls_update call that grows the factor of an
+// nL x c block to nL x nS: the old reflectors on the new columns, the
+// Householder factorisation of the trailing columns (each reflector applied
+// to the later columns and to Q^T e), and the back substitution.
+// (Integer arithmetic: the kernel's FP64 units are its bottleneck.)
+__device__ __forceinline__ long long qr_flops(int nL, int c, int nS)
+{
+    const long long q = nS - c;
+    long long f = 4 * q * ((long long)c * nL - (long long)c * (c - 1) / 2);
+    for (int t = c; t < nS; ++t) f += 2LL * (nL - t) + 4LL * (nS - t) * (nL - t);
+    return f + (long long)nS * nS;
+}
+
+// sum of nnz(A~(:,j)) over j in S (warp-uniform result)
+template <class T>
+__device__ int s_nnz(const WsT<typename T::TQ>& w, const SaiMat& A, int nS)
+{
+    int c = 0;
+    for (int t = lane_id(); t < nS; t += 32) c += (int)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]);
+    return warp_sum_int(c);
+}
+
 template <class T>
 __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out, int& l_out,
-                           double& rn_out, int& nL_out)
+                           double& rn_out, int& nL_out, long long& fl)
 {
     const int lane = lane_id();
     int nL, nS, nfact;
@@ -405,11 +427,19 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
     __syncwarp();
     int l = 0;
     double rn = 0.0;
+    fl = 0;
     for (;;) {
+        const int c0 = nfact;
         int st = ls_update<T>(w, A, nL, nS, nfact);
         if (st != ST_DONE) return st;
-        if (sizeof(typename T::TQ) < sizeof(double)) refine<T>(w, A, nL, nS);
+        const long long sn = s_nnz<T>(w, A, nS);
+        fl += qr_flops(nL, c0, nS);
+        if (sizeof(typename T::TQ) < sizeof(double)) {
+            refine<T>(w, A, nL, nS);
+            fl += 4 * sn + 2LL * nL + 2LL * nS * nS;
+        }
         const double rn2 = residual<T>(w, A, nL, nS, nullptr);
+        fl += 2 * sn + 2LL * nL;
         rn = sqrt(rn2);
         if (rn <= a.delta || l >= a.max_aug) break;
         // candidate set N \ S from the rows of L
@@ -443,11 +473,13 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         unsigned long long top[MNMAX];
 #pragma unroll
         for (int q = 0; q < MNMAX; ++q) top[q] = ULLONG_MAX;
+        int fsc = 0;
         for (int sl = lane; sl < T::HC; sl += 32) {
             const int32_t j = w.ck[sl];
             if (j < 0 || w.cf[sl]) continue;
             const double nj = A.colnorm2[j];
             if (!(nj > 0.0)) continue;
+            fsc += 2 * (int)(A.cp[j + 1] - A.cp[j]) + 5;  // r^T a_j, rho_j^2 and its key
             double d = 0.0;
             for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
                 const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
@@ -464,6 +496,7 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
                 top[q] = lo;
             }
         }
+        fl += warp_sum_int(fsc);
         int added = 0;
         for (int sel = 0; sel < a.mn; ++sel) {
             const unsigned long long best = warp_min_u64(top[0]);
@@ -492,7 +525,7 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
 // PSAI(tol), reading (A): S^(l+1) = P(a^(l+1)) u S_kept^(l), a^(l+1) = |A~| a^(l).
 template <class T>
 __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out, int& l_out,
-                           double& rn_pre, double& rn_post, int& nL_out)
+                           double& rn_pre, double& rn_post, int& nL_out, long long& fl)
 {
     const int lane = lane_id();
     int nL, nS, nfact;
@@ -506,11 +539,19 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
     int32_t* apat = w.a0;
     int32_t* anew = w.a1;
     int l = 0;
+    fl = 0;
     for (;;) {
+        const int c0 = nfact;
         int st = ls_update<T>(w, A, nL, nS, nfact);
         if (st != ST_DONE) return st;
-        if (sizeof(typename T::TQ) < sizeof(double)) refine<T>(w, A, nL, nS);
+        const long long sn = s_nnz<T>(w, A, nS);
+        fl += qr_flops(nL, c0, nS);
+        if (sizeof(typename T::TQ) < sizeof(double)) {
+            refine<T>(w, A, nL, nS);
+            fl += 4 * sn + 2LL * nL + 2LL * nS * nS;
+        }
         const double rn = sqrt(residual<T>(w, A, nL, nS, nullptr));
+        fl += 2 * sn + 2LL * nL;
         double tolk = a.tol;
         if (a.tol_mode == 0) {
             int nz = 0;
@@ -524,6 +565,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         if (rn <= a.delta || l >= a.lmax) {
             rn_pre = rn;
             rn_post = sqrt(residual<T>(w, A, nL, nS, w.kp));
+            fl += 2 * sn + 2LL * nL;
             // compact the kept entries to the front of S / m (order preserved)
             int q = 0;
             if (lane == 0) {
@@ -637,6 +679,7 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
                       : gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * T::BYTES;
     const WsT<typename T::TQ> w = bind_ws<T>(base);
     double work_bytes = 0.0;
+    long long work_flops = 0;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(next, 1);
@@ -645,8 +688,9 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
         const int32_t k = work ? work[item] : item;
         int nS = 0, l = 0, nL = 0;
         double rn = 0.0, rpost = 0.0;
-        int st = PSAI ? psai_column<T>(w, A, k, pa, nS, l, rn, rpost, nL)
-                      : spai_column<T>(w, A, k, sa, nS, l, rn, nL);
+        long long cfl = 0;
+        int st = PSAI ? psai_column<T>(w, A, k, pa, nS, l, rn, rpost, nL, cfl)
+                      : spai_column<T>(w, A, k, sa, nS, l, rn, nL, cfl);
         if (st == ST_DONE) {
             if (nS > out.smax) st = ST_OVERFLOW;
         }
@@ -660,6 +704,7 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
             for (int t = lane; t < nS; t += 32) cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
             for (int t = lane; t < nL; t += 32) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
             work_bytes += warp_sum(cb);
+            work_flops += cfl;
             if (lane == 0) {
                 out.cnt[k] = nS;
                 out.loops[k] = l;
@@ -681,7 +726,10 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
         }
         __syncwarp();
     }
-    if (lane == 0 && work_bytes > 0.0) atomicAdd(&d_swork[2 * PROF_SAI_BUILD], work_bytes);
+    if (lane == 0 && work_bytes > 0.0) {
+        atomicAdd(&d_swork[2 * PROF_SAI_BUILD], work_bytes);
+        atomicAdd(&d_swork[2 * PROF_SAI_BUILD + 1], (double)work_flops);
+    }
 }
 
 // One warp per column: rank-sort the column's slots by row into CSC.
