@@ -124,12 +124,19 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
 #pragma unroll
         for (int t = 0; t < CT; ++t) acc[t] = 0;
         const int64_t b = rp[row], e = rp[row + 1];
-        for (int64_t q = b; q < e; ++q) {
-            const T a = v[q];
-            const int32_t col = ci[q];
+        for (int64_t q0 = b; q0 < e; q0 += 8) {  // batches of 8: indices first, then the gathers
+            int32_t col[8];
+            T a[8];
 #pragma unroll
-            for (int t = 0; t < CT; ++t)
-                if (t < ng) acc[t] = fma(a, X[off[t] + col], acc[t]);
+            for (int u = 0; u < 8; ++u) {
+                col[u] = q0 + u < e ? ci[q0 + u] : 0;
+                a[u] = q0 + u < e ? v[q0 + u] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int t = 0; t < CT; ++t)
+                    if (t < ng) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
         }
 #pragma unroll
         for (int t = 0; t < CT; ++t) {
@@ -142,23 +149,199 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
     }
 }
 
+// Sliced ELL: slices of SELL_C consecutive rows, each padded to its longest
+// row and stored column-major (entry k of the slice's rows at
+// sp[slice] + k*SELL_C + lane), so a warp's matrix loads are contiguous.
+// Padding entries point at a valid column with value 0.
+constexpr int SELL_C = 32;
+constexpr int SELL_CT = 4;  // systems per pass of the sliced-ELL SpMV
+constexpr int SELL_W = 8;   // slice width held in registers
+
+// One matrix of an operator: CSR, plus a sliced-ELL copy when sp != nullptr.
+template <class T>
+struct Mat {
+    const int64_t* rp = nullptr;
+    const int32_t* ci = nullptr;
+    const T* v = nullptr;
+    const int64_t* sp = nullptr;
+    const int32_t* sci = nullptr;
+    const T* sv = nullptr;
+    int64_t nslices = 0;
+};
+
+// Sliced-ELL SpMV: one warp per slice (lane = row of the slice). A slice of
+// width <= SELL_W keeps its entries in registers and loops over the listed
+// systems SELL_CT at a time, so the matrix is read once for all systems and
+// each system costs only its gathers; wider slices take the entries in
+// batches of SELL_W per group of systems.
 template <class T, int MODE>
-void spmv(int32_t n, int64_t ld, const int64_t* rp, const int32_t* ci, const T* v, int k, const T* X, T* Y,
-          const T* B, const int* list, cudaStream_t st, const int* jstop = nullptr, int jmax = 0)
+__global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T> Am, const T* __restrict__ X,
+                                                   T* __restrict__ Y, const T* __restrict__ B,
+                                                   const int* __restrict__ list, const int* __restrict__ jstop, int jmax)
 {
+    constexpr int CT = SELL_CT, W = SELL_W;
+    if (jstop && *jstop >= jmax) return;  // the step needs no operator application
+    const int cnt = list[0];
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = w0; sl < Am.nslices; sl += nw) {
+        const int64_t b = Am.sp[sl], e = Am.sp[sl + 1];
+        const int64_t row = sl * SELL_C + lane;
+        if (e - b <= (int64_t)W * SELL_C) {
+            int32_t col[W];
+            T a[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                const int64_t q = b + (int64_t)u * SELL_C + lane;
+                col[u] = q < e ? Am.sci[q] : 0;
+                a[u] = q < e ? Am.sv[q] : (T)0;
+            }
+            for (int g0 = 0; g0 < cnt; g0 += CT) {
+                int64_t off[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) off[t] = g0 + t < cnt ? (int64_t)list[1 + g0 + t] * ld : 0;
+                T acc[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) acc[t] = 0;
+#pragma unroll
+                for (int u = 0; u < W; ++u)
+#pragma unroll
+                    for (int t = 0; t < CT; ++t)
+                        if (g0 + t < cnt) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
+                if (row < n) {
+#pragma unroll
+                    for (int t = 0; t < CT; ++t) {
+                        if (g0 + t < cnt) {
+                            if (MODE == 0) Y[off[t] + row] = acc[t];
+                            else if (MODE == 1) Y[off[t] + row] = B[off[t] + row] - acc[t];
+                            else Y[off[t] + row] += acc[t];
+                        }
+                    }
+                }
+            }
+        } else {
+            for (int g0 = 0; g0 < cnt; g0 += CT) {
+                int64_t off[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) off[t] = g0 + t < cnt ? (int64_t)list[1 + g0 + t] * ld : 0;
+                T acc[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) acc[t] = 0;
+                for (int64_t q0 = b + lane; q0 < e; q0 += (int64_t)W * SELL_C) {
+                    int32_t col[W];
+                    T a[W];
+#pragma unroll
+                    for (int u = 0; u < W; ++u) {
+                        const int64_t q = q0 + (int64_t)u * SELL_C;
+                        col[u] = q < e ? Am.sci[q] : 0;
+                        a[u] = q < e ? Am.sv[q] : (T)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < W; ++u)
+#pragma unroll
+                        for (int t = 0; t < CT; ++t)
+                            if (g0 + t < cnt) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
+                }
+                if (row < n) {
+#pragma unroll
+                    for (int t = 0; t < CT; ++t) {
+                        if (g0 + t < cnt) {
+                            if (MODE == 0) Y[off[t] + row] = acc[t];
+                            else if (MODE == 1) Y[off[t] + row] = B[off[t] + row] - acc[t];
+                            else Y[off[t] + row] += acc[t];
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// slice widths (longest row of each slice) times SELL_C, one warp per slice
+__global__ void k_sell_width(int32_t n, const int64_t* __restrict__ rp, int64_t nslices, int64_t* __restrict__ cnt)
+{
+    const int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= nslices) return;
+    const int64_t row = sl * SELL_C + lane;
+    const unsigned len = row < n ? (unsigned)(rp[row + 1] - rp[row]) : 0u;
+    const unsigned w = __reduce_max_sync(SAI_FULL, len);
+    if (lane == 0) cnt[sl] = (int64_t)w * SELL_C;
+}
+
+template <class T>
+__global__ void k_sell_fill(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, int64_t nslices, const int64_t* __restrict__ sp,
+                            int32_t* __restrict__ sci, T* __restrict__ sv)
+{
+    const int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= nslices) return;
+    const int64_t row = sl * SELL_C + lane;
+    const int64_t b = sp[sl], w = (sp[sl + 1] - b) / SELL_C;
+    const int64_t r0 = row < n ? rp[row] : 0, len = row < n ? rp[row + 1] - r0 : 0;
+    const int32_t pad = row < n ? (int32_t)row : 0;
+    for (int64_t k = 0; k < w; ++k) {
+        const int64_t q = b + k * SELL_C + lane;
+        sci[q] = k < len ? ci[r0 + k] : pad;
+        sv[q] = k < len ? (T)v[r0 + k] : (T)0;
+    }
+}
+
+template <class T, int MODE>
+void spmv(int32_t n, int64_t ld, const Mat<T>& A, int k, const T* X, T* Y, const T* B, const int* list,
+          cudaStream_t st, const int* jstop = nullptr, int jmax = 0)
+{
+    if (A.sp) {
+        int64_t g = (A.nslices + 7) / 8;
+        const int64_t cap = (int64_t)g_sms * 8;
+        if (g > cap) g = cap;
+        if (g < 1) g = 1;
+        k_spmv_sell<T, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, jstop, jmax);
+        return;
+    }
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
     int64_t g = tiles * ((k + 3) / 4);
     const int64_t cap = (int64_t)g_sms * 8;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, rp, ci, v, X, Y, B, list, jstop, jmax);
+    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, A.rp, A.ci, A.v, X, Y, B, list, jstop, jmax);
+}
+
+// Adds a sliced-ELL copy (values converted to T) of the CSR matrix (rp, ci,
+// v64) to m, unless slice padding would exceed half of nnz (then m keeps
+// only its CSR form). Synchronises the stream once to read the size.
+template <class T>
+sai_status build_sell(int32_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* v64, Buf& spb,
+                      Buf& cib, Buf& vb, Mat<T>& m, cudaStream_t st)
+{
+    if (n <= 0) return SAI_OK;
+    const int64_t ns = ((int64_t)n + SELL_C - 1) / SELL_C;
+    Buf cnt;
+    SAI_TRY(cnt.alloc(sizeof(int64_t) * (size_t)ns, st, true));
+    SAI_TRY(spb.alloc(sizeof(int64_t) * (size_t)(ns + 1), st, true));
+    const unsigned g = sai_div_up(ns * 32, 256);
+    k_sell_width<<<SAI_GRID(g), 256, 0, st>>>(n, rp, ns, cnt.as<int64_t>());
+    SAI_TRY(sai_scan_counts_i64(cnt.as<int64_t>(), spb.as<int64_t>(), ns, st));
+    int64_t total = 0;
+    SAI_CUDA(cudaMemcpyAsync(&total, spb.as<int64_t>() + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    if ((double)total > 1.5 * (double)nnz + (double)SELL_C * ns) return SAI_OK;  // too much padding: CSR
+    SAI_TRY(cib.alloc(sizeof(int32_t) * (size_t)(total > 0 ? total : 1), st, true));
+    SAI_TRY(vb.alloc(sizeof(T) * (size_t)(total > 0 ? total : 1), st, true));
+    k_sell_fill<T><<<SAI_GRID(g), 256, 0, st>>>(n, rp, ci, v64, ns, spb.as<int64_t>(), cib.as<int32_t>(), vb.as<T>());
+    SAI_CUDA(cudaGetLastError());
+    m.sp = spb.as<int64_t>();
+    m.sci = cib.as<int32_t>();
+    m.sv = vb.as<T>();
+    m.nslices = ns;
+    return SAI_OK;
 }
 
 template <class T>
-struct Ops {  // A~ and M in CSR with values of type T
-    const int64_t *Ar, *Mr;
-    const int32_t *Ac, *Mc;
-    const T *Av, *Mv;
+struct Ops {  // A~ (or A~^T) and M (or M^T) with values of type T
+    Mat<T> A, M;
 };
 
 // ---------------------------------------------------------------- item kernels
@@ -485,11 +668,11 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
         }
         {
             ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, p, ph, nullptr, S.lact, st);
+            spmv<double, 0>(n, ld, A.M, k, p, ph, nullptr, S.lact, st);
         }
         {
             ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.Ar, A.Ac, A.Av, k, ph, v, nullptr, S.lact, st);
+            spmv<double, 0>(n, ld, A.A, k, ph, v, nullptr, S.lact, st);
         }
         {
             ProfScope ps(PROF_BICG_VEC, st);
@@ -503,11 +686,11 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
         k_bicg_f2<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
         {
             ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, s, sh, nullptr, S.lgo, st);
+            spmv<double, 0>(n, ld, A.M, k, s, sh, nullptr, S.lgo, st);
         }
         {
             ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.Ar, A.Ac, A.Av, k, sh, t, nullptr, S.lgo, st);
+            spmv<double, 0>(n, ld, A.A, k, sh, t, nullptr, S.lgo, st);
         }
         {
             ProfScope ps(PROF_BICG_VEC, st);
@@ -1245,11 +1428,11 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
     // the last step of a cycle (j = m) needs no operator application
     {
         ProfScope ps(D.site_spmm, st);
-        spmv<T, 0>(n, ld, A.Mr, A.Mc, A.Mv, k, Wk.r, Wk.t, nullptr, G.ladv, st, G.jdev, G.m);
+        spmv<T, 0>(n, ld, A.M, k, Wk.r, Wk.t, nullptr, G.ladv, st, G.jdev, G.m);
     }
     {
         ProfScope ps(D.site_spmm, st);
-        spmv<T, 0>(n, ld, A.Ar, A.Ac, A.Av, k, Wk.t, Wk.z, nullptr, G.ladv, st, G.jdev, G.m);
+        spmv<T, 0>(n, ld, A.A, k, Wk.t, Wk.z, nullptr, G.ladv, st, G.jdev, G.m);
     }
     const int fp = sizeof(T) == 4;
     const int64_t pcap = (int64_t)g_sms * g_res_dots[fp], ucap = (int64_t)g_sms * g_res_upd[fp];
@@ -1356,9 +1539,9 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         if (status != SAI_OK) break;
         k_dc_trisolve<<<SAI_GRID(k), 128, tri_smem, st>>>(k, S, G);
         k_dc_combine<T><<<SAI_GRID(cb), IT_WARPS * 32, 0, st>>>(I, w, Wk.B, G);
-        spmv<T, 2>(n, ld, A.Mr, A.Mc, A.Mv, k, w, Xs, nullptr, G.lcyc, st);  // x += M V y
+        spmv<T, 2>(n, ld, A.M, k, w, Xs, nullptr, G.lcyc, st);  // x += M V y
         k_gm_cycle_end<<<SAI_GRID(1), CTRL, 0, st>>>(k, cap, S, G, fl);
-        spmv<T, 1>(n, ld, A.Ar, A.Ac, A.Av, k, Xs, r, Bs, G.lcyc, st);
+        spmv<T, 1>(n, ld, A.A, k, Xs, r, Bs, G.lcyc, st);
         k_norm2<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, G.lcyc, pt2);
         SAI_CUDA(cudaGetLastError());
     }
@@ -1480,20 +1663,21 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     // which are the CSC arrays of A~ and M
     Ops<double> A64;
     if (!prm->transpose) {
-        A64.Ar = h->Atr_rp.as<int64_t>();
-        A64.Ac = h->Atr_ci.as<int32_t>();
-        A64.Av = h->Atr_v.as<double>();
-        A64.Mr = P->Mr_rp.as<int64_t>();
-        A64.Mc = P->Mr_ci.as<int32_t>();
-        A64.Mv = P->Mr_v.as<double>();
+        A64.A.rp = h->Atr_rp.as<int64_t>();
+        A64.A.ci = h->Atr_ci.as<int32_t>();
+        A64.A.v = h->Atr_v.as<double>();
+        A64.M.rp = P->Mr_rp.as<int64_t>();
+        A64.M.ci = P->Mr_ci.as<int32_t>();
+        A64.M.v = P->Mr_v.as<double>();
     } else {
-        A64.Ar = h->At_cp.as<int64_t>();
-        A64.Ac = h->At_ri.as<int32_t>();
-        A64.Av = h->At_v.as<double>();
-        A64.Mr = P->M_cp.as<int64_t>();
-        A64.Mc = P->M_ri.as<int32_t>();
-        A64.Mv = P->M_v.as<double>();
+        A64.A.rp = h->At_cp.as<int64_t>();
+        A64.A.ci = h->At_ri.as<int32_t>();
+        A64.A.v = h->At_v.as<double>();
+        A64.M.rp = P->M_cp.as<int64_t>();
+        A64.M.ci = P->M_ri.as<int32_t>();
+        A64.M.v = P->M_v.as<double>();
     }
+    Buf sell[6];  // sliced-ELL copies of the two operators of the main loop
     int64_t tg = sai_div_up((int64_t)n * k > 0 ? (int64_t)n * k : 1, 256);
     if (tg > (int64_t)g_sms * 8) tg = (int64_t)g_sms * 8;
     const int tgrid = (int)tg;
@@ -1549,6 +1733,12 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     k_fill_int<<<SAI_GRID(1), 256, 0, st>>>(k, cap, prm->maxit);
     SAI_CUDA(cudaGetLastError());
 
+    if (prm->method == SAI_BICGSTAB || prm->precision == SAI_FP64) {
+        Ops<double> S64 = A64;
+        SAI_TRY(build_sell<double>(n, h->nnz_At, A64.A.rp, A64.A.ci, A64.A.v, sell[0], sell[1], sell[2], S64.A, st));
+        SAI_TRY(build_sell<double>(n, P->nnz, A64.M.rp, A64.M.ci, A64.M.v, sell[3], sell[4], sell[5], S64.M, st));
+        A64 = S64;
+    }
     if (prm->method == SAI_BICGSTAB) {
         SAI_TRY(bicgstab_run(I, k, A64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
     } else if (prm->precision == SAI_FP64) {
@@ -1578,15 +1768,17 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         int64_t cg = sai_div_up(h->nnz_At > P->nnz ? h->nnz_At : P->nnz, 256);
         if (cg > (int64_t)g_sms * 8) cg = (int64_t)g_sms * 8;
         if (cg < 1) cg = 1;
-        if (h->nnz_At > 0) k_cast_f32<<<SAI_GRID(cg), 256, 0, st>>>(h->nnz_At, A64.Av, a32.as<float>());
-        if (P->nnz > 0) k_cast_f32<<<SAI_GRID(cg), 256, 0, st>>>(P->nnz, A64.Mv, m32.as<float>());
+        if (h->nnz_At > 0) k_cast_f32<<<SAI_GRID(cg), 256, 0, st>>>(h->nnz_At, A64.A.v, a32.as<float>());
+        if (P->nnz > 0) k_cast_f32<<<SAI_GRID(cg), 256, 0, st>>>(P->nnz, A64.M.v, m32.as<float>());
         Ops<float> A32;
-        A32.Ar = A64.Ar;
-        A32.Ac = A64.Ac;
-        A32.Av = a32.as<float>();
-        A32.Mr = A64.Mr;
-        A32.Mc = A64.Mc;
-        A32.Mv = m32.as<float>();
+        A32.A.rp = A64.A.rp;
+        A32.A.ci = A64.A.ci;
+        A32.A.v = a32.as<float>();
+        A32.M.rp = A64.M.rp;
+        A32.M.ci = A64.M.ci;
+        A32.M.v = m32.as<float>();
+        SAI_TRY(build_sell<float>(n, h->nnz_At, A64.A.rp, A64.A.ci, A64.A.v, sell[0], sell[1], sell[2], A32.A, st));
+        SAI_TRY(build_sell<float>(n, P->nnz, A64.M.rp, A64.M.ci, A64.M.v, sell[3], sell[4], sell[5], A32.M, st));
         double* r64 = r64b.as<double>();
         float* r32 = v32b.as<float>();
         float* d32 = r32 + blk;
@@ -1616,7 +1808,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
             SAI_TRY(gmres_run<float>(I, k, prm->restart, A32, r32, d32, Wk, S, G, cap, pt, pt2, fl, D32, st));
             k_ir_update<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, Xsd, d32, beta, lir);
             k_ir_total<<<SAI_GRID(1), 32, 0, st>>>(k, lir, S.iters, tot);
-            spmv<double, 1>(n, ld, A64.Ar, A64.Ac, A64.Av, k, Xsd, r64, Bsd, lir, st);
+            spmv<double, 1>(n, ld, A64.A, k, Xsd, r64, Bsd, lir, st);
             k_norm2<double><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r64, lir, pt2);
             SAI_CUDA(cudaGetLastError());
         }
