@@ -734,12 +734,15 @@ struct Gm {
     int *lcyc, *ladv;  // lists
     int* jdev;         // number of finished basis vectors in the current cycle
     int* bcnt;         // arrival counter of the multi-block control kernels
+    double* red;       // k x PS: a step's reduced partials per system
+    int* scnt;         // k: per-system arrival counters of k_dc_step
 };
 
 constexpr int GM_MAXM = 128;             // largest restart length
 constexpr int PD = 8;                    // basis vectors per pass of the fused dot kernel
 constexpr int PS = 2 * GM_MAXM + 2;      // partial slots per (system, chunk)
-constexpr int STEP_THREADS = 1024;       // threads of the per-system control kernels
+constexpr int STEP_THREADS = 256;        // threads per block of the step kernel
+constexpr int STEP_RB = 8;               // blocks per system of the step kernel
 
 // Krylov basis: m+1 system-major blocks of k vectors in the value type T.
 template <class T>
@@ -1007,18 +1010,20 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
     __shared__ double rc[GM_MAXM + 1];
     __shared__ double csS[GM_MAXM], snS[GM_MAXM];
     __shared__ double sh[2];
-    __shared__ int stop;
+    __shared__ int stop, mine;
     const int j = *G.jdev;
     const int cnt = G.ladv[0];
     const int m = G.m;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
-    if ((int)blockIdx.x < cnt) {
-        const int c = G.ladv[1 + blockIdx.x];
+    const int sb = blockIdx.x / STEP_RB, rb = blockIdx.x % STEP_RB;
+    if (sb < cnt) {
+        const int c = G.ladv[1 + sb];
         const int ns = 2 * j + 2;
-        for (int t = wid; t < ns; t += nwarp) {
+        // the STEP_RB blocks of system c reduce its slots (one warp per slot,
+        // eight independent loads in flight per lane, summed in a fixed order)
+        for (int t = rb * nwarp + wid; t < ns; t += STEP_RB * nwarp) {
             const int slot = t < 2 * j ? t : 2 * GM_MAXM + (t - 2 * j);
             const double* p = part + ((size_t)c * PS + slot) * nch;
-            // eight independent loads in flight per lane, summed in a fixed order
             double v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = 0.0;
@@ -1031,8 +1036,25 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
             }
             double sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
             sum = warp_sum(sum);
-            if (lane == 0) red[t] = sum;
+            if (lane == 0) G.red[(size_t)c * PS + t] = sum;
         }
+        // the last of the system's blocks to arrive does the serial part
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            mine = atomicAdd(&G.scnt[c], 1) == STEP_RB - 1;
+            if (mine) {
+                __threadfence();
+                G.scnt[c] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    if (sb < cnt && mine) {
+        const int c = G.ladv[1 + sb];
+        const int ns = 2 * j + 2;
+        const volatile double* gr = G.red + (size_t)c * PS;
+        for (int t = tid; t < ns; t += blockDim.x) red[t] = gr[t];
         __syncthreads();
         // red[2i] = s_i, red[2i+1] = c_i (i < j), red[2j] = u^T u, red[2j+1] = u^T z
         if (wid == 0) {
@@ -1444,7 +1466,7 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
         ProfScope ps(D.site_dots, st);
         k_dc_dots<T><<<SAI_GRID(pb), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G.ladv, G.jdev, pt);
     }
-    k_dc_step<<<SAI_GRID(k), STEP_THREADS, 0, st>>>(k, I.nch, pt, cap, S, G, D, tiny, fl);
+    k_dc_step<<<SAI_GRID(k * STEP_RB), STEP_THREADS, 0, st>>>(k, I.nch, pt, cap, S, G, D, tiny, fl);
     {
         ProfScope ps(D.site_upd, st);
         k_dc_update<T><<<SAI_GRID(ub), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G, G.ladv, G.jdev);
@@ -1561,8 +1583,9 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
 {
     G.m = m;
     const size_t km1 = (size_t)k * (m + 1);
-    const size_t hsz = 2 * (size_t)k * (m + 1) * m + 2 * (size_t)k * m + 4 * km1 + (size_t)k * m + 2 * (size_t)k;
-    const size_t isz = 5 * (size_t)k + 2 * (size_t)(k + 1) + 2;
+    const size_t hsz = 2 * (size_t)k * (m + 1) * m + 2 * (size_t)k * m + 4 * km1 + (size_t)k * m + 2 * (size_t)k +
+                       (size_t)k * PS;
+    const size_t isz = 6 * (size_t)k + 2 * (size_t)(k + 1) + 2;
     SAI_TRY(hb.alloc(sizeof(double) * hsz, st, true));
     SAI_TRY(ib.alloc(sizeof(int) * isz, st, true));
     SAI_CUDA(cudaMemsetAsync(hb.p, 0, sizeof(double) * hsz, st));
@@ -1588,6 +1611,7 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
     hp += (size_t)k * m;
     G.alpha = hp;
     G.dco = hp + k;
+    G.red = hp + 2 * k;
     int* ip = ib.as<int>();
     G.cyc = ip;
     G.adv = ip + k;
@@ -1598,6 +1622,7 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
     G.ladv = G.lcyc + (k + 1);
     G.jdev = G.ladv + (k + 1);
     G.bcnt = G.jdev + 1;
+    G.scnt = G.bcnt + 1;
     return SAI_OK;
 }
 
