@@ -1130,17 +1130,22 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         if (!stop) {
             // first-pass coefficients of column j and the update coefficients;
             // (Hbar s)_i = sum_{q >= max(i-1,0)} Hbar(i,q) s_q over the final columns q < j,
-            // one warp per row i, lanes over q
+            // one thread per row i (adjacent rows of a column are adjacent in memory),
+            // q ascending, the column loads in batches of 8 ahead of their FMAs
             double* hpc = G.hp + (size_t)c * (m + 1);
-            for (int i = wid; i <= j; i += nwarp) {
+            for (int i = tid; i <= j; i += blockDim.x) {
                 double hs = 0.0;
-                for (int q = (i > 0 ? i - 1 : 0) + lane; q < j; q += 32)
-                    hs = fma(Huc[(size_t)q * (m + 1) + i], red[2 * q], hs);
-                hs = warp_sum(hs);
-                if (lane == 0) {
-                    const double cz = i < j ? red[2 * i + 1] : d;
-                    hpc[i] = (cz - hs) / al;
+                int q = i > 0 ? i - 1 : 0;
+                for (; q + 8 <= j; q += 8) {
+                    double hv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) hv[u] = Huc[(size_t)(q + u) * (m + 1) + i];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) hs = fma(hv[u], red[2 * (q + u)], hs);
                 }
+                for (; q < j; ++q) hs = fma(Huc[(size_t)q * (m + 1) + i], red[2 * q], hs);
+                const double cz = i < j ? red[2 * i + 1] : d;
+                hpc[i] = (cz - hs) / al;
             }
             for (int i = tid; i < j; i += blockDim.x) {
                 G.sco[(size_t)c * (m + 1) + i] = red[2 * i];
