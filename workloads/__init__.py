@@ -168,3 +168,32 @@ def zipf_columns(n=2000, alpha=1.5, cap=None, dominance=1.2, seed=SEED_BASE + 5)
         vals += [v, [dominance * np.abs(v).sum() + 1e-3]]
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
     return _finish("zipf_n%d" % n, A, dict(n=n, alpha=alpha, cap=cap, abs_tau=200.0, seed=seed))
+
+
+def aniso9(m, eps=1e-3, theta_deg=30.0):
+    """-div(K grad u) on an m x m interior grid, K = R diag(1, eps) R^T rotated by
+    theta, the 9-point stencil (central second differences, the four-point
+    cross difference for u_xy), Dirichlet boundary, h^2-scaled."""
+    th = np.deg2rad(theta_deg)
+    c, s = np.cos(th), np.sin(th)
+    k11, k22, k12 = c * c + eps * s * s, s * s + eps * c * c, (1.0 - eps) * c * s
+    n = m * m
+    idx = np.arange(n, dtype=np.int64)
+    x, y = idx % m, idx // m
+    rows, cols, vals = [idx], [idx], [np.full(n, 2.0 * (k11 + k22))]
+    for dx, dy, v in ((-1, 0, -k11), (1, 0, -k11), (0, -1, -k22), (0, 1, -k22),
+                      (1, 1, -0.5 * k12), (-1, -1, -0.5 * k12), (1, -1, 0.5 * k12), (-1, 1, 0.5 * k12)):
+        ok = (x + dx >= 0) & (x + dx < m) & (y + dy >= 0) & (y + dy < m)
+        rows.append(idx[ok]); cols.append(idx[ok] + dx + dy * m); vals.append(np.full(ok.sum(), v))
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    return canonical(A)
+
+
+def aniso9_irregular(m=1024, eps=1e-3, theta_deg=30.0, s=50, density=0.02, seed=SEED_BASE + 4):
+    """The rotated anisotropic diffusion operator on m x m plus s dense N(0,1)
+    columns. Default sizes: the 1024 x 1024 grid (n = 1048576), anisotropy
+    1e-3 at 30 degrees, 50 columns at 2 %."""
+    rng = np.random.default_rng(seed)
+    A, cols = add_dense_columns(aniso9(m, eps, theta_deg), s, density, rng)
+    return _finish("aniso9_m%d_s%d" % (m, s), A, dict(m=m, eps=eps, theta_deg=theta_deg, s=s, density=density,
+                                                    seed=seed, dense_cols=cols.tolist()))
