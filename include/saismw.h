@@ -291,6 +291,42 @@ sai_status sai_backward(const sai_csc_view* A, sai_split h, sai_precond P, const
                         int32_t iters_cap, sai_solve_report* rep, sai_stream_t stream);
 
 /* ----------------------------------------------------------------------
+ * Batches of independent systems: Procedure * for nmat irregular matrices of
+ * different orders in one call. Each matrix is split on its own (its own p
+ * and threshold); the columns of all the A~_i are built in one persistent
+ * SAI launch (the block-diagonal A~ of the batch: every column's least-squares
+ * problem only sees its own matrix); the sum(s_i + 1) Krylov systems of the
+ * batch run together in one batched FP64 BiCGStab (each system on its own
+ * matrix, with the Theorem 2 thresholds of its matrix); then SMW and rr per
+ * matrix. Supported: SPAI, and PSAI with a fixed tolerance (tol_mode 1; the
+ * tol_k of eq. (tolk) is per matrix and is not taken in a batch), both
+ * precisions of the build; BiCGStab in FP64 (GMRES and the refined Krylov form
+ * return SAI_NOT_IMPLEMENTED).
+ *   A: host array of nmat CSC views (device arrays), b, x: host arrays of nmat
+ *   device n_i-vectors. items (host, nmat): per-matrix results; rep (host):
+ *   batch totals. Returns the worst system status or an error.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t status;    /* worst Krylov status of the matrix's s+1 systems */
+    int32_t iter_max;  /* max iterations over its s+1 systems */
+    int32_t s, p;      /* irregular columns found, p = floor(nnz/n) */
+    double c;          /* ||(I + V^T What)^{-1} V^T yhat|| */
+    double rr;         /* ||b - A x|| / ||b|| */
+} sai_batch_item;
+
+typedef struct {
+    int64_t columns;   /* columns of M built (sum of n_i) */
+    int64_t nnz_M;
+    int32_t systems;   /* Krylov systems, sum of (s_i + 1) */
+    int32_t iter_max;
+    double ms_split, ms_build, ms_krylov, ms_smw;  /* device time per step */
+} sai_batch_report;
+
+sai_status sai_solve_batched(int32_t nmat, const sai_csc_view* A, const double* const* b,
+                             const sai_solve_params* prm, double* const* x, sai_batch_item* items,
+                             sai_batch_report* rep, sai_stream_t stream);
+
+/* ----------------------------------------------------------------------
  * Diagnostics (not part of the paper's method): launch counting and the
  * per-kernel measurements behind the roofline figures.
  * ---------------------------------------------------------------------- */

@@ -69,6 +69,17 @@ class _KrylovParams(C.Structure):
                 ("inner_tol", C.c_double), ("transpose", C.c_int32)]
 
 
+class _BatchItem(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iter_max", C.c_int32), ("s", C.c_int32), ("p", C.c_int32),
+                ("c", C.c_double), ("rr", C.c_double)]
+
+
+class _BatchReport(C.Structure):
+    _fields_ = [("columns", C.c_int64), ("nnz_M", C.c_int64), ("systems", C.c_int32), ("iter_max", C.c_int32),
+                ("ms_split", C.c_double), ("ms_build", C.c_double), ("ms_krylov", C.c_double),
+                ("ms_smw", C.c_double)]
+
+
 class _StageParams(C.Structure):
     _fields_ = [("krylov", _KrylovParams), ("eps", C.c_double)]
 
@@ -132,13 +143,15 @@ def load():
                                  C.POINTER(C.c_int32), i32, C.POINTER(_SolveReport), vp]
     L.sai_backward.argtypes = [C.POINTER(_CscView), vp, vp, dp, dp, C.POINTER(_StageParams), dp, dp,
                                C.POINTER(C.c_int32), i32, C.POINTER(_SolveReport), vp]
+    L.sai_solve_batched.argtypes = [i32, C.POINTER(_CscView), C.POINTER(vp), C.POINTER(_SolveParams), C.POINTER(vp),
+                                    C.POINTER(_BatchItem), C.POINTER(_BatchReport), vp]
     L.sai_launch_count.restype = C.c_uint64
     L.sai_launch_count.argtypes = []
     L.sai_profile_begin.argtypes = []
     L.sai_profile_end.argtypes = [C.POINTER(_ProfReport)]
     for f in ("sai_profile_begin", "sai_profile_end", "sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
               "sai_precond_get_info", "sai_precond_copy_out", "sai_krylov_solve", "sai_smw_recover",
-              "sai_rel_resid", "sai_solve", "sai_solve_with", "sai_backward"):
+              "sai_rel_resid", "sai_solve", "sai_solve_with", "sai_backward", "sai_solve_batched"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -415,6 +428,32 @@ class SparseSolve(torch.autograd.Function):
         A, sp, P, kw = ctx.state
         lam, gv, _, _ = backward(A, sp, P, x, gx.contiguous(), grad_vals=ctx.needs_input_grad[2], **kw)
         return None, None, gv, lam, None
+
+
+def solve_batched(As, bs, sai="spai", eps=1e-8, maxit=500, thresh_mult=10.0, abs_tau=-1.0, delta=0.4, mn=5,
+                  max_aug=10, key_bits=20, tol=0.0, tol_mode=1, lmax=10, sai_precision=0):
+    """Procedure * for a batch of independent matrices (lists of CscMatrix and
+    device b vectors): one SAI build over all their columns, one batched
+    BiCGStab over all their s_i + 1 systems, SMW per matrix.
+    Returns (xs list, per-matrix list of dicts, batch report dict)."""
+    L = load()
+    nmat = len(As)
+    views = (_CscView * nmat)(*[A.view() for A in As])
+    xs = [torch.empty(A.n, dtype=torch.float64, device=b.device) for A, b in zip(As, bs)]
+    bp = (C.c_void_p * nmat)(*[_p(b.contiguous()).value for b in bs])
+    xp = (C.c_void_p * nmat)(*[_p(x).value for x in xs])
+    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0), 0 if sai == "spai" else 1,
+                       _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
+                       _PsaiParams(delta, tol, tol_mode, lmax, sai_precision),
+                       _KrylovParams(BICGSTAB, 50, maxit, 0, 0.0, 0), eps)
+    items = (_BatchItem * nmat)()
+    rep = _BatchReport()
+    st = _check("sai_solve_batched", L.sai_solve_batched(nmat, views, bp, C.byref(prm), xp, items, C.byref(rep),
+                                                         _stream()), allow=(SAI_MAXITER, SAI_BREAKDOWN))
+    per = [dict(status=it.status, iter_max=it.iter_max, s=it.s, p=it.p, c=it.c, rr=it.rr) for it in items]
+    report = {f: getattr(rep, f) for f, _ in _BatchReport._fields_}
+    report["status"] = st
+    return xs, per, report
 
 
 def launch_count():

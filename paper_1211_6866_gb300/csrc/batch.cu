@@ -1,0 +1,773 @@
+// batch.cu -- Procedure * (§3) for a batch of independent irregular systems.
+//
+// Split: each matrix on its own (sai_split_build: its own p and threshold).
+// Build: the A~_i are laid side by side as the block-diagonal A~ of the batch
+//   (CSC and CSR copied with row / column offsets) and M is built for all of
+//   its columns in one persistent launch of the SAI kernel: the column problems
+//   of a block only reach rows and columns of that block, so each M_i is the
+//   one its matrix alone would give.
+// Solve: the sum(s_i + 1) right-hand sides [b_i, u_i1 .. u_is_i] are Krylov
+//   systems of different lengths, stored one after another. Work items are
+//   (system, chunk of BR rows), one block each, listed once for the whole
+//   batch; a stopped system's items return at once. Inner products are summed
+//   per item in a fixed order and per system over its items in order. The
+//   control kernels run one warp (or thread) per system.
+// SMW: one block per matrix solves its s_i x s_i system (partial pivoting);
+//   then x_i = yhat_i - What_i z_i, and rr per matrix.
+#include <math.h>
+
+#include <memory>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BR = 256;  // rows per work item (one block, one thread per row)
+
+enum { B_OK = 0, B_MAXITER = 5, B_BREAKDOWN = 6 };  // same values as sai_status
+
+// System table of the batch (device arrays).
+struct BSys {
+    int32_t nsys;
+    const int64_t* off;     // start of system c's vectors in the batch vectors
+    const int32_t* len;     // n of its matrix
+    const int32_t* row0;    // first row of its matrix in the block-diagonal A~
+    const int32_t* first;   // first item of system c (first[nsys] = item count)
+    const int32_t* it_sys;  // system of item q
+    const int32_t* it_r0;   // first local row of item q
+    int32_t nitems;
+};
+
+// Per-system BiCGStab state.
+struct BState {
+    double *thr, *rho, *rho_old, *alpha, *omega, *beta;
+    int *active, *iters, *status, *mode, *go;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    return t;  // valid in thread 0
+}
+
+// Sum of the item partials of system c, in item order (one warp).
+__device__ __forceinline__ double sys_sum(const BSys& Y, const double* part, int c)
+{
+    const int lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int q = Y.first[c] + lane; q < Y.first[c + 1]; q += 32) a += part[q];
+    return warp_sum(a);
+}
+
+// y_c = A~ x_c (mode 0) for the systems with flag set, over their own block;
+// A~ in CSR with global row / column indices (block diagonal).
+__global__ void __launch_bounds__(BR) k_b_spmv(BSys Y, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                               const double* __restrict__ v, const double* __restrict__ X,
+                                               double* __restrict__ Yv, const int* flags)
+{
+    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+        const int c = Y.it_sys[q];
+        if (!flags[c]) continue;
+        const int64_t i = Y.it_r0[q] + threadIdx.x;
+        if (i >= Y.len[c]) continue;
+        const int64_t o = Y.off[c];
+        const int32_t r0 = Y.row0[c];
+        const int64_t b = rp[r0 + i], e = rp[r0 + i + 1];
+        double acc = 0.0;
+        for (int64_t q0 = b; q0 < e; q0 += 8) {
+            int32_t col[8];
+            double a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                col[u] = q0 + u < e ? ci[q0 + u] - r0 : 0;
+                a[u] = q0 + u < e ? v[q0 + u] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = fma(a[u], X[o + col[u]], acc);
+        }
+        Yv[o + i] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(BR) k_b_init(BSys Y, const double* __restrict__ B, double* x, double* r, double* rh,
+                                               double* p, double* v, double* part)
+{
+    __shared__ double sh[BR / 32];
+    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+        const int c = Y.it_sys[q];
+        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        double a = 0.0;
+        if (i < Y.len[c]) {
+            const double bv = B[o + i];
+            x[o + i] = 0.0;
+            r[o + i] = bv;
+            rh[o + i] = bv;
+            p[o + i] = 0.0;
+            v[o + i] = 0.0;
+            a = bv * bv;
+        }
+        const double t = block_sum(a, sh);
+        if (threadIdx.x == 0) part[q] = t;
+    }
+}
+
+// one warp per system
+__global__ void k_b_f0(BSys Y, const double* part, BState S)
+{
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= Y.nsys) return;
+    const double bb = sys_sum(Y, part, c);
+    if ((threadIdx.x & 31) == 0) {
+        S.iters[c] = 0;
+        S.rho[c] = bb;
+        S.alpha[c] = 1.0;
+        S.omega[c] = 1.0;
+        S.mode[c] = 1;
+        S.go[c] = 0;
+        if (sqrt(bb) < S.thr[c]) {
+            S.active[c] = 0;
+            S.status[c] = B_OK;
+        } else {
+            S.active[c] = 1;
+            S.status[c] = B_MAXITER;
+        }
+    }
+}
+
+__global__ void k_b_start(int32_t nsys, int maxit, BState S)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nsys || !S.active[c]) return;
+    if (S.iters[c] >= maxit) {
+        S.active[c] = 0;
+        S.status[c] = B_MAXITER;
+    } else {
+        S.iters[c] += 1;
+        if (S.rho[c] == 0.0) {
+            S.active[c] = 0;
+            S.status[c] = B_BREAKDOWN;
+        } else {
+            S.beta[c] = S.iters[c] == 1 ? 0.0 : (S.rho[c] / S.rho_old[c]) * (S.alpha[c] / S.omega[c]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BR) k_b_p(BSys Y, const double* __restrict__ r, double* p, const double* __restrict__ v,
+                                            BState S)
+{
+    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+        const int c = Y.it_sys[q];
+        if (!S.active[c]) continue;
+        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        if (i >= Y.len[c]) continue;
+        const double be = S.beta[c], om = S.omega[c];
+        p[o + i] = S.iters[c] == 1 ? r[o + i] : r[o + i] + be * (p[o + i] - om * v[o + i]);
+    }
+}
+
+template <int ND>
+__global__ void __launch_bounds__(BR) k_b_dots(BSys Y, const double* a0, const double* b0, const double* a1,
+                                               const double* b1, const int* flags, double* part)
+{
+    __shared__ double sh[BR / 32];
+    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+        const int c = Y.it_sys[q];
+        if (!flags[c]) continue;
+        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        double s0 = 0.0, s1 = 0.0;
+        if (i < Y.len[c]) {
+            s0 = a0[o + i] * b0[o + i];
+            if (ND > 1) s1 = a1[o + i] * b1[o + i];
+        }
+        const double t0 = block_sum(s0, sh);
+        const double t1 = ND > 1 ? block_sum(s1, sh) : 0.0;
+        if (threadIdx.x == 0) {
+            part[q] = t0;
+            if (ND > 1) part[Y.nitems + q] = t1;
+        }
+    }
+}
+
+__global__ void k_b_f1(BSys Y, const double* part, BState S)
+{
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= Y.nsys || !S.active[c]) return;
+    const double rv = sys_sum(Y, part, c);
+    if ((threadIdx.x & 31) == 0) {
+        if (rv == 0.0) {
+            S.active[c] = 0;
+            S.status[c] = B_BREAKDOWN;
+        } else {
+            S.alpha[c] = S.rho[c] / rv;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BR) k_b_s(BSys Y, const double* __restrict__ r, const double* __restrict__ v, double* s,
+                                            BState S, double* part)
+{
+    __shared__ double sh[BR / 32];
+    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+        const int c = Y.it_sys[q];
+        if (!S.active[c]) continue;
+        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        double a = 0.0;
+        if (i < Y.len[c]) {
+            const double sv = r[o + i] - S.alpha[c] * v[o + i];
+            s[o + i] = sv;
+            a = sv * sv;
+        }
+        const double t = block_sum(a, sh);
+        if (threadIdx.x == 0) part[q] = t;
+    }
+}
+
+__global__ void k_b_f2(BSys Y, const double* part, BState S)
+{
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= Y.nsys) return;
+    if (!S.active[c]) {
+        if ((threadIdx.x & 31) == 0) S.go[c] = 0;
+        return;
+    }
+    const double ss = sys_sum(Y, part, c);
+    if ((threadIdx.x & 31) == 0) {
+        S.mode[c] = sqrt(ss) < S.thr[c] ? 2 : 1;
+        S.go[c] = S.mode[c] == 1;
+    }
+}
+
+__global__ void k_b_f3(BSys Y, const double* part, BState S)
+{
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= Y.nsys || !S.go[c]) return;
+    const double ts = sys_sum(Y, part, c);
+    const double tt = sys_sum(Y, part + Y.nitems, c);
+    if ((threadIdx.x & 31) == 0) {
+        if (tt == 0.0) {
+            S.active[c] = 0;
+            S.go[c] = 0;
+            S.status[c] = B_BREAKDOWN;
+        } else {
+            S.omega[c] = ts / tt;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BR) k_b_xr(BSys Y, double* x, double* r, const double* __restrict__ rh,
+                                             const double* __restrict__ ph, const double* __restrict__ sh_,
+                                             const double* __restrict__ s, const double* __restrict__ t, BState S,
+                                             double* part)
+{
+    __shared__ double sh[BR / 32];
+    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+        const int c = Y.it_sys[q];
+        if (!S.active[c]) continue;
+        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        double a0 = 0.0, a1 = 0.0;
+        if (i < Y.len[c]) {
+            const double al = S.alpha[c], om = S.omega[c];
+            double rv;
+            if (S.mode[c] == 2) {
+                x[o + i] += al * ph[o + i];
+                rv = s[o + i];
+            } else {
+                x[o + i] += al * ph[o + i] + om * sh_[o + i];
+                rv = s[o + i] - om * t[o + i];
+            }
+            r[o + i] = rv;
+            a0 = rv * rv;
+            a1 = rh[o + i] * rv;
+        }
+        const double t0 = block_sum(a0, sh);
+        const double t1 = block_sum(a1, sh);
+        if (threadIdx.x == 0) {
+            part[q] = t0;
+            part[Y.nitems + q] = t1;
+        }
+    }
+}
+
+__global__ void k_b_f4(BSys Y, const double* part, BState S)
+{
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= Y.nsys || !S.active[c]) return;
+    const double rr = sys_sum(Y, part, c);
+    const double rhr = sys_sum(Y, part + Y.nitems, c);
+    if ((threadIdx.x & 31) == 0) {
+        if (S.mode[c] == 2 || sqrt(rr) < S.thr[c]) {
+            S.active[c] = 0;
+            S.status[c] = B_OK;
+        } else if (S.omega[c] == 0.0) {
+            S.active[c] = 0;
+            S.status[c] = B_BREAKDOWN;
+        } else {
+            S.rho_old[c] = S.rho[c];
+            S.rho[c] = rhr;
+        }
+    }
+}
+
+__global__ void k_b_any(int32_t nsys, const int* active, int* any)
+{
+    __shared__ int f;
+    if (threadIdx.x == 0) f = 0;
+    __syncthreads();
+    int a = 0;
+    for (int c = threadIdx.x; c < nsys; c += blockDim.x) a |= active[c];
+    if (a) f = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) *any = f;
+}
+
+// B = [b_i, u_i1 .. u_is] per matrix (U_i scattered into its systems)
+__global__ void k_b_rhs_b(int32_t n, const double* __restrict__ b, double* __restrict__ B)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) B[i] = b[i];
+}
+
+__global__ void k_b_rhs_u(int32_t s, const int64_t* Ucp, const int32_t* Uri, const double* Uv, int32_t n, double* B)
+{
+    const int t = blockIdx.x;  // column t of U goes to the system at B + (t + 1) * n
+    for (int64_t q = Ucp[t] + threadIdx.x; q < Ucp[t + 1]; q += blockDim.x) B[(int64_t)(t + 1) * n + Uri[q]] = Uv[q];
+}
+
+// Batched SMW: block m solves (I + What_m(J_m,:)) z = yhat_m(J_m) with partial
+// pivoting (the first largest |pivot| wins), C in shared memory.
+struct BSmw {
+    const int64_t* xoff;   // start of matrix m's first system (yhat) in X
+    const int32_t* n;      // order of matrix m
+    const int32_t* s;      // irregular columns of matrix m
+    const int64_t* joff;   // start of J_m in the concatenated J
+    const int32_t* J;
+    double* z;             // concatenated z_m (offset joff)
+    double* c;             // ||z_m||
+    int* err;              // singular flag per matrix
+};
+
+__global__ void k_b_smw(BSmw W, const double* __restrict__ X, int smax)
+{
+    extern __shared__ double smem[];
+    const int m = blockIdx.x;
+    const int s = W.s[m], n = W.n[m];
+    double* C = smem;                // s x s column-major
+    double* g = smem + (size_t)smax * smax;
+    __shared__ int piv_s;
+    const int64_t xo = W.xoff[m];
+    const int32_t* J = W.J + W.joff[m];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int col = e / s, row = e - col * s;
+        C[(size_t)col * s + row] = (row == col ? 1.0 : 0.0) + X[xo + (int64_t)(col + 1) * n + J[row]];
+    }
+    for (int a = threadIdx.x; a < s; a += blockDim.x) g[a] = X[xo + J[a]];
+    __syncthreads();
+    for (int k = 0; k < s; ++k) {
+        if (threadIdx.x == 0) {
+            int p = k;
+            double best = fabs(C[(size_t)k * s + k]);
+            for (int i = k + 1; i < s; ++i)
+                if (fabs(C[(size_t)k * s + i]) > best) {
+                    best = fabs(C[(size_t)k * s + i]);
+                    p = i;
+                }
+            piv_s = best > 0.0 ? p : -1;
+        }
+        __syncthreads();
+        const int p = piv_s;
+        if (p < 0) {
+            if (threadIdx.x == 0) W.err[m] = 1;
+            return;
+        }
+        if (p != k) {
+            for (int j = threadIdx.x; j < s; j += blockDim.x) {
+                const double t = C[(size_t)j * s + k];
+                C[(size_t)j * s + k] = C[(size_t)j * s + p];
+                C[(size_t)j * s + p] = t;
+            }
+            if (threadIdx.x == 0) {
+                const double t = g[k];
+                g[k] = g[p];
+                g[p] = t;
+            }
+        }
+        __syncthreads();
+        const double akk = C[(size_t)k * s + k];
+        const double gk = g[k];
+        for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) {
+            const double l = C[(size_t)k * s + i] / akk;
+            C[(size_t)k * s + i] = l;
+            for (int j = k + 1; j < s; ++j) C[(size_t)j * s + i] -= l * C[(size_t)j * s + k];
+            g[i] -= l * gk;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* z = W.z + W.joff[m];
+        double cc = 0.0;
+        for (int j = s - 1; j >= 0; --j) {
+            double t = g[j];
+            for (int i = j + 1; i < s; ++i) t -= C[(size_t)i * s + j] * z[i];
+            z[j] = t / C[(size_t)j * s + j];
+        }
+        for (int j = 0; j < s; ++j) cc += z[j] * z[j];
+        W.c[m] = sqrt(cc);
+        W.err[m] = 0;
+    }
+}
+
+__global__ void k_b_xhat(int32_t n, int32_t s, const double* __restrict__ X, const double* __restrict__ z,
+                         double* __restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = X[i];
+    for (int t = 0; t < s; ++t) v = fma(-X[(int64_t)(t + 1) * n + i], z[t], v);
+    x[i] = v;
+}
+
+__global__ void k_b_add_i64(int64_t cnt, const int64_t* __restrict__ a, int64_t add, int64_t* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] + add;
+}
+
+__global__ void k_b_add_i32(int64_t cnt, const int32_t* __restrict__ a, int32_t add, int32_t* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] + add;
+}
+
+struct Ev {
+    cudaEvent_t e = nullptr;
+    Ev() { cudaEventCreate(&e); }
+    ~Ev() { cudaEventDestroy(e); }
+};
+
+float ms_between(cudaEvent_t a, cudaEvent_t b)
+{
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    return t;
+}
+
+unsigned grid_for(int64_t work, int64_t cap)
+{
+    int64_t g = work < cap ? work : cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const* b, const sai_solve_params* prm,
+                        double* const* x, sai_batch_item* items, sai_batch_report* rep, cudaStream_t st)
+{
+    if (nmat < 1 || !A || !b || !prm || !x || !items || !rep) return SAI_INVALID_ARG;
+    if (prm->krylov.method != SAI_BICGSTAB || prm->krylov.precision != SAI_FP64 || prm->krylov.transpose)
+        return SAI_NOT_IMPLEMENTED;
+    if (prm->sai == 1 && prm->psai.tol_mode == 0) return SAI_NOT_IMPLEMENTED;
+    if (prm->krylov.maxit < 0) return SAI_INVALID_ARG;
+    *rep = sai_batch_report{};
+    int dev = 0, sms = 0;
+    SAI_CUDA(cudaGetDevice(&dev));
+    SAI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t cap = (int64_t)sms * 8;
+    Ev e0, e1, e2, e3, e4;
+    SAI_CUDA(cudaEventRecord(e0.e, st));
+
+    // ---- split, one matrix at a time
+    std::vector<std::unique_ptr<sai_split_s>> hs((size_t)nmat);
+    for (int32_t m = 0; m < nmat; ++m) {
+        if (A[m].n < 1 || (A[m].n > 0 && (!b[m] || !x[m]))) return SAI_INVALID_ARG;
+        hs[m].reset(new sai_split_s);
+        SAI_TRY(sai_split_build(&A[m], &prm->split, st, true, hs[m].get()));
+    }
+    SAI_CUDA(cudaEventRecord(e1.e, st));
+
+    // ---- the block-diagonal A~ of the batch (CSC and CSR), ||a~_j||^2
+    std::vector<int64_t> R0(nmat + 1, 0), Z0(nmat + 1, 0);
+    double norm1 = 0.0;
+    for (int32_t m = 0; m < nmat; ++m) {
+        R0[m + 1] = R0[m] + hs[m]->n;
+        Z0[m + 1] = Z0[m] + hs[m]->nnz_At;
+        norm1 = hs[m]->norm1 > norm1 ? hs[m]->norm1 : norm1;
+    }
+    const int64_t N = R0[nmat], NZ = Z0[nmat];
+    if (N > INT32_MAX - 1) return SAI_INVALID_ARG;
+    sai_split_s bd;
+    bd.n = (int32_t)N;
+    bd.nnz_At = NZ;
+    bd.norm1 = norm1;
+    SAI_TRY(bd.At_cp.alloc(sizeof(int64_t) * (size_t)(N + 1), st, true));
+    SAI_TRY(bd.At_ri.alloc(sizeof(int32_t) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.At_v.alloc(sizeof(double) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.Atr_rp.alloc(sizeof(int64_t) * (size_t)(N + 1), st, true));
+    SAI_TRY(bd.Atr_ci.alloc(sizeof(int32_t) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.Atr_v.alloc(sizeof(double) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.colnorm2.alloc(sizeof(double) * (size_t)N, st, true));
+    for (int32_t m = 0; m < nmat; ++m) {
+        const sai_split_s& h = *hs[m];
+        const int64_t n = h.n, z = h.nnz_At;
+        const unsigned gz = grid_for(sai_div_up(z > n ? z : n, 256), cap);
+        k_b_add_i64<<<SAI_GRID(gz), 256, 0, st>>>(n, h.At_cp.as<int64_t>(), Z0[m], bd.At_cp.as<int64_t>() + R0[m]);
+        k_b_add_i64<<<SAI_GRID(gz), 256, 0, st>>>(n, h.Atr_rp.as<int64_t>(), Z0[m], bd.Atr_rp.as<int64_t>() + R0[m]);
+        if (z > 0) {
+            k_b_add_i32<<<SAI_GRID(gz), 256, 0, st>>>(z, h.At_ri.as<int32_t>(), (int32_t)R0[m],
+                                                      bd.At_ri.as<int32_t>() + Z0[m]);
+            k_b_add_i32<<<SAI_GRID(gz), 256, 0, st>>>(z, h.Atr_ci.as<int32_t>(), (int32_t)R0[m],
+                                                      bd.Atr_ci.as<int32_t>() + Z0[m]);
+            SAI_CUDA(cudaMemcpyAsync(bd.At_v.as<double>() + Z0[m], h.At_v.p, sizeof(double) * z,
+                                     cudaMemcpyDeviceToDevice, st));
+            SAI_CUDA(cudaMemcpyAsync(bd.Atr_v.as<double>() + Z0[m], h.Atr_v.p, sizeof(double) * z,
+                                     cudaMemcpyDeviceToDevice, st));
+        }
+        SAI_CUDA(cudaMemcpyAsync(bd.colnorm2.as<double>() + R0[m], h.colnorm2.p, sizeof(double) * n,
+                                 cudaMemcpyDeviceToDevice, st));
+    }
+    SAI_CUDA(cudaMemcpyAsync(bd.At_cp.as<int64_t>() + N, &Z0[nmat], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SAI_CUDA(cudaMemcpyAsync(bd.Atr_rp.as<int64_t>() + N, &Z0[nmat], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SAI_CUDA(cudaGetLastError());
+
+    // ---- one SAI build for every column of the batch
+    sai_precond_s P;
+    if (prm->sai == 0) SAI_TRY(sai_spai_build(&bd, &prm->spai, st, true, &P));
+    else SAI_TRY(sai_psai_build(&bd, &prm->psai, st, true, &P));
+    SAI_CUDA(cudaEventRecord(e2.e, st));
+
+    // ---- system table: matrix m owns systems sys0[m] .. sys0[m] + s_m
+    std::vector<int32_t> sys0(nmat + 1, 0);
+    for (int32_t m = 0; m < nmat; ++m) sys0[m + 1] = sys0[m] + hs[m]->s + 1;
+    const int32_t nsys = sys0[nmat];
+    std::vector<int64_t> off(nsys);
+    std::vector<int32_t> len(nsys), row0(nsys), first(nsys + 1);
+    std::vector<int64_t> xoff(nmat), joff(nmat + 1, 0);
+    std::vector<int32_t> nvec(nmat), svec(nmat);
+    int64_t o = 0;
+    int32_t nit = 0;
+    int smax = 1;
+    for (int32_t m = 0; m < nmat; ++m) {
+        xoff[m] = o;
+        nvec[m] = hs[m]->n;
+        svec[m] = hs[m]->s;
+        joff[m + 1] = joff[m] + hs[m]->s;
+        smax = hs[m]->s > smax ? hs[m]->s : smax;
+        for (int32_t c = sys0[m]; c < sys0[m + 1]; ++c) {
+            off[c] = o;
+            len[c] = hs[m]->n;
+            row0[c] = (int32_t)R0[m];
+            first[c] = nit;
+            o += hs[m]->n;
+            nit += (hs[m]->n + BR - 1) / BR;
+        }
+    }
+    first[nsys] = nit;
+    const int64_t NV = o;
+    std::vector<int32_t> it_sys(nit), it_r0(nit);
+    for (int32_t c = 0; c < nsys; ++c)
+        for (int32_t q = first[c]; q < first[c + 1]; ++q) {
+            it_sys[q] = c;
+            it_r0[q] = (q - first[c]) * BR;
+        }
+    Buf tab, vecs, bst, bsi, part, misc;
+    const size_t tab_bytes = sizeof(int64_t) * (nsys + nmat + nmat + 1) +
+                             sizeof(int32_t) * (3 * (size_t)nsys + 1 + 2 * (size_t)nit + 2 * (size_t)nmat + joff[nmat] + 1);
+    SAI_TRY(tab.alloc(tab_bytes + 64, st, true));
+    char* tp = tab.as<char>();
+    auto put = [&](const void* src, size_t bytes) -> char* {
+        char* at = tp;
+        if (bytes) cudaMemcpyAsync(at, src, bytes, cudaMemcpyHostToDevice, st);
+        tp += (bytes + 7) & ~size_t(7);
+        return at;
+    };
+    BSys Y;
+    Y.nsys = nsys;
+    Y.nitems = nit;
+    Y.off = (const int64_t*)put(off.data(), sizeof(int64_t) * nsys);
+    Y.len = (const int32_t*)put(len.data(), sizeof(int32_t) * nsys);
+    Y.row0 = (const int32_t*)put(row0.data(), sizeof(int32_t) * nsys);
+    Y.first = (const int32_t*)put(first.data(), sizeof(int32_t) * (nsys + 1));
+    Y.it_sys = (const int32_t*)put(it_sys.data(), sizeof(int32_t) * nit);
+    Y.it_r0 = (const int32_t*)put(it_r0.data(), sizeof(int32_t) * nit);
+    BSmw W;
+    W.xoff = (const int64_t*)put(xoff.data(), sizeof(int64_t) * nmat);
+    W.n = (const int32_t*)put(nvec.data(), sizeof(int32_t) * nmat);
+    W.s = (const int32_t*)put(svec.data(), sizeof(int32_t) * nmat);
+    W.joff = (const int64_t*)put(joff.data(), sizeof(int64_t) * (nmat + 1));
+    {
+        int32_t* Jcat = (int32_t*)tp;
+        for (int32_t m = 0; m < nmat; ++m)
+            if (hs[m]->s > 0)
+                SAI_CUDA(cudaMemcpyAsync(Jcat + joff[m], hs[m]->J.p, sizeof(int32_t) * hs[m]->s,
+                                         cudaMemcpyDeviceToDevice, st));
+        W.J = Jcat;
+        tp += (sizeof(int32_t) * (size_t)joff[nmat] + 7) & ~size_t(7);
+    }
+    SAI_TRY(vecs.alloc(sizeof(double) * (size_t)NV * 11 + 64, st, true));
+    SAI_CUDA(cudaMemsetAsync(vecs.p, 0, sizeof(double) * (size_t)NV * 11, st));
+    double* Bv = vecs.as<double>();
+    double* X = Bv + NV;
+    double* r = X + NV;
+    double* rh = r + NV;
+    double* p = rh + NV;
+    double* v = p + NV;
+    double* ph = v + NV;
+    double* s = ph + NV;
+    double* sh = s + NV;
+    double* t = sh + NV;
+    SAI_TRY(bst.alloc(sizeof(double) * 6 * (size_t)nsys, st, true));
+    SAI_TRY(bsi.alloc(sizeof(int) * (5 * (size_t)nsys + 1), st, true));
+    SAI_TRY(part.alloc(sizeof(double) * 2 * (size_t)(nit > 0 ? nit : 1), st, true));
+    SAI_TRY(misc.alloc(sizeof(double) * ((size_t)joff[nmat] + 2 * (size_t)nmat + 4), st, true));
+    BState S;
+    double* dp = bst.as<double>();
+    S.thr = dp;
+    S.rho = dp + nsys;
+    S.rho_old = dp + 2 * nsys;
+    S.alpha = dp + 3 * nsys;
+    S.omega = dp + 4 * nsys;
+    S.beta = dp + 5 * nsys;
+    int* ip = bsi.as<int>();
+    S.active = ip;
+    S.iters = ip + nsys;
+    S.status = ip + 2 * nsys;
+    S.mode = ip + 3 * nsys;
+    S.go = ip + 4 * nsys;
+    int* any = ip + 5 * nsys;
+    SAI_CUDA(cudaMemsetAsync(ip, 0, sizeof(int) * (5 * (size_t)nsys + 1), st));
+
+    // right-hand sides and the Theorem 2 thresholds of each matrix
+    std::vector<double> thr(nsys);
+    for (int32_t m = 0; m < nmat; ++m) {
+        const sai_split_s& h = *hs[m];
+        double* Bm = Bv + xoff[m];
+        k_b_rhs_b<<<SAI_GRID(sai_div_up(h.n, 256)), 256, 0, st>>>(h.n, b[m], Bm);
+        if (h.s > 0)
+            k_b_rhs_u<<<SAI_GRID(h.s), 256, 0, st>>>(h.s, h.U_cp.as<int64_t>(), h.U_ri.as<int32_t>(),
+                                                     h.U_v.as<double>(), h.n, Bm);
+    }
+    SAI_CUDA(cudaGetLastError());
+    {
+        // ||b_m||: item partials of each matrix's first system, summed on the host in item order
+        k_b_init<<<SAI_GRID(grid_for(nit, cap)), BR, 0, st>>>(Y, Bv, X, r, rh, p, v, part.as<double>());
+        std::vector<double> hp(nit);
+        SAI_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * nit, cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaStreamSynchronize(st));
+        for (int32_t m = 0; m < nmat; ++m) {
+            const int32_t c0 = sys0[m];
+            double bb = 0.0;
+            for (int32_t q = first[c0]; q < first[c0 + 1]; ++q) bb += hp[q];
+            const double bn = sqrt(bb);
+            thr[c0] = 0.5 * prm->eps * bn;  // eq. (stopb)
+            for (int32_t c = c0 + 1; c < sys0[m + 1]; ++c)
+                thr[c] = prm->eps * bn / (2.0 * sqrt((double)hs[m]->s));  // eq. (stopU2), c = 1
+        }
+    }
+    SAI_CUDA(cudaMemcpyAsync(S.thr, thr.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st));
+    SAI_CUDA(cudaEventRecord(e3.e, st));
+
+    // ---- batched BiCGStab (right preconditioning: A~ M z = rhs, y = M z)
+    const int64_t *Ar = bd.Atr_rp.as<int64_t>(), *Mr = P.Mr_rp.as<int64_t>();
+    const int32_t *Ac = bd.Atr_ci.as<int32_t>(), *Mc = P.Mr_ci.as<int32_t>();
+    const double *Av = bd.Atr_v.as<double>(), *Mv = P.Mr_v.as<double>();
+    const unsigned gi = grid_for(nit, cap);
+    const unsigned gs = sai_div_up((int64_t)nsys * 32, 256), gt = sai_div_up(nsys, 256);
+    double* pt = part.as<double>();
+    const int maxit = prm->krylov.maxit;
+    k_b_f0<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
+    int hflag = 0;
+    for (int it = 0; it < maxit; ++it) {
+        k_b_start<<<SAI_GRID(gt), 256, 0, st>>>(nsys, maxit, S);
+        k_b_p<<<SAI_GRID(gi), BR, 0, st>>>(Y, r, p, v, S);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Mr, Mc, Mv, p, ph, S.active);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Ar, Ac, Av, ph, v, S.active);
+        k_b_dots<1><<<SAI_GRID(gi), BR, 0, st>>>(Y, rh, v, nullptr, nullptr, S.active, pt);
+        k_b_f1<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
+        k_b_s<<<SAI_GRID(gi), BR, 0, st>>>(Y, r, v, s, S, pt);
+        k_b_f2<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Mr, Mc, Mv, s, sh, S.go);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Ar, Ac, Av, sh, t, S.go);
+        k_b_dots<2><<<SAI_GRID(gi), BR, 0, st>>>(Y, t, s, t, t, S.go, pt);
+        k_b_f3<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
+        k_b_xr<<<SAI_GRID(gi), BR, 0, st>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
+        k_b_f4<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
+        SAI_CUDA(cudaGetLastError());
+        if ((it + 1) % 8 == 0 || it + 1 == maxit) {
+            k_b_any<<<SAI_GRID(1), 1024, 0, st>>>(nsys, S.active, any);
+            SAI_CUDA(cudaMemcpyAsync(&hflag, any, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            if (!hflag) break;
+        }
+    }
+    k_b_start<<<SAI_GRID(gt), 256, 0, st>>>(nsys, maxit, S);  // systems still running after maxit
+    SAI_CUDA(cudaGetLastError());
+    SAI_CUDA(cudaEventRecord(e4.e, st));
+
+    // ---- SMW per matrix, x_m = yhat_m - What_m z_m, rr per matrix
+    double* zcat = misc.as<double>();
+    double* cvec = zcat + joff[nmat];
+    int* errv = (int*)(cvec + nmat);
+    W.z = zcat;
+    W.c = cvec;
+    W.err = errv;
+    SAI_CUDA(cudaMemsetAsync(cvec, 0, sizeof(double) * nmat, st));
+    SAI_CUDA(cudaMemsetAsync(errv, 0, sizeof(int) * nmat, st));
+    const size_t smw_smem = sizeof(double) * ((size_t)smax * smax + smax);
+    if (smw_smem > 48 * 1024)
+        SAI_CUDA(cudaFuncSetAttribute(k_b_smw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw_smem));
+    k_b_smw<<<SAI_GRID(nmat), 256, smw_smem, st>>>(W, X, smax);
+    for (int32_t m = 0; m < nmat; ++m)
+        k_b_xhat<<<SAI_GRID(sai_div_up(hs[m]->n, 256)), 256, 0, st>>>(hs[m]->n, hs[m]->s, X + xoff[m], zcat + joff[m],
+                                                                     x[m]);
+    SAI_CUDA(cudaGetLastError());
+    Ev e5;
+    SAI_CUDA(cudaEventRecord(e5.e, st));
+    std::vector<int> it_h(nsys), st_h(nsys), err_h(nmat);
+    std::vector<double> c_h(nmat);
+    SAI_CUDA(cudaMemcpyAsync(it_h.data(), S.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaMemcpyAsync(st_h.data(), S.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaMemcpyAsync(err_h.data(), errv, sizeof(int) * nmat, cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaMemcpyAsync(c_h.data(), cvec, sizeof(double) * nmat, cudaMemcpyDeviceToHost, st));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    sai_status worst = SAI_OK;
+    for (int32_t m = 0; m < nmat; ++m) {
+        sai_batch_item& it = items[m];
+        it = sai_batch_item{};
+        it.s = hs[m]->s;
+        it.p = hs[m]->p;
+        it.c = c_h[m];
+        for (int32_t c = sys0[m]; c < sys0[m + 1]; ++c) {
+            if (it_h[c] > it.iter_max) it.iter_max = it_h[c];
+            if (st_h[c] != B_OK && it.status == SAI_OK) it.status = st_h[c];
+        }
+        if (err_h[m]) it.status = SAI_SINGULAR;
+        double nn[2] = {0.0, 0.0};
+        SAI_TRY(sai_csc_residual_norms(A[m].n, A[m].col_ptr, A[m].row_idx, A[m].val, b[m], x[m], nn, st));
+        it.rr = nn[1] > 0.0 ? sqrt(nn[0] / nn[1]) : sqrt(nn[0]);
+        if (it.iter_max > rep->iter_max) rep->iter_max = it.iter_max;
+        if (it.status != SAI_OK && worst == SAI_OK) worst = (sai_status)it.status;
+    }
+    rep->columns = N;
+    rep->nnz_M = P.nnz;
+    rep->systems = nsys;
+    rep->ms_split = ms_between(e0.e, e1.e);
+    rep->ms_build = ms_between(e1.e, e2.e);
+    rep->ms_krylov = ms_between(e2.e, e4.e);
+    rep->ms_smw = ms_between(e4.e, e5.e);
+    return worst;
+}
+
+}  // namespace
+
+extern "C" sai_status sai_solve_batched(int32_t nmat, const sai_csc_view* A, const double* const* b,
+                                        const sai_solve_params* prm, double* const* x, sai_batch_item* items,
+                                        sai_batch_report* rep, sai_stream_t stream)
+{
+    sai_pool_init_once();
+    return batched_impl(nmat, A, b, prm, x, items, rep, (cudaStream_t)stream);
+}

@@ -197,3 +197,44 @@ def aniso9_irregular(m=1024, eps=1e-3, theta_deg=30.0, s=50, density=0.02, seed=
     A, cols = add_dense_columns(aniso9(m, eps, theta_deg), s, density, rng)
     return _finish("aniso9_m%d_s%d" % (m, s), A, dict(m=m, eps=eps, theta_deg=theta_deg, s=s, density=density,
                                                     seed=seed, dense_cols=cols.tolist()))
+
+
+def rgg_irregular(n, seed, smax=20):
+    """One matrix of the batched workload: the Laplacian D - Adj of a random
+    geometric graph on n uniform points in the unit square with radius
+    sqrt(8/(pi n)) (average degree 8); each stored off-diagonal perturbed by
+    xi |a_ii|, xi ~ U(-0.1, 0.1) (nonsymmetric); then
+    a_jj = max(a_jj, 1.05 sum_{i != j} |a_ij|, 1) (strict column dominance, so
+    A~ stays nonsingular by Theorem 3(i); the 1 covers isolated points); plus
+    s ~ U{1..smax} dense N(0,1) columns of density ~U[1%, 10%]."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 2))
+    pairs = cKDTree(pts).query_pairs(np.sqrt(8.0 / (np.pi * n)), output_type="ndarray")
+    i, j = pairs[:, 0], pairs[:, 1]
+    deg = np.bincount(np.concatenate([i, j]), minlength=n).astype(np.float64)
+    r = np.concatenate([i, j])
+    c = np.concatenate([j, i])
+    v = -1.0 + rng.uniform(-0.1, 0.1, size=r.size) * deg[r]
+    A = sp.coo_matrix((np.concatenate([v, deg]), (np.concatenate([r, np.arange(n)]), np.concatenate([c, np.arange(n)]))),
+                      shape=(n, n)).tocsc()
+    A.sum_duplicates()
+
+    def dominate(A, floor):
+        d = A.diagonal()
+        off = np.asarray(abs(A).sum(axis=0)).ravel() - np.abs(d)
+        return sp.csc_matrix(A + sp.diags(np.maximum(np.maximum(np.abs(d), 1.05 * off), floor) - d))
+
+    A = dominate(A, 1.0)
+    s = int(rng.integers(1, smax + 1))
+    A, cols = add_dense_columns(A, s, float(rng.uniform(0.01, 0.10)), rng)
+    A = dominate(sp.csc_matrix(A, dtype=np.float64), 0.0)  # dominance again over the enlarged columns
+    return _finish("rgg_n%d" % n, A, dict(n=n, s_generated=s, dense_cols=cols.tolist(), seed=seed))
+
+
+def rgg_batch(count=256, nmin=1000, nmax=50000, seed=SEED_BASE + 3):
+    """The batched workload: count matrices of rgg_irregular with n ~ U[nmin, nmax]."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(nmin, nmax + 1, size=count)
+    return [rgg_irregular(int(n), seed=seed * 1000 + q) for q, n in enumerate(ns)]
