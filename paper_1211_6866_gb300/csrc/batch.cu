@@ -11,7 +11,9 @@
 //   (system, chunk of BR rows), one block each, listed once for the whole
 //   batch; a stopped system's items return at once. Inner products are summed
 //   per item in a fixed order and per system over its items in order. The
-//   control kernels run one warp (or thread) per system.
+//   control kernels run one warp (or thread) per system. Groups of 8
+//   iterations are captured once as a CUDA graph and replayed, with one host
+//   check of the "any system still running" flag per group.
 // SMW: one block per matrix solves its s_i x s_i system (partial pivoting);
 //   then x_i = yhat_i - What_i z_i, and rr per matrix.
 #include <math.h>
@@ -680,32 +682,80 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     double* pt = part.as<double>();
     const int maxit = prm->krylov.maxit;
     k_b_f0<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
-    int hflag = 0;
-    for (int it = 0; it < maxit; ++it) {
-        k_b_start<<<SAI_GRID(gt), 256, 0, st>>>(nsys, maxit, S);
-        k_b_p<<<SAI_GRID(gi), BR, 0, st>>>(Y, r, p, v, S);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Mr, Mc, Mv, p, ph, S.active);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Ar, Ac, Av, ph, v, S.active);
-        k_b_dots<1><<<SAI_GRID(gi), BR, 0, st>>>(Y, rh, v, nullptr, nullptr, S.active, pt);
-        k_b_f1<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
-        k_b_s<<<SAI_GRID(gi), BR, 0, st>>>(Y, r, v, s, S, pt);
-        k_b_f2<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Mr, Mc, Mv, s, sh, S.go);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Ar, Ac, Av, sh, t, S.go);
-        k_b_dots<2><<<SAI_GRID(gi), BR, 0, st>>>(Y, t, s, t, t, S.go, pt);
-        k_b_f3<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
-        k_b_xr<<<SAI_GRID(gi), BR, 0, st>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
-        k_b_f4<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
-        SAI_CUDA(cudaGetLastError());
-        if ((it + 1) % 8 == 0 || it + 1 == maxit) {
-            k_b_any<<<SAI_GRID(1), 1024, 0, st>>>(nsys, S.active, any);
-            SAI_CUDA(cudaMemcpyAsync(&hflag, any, sizeof(int), cudaMemcpyDeviceToHost, st));
-            SAI_CUDA(cudaStreamSynchronize(st));
-            if (!hflag) break;
+    SAI_CUDA(cudaGetLastError());
+    auto iteration = [&](cudaStream_t q) {
+        k_b_start<<<SAI_GRID(gt), 256, 0, q>>>(nsys, maxit, S);
+        k_b_p<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, p, v, S);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Mr, Mc, Mv, p, ph, S.active);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Ar, Ac, Av, ph, v, S.active);
+        k_b_dots<1><<<SAI_GRID(gi), BR, 0, q>>>(Y, rh, v, nullptr, nullptr, S.active, pt);
+        k_b_f1<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
+        k_b_s<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, v, s, S, pt);
+        k_b_f2<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Mr, Mc, Mv, s, sh, S.go);
+        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Ar, Ac, Av, sh, t, S.go);
+        k_b_dots<2><<<SAI_GRID(gi), BR, 0, q>>>(Y, t, s, t, t, S.go, pt);
+        k_b_f3<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
+        k_b_xr<<<SAI_GRID(gi), BR, 0, q>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
+        k_b_f4<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
+    };
+    constexpr int ITERS_PER_CHECK = 8, LAUNCHES = ITERS_PER_CHECK * 14 + 1;
+    // Groups of ITERS_PER_CHECK iterations (and the any-active test) run as one
+    // CUDA graph, captured once on a library stream ordered after the caller's;
+    // iterations past maxit change nothing (k_b_start retires those systems).
+    cudaStream_t q = st;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    if (!sai_prof_on()) {
+        cudaStream_t aux = sai_aux_stream();
+        if (aux) {
+            SAI_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+            SAI_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+            SAI_CUDA(cudaEventRecord(ev_in, st));
+            SAI_CUDA(cudaStreamWaitEvent(aux, ev_in, 0));
+            q = aux;
+            cudaGraph_t graph = nullptr;
+            SAI_CUDA(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < ITERS_PER_CHECK; ++k) iteration(q);
+            k_b_any<<<SAI_GRID(1), 1024, 0, q>>>(nsys, S.active, any);
+            cudaError_t e = cudaStreamEndCapture(q, &graph);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                gexec = nullptr;
+                (void)cudaGetLastError();
+            }
+            sai_count_grid_add(-(long long)LAUNCHES);  // captured, not run: counted at replay
         }
     }
-    k_b_start<<<SAI_GRID(gt), 256, 0, st>>>(nsys, maxit, S);  // systems still running after maxit
+    int hflag = 0;
+    sai_status kst = SAI_OK;
+    for (int it = 0; it < maxit; it += ITERS_PER_CHECK) {
+        if (gexec) {
+            if (cudaGraphLaunch(gexec, q) != cudaSuccess) {
+                kst = SAI_CUDA_ERROR;
+                break;
+            }
+            sai_count_grid_add(LAUNCHES);
+        } else {
+            for (int k = 0; k < ITERS_PER_CHECK; ++k) iteration(q);
+            k_b_any<<<SAI_GRID(1), 1024, 0, q>>>(nsys, S.active, any);
+        }
+        SAI_CUDA(cudaGetLastError());
+        SAI_CUDA(cudaMemcpyAsync(&hflag, any, sizeof(int), cudaMemcpyDeviceToHost, q));
+        SAI_CUDA(cudaStreamSynchronize(q));
+        if (!hflag) break;
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    k_b_start<<<SAI_GRID(gt), 256, 0, q>>>(nsys, maxit, S);  // systems still running after maxit
+    if (ev_in) {
+        cudaEventRecord(ev_out, q);
+        cudaStreamWaitEvent(st, ev_out, 0);
+        cudaEventDestroy(ev_in);
+        cudaEventDestroy(ev_out);
+    }
     SAI_CUDA(cudaGetLastError());
+    if (kst != SAI_OK) return kst;
     SAI_CUDA(cudaEventRecord(e4.e, st));
 
     // ---- SMW per matrix, x_m = yhat_m - What_m z_m, rr per matrix
