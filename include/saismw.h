@@ -142,6 +142,26 @@ typedef struct {
 
 typedef struct sai_precond_s* sai_precond;
 
+/* Schedule of the SAI build (not part of the method: every configuration
+ * gives the same M). warps_t0: warps per block of the shared-memory tier (4
+ * or 8); blocks_per_sm_t12: blocks per SM of the global-memory tiers (1, 2
+ * or 4); heavy_first: 1 puts the columns of A~ with more than twice the
+ * average entry count at the head of the work queue. ms: the sampled build
+ * time measured by sai_build_autotune (0 otherwise). Default {8, 2, 0}. */
+typedef struct {
+    int32_t warps_t0;
+    int32_t blocks_per_sm_t12;
+    int32_t heavy_first;
+    float ms;
+} sai_build_config;
+
+typedef struct {
+    sai_build_config chosen;
+    int32_t sample_columns;      /* columns of the strided sample timed */
+    int32_t ncand;
+    sai_build_config cand[12];   /* every candidate with its time */
+} sai_build_tuning;
+
 typedef struct {
     int32_t n;
     int64_t nnz_M;
@@ -154,6 +174,18 @@ typedef struct {
 sai_status sai_build_spai(sai_split h, const sai_spai_params* prm, sai_stream_t stream, sai_precond* out);
 sai_status sai_build_psai(sai_split h, const sai_psai_params* prm, sai_stream_t stream, sai_precond* out);
 sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info);
+
+/* Autotuner of the build schedule: times the build of a strided sample of
+ * h's columns (about 1/16 of them, at least 4096 when n allows) under each
+ * candidate configuration (warps_t0 x blocks_per_sm_t12 x heavy_first), with
+ * sai = 0 (SPAI, spai params) or 1 (PSAI, psai params), and makes the fastest
+ * the process-wide configuration of later builds. out (host) receives the
+ * candidates and the choice. Synchronises the stream. */
+sai_status sai_build_autotune(sai_split h, int32_t sai, const sai_spai_params* spai, const sai_psai_params* psai,
+                              sai_stream_t stream, sai_build_tuning* out);
+/* Sets the process-wide build configuration; NULL restores the default.
+ * Returns SAI_INVALID_ARG for values outside the candidate ranges. */
+sai_status sai_build_set_config(const sai_build_config* cfg);
 /* M as CSC (rows ascending per column): col_ptr n+1, row_idx/val nnz_M.
  * loops[n]: augmentation steps (SPAI) or last loop index (PSAI).
  * res[n]: final LS residual (pre-drop for PSAI). res_post[n] (PSAI only,

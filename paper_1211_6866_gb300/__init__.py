@@ -80,6 +80,16 @@ class _BatchReport(C.Structure):
                 ("ms_smw", C.c_double)]
 
 
+class _BuildConfig(C.Structure):
+    _fields_ = [("warps_t0", C.c_int32), ("blocks_per_sm_t12", C.c_int32), ("heavy_first", C.c_int32),
+                ("ms", C.c_float)]
+
+
+class _BuildTuning(C.Structure):
+    _fields_ = [("chosen", _BuildConfig), ("sample_columns", C.c_int32), ("ncand", C.c_int32),
+                ("cand", _BuildConfig * 12)]
+
+
 class _StageParams(C.Structure):
     _fields_ = [("krylov", _KrylovParams), ("eps", C.c_double)]
 
@@ -145,13 +155,17 @@ def load():
                                C.POINTER(C.c_int32), i32, C.POINTER(_SolveReport), vp]
     L.sai_solve_batched.argtypes = [i32, C.POINTER(_CscView), C.POINTER(vp), C.POINTER(_SolveParams), C.POINTER(vp),
                                     C.POINTER(_BatchItem), C.POINTER(_BatchReport), vp]
+    L.sai_build_autotune.argtypes = [vp, i32, C.POINTER(_SpaiParams), C.POINTER(_PsaiParams), vp,
+                                     C.POINTER(_BuildTuning)]
+    L.sai_build_set_config.argtypes = [C.POINTER(_BuildConfig)]
     L.sai_launch_count.restype = C.c_uint64
     L.sai_launch_count.argtypes = []
     L.sai_profile_begin.argtypes = []
     L.sai_profile_end.argtypes = [C.POINTER(_ProfReport)]
     for f in ("sai_profile_begin", "sai_profile_end", "sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
               "sai_precond_get_info", "sai_precond_copy_out", "sai_krylov_solve", "sai_smw_recover",
-              "sai_rel_resid", "sai_solve", "sai_solve_with", "sai_backward", "sai_solve_batched"):
+              "sai_rel_resid", "sai_solve", "sai_solve_with", "sai_backward", "sai_solve_batched",
+              "sai_build_autotune", "sai_build_set_config"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -273,6 +287,33 @@ def build_spai(sp, delta=0.4, mn=5, max_aug=10, key_bits=20, precision=0):
     prm = _SpaiParams(delta, mn, max_aug, key_bits, precision)
     _check("sai_build_spai", L.sai_build_spai(sp._h, C.byref(prm), _stream(), C.byref(h)))
     return Precond(h.value)
+
+
+def _cfg_dict(c):
+    return dict(warps_t0=c.warps_t0, blocks_per_sm_t12=c.blocks_per_sm_t12, heavy_first=c.heavy_first, ms=c.ms)
+
+
+def build_autotune(sp, sai="spai", delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10,
+                   precision=0):
+    """Times the build schedule candidates on a sample of sp's columns and makes
+    the fastest the configuration of later builds. Returns (chosen, candidates)."""
+    L = load()
+    t = _BuildTuning()
+    sprm = _SpaiParams(delta, mn, max_aug, key_bits, precision)
+    pprm = _PsaiParams(delta, tol, tol_mode, lmax, precision)
+    _check("sai_build_autotune", L.sai_build_autotune(sp._h, 0 if sai == "spai" else 1, C.byref(sprm), C.byref(pprm),
+                                                      _stream(), C.byref(t)))
+    return _cfg_dict(t.chosen), [_cfg_dict(t.cand[i]) for i in range(t.ncand)]
+
+
+def build_set_config(warps_t0=None, blocks_per_sm_t12=2, heavy_first=0):
+    """Sets the build schedule (warps_t0=None restores the default)."""
+    L = load()
+    if warps_t0 is None:
+        _check("sai_build_set_config", L.sai_build_set_config(None))
+    else:
+        c = _BuildConfig(warps_t0, blocks_per_sm_t12, heavy_first, 0.0)
+        _check("sai_build_set_config", L.sai_build_set_config(C.byref(c)))
 
 
 def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10, precision=0):

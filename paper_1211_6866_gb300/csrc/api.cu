@@ -236,6 +236,15 @@ sai_status sai_split_copy_out(sai_split h, int64_t* At_col_ptr, int32_t* At_row_
 
 void sai_split_destroy(sai_split h) { delete h; }
 
+sai_status sai_build_autotune(sai_split h, int32_t sai, const sai_spai_params* spai, const sai_psai_params* psai,
+                              sai_stream_t stream, sai_build_tuning* out)
+{
+    sai_pool_init_once();
+    return sai_build_autotune_run(h, sai, spai, psai, S(stream), out);
+}
+
+sai_status sai_build_set_config(const sai_build_config* cfg) { return sai_build_set_config_run(cfg); }
+
 sai_status sai_build_spai(sai_split h, const sai_spai_params* prm, sai_stream_t stream, sai_precond* out)
 {
     if (!out) return SAI_INVALID_ARG;

@@ -80,6 +80,9 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
                           const double* thr, const sai_krylov_params* prm, double* X, int32_t* iters,
                           int32_t* status, cudaStream_t st);
 sai_status sai_smw_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st);
+sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_spai_params* sp,
+                                  const sai_psai_params* pp, cudaStream_t st, sai_build_tuning* out);
+sai_status sai_build_set_config_run(const sai_build_config* cfg);
 // Theorem 1 for A^T = A~^T + V U^T: x = yhat - What (I + U^T What)^{-1} (U^T yhat)
 sai_status sai_smw_adj_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st);
 

@@ -28,6 +28,8 @@
 // the result does not depend on the tier that finished a column.
 #include <float.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace {
@@ -777,10 +779,10 @@ int g_num_sms = 0;
 template <class T, bool SMEM, bool PSAI>
 sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, const int32_t* work, int32_t nwork,
                        int* next, const Out& out, int32_t* ovf_list, int* ovf_cnt, int* err, int tier_id,
-                       cudaStream_t st)
+                       const sai_build_config& cfg, cudaStream_t st)
 {
     if (nwork <= 0) return SAI_OK;
-    const int warps_per_block = 8;
+    const int warps_per_block = SMEM ? cfg.warps_t0 : 8;
     const int threads = 32 * warps_per_block;
     int blocks;
     Buf scratch;
@@ -793,7 +795,7 @@ sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, 
         if (per_sm < 1) per_sm = 1;
         blocks = g_num_sms * per_sm;
     } else {
-        blocks = g_num_sms * 2;
+        blocks = g_num_sms * cfg.blocks_per_sm_t12;
         const int need = (nwork + warps_per_block - 1) / warps_per_block;
         if (blocks > need) blocks = need;
         SAI_TRY(scratch.alloc(T::BYTES * (size_t)warps_per_block * blocks, st, true));
@@ -824,10 +826,48 @@ struct Tiers<float> {
     using T2 = Tier2F;
 };
 
+// Build configuration: the tier-0 warps per block, the blocks per SM of the
+// global-memory tiers and the order of the tier-0 work queue (heavy_first:
+// the columns of A~ with more than twice the average number of entries, in
+// index order, then the rest, in index order). Every column's result is the
+// same under any configuration; only the schedule changes.
+std::mutex g_cfg_mu;
+sai_build_config g_cfg = {8, 2, 0, 0.f};
+
+sai_build_config current_config()
+{
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    return g_cfg;
+}
+
+// heavy[i] = nnz(A~ e_{list_i}) > thr (list = nullptr: i itself)
+__global__ void k_heavy_flags(int32_t m, const int32_t* __restrict__ list, const int64_t* __restrict__ cp, double thr,
+                              int32_t* __restrict__ flag)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = list ? list[i] : (int32_t)i;
+        flag[i] = (double)(cp[k + 1] - cp[k]) > thr;
+    }
+}
+
+// stable partition: heavy entries first (pos = prefix of heavy flags), then
+// the others (pos = H + i - prefix)
+__global__ void k_heavy_scatter(int32_t m, const int32_t* __restrict__ list, const int32_t* __restrict__ flag,
+                                const int64_t* __restrict__ pre, int32_t* __restrict__ out)
+{
+    const int64_t H = pre[m];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = list ? list[i] : (int32_t)i;
+        out[flag[i] ? pre[i] : H + (i - pre[i])] = k;
+    }
+}
+
 template <bool PSAI, class TQ>
 sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs& pa, int32_t smax, double delta,
-                        cudaStream_t st, bool async, sai_precond_s* P)
+                        cudaStream_t st, bool async, sai_precond_s* P, const int32_t* cols = nullptr,
+                        int32_t ncols = -1, const sai_build_config* cfgp = nullptr)
 {
+    const sai_build_config cfg = cfgp ? *cfgp : current_config();
     if (g_num_sms == 0) {
         int dev = 0;
         SAI_CUDA(cudaGetDevice(&dev));
@@ -878,19 +918,36 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     using T0 = typename Tiers<TQ>::T0;
     using T1 = typename Tiers<TQ>::T1;
     using T2 = typename Tiers<TQ>::T2;
-    SAI_TRY((launch_tier<T0, true, PSAI>(A, sa, pa, nullptr, n, c + 0, out, ovf0.as<int32_t>(), c + 1, c + 3, 0,
+    // tier-0 work queue: all columns (or the given list), optionally heavy ones first
+    const int32_t nq = cols ? ncols : n;
+    const int32_t* queue = cols;
+    Buf qbuf, qflag, qpre;
+    if (cfg.heavy_first && nq > 0) {
+        SAI_TRY(qbuf.alloc(sizeof(int32_t) * (size_t)nq, st, true));
+        SAI_TRY(qflag.alloc(sizeof(int32_t) * (size_t)nq, st, true));
+        SAI_TRY(qpre.alloc(sizeof(int64_t) * ((size_t)nq + 1), st, true));
+        const double thr = n > 0 ? 2.0 * (double)h->nnz_At / (double)n : 0.0;
+        const unsigned g = sai_div_up(nq, 256) < (unsigned)g_num_sms * 8 ? sai_div_up(nq, 256) : g_num_sms * 8;
+        k_heavy_flags<<<SAI_GRID(g), 256, 0, st>>>(nq, cols, A.cp, thr, qflag.as<int32_t>());
+        SAI_TRY(sai_scan_counts_i32(qflag.as<int32_t>(), qpre.as<int64_t>(), nq, st));
+        k_heavy_scatter<<<SAI_GRID(g), 256, 0, st>>>(nq, cols, qflag.as<int32_t>(), qpre.as<int64_t>(),
+                                                     qbuf.as<int32_t>());
+        SAI_CUDA(cudaGetLastError());
+        queue = qbuf.as<int32_t>();
+    }
+    SAI_TRY((launch_tier<T0, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovf0.as<int32_t>(), c + 1, c + 3, 0, cfg,
                                             st)));
     int hc[4];
     SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));
     if (hc[1] > 0) {
         SAI_TRY((launch_tier<T1, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), hc[1], c + 0, out, ovf1.as<int32_t>(),
-                                                 c + 2, c + 3, 1, st)));
+                                                 c + 2, c + 3, 1, cfg, st)));
         SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
         SAI_CUDA(cudaStreamSynchronize(st));
         if (hc[2] > 0)
             SAI_TRY((launch_tier<T2, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out, nullptr,
-                                                     nullptr, c + 3, 2, st)));
+                                                     nullptr, c + 3, 2, cfg, st)));
     }
     // assemble M (CSC, rows ascending) and its CSR copy
     SAI_TRY(P->M_cp.alloc(sizeof(int64_t) * (nn + 1), st, async));
@@ -969,6 +1026,123 @@ sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cuda
     if (prm->precision == SAI_FP32_REFINE64)
         return build_common<true, float>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
     return build_common<true, double>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
+}
+
+namespace {
+__global__ void k_strided(int32_t m, int32_t stride, int32_t* out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)(i * stride);
+}
+
+bool config_ok(const sai_build_config& c)
+{
+    return (c.warps_t0 == 4 || c.warps_t0 == 8) &&
+           (c.blocks_per_sm_t12 == 1 || c.blocks_per_sm_t12 == 2 || c.blocks_per_sm_t12 == 4) &&
+           (c.heavy_first == 0 || c.heavy_first == 1);
+}
+}  // namespace
+
+sai_status sai_build_set_config_run(const sai_build_config* cfg)
+{
+    sai_build_config c = cfg ? *cfg : sai_build_config{8, 2, 0, 0.f};
+    if (!config_ok(c)) return SAI_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    g_cfg = c;
+    return SAI_OK;
+}
+
+sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_spai_params* sp,
+                                  const sai_psai_params* pp, cudaStream_t st, sai_build_tuning* out)
+{
+    if (!h || !out || (sai != 0 && sai != 1) || (sai == 0 && !sp) || (sai == 1 && !pp)) return SAI_INVALID_ARG;
+    // parameters are checked by a full-validation build path below (same rules)
+    if (sai == 0 && (sp->mn < 1 || sp->mn > MNMAX || sp->max_aug < 0 || sp->key_bits < 1 || sp->key_bits > 31 ||
+                     !(sp->delta >= 0.0) || (sp->precision != SAI_FP64 && sp->precision != SAI_FP32_REFINE64)))
+        return SAI_INVALID_ARG;
+    if (sai == 1 && (pp->lmax < 0 || (pp->tol_mode != 0 && pp->tol_mode != 1) || !(pp->delta >= 0.0) ||
+                     !(pp->tol >= 0.0) || (pp->precision != SAI_FP64 && pp->precision != SAI_FP32_REFINE64)))
+        return SAI_INVALID_ARG;
+    if (g_num_sms == 0) {
+        int dev = 0;
+        SAI_CUDA(cudaGetDevice(&dev));
+        SAI_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    *out = sai_build_tuning{};
+    const int32_t n = h->n;
+    if (n <= 0) return SAI_OK;
+    int32_t stride = n / 65536 > 1 ? n / 65536 : 1;
+    if (n / stride < 4096 && stride > 1) stride = n / 4096 > 1 ? n / 4096 : 1;
+    const int32_t m = (n + stride - 1) / stride;
+    Buf list;
+    SAI_TRY(list.alloc(sizeof(int32_t) * (size_t)m, st, true));
+    k_strided<<<SAI_GRID(sai_div_up(m, 256) < 1024u ? sai_div_up(m, 256) : 1024u), 256, 0, st>>>(m, stride,
+                                                                                             list.as<int32_t>());
+    SAI_CUDA(cudaGetLastError());
+    SpaiArgs sa = {};
+    PsaiArgs pa = {};
+    int32_t smax = Tier2::SCAP;
+    double delta = 0.0;
+    bool f32 = false;
+    if (sai == 0) {
+        sa.delta = sp->delta;
+        sa.scale = ldexp(1.0, sp->key_bits);
+        sa.mn = sp->mn;
+        sa.max_aug = sp->max_aug;
+        const long long bound = 1 + (long long)sp->mn * sp->max_aug;
+        smax = (int32_t)(bound < Tier2::SCAP ? bound : Tier2::SCAP);
+        delta = sp->delta;
+        f32 = sp->precision == SAI_FP32_REFINE64;
+    } else {
+        pa.delta = pp->delta;
+        pa.tol = pp->tol;
+        pa.tol_mode = pp->tol_mode;
+        pa.lmax = pp->lmax;
+        delta = pp->delta;
+        f32 = pp->precision == SAI_FP32_REFINE64;
+    }
+    cudaEvent_t e0, e1;
+    SAI_CUDA(cudaEventCreate(&e0));
+    SAI_CUDA(cudaEventCreate(&e1));
+    int best = -1;
+    for (int w : {4, 8})
+        for (int b : {1, 2, 4})
+            for (int hf : {0, 1}) {
+                sai_build_config c = {w, b, hf, 0.f};
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {  // the first run warms the pool and the caches
+                    sai_precond_s P;
+                    SAI_CUDA(cudaEventRecord(e0, st));
+                    sai_status r;
+                    if (sai == 0)
+                        r = f32 ? build_common<false, float>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(),
+                                                             m, &c)
+                                : build_common<false, double>(h, sa, pa, smax, delta, st, true, &P,
+                                                              list.as<int32_t>(), m, &c);
+                    else
+                        r = f32 ? build_common<true, float>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(),
+                                                            m, &c)
+                                : build_common<true, double>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(),
+                                                             m, &c);
+                    if (r != SAI_OK) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return r;
+                    }
+                    SAI_CUDA(cudaEventRecord(e1, st));
+                    SAI_CUDA(cudaEventSynchronize(e1));
+                    SAI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                }
+                c.ms = ms;
+                out->cand[out->ncand] = c;
+                if (best < 0 || ms < out->cand[best].ms) best = out->ncand;
+                ++out->ncand;
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out->chosen = out->cand[best];
+    out->sample_columns = m;
+    return sai_build_set_config_run(&out->chosen);
 }
 
 sai_status sai_build_work_reset()
