@@ -768,10 +768,13 @@ __global__ void k_stats(int32_t n, const int32_t* loops, const double* res, doub
     }
 }
 
+// columns not built in this call (outside a column list) hold tier -1
 __global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&out[2 + tier[k]], 1);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int t = tier[k];
+        if (t >= 0 && t < 3) atomicAdd(&out[2 + t], 1);
+    }
 }
 
 int g_num_sms = 0;
@@ -904,6 +907,10 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     SAI_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(int) * 16, st));
     SAI_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->res_post.p, 0, sizeof(double) * nn, st));
+    // per-column outputs start defined: a column list builds only some columns
+    SAI_CUDA(cudaMemsetAsync(tier.p, 0xff, sizeof(int32_t) * nn, st));
+    SAI_CUDA(cudaMemsetAsync(P->loops.p, 0, sizeof(int32_t) * nn, st));
+    SAI_CUDA(cudaMemsetAsync(P->res.p, 0, sizeof(double) * nn, st));
     int* c = ctr.as<int>();  // [0] next, [1] ovf count t0, [2] ovf count t1, [3] err, [4..] stats
     Out out;
     out.smax = smax;
