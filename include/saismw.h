@@ -167,7 +167,7 @@ typedef struct {
     int64_t nnz_M;
     int32_t n_c;        /* columns whose final (pre-drop) residual > delta */
     int32_t l_m;        /* largest loop index used over all columns */
-    int32_t n_tier[3];  /* columns finished per workspace tier */
+    int32_t n_tier[4];  /* columns finished per workspace tier: 0 shared memory, 1-3 global memory */
     double build_ms;    /* device time of the build, CUDA events */
 } sai_precond_info;
 
@@ -220,6 +220,9 @@ typedef struct {
 } sai_krylov_params;
 
 /* B, X: n x k row-major device blocks. thr, iters, status: host arrays of k.
+ * k: 1..256 for GMRES and the refined form; 1..262144 for FP64 BiCGStab
+ * (SAI_INVALID_ARG beyond). The solver keeps about 10 n x k FP64 blocks of
+ * its own (BiCGStab) and returns SAI_OOM when they do not fit.
  * Returns SAI_OK, SAI_MAXITER or SAI_BREAKDOWN (the first non-OK system
  * status), or an error. Synchronises the stream. */
 sai_status sai_krylov_solve(sai_split h, sai_precond P, int32_t k, const double* B, const double* thr,
@@ -231,7 +234,10 @@ sai_status sai_krylov_solve(sai_split h, sai_precond P, int32_t k, const double*
  *   xhat = yhat - What (I + V^T What)^{-1} (V^T yhat)
  * Y: n x (s+1) row-major, column 0 = yhat, columns 1..s = What.
  * x: n. c_out (host, may be NULL): c = ||(I + V^T What)^{-1} V^T yhat||.
- * Gaussian elimination with partial pivoting on the s x s matrix.
+ * Gaussian elimination with partial pivoting on the s x s matrix (the
+ * largest |pivot|, the first row on ties): one thread block for s <= 256, a
+ * blocked right-looking LU (panels of 16 columns, FP64 tiles for the
+ * trailing update) for larger s. SAI_SINGULAR on a zero pivot.
  * ---------------------------------------------------------------------- */
 sai_status sai_smw_recover(sai_split h, const double* Y, double* x, double* c_out, sai_stream_t stream);
 

@@ -284,7 +284,7 @@ sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info)
     info->nnz_M = P->nnz;
     info->n_c = P->n_c;
     info->l_m = P->l_m;
-    for (int q = 0; q < 3; ++q) info->n_tier[q] = P->n_tier[q];
+    for (int q = 0; q < 4; ++q) info->n_tier[q] = P->n_tier[q];
     info->build_ms = P->ms;
     return SAI_OK;
 }
@@ -336,16 +336,20 @@ sai_status sai_rel_resid(const sai_csc_view* A, const double* b, const double* x
 // ---------------------------------------------------------------- Procedure *
 namespace {
 
-// B = [b, u_1 .. u_s] as an n x (s+1) row-major block
-__global__ void k_fill_rhs(int32_t n, int32_t s, const double* b, const int64_t* Ucp, const int32_t* Uri,
-                           const double* Uv, double* B)
+// column 0 of the n x (s+1) row-major block B (the rest is cleared first)
+__global__ void k_put_col0(int32_t n, int32_t s, const double* b, double* B)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t ld = (int64_t)s + 1;
-    if (i < n) {
-        B[i * ld] = b[i];
-        for (int t = 0; t < s; ++t) B[i * ld + 1 + t] = 0.0;
-    }
+    if (i < n) B[i * ((int64_t)s + 1)] = b[i];
+}
+
+// B = [b, 0 .. 0] as an n x (s+1) row-major block
+sai_status fill_rhs(int32_t n, int32_t s, const double* b, double* B, cudaStream_t st)
+{
+    if (n <= 0) return SAI_OK;
+    SAI_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)n * ((size_t)s + 1), st));
+    k_put_col0<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, b, B);
+    return SAI_OK;
 }
 
 __global__ void k_scatter_U(int32_t s, const int64_t* Ucp, const int32_t* Uri, const double* Uv, double* B)
@@ -440,7 +444,7 @@ void report_handles(const sai_split_s& h, const sai_precond_s& P, sai_solve_repo
     rep->precond.nnz_M = P.nnz;
     rep->precond.n_c = P.n_c;
     rep->precond.l_m = P.l_m;
-    for (int q = 0; q < 3; ++q) rep->precond.n_tier[q] = P.n_tier[q];
+    for (int q = 0; q < 4; ++q) rep->precond.n_tier[q] = P.n_tier[q];
     rep->precond.build_ms = P.ms;
 }
 
@@ -504,7 +508,7 @@ sai_status solve_steps(const sai_csc_view* A, const sai_split_s& h, const sai_pr
     Buf Bb, Yb;
     SAI_TRY(Bb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
     SAI_TRY(Yb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
-    if (n > 0) k_fill_rhs<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, b, nullptr, nullptr, nullptr, Bb.as<double>());
+    SAI_TRY(fill_rhs(n, s, b, Bb.as<double>(), st));
     if (s > 0)
         k_scatter_U<<<SAI_GRID(s), 256, 0, st>>>(s, h.U_cp.as<int64_t>(), h.U_ri.as<int32_t>(), h.U_v.as<double>(),
                                        Bb.as<double>());
@@ -592,7 +596,7 @@ sai_status backward_impl(const sai_csc_view* A, const sai_split_s* h, const sai_
     Buf Bb, Yb;
     SAI_TRY(Bb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
     SAI_TRY(Yb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
-    if (n > 0) k_fill_rhs<<<SAI_GRID(sai_div_up(n, 256)), 256, 0, st>>>(n, s, g, nullptr, nullptr, nullptr, Bb.as<double>());
+    SAI_TRY(fill_rhs(n, s, g, Bb.as<double>(), st));
     if (s > 0) k_set_units<<<SAI_GRID(sai_div_up(s, 256)), 256, 0, st>>>(s, h->J.as<int32_t>(), Bb.as<double>());
     SAI_CUDA(cudaGetLastError());
     double gnorm = 0.0;

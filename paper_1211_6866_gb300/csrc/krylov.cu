@@ -29,7 +29,8 @@
 
 namespace {
 
-constexpr int CTRL = 256;      // threads of the single-block control kernels (>= k)
+constexpr int CTRL = 256;      // threads of the single-block control kernels (>= k of GMRES)
+constexpr int KBIG = 1 << 18;  // systems per FP64 BiCGStab call (its control kernels loop over systems)
 constexpr int CHUNK = 1024;    // rows per (system, chunk) reduction item (one warp)
 constexpr int CHUNK_U = 256;   // rows per item of the GMRES update (no per-vector reduction)
 constexpr int TILE = 256;      // rows per SpMV item (one block)
@@ -75,6 +76,45 @@ __device__ __forceinline__ void build_list(int k, const int* mask, int* list)
     list[0] = q;
 }
 
+// The same list built by the whole block (any k): each thread counts a
+// contiguous run of systems, a block scan gives each run its offset, and the
+// runs are written in order, so the list is ascending like build_list's.
+// Every thread of the block calls it after a __syncthreads that makes the
+// mask final; it ends with one, so list[0] is visible to the block after it.
+__device__ void build_list_block(int k, const int* mask, int* list)
+{
+    __shared__ int wsum[32];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5, nwarps = (nt + 31) >> 5;
+    const int per = (k + nt - 1) / nt;
+    const int c0 = tid * per < k ? tid * per : k;
+    const int c1 = c0 + per < k ? c0 + per : k;
+    int cnt = 0;
+    for (int c = c0; c < c1; ++c) cnt += mask[c] != 0;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(SAI_FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int v = lane < nwarps ? wsum[lane] : 0;
+        int w = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(SAI_FULL, w, o);
+            if (lane >= o) w += u;
+        }
+        if (lane < nwarps) wsum[lane] = w - v;  // exclusive offset of warp `lane`
+    }
+    __syncthreads();
+    int pos = wsum[wid] + incl - cnt;
+    for (int c = c0; c < c1; ++c)
+        if (mask[c]) list[1 + pos++] = c;
+    if (tid == nt - 1) list[0] = pos;
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- layout
 __global__ void k_to_soa(int64_t n, int k, int64_t ld, const double* __restrict__ B, double* __restrict__ Bs)
 {
@@ -94,12 +134,66 @@ __global__ void k_from_soa(int64_t n, int k, int64_t ld, const double* __restric
     }
 }
 
+// The same two copies through 32 x 32 shared-memory tiles (32 x 8 threads),
+// so that both the row-major and the system-major side are accessed in
+// contiguous runs; used when k is at least 32.
+template <bool TO_SOA>
+__global__ void __launch_bounds__(256) k_soa_tiled(int64_t n, int k, int64_t ld, const double* __restrict__ src,
+                                                   double* __restrict__ dst)
+{
+    __shared__ double tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t ti = (n + 31) / 32, tc = (k + 31) / 32;
+    for (int64_t t = blockIdx.x; t < ti * tc; t += gridDim.x) {
+        const int64_t i0 = (t / tc) * 32;
+        const int c0 = (int)(t % tc) * 32;
+        if (TO_SOA) {
+            for (int j = ty; j < 32; j += 8) {  // rows i0 + j, columns c0 + tx
+                const int64_t i = i0 + j;
+                const int c = c0 + tx;
+                if (i < n && c < k) tile[j][tx] = src[i * k + c];
+            }
+            __syncthreads();
+            for (int j = ty; j < 32; j += 8) {  // system c0 + j, rows i0 + tx
+                const int c = c0 + j;
+                const int64_t i = i0 + tx;
+                if (i < n && c < k) dst[(int64_t)c * ld + i] = tile[tx][j];
+            }
+        } else {
+            for (int j = ty; j < 32; j += 8) {  // system c0 + j, rows i0 + tx
+                const int c = c0 + j;
+                const int64_t i = i0 + tx;
+                if (i < n && c < k) tile[tx][j] = src[(int64_t)c * ld + i];
+            }
+            __syncthreads();
+            for (int j = ty; j < 32; j += 8) {  // rows i0 + j, columns c0 + tx
+                const int64_t i = i0 + j;
+                const int c = c0 + tx;
+                if (i < n && c < k) dst[i * k + c] = tile[j][tx];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- SpMV over a list
+// When the k systems' vectors exceed what L2 holds next to the matrix, the
+// SpMVs take their items system-group-major (template flag GM, chosen on the
+// host from k): the warps running at one time then gather from the vectors
+// of a few systems, which stay in L2, instead of from all of them. Each
+// item's arithmetic is the same either way.
+constexpr int64_t SPMV_GMAJ_BYTES = 64ll << 20;
+inline bool spmv_group_major(int k, int64_t n, size_t esz)
+{
+    return (int64_t)k * n * (int64_t)esz > SPMV_GMAJ_BYTES;
+}
+
 // Y[c] = A X[c] (mode 0), B[c] - A X[c] (mode 1) or Y[c] + A X[c] (mode 2) for the systems in list, in
 // the value type T (FP64, or FP32 for the inner solves of the refined GMRES).
 // Items are (row tile, system), tile-major, so the systems of a tile reuse
-// the tile's matrix rows from cache. One thread per row (CSR).
-template <class T, int MODE>
+// the tile's matrix rows from cache (system-group-major for many systems, as
+// above). One thread per row (CSR).
+template <class T, int MODE, bool GM>
 __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const T* __restrict__ v,
                                                const T* __restrict__ X, T* __restrict__ Y,
@@ -112,8 +206,8 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
     const int groups = (cnt + CT - 1) / CT;
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
     for (int64_t it = blockIdx.x; it < tiles * groups; it += gridDim.x) {
-        const int64_t tile = it / groups;
-        const int g0 = (int)(it - tile * groups) * CT;
+        const int64_t tile = GM ? it % tiles : it / groups;
+        const int g0 = (int)(GM ? it / tiles : it - tile * groups) * CT;
         const int ng = min(CT, cnt - g0);
         const int64_t row = tile * TILE + threadIdx.x;
         if (row >= n) continue;
@@ -173,8 +267,13 @@ struct Mat {
 // width <= SELL_W keeps its entries in registers and loops over the listed
 // systems SELL_CT at a time, so the matrix is read once for all systems and
 // each system costs only its gathers; wider slices take the entries in
-// batches of SELL_W per group of systems.
-template <class T, int MODE>
+// batches of SELL_W per group of systems. With many systems (the
+// system-group-major case above) a warp's item is one slice for a
+// supergroup of SELL_SG systems, supergroup-major, which keeps the gathers
+// in L2 and gives every SM enough warps; otherwise an item is a slice for
+// all listed systems.
+constexpr int SELL_SG = 16;
+template <class T, int MODE, bool GM>
 __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T> Am, const T* __restrict__ X,
                                                    T* __restrict__ Y, const T* __restrict__ B,
                                                    const int* __restrict__ list, const int* __restrict__ jstop, int jmax)
@@ -182,10 +281,15 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
     constexpr int CT = SELL_CT, W = SELL_W;
     if (jstop && *jstop >= jmax) return;  // the step needs no operator application
     const int cnt = list[0];
+    const int64_t nitems = GM ? (int64_t)((cnt + SELL_SG - 1) / SELL_SG) * Am.nslices : Am.nslices;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t sl = w0; sl < Am.nslices; sl += nw) {
+    for (int64_t itm = w0; itm < nitems; itm += nw) {
+        const int64_t sgi = GM ? itm / Am.nslices : 0;
+        const int64_t sl = GM ? itm - sgi * Am.nslices : itm;
+        const int gb = GM ? (int)sgi * SELL_SG : 0;
+        const int ge = GM ? (gb + SELL_SG < cnt ? gb + SELL_SG : cnt) : cnt;
         const int64_t b = Am.sp[sl], e = Am.sp[sl + 1];
         const int64_t row = sl * SELL_C + lane;
         if (e - b <= (int64_t)W * SELL_C) {
@@ -197,10 +301,10 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
                 col[u] = q < e ? Am.sci[q] : 0;
                 a[u] = q < e ? Am.sv[q] : (T)0;
             }
-            for (int g0 = 0; g0 < cnt; g0 += CT) {
+            for (int g0 = gb; g0 < ge; g0 += CT) {
                 int64_t off[CT];
 #pragma unroll
-                for (int t = 0; t < CT; ++t) off[t] = g0 + t < cnt ? (int64_t)list[1 + g0 + t] * ld : 0;
+                for (int t = 0; t < CT; ++t) off[t] = g0 + t < ge ? (int64_t)list[1 + g0 + t] * ld : 0;
                 T acc[CT];
 #pragma unroll
                 for (int t = 0; t < CT; ++t) acc[t] = 0;
@@ -208,11 +312,11 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
                 for (int u = 0; u < W; ++u)
 #pragma unroll
                     for (int t = 0; t < CT; ++t)
-                        if (g0 + t < cnt) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
+                        if (g0 + t < ge) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
                 if (row < n) {
 #pragma unroll
                     for (int t = 0; t < CT; ++t) {
-                        if (g0 + t < cnt) {
+                        if (g0 + t < ge) {
                             if (MODE == 0) Y[off[t] + row] = acc[t];
                             else if (MODE == 1) Y[off[t] + row] = B[off[t] + row] - acc[t];
                             else Y[off[t] + row] += acc[t];
@@ -221,10 +325,10 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
                 }
             }
         } else {
-            for (int g0 = 0; g0 < cnt; g0 += CT) {
+            for (int g0 = gb; g0 < ge; g0 += CT) {
                 int64_t off[CT];
 #pragma unroll
-                for (int t = 0; t < CT; ++t) off[t] = g0 + t < cnt ? (int64_t)list[1 + g0 + t] * ld : 0;
+                for (int t = 0; t < CT; ++t) off[t] = g0 + t < ge ? (int64_t)list[1 + g0 + t] * ld : 0;
                 T acc[CT];
 #pragma unroll
                 for (int t = 0; t < CT; ++t) acc[t] = 0;
@@ -241,12 +345,12 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
                     for (int u = 0; u < W; ++u)
 #pragma unroll
                         for (int t = 0; t < CT; ++t)
-                            if (g0 + t < cnt) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
+                            if (g0 + t < ge) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
                 }
                 if (row < n) {
 #pragma unroll
                     for (int t = 0; t < CT; ++t) {
-                        if (g0 + t < cnt) {
+                        if (g0 + t < ge) {
                             if (MODE == 0) Y[off[t] + row] = acc[t];
                             else if (MODE == 1) Y[off[t] + row] = B[off[t] + row] - acc[t];
                             else Y[off[t] + row] += acc[t];
@@ -293,12 +397,15 @@ template <class T, int MODE>
 void spmv(int32_t n, int64_t ld, const Mat<T>& A, int k, const T* X, T* Y, const T* B, const int* list,
           cudaStream_t st, const int* jstop = nullptr, int jmax = 0)
 {
+    const bool gm = spmv_group_major(k, n, sizeof(T));
     if (A.sp) {
-        int64_t g = (A.nslices + 7) / 8;
+        // items: slices, times supergroups of SELL_SG systems when k is large
+        int64_t g = (A.nslices * (gm ? (k + SELL_SG - 1) / SELL_SG : 1) + 7) / 8;
         const int64_t cap = (int64_t)g_sms * 8;
         if (g > cap) g = cap;
         if (g < 1) g = 1;
-        k_spmv_sell<T, MODE><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, jstop, jmax);
+        if (gm) k_spmv_sell<T, MODE, true><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, jstop, jmax);
+        else k_spmv_sell<T, MODE, false><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, jstop, jmax);
         return;
     }
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
@@ -306,7 +413,8 @@ void spmv(int32_t n, int64_t ld, const Mat<T>& A, int k, const T* X, T* Y, const
     const int64_t cap = (int64_t)g_sms * 8;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    k_spmv<T, MODE><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, A.rp, A.ci, A.v, X, Y, B, list, jstop, jmax);
+    if (gm) k_spmv<T, MODE, true><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, A.rp, A.ci, A.v, X, Y, B, list, jstop, jmax);
+    else k_spmv<T, MODE, false><<<SAI_GRID(g), TILE, 0, st>>>(n, ld, A.rp, A.ci, A.v, X, Y, B, list, jstop, jmax);
 }
 
 // Adds a sliced-ELL copy (values converted to T) of the CSR matrix (rp, ci,
@@ -354,6 +462,9 @@ struct Items {
 };
 
 __host__ __device__ __forceinline__ int nchunks(int64_t n) { return (int)((n + CHUNK - 1) / CHUNK); }
+
+// threads of a single-block control kernel for k systems (it loops over them)
+inline int ctl_threads(int k) { return k <= CTRL ? CTRL : 1024; }
 
 int item_blocks(int64_t n, int k)
 {
@@ -420,8 +531,7 @@ __global__ void k_bicg_init(Items I, int k, const double* __restrict__ Bs, doubl
 
 __global__ void k_bicg_f0(int k, int nch, const double* part, Sys S)
 {
-    const int c = threadIdx.x;
-    if (c < k) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
         const double bb = sum_chunks(part, 0, c, k, nch);
         S.iters[c] = 0;
         S.rho[c] = bb;  // r^T rhat with r = rhat = b
@@ -438,14 +548,14 @@ __global__ void k_bicg_f0(int k, int nch, const double* part, Sys S)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) build_list(k, S.active, S.lact);
+    build_list_block(k, S.active, S.lact);
 }
 
 // iteration start: count it, test rho, form beta
 __global__ void k_bicg_start(int k, int maxit, Sys S)
 {
-    const int c = threadIdx.x;
-    if (c < k && S.active[c]) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!S.active[c]) continue;
         if (S.iters[c] >= maxit) {
             S.active[c] = 0;
             S.status[c] = ST_MAXITER;
@@ -460,7 +570,7 @@ __global__ void k_bicg_start(int k, int maxit, Sys S)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) build_list(k, S.active, S.lact);
+    build_list_block(k, S.active, S.lact);
 }
 
 __global__ void k_bicg_p(Items I, const double* __restrict__ r, double* p, const double* __restrict__ v, Sys S)
@@ -499,14 +609,14 @@ __global__ void k_dots(Items I, int k, const double* a0, const double* b0, const
 
 __global__ void k_bicg_f1(int k, int nch, const double* part, Sys S, Dims D)
 {
-    const int c = threadIdx.x;
     const int k1 = S.lact[0];
-    if (c == 0 && k1 > 0) {
+    if (threadIdx.x == 0 && k1 > 0) {
         spmm_work(D, D.nnzM, k1);
         spmm_work(D, D.nnzA, k1);
         kwork_add(PROF_BICG_VEC, 8.0 * D.n * k1 * (4 + 2), D.n * k1 * (3 + 2));  // p update, rhat^T v
     }
-    if (c < k && S.active[c]) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!S.active[c]) continue;
         const double rv = sum_chunks(part, 0, c, k, nch);
         if (rv == 0.0) {
             S.active[c] = 0;
@@ -516,7 +626,7 @@ __global__ void k_bicg_f1(int k, int nch, const double* part, Sys S, Dims D)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) build_list(k, S.active, S.lact);
+    build_list_block(k, S.active, S.lact);
 }
 
 __global__ void k_bicg_s(Items I, int k, const double* __restrict__ r, const double* __restrict__ v, double* s,
@@ -539,10 +649,9 @@ __global__ void k_bicg_s(Items I, int k, const double* __restrict__ r, const dou
 
 __global__ void k_bicg_f2(int k, int nch, const double* part, Sys S, Dims D)
 {
-    const int c = threadIdx.x;
     const int k2 = S.lact[0];
-    if (c == 0 && k2 > 0) kwork_add(PROF_BICG_VEC, 8.0 * D.n * k2 * 3, D.n * k2 * 4.0);  // s, ||s||
-    if (c < k) {
+    if (threadIdx.x == 0 && k2 > 0) kwork_add(PROF_BICG_VEC, 8.0 * D.n * k2 * 3, D.n * k2 * 4.0);  // s, ||s||
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
         if (S.active[c]) {
             const double ss = sum_chunks(part, 0, c, k, nch);
             S.mode[c] = sqrt(ss) < S.thr[c] ? 2 : 1;
@@ -552,19 +661,19 @@ __global__ void k_bicg_f2(int k, int nch, const double* part, Sys S, Dims D)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) build_list(k, S.go, S.lgo);
+    build_list_block(k, S.go, S.lgo);
 }
 
 __global__ void k_bicg_f3(int k, int nch, const double* part, Sys S, Dims D)
 {
-    const int c = threadIdx.x;
     const int k3 = S.lgo[0];
-    if (c == 0 && k3 > 0) {
+    if (threadIdx.x == 0 && k3 > 0) {
         spmm_work(D, D.nnzM, k3);
         spmm_work(D, D.nnzA, k3);
         kwork_add(PROF_BICG_VEC, 8.0 * D.n * k3 * 2, D.n * k3 * 4.0);  // t^T s, t^T t
     }
-    if (c < k && S.go[c]) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!S.go[c]) continue;
         const double ts = sum_chunks(part, 0, c, k, nch), tt = sum_chunks(part, 1, c, k, nch);
         if (tt == 0.0) {
             S.active[c] = 0;
@@ -575,7 +684,7 @@ __global__ void k_bicg_f3(int k, int nch, const double* part, Sys S, Dims D)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) build_list(k, S.active, S.lact);
+    build_list_block(k, S.active, S.lact);
 }
 
 __global__ void k_bicg_xr(Items I, int k, double* x, double* r, const double* __restrict__ rh,
@@ -612,10 +721,10 @@ __global__ void k_bicg_xr(Items I, int k, double* x, double* r, const double* __
 
 __global__ void k_bicg_f4(int k, int nch, const double* part, Sys S, Dims D, int* any_active)
 {
-    const int c = threadIdx.x;
     const int k4 = S.lact[0];
-    if (c == 0 && k4 > 0) kwork_add(PROF_BICG_VEC, 8.0 * D.n * k4 * 8, D.n * k4 * 10.0);  // x, r, two dots
-    if (c < k && S.active[c]) {
+    if (threadIdx.x == 0 && k4 > 0) kwork_add(PROF_BICG_VEC, 8.0 * D.n * k4 * 8, D.n * k4 * 10.0);  // x, r, two dots
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!S.active[c]) continue;
         const double rr = sum_chunks(part, 0, c, k, nch), rhr = sum_chunks(part, 1, c, k, nch);
         if (S.mode[c] == 2 || sqrt(rr) < S.thr[c]) {
             S.active[c] = 0;
@@ -629,10 +738,8 @@ __global__ void k_bicg_f4(int k, int nch, const double* part, Sys S, Dims D, int
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        build_list(k, S.active, S.lact);
-        *any_active = S.lact[0] > 0;
-    }
+    build_list_block(k, S.active, S.lact);
+    if (threadIdx.x == 0) *any_active = S.lact[0] > 0;
 }
 
 
@@ -645,6 +752,7 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
     const int ib = item_blocks(n > 0 ? n : 1, k);
     const int nch = I.nch;
     const int check_every = 4;
+    const int ct = ctl_threads(k);
     int hflag = 0;
     Buf vecs;
     SAI_TRY(vecs.alloc(sizeof(double) * blk * 8 + 8, st, true));
@@ -658,10 +766,10 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
     double* sh = s + blk;
     double* t = sh + blk;
     k_bicg_init<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r, rh, p, v, S.lall, pt);
-    k_bicg_f0<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S);
+    k_bicg_f0<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S);
     SAI_CUDA(cudaGetLastError());
     for (int it = 0; it < maxit; ++it) {
-        k_bicg_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, maxit, S);
+        k_bicg_start<<<SAI_GRID(1), ct, 0, st>>>(k, maxit, S);
         {
             ProfScope ps(PROF_BICG_VEC, st);
             k_bicg_p<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, p, v, S);
@@ -678,12 +786,12 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
             ProfScope ps(PROF_BICG_VEC, st);
             k_dots<1><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, rh, v, nullptr, nullptr, S.lact, pt);
         }
-        k_bicg_f1<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
+        k_bicg_f1<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D);
         {
             ProfScope ps(PROF_BICG_VEC, st);
             k_bicg_s<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, v, s, S, pt);
         }
-        k_bicg_f2<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
+        k_bicg_f2<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D);
         {
             ProfScope ps(PROF_SPMM, st);
             spmv<double, 0>(n, ld, A.M, k, s, sh, nullptr, S.lgo, st);
@@ -696,12 +804,12 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
             ProfScope ps(PROF_BICG_VEC, st);
             k_dots<2><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, t, s, t, t, S.lgo, pt);
         }
-        k_bicg_f3<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D);
+        k_bicg_f3<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D);
         {
             ProfScope ps(PROF_BICG_VEC, st);
             k_bicg_xr<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Xsd, r, rh, ph, sh, s, t, S, pt);
         }
-        k_bicg_f4<<<SAI_GRID(1), CTRL, 0, st>>>(k, nch, pt, S, D, fl);
+        k_bicg_f4<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D, fl);
         SAI_CUDA(cudaGetLastError());
         if ((it + 1) % check_every == 0 || it + 1 == maxit) {
             SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -710,7 +818,7 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
         }
     }
     // systems still active after maxit passes
-    k_bicg_start<<<SAI_GRID(1), CTRL, 0, st>>>(k, maxit, S);
+    k_bicg_start<<<SAI_GRID(1), ct, 0, st>>>(k, maxit, S);
     SAI_CUDA(cudaGetLastError());
     return SAI_OK;
 }
@@ -1343,10 +1451,8 @@ __global__ void k_gm_cycle_end(int k, const int* cap, Sys S, Gm G, int* any_left
 
 __global__ void k_list_all(int k, int* list)
 {
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < k; ++c) list[1 + c] = c;
-        list[0] = k;
-    }
+    for (int c = threadIdx.x; c < k; c += blockDim.x) list[1 + c] = c;
+    if (threadIdx.x == 0) list[0] = k;
 }
 
 __global__ void k_fill_int(int k, int* a, int v)
@@ -1657,7 +1763,9 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
                           const double* thr, const sai_krylov_params* prm, double* X, int32_t* iters,
                           int32_t* status, cudaStream_t st)
 {
-    if (!h || !P || !prm || !thr || !iters || !status || k < 1 || k > CTRL) return SAI_INVALID_ARG;
+    if (!h || !P || !prm || !thr || !iters || !status || k < 1) return SAI_INVALID_ARG;
+    const bool big_ok = prm->method == SAI_BICGSTAB && prm->precision == SAI_FP64;
+    if (k > (big_ok ? KBIG : CTRL)) return SAI_INVALID_ARG;
     if (prm->maxit < 0 || (prm->method == SAI_GMRES && (prm->restart < 1 || prm->restart >= GM_MAXM)))
         return SAI_INVALID_ARG;
     if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES) return SAI_INVALID_ARG;
@@ -1715,7 +1823,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     Buf sysd, sysi, part, part2, flag, Bs, Xs, capb;
     SAI_TRY(sysd.alloc(sizeof(double) * 7 * k, st, true));
     SAI_TRY(sysi.alloc(sizeof(int) * (5 * k + 3 * (k + 1)), st, true));
-    SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * (PS > 2 ? PS : 2), st, true));
+    const int nslot = prm->method == SAI_BICGSTAB ? 2 : (PS > 2 ? PS : 2);  // partial sums per (system, chunk)
+    SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * nslot, st, true));
     SAI_TRY(part2.alloc(sizeof(double) * (size_t)k * I.nch * 2, st, true));
     SAI_TRY(flag.alloc(sizeof(int) * 4, st, true));
     SAI_TRY(Bs.alloc(sizeof(double) * blk + 8, st, true));
@@ -1758,8 +1867,11 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     double* pt = part.as<double>();
     double* pt2 = part2.as<double>();
     int* cap = capb.as<int>();
-    if (n > 0) k_to_soa<<<SAI_GRID(tgrid), 256, 0, st>>>(n, k, ld, B, Bsd);
-    k_list_all<<<SAI_GRID(1), 32, 0, st>>>(k, S.lall);
+    const int64_t ttiles = ((int64_t)n + 31) / 32 * ((k + 31) / 32);
+    const unsigned tblk = (unsigned)(ttiles < (int64_t)g_sms * 16 ? (ttiles > 0 ? ttiles : 1) : (int64_t)g_sms * 16);
+    if (n > 0 && k >= 32) k_soa_tiled<true><<<SAI_GRID(tblk), 256, 0, st>>>(n, k, ld, B, Bsd);
+    else if (n > 0) k_to_soa<<<SAI_GRID(tgrid), 256, 0, st>>>(n, k, ld, B, Bsd);
+    k_list_all<<<SAI_GRID(1), 256, 0, st>>>(k, S.lall);
     k_fill_int<<<SAI_GRID(1), 256, 0, st>>>(k, cap, prm->maxit);
     SAI_CUDA(cudaGetLastError());
 
@@ -1846,7 +1958,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         k_ir_finish<<<SAI_GRID(1), CTRL, 0, st>>>(k, done, status64, tot, S.status, S.iters);
         SAI_CUDA(cudaGetLastError());
     }
-    if (n > 0) k_from_soa<<<SAI_GRID(tgrid), 256, 0, st>>>(n, k, ld, Xsd, X);
+    if (n > 0 && k >= 32) k_soa_tiled<false><<<SAI_GRID(tblk), 256, 0, st>>>(n, k, ld, Xsd, X);
+    else if (n > 0) k_from_soa<<<SAI_GRID(tgrid), 256, 0, st>>>(n, k, ld, Xsd, X);
     SAI_CUDA(cudaGetLastError());
     SAI_CUDA(cudaMemcpyAsync(iters, S.iters, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaMemcpyAsync(status, S.status, sizeof(int) * k, cudaMemcpyDeviceToHost, st));

@@ -24,8 +24,10 @@
 //
 // Workspace tiers: tier 0 lives in shared memory (most columns of regular
 // sparse matrices); a column that outgrows it is queued and restarted in the
-// global-memory tiers 1 and 2. Restarting reproduces the same arithmetic, so
-// the result does not depend on the tier that finished a column.
+// global-memory tiers 1, 2 and 3 (tier 3 for columns whose rows reach more
+// than 4096 candidate columns, as in heavy-tailed matrices). Restarting
+// reproduces the same arithmetic, so the result does not depend on the tier
+// that finished a column.
 #include <float.h>
 
 #include <mutex>
@@ -105,9 +107,11 @@ struct Tier {
 using Tier0 = Tier<64, 16, 128, 512>;      // shared memory, ~13.7 KB per warp
 using Tier1 = Tier<256, 64, 512, 2048>;    // global memory, ~150 KB per warp
 using Tier2 = Tier<1024, 128, 2048, 8192>; // global memory, ~1.1 MB per warp
+using Tier3 = Tier<2048, 128, 4096, 65536>; // global memory, ~2.4 MB per warp (up to 32768 candidates)
 using Tier0F = Tier<64, 16, 128, 512, float>;
 using Tier1F = Tier<256, 64, 512, 2048, float>;
 using Tier2F = Tier<1024, 128, 2048, 8192, float>;
+using Tier3F = Tier<2048, 128, 4096, 65536, float>;
 
 template <class TQ>
 struct WsT {
@@ -773,7 +777,7 @@ __global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int t = tier[k];
-        if (t >= 0 && t < 3) atomicAdd(&out[2 + t], 1);
+        if (t >= 0 && t < 4) atomicAdd(&out[2 + t], 1);
     }
 }
 
@@ -821,12 +825,14 @@ struct Tiers<double> {
     using T0 = Tier0;
     using T1 = Tier1;
     using T2 = Tier2;
+    using T3 = Tier3;
 };
 template <>
 struct Tiers<float> {
     using T0 = Tier0F;
     using T1 = Tier1F;
     using T2 = Tier2F;
+    using T3 = Tier3F;
 };
 
 // Build configuration: the tier-0 warps per block, the blocks per SM of the
@@ -911,7 +917,7 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     SAI_CUDA(cudaMemsetAsync(tier.p, 0xff, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->loops.p, 0, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->res.p, 0, sizeof(double) * nn, st));
-    int* c = ctr.as<int>();  // [0] next, [1] ovf count t0, [2] ovf count t1, [3] err, [4..] stats
+    int* c = ctr.as<int>();  // [0] next, [1..2] ovf counts t0, t1, [3] err, [4..9] stats, [10] ovf count t2
     Out out;
     out.smax = smax;
     out.cnt = cnt.as<int32_t>();
@@ -925,6 +931,7 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     using T0 = typename Tiers<TQ>::T0;
     using T1 = typename Tiers<TQ>::T1;
     using T2 = typename Tiers<TQ>::T2;
+    using T3 = typename Tiers<TQ>::T3;
     // tier-0 work queue: all columns (or the given list), optionally heavy ones first
     const int32_t nq = cols ? ncols : n;
     const int32_t* queue = cols;
@@ -952,9 +959,17 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
                                                  c + 2, c + 3, 1, cfg, st)));
         SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
         SAI_CUDA(cudaStreamSynchronize(st));
-        if (hc[2] > 0)
-            SAI_TRY((launch_tier<T2, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out, nullptr,
-                                                     nullptr, c + 3, 2, cfg, st)));
+        if (hc[2] > 0) {
+            // tier 2 queues its overflows in ovf0 (tier 1's input, no longer read)
+            SAI_TRY((launch_tier<T2, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out, ovf0.as<int32_t>(),
+                                                     c + 10, c + 3, 2, cfg, st)));
+            int h3 = 0;
+            SAI_CUDA(cudaMemcpyAsync(&h3, c + 10, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            if (h3 > 0)
+                SAI_TRY((launch_tier<T3, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), h3, c + 0, out, nullptr,
+                                                         nullptr, c + 3, 3, cfg, st)));
+        }
     }
     // assemble M (CSC, rows ascending) and its CSR copy
     SAI_TRY(P->M_cp.alloc(sizeof(int64_t) * (nn + 1), st, async));
@@ -981,14 +996,12 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
         k_tier_count<<<SAI_GRID(g_num_sms * 2), 256, 0, st>>>(n, tier.as<int32_t>(), c + 4);
     }
     SAI_CUDA(cudaGetLastError());
-    int hs[5];
+    int hs[6];
     SAI_CUDA(cudaMemcpyAsync(hs, c + 4, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));
     P->n_c = hs[0];
     P->l_m = hs[1];
-    P->n_tier[0] = hs[2];
-    P->n_tier[1] = hs[3];
-    P->n_tier[2] = hs[4];
+    for (int q = 0; q < 4; ++q) P->n_tier[q] = hs[2 + q];
     SAI_CUDA(cudaEventElapsedTime(&P->ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
