@@ -743,6 +743,128 @@ __global__ void k_bicg_f4(int k, int nch, const double* part, Sys S, Dims D, int
 }
 
 
+// ---------------------------------------------------------------- panel SpMV (many systems)
+// For thousands of systems the FP64 BiCGStab applies its operators in a
+// panel layout: the listed systems, PNL at a time, row-major within a panel
+// (P[(pc * n + row) * PNL + j] holds system list[pc * PNL + j] at row). A
+// warp then reads PNL contiguous values per matrix entry instead of PNL
+// scattered words, a warp per row keeps every lane busy whatever the row's
+// length, and one panel (n x PNL values) stays in L2 while the warps sweep
+// its rows. Each row's sum runs over its CSR entries in order from zero, as
+// in k_spmv and k_spmv_sell, so a system gets the same bits as there.
+constexpr int PNL = 64;
+
+// system-major X (the systems of list) -> panels, tiles of 32 rows x PNL systems
+__global__ void __launch_bounds__(256) k_pnl_gather(int32_t n, int64_t ld, const double* __restrict__ X,
+                                                    const int* __restrict__ list, double* __restrict__ P)
+{
+    __shared__ double t[PNL][33];
+    const int cnt = list[0];
+    const int np = (cnt + PNL - 1) / PNL;
+    const int64_t rt = ((int64_t)n + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t it = blockIdx.x; it < rt * np; it += gridDim.x) {
+        const int pc = (int)(it / rt);
+        const int64_t r0 = (it - (int64_t)pc * rt) * 32;
+        for (int j = ty; j < PNL; j += 8) {  // system pc * PNL + j, rows r0 + tx
+            const int c = pc * PNL + j;
+            const int64_t row = r0 + tx;
+            t[j][tx] = (c < cnt && row < n) ? X[(int64_t)list[1 + c] * ld + row] : 0.0;
+        }
+        __syncthreads();
+        for (int r = ty; r < 32; r += 8) {  // row r0 + r: systems 2 tx, 2 tx + 1
+            const int64_t row = r0 + r;
+            if (row < n)
+                reinterpret_cast<double2*>(P + ((int64_t)pc * n + row) * PNL)[tx] =
+                    make_double2(t[2 * tx][r], t[2 * tx + 1][r]);
+        }
+        __syncthreads();
+    }
+}
+
+// panels -> system-major Y (the systems of list)
+__global__ void __launch_bounds__(256) k_pnl_scatter(int32_t n, int64_t ld, const double* __restrict__ P,
+                                                     const int* __restrict__ list, double* __restrict__ Y)
+{
+    __shared__ double t[PNL][33];
+    const int cnt = list[0];
+    const int np = (cnt + PNL - 1) / PNL;
+    const int64_t rt = ((int64_t)n + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t it = blockIdx.x; it < rt * np; it += gridDim.x) {
+        const int pc = (int)(it / rt);
+        const int64_t r0 = (it - (int64_t)pc * rt) * 32;
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t row = r0 + r;
+            if (row < n) {
+                const double2 v = reinterpret_cast<const double2*>(P + ((int64_t)pc * n + row) * PNL)[tx];
+                t[2 * tx][r] = v.x;
+                t[2 * tx + 1][r] = v.y;
+            }
+        }
+        __syncthreads();
+        for (int j = ty; j < PNL; j += 8) {
+            const int c = pc * PNL + j;
+            const int64_t row = r0 + tx;
+            if (c < cnt && row < n) Y[(int64_t)list[1 + c] * ld + row] = t[j][tx];
+        }
+        __syncthreads();
+    }
+}
+
+// Pout = A Pin on the panels of the listed systems (CSR of A); one warp per
+// (panel, row), panel-major; lane l holds systems 2 l and 2 l + 1
+__global__ void __launch_bounds__(256) k_pnl_spmm(int32_t n, const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                  const int* __restrict__ list, const double* __restrict__ Pin,
+                                                  double* __restrict__ Pout)
+{
+    const int cnt = list[0];
+    const int np = (cnt + PNL - 1) / PNL;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = w0; it < (int64_t)np * n; it += nw) {
+        const int64_t pc = it / n, row = it - pc * n;
+        const double2* X = reinterpret_cast<const double2*>(Pin + pc * n * PNL);
+        double a0 = 0.0, a1 = 0.0;
+        const int64_t b = rp[row], e = rp[row + 1];
+        for (int64_t q0 = b; q0 < e; q0 += 32) {
+            const int64_t q = q0 + lane;
+            const int32_t cl = q < e ? ci[q] : 0;
+            const double av = q < e ? v[q] : 0.0;
+            const int m = e - q0 < 32 ? (int)(e - q0) : 32;
+            for (int u = 0; u < m; ++u) {
+                const int32_t c = __shfl_sync(SAI_FULL, cl, u);
+                const double a = __shfl_sync(SAI_FULL, av, u);
+                const double2 x = X[(int64_t)c * (PNL / 2) + lane];
+                a0 = fma(a, x.x, a0);
+                a1 = fma(a, x.y, a1);
+            }
+        }
+        reinterpret_cast<double2*>(Pout + (pc * n + row) * PNL)[lane] = make_double2(a0, a1);
+    }
+}
+
+// Y2 = A (Y1 = M X) for the listed systems through the panels P1, P2
+// (n x PNL * ceil(k / PNL) values each): gather, two SpMMs, two scatters.
+void pnl_apply2(int32_t n, int64_t ld, int k, const Ops<double>& A, const double* X, double* Y1, double* Y2,
+                const int* list, double* P1, double* P2, cudaStream_t st)
+{
+    const int64_t np = (k + PNL - 1) / PNL;
+    const int64_t tiles = ((int64_t)n + 31) / 32 * np;
+    const int64_t tb = tiles < (int64_t)g_sms * 16 ? (tiles > 0 ? tiles : 1) : (int64_t)g_sms * 16;
+    const int64_t warps = np * n;
+    int64_t sb = (warps + 7) / 8;
+    if (sb > (int64_t)g_sms * 8) sb = (int64_t)g_sms * 8;
+    if (sb < 1) sb = 1;
+    k_pnl_gather<<<SAI_GRID(tb), 256, 0, st>>>(n, ld, X, list, P1);
+    k_pnl_spmm<<<SAI_GRID(sb), 256, 0, st>>>(n, A.M.rp, A.M.ci, A.M.v, list, P1, P2);
+    k_pnl_scatter<<<SAI_GRID(tb), 256, 0, st>>>(n, ld, P2, list, Y1);
+    k_pnl_spmm<<<SAI_GRID(sb), 256, 0, st>>>(n, A.A.rp, A.A.ci, A.A.v, list, P2, P1);
+    k_pnl_scatter<<<SAI_GRID(tb), 256, 0, st>>>(n, ld, P1, list, Y2);
+}
+
 sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const double* Bsd, double* Xsd, Sys& S,
                         double* pt, int* fl, int maxit, const Dims& D, cudaStream_t st)
 {
@@ -765,6 +887,16 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
     double* s = ph + blk;
     double* sh = s + blk;
     double* t = sh + blk;
+    // many systems: the operators are applied in the panel layout
+    const bool pnl = k > CTRL && spmv_group_major(k, n, sizeof(double));
+    Buf pbuf;
+    double *P1 = nullptr, *P2 = nullptr;
+    if (pnl) {
+        const size_t pe = (size_t)(n > 0 ? n : 1) * PNL * (size_t)((k + PNL - 1) / PNL);
+        SAI_TRY(pbuf.alloc(sizeof(double) * pe * 2, st, true));
+        P1 = pbuf.as<double>();
+        P2 = P1 + pe;
+    }
     k_bicg_init<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r, rh, p, v, S.lall, pt);
     k_bicg_f0<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S);
     SAI_CUDA(cudaGetLastError());
@@ -774,13 +906,18 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
             ProfScope ps(PROF_BICG_VEC, st);
             k_bicg_p<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, p, v, S);
         }
-        {
+        if (pnl) {
             ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.M, k, p, ph, nullptr, S.lact, st);
-        }
-        {
-            ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.A, k, ph, v, nullptr, S.lact, st);
+            pnl_apply2(n, ld, k, A, p, ph, v, S.lact, P1, P2, st);
+        } else {
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, A.M, k, p, ph, nullptr, S.lact, st);
+            }
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, A.A, k, ph, v, nullptr, S.lact, st);
+            }
         }
         {
             ProfScope ps(PROF_BICG_VEC, st);
@@ -792,13 +929,18 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
             k_bicg_s<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r, v, s, S, pt);
         }
         k_bicg_f2<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D);
-        {
+        if (pnl) {
             ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.M, k, s, sh, nullptr, S.lgo, st);
-        }
-        {
-            ProfScope ps(PROF_SPMM, st);
-            spmv<double, 0>(n, ld, A.A, k, sh, t, nullptr, S.lgo, st);
+            pnl_apply2(n, ld, k, A, s, sh, t, S.lgo, P1, P2, st);
+        } else {
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, A.M, k, s, sh, nullptr, S.lgo, st);
+            }
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, A.A, k, sh, t, nullptr, S.lgo, st);
+            }
         }
         {
             ProfScope ps(PROF_BICG_VEC, st);
