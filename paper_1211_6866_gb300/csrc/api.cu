@@ -123,6 +123,7 @@ sai_status sai_profile_begin(void)
     }
     SAI_TRY(sai_krylov_work_reset());
     SAI_TRY(sai_build_work_reset());
+    SAI_TRY(sai_batch_work_reset());
     SAI_CUDA(cudaDeviceSynchronize());
     g_launches.store(0);
     g_prof.store(true);
@@ -136,9 +137,10 @@ sai_status sai_profile_end(sai_profile_report* out)
     SAI_CUDA(cudaDeviceSynchronize());
     memset(out, 0, sizeof(*out));
     out->launches = g_launches.load();
-    double wk[PROF_NSITES * 2], wb[PROF_NSITES * 2];
+    double wk[PROF_NSITES * 2], wb[PROF_NSITES * 2], wt[PROF_NSITES * 2];
     SAI_TRY(sai_krylov_work_read(wk));
     SAI_TRY(sai_build_work_read(wb));
+    SAI_TRY(sai_batch_work_read(wt));
     std::lock_guard<std::mutex> lk(g_prof_mu);
     out->nsites = PROF_NSITES;
     for (int q = 0; q < PROF_NSITES; ++q) {
@@ -165,8 +167,8 @@ sai_status sai_profile_end(sai_profile_report* out)
         const size_t timed = n_head + n_tail;
         ps.timed = (int64_t)timed;
         g_prof_ev[q].clear();
-        ps.bytes = wk[2 * q] + wb[2 * q];
-        ps.flops = wk[2 * q + 1] + wb[2 * q + 1];
+        ps.bytes = wk[2 * q] + wb[2 * q] + wt[2 * q];
+        ps.flops = wk[2 * q + 1] + wb[2 * q + 1] + wt[2 * q + 1];
     }
     return SAI_OK;
 }

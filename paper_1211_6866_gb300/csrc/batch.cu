@@ -38,8 +38,35 @@ struct BSys {
     const int32_t* first;   // first item of system c (first[nsys] = item count)
     const int32_t* it_sys;  // system of item q
     const int32_t* it_r0;   // first local row of item q
+    const int32_t* nsm;     // systems of c's matrix (s + 1)
     int32_t nitems;
 };
+
+// Algorithmic work of the batched BiCGStab, added per system by the control
+// kernels and read by the profile: an SpMV reads its matrix block once for
+// all the systems of the matrix (a 1/(s+1) share per system) and the
+// system's input and output vectors once.
+__device__ double d_bwork[PROF_NSITES * 2];
+
+struct BWork {
+    const int64_t* Arp;  // CSR row pointers of the block-diagonal A~ and M
+    const int64_t* Mrp;
+};
+
+__device__ __forceinline__ void bwork_add(int site, double bytes, double flops)
+{
+    atomicAdd(&d_bwork[2 * site], bytes);
+    atomicAdd(&d_bwork[2 * site + 1], flops);
+}
+
+// the two SpMVs (M, then A~) of one half iteration of system c
+__device__ void bwork_pair(const BSys& Y, const BWork& Wk, int c)
+{
+    const int64_t r0 = Y.row0[c], n = Y.len[c];
+    const double nA = (double)(Wk.Arp[r0 + n] - Wk.Arp[r0]), nM = (double)(Wk.Mrp[r0 + n] - Wk.Mrp[r0]);
+    const double bytes = (12.0 * (nA + nM) + 16.0 * (double)(n + 1)) / (double)Y.nsm[c] + 32.0 * (double)n;
+    bwork_add(PROF_SPMM, bytes, 2.0 * (nA + nM));
+}
 
 // Per-system BiCGStab state.
 struct BState {
@@ -198,12 +225,14 @@ __global__ void __launch_bounds__(BR) k_b_dots(BSys Y, const double* a0, const d
     }
 }
 
-__global__ void k_b_f1(BSys Y, const double* part, BState S)
+__global__ void k_b_f1(BSys Y, const double* part, BState S, BWork Wk)
 {
     const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (c >= Y.nsys || !S.active[c]) return;
     const double rv = sys_sum(Y, part, c);
     if ((threadIdx.x & 31) == 0) {
+        bwork_pair(Y, Wk, c);
+        bwork_add(PROF_BICG_VEC, 8.0 * Y.len[c] * (4 + 2), (double)Y.len[c] * (3 + 2));  // p update, rhat^T v
         if (rv == 0.0) {
             S.active[c] = 0;
             S.status[c] = B_BREAKDOWN;
@@ -242,18 +271,21 @@ __global__ void k_b_f2(BSys Y, const double* part, BState S)
     }
     const double ss = sys_sum(Y, part, c);
     if ((threadIdx.x & 31) == 0) {
+        bwork_add(PROF_BICG_VEC, 8.0 * Y.len[c] * 3, 4.0 * Y.len[c]);  // s, ||s||
         S.mode[c] = sqrt(ss) < S.thr[c] ? 2 : 1;
         S.go[c] = S.mode[c] == 1;
     }
 }
 
-__global__ void k_b_f3(BSys Y, const double* part, BState S)
+__global__ void k_b_f3(BSys Y, const double* part, BState S, BWork Wk)
 {
     const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (c >= Y.nsys || !S.go[c]) return;
     const double ts = sys_sum(Y, part, c);
     const double tt = sys_sum(Y, part + Y.nitems, c);
     if ((threadIdx.x & 31) == 0) {
+        bwork_pair(Y, Wk, c);
+        bwork_add(PROF_BICG_VEC, 8.0 * Y.len[c] * 2, 4.0 * Y.len[c]);  // t^T s, t^T t
         if (tt == 0.0) {
             S.active[c] = 0;
             S.go[c] = 0;
@@ -305,6 +337,7 @@ __global__ void k_b_f4(BSys Y, const double* part, BState S)
     const double rr = sys_sum(Y, part, c);
     const double rhr = sys_sum(Y, part + Y.nitems, c);
     if ((threadIdx.x & 31) == 0) {
+        bwork_add(PROF_BICG_VEC, 8.0 * Y.len[c] * 8, 10.0 * Y.len[c]);  // x, r, two dots
         if (S.mode[c] == 2 || sqrt(rr) < S.thr[c]) {
             S.active[c] = 0;
             S.status[c] = B_OK;
@@ -547,7 +580,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     for (int32_t m = 0; m < nmat; ++m) sys0[m + 1] = sys0[m] + hs[m]->s + 1;
     const int32_t nsys = sys0[nmat];
     std::vector<int64_t> off(nsys);
-    std::vector<int32_t> len(nsys), row0(nsys), first(nsys + 1);
+    std::vector<int32_t> len(nsys), row0(nsys), first(nsys + 1), nsm(nsys);
     std::vector<int64_t> xoff(nmat), joff(nmat + 1, 0);
     std::vector<int32_t> nvec(nmat), svec(nmat);
     int64_t o = 0;
@@ -563,6 +596,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
             off[c] = o;
             len[c] = hs[m]->n;
             row0[c] = (int32_t)R0[m];
+            nsm[c] = hs[m]->s + 1;
             first[c] = nit;
             o += hs[m]->n;
             nit += (hs[m]->n + BR - 1) / BR;
@@ -578,7 +612,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
         }
     Buf tab, vecs, bst, bsi, part, misc;
     const size_t tab_bytes = sizeof(int64_t) * (nsys + nmat + nmat + 1) +
-                             sizeof(int32_t) * (3 * (size_t)nsys + 1 + 2 * (size_t)nit + 2 * (size_t)nmat + joff[nmat] + 1);
+                             sizeof(int32_t) * (4 * (size_t)nsys + 1 + 2 * (size_t)nit + 2 * (size_t)nmat + joff[nmat] + 1);
     SAI_TRY(tab.alloc(tab_bytes + 64, st, true));
     char* tp = tab.as<char>();
     auto put = [&](const void* src, size_t bytes) -> char* {
@@ -596,6 +630,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     Y.first = (const int32_t*)put(first.data(), sizeof(int32_t) * (nsys + 1));
     Y.it_sys = (const int32_t*)put(it_sys.data(), sizeof(int32_t) * nit);
     Y.it_r0 = (const int32_t*)put(it_r0.data(), sizeof(int32_t) * nit);
+    Y.nsm = (const int32_t*)put(nsm.data(), sizeof(int32_t) * nsys);
     BSmw W;
     W.xoff = (const int64_t*)put(xoff.data(), sizeof(int64_t) * nmat);
     W.n = (const int32_t*)put(nvec.data(), sizeof(int32_t) * nmat);
@@ -683,20 +718,51 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     const int maxit = prm->krylov.maxit;
     k_b_f0<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
     SAI_CUDA(cudaGetLastError());
+    BWork Wk;
+    Wk.Arp = Ar;
+    Wk.Mrp = Mr;
+    // profile scopes act only while a profile is open, when no graph is captured
     auto iteration = [&](cudaStream_t q) {
         k_b_start<<<SAI_GRID(gt), 256, 0, q>>>(nsys, maxit, S);
-        k_b_p<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, p, v, S);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Mr, Mc, Mv, p, ph, S.active);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Ar, Ac, Av, ph, v, S.active);
-        k_b_dots<1><<<SAI_GRID(gi), BR, 0, q>>>(Y, rh, v, nullptr, nullptr, S.active, pt);
-        k_b_f1<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
-        k_b_s<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, v, s, S, pt);
+        {
+            ProfScope ps(PROF_BICG_VEC, q);
+            k_b_p<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, p, v, S);
+        }
+        {
+            ProfScope ps(PROF_SPMM, q);
+            k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Mr, Mc, Mv, p, ph, S.active);
+        }
+        {
+            ProfScope ps(PROF_SPMM, q);
+            k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Ar, Ac, Av, ph, v, S.active);
+        }
+        {
+            ProfScope ps(PROF_BICG_VEC, q);
+            k_b_dots<1><<<SAI_GRID(gi), BR, 0, q>>>(Y, rh, v, nullptr, nullptr, S.active, pt);
+        }
+        k_b_f1<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S, Wk);
+        {
+            ProfScope ps(PROF_BICG_VEC, q);
+            k_b_s<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, v, s, S, pt);
+        }
         k_b_f2<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Mr, Mc, Mv, s, sh, S.go);
-        k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Ar, Ac, Av, sh, t, S.go);
-        k_b_dots<2><<<SAI_GRID(gi), BR, 0, q>>>(Y, t, s, t, t, S.go, pt);
-        k_b_f3<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
-        k_b_xr<<<SAI_GRID(gi), BR, 0, q>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
+        {
+            ProfScope ps(PROF_SPMM, q);
+            k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Mr, Mc, Mv, s, sh, S.go);
+        }
+        {
+            ProfScope ps(PROF_SPMM, q);
+            k_b_spmv<<<SAI_GRID(gi), BR, 0, q>>>(Y, Ar, Ac, Av, sh, t, S.go);
+        }
+        {
+            ProfScope ps(PROF_BICG_VEC, q);
+            k_b_dots<2><<<SAI_GRID(gi), BR, 0, q>>>(Y, t, s, t, t, S.go, pt);
+        }
+        k_b_f3<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S, Wk);
+        {
+            ProfScope ps(PROF_BICG_VEC, q);
+            k_b_xr<<<SAI_GRID(gi), BR, 0, q>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
+        }
         k_b_f4<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
     };
     constexpr int ITERS_PER_CHECK = 8, LAUNCHES = ITERS_PER_CHECK * 14 + 1;
@@ -820,4 +886,17 @@ extern "C" sai_status sai_solve_batched(int32_t nmat, const sai_csc_view* A, con
 {
     sai_pool_init_once();
     return batched_impl(nmat, A, b, prm, x, items, rep, (cudaStream_t)stream);
+}
+
+sai_status sai_batch_work_reset()
+{
+    double z[PROF_NSITES * 2] = {};
+    SAI_CUDA(cudaMemcpyToSymbol(d_bwork, z, sizeof(z)));
+    return SAI_OK;
+}
+
+sai_status sai_batch_work_read(double* out)
+{
+    SAI_CUDA(cudaMemcpyFromSymbol(out, d_bwork, sizeof(double) * PROF_NSITES * 2));
+    return SAI_OK;
 }

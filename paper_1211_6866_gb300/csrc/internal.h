@@ -96,3 +96,5 @@ sai_status sai_krylov_work_reset();
 sai_status sai_krylov_work_read(double* out /* PROF_NSITES x 2 */);
 sai_status sai_build_work_reset();
 sai_status sai_build_work_read(double* out /* PROF_NSITES x 2 */);
+sai_status sai_batch_work_reset();
+sai_status sai_batch_work_read(double* out /* PROF_NSITES x 2 */);
