@@ -1,6 +1,7 @@
 // batch.cu -- Procedure * (§3) for a batch of independent irregular systems.
 //
-// Split: each matrix on its own (sai_split_build: its own p and threshold).
+// Split: each matrix on its own (sai_split_build: its own p and threshold),
+//   several at a time on worker streams.
 // Build: the A~_i are laid side by side as the block-diagonal A~ of the batch
 //   (CSC and CSR copied with row / column offsets) and M is built for all of
 //   its columns in one persistent launch of the SAI kernel: the column problems
@@ -8,9 +9,10 @@
 //   one its matrix alone would give.
 // Solve: the sum(s_i + 1) right-hand sides [b_i, u_i1 .. u_is_i] are Krylov
 //   systems of different lengths, stored one after another. Work items are
-//   (system, chunk of BR rows), one block each, listed once for the whole
-//   batch; a stopped system's items return at once. Inner products are summed
-//   per item in a fixed order and per system over its items in order. The
+//   (system, chunk of BR rows), listed once for the whole batch: one block
+//   each in the SpMV (a thread per row), one warp each in the vector kernels;
+//   a stopped system's items return at once. Inner products are summed per
+//   item in a fixed order and per system over its items in order. The
 //   control kernels run one warp (or thread) per system. Groups of 8
 //   iterations are captured once as a CUDA graph and replayed, with one host
 //   check of the "any system still running" flag per group.
@@ -19,6 +21,7 @@
 #include <math.h>
 
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -74,19 +77,6 @@ struct BState {
     int *active, *iters, *status, *mode, *go;
 };
 
-__device__ __forceinline__ double block_sum(double v, double* sh)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    return t;  // valid in thread 0
-}
-
 // Sum of the item partials of system c, in item order (one warp).
 __device__ __forceinline__ double sys_sum(const BSys& Y, const double* part, int c)
 {
@@ -126,25 +116,38 @@ __global__ void __launch_bounds__(BR) k_b_spmv(BSys Y, const int64_t* __restrict
     }
 }
 
+// The vector kernels take one warp per item (system, BR rows): lane l holds
+// rows r0 + l + 32 t (t < RPL), whose loads are independent, and the item's
+// partial sums are reduced by shuffles, in a fixed order.
+constexpr int RPL = BR / 32;
+#define FOR_WARP_ITEMS(Y, q)                                                                                 \
+    for (int32_t q = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); q < (Y).nitems;      \
+         q += (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5))
+
 __global__ void __launch_bounds__(BR) k_b_init(BSys Y, const double* __restrict__ B, double* x, double* r, double* rh,
                                                double* p, double* v, double* part)
 {
-    __shared__ double sh[BR / 32];
-    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    FOR_WARP_ITEMS(Y, q)
+    {
         const int c = Y.it_sys[q];
-        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        const int64_t o = Y.off[c], r0 = Y.it_r0[q], n = Y.len[c];
         double a = 0.0;
-        if (i < Y.len[c]) {
-            const double bv = B[o + i];
-            x[o + i] = 0.0;
-            r[o + i] = bv;
-            rh[o + i] = bv;
-            p[o + i] = 0.0;
-            v[o + i] = 0.0;
-            a = bv * bv;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int64_t i = r0 + lane + 32 * t;
+            if (i < n) {
+                const double bv = B[o + i];
+                x[o + i] = 0.0;
+                r[o + i] = bv;
+                rh[o + i] = bv;
+                p[o + i] = 0.0;
+                v[o + i] = 0.0;
+                a = fma(bv, bv, a);
+            }
         }
-        const double t = block_sum(a, sh);
-        if (threadIdx.x == 0) part[q] = t;
+        a = warp_sum(a);
+        if (lane == 0) part[q] = a;
     }
 }
 
@@ -192,13 +195,19 @@ __global__ void k_b_start(int32_t nsys, int maxit, BState S)
 __global__ void __launch_bounds__(BR) k_b_p(BSys Y, const double* __restrict__ r, double* p, const double* __restrict__ v,
                                             BState S)
 {
-    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    FOR_WARP_ITEMS(Y, q)
+    {
         const int c = Y.it_sys[q];
         if (!S.active[c]) continue;
-        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
-        if (i >= Y.len[c]) continue;
+        const int64_t o = Y.off[c], r0 = Y.it_r0[q], n = Y.len[c];
         const double be = S.beta[c], om = S.omega[c];
-        p[o + i] = S.iters[c] == 1 ? r[o + i] : r[o + i] + be * (p[o + i] - om * v[o + i]);
+        const bool first = S.iters[c] == 1;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int64_t i = r0 + lane + 32 * t;
+            if (i < n) p[o + i] = first ? r[o + i] : r[o + i] + be * (p[o + i] - om * v[o + i]);
+        }
     }
 }
 
@@ -206,21 +215,26 @@ template <int ND>
 __global__ void __launch_bounds__(BR) k_b_dots(BSys Y, const double* a0, const double* b0, const double* a1,
                                                const double* b1, const int* flags, double* part)
 {
-    __shared__ double sh[BR / 32];
-    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    FOR_WARP_ITEMS(Y, q)
+    {
         const int c = Y.it_sys[q];
         if (!flags[c]) continue;
-        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        const int64_t o = Y.off[c], r0 = Y.it_r0[q], n = Y.len[c];
         double s0 = 0.0, s1 = 0.0;
-        if (i < Y.len[c]) {
-            s0 = a0[o + i] * b0[o + i];
-            if (ND > 1) s1 = a1[o + i] * b1[o + i];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int64_t i = r0 + lane + 32 * t;
+            if (i < n) {
+                s0 = fma(a0[o + i], b0[o + i], s0);
+                if (ND > 1) s1 = fma(a1[o + i], b1[o + i], s1);
+            }
         }
-        const double t0 = block_sum(s0, sh);
-        const double t1 = ND > 1 ? block_sum(s1, sh) : 0.0;
-        if (threadIdx.x == 0) {
-            part[q] = t0;
-            if (ND > 1) part[Y.nitems + q] = t1;
+        s0 = warp_sum(s0);
+        if (ND > 1) s1 = warp_sum(s1);
+        if (lane == 0) {
+            part[q] = s0;
+            if (ND > 1) part[Y.nitems + q] = s1;
         }
     }
 }
@@ -245,19 +259,25 @@ __global__ void k_b_f1(BSys Y, const double* part, BState S, BWork Wk)
 __global__ void __launch_bounds__(BR) k_b_s(BSys Y, const double* __restrict__ r, const double* __restrict__ v, double* s,
                                             BState S, double* part)
 {
-    __shared__ double sh[BR / 32];
-    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    FOR_WARP_ITEMS(Y, q)
+    {
         const int c = Y.it_sys[q];
         if (!S.active[c]) continue;
-        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        const int64_t o = Y.off[c], r0 = Y.it_r0[q], n = Y.len[c];
+        const double al = S.alpha[c];
         double a = 0.0;
-        if (i < Y.len[c]) {
-            const double sv = r[o + i] - S.alpha[c] * v[o + i];
-            s[o + i] = sv;
-            a = sv * sv;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int64_t i = r0 + lane + 32 * t;
+            if (i < n) {
+                const double sv = r[o + i] - al * v[o + i];
+                s[o + i] = sv;
+                a = fma(sv, sv, a);
+            }
         }
-        const double t = block_sum(a, sh);
-        if (threadIdx.x == 0) part[q] = t;
+        a = warp_sum(a);
+        if (lane == 0) part[q] = a;
     }
 }
 
@@ -301,31 +321,37 @@ __global__ void __launch_bounds__(BR) k_b_xr(BSys Y, double* x, double* r, const
                                              const double* __restrict__ s, const double* __restrict__ t, BState S,
                                              double* part)
 {
-    __shared__ double sh[BR / 32];
-    for (int32_t q = blockIdx.x; q < Y.nitems; q += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    FOR_WARP_ITEMS(Y, q)
+    {
         const int c = Y.it_sys[q];
         if (!S.active[c]) continue;
-        const int64_t i = Y.it_r0[q] + threadIdx.x, o = Y.off[c];
+        const int64_t o = Y.off[c], r0 = Y.it_r0[q], n = Y.len[c];
+        const double al = S.alpha[c], om = S.omega[c];
+        const bool half = S.mode[c] == 2;
         double a0 = 0.0, a1 = 0.0;
-        if (i < Y.len[c]) {
-            const double al = S.alpha[c], om = S.omega[c];
-            double rv;
-            if (S.mode[c] == 2) {
-                x[o + i] += al * ph[o + i];
-                rv = s[o + i];
-            } else {
-                x[o + i] += al * ph[o + i] + om * sh_[o + i];
-                rv = s[o + i] - om * t[o + i];
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+            const int64_t i = r0 + lane + 32 * u;
+            if (i < n) {
+                double rv;
+                if (half) {
+                    x[o + i] += al * ph[o + i];
+                    rv = s[o + i];
+                } else {
+                    x[o + i] += al * ph[o + i] + om * sh_[o + i];
+                    rv = s[o + i] - om * t[o + i];
+                }
+                r[o + i] = rv;
+                a0 = fma(rv, rv, a0);
+                a1 = fma(rh[o + i], rv, a1);
             }
-            r[o + i] = rv;
-            a0 = rv * rv;
-            a1 = rh[o + i] * rv;
         }
-        const double t0 = block_sum(a0, sh);
-        const double t1 = block_sum(a1, sh);
-        if (threadIdx.x == 0) {
-            part[q] = t0;
-            part[Y.nitems + q] = t1;
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane == 0) {
+            part[q] = a0;
+            part[Y.nitems + q] = a1;
         }
     }
 }
@@ -516,12 +542,76 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     Ev e0, e1, e2, e3, e4;
     SAI_CUDA(cudaEventRecord(e0.e, st));
 
-    // ---- split, one matrix at a time
+    // ---- split: each matrix on its own. A split waits on the host for its
+    // counts, so the matrices are spread over worker streams, each driven by
+    // a host thread, and those waits overlap. The worker streams start after
+    // st, st waits for all of them, and they wait for st again before the
+    // split handles (whose buffers they own) are freed.
+    for (int32_t m = 0; m < nmat; ++m)
+        if (A[m].n < 1 || !b[m] || !x[m]) return SAI_INVALID_ARG;
+    const int nthr = nmat < 8 ? nmat : 8;
+    struct Workers {
+        std::vector<cudaStream_t> s;
+        ~Workers()
+        {
+            for (cudaStream_t q : s) cudaStreamDestroy(q);
+        }
+    } wk;
+    {
+        cudaEvent_t ev = nullptr;
+        SAI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        SAI_CUDA(cudaEventRecord(ev, st));
+        for (int t = 0; t < nthr; ++t) {
+            cudaStream_t q = nullptr;
+            if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaEventDestroy(ev);
+                return SAI_CUDA_ERROR;
+            }
+            wk.s.push_back(q);
+            SAI_CUDA(cudaStreamWaitEvent(q, ev, 0));
+        }
+        cudaEventDestroy(ev);
+    }
     std::vector<std::unique_ptr<sai_split_s>> hs((size_t)nmat);
-    for (int32_t m = 0; m < nmat; ++m) {
-        if (A[m].n < 1 || (A[m].n > 0 && (!b[m] || !x[m]))) return SAI_INVALID_ARG;
-        hs[m].reset(new sai_split_s);
-        SAI_TRY(sai_split_build(&A[m], &prm->split, st, true, hs[m].get()));
+    struct Join {  // destroyed before hs: the worker streams wait for st's use of the splits
+        const std::vector<cudaStream_t>& s;
+        cudaStream_t main;
+        ~Join()
+        {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                cudaStreamSynchronize(main);
+                return;
+            }
+            cudaEventRecord(ev, main);
+            for (cudaStream_t q : s) cudaStreamWaitEvent(q, ev, 0);
+            cudaEventDestroy(ev);
+        }
+    } join{wk.s, st};
+    {
+        std::vector<sai_status> tst((size_t)nthr, SAI_OK);
+        std::vector<std::thread> th;
+        for (int t = 0; t < nthr; ++t)
+            th.emplace_back([&, t] {
+                if (cudaSetDevice(dev) != cudaSuccess) {
+                    tst[t] = SAI_CUDA_ERROR;
+                    return;
+                }
+                for (int32_t m = t; m < nmat && tst[t] == SAI_OK; m += nthr) {
+                    hs[m].reset(new sai_split_s);
+                    tst[t] = sai_split_build(&A[m], &prm->split, wk.s[t], true, hs[m].get());
+                }
+            });
+        for (auto& h : th) h.join();
+        for (int t = 0; t < nthr; ++t) {
+            cudaEvent_t ev = nullptr;
+            SAI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            SAI_CUDA(cudaEventRecord(ev, wk.s[t]));
+            SAI_CUDA(cudaStreamWaitEvent(st, ev, 0));
+            cudaEventDestroy(ev);
+        }
+        for (int t = 0; t < nthr; ++t)
+            if (tst[t] != SAI_OK) return tst[t];
     }
     SAI_CUDA(cudaEventRecord(e1.e, st));
 
@@ -691,7 +781,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     SAI_CUDA(cudaGetLastError());
     {
         // ||b_m||: item partials of each matrix's first system, summed on the host in item order
-        k_b_init<<<SAI_GRID(grid_for(nit, cap)), BR, 0, st>>>(Y, Bv, X, r, rh, p, v, part.as<double>());
+        k_b_init<<<SAI_GRID(grid_for(sai_div_up(nit, BR / 32), cap)), BR, 0, st>>>(Y, Bv, X, r, rh, p, v, part.as<double>());
         std::vector<double> hp(nit);
         SAI_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * nit, cudaMemcpyDeviceToHost, st));
         SAI_CUDA(cudaStreamSynchronize(st));
@@ -712,7 +802,8 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     const int64_t *Ar = bd.Atr_rp.as<int64_t>(), *Mr = P.Mr_rp.as<int64_t>();
     const int32_t *Ac = bd.Atr_ci.as<int32_t>(), *Mc = P.Mr_ci.as<int32_t>();
     const double *Av = bd.Atr_v.as<double>(), *Mv = P.Mr_v.as<double>();
-    const unsigned gi = grid_for(nit, cap);
+    const unsigned gi = grid_for(nit, cap);                   // SpMV: one block per item
+    const unsigned gw = grid_for(sai_div_up(nit, BR / 32), cap);  // vector kernels: one warp per item
     const unsigned gs = sai_div_up((int64_t)nsys * 32, 256), gt = sai_div_up(nsys, 256);
     double* pt = part.as<double>();
     const int maxit = prm->krylov.maxit;
@@ -726,7 +817,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
         k_b_start<<<SAI_GRID(gt), 256, 0, q>>>(nsys, maxit, S);
         {
             ProfScope ps(PROF_BICG_VEC, q);
-            k_b_p<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, p, v, S);
+            k_b_p<<<SAI_GRID(gw), BR, 0, q>>>(Y, r, p, v, S);
         }
         {
             ProfScope ps(PROF_SPMM, q);
@@ -738,12 +829,12 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
         }
         {
             ProfScope ps(PROF_BICG_VEC, q);
-            k_b_dots<1><<<SAI_GRID(gi), BR, 0, q>>>(Y, rh, v, nullptr, nullptr, S.active, pt);
+            k_b_dots<1><<<SAI_GRID(gw), BR, 0, q>>>(Y, rh, v, nullptr, nullptr, S.active, pt);
         }
         k_b_f1<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S, Wk);
         {
             ProfScope ps(PROF_BICG_VEC, q);
-            k_b_s<<<SAI_GRID(gi), BR, 0, q>>>(Y, r, v, s, S, pt);
+            k_b_s<<<SAI_GRID(gw), BR, 0, q>>>(Y, r, v, s, S, pt);
         }
         k_b_f2<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
         {
@@ -756,12 +847,12 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
         }
         {
             ProfScope ps(PROF_BICG_VEC, q);
-            k_b_dots<2><<<SAI_GRID(gi), BR, 0, q>>>(Y, t, s, t, t, S.go, pt);
+            k_b_dots<2><<<SAI_GRID(gw), BR, 0, q>>>(Y, t, s, t, t, S.go, pt);
         }
         k_b_f3<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S, Wk);
         {
             ProfScope ps(PROF_BICG_VEC, q);
-            k_b_xr<<<SAI_GRID(gi), BR, 0, q>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
+            k_b_xr<<<SAI_GRID(gw), BR, 0, q>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
         }
         k_b_f4<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
     };
