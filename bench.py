@@ -22,8 +22,8 @@ here) on the host cores on a bounded sample of the same workload, scaled to
 the metric's unit.
 
 --workload selects another workload; each prints its own JSON line:
-  zipf1e5   the heavy-tailed Zipf-count matrix at n = 1e5 (s = 5343, so 5344
-            systems per solve): step = split -> SPAI(0.4, 5, 10) -> BiCGStab
+  zipf      the heavy-tailed Zipf-count matrix, n = 1e5 by default (--zipf-n;
+            s = 5343, so 5344 systems per solve): step = split -> SPAI(0.4, 5, 10) -> BiCGStab
             forward solve of x(A, b) -> backward pass (the s+1 transposed
             solves with M^T and the adjoint SMW) for a seeded g = dL/dx;
             value = seconds per step (FP64 throughout).
@@ -33,6 +33,7 @@ the metric's unit.
             SMW); value = columns of M built per second of the whole batch.
 """
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -163,6 +164,33 @@ def site_roofline(name, s, peaks):
     return r
 
 
+TRAFFIC_MD = os.path.join(ROOT, "profiles", "traffic_convdiff3d64_bench_step.md")
+
+
+def measured_traffic(site):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum,
+    averaged over every launch of the site's kernel in one ncu capture of the
+    timed step) from the committed summary, or None when there is none or the
+    kernel's source file has changed since (its sha256 prefix is recorded)."""
+    try:
+        with open(TRAFFIC_MD) as f:
+            text = f.read()
+    except OSError:
+        return None
+    for line in text.splitlines():
+        parts = [q.strip().strip("`") for q in line.strip().strip("|").split("|")]
+        if len(parts) < 6 or parts[0] != site:
+            continue
+        try:
+            with open(os.path.join(ROOT, parts[4]), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest()[:16] != parts[5]:
+                    return None
+            return float(parts[3])
+        except (OSError, ValueError):
+            return None
+    return None
+
+
 def roofline(prof, peaks):
     """Dominant profiled site (largest device time): achieved vs its binding peak;
     every site's figures under "sites"."""
@@ -171,7 +199,7 @@ def roofline(prof, peaks):
         return None
     name = max(sites, key=lambda k: sites[k]["ms"])
     r = site_roofline(name, sites[name], peaks)
-    r.update({"kernel": name, "traffic": None,
+    r.update({"kernel": name, "traffic": measured_traffic(name),
               "measured": "CUDA events on the first 16 launches of each site and every 7th after, "
                           "one profiled step after the timed steps",
               "sites": {k: dict(ms=round(v["ms"], 3), **{q: (round(x, 4) if isinstance(x, float) else x)
@@ -420,15 +448,18 @@ def _gpu_setup():
     return torch, sai, dist, ws, rank, local
 
 
-def _timed_steps(torch, sai, dist, step, nsteps, flush, profile=False):
+def _timed_steps(torch, sai, dist, step, nsteps, flush, profile=False, label=None):
     """Device time per step (CUDA events on the current stream, L2 flushed
-    before each step outside the events), max over ranks."""
+    before each step outside the events), max over ranks; label opens an NVTX
+    range around the steps."""
     stream = torch.cuda.current_stream()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     if profile:
         sai.profile_begin()
+    if label:
+        nvtx(torch, label)
     ms, out = [], None
     for _ in range(nsteps):
         flush.zero_()
@@ -439,6 +470,8 @@ def _timed_steps(torch, sai, dist, step, nsteps, flush, profile=False):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    if label:
+        nvtx(torch, None)
     prof = sai.profile_end() if profile else None
     total = float(np.sum(ms))
     if dist:
@@ -492,7 +525,7 @@ def zipf_oracle_sample(P, nsample=4):
 
 def run_zipf(args):
     torch, sai, dist, ws, rank, local = _gpu_setup()
-    P = W.zipf_columns(n=100000, seed=W.SEED_BASE + 5 + rank)  # replicas: one independent system per rank
+    P = W.zipf_columns(n=args.zipf_n, seed=W.SEED_BASE + 5 + rank)  # replicas: one independent system per rank
     A, n = P.A, P.n
     dA = sai.CscMatrix.from_arrays(A.indptr, A.indices, A.data, n)
     b = torch.as_tensor(P.b, device="cuda")
@@ -511,7 +544,7 @@ def run_zipf(args):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = sai.launch_count()
-    ms_step, out, _ = _timed_steps(torch, sai, dist, step, args.steps, flush)
+    ms_step, out, _ = _timed_steps(torch, sai, dist, step, args.steps, flush, label="bench_timed")
     launches = sai.launch_count() - l0
     clk = clocks.stop()
     _, _, prof = _timed_steps(torch, sai, dist, step, 1, flush, profile=True)
@@ -548,13 +581,14 @@ def run_zipf(args):
     sp_, Pc, it, rf, itb, rb = out
     peaks = load_peaks()
     line = {
-        "metric": "x(A_values, b) forward + backward time, Zipf-count matrix n=1e5",
+        "metric": "x(A_values, b) forward + backward time, Zipf-count matrix n=%d" % n,
         "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "zipf1e5: n=100000, column counts min(Zipf(1.5), 5000) at random rows, N(0,1) "
+        "config": {"workload": "zipf: n=%d, column counts min(Zipf(1.5), cap) at random rows, N(0,1) " % n +
                                "values, a_jj = 1.2 sum|a_ij|; irregular above tau=200; SPAI(0.4,5,10); BiCGStab "
                                "to eps 1e-10 on the s+1 forward and s+1 transposed systems; b = A*ones, g ~ N(0,1)",
+                   "cap": int(P.params["cap"]),
                    "n": n, "nnz": int(A.nnz), "s": sp_.s, "p": sp_.p, "nnz_M": Pc.nnz,
                    "l2": "flushed by a 256 MB write between timed steps"},
         "stage_ms": {"build": Pc.build_ms, "forward_krylov": rf["ms_krylov"], "forward_smw": rf["ms_smw"],
@@ -596,7 +630,7 @@ def run_batch(args):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = sai.launch_count()
-    ms_step, out, _ = _timed_steps(torch, sai, dist, step, args.steps, flush)
+    ms_step, out, _ = _timed_steps(torch, sai, dist, step, args.steps, flush, label="bench_timed")
     launches = sai.launch_count() - l0
     clk = clocks.stop()
     _, _, prof = _timed_steps(torch, sai, dist, step, 1, flush, profile=True)
@@ -659,11 +693,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="convdiff3d64", choices=["convdiff3d64", "zipf1e5", "batch256"])
+    ap.add_argument("--workload", default="convdiff3d64", choices=["convdiff3d64", "zipf", "batch256"])
+    ap.add_argument("--zipf-n", type=int, default=100000, help="order of the Zipf-count matrix (--workload zipf)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "zipf1e5":
+    if args.workload == "zipf":
         return run_zipf(args)
     if args.workload == "batch256":
         return run_batch(args)

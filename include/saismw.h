@@ -70,6 +70,9 @@ typedef struct {
  * ties to the smaller row; p_keep nearest when no diagonal is stored);
  * p_keep <= 0 means p_keep = p (the paper's choice p^ = p). Dropped entries
  * form U (n x s), V = [e_J0 ... e_J(s-1)] with J ascending.
+ * abs_tau = +infinity keeps every column: A~ = A and s = 0, so the builders
+ * and sai_solve work on A itself (the S-SPAI / S-PSAI baselines of
+ * section 5).
  * ---------------------------------------------------------------------- */
 typedef struct {
     double thresh_mult;

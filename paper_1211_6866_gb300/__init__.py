@@ -271,7 +271,9 @@ class Precond:
 
 
 def split(A, thresh_mult=10.0, abs_tau=-1.0, ge=False, p_keep=0):
-    """Step 1 of Procedure *: detect the irregular columns and split A = A~ + U V^T."""
+    """Step 1 of Procedure *: detect the irregular columns and split A = A~ + U V^T.
+    abs_tau=float("inf") keeps every column (A~ = A, s = 0): the S-SPAI and
+    S-PSAI baselines build on A itself."""
     L = load()
     h = C.c_void_p()
     v = A.view()

@@ -475,14 +475,27 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         ncand = warp_sum_int(ncand);
         if (__any_sync(SAI_FULL, ovf) || ncand + nS > T::HC / 2) return ST_OVERFLOW;
         __syncwarp();
-        // profitability keys and a per-lane sorted top list
+        // compact the candidates (occupied slots not in S) to the front of ck,
+        // in slot order, so that the scoring keeps every lane on a candidate;
+        // a chunk is read whole before it is written, and the writes stay at
+        // or below it
+        int nc = 0;
+        for (int s0 = 0; s0 < T::HC; s0 += 32) {
+            const int32_t j = w.ck[s0 + lane];
+            const bool keep = j >= 0 && !w.cf[s0 + lane];
+            const unsigned km = __ballot_sync(SAI_FULL, keep);
+            if (keep) w.ck[nc + __popc(km & ((1u << lane) - 1u))] = j;
+            nc += __popc(km);
+            __syncwarp();
+        }
+        // profitability keys and a per-lane sorted top list (the selection of
+        // the mn smallest keys below does not depend on which lane scored what)
         unsigned long long top[MNMAX];
 #pragma unroll
         for (int q = 0; q < MNMAX; ++q) top[q] = ULLONG_MAX;
         int fsc = 0;
-        for (int sl = lane; sl < T::HC; sl += 32) {
-            const int32_t j = w.ck[sl];
-            if (j < 0 || w.cf[sl]) continue;
+        for (int idx = lane; idx < nc; idx += 32) {
+            const int32_t j = w.ck[idx];
             const double nj = A.colnorm2[j];
             if (!(nj > 0.0)) continue;
             fsc += 2 * (int)(A.cp[j + 1] - A.cp[j]) + 5;  // r^T a_j, rho_j^2 and its key
@@ -775,9 +788,16 @@ __global__ void k_stats(int32_t n, const int32_t* loops, const double* res, doub
 // columns not built in this call (outside a column list) hold tier -1
 __global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
 {
+    int c[4] = {0, 0, 0, 0};
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int t = tier[k];
-        if (t >= 0 && t < 4) atomicAdd(&out[2 + t], 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[q] += t == q;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int w = warp_sum_int(c[q]);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&out[2 + q], w);
     }
 }
 

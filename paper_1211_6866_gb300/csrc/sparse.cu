@@ -137,27 +137,39 @@ sai_status sai_scan_counts_i64(const int64_t* in, int64_t* out, int64_t n, cudaS
 }
 
 // ------------------------------------------------------------------ validate
+// one warp per column: the column's bounds, every row index in range and
+// each one above its predecessor
 __global__ void k_validate_csc(int32_t nrows, int32_t ncols, int64_t nnz, const int64_t* cp, const int32_t* ri,
                                int* bad)
 {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (j >= ncols) return;
-    int64_t b = cp[j], e = cp[j + 1];
-    if (j == 0 && b != 0) atomicOr(bad, 1);
-    if (j == ncols - 1 && e != nnz) atomicOr(bad, 2);
+    const int64_t b = cp[j], e = cp[j + 1];
+    if (lane == 0) {
+        if (j == 0 && b != 0) atomicOr(bad, 1);
+        if (j == ncols - 1 && e != nnz) atomicOr(bad, 2);
+    }
     if (e < b || b < 0 || e > nnz) {
-        atomicOr(bad, 4);
+        if (lane == 0) atomicOr(bad, 4);
         return;
     }
-    int32_t prev = -1;
-    for (int64_t t = b; t < e; ++t) {
-        int32_t i = ri[t];
-        if (i < 0 || i >= nrows || i <= prev) {
-            atomicOr(bad, 8);
-            return;
+    bool ok = true;
+    for (int64_t t0 = b + lane; t0 < e; t0 += 32 * 4) {
+        int32_t i[4], nx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = t0 + 32 * u;
+            i[u] = t < e ? ri[t] : 0;
+            nx[u] = t + 1 < e ? ri[t + 1] : INT32_MAX;
         }
-        prev = i;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = t0 + 32 * u;
+            if (t < e && (i[u] < 0 || i[u] >= nrows || nx[u] <= i[u])) ok = false;
+        }
     }
+    if (!__all_sync(SAI_FULL, ok) && lane == 0) atomicOr(bad, 8);
 }
 
 sai_status sai_validate_csc(int32_t nrows, int32_t ncols, int64_t nnz, const int64_t* cp, const int32_t* ri,
@@ -167,7 +179,8 @@ sai_status sai_validate_csc(int32_t nrows, int32_t ncols, int64_t nnz, const int
     Buf bad;
     SAI_TRY(bad.alloc(sizeof(int), st, true));
     SAI_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    k_validate_csc<<<SAI_GRID(sai_div_up(ncols, 256)), 256, 0, st>>>(nrows, ncols, nnz, cp, ri, bad.as<int>());
+    k_validate_csc<<<SAI_GRID(sai_div_up((int64_t)ncols * 32, 256)), 256, 0, st>>>(nrows, ncols, nnz, cp, ri,
+                                                                                  bad.as<int>());
     SAI_CUDA(cudaGetLastError());
     int h = 0;
     SAI_CUDA(cudaMemcpyAsync(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -314,8 +327,21 @@ __global__ void k_csc_axpy(int32_t n, const int64_t* cp, const int32_t* ri, cons
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (w >= n) return;
-    double xj = x[w];
-    for (int64_t t = cp[w] + lane; t < cp[w + 1]; t += 32) atomicAdd(&y[ri[t]], cv[t] * xj);
+    const double xj = x[w];
+    const int64_t e = cp[w + 1];
+    for (int64_t t0 = cp[w] + lane; t0 < e; t0 += 32 * 8) {  // eight entries in flight per lane
+        int32_t r[8];
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t t = t0 + 32 * u;
+            r[u] = t < e ? ri[t] : 0;
+            a[u] = t < e ? cv[t] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (t0 + 32 * u < e) atomicAdd(&y[r[u]], a[u] * xj);
+    }
 }
 
 __global__ void k_resid_norms(int32_t n, const double* b, const double* ax, double* out)

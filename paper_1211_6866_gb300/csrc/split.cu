@@ -102,17 +102,31 @@ __global__ void k_copy_split(int32_t n, const int64_t* cp, const int32_t* ri, co
         }
         return;
     }
+    // an irregular column can hold thousands of entries: eight in flight per lane
     int64_t t = pos[j];
     int64_t a0 = w0[t], a1 = w1[t];
     int64_t ou = U_cp[t];
-    for (int64_t q = b + lane; q < e; q += 32) {
-        if (q >= a0 && q < a1) {
-            At_ri[oa + (q - a0)] = ri[q];
-            At_v[oa + (q - a0)] = v[q];
-        } else {
-            int64_t d = q < a0 ? (q - b) : (q - b) - (a1 - a0);
-            U_ri[ou + d] = ri[q];
-            U_v[ou + d] = v[q];
+    for (int64_t q0 = b + lane; q0 < e; q0 += 32 * 8) {
+        int32_t r[8];
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t q = q0 + 32 * u;
+            r[u] = q < e ? ri[q] : 0;
+            x[u] = q < e ? v[q] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t q = q0 + 32 * u;
+            if (q >= e) continue;
+            if (q >= a0 && q < a1) {
+                At_ri[oa + (q - a0)] = r[u];
+                At_v[oa + (q - a0)] = x[u];
+            } else {
+                int64_t d = q < a0 ? (q - b) : (q - b) - (a1 - a0);
+                U_ri[ou + d] = r[u];
+                U_v[ou + d] = x[u];
+            }
         }
     }
 }
@@ -120,16 +134,23 @@ __global__ void k_copy_split(int32_t n, const int64_t* cp, const int32_t* ri, co
 __global__ void k_colstats(int32_t n, const int64_t* cp, const double* v, double* colnorm2,
                            unsigned long long* norm1_bits)
 {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    double s2 = 0.0, s1 = 0.0;
-    for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
-        s2 += v[q] * v[q];
-        s1 += fabs(v[q]);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double s1 = 0.0;
+    if (j < n) {
+        double s2 = 0.0;
+        for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
+            s2 += v[q] * v[q];
+            s1 += fabs(v[q]);
+        }
+        colnorm2[j] = s2;
     }
-    colnorm2[j] = s2;
-    // non-negative doubles order like their bit patterns
-    atomicMax(norm1_bits, (unsigned long long)__double_as_longlong(s1));
+    // non-negative doubles order like their bit patterns: the warp's largest, then one atomic
+    unsigned long long m = (unsigned long long)__double_as_longlong(s1);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(SAI_FULL, m, o);
+        m = w > m ? w : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(norm1_bits, m);
 }
 
 sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, cudaStream_t st, bool async,
