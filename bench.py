@@ -151,7 +151,10 @@ def site_roofline(name, s, peaks):
     alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
     t_hbm = bytes_l / (hbm * 1e9)
     t_alu = flops_l / (alu_peak * 1e12)
-    if flops_l > 0 and t_alu > t_hbm:
+    if bytes_l == 0 and flops_l == 0:  # control kernels: no algorithmic traffic to set against a peak
+        r = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+             "peak_source": "no algorithmic bytes or flops (control kernel)"}
+    elif flops_l > 0 and t_alu > t_hbm:
         ach = flops_l / avg_s / 1e12
         r = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
              "peak_source": ("FP32" if fp32 else "FP64") + " ALU nominal from unit counts and clocks"}

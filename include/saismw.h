@@ -196,6 +196,14 @@ sai_status sai_build_set_config(const sai_build_config* cfg);
 sai_status sai_precond_copy_out(sai_precond P, int64_t* col_ptr, int32_t* row_idx, double* val,
                                 int32_t* loops, double* res, double* res_post, sai_stream_t stream);
 void sai_precond_destroy(sai_precond P);
+/* A preconditioner handle for a given M (n x n CSC on the device, rows
+ * ascending per column, caller-owned and only read): for an M saved from
+ * an earlier build (sai_precond_copy_out) and loaded again, so that later
+ * right-hand sides skip the build (the paper keeps M for sequences of
+ * right-hand sides). The arrays are copied and checked
+ * (SAI_INVALID_ARG on a malformed CSC); the CSR copy is built; the
+ * per-column statistics are zeros. Synchronises the stream. */
+sai_status sai_precond_create(const sai_csc_view* M, sai_stream_t stream, sai_precond* out);
 
 /* ----------------------------------------------------------------------
  * Step 3: k systems A~ X(:,c) = B(:,c) solved together, right

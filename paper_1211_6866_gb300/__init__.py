@@ -140,6 +140,7 @@ def load():
     L.sai_build_spai.argtypes = [vp, C.POINTER(_SpaiParams), vp, C.POINTER(vp)]
     L.sai_build_psai.argtypes = [vp, C.POINTER(_PsaiParams), vp, C.POINTER(vp)]
     L.sai_precond_get_info.argtypes = [vp, C.POINTER(_PrecondInfo)]
+    L.sai_precond_create.argtypes = [C.POINTER(_CscView), vp, C.POINTER(vp)]
     L.sai_precond_copy_out.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
     L.sai_precond_destroy.argtypes = [vp]
     L.sai_precond_destroy.restype = None
@@ -325,6 +326,35 @@ def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10, precision=0):
     prm = _PsaiParams(delta, tol, tol_mode, lmax, precision)
     _check("sai_build_psai", L.sai_build_psai(sp._h, C.byref(prm), _stream(), C.byref(h)))
     return Precond(h.value)
+
+
+def precond_from_csc(M):
+    """A preconditioner handle for a given M (CscMatrix on the device, rows
+    ascending per column), e.g. one saved by save_precond and loaded again."""
+    L = load()
+    h = C.c_void_p()
+    v = M.view()
+    _check("sai_precond_create", L.sai_precond_create(C.byref(v), _stream(), C.byref(h)))
+    return Precond(h.value)
+
+
+def save_precond(P, path):
+    """Writes M (CSC: n, col_ptr, row_idx, val) to path as a .npz file, so a
+    later process can solve further right-hand sides without the build."""
+    import numpy as np
+
+    Mc = P.arrays()[0]
+    np.savez(path, n=np.int64(Mc.n), col_ptr=Mc.col_ptr.cpu().numpy(), row_idx=Mc.row_idx.cpu().numpy(),
+             val=Mc.val.cpu().numpy())
+
+
+def load_precond(path, device="cuda"):
+    """The preconditioner saved by save_precond, as a handle on the device."""
+    import numpy as np
+
+    with np.load(path) as z:
+        M = CscMatrix.from_arrays(z["col_ptr"], z["row_idx"], z["val"], int(z["n"]), device=device)
+    return precond_from_csc(M)
 
 
 def krylov_solve(sp, P, B, thr, method=BICGSTAB, restart=50, maxit=500, precision=0, inner_tol=0.0,

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 
 #include <atomic>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string.h>
@@ -26,7 +27,7 @@ struct ProfPair {
 static std::vector<ProfPair> g_prof_ev[PROF_NSITES];
 static const char* k_site_names[PROF_NSITES] = {"sai_build",          "krylov_spmm",     "gmres_project",
                                                 "gmres_update",       "bicgstab_vector", "krylov_spmm_fp32",
-                                                "gmres_project_fp32", "gmres_update_fp32"};
+                                                "gmres_project_fp32", "gmres_update_fp32", "gmres_step"};
 static const size_t k_ev_pool = 1 << 16;
 
 unsigned sai_count_grid(unsigned g)
@@ -276,6 +277,44 @@ sai_status sai_build_psai(sai_split h, const sai_psai_params* prm, sai_stream_t 
         return st;
     }
     *out = P;
+    return SAI_OK;
+}
+
+sai_status sai_precond_create(const sai_csc_view* M, sai_stream_t stream, sai_precond* out)
+{
+    if (!out) return SAI_INVALID_ARG;
+    *out = nullptr;
+    if (!M || M->n < 0 || M->nnz < 0 || (M->n > 0 && !M->col_ptr) || (M->nnz > 0 && (!M->row_idx || !M->val)))
+        return SAI_INVALID_ARG;
+    sai_pool_init_once();
+    cudaStream_t st = S(stream);
+    const int32_t n = M->n;
+    const int64_t nnz = M->nnz;
+    SAI_TRY(sai_validate_csc(n, n, nnz, M->col_ptr, M->row_idx, st));
+    std::unique_ptr<sai_precond_s> P(new (std::nothrow) sai_precond_s());
+    if (!P) return SAI_OOM;
+    P->n = n;
+    P->nnz = nnz;
+    const size_t nn = (size_t)(n > 0 ? n : 1), nz = (size_t)(nnz > 0 ? nnz : 1);
+    SAI_TRY(P->M_cp.alloc(sizeof(int64_t) * (nn + 1), st, false));
+    SAI_TRY(P->M_ri.alloc(sizeof(int32_t) * nz, st, false));
+    SAI_TRY(P->M_v.alloc(sizeof(double) * nz, st, false));
+    SAI_TRY(P->loops.alloc(sizeof(int32_t) * nn, st, false));
+    SAI_TRY(P->res.alloc(sizeof(double) * nn, st, false));
+    SAI_TRY(P->res_post.alloc(sizeof(double) * nn, st, false));
+    const cudaMemcpyKind D = cudaMemcpyDeviceToDevice;
+    SAI_CUDA(cudaMemcpyAsync(P->M_cp.p, M->col_ptr, sizeof(int64_t) * ((size_t)n + 1), D, st));
+    if (nnz > 0) {
+        SAI_CUDA(cudaMemcpyAsync(P->M_ri.p, M->row_idx, sizeof(int32_t) * (size_t)nnz, D, st));
+        SAI_CUDA(cudaMemcpyAsync(P->M_v.p, M->val, sizeof(double) * (size_t)nnz, D, st));
+    }
+    SAI_CUDA(cudaMemsetAsync(P->loops.p, 0, sizeof(int32_t) * nn, st));
+    SAI_CUDA(cudaMemsetAsync(P->res.p, 0, sizeof(double) * nn, st));
+    SAI_CUDA(cudaMemsetAsync(P->res_post.p, 0, sizeof(double) * nn, st));
+    SAI_TRY(sai_csc_to_csr(n, n, nnz, P->M_cp.as<int64_t>(), P->M_ri.as<int32_t>(), P->M_v.as<double>(), P->Mr_rp,
+                           P->Mr_ci, P->Mr_v, st, false));
+    SAI_CUDA(cudaStreamSynchronize(st));
+    *out = P.release();
     return SAI_OK;
 }
 

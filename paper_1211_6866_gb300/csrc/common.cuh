@@ -89,7 +89,8 @@ enum {
     PROF_SPMM32 = 5,     // FP32 SpMV of the refined GMRES inner solves
     PROF_GM_DOTS32 = 6,  // FP32 projections
     PROF_GM_UPDATE32 = 7,// FP32 updates
-    PROF_NSITES = 8
+    PROF_GM_STEP = 8,    // GMRES step control (reductions, Givens, coefficients)
+    PROF_NSITES = 9
 };
 struct ProfScope {
     int site;

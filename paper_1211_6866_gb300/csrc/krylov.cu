@@ -1261,6 +1261,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
     __shared__ double csS[GM_MAXM], snS[GM_MAXM];
     __shared__ double sh[2];
     __shared__ int stop, mine;
+    extern __shared__ double hsm[];  // columns q < j of Hbar (leading dimension m + 1)
     const int j = *G.jdev;
     const int cnt = G.ladv[0];
     const int m = G.m;
@@ -1383,17 +1384,21 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
             // one thread per row i (adjacent rows of a column are adjacent in memory),
             // q ascending, the column loads in batches of 8 ahead of their FMAs
             double* hpc = G.hp + (size_t)c * (m + 1);
+            // Hbar's final columns to shared memory in one round of loads (column j-1
+            // was written above by this block)
+            for (int e = tid; e < j * (m + 1); e += blockDim.x) hsm[e] = Huc[e];
+            __syncthreads();
             for (int i = tid; i <= j; i += blockDim.x) {
                 double hs = 0.0;
                 int q = i > 0 ? i - 1 : 0;
                 for (; q + 8 <= j; q += 8) {
                     double hv[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) hv[u] = Huc[(size_t)(q + u) * (m + 1) + i];
+                    for (int u = 0; u < 8; ++u) hv[u] = hsm[(size_t)(q + u) * (m + 1) + i];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) hs = fma(hv[u], red[2 * (q + u)], hs);
                 }
-                for (; q < j; ++q) hs = fma(Huc[(size_t)q * (m + 1) + i], red[2 * q], hs);
+                for (; q < j; ++q) hs = fma(hsm[(size_t)q * (m + 1) + i], red[2 * q], hs);
                 const double cz = i < j ? red[2 * i + 1] : d;
                 hpc[i] = (cz - hs) / al;
             }
@@ -1694,6 +1699,9 @@ struct GmWork {  // device buffers of one GMRES engine
 };
 
 // One Arnoldi step (5 launches) for the advancing systems, index j on the device.
+// dynamic shared memory of k_dc_step: the final columns of Hbar, m x (m+1) doubles
+inline size_t step_smem(int m) { return sizeof(double) * (size_t)m * (size_t)(m + 1); }
+
 template <class T>
 void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, Sys& S, Gm& G, const int* cap,
                   double* pt, int* fl, const Dims& D, double tiny, cudaStream_t st)
@@ -1719,7 +1727,10 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
         ProfScope ps(D.site_dots, st);
         k_dc_dots<T><<<SAI_GRID(pb), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G.ladv, G.jdev, pt);
     }
-    k_dc_step<<<SAI_GRID(k * STEP_RB), STEP_THREADS, 0, st>>>(k, I.nch, pt, cap, S, G, D, tiny, fl);
+    {
+        ProfScope ps(PROF_GM_STEP, st);
+        k_dc_step<<<SAI_GRID(k * STEP_RB), STEP_THREADS, step_smem(G.m), st>>>(k, I.nch, pt, cap, S, G, D, tiny, fl);
+    }
     {
         ProfScope ps(D.site_upd, st);
         k_dc_update<T><<<SAI_GRID(ub), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G, G.ladv, G.jdev);
@@ -1744,9 +1755,11 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
     if (cb > (int64_t)g_sms * 8) cb = (int64_t)g_sms * 8;
     // alpha^2 below 64 unit roundoffs of u^T u: u lies in span(V) to working accuracy
     const double tiny = 64.0 * (sizeof(T) == 4 ? 5.96e-8 : 1.11e-16);
+    // dynamic shared memory of the two kernels that stage Hbar / R (their
+    // static shared memory counts against the same per-block limit)
     const size_t tri_smem = sizeof(double) * ((size_t)m * (m + 1) + m);
-    if (tri_smem > 48 * 1024)
-        SAI_CUDA(cudaFuncSetAttribute(k_dc_trisolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
+    SAI_CUDA(cudaFuncSetAttribute(k_dc_trisolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
+    SAI_CUDA(cudaFuncSetAttribute(k_dc_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem(m)));
     int hflag = 0;
     T* r = Wk.r;
     T* w = Wk.w;
