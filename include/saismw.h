@@ -79,6 +79,12 @@ typedef struct {
     double abs_tau;
     int32_t ge;
     int32_t p_keep;
+    int32_t keep_rule; /* 0: the diagonal and the p_keep-1 entries nearest to it
+                          (the paper's choice); 1: the diagonal and the p_keep-1
+                          entries of largest magnitude (the other rule of section 4;
+                          ties to the smaller row; p_keep largest without a
+                          diagonal). Other values: SAI_INVALID_ARG. */
+    int32_t reserved;  /* 0 */
 } sai_split_params;
 
 typedef struct sai_split_s* sai_split;

@@ -128,11 +128,14 @@ def detect(A, mult=10.0, abs_tau=-1.0, ge=False):
     return J[: s.value].copy(), p.value, tau.value
 
 
-def split(A, J, p_keep):
+def split(A, J, p_keep, rule=0):
+    """A = A~ + U V^T; rule 0 keeps the p_keep entries nearest to the diagonal,
+    rule 1 the diagonal and the p_keep-1 largest in magnitude (section 4)."""
     a = _In(A)
     J = np.ascontiguousarray(J, dtype=np.int32)
     At, U = _Csc(), _Csc()
-    _check("split", lib().orc_split(C.byref(a.s), _ptr(J, _i32p), len(J), int(p_keep), C.byref(At), C.byref(U)))
+    _check("split", lib().orc_split_rule(C.byref(a.s), _ptr(J, _i32p), len(J), int(p_keep), int(rule), C.byref(At),
+                                         C.byref(U)))
     return _take(At), _take(U)
 
 

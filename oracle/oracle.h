@@ -61,6 +61,11 @@ int orc_detect(const orc_csc* A, double mult, double abs_tau, int ge,
  * and U (n x s, column t holds the dropped entries of column J[t]). */
 int orc_split(const orc_csc* A, const int32_t* J, int32_t s, int32_t p_keep,
               orc_csc* At_out, orc_csc* U_out);
+/* the same with a keep rule: 0 = the diagonal and the p_keep-1 nearest entries
+ * (as orc_split), 1 = the diagonal and the p_keep-1 entries of largest
+ * magnitude (ties to the smaller row; p_keep largest without a diagonal) */
+int orc_split_rule(const orc_csc* A, const int32_t* J, int32_t s, int32_t p_keep, int32_t rule,
+                   orc_csc* At_out, orc_csc* U_out);
 
 /* ---- section 2.1: SPAI (Grote-Huckle adaptive augmentation) -------------- */
 

@@ -3,6 +3,7 @@
  * p-1 nonzeros nearest to it), which defines A = A~ + U V^T, eq. (split).
  * Test infrastructure only. */
 #include "oracle_internal.h"
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -39,10 +40,38 @@ int orc_detect(const orc_csc* A, double mult, double abs_tau, int ge,
  * and the p-1 stored entries with the smallest distance |i - j|; on equal
  * distance the smaller row index is taken first. Everything dropped goes to
  * U, so A = A~ + U V^T holds entry by entry. */
+/* off-diagonal entry of an irregular column, for the largest-magnitude rule */
+typedef struct {
+    double mag;
+    int32_t row;
+    int64_t pos;
+} mag_entry;
+
+/* |a_ij| descending, then the smaller row first */
+static int cmp_mag(const void* x, const void* y)
+{
+    const mag_entry* a = (const mag_entry*)x;
+    const mag_entry* b = (const mag_entry*)y;
+    if (a->mag > b->mag) return -1;
+    if (a->mag < b->mag) return 1;
+    return (a->row > b->row) - (a->row < b->row);
+}
+
 int orc_split(const orc_csc* A, const int32_t* J, int32_t s, int32_t p_keep,
               orc_csc* At_out, orc_csc* U_out)
 {
-    if (!orc_csc_valid(A) || A->nrows != A->ncols || s < 0 || p_keep < 1) return ORC_BAD_INPUT;
+    return orc_split_rule(A, J, s, p_keep, 0, At_out, U_out);
+}
+
+/* rule 0 keeps the diagonal and the p_keep-1 entries nearest to it (the
+ * choice of section 4); rule 1 keeps the diagonal and the p_keep-1 entries
+ * of largest magnitude (the other rule named there), equal magnitudes to the
+ * smaller row, or the p_keep largest when no diagonal is stored. */
+int orc_split_rule(const orc_csc* A, const int32_t* J, int32_t s, int32_t p_keep, int32_t rule,
+                   orc_csc* At_out, orc_csc* U_out)
+{
+    if (!orc_csc_valid(A) || A->nrows != A->ncols || s < 0 || p_keep < 1 || (rule != 0 && rule != 1))
+        return ORC_BAD_INPUT;
     int32_t n = A->ncols;
     int64_t nnz = orc_nnz(A);
     /* map column -> position in J (or -1) */
@@ -62,6 +91,27 @@ int orc_split(const orc_csc* A, const int32_t* J, int32_t s, int32_t p_keep,
         if (slot[j] < 0) continue;
         int64_t b = A->col_ptr[j], e = A->col_ptr[j + 1];
         for (int64_t t = b; t < e; ++t) keep[t] = 0;
+        if (rule == 1) {
+            mag_entry* ent = (mag_entry*)orc_xmalloc((size_t)(e - b + 1) * sizeof(mag_entry));
+            int64_t m = 0;
+            int has_diag = 0;
+            for (int64_t t = b; t < e; ++t) {
+                if (A->row_idx[t] == j) {
+                    keep[t] = 1;
+                    has_diag = 1;
+                    continue;
+                }
+                ent[m].mag = fabs(A->val[t]);
+                ent[m].row = A->row_idx[t];
+                ent[m].pos = t;
+                ++m;
+            }
+            qsort(ent, (size_t)m, sizeof(mag_entry), cmp_mag);
+            int64_t want = has_diag ? (int64_t)p_keep - 1 : (int64_t)p_keep;
+            for (int64_t q = 0; q < m && q < want; ++q) keep[ent[q].pos] = 1;
+            free(ent);
+            continue;
+        }
         /* first stored row >= j */
         int64_t mid = b;
         while (mid < e && A->row_idx[mid] < j) ++mid;

@@ -41,7 +41,11 @@ class _CscView(C.Structure):
 
 
 class _SplitParams(C.Structure):
-    _fields_ = [("thresh_mult", C.c_double), ("abs_tau", C.c_double), ("ge", C.c_int32), ("p_keep", C.c_int32)]
+    _fields_ = [("thresh_mult", C.c_double), ("abs_tau", C.c_double), ("ge", C.c_int32), ("p_keep", C.c_int32),
+                ("keep_rule", C.c_int32), ("reserved", C.c_int32)]
+
+
+_KEEP = {"nearest": 0, "largest": 1}
 
 
 class _SplitInfo(C.Structure):
@@ -271,14 +275,16 @@ class Precond:
         return CscMatrix(self.n, cp, ri, v), loops, res, post
 
 
-def split(A, thresh_mult=10.0, abs_tau=-1.0, ge=False, p_keep=0):
+def split(A, thresh_mult=10.0, abs_tau=-1.0, ge=False, p_keep=0, keep="nearest"):
     """Step 1 of Procedure *: detect the irregular columns and split A = A~ + U V^T.
-    abs_tau=float("inf") keeps every column (A~ = A, s = 0): the S-SPAI and
-    S-PSAI baselines build on A itself."""
+    keep="nearest" keeps the diagonal and the p-1 entries nearest to it (the
+    paper's choice), keep="largest" the diagonal and the p-1 largest in
+    magnitude (the other rule of section 4). abs_tau=float("inf") keeps every
+    column (A~ = A, s = 0): the S-SPAI and S-PSAI baselines build on A itself."""
     L = load()
     h = C.c_void_p()
     v = A.view()
-    prm = _SplitParams(thresh_mult, abs_tau, int(ge), int(p_keep))
+    prm = _SplitParams(thresh_mult, abs_tau, int(ge), int(p_keep), _KEEP[keep], 0)
     _check("sai_split_create", L.sai_split_create(C.byref(v), C.byref(prm), _stream(), C.byref(h)))
     return Split(h.value)
 
@@ -396,14 +402,14 @@ def rel_resid(A, b, x):
 
 def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0, abs_tau=-1.0,
           delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, x=None, krylov_precision=0,
-          inner_tol=0.0, sai_precision=0):
+          inner_tol=0.0, sai_precision=0, keep="nearest"):
     """Procedure * on the device. krylov_precision=1 selects the FP32-inner /
     FP64-refined GMRES; sai_precision=1 the FP32 QR + FP64 refinement build.
     Returns (x, iters list, report dict)."""
     L = load()
     if x is None:
         x = torch.empty(A.n, dtype=torch.float64, device=b.device)
-    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0), 0 if sai == "spai" else 1,
+    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
                        _PsaiParams(delta, tol, tol_mode, lmax, sai_precision),
                        _KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit, krylov_precision,
@@ -504,7 +510,7 @@ class SparseSolve(torch.autograd.Function):
 
 
 def solve_batched(As, bs, sai="spai", eps=1e-8, maxit=500, thresh_mult=10.0, abs_tau=-1.0, delta=0.4, mn=5,
-                  max_aug=10, key_bits=20, tol=0.0, tol_mode=1, lmax=10, sai_precision=0):
+                  max_aug=10, key_bits=20, tol=0.0, tol_mode=1, lmax=10, sai_precision=0, keep="nearest"):
     """Procedure * for a batch of independent matrices (lists of CscMatrix and
     device b vectors): one SAI build over all their columns, one batched
     BiCGStab over all their s_i + 1 systems, SMW per matrix.
@@ -515,7 +521,7 @@ def solve_batched(As, bs, sai="spai", eps=1e-8, maxit=500, thresh_mult=10.0, abs
     xs = [torch.empty(A.n, dtype=torch.float64, device=b.device) for A, b in zip(As, bs)]
     bp = (C.c_void_p * nmat)(*[_p(b.contiguous()).value for b in bs])
     xp = (C.c_void_p * nmat)(*[_p(x).value for x in xs])
-    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0), 0 if sai == "spai" else 1,
+    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
                        _PsaiParams(delta, tol, tol_mode, lmax, sai_precision),
                        _KrylovParams(BICGSTAB, 50, maxit, 0, 0.0, 0), eps)

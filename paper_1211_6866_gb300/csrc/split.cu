@@ -7,6 +7,9 @@
 //   k_window        for each irregular column: the kept entries are a contiguous
 //                   window of its sorted rows around the diagonal (diagonal plus the
 //                   p_keep-1 nearest, ties to the smaller row)      (one thread / column)
+//   k_keep_largest  the other rule of section 4: the diagonal and the p_keep-1
+//                   entries of largest magnitude (ties to the smaller row) of each
+//                   irregular column, as per-entry keep flags      (one block / column)
 //   k_copy_split    copies A into A~ (window only for irregular columns) and U
 //                   (the rest)                                      (one warp / column)
 //   k_colstats      ||a~_j||^2 and sum_i |a~_ij| per column, max -> ||A~||_1
@@ -30,7 +33,7 @@ __global__ void k_compact_J(int32_t n, const int32_t* flag, const int64_t* pos, 
 // Two-pointer walk outwards from the diagonal: the kept set of an irregular
 // column is [w0, w1) in its sorted entry range.
 __global__ void k_window(int32_t s, const int32_t* J, const int64_t* cp, const int32_t* ri, int32_t p_keep,
-                         int64_t* w0, int64_t* w1)
+                         int64_t* w0, int64_t* w1, int64_t* nkeep)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= s) return;
@@ -67,17 +70,102 @@ __global__ void k_window(int32_t s, const int32_t* J, const int64_t* cp, const i
     }
     w0[t] = a0;
     w1[t] = a1;
+    nkeep[t] = a1 - a0;
+}
+
+// sum of an int over the block (blockDim.x = 256), the result in every thread
+__device__ __forceinline__ long long block_sum_ll(long long x, long long* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(SAI_FULL, x, o);
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    long long t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long mag_key(double v)
+{
+    return (unsigned long long)__double_as_longlong(fabs(v));  // orders like |v|
+}
+
+// Keep flags of the second rule of section 4, one block (256 threads) per
+// irregular column: K = p_keep-1 off-diagonal entries with the diagonal, or
+// K = p_keep without one. The K-th largest key T is found bit by bit from
+// the top (the largest T with #{key >= T} >= K); entries above T are kept,
+// and entries equal to T in row order until K are kept.
+__global__ void __launch_bounds__(256) k_keep_largest(int32_t s, const int32_t* J, const int64_t* cp,
+                                                      const int32_t* ri, const double* v, int32_t p_keep,
+                                                      uint8_t* keep, int64_t* nkeep)
+{
+    __shared__ long long red[8];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int32_t t = blockIdx.x; t < s; t += gridDim.x) {
+        const int32_t j = J[t];
+        const int64_t b = cp[j], e = cp[j + 1];
+        long long dq = -1;
+        for (int64_t q = b + tid; q < e; q += 256)
+            if (ri[q] == j) dq = q;
+        // the diagonal's position (rows are distinct: at most one thread finds it)
+        const long long dsum = block_sum_ll(dq + 1, red) - 1;
+        const int hasd = dsum >= 0;
+        const long long K = hasd ? p_keep - 1 : p_keep;
+        const long long off = (e - b) - hasd;
+        if (off <= K || K <= 0) {
+            for (int64_t q = b + tid; q < e; q += 256) keep[q] = (off <= K) || q == dsum;
+            if (tid == 0) nkeep[t] = off <= K ? e - b : hasd;
+            __syncthreads();
+            continue;
+        }
+        unsigned long long T = 0;
+        for (int bit = 63; bit >= 0; --bit) {
+            const unsigned long long cand = T | (1ull << bit);
+            long long c = 0;
+            for (int64_t q = b + tid; q < e; q += 256) c += (q != dsum && mag_key(v[q]) >= cand);
+            if (block_sum_ll(c, red) >= K) T = cand;
+        }
+        long long cg = 0;
+        for (int64_t q = b + tid; q < e; q += 256) cg += (q != dsum && mag_key(v[q]) > T);
+        const long long need = K - block_sum_ll(cg, red);  // >= 1 ties at T to keep
+        long long carry = 0;
+        for (int64_t base = b; base < e; base += 256) {
+            const int64_t q = base + tid;
+            const bool valid = q < e;
+            const unsigned long long kq = valid ? mag_key(v[q]) : 0ull;
+            const int tie = valid && q != dsum && kq == T;
+            int w = tie;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(SAI_FULL, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane == 31) red[wid] = w;
+            __syncthreads();
+            long long before = 0, tot = 0;
+            for (int u = 0; u < 8; ++u) {
+                if (u < wid) before += red[u];
+                tot += red[u];
+            }
+            const long long rank = carry + before + w - tie;
+            if (valid) keep[q] = q == dsum || (q != dsum && kq > T) || (tie && rank < need);
+            carry += tot;
+            __syncthreads();
+        }
+        if (tid == 0) nkeep[t] = K + hasd;
+        __syncthreads();
+    }
 }
 
 __global__ void k_count_split(int32_t n, const int64_t* cp, const int32_t* flag, const int64_t* pos,
-                              const int64_t* w0, const int64_t* w1, int64_t* cnt_At, int64_t* cnt_U)
+                              const int64_t* nkeep, int64_t* cnt_At, int64_t* cnt_U)
 {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int64_t c = cp[j + 1] - cp[j];
     if (flag[j]) {
         int64_t t = pos[j];
-        int64_t kept = w1[t] - w0[t];
+        int64_t kept = nkeep[t];
         cnt_At[j] = kept;
         cnt_U[t] = c - kept;
     } else {
@@ -87,8 +175,8 @@ __global__ void k_count_split(int32_t n, const int64_t* cp, const int32_t* flag,
 
 __global__ void k_copy_split(int32_t n, const int64_t* cp, const int32_t* ri, const double* v,
                              const int32_t* flag, const int64_t* pos, const int64_t* w0, const int64_t* w1,
-                             const int64_t* At_cp, int32_t* At_ri, double* At_v, const int64_t* U_cp,
-                             int32_t* U_ri, double* U_v)
+                             const uint8_t* kf, const int64_t* At_cp, int32_t* At_ri, double* At_v,
+                             const int64_t* U_cp, int32_t* U_ri, double* U_v)
 {
     int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -102,8 +190,29 @@ __global__ void k_copy_split(int32_t n, const int64_t* cp, const int32_t* ri, co
         }
         return;
     }
-    // an irregular column can hold thousands of entries: eight in flight per lane
     int64_t t = pos[j];
+    if (kf) {  // per-entry keep flags: kept and dropped entries each in row order
+        int64_t ka = 0, ku = 0;
+        const int64_t ou = U_cp[t];
+        const unsigned lt = (1u << lane) - 1u;
+        for (int64_t base = b; base < e; base += 32) {
+            const int64_t q = base + lane;
+            const bool valid = q < e;
+            const bool k = valid && kf[q];
+            const unsigned mk = __ballot_sync(SAI_FULL, k), md = __ballot_sync(SAI_FULL, valid && !k);
+            if (k) {
+                At_ri[oa + ka + __popc(mk & lt)] = ri[q];
+                At_v[oa + ka + __popc(mk & lt)] = v[q];
+            } else if (valid) {
+                U_ri[ou + ku + __popc(md & lt)] = ri[q];
+                U_v[ou + ku + __popc(md & lt)] = v[q];
+            }
+            ka += __popc(mk);
+            ku += __popc(md);
+        }
+        return;
+    }
+    // an irregular column can hold thousands of entries: eight in flight per lane
     int64_t a0 = w0[t], a1 = w1[t];
     int64_t ou = U_cp[t];
     for (int64_t q0 = b + lane; q0 < e; q0 += 32 * 8) {
@@ -156,7 +265,8 @@ __global__ void k_colstats(int32_t n, const int64_t* cp, const double* v, double
 sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, cudaStream_t st, bool async,
                            sai_split_s* h)
 {
-    if (!A || !prm || !h || A->n < 0 || A->nnz < 0) return SAI_INVALID_ARG;
+    if (!A || !prm || !h || A->n < 0 || A->nnz < 0 || (prm->keep_rule != 0 && prm->keep_rule != 1))
+        return SAI_INVALID_ARG;
     if (A->n > 0 && (!A->col_ptr || (A->nnz > 0 && (!A->row_idx || !A->val)))) return SAI_INVALID_ARG;
     const int32_t n = A->n;
     const int64_t nnz = A->nnz;
@@ -185,17 +295,28 @@ sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, c
 
     SAI_TRY(h->J.alloc(sizeof(int32_t) * (size_t)(s > 0 ? s : 1), st, async));
     if (n > 0) k_compact_J<<<SAI_GRID(gb), 256, 0, st>>>(n, flag.as<int32_t>(), pos.as<int64_t>(), h->J.as<int32_t>());
-    Buf w0, w1, cntA, cntU;
+    Buf w0, w1, nkeep, kflag, cntA, cntU;
     SAI_TRY(w0.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
     SAI_TRY(w1.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
+    SAI_TRY(nkeep.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
     SAI_TRY(cntA.alloc(sizeof(int64_t) * (size_t)(n + 1), st, true));
     SAI_TRY(cntU.alloc(sizeof(int64_t) * (size_t)(s + 1), st, true));
-    if (s > 0)
+    const bool largest = prm->keep_rule == 1;
+    if (largest) SAI_TRY(kflag.alloc((size_t)(nnz > 0 ? nnz : 1), st, true));
+    if (s > 0 && !largest)
         k_window<<<SAI_GRID(sai_div_up(s, 128)), 128, 0, st>>>(s, h->J.as<int32_t>(), A->col_ptr, A->row_idx, h->p_keep,
-                                                     w0.as<int64_t>(), w1.as<int64_t>());
+                                                     w0.as<int64_t>(), w1.as<int64_t>(), nkeep.as<int64_t>());
+    if (s > 0 && largest) {
+        int dev = 0, sms = 0;
+        SAI_CUDA(cudaGetDevice(&dev));
+        SAI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const unsigned g = (unsigned)(s < sms * 8 ? s : sms * 8);
+        k_keep_largest<<<SAI_GRID(g), 256, 0, st>>>(s, h->J.as<int32_t>(), A->col_ptr, A->row_idx, A->val, h->p_keep,
+                                                   kflag.as<uint8_t>(), nkeep.as<int64_t>());
+    }
     if (n > 0)
-        k_count_split<<<SAI_GRID(gb), 256, 0, st>>>(n, A->col_ptr, flag.as<int32_t>(), pos.as<int64_t>(), w0.as<int64_t>(),
-                                          w1.as<int64_t>(), cntA.as<int64_t>(), cntU.as<int64_t>());
+        k_count_split<<<SAI_GRID(gb), 256, 0, st>>>(n, A->col_ptr, flag.as<int32_t>(), pos.as<int64_t>(),
+                                          nkeep.as<int64_t>(), cntA.as<int64_t>(), cntU.as<int64_t>());
     SAI_TRY(h->At_cp.alloc(sizeof(int64_t) * (size_t)(n + 1), st, async));
     SAI_TRY(h->U_cp.alloc(sizeof(int64_t) * (size_t)(s + 1), st, async));
     SAI_TRY(sai_scan_counts_i64(cntA.as<int64_t>(), h->At_cp.as<int64_t>(), n, st));
@@ -213,7 +334,8 @@ sai_status sai_split_build(const sai_csc_view* A, const sai_split_params* prm, c
     if (n > 0)
         k_copy_split<<<SAI_GRID(sai_div_up((int64_t)n * 32, 256)), 256, 0, st>>>(
             n, A->col_ptr, A->row_idx, A->val, flag.as<int32_t>(), pos.as<int64_t>(), w0.as<int64_t>(),
-            w1.as<int64_t>(), h->At_cp.as<int64_t>(), h->At_ri.as<int32_t>(), h->At_v.as<double>(),
+            w1.as<int64_t>(), largest ? kflag.as<uint8_t>() : nullptr, h->At_cp.as<int64_t>(), h->At_ri.as<int32_t>(),
+            h->At_v.as<double>(),
             h->U_cp.as<int64_t>(), h->U_ri.as<int32_t>(), h->U_v.as<double>());
     SAI_CUDA(cudaGetLastError());
     SAI_TRY(sai_csc_to_csr(n, n, h->nnz_At, h->At_cp.as<int64_t>(), h->At_ri.as<int32_t>(), h->At_v.as<double>(),

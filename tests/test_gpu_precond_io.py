@@ -1,8 +1,8 @@
 """Saving M and loading it again for later right-hand sides (sai_precond_create).
 
 M built once, written to a file, read back as a new handle: the loaded M is
-the same CSC bit for bit, and Procedure * steps 3-5 with it give the same x,
-iteration counts and rr as with the built handle. Malformed CSC input is
+the same CSC bit for bit, and Procedure * steps 3-5 with it give the same x
+and iteration counts as with the built handle (rr to its atomic-sum noise). Malformed CSC input is
 refused with SAI_INVALID_ARG.
 """
 import numpy as np
@@ -38,7 +38,9 @@ def test_saved_m_solves_like_the_built_one(kind, tmp_path):
     for rhs in (P.b, rng.standard_normal(P.n)):
         x1, it1, r1 = sai.solve_with(dA, sp_, Pc, _dev(rhs), eps=1e-8)
         x2, it2, r2 = sai.solve_with(dA, sp_, Pl, _dev(rhs), eps=1e-8)
-        assert it1 == it2 and torch.equal(x1, x2) and r1["rr"] == r2["rr"] and r1["rr"] < 1e-8
+        # rr sums A x with atomics (its last bits vary between runs); x is the same bits
+        assert it1 == it2 and torch.equal(x1, x2) and r1["rr"] < 1e-8
+        assert r2["rr"] == pytest.approx(r1["rr"], rel=1e-9)
 
 
 def test_malformed_m_is_refused():

@@ -539,3 +539,68 @@ def test_zipf_workload_structure():
     assert np.all(np.abs(d) > 1.19 * off)
     J, p, tau = O.detect(A, abs_tau=200.0)
     assert tau == 200.0 and len(J) == int((cnt > 200).sum()) and len(J) > 10
+
+
+# ---- the largest-magnitude split rule (section 4, the second approach) ----
+def _col(M, j):
+    M = sp.csc_matrix(M)
+    return dict(zip(M.indices[M.indptr[j]:M.indptr[j + 1]].tolist(), M.data[M.indptr[j]:M.indptr[j + 1]].tolist()))
+
+
+def test_split_largest_hand_worked():
+    """Column 2 of an 8 x 8 matrix holds 10 (diagonal), -3, 4, 2, -2, 0.5,
+    -0.5, 0.1; p_keep = 3 keeps the diagonal and the two largest: rows 1
+    (-3) and 6 (4). The nearest rule keeps rows 1 and 3 instead."""
+    n = 8
+    A = sp.lil_matrix((n, n))
+    for i in range(n):
+        A[i, i] = 1.0
+    for r, v in zip(range(8), [0.5, -3.0, 10.0, 2.0, -2.0, 0.1, 4.0, -0.5]):
+        A[r, 2] = v
+    A = sp.csc_matrix(A)
+    At, U = O.split(A, [2], 3, rule=1)
+    assert _col(At, 2) == {1: -3.0, 2: 10.0, 6: 4.0}
+    assert _col(U, 0) == {0: 0.5, 3: 2.0, 4: -2.0, 5: 0.1, 7: -0.5}
+    At0, _ = O.split(A, [2], 3, rule=0)
+    assert _col(At0, 2) == {1: -3.0, 2: 10.0, 3: 2.0}
+
+
+def test_split_largest_ties_and_no_diagonal():
+    """Equal magnitudes go to the smaller row; without a stored diagonal the
+    p_keep largest are kept."""
+    n = 10
+    A = sp.lil_matrix((n, n))
+    for i in range(n):
+        A[i, i] = 2.0
+    for r in (0, 3, 5, 8, 9):  # column 4: five entries of magnitude 1, one of 5
+        A[r, 4] = -1.0 if r % 2 else 1.0
+    A[1, 4] = 5.0
+    A = sp.csc_matrix(A)
+    At, _ = O.split(A, [4], 4, rule=1)
+    assert sorted(_col(At, 4)) == [0, 1, 3, 4]  # diagonal, the 5, then the two smallest rows of the ties
+    B = sp.lil_matrix(A)
+    B[4, 4] = 0.0
+    B = sp.csc_matrix(B)
+    B.eliminate_zeros()
+    Bt, _ = O.split(B, [4], 3, rule=1)
+    assert sorted(_col(Bt, 4)) == [0, 1, 3]
+
+
+def test_split_largest_brute_force():
+    """Random column-dominant matrices with dense columns: the kept entries of
+    every irregular column equal the diagonal plus the first p-1 off-diagonal
+    entries sorted by (-|a_ij|, i); A = A~ + U V^T exactly."""
+    for trial in range(4):
+        A = _dominant(300, 5, seed=trial, s=4, dense_nnz=60)
+        A = sp.csc_matrix(A)
+        J, p, _ = O.detect(A)
+        At, U = O.split(A, J, p, rule=1)
+        At, U = sp.csc_matrix(At), sp.csc_matrix(U)
+        for t, j in enumerate(J):
+            c = _col(A, j)
+            off = sorted(((-abs(v), i) for i, v in c.items() if i != j))
+            want = {i for _, i in off[:p - 1]} | ({j} if j in c else set())
+            assert set(_col(At, j)) == want
+            assert set(_col(U, t)) == set(c) - want
+        V = sp.csc_matrix((np.ones(len(J)), (np.asarray(J), np.arange(len(J)))), shape=(A.shape[0], len(J)))
+        assert abs(At + U @ V.T - A).max() == 0.0
