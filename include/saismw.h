@@ -138,8 +138,9 @@ typedef struct {
 
 /* PSAI(tol) (section 2.2). Loop l = 0..lmax: solve on S^(l), drop
  * |m_jk| <= tol_k with tol_k = delta/(nnz(m_k) ||A~||_1) (tol_mode 0,
- * eq. (tolk)) or tol_k = tol (tol_mode 1); stop when the pre-drop residual
- * <= delta or l = lmax and emit the kept entries of that solution; else
+ * eq. (tolk)) or tol_k = tol (tol_mode 1), or keep only the lfill largest
+ * (tol_mode 2, PSAI(lfill)); stop when the pre-drop residual <= delta or
+ * l = lmax and emit the kept entries of that solution; else
  * S^(l+1) = P(|A~| a^(l)) u S_kept^(l) with a^(0) = e_k. */
 typedef struct {
     double delta;      /* paper: 0.4 */
@@ -147,6 +148,9 @@ typedef struct {
     int32_t tol_mode;
     int32_t lmax;      /* paper: 10 */
     int32_t precision; /* as for SPAI; the drop test uses the refined solution */
+    int32_t lfill;     /* tol_mode 2 only: PSAI(lfill) keeps the lfill entries of
+                          largest magnitude of each newly computed m_k (equal
+                          magnitudes to the smaller column index), >= 1 */
 } sai_psai_params;
 
 typedef struct sai_precond_s* sai_precond;

@@ -97,6 +97,8 @@ typedef struct {
     int32_t tol_mode;  /* 0: tol_k = delta/(nnz(m_k) ||A~||_1), eq. (tolk);  */
                        /* 1: tol_k = tol                                    */
     int32_t lmax;      /* loops l = 0..lmax                                 */
+    int32_t lfill;     /* tol_mode 2, PSAI(lfill): keep the lfill entries of */
+                       /* largest magnitude (ties to the smaller index)      */
 } orc_psai_params;
 
 /* Builds columns [c0,c1) of M. loops_out[k] = last loop index l used,

@@ -1,6 +1,8 @@
 /* oracle_sai.c -- the two F-norm-minimisation SAI builders of section 2:
  *   SPAI      (section 2.1, eqs. (candi), (ls1d), (muj), (rhoj)),
- *   PSAI(tol) (section 2.2, power pattern growth and eq. (tolk)).
+ *   PSAI(tol) (section 2.2, power pattern growth and eq. (tolk)), and
+ *   PSAI(lfill), which keeps the lfill largest entries instead (section 2.2
+ *   names it).
  * Both solve min ||A~ m_k - e_k|| column by column, eq. (subprob), through the
  * reduced problem min ||A^_k m^_k - e^_k||, eq. (lsprob), by Householder QR.
  * The reduced problem is rebuilt and refactored from scratch at every loop;
@@ -363,13 +365,26 @@ static int psai_column(sai_ws* w, const orc_psai_params* prm, int32_t k, char* k
             S_off[l + 1] = used;
             res_hist[l] = rn;
         }
-        double tolk = prm->tol;
-        if (prm->tol_mode == 0) {
-            int32_t nz = 0;
-            for (int32_t t = 0; t < w->nS; ++t) nz += (w->m[t] != 0.0);
-            tolk = (nz > 0 && w->norm1 > 0.0) ? prm->delta / ((double)nz * w->norm1) : 0.0;
+        if (prm->tol_mode == 2) {
+            /* PSAI(lfill): keep the lfill entries of largest magnitude, equal
+             * magnitudes to the smaller column index (counted one by one) */
+            for (int32_t t = 0; t < w->nS; ++t) {
+                int32_t rank = 0;
+                for (int32_t u = 0; u < w->nS; ++u) {
+                    const double mu = fabs(w->m[u]), mt = fabs(w->m[t]);
+                    if (mu > mt || (mu == mt && w->S[u] < w->S[t])) ++rank;
+                }
+                keep[t] = (char)(rank < prm->lfill);
+            }
+        } else {
+            double tolk = prm->tol;
+            if (prm->tol_mode == 0) {
+                int32_t nz = 0;
+                for (int32_t t = 0; t < w->nS; ++t) nz += (w->m[t] != 0.0);
+                tolk = (nz > 0 && w->norm1 > 0.0) ? prm->delta / ((double)nz * w->norm1) : 0.0;
+            }
+            for (int32_t t = 0; t < w->nS; ++t) keep[t] = (char)(fabs(w->m[t]) > tolk);
         }
-        for (int32_t t = 0; t < w->nS; ++t) keep[t] = (char)(fabs(w->m[t]) > tolk);
         if (rn <= prm->delta || l >= prm->lmax) {
             /* residual of the emitted (dropped) column, on L */
             double* r2 = (double*)orc_xcalloc((size_t)w->nL, sizeof(double));
@@ -426,8 +441,8 @@ static int psai_column(sai_ws* w, const orc_psai_params* prm, int32_t k, char* k
 int orc_psai(const orc_csc* At, const orc_psai_params* prm, int32_t c0, int32_t c1,
              orc_csc* M_out, int32_t* loops_out, double* res_pre, double* res_post)
 {
-    if (!orc_csc_valid(At) || At->nrows != At->ncols || !prm || prm->lmax < 0 ||
-        (prm->tol_mode != 0 && prm->tol_mode != 1))
+    if (!orc_csc_valid(At) || At->nrows != At->ncols || !prm || prm->lmax < 0 || prm->tol_mode < 0 ||
+        prm->tol_mode > 2 || (prm->tol_mode == 2 && prm->lfill < 1))
         return ORC_BAD_INPUT;
     int32_t n = At->ncols;
     if (c0 < 0) c0 = 0;

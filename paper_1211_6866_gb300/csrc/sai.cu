@@ -64,6 +64,7 @@ struct SpaiArgs {
 struct PsaiArgs {
     double delta, tol;
     int tol_mode, lmax;
+    int lfill;  // tol_mode 2
 };
 
 struct Out {
@@ -578,8 +579,23 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             nz = warp_sum_int(nz);
             tolk = (nz > 0 && A.norm1 > 0.0) ? a.delta / ((double)nz * A.norm1) : 0.0;
         }
-        // keep flags: kp[t] = |m_t| > tol_k
-        for (int t = lane; t < nS; t += 32) w.kp[t] = (uint8_t)(fabs(w.m[t]) > tolk);
+        if (a.tol_mode == 2) {
+            // PSAI(lfill): kp[t] = m_t is among the lfill largest in magnitude
+            // (equal magnitudes to the smaller column index)
+            for (int t = lane; t < nS; t += 32) {
+                const double mt = fabs(w.m[t]);
+                const int32_t jt = w.S[t];
+                int rank = 0;
+                for (int u = 0; u < nS; ++u) {
+                    const double mu = fabs(w.m[u]);
+                    rank += (mu > mt) || (mu == mt && w.S[u] < jt);
+                }
+                w.kp[t] = (uint8_t)(rank < a.lfill);
+            }
+        } else {
+            // keep flags: kp[t] = |m_t| > tol_k
+            for (int t = lane; t < nS; t += 32) w.kp[t] = (uint8_t)(fabs(w.m[t]) > tolk);
+        }
         __syncwarp();
         if (rn <= a.delta || l >= a.lmax) {
             rn_pre = rn;
@@ -1054,7 +1070,8 @@ sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cuda
                           sai_precond_s* P)
 {
     if (!h || !prm || !P) return SAI_INVALID_ARG;
-    if (prm->lmax < 0 || (prm->tol_mode != 0 && prm->tol_mode != 1) || !(prm->delta >= 0.0) || !(prm->tol >= 0.0))
+    if (prm->lmax < 0 || prm->tol_mode < 0 || prm->tol_mode > 2 || !(prm->delta >= 0.0) || !(prm->tol >= 0.0) ||
+        (prm->tol_mode == 2 && prm->lfill < 1))
         return SAI_INVALID_ARG;
     if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     SpaiArgs sa = {};
@@ -1063,6 +1080,7 @@ sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cuda
     pa.tol = prm->tol;
     pa.tol_mode = prm->tol_mode;
     pa.lmax = prm->lmax;
+    pa.lfill = prm->lfill;
     if (prm->precision == SAI_FP32_REFINE64)
         return build_common<true, float>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
     return build_common<true, double>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
@@ -1100,7 +1118,7 @@ sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_s
     if (sai == 0 && (sp->mn < 1 || sp->mn > MNMAX || sp->max_aug < 0 || sp->key_bits < 1 || sp->key_bits > 31 ||
                      !(sp->delta >= 0.0) || (sp->precision != SAI_FP64 && sp->precision != SAI_FP32_REFINE64)))
         return SAI_INVALID_ARG;
-    if (sai == 1 && (pp->lmax < 0 || (pp->tol_mode != 0 && pp->tol_mode != 1) || !(pp->delta >= 0.0) ||
+    if (sai == 1 && (pp->lmax < 0 || pp->tol_mode < 0 || pp->tol_mode > 2 || (pp->tol_mode == 2 && pp->lfill < 1) || !(pp->delta >= 0.0) ||
                      !(pp->tol >= 0.0) || (pp->precision != SAI_FP64 && pp->precision != SAI_FP32_REFINE64)))
         return SAI_INVALID_ARG;
     if (g_num_sms == 0) {
@@ -1138,6 +1156,7 @@ sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_s
         pa.tol = pp->tol;
         pa.tol_mode = pp->tol_mode;
         pa.lmax = pp->lmax;
+        pa.lfill = pp->lfill;
         delta = pp->delta;
         f32 = pp->precision == SAI_FP32_REFINE64;
     }

@@ -604,3 +604,44 @@ def test_split_largest_brute_force():
             assert set(_col(U, t)) == set(c) - want
         V = sp.csc_matrix((np.ones(len(J)), (np.asarray(J), np.arange(len(J)))), shape=(A.shape[0], len(J)))
         assert abs(At + U @ V.T - A).max() == 0.0
+
+
+# ---- PSAI(lfill): the lfill largest entries of each m_k (section 2.2) ----
+def test_psai_lfill_large_equals_no_drop():
+    """With lfill beyond any pattern size nothing is dropped: the same M as a
+    fixed tol of 0."""
+    At = W.convdiff2d_irregular(m=16, s=0).A
+    M1 = sp.csc_matrix(O.psai(At, 0.2, 0.0, 1, 3)[0])
+    M2 = sp.csc_matrix(O.psai(At, 0.2, tol_mode=2, lmax=3, lfill=10 ** 6)[0])
+    assert np.array_equal(M1.indptr, M2.indptr) and np.array_equal(M1.indices, M2.indices)
+    assert np.array_equal(M1.data, M2.data)
+
+
+def test_psai_lfill_diagonal_and_count():
+    d = np.arange(1.0, 21.0)
+    Md = sp.csc_matrix(O.psai(sp.diags(d).tocsc(), 0.1, tol_mode=2, lmax=4, lfill=1)[0])
+    assert np.allclose(Md.toarray(), np.diag(1.0 / d), rtol=0, atol=1e-15)
+    At = W.convdiff2d_irregular(m=16, s=0).A
+    M = sp.csc_matrix(O.psai(At, 0.05, tol_mode=2, lmax=3, lfill=4)[0])
+    assert np.diff(M.indptr).max() <= 4
+
+
+def test_psai_lfill_brute_force():
+    """Each emitted column equals the lfill entries of largest magnitude
+    (ties to the smaller index) of the dense least-squares solution on the
+    last loop's pattern."""
+    At = sp.csc_matrix(W.convdiff2d_irregular(m=16, s=0).A)
+    n = At.shape[0]
+    M = sp.csc_matrix(O.psai(At, 0.05, tol_mode=2, lmax=3, lfill=6)[0])
+    A = At.toarray()
+    for k in range(0, n, 17):
+        pats, _ = O.psai_trace(At, k, 0.05, tol_mode=2, lmax=3, lfill=6)
+        S = np.asarray(pats[-1])
+        e = np.zeros(n)
+        e[k] = 1.0
+        m = np.linalg.lstsq(A[:, S], e, rcond=None)[0]
+        order = sorted(range(len(S)), key=lambda t: (-abs(m[t]), S[t]))[:6]
+        want = {int(S[t]): m[t] for t in order}
+        got = dict(zip(M.indices[M.indptr[k]:M.indptr[k + 1]].tolist(), M.data[M.indptr[k]:M.indptr[k + 1]].tolist()))
+        assert set(got) == set(want), k
+        assert all(abs(got[j] - want[j]) <= 1e-10 * max(abs(v) for v in want.values()) for j in want)
