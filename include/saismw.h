@@ -151,6 +151,12 @@ typedef struct {
     int32_t lfill;     /* tol_mode 2 only: PSAI(lfill) keeps the lfill entries of
                           largest magnitude of each newly computed m_k (equal
                           magnitudes to the smaller column index), >= 1 */
+    int32_t growth;    /* 0: S^(l+1) = P(a^(l+1)) u S_kept^(l) (reading A, the
+                          default); 1: S^(l+1) = S_kept^(l) u (P(a^(l+1)) \ P(a^(l))),
+                          dropped positions never return (reading C); a column
+                          whose next pattern would be empty stops and emits its
+                          (empty) kept set. Other values: SAI_INVALID_ARG. */
+    int32_t reserved;  /* 0 */
 } sai_psai_params;
 
 typedef struct sai_precond_s* sai_precond;

@@ -33,7 +33,7 @@ class _SpaiParams(C.Structure):
 
 class _PsaiParams(C.Structure):
     _fields_ = [("delta", C.c_double), ("tol", C.c_double), ("tol_mode", C.c_int32), ("lmax", C.c_int32),
-                ("lfill", C.c_int32)]
+                ("lfill", C.c_int32), ("growth", C.c_int32)]
 
 
 class _SolveParams(C.Structure):
@@ -177,12 +177,13 @@ def spai_trace(At, k, delta, mn=5, max_aug=10, key_bits=20, cap=1 << 20):
     return _trace(lib().orc_spai_trace, At, _SpaiParams(delta, mn, max_aug, key_bits), k, cap)
 
 
-def psai(At, delta, tol=0.0, tol_mode=0, lmax=10, cols=None, lfill=0):
-    """Returns (M csc, loops[n], res_pre[n], res_post[n]). tol_mode 2: PSAI(lfill)."""
+def psai(At, delta, tol=0.0, tol_mode=0, lmax=10, cols=None, lfill=0, growth=0):
+    """Returns (M csc, loops[n], res_pre[n], res_post[n]). tol_mode 2: PSAI(lfill);
+    growth 1: pattern growth reading (C)."""
     a = _In(At)
     n = a.shape[1]
     c0, c1 = _cols(n, cols)
-    prm = _PsaiParams(delta, tol, tol_mode, lmax, lfill)
+    prm = _PsaiParams(delta, tol, tol_mode, lmax, lfill, growth)
     loops = np.zeros(max(n, 1), np.int32)
     pre = np.zeros(max(n, 1), np.float64)
     post = np.zeros(max(n, 1), np.float64)
@@ -192,8 +193,8 @@ def psai(At, delta, tol=0.0, tol_mode=0, lmax=10, cols=None, lfill=0):
     return _take(M), loops[:n], pre[:n], post[:n]
 
 
-def psai_trace(At, k, delta, tol=0.0, tol_mode=0, lmax=10, cap=1 << 22, lfill=0):
-    return _trace(lib().orc_psai_trace, At, _PsaiParams(delta, tol, tol_mode, lmax, lfill), k, cap)
+def psai_trace(At, k, delta, tol=0.0, tol_mode=0, lmax=10, cap=1 << 22, lfill=0, growth=0):
+    return _trace(lib().orc_psai_trace, At, _PsaiParams(delta, tol, tol_mode, lmax, lfill, growth), k, cap)
 
 
 def bicgstab(At, M, rhs, thr, maxit=500):

@@ -99,6 +99,8 @@ typedef struct {
     int32_t lmax;      /* loops l = 0..lmax                                 */
     int32_t lfill;     /* tol_mode 2, PSAI(lfill): keep the lfill entries of */
                        /* largest magnitude (ties to the smaller index)      */
+    int32_t growth;    /* 0: S' = P(a^(l+1)) u S_kept (reading A);          */
+                       /* 1: S' = S_kept u (P(a^(l+1)) \ P(a^(l))) (reading C) */
 } orc_psai_params;
 
 /* Builds columns [c0,c1) of M. loops_out[k] = last loop index l used,

@@ -415,6 +415,45 @@ static int psai_column(sai_ws* w, const orc_psai_params* prm, int32_t k, char* k
             }
         }
         for (int32_t t = 0; t < nb; ++t) w->colmark[w->tmp[t]] = -1;
+        if (prm->growth == 1) {
+            /* reading (C): S^(l+1) = S_kept^(l) u (P(a^(l+1)) \ P(a^(l))),
+             * ascending; a dropped position never comes back */
+            char* old_pat = (char*)orc_xcalloc((size_t)n, 1);
+            char* in_next = (char*)orc_xcalloc((size_t)n, 1);
+            int32_t* next = (int32_t*)orc_xmalloc(((size_t)w->nS + (size_t)nb + 1) * sizeof(int32_t));
+            int32_t ns = 0;
+            for (int32_t t = 0; t < na; ++t) old_pat[apat[t]] = 1;
+            for (int32_t t = 0; t < w->nS; ++t)
+                if (keep[t] && !in_next[w->S[t]]) {
+                    in_next[w->S[t]] = 1;
+                    next[ns++] = w->S[t];
+                }
+            for (int32_t t = 0; t < nb; ++t) {
+                const int32_t i = w->tmp[t];
+                if (!old_pat[i] && !in_next[i]) {
+                    in_next[i] = 1;
+                    next[ns++] = i;
+                }
+            }
+            free(old_pat);
+            free(in_next);
+            if (ns == 0) {
+                /* nothing kept and no new position: stop at loop l, emitting
+                 * the (empty) kept set of this solution */
+                free(next);
+                *res_post = 1.0; /* the emitted column is empty: ||0 - e_k|| */
+                *res_pre = rn;
+                *loops = l;
+                break;
+            }
+            memcpy(apat, w->tmp, (size_t)nb * sizeof(int32_t));
+            na = nb;
+            qsort(next, (size_t)ns, sizeof(int32_t), cmp_i32);
+            memcpy(w->S, next, (size_t)ns * sizeof(int32_t));
+            w->nS = ns;
+            free(next);
+            continue;
+        }
         memcpy(apat, w->tmp, (size_t)nb * sizeof(int32_t));
         na = nb;
         /* S^(l+1) = P(a^(l+1)) u S_kept^(l), ascending */
@@ -442,7 +481,7 @@ int orc_psai(const orc_csc* At, const orc_psai_params* prm, int32_t c0, int32_t 
              orc_csc* M_out, int32_t* loops_out, double* res_pre, double* res_post)
 {
     if (!orc_csc_valid(At) || At->nrows != At->ncols || !prm || prm->lmax < 0 || prm->tol_mode < 0 ||
-        prm->tol_mode > 2 || (prm->tol_mode == 2 && prm->lfill < 1))
+        prm->tol_mode > 2 || (prm->tol_mode == 2 && prm->lfill < 1) || (prm->growth != 0 && prm->growth != 1))
         return ORC_BAD_INPUT;
     int32_t n = At->ncols;
     if (c0 < 0) c0 = 0;

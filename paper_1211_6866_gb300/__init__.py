@@ -46,6 +46,7 @@ class _SplitParams(C.Structure):
 
 
 _KEEP = {"nearest": 0, "largest": 1}
+_GROWTH = {"A": 0, "C": 1}
 
 
 class _SplitInfo(C.Structure):
@@ -60,7 +61,7 @@ class _SpaiParams(C.Structure):
 
 class _PsaiParams(C.Structure):
     _fields_ = [("delta", C.c_double), ("tol", C.c_double), ("tol_mode", C.c_int32), ("lmax", C.c_int32),
-                ("precision", C.c_int32), ("lfill", C.c_int32)]
+                ("precision", C.c_int32), ("lfill", C.c_int32), ("growth", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _PrecondInfo(C.Structure):
@@ -303,13 +304,13 @@ def _cfg_dict(c):
 
 
 def build_autotune(sp, sai="spai", delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10,
-                   precision=0, lfill=0):
+                   precision=0, lfill=0, growth="A"):
     """Times the build schedule candidates on a sample of sp's columns and makes
     the fastest the configuration of later builds. Returns (chosen, candidates)."""
     L = load()
     t = _BuildTuning()
     sprm = _SpaiParams(delta, mn, max_aug, key_bits, precision)
-    pprm = _PsaiParams(delta, tol, tol_mode, lmax, precision, lfill)
+    pprm = _PsaiParams(delta, tol, tol_mode, lmax, precision, lfill, _GROWTH[growth], 0)
     _check("sai_build_autotune", L.sai_build_autotune(sp._h, 0 if sai == "spai" else 1, C.byref(sprm), C.byref(pprm),
                                                       _stream(), C.byref(t)))
     return _cfg_dict(t.chosen), [_cfg_dict(t.cand[i]) for i in range(t.ncand)]
@@ -325,12 +326,14 @@ def build_set_config(warps_t0=None, blocks_per_sm_t12=2, heavy_first=0):
         _check("sai_build_set_config", L.sai_build_set_config(C.byref(c)))
 
 
-def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10, precision=0, lfill=0):
+def build_psai(sp, delta=0.4, tol=0.0, tol_mode=0, lmax=10, precision=0, lfill=0, growth="A"):
     """precision 1: FP32 QR with one FP64 refinement step per loop; tol_mode 2
-    with lfill: PSAI(lfill), the lfill largest entries of each m_k kept."""
+    with lfill: PSAI(lfill), the lfill largest entries of each m_k kept;
+    growth "C": dropped positions never return (the pattern grows only by
+    the new positions of the power sequence)."""
     L = load()
     h = C.c_void_p()
-    prm = _PsaiParams(delta, tol, tol_mode, lmax, precision, lfill)
+    prm = _PsaiParams(delta, tol, tol_mode, lmax, precision, lfill, _GROWTH[growth], 0)
     _check("sai_build_psai", L.sai_build_psai(sp._h, C.byref(prm), _stream(), C.byref(h)))
     return Precond(h.value)
 
@@ -403,7 +406,7 @@ def rel_resid(A, b, x):
 
 def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0, abs_tau=-1.0,
           delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, x=None, krylov_precision=0,
-          inner_tol=0.0, sai_precision=0, keep="nearest", lfill=0):
+          inner_tol=0.0, sai_precision=0, keep="nearest", lfill=0, growth="A"):
     """Procedure * on the device. krylov_precision=1 selects the FP32-inner /
     FP64-refined GMRES; sai_precision=1 the FP32 QR + FP64 refinement build.
     Returns (x, iters list, report dict)."""
@@ -412,7 +415,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
         x = torch.empty(A.n, dtype=torch.float64, device=b.device)
     prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
-                       _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill),
+                       _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill, _GROWTH[growth], 0),
                        _KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit, krylov_precision,
                                      inner_tol, 0), eps)
     cap = A.n + 1
@@ -511,7 +514,8 @@ class SparseSolve(torch.autograd.Function):
 
 
 def solve_batched(As, bs, sai="spai", eps=1e-8, maxit=500, thresh_mult=10.0, abs_tau=-1.0, delta=0.4, mn=5,
-                  max_aug=10, key_bits=20, tol=0.0, tol_mode=1, lmax=10, sai_precision=0, keep="nearest", lfill=0):
+                  max_aug=10, key_bits=20, tol=0.0, tol_mode=1, lmax=10, sai_precision=0, keep="nearest", lfill=0,
+                  growth="A"):
     """Procedure * for a batch of independent matrices (lists of CscMatrix and
     device b vectors): one SAI build over all their columns, one batched
     BiCGStab over all their s_i + 1 systems, SMW per matrix.
@@ -524,7 +528,7 @@ def solve_batched(As, bs, sai="spai", eps=1e-8, maxit=500, thresh_mult=10.0, abs
     xp = (C.c_void_p * nmat)(*[_p(x).value for x in xs])
     prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
-                       _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill),
+                       _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill, _GROWTH[growth], 0),
                        _KrylovParams(BICGSTAB, 50, maxit, 0, 0.0, 0), eps)
     items = (_BatchItem * nmat)()
     rep = _BatchReport()

@@ -64,7 +64,8 @@ struct SpaiArgs {
 struct PsaiArgs {
     double delta, tol;
     int tol_mode, lmax;
-    int lfill;  // tol_mode 2
+    int lfill;   // tol_mode 2
+    int growth;  // 0: reading (A); 1: reading (C), dropped positions stay dropped
 };
 
 struct Out {
@@ -617,6 +618,96 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             nL_out = nL;
             return ST_DONE;
         }
+        if (a.growth == 1) {
+            // reading (C): S^(l+1) = S_kept^(l) u (P(a^(l+1)) \ P(a^(l))), so a
+            // dropped position never comes back. Hash flags: 2 in P(a^(l)),
+            // 8 kept member of S^(l), 4 in P(a^(l+1)).
+            for (int q = lane; q < T::HC; q += 32) {
+                w.ck[q] = -1;
+                w.cf[q] = 0;
+            }
+            __syncwarp();
+            bool ovf = false;
+            for (int t = lane; t < na; t += 32) {
+                bool ins;
+                const int sl = hinsert<T::HC>(w.ck, apat[t], ins);
+                if (sl < 0) ovf = true;
+                else w.cf[sl] |= 2;
+            }
+            __syncwarp();
+            int nk = 0;
+            for (int t = lane; t < nS; t += 32) {
+                if (!w.kp[t]) continue;
+                ++nk;
+                bool ins;
+                const int sl = hinsert<T::HC>(w.ck, w.S[t], ins);
+                if (sl < 0) ovf = true;
+                else w.cf[sl] |= 8;
+            }
+            nk = warp_sum_int(nk);
+            __syncwarp();
+            for (int t = 0; t < na; ++t) {
+                const int32_t j = apat[t];
+                const int64_t b = A.cp[j], e = A.cp[j + 1];
+                for (int64_t q = b + lane; q < e; q += 32) {
+                    bool ins;
+                    const int sl = hinsert<T::HC>(w.ck, A.ri[q], ins);
+                    if (sl < 0) ovf = true;
+                    else w.cf[sl] |= 4;
+                }
+                __syncwarp();
+            }
+            if (__any_sync(SAI_FULL, ovf)) return ST_OVERFLOW;
+            const unsigned lt = (1u << lane) - 1u;
+            int nb = 0, nf = 0;
+            for (int s0 = 0; s0 < T::HC; s0 += 32) {
+                const int32_t key = w.ck[s0 + lane];
+                const uint8_t f = key >= 0 ? w.cf[s0 + lane] : (uint8_t)0;
+                const unsigned mn = __ballot_sync(SAI_FULL, (f & 4) != 0);
+                const unsigned mf = __ballot_sync(SAI_FULL, (f & 4) != 0 && (f & 10) == 0);
+                if (nb + __popc(mn) > T::SCAP) return ST_OVERFLOW;
+                if (f & 4) anew[nb + __popc(mn & lt)] = key;
+                nb += __popc(mn);
+                nf += __popc(mf);
+            }
+            __syncwarp();
+            if (nk + nf == 0) {
+                // nothing kept and no new position: the column stops at loop l
+                rn_pre = rn;
+                rn_post = sqrt(residual<T>(w, A, nL, nS, w.kp));
+                fl += 2 * sn + 2LL * nL;
+                nS_out = 0;
+                l_out = l;
+                nL_out = nL;
+                return ST_DONE;
+            }
+            if (nk + nf > T::SCAP) return ST_OVERFLOW;
+            const bool dropped = nk < nS;
+            if (dropped && lane == 0) {  // the kept members, in list order, to the front
+                int q = 0;
+                for (int t = 0; t < nS; ++t)
+                    if (w.kp[t]) w.S[q++] = w.S[t];
+            }
+            __syncwarp();
+            int q = nk;
+            for (int s0 = 0; s0 < T::HC; s0 += 32) {  // then the frontier, in slot order
+                const int32_t key = w.ck[s0 + lane];
+                const uint8_t f = key >= 0 ? w.cf[s0 + lane] : (uint8_t)0;
+                const bool fr = (f & 4) != 0 && (f & 10) == 0;
+                const unsigned mf = __ballot_sync(SAI_FULL, fr);
+                if (fr) w.S[q + __popc(mf & lt)] = key;
+                q += __popc(mf);
+            }
+            __syncwarp();
+            if (dropped) col_init<T>(w, k, nL, nS, nfact);  // refactor from scratch on the new pattern
+            nS = q;
+            int32_t* sw = apat;
+            apat = anew;
+            anew = sw;
+            na = nb;
+            ++l;
+            continue;
+        }
         // a^(l+1): union of the column patterns of a^(l); positions in entry order
         for (int q = lane; q < T::HC; q += 32) {
             w.ck[q] = -1;
@@ -1071,7 +1162,7 @@ sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cuda
 {
     if (!h || !prm || !P) return SAI_INVALID_ARG;
     if (prm->lmax < 0 || prm->tol_mode < 0 || prm->tol_mode > 2 || !(prm->delta >= 0.0) || !(prm->tol >= 0.0) ||
-        (prm->tol_mode == 2 && prm->lfill < 1))
+        (prm->tol_mode == 2 && prm->lfill < 1) || (prm->growth != 0 && prm->growth != 1))
         return SAI_INVALID_ARG;
     if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     SpaiArgs sa = {};
@@ -1081,6 +1172,7 @@ sai_status sai_psai_build(const sai_split_s* h, const sai_psai_params* prm, cuda
     pa.tol_mode = prm->tol_mode;
     pa.lmax = prm->lmax;
     pa.lfill = prm->lfill;
+    pa.growth = prm->growth;
     if (prm->precision == SAI_FP32_REFINE64)
         return build_common<true, float>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
     return build_common<true, double>(h, sa, pa, Tier2::SCAP, prm->delta, st, async, P);
@@ -1118,7 +1210,8 @@ sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_s
     if (sai == 0 && (sp->mn < 1 || sp->mn > MNMAX || sp->max_aug < 0 || sp->key_bits < 1 || sp->key_bits > 31 ||
                      !(sp->delta >= 0.0) || (sp->precision != SAI_FP64 && sp->precision != SAI_FP32_REFINE64)))
         return SAI_INVALID_ARG;
-    if (sai == 1 && (pp->lmax < 0 || pp->tol_mode < 0 || pp->tol_mode > 2 || (pp->tol_mode == 2 && pp->lfill < 1) || !(pp->delta >= 0.0) ||
+    if (sai == 1 && (pp->lmax < 0 || pp->tol_mode < 0 || pp->tol_mode > 2 || (pp->tol_mode == 2 && pp->lfill < 1) ||
+                     (pp->growth != 0 && pp->growth != 1) || !(pp->delta >= 0.0) ||
                      !(pp->tol >= 0.0) || (pp->precision != SAI_FP64 && pp->precision != SAI_FP32_REFINE64)))
         return SAI_INVALID_ARG;
     if (g_num_sms == 0) {
@@ -1157,6 +1250,7 @@ sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_s
         pa.tol_mode = pp->tol_mode;
         pa.lmax = pp->lmax;
         pa.lfill = pp->lfill;
+        pa.growth = pp->growth;
         delta = pp->delta;
         f32 = pp->precision == SAI_FP32_REFINE64;
     }

@@ -645,3 +645,50 @@ def test_psai_lfill_brute_force():
         got = dict(zip(M.indices[M.indptr[k]:M.indptr[k + 1]].tolist(), M.data[M.indptr[k]:M.indptr[k + 1]].tolist()))
         assert set(got) == set(want), k
         assert all(abs(got[j] - want[j]) <= 1e-10 * max(abs(v) for v in want.values()) for j in want)
+
+
+# ---- PSAI growth reading (C): dropped positions never return (section 2.2) ----
+def _power_patterns(At, k, L):
+    """P(a^(l)) for l = 0..L, a^(0) = e_k, a^(l+1) = |A~| a^(l) (structural)."""
+    B = abs(sp.csc_matrix(At)).astype(bool).astype(np.int64)
+    a = np.zeros(At.shape[0], dtype=np.int64)
+    a[k] = 1
+    pats = [set([k])]
+    for _ in range(L):
+        a = (B @ a > 0).astype(np.int64)
+        pats.append(set(np.flatnonzero(a).tolist()))
+    return pats
+
+
+def test_psai_growth_c_brute_force():
+    """Traced patterns of sampled columns: S^(l) inside P(a^(l)); a position
+    that leaves S never returns; and S^(l+1) = {j in S^(l): |m_j| > tol} u
+    (P(a^(l+1)) minus P(a^(l))) with m the dense least-squares solution on S^(l)."""
+    At = sp.csc_matrix(W.convdiff2d_irregular(m=16, s=0).A)
+    A = At.toarray()
+    n, tol, lmax = At.shape[0], 2e-3, 4
+    for k in range(0, n, 23):
+        pats, _ = O.psai_trace(At, k, 0.0, tol, 1, lmax, growth=1)
+        P = _power_patterns(At, k, len(pats))
+        gone = set()
+        for l, S in enumerate(pats):
+            S = [int(j) for j in S]
+            assert set(S) <= P[l], (k, l)
+            assert not (set(S) & gone), (k, l)
+            if l + 1 < len(pats):
+                e = np.zeros(n)
+                e[k] = 1.0
+                m = np.linalg.lstsq(A[:, S], e, rcond=None)[0]
+                kept = {j for j, v in zip(S, m) if abs(v) > tol}
+                assert set(int(j) for j in pats[l + 1]) == kept | (P[l + 1] - P[l]), (k, l)
+                gone |= set(S) - kept
+
+
+def test_psai_growth_c_differs_from_a_and_diagonal():
+    At = W.convdiff2d_irregular(m=16, s=0).A
+    Ma = sp.csc_matrix(O.psai(At, 0.05, 1e-3, 1, 4)[0])
+    Mc = sp.csc_matrix(O.psai(At, 0.05, 1e-3, 1, 4, growth=1)[0])
+    assert (Ma != Mc).nnz > 0 and Mc.nnz < Ma.nnz
+    d = np.arange(1.0, 21.0)
+    Md = sp.csc_matrix(O.psai(sp.diags(d).tocsc(), 0.1, 1e-3, 1, 4, growth=1)[0])
+    assert np.allclose(Md.toarray(), np.diag(1.0 / d), rtol=0, atol=1e-15)
