@@ -170,11 +170,36 @@ def site_roofline(name, s, peaks):
 TRAFFIC_MD = os.path.join(ROOT, "profiles", "traffic_convdiff3d64_bench_step.md")
 
 
+def source_digest(ref):
+    """sha256 prefix of a source: "path" (the whole file) or "path::kernel"
+    (the kernel's definition, from the line holding its __global__ to the
+    first closing brace at the start of a line)."""
+    path, _, kernel = ref.partition("::")
+    with open(os.path.join(ROOT, path), "rb") as f:
+        text = f.read()
+    if kernel:
+        at = -1
+        for pos in range(len(text)):
+            pos = text.find((kernel + "(").encode(), pos)
+            if pos < 0:
+                break
+            head = text.rfind(b"__global__", 0, pos)
+            if head >= 0 and text.rfind(b";", head, pos) < 0 and text.rfind(b"}", head, pos) < 0:
+                at = text.rfind(b"\n", 0, head) + 1
+                break
+            pos += 1
+        if at < 0:
+            raise ValueError("kernel not found: " + ref)
+        end = text.find(b"\n}\n", at)
+        text = text[at:end + 3]
+    return hashlib.sha256(text).hexdigest()[:16]
+
+
 def measured_traffic(site):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum,
     averaged over every launch of the site's kernel in one ncu capture of the
     timed step) from the committed summary, or None when there is none or the
-    kernel's source file has changed since (its sha256 prefix is recorded)."""
+    kernel's source has changed since (its sha256 prefix is recorded)."""
     try:
         with open(TRAFFIC_MD) as f:
             text = f.read()
@@ -185,9 +210,8 @@ def measured_traffic(site):
         if len(parts) < 6 or parts[0] != site:
             continue
         try:
-            with open(os.path.join(ROOT, parts[4]), "rb") as f:
-                if hashlib.sha256(f.read()).hexdigest()[:16] != parts[5]:
-                    return None
+            if source_digest(parts[4]) != parts[5]:
+                return None
             return float(parts[3])
         except (OSError, ValueError):
             return None
