@@ -124,6 +124,11 @@ int orc_bicgstab(const orc_csc* At, const orc_csc* M, const double* rhs, double 
 
 /* Restarted GMRES(m), modified Gram-Schmidt Arnoldi, Givens rotations,
  * stop on the Givens residual estimate < thr; *iters counts inner steps. */
+/* CGS on A~ M z = rhs returning y = M z; the recursive residual is tested
+ * after each iteration (two applications of A~ M). */
+int orc_cgs(const orc_csc* At, const orc_csc* M, const double* rhs, double thr, int32_t maxit, double* y,
+            int32_t* iters);
+
 int orc_gmres(const orc_csc* At, const orc_csc* M, const double* rhs, double thr,
               int32_t restart, int32_t maxit, double* y, int32_t* iters);
 
@@ -146,7 +151,7 @@ typedef struct {
     int32_t sai;          /* 0: SPAI, 1: PSAI(tol) */
     orc_spai_params spai;
     orc_psai_params psai;
-    int32_t krylov;       /* 0: BiCGStab, 1: GMRES(restart) */
+    int32_t krylov;       /* 0: BiCGStab, 1: GMRES(restart), 2: CGS */
     int32_t restart;
     int32_t maxit;
     double eps;

@@ -98,6 +98,92 @@ int orc_bicgstab(const orc_csc* At, const orc_csc* M, const double* rhs, double 
     return status;
 }
 
+
+/* CGS (Sonneveld's conjugate gradient squared) on A~ M z = rhs, returning
+ * y = M z directly: two applications of A~ M per iteration, the recursive
+ * residual tested after each iteration (section 5 names CGS among the other
+ * solvers tried). */
+int orc_cgs(const orc_csc* At, const orc_csc* M, const double* rhs, double thr, int32_t maxit, double* y,
+            int32_t* iters)
+{
+    int32_t n = At->ncols;
+    double* r = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* rh = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* u = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* p = (double*)orc_xcalloc((size_t)n, sizeof(double));
+    double* q = (double*)orc_xcalloc((size_t)n, sizeof(double));
+    double* ph = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* v = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* w = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* wh = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* qh = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    for (int32_t i = 0; i < n; ++i) {
+        y[i] = 0.0;
+        r[i] = rhs[i];
+        rh[i] = rhs[i];
+    }
+    int status = ORC_MAXITER;
+    int32_t it = 0;
+    double rho_prev = 1.0;
+    if (orc_norm2(n, r) < thr) {
+        status = ORC_OK;
+    } else {
+        for (it = 1; it <= maxit; ++it) {
+            double rho = orc_dot(n, rh, r);
+            if (rho == 0.0) {
+                status = ORC_BREAKDOWN;
+                break;
+            }
+            if (it == 1) {
+                memcpy(u, r, (size_t)n * sizeof(double));
+                memcpy(p, u, (size_t)n * sizeof(double));
+            } else {
+                double beta = rho / rho_prev;
+                for (int32_t i = 0; i < n; ++i) {
+                    u[i] = r[i] + beta * q[i];
+                    p[i] = u[i] + beta * (q[i] + beta * p[i]);
+                }
+            }
+            orc_csc_matvec(M, p, ph);
+            orc_csc_matvec(At, ph, v);
+            double sigma = orc_dot(n, rh, v);
+            if (sigma == 0.0) {
+                status = ORC_BREAKDOWN;
+                break;
+            }
+            double alpha = rho / sigma;
+            for (int32_t i = 0; i < n; ++i) {
+                q[i] = u[i] - alpha * v[i];
+                w[i] = u[i] + q[i];
+            }
+            orc_csc_matvec(M, w, wh);
+            orc_csc_matvec(At, wh, qh);
+            for (int32_t i = 0; i < n; ++i) {
+                y[i] += alpha * wh[i];
+                r[i] -= alpha * qh[i];
+            }
+            if (orc_norm2(n, r) < thr) {
+                status = ORC_OK;
+                break;
+            }
+            rho_prev = rho;
+        }
+        if (it > maxit) it = maxit;
+    }
+    *iters = it;
+    free(r);
+    free(rh);
+    free(u);
+    free(p);
+    free(q);
+    free(ph);
+    free(v);
+    free(w);
+    free(wh);
+    free(qh);
+    return status;
+}
+
 /* Restarted GMRES(m) on A~ M z = rhs, y = M z. Arnoldi by modified
  * Gram-Schmidt, least squares by Givens rotations; the cycle stops when the
  * rotated residual estimate |g_{j+1}| < thr; each restart recomputes the

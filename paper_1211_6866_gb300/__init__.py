@@ -24,7 +24,8 @@ _LIBPATH = os.path.join(_HERE, "libsaismw.so")
 
 SAI_OK, SAI_INVALID_ARG, SAI_CUDA_ERROR, SAI_OOM, SAI_PATTERN_OVERFLOW, SAI_MAXITER, SAI_BREAKDOWN, \
     SAI_SINGULAR, SAI_NOT_IMPLEMENTED = range(9)
-BICGSTAB, GMRES = 0, 1
+BICGSTAB, GMRES, CGS = 0, 1, 2
+_METHOD = {"bicgstab": BICGSTAB, "gmres": GMRES, "cgs": CGS}
 
 
 class SaiError(RuntimeError):
@@ -416,7 +417,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
     prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
                        _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill, _GROWTH[growth], 0),
-                       _KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit, krylov_precision,
+                       _KrylovParams(_METHOD[krylov], restart, maxit, krylov_precision,
                                      inner_tol, 0), eps)
     cap = A.n + 1
     iters = (C.c_int32 * cap)()
@@ -441,7 +442,7 @@ def _report(rep, st):
 
 
 def _stage(krylov, eps, maxit, restart, krylov_precision, inner_tol):
-    return _StageParams(_KrylovParams(BICGSTAB if krylov == "bicgstab" else GMRES, restart, maxit, krylov_precision,
+    return _StageParams(_KrylovParams(_METHOD[krylov], restart, maxit, krylov_precision,
                                       inner_tol, 0), eps)
 
 

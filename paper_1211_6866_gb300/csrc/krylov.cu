@@ -965,6 +965,244 @@ sai_status bicgstab_run(const Items& I, int k, const Ops<double>& A, const doubl
     return SAI_OK;
 }
 
+// ================================================================== CGS
+// Conjugate gradient squared (Sonneveld) on A~ M z = b with y = M z, one
+// system per entry of the list (section 5 names CGS among the other solvers
+// tried). Per iteration:
+//   rho = rhat^T r;  beta = rho / rho_old;  u = r + beta q;  p = u + beta (q + beta p)
+//   (u = p = r in the first iteration);  phat = M p;  v = A~ phat;
+//   alpha = rho / rhat^T v;  q = u - alpha v;  w = M (u + q);  y += alpha w;
+//   r -= alpha A~ w
+// and the recursive residual is tested after the iteration.
+__global__ void k_cgs_init(Items I, int k, const double* __restrict__ Bs, double* x, double* r, double* rh,
+                           double* q, double* p, const int* list, double* part)
+{
+    FOR_ITEMS(I, list, c, r0, r1)
+    {
+        double acc = 0.0;
+        const int64_t o = (int64_t)c * I.ld;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) {
+            const double b = Bs[o + i];
+            x[o + i] = 0.0;
+            r[o + i] = b;
+            rh[o + i] = b;
+            q[o + i] = 0.0;
+            p[o + i] = 0.0;
+            acc = fma(b, b, acc);
+        }
+        acc = warp_sum(acc);
+        if (lane_ == 0) part[pidx(0, c, q_, k, I.nch)] = acc;
+    }
+}
+
+// iteration start: count it, test rho, form beta
+__global__ void k_cgs_start(int k, int maxit, Sys S)
+{
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!S.active[c]) continue;
+        if (S.iters[c] >= maxit) {
+            S.active[c] = 0;
+            S.status[c] = ST_MAXITER;
+        } else {
+            S.iters[c] += 1;
+            if (S.rho[c] == 0.0) {
+                S.active[c] = 0;
+                S.status[c] = ST_BREAKDOWN;
+            } else {
+                S.beta[c] = S.iters[c] == 1 ? 0.0 : S.rho[c] / S.rho_old[c];
+            }
+        }
+    }
+    __syncthreads();
+    build_list_block(k, S.active, S.lact);
+}
+
+__global__ void k_cgs_up(Items I, const double* __restrict__ r, double* u, double* p, const double* __restrict__ q,
+                         Sys S)
+{
+    FOR_ITEMS(I, S.lact, c, r0, r1)
+    {
+        const double be = S.beta[c];
+        const bool first = S.iters[c] == 1;
+        const int64_t o = (int64_t)c * I.ld;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) {
+            const double uv = first ? r[o + i] : r[o + i] + be * q[o + i];
+            u[o + i] = uv;
+            p[o + i] = first ? uv : uv + be * (q[o + i] + be * p[o + i]);
+        }
+    }
+}
+
+__global__ void k_cgs_f1(int k, int nch, const double* part, Sys S, Dims D)
+{
+    const int k1 = S.lact[0];
+    if (threadIdx.x == 0 && k1 > 0) {
+        spmm_work(D, D.nnzM, k1);
+        spmm_work(D, D.nnzA, k1);
+        kwork_add(PROF_BICG_VEC, 8.0 * D.n * k1 * (5 + 2), D.n * k1 * (6 + 2));  // u, p updates, rhat^T v
+    }
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!S.active[c]) continue;
+        const double sg = sum_chunks(part, 0, c, k, nch);
+        if (sg == 0.0) {
+            S.active[c] = 0;
+            S.status[c] = ST_BREAKDOWN;
+        } else {
+            S.alpha[c] = S.rho[c] / sg;
+        }
+    }
+    __syncthreads();
+    build_list_block(k, S.active, S.lact);
+}
+
+__global__ void k_cgs_q(Items I, const double* __restrict__ u, const double* __restrict__ v, double* q, double* w,
+                        Sys S)
+{
+    FOR_ITEMS(I, S.lact, c, r0, r1)
+    {
+        const double al = S.alpha[c];
+        const int64_t o = (int64_t)c * I.ld;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) {
+            const double qv = u[o + i] - al * v[o + i];
+            q[o + i] = qv;
+            w[o + i] = u[o + i] + qv;
+        }
+    }
+}
+
+__global__ void k_cgs_xr(Items I, int k, double* x, double* r, const double* __restrict__ rh,
+                         const double* __restrict__ wh, const double* __restrict__ qh, Sys S, double* part)
+{
+    FOR_ITEMS(I, S.lact, c, r0, r1)
+    {
+        const double al = S.alpha[c];
+        double a0 = 0.0, a1 = 0.0;
+        const int64_t o = (int64_t)c * I.ld;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) {
+            x[o + i] += al * wh[o + i];
+            const double rv = r[o + i] - al * qh[o + i];
+            r[o + i] = rv;
+            a0 = fma(rv, rv, a0);
+            a1 = fma(rh[o + i], rv, a1);
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane_ == 0) {
+            part[pidx(0, c, q_, k, I.nch)] = a0;
+            part[pidx(1, c, q_, k, I.nch)] = a1;
+        }
+    }
+}
+
+__global__ void k_cgs_f2(int k, int nch, const double* part, Sys S, Dims D, int* any_active)
+{
+    const int k2 = S.lact[0];
+    if (threadIdx.x == 0 && k2 > 0) {
+        spmm_work(D, D.nnzM, k2);
+        spmm_work(D, D.nnzA, k2);
+        kwork_add(PROF_BICG_VEC, 8.0 * D.n * k2 * (4 + 6), D.n * k2 * (3 + 8));  // q, w; x, r, two dots
+    }
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (!S.active[c]) continue;
+        const double rr = sum_chunks(part, 0, c, k, nch), rhr = sum_chunks(part, 1, c, k, nch);
+        if (sqrt(rr) < S.thr[c]) {
+            S.active[c] = 0;
+            S.status[c] = ST_OK;
+        } else {
+            S.rho_old[c] = S.rho[c];
+            S.rho[c] = rhr;
+        }
+    }
+    __syncthreads();
+    build_list_block(k, S.active, S.lact);
+    if (threadIdx.x == 0) *any_active = S.lact[0] > 0;
+}
+
+sai_status cgs_run(const Items& I, int k, const Ops<double>& A, const double* Bsd, double* Xsd, Sys& S, double* pt,
+                   int* fl, int maxit, const Dims& D, cudaStream_t st)
+{
+    const int32_t n = I.n;
+    const int64_t ld = I.ld;
+    const size_t blk = (size_t)ld * k;
+    const int ib = item_blocks(n > 0 ? n : 1, k);
+    const int nch = I.nch;
+    const int check_every = 4;
+    const int ct = ctl_threads(k);
+    int hflag = 0;
+    Buf vecs;
+    SAI_TRY(vecs.alloc(sizeof(double) * blk * 9 + 8, st, true));
+    SAI_CUDA(cudaMemsetAsync(vecs.p, 0, sizeof(double) * blk * 9, st));
+    double* r = vecs.as<double>();
+    double* rh = r + blk;
+    double* u = rh + blk;
+    double* p = u + blk;
+    double* q = p + blk;
+    double* ph = q + blk;
+    double* v = ph + blk;
+    double* w = v + blk;
+    double* wh = w + blk;
+    double* qh = ph;  // A~ M w reuses phat's block: phat is dead once v = A~ phat is formed
+    const bool pnl = k > CTRL && spmv_group_major(k, n, sizeof(double));
+    Buf pbuf;
+    double *P1 = nullptr, *P2 = nullptr;
+    if (pnl) {
+        const size_t pe = (size_t)(n > 0 ? n : 1) * PNL * (size_t)((k + PNL - 1) / PNL);
+        SAI_TRY(pbuf.alloc(sizeof(double) * pe * 2, st, true));
+        P1 = pbuf.as<double>();
+        P2 = P1 + pe;
+    }
+    auto apply2 = [&](const double* X, double* Y1, double* Y2) {  // Y1 = M X, Y2 = A~ Y1
+        if (pnl) {
+            ProfScope ps(PROF_SPMM, st);
+            pnl_apply2(n, ld, k, A, X, Y1, Y2, S.lact, P1, P2, st);
+        } else {
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, A.M, k, X, Y1, nullptr, S.lact, st);
+            }
+            {
+                ProfScope ps(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, A.A, k, Y1, Y2, nullptr, S.lact, st);
+            }
+        }
+    };
+    k_cgs_init<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r, rh, q, p, S.lall, pt);
+    k_bicg_f0<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S);  // rho = b^T b, the first test on ||b||
+    SAI_CUDA(cudaGetLastError());
+    for (int it = 0; it < maxit; ++it) {
+        k_cgs_start<<<SAI_GRID(1), ct, 0, st>>>(k, maxit, S);
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_cgs_up<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, u, p, q, S);
+        }
+        apply2(p, ph, v);
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_dots<1><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, rh, v, nullptr, nullptr, S.lact, pt);
+        }
+        k_cgs_f1<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D);
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_cgs_q<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, u, v, q, w, S);
+        }
+        apply2(w, wh, qh);
+        {
+            ProfScope ps(PROF_BICG_VEC, st);
+            k_cgs_xr<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Xsd, r, rh, wh, qh, S, pt);
+        }
+        k_cgs_f2<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D, fl);
+        SAI_CUDA(cudaGetLastError());
+        if ((it + 1) % check_every == 0 || it + 1 == maxit) {
+            SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            if (!hflag) break;
+        }
+    }
+    k_cgs_start<<<SAI_GRID(1), ct, 0, st>>>(k, maxit, S);  // systems still active after maxit
+    SAI_CUDA(cudaGetLastError());
+    return SAI_OK;
+}
+
 // ================================================================== GMRES(m)
 // Control state (FP64 scalars and flags), shared by the FP64 and FP32 engines.
 struct Gm {
@@ -1919,11 +2157,11 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
                           int32_t* status, cudaStream_t st)
 {
     if (!h || !P || !prm || !thr || !iters || !status || k < 1) return SAI_INVALID_ARG;
-    const bool big_ok = prm->method == SAI_BICGSTAB && prm->precision == SAI_FP64;
+    const bool big_ok = (prm->method == SAI_BICGSTAB || prm->method == SAI_CGS) && prm->precision == SAI_FP64;
     if (k > (big_ok ? KBIG : CTRL)) return SAI_INVALID_ARG;
     if (prm->maxit < 0 || (prm->method == SAI_GMRES && (prm->restart < 1 || prm->restart >= GM_MAXM)))
         return SAI_INVALID_ARG;
-    if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES) return SAI_INVALID_ARG;
+    if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES && prm->method != SAI_CGS) return SAI_INVALID_ARG;
     if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     if (prm->transpose != 0 && prm->transpose != 1) return SAI_INVALID_ARG;
     if (prm->precision == SAI_FP32_REFINE64 && prm->method != SAI_GMRES) return SAI_NOT_IMPLEMENTED;
@@ -1978,7 +2216,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     Buf sysd, sysi, part, part2, flag, Bs, Xs, capb;
     SAI_TRY(sysd.alloc(sizeof(double) * 7 * k, st, true));
     SAI_TRY(sysi.alloc(sizeof(int) * (5 * k + 3 * (k + 1)), st, true));
-    const int nslot = prm->method == SAI_BICGSTAB ? 2 : (PS > 2 ? PS : 2);  // partial sums per (system, chunk)
+    const int nslot = prm->method != SAI_GMRES ? 2 : (PS > 2 ? PS : 2);  // partial sums per (system, chunk)
     SAI_TRY(part.alloc(sizeof(double) * (size_t)k * I.nch * nslot, st, true));
     SAI_TRY(part2.alloc(sizeof(double) * (size_t)k * I.nch * 2, st, true));
     SAI_TRY(flag.alloc(sizeof(int) * 4, st, true));
@@ -2030,7 +2268,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     k_fill_int<<<SAI_GRID(1), 256, 0, st>>>(k, cap, prm->maxit);
     SAI_CUDA(cudaGetLastError());
 
-    if (prm->method == SAI_BICGSTAB || prm->precision == SAI_FP64) {
+    if (prm->method != SAI_GMRES || prm->precision == SAI_FP64) {
         Ops<double> S64 = A64;
         SAI_TRY(build_sell<double>(n, h->nnz_At, A64.A.rp, A64.A.ci, A64.A.v, sell[0], sell[1], sell[2], S64.A, st));
         SAI_TRY(build_sell<double>(n, P->nnz, A64.M.rp, A64.M.ci, A64.M.v, sell[3], sell[4], sell[5], S64.M, st));
@@ -2038,6 +2276,8 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     }
     if (prm->method == SAI_BICGSTAB) {
         SAI_TRY(bicgstab_run(I, k, A64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
+    } else if (prm->method == SAI_CGS) {
+        SAI_TRY(cgs_run(I, k, A64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
     } else if (prm->precision == SAI_FP64) {
         Gm G;
         Buf hb, ibuf, vb, wb;

@@ -692,3 +692,37 @@ def test_psai_growth_c_differs_from_a_and_diagonal():
     d = np.arange(1.0, 21.0)
     Md = sp.csc_matrix(O.psai(sp.diags(d).tocsc(), 0.1, 1e-3, 1, 4, growth=1)[0])
     assert np.allclose(Md.toarray(), np.diag(1.0 / d), rtol=0, atol=1e-15)
+
+
+# ---- CGS (section 5 names it among the other solvers) ----
+def test_cgs_exact_preconditioner_one_iteration():
+    """With M = A~^{-1} the preconditioned operator is I: CGS ends after one
+    iteration with y = A~^{-1} b."""
+    A = sp.csc_matrix(_dominant(60, 4, seed=3))
+    Minv = sp.csc_matrix(np.linalg.inv(A.toarray()))
+    b = np.random.default_rng(1).standard_normal(60)
+    y, it, st = O.cgs(A, Minv, b, 1e-10 * np.linalg.norm(b))
+    assert st == O.OK and it == 1
+    np.testing.assert_allclose(y, np.linalg.solve(A.toarray(), b), rtol=0, atol=1e-12)
+
+
+def test_cgs_finite_termination_and_agreement():
+    """On a small nonsymmetric system CGS reaches the dense solution within
+    n + 1 iterations (finite termination in exact arithmetic), and on the 2D
+    workload it meets its threshold and agrees with BiCGStab's solution."""
+    A = sp.csc_matrix(_dominant(8, 3, seed=5))
+    I = sp.identity(8, format="csc")
+    b = np.arange(1.0, 9.0)
+    y, it, st = O.cgs(A, I, b, 1e-12 * np.linalg.norm(b), maxit=9)
+    assert st == O.OK and it <= 9
+    np.testing.assert_allclose(y, np.linalg.solve(A.toarray(), b), rtol=0, atol=1e-9)
+    P = W.convdiff2d_irregular()
+    J, p, _ = O.detect(P.A)
+    At, _ = O.split(P.A, J, p)
+    M = O.spai(At, 0.4, 5, 10)[0]
+    thr = 0.5e-10 * np.linalg.norm(P.b)
+    yc, itc, stc = O.cgs(At, M, P.b, thr)
+    yb, itb, stb = O.bicgstab(At, M, P.b, thr)
+    assert stc == O.OK and stb == O.OK
+    assert np.linalg.norm(P.b - sp.csc_matrix(At) @ yc) < 1.01 * thr
+    np.testing.assert_allclose(yc, yb, rtol=0, atol=1e-7)
