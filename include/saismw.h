@@ -229,10 +229,11 @@ sai_status sai_precond_create(const sai_csc_view* M, sai_stream_t stream, sai_pr
  * systems are frozen. BiCGStab tests after the half and the full step (a
  * half-step exit counts a full iteration); GMRES(restart) tests the Givens
  * residual estimate and restarts from the true residual; CGS (conjugate
- * gradient squared, two applications of A~ M per iteration) tests the
- * recursive residual after each iteration.
+ * gradient squared, two applications of A~ M per iteration) and BiCG (one
+ * application of A~ M and one of its transpose M^T A~^T per iteration) test
+ * the recursive residual after each iteration.
  * ---------------------------------------------------------------------- */
-typedef enum { SAI_BICGSTAB = 0, SAI_GMRES = 1, SAI_CGS = 2 } sai_krylov_method;
+typedef enum { SAI_BICGSTAB = 0, SAI_GMRES = 1, SAI_CGS = 2, SAI_BICG = 3 } sai_krylov_method;
 
 typedef struct {
     int32_t method;
@@ -249,8 +250,8 @@ typedef struct {
 } sai_krylov_params;
 
 /* B, X: n x k row-major device blocks. thr, iters, status: host arrays of k.
- * k: 1..256 for GMRES and the refined form; 1..262144 for FP64 BiCGStab
- * and CGS (SAI_INVALID_ARG beyond). The solver keeps about 10 n x k FP64 blocks of
+ * k: 1..256 for GMRES and the refined form; 1..262144 for FP64 BiCGStab,
+ * CGS and BiCG (SAI_INVALID_ARG beyond). The solver keeps about 10 n x k FP64 blocks of
  * its own (BiCGStab) and returns SAI_OOM when they do not fit.
  * Returns SAI_OK, SAI_MAXITER or SAI_BREAKDOWN (the first non-OK system
  * status), or an error. Synchronises the stream. */

@@ -207,6 +207,16 @@ def bicgstab(At, M, rhs, thr, maxit=500):
     return y, it.value, st
 
 
+def bicg(At, M, rhs, thr, maxit=500):
+    a, m = _In(At), _In(M)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    y = np.zeros_like(rhs)
+    it = C.c_int32()
+    st = lib().orc_bicg(C.byref(a.s), C.byref(m.s), _ptr(rhs, _f64p), C.c_double(thr), int(maxit), _ptr(y, _f64p),
+                        C.byref(it))
+    return y, it.value, st
+
+
 def cgs(At, M, rhs, thr, maxit=500):
     a, m = _In(At), _In(M)
     rhs = np.ascontiguousarray(rhs, dtype=np.float64)
@@ -257,7 +267,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
     b = np.ascontiguousarray(b, dtype=np.float64)
     prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
-                       {"bicgstab": 0, "gmres": 1, "cgs": 2}[krylov], restart, maxit, eps)
+                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3}[krylov], restart, maxit, eps)
     x = np.zeros(n)
     iters = np.zeros(n + 1, np.int32)
     rep = _SolveReport()
@@ -301,7 +311,7 @@ def backward(A, x, g, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restar
     g = np.ascontiguousarray(g, dtype=np.float64)
     prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
-                       {"bicgstab": 0, "gmres": 1, "cgs": 2}[krylov], restart, maxit, eps)
+                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3}[krylov], restart, maxit, eps)
     lam = np.zeros(n)
     gv = np.zeros(a.nnz)
     iters = np.zeros(n + 1, np.int32)

@@ -124,6 +124,11 @@ int orc_bicgstab(const orc_csc* At, const orc_csc* M, const double* rhs, double 
 
 /* Restarted GMRES(m), modified Gram-Schmidt Arnoldi, Givens rotations,
  * stop on the Givens residual estimate < thr; *iters counts inner steps. */
+/* BiCG on A~ M z = rhs returning y = M z, shadow sequence with M^T A~^T;
+ * the residual is tested after each iteration. */
+int orc_bicg(const orc_csc* At, const orc_csc* M, const double* rhs, double thr, int32_t maxit, double* y,
+             int32_t* iters);
+
 /* CGS on A~ M z = rhs returning y = M z; the recursive residual is tested
  * after each iteration (two applications of A~ M). */
 int orc_cgs(const orc_csc* At, const orc_csc* M, const double* rhs, double thr, int32_t maxit, double* y,
@@ -151,7 +156,7 @@ typedef struct {
     int32_t sai;          /* 0: SPAI, 1: PSAI(tol) */
     orc_spai_params spai;
     orc_psai_params psai;
-    int32_t krylov;       /* 0: BiCGStab, 1: GMRES(restart), 2: CGS */
+    int32_t krylov;       /* 0: BiCGStab, 1: GMRES(restart), 2: CGS, 3: BiCG */
     int32_t restart;
     int32_t maxit;
     double eps;

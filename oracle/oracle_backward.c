@@ -115,6 +115,7 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
             int ks;
             if (prm->krylov == 0) ks = orc_bicgstab(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 2) ks = orc_cgs(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
+            else if (prm->krylov == 3) ks = orc_bicg(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else ks = orc_gmres(&AtT, &MT, rhs, thr, prm->restart, prm->maxit, Y + (size_t)q * n, &it);
             if (ks != ORC_OK && rep->status == ORC_OK) rep->status = ks;
             if (ks == ORC_BAD_INPUT) st = ks;

@@ -99,6 +99,92 @@ int orc_bicgstab(const orc_csc* At, const orc_csc* M, const double* rhs, double 
 }
 
 
+
+/* BiCG on A~ M z = rhs, returning y = M z: the shadow sequence runs with
+ * (A~ M)^T = M^T A~^T, shadow residual = rhs; the residual is tested after
+ * each iteration (section 5 names BiCG among the other solvers tried). */
+int orc_bicg(const orc_csc* At, const orc_csc* M, const double* rhs, double thr, int32_t maxit, double* y,
+             int32_t* iters)
+{
+    int32_t n = At->ncols;
+    orc_csc AtT, MT;
+    if (orc_csc_transpose(At, &AtT) != ORC_OK) return ORC_NOMEM;
+    if (orc_csc_transpose(M, &MT) != ORC_OK) {
+        orc_csc_free(&AtT);
+        return ORC_NOMEM;
+    }
+    double* r = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* rs = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* p = (double*)orc_xcalloc((size_t)n, sizeof(double));
+    double* ps = (double*)orc_xcalloc((size_t)n, sizeof(double));
+    double* z = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* q = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* zs = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    double* qs = (double*)orc_xmalloc((size_t)n * sizeof(double));
+    for (int32_t i = 0; i < n; ++i) {
+        y[i] = 0.0;
+        r[i] = rhs[i];
+        rs[i] = rhs[i];
+    }
+    int status = ORC_MAXITER;
+    int32_t it = 0;
+    double rho_prev = 1.0;
+    if (orc_norm2(n, r) < thr) {
+        status = ORC_OK;
+    } else {
+        for (it = 1; it <= maxit; ++it) {
+            double rho = orc_dot(n, rs, r);
+            if (rho == 0.0) {
+                status = ORC_BREAKDOWN;
+                break;
+            }
+            if (it == 1) {
+                memcpy(p, r, (size_t)n * sizeof(double));
+                memcpy(ps, rs, (size_t)n * sizeof(double));
+            } else {
+                double beta = rho / rho_prev;
+                for (int32_t i = 0; i < n; ++i) {
+                    p[i] = r[i] + beta * p[i];
+                    ps[i] = rs[i] + beta * ps[i];
+                }
+            }
+            orc_csc_matvec(M, p, z);      /* z = M p        */
+            orc_csc_matvec(At, z, q);     /* q = A~ M p     */
+            orc_csc_matvec(&AtT, ps, zs); /* A~^T ps        */
+            orc_csc_matvec(&MT, zs, qs);  /* M^T A~^T ps    */
+            double sigma = orc_dot(n, ps, q);
+            if (sigma == 0.0) {
+                status = ORC_BREAKDOWN;
+                break;
+            }
+            double alpha = rho / sigma;
+            for (int32_t i = 0; i < n; ++i) {
+                y[i] += alpha * z[i];
+                r[i] -= alpha * q[i];
+                rs[i] -= alpha * qs[i];
+            }
+            if (orc_norm2(n, r) < thr) {
+                status = ORC_OK;
+                break;
+            }
+            rho_prev = rho;
+        }
+        if (it > maxit) it = maxit;
+    }
+    *iters = it;
+    free(r);
+    free(rs);
+    free(p);
+    free(ps);
+    free(z);
+    free(q);
+    free(zs);
+    free(qs);
+    orc_csc_free(&AtT);
+    orc_csc_free(&MT);
+    return status;
+}
+
 /* CGS (Sonneveld's conjugate gradient squared) on A~ M z = rhs, returning
  * y = M z directly: two applications of A~ M per iteration, the recursive
  * residual tested after each iteration (section 5 names CGS among the other

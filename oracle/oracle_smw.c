@@ -108,6 +108,7 @@ int orc_solve(const orc_csc* A, const double* b, const orc_solve_params* prm,
             int ks;
             if (prm->krylov == 0) ks = orc_bicgstab(&At, &M, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 2) ks = orc_cgs(&At, &M, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
+            else if (prm->krylov == 3) ks = orc_bicg(&At, &M, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else ks = orc_gmres(&At, &M, rhs, thr, prm->restart, prm->maxit, Y + (size_t)q * n, &it);
             if (ks != ORC_OK && rep->status == ORC_OK) rep->status = ks;
             if (ks == ORC_BAD_INPUT) st = ks;

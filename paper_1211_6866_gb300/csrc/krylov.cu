@@ -1203,6 +1203,155 @@ sai_status cgs_run(const Items& I, int k, const Ops<double>& A, const double* Bs
     return SAI_OK;
 }
 
+// ================================================================== BiCG
+// Biconjugate gradients on K z = b with K = A~ M, y = M z (section 5 names
+// BiCG among the other solvers tried). The shadow sequence runs with
+// K^T = M^T A~^T (the CSC arrays serve as CSR of the transposes), shadow
+// residual rs = b. Per iteration:
+//   rho = rs^T r;  p = r + beta p;  ps = rs + beta ps  (beta = rho / rho_old,
+//   p = r, ps = rs first);  z = M p;  q = A~ z;  qs = K^T ps;
+//   alpha = rho / ps^T q;  y += alpha z;  r -= alpha q;  rs -= alpha qs
+// with the control kernels of CGS (same recurrences for rho, beta, alpha).
+__global__ void k_bicg2_init(Items I, int k, const double* __restrict__ Bs, double* x, double* r, double* rs,
+                             const int* list, double* part)
+{
+    FOR_ITEMS(I, list, c, r0, r1)
+    {
+        double acc = 0.0;
+        const int64_t o = (int64_t)c * I.ld;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) {
+            const double b = Bs[o + i];
+            x[o + i] = 0.0;
+            r[o + i] = b;
+            rs[o + i] = b;
+            acc = fma(b, b, acc);
+        }
+        acc = warp_sum(acc);
+        if (lane_ == 0) part[pidx(0, c, q_, k, I.nch)] = acc;
+    }
+}
+
+__global__ void k_bicg2_up(Items I, const double* __restrict__ r, const double* __restrict__ rs, double* p,
+                           double* ps, Sys S)
+{
+    FOR_ITEMS(I, S.lact, c, r0, r1)
+    {
+        const double be = S.beta[c];
+        const bool first = S.iters[c] == 1;
+        const int64_t o = (int64_t)c * I.ld;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) {
+            p[o + i] = first ? r[o + i] : r[o + i] + be * p[o + i];
+            ps[o + i] = first ? rs[o + i] : rs[o + i] + be * ps[o + i];
+        }
+    }
+}
+
+__global__ void k_bicg2_xr(Items I, int k, double* x, double* r, double* rs, const double* __restrict__ z,
+                           const double* __restrict__ q, const double* __restrict__ qs, Sys S, double* part)
+{
+    FOR_ITEMS(I, S.lact, c, r0, r1)
+    {
+        const double al = S.alpha[c];
+        double a0 = 0.0, a1 = 0.0;
+        const int64_t o = (int64_t)c * I.ld;
+        for (int64_t i = r0 + lane_; i < r1; i += 32) {
+            x[o + i] += al * z[o + i];
+            const double rv = r[o + i] - al * q[o + i];
+            const double sv = rs[o + i] - al * qs[o + i];
+            r[o + i] = rv;
+            rs[o + i] = sv;
+            a0 = fma(rv, rv, a0);
+            a1 = fma(sv, rv, a1);
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane_ == 0) {
+            part[pidx(0, c, q_, k, I.nch)] = a0;
+            part[pidx(1, c, q_, k, I.nch)] = a1;
+        }
+    }
+}
+
+// A: the pair of K (M applied first, then A~); T: the pair of K^T (A~^T first, then M^T)
+sai_status bicg_run(const Items& I, int k, const Ops<double>& A, const Ops<double>& T, const double* Bsd,
+                    double* Xsd, Sys& S, double* pt, int* fl, int maxit, const Dims& D, cudaStream_t st)
+{
+    const int32_t n = I.n;
+    const int64_t ld = I.ld;
+    const size_t blk = (size_t)ld * k;
+    const int ib = item_blocks(n > 0 ? n : 1, k);
+    const int nch = I.nch;
+    const int check_every = 4;
+    const int ct = ctl_threads(k);
+    int hflag = 0;
+    Buf vecs;
+    SAI_TRY(vecs.alloc(sizeof(double) * blk * 8 + 8, st, true));
+    SAI_CUDA(cudaMemsetAsync(vecs.p, 0, sizeof(double) * blk * 8, st));
+    double* r = vecs.as<double>();
+    double* rs = r + blk;
+    double* p = rs + blk;
+    double* ps = p + blk;
+    double* z = ps + blk;
+    double* q = z + blk;
+    double* zs = q + blk;
+    double* qs = zs + blk;
+    const bool pnl = k > CTRL && spmv_group_major(k, n, sizeof(double));
+    Buf pbuf;
+    double *P1 = nullptr, *P2 = nullptr;
+    if (pnl) {
+        const size_t pe = (size_t)(n > 0 ? n : 1) * PNL * (size_t)((k + PNL - 1) / PNL);
+        SAI_TRY(pbuf.alloc(sizeof(double) * pe * 2, st, true));
+        P1 = pbuf.as<double>();
+        P2 = P1 + pe;
+    }
+    auto apply2 = [&](const Ops<double>& O, const double* X, double* Y1, double* Y2) {  // Y1 = O.M X, Y2 = O.A Y1
+        if (pnl) {
+            ProfScope ps_(PROF_SPMM, st);
+            pnl_apply2(n, ld, k, O, X, Y1, Y2, S.lact, P1, P2, st);
+        } else {
+            {
+                ProfScope ps_(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, O.M, k, X, Y1, nullptr, S.lact, st);
+            }
+            {
+                ProfScope ps_(PROF_SPMM, st);
+                spmv<double, 0>(n, ld, O.A, k, Y1, Y2, nullptr, S.lact, st);
+            }
+        }
+    };
+    k_bicg2_init<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bsd, Xsd, r, rs, S.lall, pt);
+    k_bicg_f0<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S);  // rho = b^T b, the first test on ||b||
+    SAI_CUDA(cudaGetLastError());
+    for (int it = 0; it < maxit; ++it) {
+        k_cgs_start<<<SAI_GRID(1), ct, 0, st>>>(k, maxit, S);
+        {
+            ProfScope ps_(PROF_BICG_VEC, st);
+            k_bicg2_up<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, r, rs, p, ps, S);
+        }
+        apply2(A, p, z, q);
+        apply2(T, ps, zs, qs);
+        {
+            ProfScope ps_(PROF_BICG_VEC, st);
+            k_dots<1><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, ps, q, nullptr, nullptr, S.lact, pt);
+        }
+        k_cgs_f1<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D);
+        {
+            ProfScope ps_(PROF_BICG_VEC, st);
+            k_bicg2_xr<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Xsd, r, rs, z, q, qs, S, pt);
+        }
+        k_cgs_f2<<<SAI_GRID(1), ct, 0, st>>>(k, nch, pt, S, D, fl);
+        SAI_CUDA(cudaGetLastError());
+        if ((it + 1) % check_every == 0 || it + 1 == maxit) {
+            SAI_CUDA(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            if (!hflag) break;
+        }
+    }
+    k_cgs_start<<<SAI_GRID(1), ct, 0, st>>>(k, maxit, S);  // systems still active after maxit
+    SAI_CUDA(cudaGetLastError());
+    return SAI_OK;
+}
+
 // ================================================================== GMRES(m)
 // Control state (FP64 scalars and flags), shared by the FP64 and FP32 engines.
 struct Gm {
@@ -2157,11 +2306,13 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
                           int32_t* status, cudaStream_t st)
 {
     if (!h || !P || !prm || !thr || !iters || !status || k < 1) return SAI_INVALID_ARG;
-    const bool big_ok = (prm->method == SAI_BICGSTAB || prm->method == SAI_CGS) && prm->precision == SAI_FP64;
+    const bool big_ok =
+        (prm->method == SAI_BICGSTAB || prm->method == SAI_CGS || prm->method == SAI_BICG) && prm->precision == SAI_FP64;
     if (k > (big_ok ? KBIG : CTRL)) return SAI_INVALID_ARG;
     if (prm->maxit < 0 || (prm->method == SAI_GMRES && (prm->restart < 1 || prm->restart >= GM_MAXM)))
         return SAI_INVALID_ARG;
-    if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES && prm->method != SAI_CGS) return SAI_INVALID_ARG;
+    if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES && prm->method != SAI_CGS && prm->method != SAI_BICG)
+        return SAI_INVALID_ARG;
     if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     if (prm->transpose != 0 && prm->transpose != 1) return SAI_INVALID_ARG;
     if (prm->precision == SAI_FP32_REFINE64 && prm->method != SAI_GMRES) return SAI_NOT_IMPLEMENTED;
@@ -2278,6 +2429,26 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         SAI_TRY(bicgstab_run(I, k, A64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
     } else if (prm->method == SAI_CGS) {
         SAI_TRY(cgs_run(I, k, A64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
+    } else if (prm->method == SAI_BICG) {
+        // the pair of K^T = M^T A~^T (or M A~ for the transposed solves):
+        // A~'s other orientation first, then M's
+        Ops<double> T64;
+        if (!prm->transpose) {
+            T64.M.rp = h->At_cp.as<int64_t>();
+            T64.M.ci = h->At_ri.as<int32_t>();
+            T64.M.v = h->At_v.as<double>();
+            T64.A.rp = P->M_cp.as<int64_t>();
+            T64.A.ci = P->M_ri.as<int32_t>();
+            T64.A.v = P->M_v.as<double>();
+        } else {
+            T64.M.rp = h->Atr_rp.as<int64_t>();
+            T64.M.ci = h->Atr_ci.as<int32_t>();
+            T64.M.v = h->Atr_v.as<double>();
+            T64.A.rp = P->Mr_rp.as<int64_t>();
+            T64.A.ci = P->Mr_ci.as<int32_t>();
+            T64.A.v = P->Mr_v.as<double>();
+        }
+        SAI_TRY(bicg_run(I, k, A64, T64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
     } else if (prm->precision == SAI_FP64) {
         Gm G;
         Buf hb, ibuf, vb, wb;

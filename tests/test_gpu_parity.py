@@ -162,7 +162,8 @@ def test_psai_matches_oracle(case):
 
 # ------------------------------------------------------------------ Krylov + SMW
 
-@pytest.mark.parametrize("method,restart", [("bicgstab", 30), ("gmres", 30), ("gmres", 20), ("cgs", 30)])
+@pytest.mark.parametrize("method,restart", [("bicgstab", 30), ("gmres", 30), ("gmres", 20), ("cgs", 30),
+                                            ("bicg", 30)])
 def test_krylov_multi_rhs_matches_oracle(method, restart):
     """The s+1 systems in one call against the oracle's solves one by one;
     GMRES(20) is the restart length of the paper's remark on other solvers (section 5)."""
@@ -180,7 +181,7 @@ def test_krylov_multi_rhs_matches_oracle(method, restart):
     B[:, 1:] = U.toarray()
     bn = np.linalg.norm(P.b)
     thr = [0.5e-8 * bn] + [1e-8 * bn / (2 * np.sqrt(s))] * s
-    meth = {"bicgstab": sai.BICGSTAB, "gmres": sai.GMRES, "cgs": sai.CGS}[method]
+    meth = {"bicgstab": sai.BICGSTAB, "gmres": sai.GMRES, "cgs": sai.CGS, "bicg": sai.BICG}[method]
     X, iters, stat, st = sai.krylov_solve(h, Pc, torch.as_tensor(B, device="cuda"), thr, method=meth,
                                           restart=restart)
     X = X.cpu().numpy()
@@ -190,6 +191,8 @@ def test_krylov_multi_rhs_matches_oracle(method, restart):
             y, it, sto = O.bicgstab(At, Mo, B[:, q], thr[q])
         elif method == "cgs":
             y, it, sto = O.cgs(At, Mo, B[:, q], thr[q])
+        elif method == "bicg":
+            y, it, sto = O.bicg(At, Mo, B[:, q], thr[q])
         else:
             y, it, sto = O.gmres(At, Mo, B[:, q], thr[q], restart=restart)
         assert sto == O.OK

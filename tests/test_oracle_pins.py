@@ -726,3 +726,30 @@ def test_cgs_finite_termination_and_agreement():
     assert stc == O.OK and stb == O.OK
     assert np.linalg.norm(P.b - sp.csc_matrix(At) @ yc) < 1.01 * thr
     np.testing.assert_allclose(yc, yb, rtol=0, atol=1e-7)
+
+
+def test_bicg_exact_preconditioner_termination_and_agreement():
+    """BiCG: with M = A~^{-1} one iteration gives y = A~^{-1} b; without a
+    preconditioner it reaches the dense solution of an 8 x 8 nonsymmetric
+    system within n + 1 iterations; on the 2D workload it agrees with
+    BiCGStab's solution."""
+    A = sp.csc_matrix(_dominant(60, 4, seed=3))
+    Minv = sp.csc_matrix(np.linalg.inv(A.toarray()))
+    b = np.random.default_rng(1).standard_normal(60)
+    y, it, st = O.bicg(A, Minv, b, 1e-10 * np.linalg.norm(b))
+    assert st == O.OK and it == 1
+    np.testing.assert_allclose(y, np.linalg.solve(A.toarray(), b), rtol=0, atol=1e-12)
+    A8 = sp.csc_matrix(_dominant(8, 3, seed=5))
+    b8 = np.arange(1.0, 9.0)
+    y8, it8, st8 = O.bicg(A8, sp.identity(8, format="csc"), b8, 1e-12 * np.linalg.norm(b8), maxit=9)
+    assert st8 == O.OK and it8 <= 9
+    np.testing.assert_allclose(y8, np.linalg.solve(A8.toarray(), b8), rtol=0, atol=1e-9)
+    P = W.convdiff2d_irregular()
+    J, p, _ = O.detect(P.A)
+    At, _ = O.split(P.A, J, p)
+    M = O.spai(At, 0.4, 5, 10)[0]
+    thr = 0.5e-10 * np.linalg.norm(P.b)
+    yg, _, sg = O.bicg(At, M, P.b, thr)
+    yb, _, sb = O.bicgstab(At, M, P.b, thr)
+    assert sg == O.OK and sb == O.OK
+    np.testing.assert_allclose(yg, yb, rtol=0, atol=1e-7)
