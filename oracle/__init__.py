@@ -277,6 +277,43 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
     return x, iters[: rep.s + 1].copy(), report
 
 
+def dmperm(A):
+    """Zero-diagonal repair of section 5: a maximum transversal of A.
+    Returns (p, rank): p[j] = row matched to column j (-1 if unmatched)."""
+    a = _In(A)
+    n = a.shape[1]
+    p = np.zeros(max(n, 1), np.int32)
+    r = C.c_int32()
+    _check("dmperm", lib().orc_dmperm(C.byref(a.s), _ptr(p, _i32p), C.byref(r)))
+    return p[:n].copy(), r.value
+
+
+def permute_rows(A, p):
+    """B = A(p,:): row j of B is row p[j] of A."""
+    a = _In(A)
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    out = _Csc()
+    _check("permute_rows", lib().orc_permute_rows(C.byref(a.s), _ptr(p, _i32p), C.byref(out)))
+    return _take(out)
+
+
+def solve_repaired(A, b, **kw):
+    """Procedure * after the section 5 preprocessing: when A has a zero
+    diagonal, solve A(p,:) x = b(p) with p = dmperm(A) (the solution x is
+    A's). Returns (x, iters, report, p); report["rr"] is taken on A itself."""
+    p, rank = dmperm(A)
+    n = A.shape[0]
+    if rank < n:
+        raise OracleError("solve_repaired: structurally singular", SINGULAR)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if np.array_equal(p, np.arange(n)):
+        x, it, rep = solve(A, b, **kw)
+    else:
+        x, it, rep = solve(permute_rows(A, p), b[p], **kw)
+    rep["rr"] = rel_resid(A, b, x)
+    return x, it, rep, p
+
+
 def csc_transpose(A):
     """A^T as a canonical CSC (the oracle's own transpose)."""
     a = _In(A)

@@ -199,6 +199,20 @@ int orc_smw_adjoint(int32_t n, int32_t s, const double* yhat, const double* W, c
 int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_solve_params* prm,
                  double* lambda_out, double* grad_vals, int32_t* iters_out, orc_solve_report* rep);
 
+/* ---- section 5 preprocessing: zero-diagonal repair (row DM permutation) -- */
+
+/* A maximum transversal of A (MATLAB dmperm with one output): p_out[j] = the
+ * row matched to column j, or -1; *rank_out = the number of matched columns
+ * (the structural rank). Entries count when stored with a nonzero value. A
+ * zero-free diagonal gives p = identity; otherwise the nonzero diagonal
+ * entries start the matching and depth-first augmenting paths from the
+ * unmatched columns (ascending) complete it. */
+int orc_dmperm(const orc_csc* A, int32_t* p_out, int32_t* rank_out);
+
+/* B = A(p,:) (row j of B is row p[j] of A); p must be a permutation of
+ * 0..n-1 (ORC_BAD_INPUT otherwise). Arrays malloc'd, free with orc_csc_free. */
+int orc_permute_rows(const orc_csc* A, const int32_t* p, orc_csc* B_out);
+
 #ifdef __cplusplus
 }
 #endif

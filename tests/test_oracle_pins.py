@@ -753,3 +753,114 @@ def test_bicg_exact_preconditioner_termination_and_agreement():
     yb, _, sb = O.bicgstab(At, M, P.b, thr)
     assert sg == O.OK and sb == O.OK
     np.testing.assert_allclose(yg, yb, rtol=0, atol=1e-7)
+
+
+# ------------------------------------------- zero-diagonal repair (section 5)
+
+def _check_transversal(A, p, rank):
+    """p is a matching: each matched column j has a stored nonzero at row
+    p[j], no row is used twice, and exactly rank columns are matched."""
+    A = sp.csc_matrix(A)
+    matched = p >= 0
+    assert matched.sum() == rank
+    assert len(set(p[matched].tolist())) == rank
+    for j in np.nonzero(matched)[0]:
+        assert A[p[j], j] != 0
+
+
+def _random_pattern(n, density, rng, zero_vals=0):
+    M = sp.random(n, n, density=density, random_state=rng, format="csc")
+    M.data = rng.standard_normal(M.data.size)
+    M = sp.csc_matrix(M)
+    M.sort_indices()
+    if zero_vals and M.nnz:  # stored entries with value zero do not count
+        M.data[rng.choice(M.nnz, size=min(zero_vals, M.nnz), replace=False)] = 0.0
+    return M
+
+
+def test_dmperm_rank_is_the_structural_rank():
+    """The transversal's size equals scipy's structural rank (a library
+    maximum bipartite matching) on random patterns, singular ones included,
+    and the matching is valid."""
+    from scipy.sparse.csgraph import structural_rank
+    rng = np.random.default_rng(7)
+    for trial in range(60):
+        n = int(rng.integers(1, 40))
+        A = _random_pattern(n, float(rng.choice([0.02, 0.05, 0.1, 0.3])), rng)
+        p, rank = O.dmperm(A)
+        _check_transversal(A, p, rank)
+        assert rank == structural_rank(A), trial
+
+
+def test_dmperm_brute_force_small():
+    """n <= 6: the largest number of nonzeros (sigma(j), j) over all n!
+    permutations sigma is the maximum transversal's size; stored zeros do
+    not count."""
+    import itertools
+    rng = np.random.default_rng(8)
+    for trial in range(40):
+        n = int(rng.integers(1, 7))
+        A = _random_pattern(n, 0.4, rng, zero_vals=int(rng.integers(0, 4)))
+        assert A.nnz == len(A.data)
+        D = A.toarray()
+        best = max(sum(D[s[j], j] != 0 for j in range(n)) for s in itertools.permutations(range(n)))
+        p, rank = O.dmperm(A)
+        _check_transversal(A, p, rank)
+        assert rank == best, trial
+
+
+def test_dmperm_keeps_a_zero_free_diagonal_and_fills_holes():
+    """A zero-free diagonal gives the identity; a cyclic shift of rows is
+    undone exactly when the shifted rows' only other entries are elsewhere
+    (a permuted diagonal matrix has one perfect matching)."""
+    P = W.convdiff2d_irregular(m=12, s=1, density=0.3)
+    p, rank = O.dmperm(P.A)
+    assert rank == P.n and np.array_equal(p, np.arange(P.n))
+    n = 9
+    q = np.roll(np.arange(n), 2)
+    A = sp.csc_matrix(sp.csr_matrix(sp.diags(np.arange(1.0, n + 1)))[q, :])
+    p, rank = O.dmperm(A)
+    assert rank == n and np.array_equal(A[p, :].toarray(), np.diag(np.arange(1.0, n + 1)))
+    # one empty column and one empty row: rank n - 1, the empty column unmatched
+    A = sp.lil_matrix(np.eye(5))
+    A[3, 3] = 0.0
+    A[3, 4] = 1.0
+    A[4, 4] = 0.0
+    A = sp.csc_matrix(A)
+    A.eliminate_zeros()
+    p, rank = O.dmperm(A)
+    assert rank == 4 and p[3] == -1 and p[4] == 3
+
+
+def test_dmperm_repairs_the_displaced_workload():
+    """Rows cycled out of place: the repaired matrix has a zero-free diagonal."""
+    from scipy.sparse.csgraph import structural_rank
+    P = W.rows_displaced(W.convdiff3d_irregular(m=12, s=3, density=0.1))
+    assert (P.A.diagonal() == 0).sum() > 0
+    p, rank = O.dmperm(P.A)
+    assert rank == P.n == structural_rank(P.A)
+    _check_transversal(P.A, p, rank)
+    assert (O.permute_rows(P.A, p).diagonal() != 0).all()
+
+
+def test_permute_rows_is_fancy_indexing():
+    """B = A(p,:) equals scipy's row indexing, values bit for bit."""
+    rng = np.random.default_rng(9)
+    A = W.convdiff3d_irregular(m=10, s=2, density=0.4).A
+    for _ in range(3):
+        p = rng.permutation(A.shape[0]).astype(np.int32)
+        B = O.permute_rows(A, p)
+        R = sp.csc_matrix(A[p, :])
+        R.sort_indices()
+        assert np.array_equal(B.indptr, R.indptr) and np.array_equal(B.indices, R.indices)
+        assert np.array_equal(B.data, R.data)
+    with pytest.raises(O.OracleError):
+        O.permute_rows(A, np.zeros(A.shape[0], np.int32))
+
+
+def test_solve_after_repair_meets_eps():
+    """Procedure * on the repaired system returns A's solution (rr on A)."""
+    P = W.rows_displaced(W.convdiff2d_irregular())
+    x, it, rep, p = O.solve_repaired(P.A, P.b, eps=1e-8)
+    assert rep["rr"] < 1e-8 and rep["s"] == 3
+    assert np.abs(x - 1.0).max() < 1e-5

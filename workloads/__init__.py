@@ -127,6 +127,22 @@ def convdiff3d_irregular(m=64, pe=10.0, s=10, density=0.05, scale=0.5, seed=SEED
                                                         seed=seed, dense_cols=cols.tolist()))
 
 
+def rows_displaced(P, frac=0.05, seed=SEED_BASE + 6):
+    """The system of P with a seeded cycle over round(frac*n) of its rows
+    (A' = A(q,:), b' = b(q), same solution x): most of the moved rows put a
+    zero on the diagonal, like the circuit matrices that section 5 permutes
+    before the method."""
+    rng = np.random.default_rng(seed)
+    n = P.A.shape[0]
+    m = max(2, int(round(frac * n)))
+    R = rng.choice(n, size=m, replace=False)
+    q = np.arange(n)
+    q[R] = np.roll(R, -1)  # row R[t] of A' is row R[t+1] of A
+    A = canonical(P.A[q, :])
+    params = dict(P.params, displaced=m, frac=frac, seed_rows=seed)
+    return Problem(P.name + "_zd%d" % m, A, np.ascontiguousarray(P.b[q]), params)
+
+
 def random_sparse_dominant(n, nnz_per_col, s, dense_nnz, seed, dominance=1.2):
     """Small irregular test matrix: random sparse body, s dense columns, column dominance.
 
