@@ -84,7 +84,12 @@ typedef struct {
                           entries of largest magnitude (the other rule of section 4;
                           ties to the smaller row; p_keep largest without a
                           diagonal). Other values: SAI_INVALID_ARG. */
-    int32_t reserved;  /* 0 */
+    int32_t zero_diag; /* sai_solve only: 1 applies the zero-diagonal repair of
+                          section 5 first (see sai_dmperm): when A has a zero on
+                          its diagonal, the method runs on A(p,:) x = b(p) with p
+                          a maximum transversal (SAI_SINGULAR when A is
+                          structurally singular). 0: off. sai_split_create and
+                          sai_solve_batched take 0 only (SAI_INVALID_ARG). */
 } sai_split_params;
 
 typedef struct sai_split_s* sai_split;
@@ -109,6 +114,34 @@ sai_status sai_split_copy_out(sai_split h, int64_t* At_col_ptr, int32_t* At_row_
                               int64_t* U_col_ptr, int32_t* U_row_idx, double* U_val, int32_t* J,
                               sai_stream_t stream);
 void sai_split_destroy(sai_split h);
+
+/* ----------------------------------------------------------------------
+ * Zero-diagonal repair (section 5, before the method): the paper permutes
+ * the rows of the matrices that have zeros on the diagonal with MATLAB's
+ * dmperm so that the diagonal, which the split keeps and SPAI's initial
+ * pattern P(I) starts from, becomes nonzero.
+ * ---------------------------------------------------------------------- */
+
+/* A maximum transversal of the square A: p[j] (device, n entries, caller
+ * owned) = the row matched to column j, or -1 when column j stays unmatched;
+ * A(p,:) has a zero-free diagonal when *rank_out == n. An entry counts when
+ * it is stored with a nonzero value. A zero-free diagonal gives the
+ * identity; otherwise the nonzero diagonal entries start the matching and
+ * phases of shortest augmenting paths complete it (ties to the smaller
+ * column and row, so p is reproducible). rank_out (host): the number of
+ * matched columns, the structural rank of A. moved_out (host, may be NULL):
+ * the number of columns j with p[j] != j. Rows must be strictly ascending
+ * per column (SAI_INVALID_ARG otherwise). Synchronises the stream. */
+sai_status sai_dmperm(const sai_csc_view* A, int32_t* p, int32_t* rank_out, int32_t* moved_out,
+                      sai_stream_t stream);
+
+/* B = A(p,:): row j of B is row p[j] of A (entry (i, c) of A becomes entry
+ * (pinv[i], c) of B, pinv[p[j]] = j). p: device, a permutation of 0..n-1
+ * (SAI_INVALID_ARG otherwise). B: caller-owned device CSC arrays of
+ * n+1, nnz and nnz entries, rows ascending per column; the values are A's,
+ * bit for bit. Synchronises the stream. */
+sai_status sai_permute_rows(const sai_csc_view* A, const int32_t* p, int64_t* B_col_ptr, int32_t* B_row_idx,
+                            double* B_val, sai_stream_t stream);
 
 /* ----------------------------------------------------------------------
  * Step 2: sparse approximate inverse M ~ A~^{-1}, min ||A~ M - I||_F,
@@ -313,7 +346,10 @@ typedef struct {
     int32_t iter_max;             /* max iterations over the s+1 systems */
     double c;
     double rr;                    /* ||b - A xhat|| / ||b|| */
-    double ms_split, ms_build, ms_krylov, ms_smw;  /* device time per step */
+    double ms_split, ms_build, ms_krylov, ms_smw;  /* device time per step
+                                     (ms_split includes the zero-diagonal repair) */
+    int32_t moved;                /* zero_diag: columns j with p[j] != j (0: A kept) */
+    int32_t reserved;
 } sai_solve_report;
 
 /* iters (host, may be NULL): s+1 iteration counts in the order [b, u_1..u_s];

@@ -43,7 +43,7 @@ class _CscView(C.Structure):
 
 class _SplitParams(C.Structure):
     _fields_ = [("thresh_mult", C.c_double), ("abs_tau", C.c_double), ("ge", C.c_int32), ("p_keep", C.c_int32),
-                ("keep_rule", C.c_int32), ("reserved", C.c_int32)]
+                ("keep_rule", C.c_int32), ("zero_diag", C.c_int32)]
 
 
 _KEEP = {"nearest": 0, "largest": 1}
@@ -108,7 +108,7 @@ class _SolveParams(C.Structure):
 class _SolveReport(C.Structure):
     _fields_ = [("split", _SplitInfo), ("precond", _PrecondInfo), ("status", C.c_int32), ("iter_max", C.c_int32),
                 ("c", C.c_double), ("rr", C.c_double), ("ms_split", C.c_double), ("ms_build", C.c_double),
-                ("ms_krylov", C.c_double), ("ms_smw", C.c_double)]
+                ("ms_krylov", C.c_double), ("ms_smw", C.c_double), ("moved", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _ProfSite(C.Structure):
@@ -165,6 +165,8 @@ def load():
     L.sai_build_autotune.argtypes = [vp, i32, C.POINTER(_SpaiParams), C.POINTER(_PsaiParams), vp,
                                      C.POINTER(_BuildTuning)]
     L.sai_build_set_config.argtypes = [C.POINTER(_BuildConfig)]
+    L.sai_dmperm.argtypes = [C.POINTER(_CscView), dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp]
+    L.sai_permute_rows.argtypes = [C.POINTER(_CscView), dp, dp, dp, dp, vp]
     L.sai_launch_count.restype = C.c_uint64
     L.sai_launch_count.argtypes = []
     L.sai_profile_begin.argtypes = []
@@ -172,7 +174,7 @@ def load():
     for f in ("sai_profile_begin", "sai_profile_end", "sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
               "sai_precond_get_info", "sai_precond_copy_out", "sai_krylov_solve", "sai_smw_recover",
               "sai_rel_resid", "sai_solve", "sai_solve_with", "sai_backward", "sai_solve_batched",
-              "sai_build_autotune", "sai_build_set_config"):
+              "sai_build_autotune", "sai_build_set_config", "sai_dmperm", "sai_permute_rows"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -405,16 +407,42 @@ def rel_resid(A, b, x):
     return rr.value
 
 
+def dmperm(A):
+    """Zero-diagonal repair of section 5: a maximum transversal of A.
+    Returns (p, rank, moved): p (device int32) with p[j] = the row matched to
+    column j (-1 if unmatched), the structural rank, and the number of
+    columns with p[j] != j."""
+    L = load()
+    p = torch.empty(max(A.n, 1), dtype=torch.int32, device=A.col_ptr.device)
+    rank, moved = C.c_int32(), C.c_int32()
+    v = A.view()
+    _check("sai_dmperm", L.sai_dmperm(C.byref(v), _p(p), C.byref(rank), C.byref(moved), _stream()))
+    return p[: A.n], rank.value, moved.value
+
+
+def permute_rows(A, p):
+    """B = A(p,:) (row j of B is row p[j] of A) as a new CscMatrix."""
+    L = load()
+    p = torch.as_tensor(p, dtype=torch.int32, device=A.col_ptr.device).contiguous()
+    B = CscMatrix(A.n, torch.empty_like(A.col_ptr), torch.empty_like(A.row_idx), torch.empty_like(A.val))
+    v = A.view()
+    _check("sai_permute_rows", L.sai_permute_rows(C.byref(v), _p(p), _p(B.col_ptr), _p(B.row_idx), _p(B.val),
+                                                  _stream()))
+    return B
+
+
 def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0, abs_tau=-1.0,
           delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, x=None, krylov_precision=0,
-          inner_tol=0.0, sai_precision=0, keep="nearest", lfill=0, growth="A"):
+          inner_tol=0.0, sai_precision=0, keep="nearest", lfill=0, growth="A", zero_diag=False):
     """Procedure * on the device. krylov_precision=1 selects the FP32-inner /
-    FP64-refined GMRES; sai_precision=1 the FP32 QR + FP64 refinement build.
-    Returns (x, iters list, report dict)."""
+    FP64-refined GMRES; sai_precision=1 the FP32 QR + FP64 refinement build;
+    zero_diag=True first applies the zero-diagonal repair of section 5
+    (report["moved"] columns moved). Returns (x, iters list, report dict)."""
     L = load()
     if x is None:
         x = torch.empty(A.n, dtype=torch.float64, device=b.device)
-    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
+    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], int(bool(zero_diag))),
+                       0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
                        _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill, _GROWTH[growth], 0),
                        _KrylovParams(_METHOD[krylov], restart, maxit, krylov_precision,
@@ -430,7 +458,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
                   nnz_M=rep.precond.nnz_M, n_c=rep.precond.n_c, l_m=rep.precond.l_m,
                   n_tier=list(rep.precond.n_tier), status=st, iter_max=rep.iter_max, c=rep.c, rr=rep.rr,
                   ms_split=rep.ms_split, ms_build=rep.ms_build, ms_krylov=rep.ms_krylov, ms_smw=rep.ms_smw,
-                  build_ms=rep.precond.build_ms)
+                  build_ms=rep.precond.build_ms, moved=rep.moved)
     return x, list(iters[: s + 1]), report
 
 

@@ -194,6 +194,7 @@ sai_status sai_split_create(const sai_csc_view* A, const sai_split_params* prm, 
 {
     if (!out) return SAI_INVALID_ARG;
     *out = nullptr;
+    if (prm && prm->zero_diag != 0) return SAI_INVALID_ARG;  // the repair belongs to sai_solve
     sai_pool_init_once();
     sai_split_s* h = new (std::nothrow) sai_split_s();
     if (!h) return SAI_OOM;
@@ -584,10 +585,35 @@ float elapsed(cudaEvent_t a, cudaEvent_t b)
 sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
                       int32_t* iters, int32_t iters_cap, sai_solve_report* rep, cudaStream_t st)
 {
-    if (!A || !prm || !rep || (A->n > 0 && (!b || !x))) return SAI_INVALID_ARG;
+    if (!A || !prm || !rep || (A->n > 0 && (!b || !x)) || (prm->split.zero_diag != 0 && prm->split.zero_diag != 1))
+        return SAI_INVALID_ARG;
     *rep = sai_solve_report{};
     Ev e0, e1, e2, e3, e4, e5;
     SAI_CUDA(cudaEventRecord(e0.e, st));
+    // zero-diagonal repair (section 5): the method then runs on A(p,:) x = b(p)
+    Buf pb, bcp, bri, bv, bb;
+    sai_csc_view Ap = *A;
+    if (prm->split.zero_diag && A->n > 0) {
+        SAI_TRY(pb.alloc(sizeof(int32_t) * (size_t)A->n, st, true));
+        int32_t rank = 0, moved = 0;
+        SAI_TRY(sai_dmperm_run(A, pb.as<int32_t>(), &rank, &moved, st));
+        if (rank < A->n) return SAI_SINGULAR;
+        rep->moved = moved;
+        if (moved > 0) {
+            SAI_TRY(bcp.alloc(sizeof(int64_t) * ((size_t)A->n + 1), st, true));
+            SAI_TRY(bri.alloc(sizeof(int32_t) * (size_t)A->nnz + 4, st, true));
+            SAI_TRY(bv.alloc(sizeof(double) * (size_t)A->nnz + 8, st, true));
+            SAI_TRY(bb.alloc(sizeof(double) * (size_t)A->n, st, true));
+            SAI_TRY(sai_permute_rows_run(A, pb.as<int32_t>(), bcp.as<int64_t>(), bri.as<int32_t>(), bv.as<double>(),
+                                         st));
+            SAI_TRY(sai_gather_vec(A->n, pb.as<int32_t>(), b, bb.as<double>(), st));
+            Ap.col_ptr = bcp.as<int64_t>();
+            Ap.row_idx = bri.as<int32_t>();
+            Ap.val = bv.as<double>();
+            A = &Ap;
+            b = bb.as<double>();
+        }
+    }
     sai_split_s h;
     SAI_TRY(sai_split_build(A, &prm->split, st, true, &h));
     SAI_CUDA(cudaEventRecord(e1.e, st));
@@ -700,4 +726,21 @@ extern "C" sai_status sai_backward(const sai_csc_view* A, sai_split h, sai_preco
 {
     sai_pool_init_once();
     return backward_impl(A, h, P, x, g, prm, lambda, grad_vals, iters, iters_cap, rep, S(stream));
+}
+
+extern "C" sai_status sai_dmperm(const sai_csc_view* A, int32_t* p, int32_t* rank_out, int32_t* moved_out,
+                                 sai_stream_t stream)
+{
+    sai_pool_init_once();
+    return sai_dmperm_run(A, p, rank_out, moved_out, S(stream));
+}
+
+extern "C" sai_status sai_permute_rows(const sai_csc_view* A, const int32_t* p, int64_t* B_col_ptr,
+                                       int32_t* B_row_idx, double* B_val, sai_stream_t stream)
+{
+    sai_pool_init_once();
+    const sai_status r = sai_permute_rows_run(A, p, B_col_ptr, B_row_idx, B_val, S(stream));
+    if (r != SAI_OK) return r;
+    SAI_CUDA(cudaStreamSynchronize(S(stream)));
+    return SAI_OK;
 }

@@ -533,7 +533,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     if (prm->krylov.method != SAI_BICGSTAB || prm->krylov.precision != SAI_FP64 || prm->krylov.transpose)
         return SAI_NOT_IMPLEMENTED;
     if (prm->sai == 1 && prm->psai.tol_mode == 0) return SAI_NOT_IMPLEMENTED;
-    if (prm->krylov.maxit < 0) return SAI_INVALID_ARG;
+    if (prm->krylov.maxit < 0 || prm->split.zero_diag != 0) return SAI_INVALID_ARG;
     *rep = sai_batch_report{};
     int dev = 0, sms = 0;
     SAI_CUDA(cudaGetDevice(&dev));

@@ -86,6 +86,13 @@ sai_status sai_build_set_config_run(const sai_build_config* cfg);
 // Theorem 1 for A^T = A~^T + V U^T: x = yhat - What (I + U^T What)^{-1} (U^T yhat)
 sai_status sai_smw_adj_run(const sai_split_s* h, const double* Y, double* x, double* c_out, cudaStream_t st);
 
+// Zero-diagonal repair (section 5): maximum transversal p (p[j] = row of
+// column j, -1 if unmatched), B = A(p,:), and y = x(p).
+sai_status sai_dmperm_run(const sai_csc_view* A, int32_t* p, int32_t* rank_out, int32_t* moved_out, cudaStream_t st);
+sai_status sai_permute_rows_run(const sai_csc_view* A, const int32_t* p, int64_t* Bcp, int32_t* Bri, double* Bv,
+                                cudaStream_t st);
+sai_status sai_gather_vec(int32_t n, const int32_t* p, const double* x, double* y, cudaStream_t st);
+
 void sai_pool_init_once();
 // Library-owned non-blocking stream of the current device (for graph capture), or nullptr.
 cudaStream_t sai_aux_stream();
