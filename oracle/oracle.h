@@ -205,8 +205,8 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
  * row matched to column j, or -1; *rank_out = the number of matched columns
  * (the structural rank). Entries count when stored with a nonzero value. A
  * zero-free diagonal gives p = identity; otherwise the nonzero diagonal
- * entries start the matching and depth-first augmenting paths from the
- * unmatched columns (ascending) complete it. */
+ * entries start the matching and shortest augmenting paths (breadth-first
+ * search) from the unmatched columns (ascending) complete it. */
 int orc_dmperm(const orc_csc* A, int32_t* p_out, int32_t* rank_out);
 
 /* B = A(p,:) (row j of B is row p[j] of A); p must be a permutation of

@@ -13,10 +13,13 @@
  *     matrices with zero diagonals are permuted;
  *   - otherwise the columns whose diagonal is nonzero start matched to it,
  *     and each unmatched column, in ascending order, looks for an augmenting
- *     path by depth-first search over the alternating paths, taking a free
- *     row of a newly reached column before going deeper (the cheap
- *     assignment of Duff's search); the path is flipped when found (a
- *     matching is maximum iff no augmenting path exists).
+ *     path by breadth-first search over the alternating paths (rows in
+ *     ascending order, columns first in first out) and flips the first,
+ *     hence shortest, one found; a column without one stays unmatched (a
+ *     matching is maximum iff no augmenting path exists, and a column that
+ *     finds none cannot find one later).
+ * Shortest paths move as few rows as the search allows: the rows whose
+ * diagonal was already nonzero stay in place unless a path needs them.
  * Several maximum transversals usually exist; only their size (the
  * structural rank) is unique.
  */
@@ -42,9 +45,8 @@ int orc_dmperm(const orc_csc* A, int32_t* p_out, int32_t* rank_out)
     int32_t* match_col = (int32_t*)orc_xmalloc((size_t)n * sizeof(int32_t)); /* row of column j */
     int32_t* match_row = (int32_t*)orc_xmalloc((size_t)n * sizeof(int32_t)); /* column of row i */
     int32_t* seen = (int32_t*)orc_xmalloc((size_t)n * sizeof(int32_t));      /* search stamp per row */
-    int32_t* st_col = (int32_t*)orc_xmalloc((size_t)n * sizeof(int32_t));    /* DFS stack: column */
-    int64_t* st_pos = (int64_t*)orc_xmalloc((size_t)n * sizeof(int64_t));    /*   next entry to try */
-    int32_t* st_row = (int32_t*)orc_xmalloc((size_t)n * sizeof(int32_t));    /*   row taken at this level */
+    int32_t* via = (int32_t*)orc_xmalloc((size_t)n * sizeof(int32_t));       /* column that reached row i */
+    int32_t* queue = (int32_t*)orc_xmalloc((size_t)n * sizeof(int32_t));     /* columns, first in first out */
     for (int32_t i = 0; i < n; ++i) {
         match_col[i] = -1;
         match_row[i] = -1;
@@ -57,63 +59,46 @@ int orc_dmperm(const orc_csc* A, int32_t* p_out, int32_t* rank_out)
             match_row[j] = j;
             ++rank;
         }
-    if (rank < n) {
-        for (int32_t j = 0; j < n; ++j) {
-            if (match_col[j] >= 0) continue;
-            /* one search from the unmatched column j; rows seen in it are not revisited */
-            int32_t top = 0;
-            st_col[0] = j;
-            st_pos[0] = A->col_ptr[j];
-            int found = 0;
-            while (top >= 0 && !found) {
-                const int32_t c = st_col[top];
-                int32_t next = -1;
-                if (st_pos[top] == A->col_ptr[c]) {  /* first visit: a free row of c ends the path at once */
-                    for (int64_t t = A->col_ptr[c]; t < A->col_ptr[c + 1]; ++t)
-                        if (entry_counts(A, t) && match_row[A->row_idx[t]] < 0 && seen[A->row_idx[t]] != j) {
-                            next = A->row_idx[t];
-                            break;
-                        }
+    for (int32_t j = 0; j < n && rank < n; ++j) {
+        if (match_col[j] >= 0) continue;
+        /* breadth-first search from the unmatched column j over alternating
+         * paths: a row is reached from a column through any nonzero, a
+         * column from its matched row; the first free row reached ends a
+         * shortest augmenting path */
+        int32_t head = 0, tail = 0, end = -1;
+        queue[tail++] = j;
+        while (head < tail && end < 0) {
+            const int32_t c = queue[head++];
+            for (int64_t t = A->col_ptr[c]; t < A->col_ptr[c + 1]; ++t) {
+                const int32_t i = A->row_idx[t];
+                if (!entry_counts(A, t) || seen[i] == j) continue;
+                seen[i] = j;
+                via[i] = c;
+                if (match_row[i] < 0) {
+                    end = i;
+                    break;
                 }
-                while (next < 0 && st_pos[top] < A->col_ptr[c + 1]) {
-                    const int64_t t = st_pos[top]++;
-                    const int32_t i = A->row_idx[t];
-                    if (entry_counts(A, t) && seen[i] != j) {
-                        next = i;
-                        break;
-                    }
-                }
-                if (next < 0) {  /* column c has no unexplored row: back up */
-                    --top;
-                    continue;
-                }
-                seen[next] = j;
-                st_row[top] = next;
-                if (match_row[next] < 0) {
-                    found = 1;   /* free row: the stack holds an augmenting path */
-                } else {
-                    ++top;       /* follow the matched edge of row next */
-                    st_col[top] = match_row[next];
-                    st_pos[top] = A->col_ptr[st_col[top]];
-                }
-            }
-            if (found) {
-                for (int32_t l = top; l >= 0; --l) {  /* flip the path: column st_col[l] takes row st_row[l] */
-                    match_col[st_col[l]] = st_row[l];
-                    match_row[st_row[l]] = st_col[l];
-                }
-                ++rank;
+                queue[tail++] = match_row[i];
             }
         }
+        if (end < 0) continue;  /* no augmenting path from j: column j stays unmatched */
+        for (int32_t i = end;;) {  /* flip the path back to j */
+            const int32_t c = via[i];
+            const int32_t i_prev = match_col[c];
+            match_col[c] = i;
+            match_row[i] = c;
+            if (c == j) break;
+            i = i_prev;
+        }
+        ++rank;
     }
     for (int32_t j = 0; j < n; ++j) p_out[j] = match_col[j];
     *rank_out = rank;
     free(match_col);
     free(match_row);
     free(seen);
-    free(st_col);
-    free(st_pos);
-    free(st_row);
+    free(via);
+    free(queue);
     return ORC_OK;
 }
 
