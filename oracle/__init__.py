@@ -237,6 +237,22 @@ def gmres(At, M, rhs, thr, restart=50, maxit=500):
     return y, it.value, st
 
 
+def block_gmres(At, M, B, thr, restart=50, maxit=500):
+    """Block GMRES(restart) on A~ M Z = B (n x k), Y = M Z; thr: k thresholds.
+    Returns (Y (n x k), block steps, status)."""
+    a, m = _In(At), _In(M)
+    B = np.asfortranarray(B, dtype=np.float64)
+    n, k = B.shape
+    thr = np.ascontiguousarray(thr, dtype=np.float64)
+    Y = np.zeros((n, k), order="F")
+    it = C.c_int32()
+    st = lib().orc_block_gmres(C.byref(a.s), C.byref(m.s), int(k), _ptr(B, _f64p), _ptr(thr, _f64p), int(restart),
+                               int(maxit), _ptr(Y, _f64p), C.byref(it))
+    if st == BAD_INPUT:
+        raise OracleError("block_gmres", st)
+    return Y, it.value, st
+
+
 def smw(yhat, W, J):
     """W: (n, s) array. Returns (xhat, z, c)."""
     yhat = np.ascontiguousarray(yhat, dtype=np.float64)
@@ -267,7 +283,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
     b = np.ascontiguousarray(b, dtype=np.float64)
     prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
-                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3}[krylov], restart, maxit, eps)
+                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3, "bgmres": 4}[krylov], restart, maxit, eps)
     x = np.zeros(n)
     iters = np.zeros(n + 1, np.int32)
     rep = _SolveReport()
@@ -348,7 +364,7 @@ def backward(A, x, g, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restar
     g = np.ascontiguousarray(g, dtype=np.float64)
     prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
-                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3}[krylov], restart, maxit, eps)
+                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3, "bgmres": 4}[krylov], restart, maxit, eps)
     lam = np.zeros(n)
     gv = np.zeros(a.nnz)
     iters = np.zeros(n + 1, np.int32)

@@ -10,7 +10,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["oracle_core.c", "oracle_split.c", "oracle_sai.c", "oracle_krylov.c", "oracle_smw.c", "oracle_backward.c",
-           "oracle_perm.c"]
+           "oracle_perm.c", "oracle_block.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -156,7 +156,8 @@ typedef struct {
     int32_t sai;          /* 0: SPAI, 1: PSAI(tol) */
     orc_spai_params spai;
     orc_psai_params psai;
-    int32_t krylov;       /* 0: BiCGStab, 1: GMRES(restart), 2: CGS, 3: BiCG */
+    int32_t krylov;       /* 0: BiCGStab, 1: GMRES(restart), 2: CGS, 3: BiCG,
+                             4: block GMRES(restart) over all s+1 systems */
     int32_t restart;
     int32_t maxit;
     double eps;
@@ -198,6 +199,19 @@ int orc_smw_adjoint(int32_t n, int32_t s, const double* yhat, const double* W, c
  * rep->rr = ||g - A^T lambda|| / ||g||, rep->c = ||z||. */
 int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_solve_params* prm,
                  double* lambda_out, double* grad_vals, int32_t* iters_out, orc_solve_report* rep);
+
+/* ---- block Krylov alternative for the s+1 systems (section 3) ---------- */
+
+/* Block GMRES(m) with right preconditioning on A~ M Z = B, Y = M Z, for the
+ * k right-hand sides of B (n x k column-major); Y (n x k column-major) out.
+ * Each column c stops at ||B e_c - A~ Y e_c|| < thr[c] (the least-squares
+ * estimate inside a cycle, the true residual at a cycle start); the cycle's
+ * block steps stop when every column meets its threshold. *iters = block
+ * steps in all (each applies A~ and M to k vectors). Returns ORC_OK,
+ * ORC_MAXITER (maxit block steps) or ORC_BREAKDOWN (a zero pivot of the
+ * reduced block Hessenberg matrix). */
+int orc_block_gmres(const orc_csc* At, const orc_csc* M, int32_t k, const double* B, const double* thr, int32_t m,
+                    int32_t maxit, double* Y, int32_t* iters);
 
 /* ---- section 5 preprocessing: zero-diagonal repair (row DM permutation) -- */
 

@@ -100,6 +100,10 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
         double gnorm = orc_norm2(n, g);
         double* Y = (double*)orc_xcalloc((size_t)(s + 1) * (size_t)n, sizeof(double)); /* [yhat, w_1..w_s] */
         double* rhs = (double*)orc_xmalloc((size_t)n * sizeof(double));
+        double* Bblk = prm->krylov == 4 ? (double*)orc_xmalloc((size_t)(s + 1) * (size_t)n * sizeof(double)) : NULL;
+        double* blk_thr = prm->krylov == 4 ? (double*)orc_xmalloc((size_t)(s + 1) * sizeof(double)) : NULL;
+        int blk_st = ORC_OK;
+        int32_t blk_it = 0;
         rep->status = ORC_OK;
         for (int32_t q = 0; q <= s && st == ORC_OK; ++q) {
             double thr;
@@ -113,7 +117,22 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
             }
             int32_t it = 0;
             int ks;
-            if (prm->krylov == 0) ks = orc_bicgstab(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
+            if (prm->krylov == 4) {
+                /* block GMRES: all s+1 transposed systems at once, at q = 0 */
+                if (q == 0) {
+                    blk_thr[0] = thr;
+                    memcpy(Bblk, rhs, (size_t)n * sizeof(double));
+                    for (int32_t t = 1; t <= s; ++t) {
+                        double* bt = Bblk + (size_t)t * n;
+                        for (int32_t i = 0; i < n; ++i) bt[i] = 0.0;
+                        bt[J[t - 1]] = 1.0;
+                        blk_thr[t] = prm->eps * gnorm / (2.0 * sqrt((double)s));
+                    }
+                    blk_st = orc_block_gmres(&AtT, &MT, s + 1, Bblk, blk_thr, prm->restart, prm->maxit, Y, &blk_it);
+                }
+                ks = blk_st;
+                it = blk_it;
+            } else if (prm->krylov == 0) ks = orc_bicgstab(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 2) ks = orc_cgs(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 3) ks = orc_bicg(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else ks = orc_gmres(&AtT, &MT, rhs, thr, prm->restart, prm->maxit, Y + (size_t)q * n, &it);
@@ -144,6 +163,8 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
         }
         free(Y);
         free(rhs);
+        free(Bblk);
+        free(blk_thr);
     }
     free(loops);
     free(res);

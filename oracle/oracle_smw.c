@@ -93,6 +93,10 @@ int orc_solve(const orc_csc* A, const double* b, const orc_solve_params* prm,
         double* rhs = (double*)orc_xmalloc((size_t)n * sizeof(double));
         double* tmp = (double*)orc_xmalloc((size_t)n * sizeof(double));
         double rW2 = 0.0, ry = 0.0;
+        double* Bblk = prm->krylov == 4 ? (double*)orc_xmalloc((size_t)(s + 1) * (size_t)n * sizeof(double)) : NULL;
+        double* blk_thr = prm->krylov == 4 ? (double*)orc_xmalloc((size_t)(s + 1) * sizeof(double)) : NULL;
+        int blk_st = ORC_OK;
+        int32_t blk_it = 0;
         rep->status = ORC_OK;
         for (int32_t q = 0; q <= s && st == ORC_OK; ++q) {
             double thr;
@@ -106,7 +110,22 @@ int orc_solve(const orc_csc* A, const double* b, const orc_solve_params* prm,
             }
             int32_t it = 0;
             int ks;
-            if (prm->krylov == 0) ks = orc_bicgstab(&At, &M, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
+            if (prm->krylov == 4) {
+                /* block GMRES: all s+1 systems at once, at q = 0 */
+                if (q == 0) {
+                    blk_thr[0] = thr;
+                    memcpy(Bblk, rhs, (size_t)n * sizeof(double));
+                    for (int32_t t = 1; t <= s; ++t) {
+                        double* bt = Bblk + (size_t)t * n;
+                        for (int32_t i = 0; i < n; ++i) bt[i] = 0.0;
+                        for (int64_t e = U.col_ptr[t - 1]; e < U.col_ptr[t]; ++e) bt[U.row_idx[e]] = U.val[e];
+                        blk_thr[t] = prm->eps * bnorm / (2.0 * sqrt((double)s));
+                    }
+                    blk_st = orc_block_gmres(&At, &M, s + 1, Bblk, blk_thr, prm->restart, prm->maxit, Y, &blk_it);
+                }
+                ks = blk_st;
+                it = blk_it;
+            } else if (prm->krylov == 0) ks = orc_bicgstab(&At, &M, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 2) ks = orc_cgs(&At, &M, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 3) ks = orc_bicg(&At, &M, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else ks = orc_gmres(&At, &M, rhs, thr, prm->restart, prm->maxit, Y + (size_t)q * n, &it);
@@ -135,6 +154,8 @@ int orc_solve(const orc_csc* A, const double* b, const orc_solve_params* prm,
         free(Y);
         free(rhs);
         free(tmp);
+        free(Bblk);
+        free(blk_thr);
     }
     free(loops);
     free(res);

@@ -864,3 +864,80 @@ def test_solve_after_repair_meets_eps():
     x, it, rep, p = O.solve_repaired(P.A, P.b, eps=1e-8)
     assert rep["rr"] < 1e-8 and rep["s"] == 3
     assert np.abs(x - 1.0).max() < 1e-5
+
+
+# ------------------------------------------------ block GMRES (section 3)
+
+def _small_system(n, k, seed):
+    rng = np.random.default_rng(seed)
+    At = sp.csc_matrix(sp.random(n, n, density=0.2, random_state=rng) + sp.diags(3.0 + rng.random(n)))
+    At.sort_indices()
+    B = rng.standard_normal((n, k))
+    return At, B
+
+
+def test_block_gmres_with_one_column_is_gmres():
+    """k = 1: the block method is GMRES itself (same step count, same
+    solution to rounding)."""
+    P = W.convdiff2d_irregular()
+    At = sp.csc_matrix(O.split(P.A, *O.detect(P.A)[:2])[0])
+    M = sp.csc_matrix(O.spai(At, 0.4, 5, 10)[0])
+    thr = 0.5e-8 * np.linalg.norm(P.b)
+    y, it, st = O.gmres(At, M, P.b, thr, restart=30)
+    Y, itb, stb = O.block_gmres(At, M, P.b[:, None], [thr], restart=30)
+    assert st == stb == O.OK and it == itb
+    np.testing.assert_allclose(Y[:, 0], y, rtol=0, atol=1e-9)
+
+
+def test_block_gmres_exact_preconditioner_one_step():
+    """M = A~^{-1}: A~M = I, the block Krylov space of B holds every
+    solution, one block step solves all columns."""
+    At, B = _small_system(40, 3, 21)
+    M = sp.csc_matrix(np.linalg.inv(At.toarray()))
+    Y, it, st = O.block_gmres(At, M, B, np.full(3, 1e-10), restart=5)
+    assert st == O.OK and it == 1
+    np.testing.assert_allclose(At @ Y, B, rtol=0, atol=1e-10)
+
+
+def test_block_gmres_finite_termination():
+    """Without restarts the block space reaches dimension n after
+    ceil(n / k) steps: the exact solution by then (dense solve)."""
+    n, k = 12, 3
+    At, B = _small_system(n, k, 22)
+    M = sp.identity(n, format="csc")
+    Y, it, st = O.block_gmres(At, M, B, np.full(k, 1e-11), restart=10, maxit=10)
+    assert st == O.OK and it <= n // k
+    np.testing.assert_allclose(Y, np.linalg.solve(At.toarray(), B), rtol=0, atol=1e-10)
+
+
+def test_block_gmres_minimises_over_the_block_krylov_space():
+    """After j block steps (no restart, thresholds never met), column c's
+    residual is min ||b_c - K t|| over t in the block Krylov space
+    span[B, KB, .., K^{j-1}B], K = A~M (dense least squares)."""
+    n, k = 60, 3
+    At, B = _small_system(n, k, 23)
+    rng = np.random.default_rng(24)
+    M = sp.csc_matrix(sp.diags(1.0 / At.diagonal()) + sp.random(n, n, density=0.05, random_state=rng) * 0.01)
+    K = At.toarray() @ M.toarray()
+    for j in (1, 2, 4, 6):
+        Y, it, st = O.block_gmres(At, M, B, np.zeros(k), restart=10, maxit=j)
+        assert it == j and st == O.MAXITER
+        blocks = [B]
+        for _ in range(j - 1):
+            blocks.append(K @ blocks[-1])
+        Q, _ = np.linalg.qr(np.hstack(blocks))
+        KQ = K @ Q
+        for c in range(k):
+            t = np.linalg.lstsq(KQ, B[:, c], rcond=None)[0]
+            best = np.linalg.norm(B[:, c] - KQ @ t)
+            got = np.linalg.norm(B[:, c] - At @ Y[:, c])
+            assert abs(got - best) <= 1e-10 * np.linalg.norm(B[:, c]), (j, c, got, best)
+
+
+def test_procedure_with_block_gmres_meets_theorem2():
+    """Procedure * with block GMRES(30) on the 2D workload: rr < eps and the
+    Theorem 2 inequality rr <= ||r_y|| + c ||R_W||."""
+    P = W.convdiff2d_irregular()
+    x, it, rep = O.solve(P.A, P.b, krylov="bgmres", restart=30, eps=1e-8)
+    assert rep["status"] == O.OK and len(set(it.tolist())) == 1
+    assert rep["rr"] < 1e-8 and rep["rr"] <= rep["bound"] / np.linalg.norm(P.b) * (1 + 1e-6)
