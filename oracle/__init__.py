@@ -239,18 +239,18 @@ def gmres(At, M, rhs, thr, restart=50, maxit=500):
 
 def block_gmres(At, M, B, thr, restart=50, maxit=500):
     """Block GMRES(restart) on A~ M Z = B (n x k), Y = M Z; thr: k thresholds.
-    Returns (Y (n x k), block steps, status)."""
+    Returns (Y (n x k), block steps per column, status)."""
     a, m = _In(At), _In(M)
     B = np.asfortranarray(B, dtype=np.float64)
     n, k = B.shape
     thr = np.ascontiguousarray(thr, dtype=np.float64)
     Y = np.zeros((n, k), order="F")
-    it = C.c_int32()
+    it = np.zeros(k, np.int32)
     st = lib().orc_block_gmres(C.byref(a.s), C.byref(m.s), int(k), _ptr(B, _f64p), _ptr(thr, _f64p), int(restart),
-                               int(maxit), _ptr(Y, _f64p), C.byref(it))
+                               int(maxit), _ptr(Y, _f64p), _ptr(it, _i32p))
     if st == BAD_INPUT:
         raise OracleError("block_gmres", st)
-    return Y, it.value, st
+    return Y, it, st
 
 
 def smw(yhat, W, J):

@@ -204,12 +204,13 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
 
 /* Block GMRES(m) with right preconditioning on A~ M Z = B, Y = M Z, for the
  * k right-hand sides of B (n x k column-major); Y (n x k column-major) out.
- * Each column c stops at ||B e_c - A~ Y e_c|| < thr[c] (the least-squares
- * estimate inside a cycle, the true residual at a cycle start); the cycle's
- * block steps stop when every column meets its threshold. *iters = block
- * steps in all (each applies A~ and M to k vectors). Returns ORC_OK,
- * ORC_MAXITER (maxit block steps) or ORC_BREAKDOWN (a zero pivot of the
- * reduced block Hessenberg matrix). */
+ * At each cycle start a column whose true residual ||B e_c - A~ Y e_c|| is
+ * below thr[c] is frozen and the others form the cycle's block; the
+ * cycle's block steps stop when every column's least-squares residual is
+ * below its threshold (or after m steps). iters[c] (k entries) = the block
+ * steps column c took part in. Returns ORC_OK, ORC_MAXITER (maxit block
+ * steps) or ORC_BREAKDOWN (a zero pivot of the reduced block Hessenberg
+ * matrix). */
 int orc_block_gmres(const orc_csc* At, const orc_csc* M, int32_t k, const double* B, const double* thr, int32_t m,
                     int32_t maxit, double* Y, int32_t* iters);
 

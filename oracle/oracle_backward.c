@@ -103,7 +103,7 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
         double* Bblk = prm->krylov == 4 ? (double*)orc_xmalloc((size_t)(s + 1) * (size_t)n * sizeof(double)) : NULL;
         double* blk_thr = prm->krylov == 4 ? (double*)orc_xmalloc((size_t)(s + 1) * sizeof(double)) : NULL;
         int blk_st = ORC_OK;
-        int32_t blk_it = 0;
+        int32_t* blk_it = prm->krylov == 4 ? (int32_t*)orc_xcalloc((size_t)(s + 1), sizeof(int32_t)) : NULL;
         rep->status = ORC_OK;
         for (int32_t q = 0; q <= s && st == ORC_OK; ++q) {
             double thr;
@@ -128,10 +128,10 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
                         bt[J[t - 1]] = 1.0;
                         blk_thr[t] = prm->eps * gnorm / (2.0 * sqrt((double)s));
                     }
-                    blk_st = orc_block_gmres(&AtT, &MT, s + 1, Bblk, blk_thr, prm->restart, prm->maxit, Y, &blk_it);
+                    blk_st = orc_block_gmres(&AtT, &MT, s + 1, Bblk, blk_thr, prm->restart, prm->maxit, Y, blk_it);
                 }
                 ks = blk_st;
-                it = blk_it;
+                it = blk_it[q];
             } else if (prm->krylov == 0) ks = orc_bicgstab(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 2) ks = orc_cgs(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
             else if (prm->krylov == 3) ks = orc_bicg(&AtT, &MT, rhs, thr, prm->maxit, Y + (size_t)q * n, &it);
@@ -165,6 +165,7 @@ int orc_backward(const orc_csc* A, const double* x, const double* g, const orc_s
         free(rhs);
         free(Bblk);
         free(blk_thr);
+        free(blk_it);
     }
     free(loops);
     free(res);
