@@ -387,6 +387,21 @@ def run_ours(args):
     _, _, prof = timed(OPT_KW, 1, True)
     ms_plain, reps_plain, _ = timed(PLAIN_KW, max(1, min(args.steps, 3)), False)
     value = ws * 2 * n / (ms_step / 1e3)
+    # the block Krylov alternative on the same SPAI systems: block GMRES(50)
+    # in the refined and the plain FP64 form, one solve each after one warm-up
+    blk = {}
+    for form, fkw in (("refined", dict(krylov_precision=1)), ("fp64", dict(krylov_precision=0))):
+        kw = dict(SPAI_KW, **dict(KRYLOV_KW, krylov="bgmres"), **fkw)
+        sai.solve(dA, b, **kw)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it_b, rep_b = sai.solve(dA, b, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        blk[form] = {"ms": e0.elapsed_time(e1), "krylov_ms": rep_b["ms_krylov"], "block_steps": it_b,
+                     "rr": rep_b["rr"], "status_ok": rep_b["status"] == sai.SAI_OK}
 
     # e2e: public API from pinned host buffers, copies inside the timing
     hA = [torch.as_tensor(a).pin_memory() for a in (A.indptr.astype(np.int64), A.indices.astype(np.int32),
@@ -435,6 +450,7 @@ def run_ours(args):
                        "iters": {k: r[1] for k, r in zip(("spai", "psai"), reps_plain[-1])},
                        "rr": {k: r[2]["rr"] for k, r in zip(("spai", "psai"), reps_plain[-1])}},
         "vs_plain_fp64": ms_plain / ms_step,
+        "block_gmres_spai": blk,
         "roofline": roofline(prof, peaks),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": float(np.mean(e2e_ms))},

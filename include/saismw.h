@@ -264,16 +264,24 @@ sai_status sai_precond_create(const sai_csc_view* M, sai_stream_t stream, sai_pr
  * residual estimate and restarts from the true residual; CGS (conjugate
  * gradient squared, two applications of A~ M per iteration) and BiCG (one
  * application of A~ M and one of its transpose M^T A~^T per iteration) test
- * the recursive residual after each iteration.
+ * the recursive residual after each iteration. Block GMRES(restart)
+ * (SAI_BGMRES, the block Krylov alternative named after Theorem 2) runs the
+ * systems still active at a cycle start as one block of a shared block
+ * Krylov space (block Arnoldi with two passes of block classical
+ * Gram-Schmidt and a shifted Cholesky QR of each new block, Householder
+ * reduction of the block Hessenberg matrix); it tests every system's
+ * least-squares residual after each block step, ends the cycle when all
+ * meet their thresholds and restarts from the true residuals; iters counts
+ * block steps (each applies A~ and M to every active system).
  * ---------------------------------------------------------------------- */
-typedef enum { SAI_BICGSTAB = 0, SAI_GMRES = 1, SAI_CGS = 2, SAI_BICG = 3 } sai_krylov_method;
+typedef enum { SAI_BICGSTAB = 0, SAI_GMRES = 1, SAI_CGS = 2, SAI_BICG = 3, SAI_BGMRES = 4 } sai_krylov_method;
 
 typedef struct {
     int32_t method;
-    int32_t restart;   /* GMRES(m); ignored by BiCGStab */
+    int32_t restart;   /* GMRES(m) and block GMRES(m), 1..255; ignored by the others */
     int32_t maxit;     /* paper: 500 */
-    int32_t precision; /* SAI_FP64, or SAI_FP32_REFINE64 (GMRES only): FP32 inner
-                          GMRES solves of A~ d = r/||r|| refined in FP64 --
+    int32_t precision; /* SAI_FP64, or SAI_FP32_REFINE64 (GMRES and block GMRES):
+                          FP32 inner solves of A~ d = r/||r|| refined in FP64 --
                           r = b - A~ x, x += ||r|| d and every stop test in FP64;
                           maxit then bounds the total inner iterations */
     double inner_tol;  /* relative inner tolerance of the refined form; <= 0 -> 1e-4 */
@@ -283,8 +291,9 @@ typedef struct {
 } sai_krylov_params;
 
 /* B, X: n x k row-major device blocks. thr, iters, status: host arrays of k.
- * k: 1..256 for GMRES and the refined form; 1..262144 for FP64 BiCGStab,
- * CGS and BiCG (SAI_INVALID_ARG beyond). The solver keeps about 10 n x k FP64 blocks of
+ * k: 1..256 for GMRES and its refined form; 1..32 for block GMRES (FP64,
+ * or refined: FP32 inner block solves, FP64 outside, as for GMRES);
+ * 1..262144 for FP64 BiCGStab, CGS and BiCG (SAI_INVALID_ARG beyond). The solver keeps about 10 n x k FP64 blocks of
  * its own (BiCGStab) and returns SAI_OOM when they do not fit.
  * Returns SAI_OK, SAI_MAXITER or SAI_BREAKDOWN (the first non-OK system
  * status), or an error. Synchronises the stream. */

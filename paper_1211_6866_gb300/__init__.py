@@ -24,8 +24,8 @@ _LIBPATH = os.path.join(_HERE, "libsaismw.so")
 
 SAI_OK, SAI_INVALID_ARG, SAI_CUDA_ERROR, SAI_OOM, SAI_PATTERN_OVERFLOW, SAI_MAXITER, SAI_BREAKDOWN, \
     SAI_SINGULAR, SAI_NOT_IMPLEMENTED = range(9)
-BICGSTAB, GMRES, CGS, BICG = 0, 1, 2, 3
-_METHOD = {"bicgstab": BICGSTAB, "gmres": GMRES, "cgs": CGS, "bicg": BICG}
+BICGSTAB, GMRES, CGS, BICG, BGMRES = 0, 1, 2, 3, 4
+_METHOD = {"bicgstab": BICGSTAB, "gmres": GMRES, "cgs": CGS, "bicg": BICG, "bgmres": BGMRES}
 
 
 class SaiError(RuntimeError):

@@ -2299,6 +2299,563 @@ sai_status gm_work_alloc(size_t blk, int m, Buf& vb, Buf& wb, GmWork<T>& Wk, cud
     return SAI_OK;
 }
 
+// ------------------------------------------------------------------ block GMRES(m)
+// The block Krylov alternative for the s+1 systems (section 3, after
+// Theorem 2): block GMRES (Vital) with right preconditioning, FP64. The kb
+// systems still active at a cycle start share one block Krylov space of
+// A~M; their compact positions a = 0..kb-1 map to systems lact[1+a]. The
+// basis blocks V_0, V_1, .. (kb vectors each) follow one another, so basis
+// vector b = j*kb + a sits at V + b*ld and any leading part of the basis is
+// one contiguous range. One block step:
+//   T = M V_j, W = A~ T                  (the SpMV of the other solvers)
+//   H = V^T W, W -= V H, twice           (block classical Gram-Schmidt)
+//   W = V_{j+1} R                        (shifted Cholesky QR, three passes:
+//                                         Fukaya, Kannan, Nakatsukasa,
+//                                         Yamamoto, Yanagisawa 2020)
+//   one block reduces the new block column of Hbar with Householder
+//   reflections on rows q..q+kb of each column q, applies them to G and
+//   tests every column's least-squares residual against its threshold.
+// At a cycle end Y = Rtri^{-1} G_top, X[lact] += M (V Y), R = B - A~ X.
+// In exact arithmetic the iterates are those of block GMRES with block
+// modified Gram-Schmidt and Householder QR.
+
+constexpr int BG_KMAX = 32;  // largest block (systems per block)
+constexpr int BG_CR = 1024;  // rows per chunk of the Gram kernel
+constexpr int BG_GV = 8;     // basis vectors per Gram block (one per warp)
+constexpr int BG_UT = 256;   // threads (rows) per block of the update kernels
+constexpr int BG_HB = 64;    // rows of H staged at a time by the update kernel
+
+template <class T>
+struct Bg {
+    T *V, *T1, *Z, *R;      // basis ((m+1)*k vectors of ld), work blocks and residuals of k vectors (type T)
+    double *Hb;             // Hbar, column-major, ldh = (m+1)*k rows, m*k columns
+    double *hv, *hbeta;     // reflector of column q: hv[q*(k+1) + l], l = 0..kb; its beta
+    double *G;              // (m+1)*k x k, column-major (ldh)
+    double *Ys;             // the cycle's solution coefficients, m*k x k, column-major (ld m*k)
+    double *Rt, *Rp;        // k x k column-major: R of the QR (product of passes), one pass's R
+    double *Gm;             // k x k Gram matrix of one QR pass
+    double *H1, *H2;        // the two Gram-Schmidt passes' coefficients, nv x kb (ld nv)
+    double *part;           // Gram partials [chunk][b][c]
+    int *lact, *lid;        // active systems (count + ids); identity list (count + 0..kb-1)
+    int *flags;             // [0] every column converged, [1] error, [2] kb
+    int m, k;
+    int64_t ldh;
+};
+
+template <class T, int KB>
+__global__ void __launch_bounds__(BG_GV * 32)
+k_bg_gram(int32_t n, int64_t ld, const T* __restrict__ V, int nv, const T* __restrict__ W, int kb,
+          double* __restrict__ part)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.y * BG_GV + warp;
+    if (b >= nv) return;
+    const int64_t r0 = (int64_t)blockIdx.x * BG_CR;
+    const int64_t r1 = r0 + BG_CR < n ? r0 + BG_CR : n;
+    T acc[KB];
+#pragma unroll
+    for (int c = 0; c < KB; ++c) acc[c] = 0;
+    const T* v = V + (int64_t)b * ld;
+    for (int64_t r = r0 + lane; r < r1; r += 32) {
+        const T x = v[r];
+#pragma unroll
+        for (int c = 0; c < KB; ++c)
+            if (c < kb) acc[c] = fma(x, W[(int64_t)c * ld + r], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < KB; ++c)
+        if (c < kb) {
+            const T s = warp_sum_t(acc[c]);
+            if (lane == 0) part[((int64_t)blockIdx.x * nv + b) * kb + c] = (double)s;
+        }
+}
+
+// H[c*nv + b] = sum over chunks (fixed order) of part[q][b][c]
+__global__ void k_bg_reduce(int nch, int nv, int kb, const double* __restrict__ part, double* __restrict__ H)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nv * kb) return;
+    const int b = t / kb, c = t % kb;
+    double s = 0.0;
+    for (int q = 0; q < nch; ++q) s += part[((int64_t)q * nv + b) * kb + c];
+    H[(int64_t)c * nv + b] = s;
+}
+
+// W -= V H (overwrite = 0) or W = V H (overwrite = 1); H: nv x kb, ld ldhh
+template <class T, int KB>
+__global__ void __launch_bounds__(BG_UT)
+k_bg_update(int32_t n, int64_t ld, const T* __restrict__ V, int nv, const double* __restrict__ H, int ldhh,
+            int kb, T* __restrict__ W, int overwrite)
+{
+    __shared__ T hs[BG_HB * KB];
+    const T sgn = overwrite ? T(1) : T(-1);
+    for (int64_t base = (int64_t)blockIdx.x * BG_UT; base < n; base += (int64_t)gridDim.x * BG_UT) {
+        const int64_t r = base + threadIdx.x;
+        const bool ok = r < n;
+        T acc[KB];
+#pragma unroll
+        for (int c = 0; c < KB; ++c) acc[c] = (!overwrite && ok && c < kb) ? W[(int64_t)c * ld + r] : T(0);
+        for (int b0 = 0; b0 < nv; b0 += BG_HB) {
+            const int bl = nv - b0 < BG_HB ? nv - b0 : BG_HB;
+            __syncthreads();
+            for (int e = threadIdx.x; e < bl * KB; e += BG_UT) {
+                const int t = e / KB, c = e % KB;
+                hs[e] = c < kb ? (T)H[(int64_t)c * ldhh + b0 + t] : T(0);
+            }
+            __syncthreads();
+            if (ok)
+                for (int t = 0; t < bl; ++t) {
+                    const T x = sgn * V[(int64_t)(b0 + t) * ld + r];
+#pragma unroll
+                    for (int c = 0; c < KB; ++c) acc[c] = fma(x, hs[t * KB + c], acc[c]);
+                }
+        }
+        if (ok)
+#pragma unroll
+            for (int c = 0; c < KB; ++c)
+                if (c < kb) W[(int64_t)c * ld + r] = acc[c];
+    }
+}
+
+// one QR pass's Cholesky factor: Gm (+ shift on the first pass) = Rp^T Rp,
+// Rt = Rp Rt (Rt = Rp on the first pass); a pivot <= 0 sets flags[1]
+__global__ void __launch_bounds__(1024) k_bg_chol(int kb, double leff, double unit, const double* __restrict__ Gm,
+                                                  double* Rp, double* Rt, int first, int* flags)
+{
+    __shared__ double a[BG_KMAX][BG_KMAX + 1];
+    __shared__ double rt[BG_KMAX][BG_KMAX + 1];
+    __shared__ double sh;
+    const int t = threadIdx.x;
+    const int i = t / BG_KMAX, q = t % BG_KMAX;
+    if (i < kb && q < kb) a[i][q] = Gm[q * kb + i];
+    __syncthreads();
+    if (t == 0) {
+        double tr = 0.0;
+        for (int c = 0; c < kb; ++c) tr += a[c][c];
+        // shift of the first pass: 11 (leff kb + kb (kb + 1)) u ||W||_F^2, leff
+        // the length of the summations that formed Gm, u the unit roundoff
+        sh = first ? 11.0 * (leff * kb + (double)kb * (kb + 1)) * unit * tr : 0.0;
+    }
+    __syncthreads();
+    if (i < kb && i == q) a[i][i] += sh;
+    __syncthreads();
+    for (int p = 0; p < kb; ++p) {
+        if (t == 0) {
+            double d = a[p][p];
+            if (!(d > 0.0)) {
+                atomicExch(&flags[1], 1);
+                d = 1.0;
+            }
+            a[p][p] = sqrt(d);
+        }
+        __syncthreads();
+        if (t > p && t < kb) a[p][t] /= a[p][p];
+        __syncthreads();
+        if (i > p && i < kb && q >= i && q < kb) a[i][q] -= a[p][i] * a[p][q];
+        __syncthreads();
+    }
+    // a's upper triangle is Rp
+    if (i < kb && q < kb) {
+        const double r = q >= i ? a[i][q] : 0.0;
+        Rp[q * kb + i] = r;
+        if (first) Rt[q * kb + i] = r;
+        else rt[i][q] = Rt[q * kb + i];
+    }
+    __syncthreads();
+    if (!first && i < kb && q < kb) {
+        double s = 0.0;
+        for (int u = i; u <= q; ++u) s += a[i][u] * rt[u][q];
+        Rt[q * kb + i] = q >= i ? s : 0.0;
+    }
+}
+
+// W = W Rp^{-1}, row by row
+template <class T, int KB>
+__global__ void __launch_bounds__(BG_UT) k_bg_trsm(int32_t n, int64_t ld, T* __restrict__ W, int kb,
+                                                   const double* __restrict__ Rp)
+{
+    __shared__ T r[KB * KB];
+    for (int e = threadIdx.x; e < KB * KB; e += BG_UT) {
+        const int i = e % KB, q = e / KB;
+        r[e] = (i < kb && q < kb) ? (T)Rp[q * kb + i] : T(1);
+    }
+    __syncthreads();
+    for (int64_t row = (int64_t)blockIdx.x * BG_UT + threadIdx.x; row < n; row += (int64_t)gridDim.x * BG_UT) {
+        T y[KB];
+#pragma unroll
+        for (int c = 0; c < KB; ++c) {
+            if (c < kb) {
+                T s = W[(int64_t)c * ld + row];
+#pragma unroll
+                for (int i = 0; i < c; ++i) s -= y[i] * r[c * KB + i];
+                y[c] = s / r[c * KB + c];
+                W[(int64_t)c * ld + row] = y[c];
+            } else {
+                y[c] = 0;
+            }
+        }
+    }
+}
+
+// the reflector of column q (rows q..q+kb, hv[0..kb], beta) applied by one
+// warp to the column x (rows q..q+kb of a column-major array)
+__device__ __forceinline__ void bg_reflect(const double* __restrict__ v, double beta, double* x, int kb, int lane)
+{
+    double d = 0.0;
+    for (int l = lane; l <= kb; l += 32) d = fma(v[l], x[l], d);
+    d = warp_sum(d) * beta;
+    for (int l = lane; l <= kb; l += 32) x[l] -= d * v[l];
+    __syncwarp();
+}
+
+// block step j: assemble the new block column of Hbar, reduce it, update G,
+// test each column; one block of 32 * BG_KMAX threads, warp a owns column a
+template <class T>
+__global__ void __launch_bounds__(32 * BG_KMAX) k_bg_lsq(int j, Bg<T> B, Sys S, const int* __restrict__ cap)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kb = B.flags[2];
+    const int nv = (j + 1) * kb;
+    const int64_t ldh = B.ldh;
+    double* col = B.Hb + (int64_t)(j * kb + (warp < kb ? warp : 0)) * ldh;
+    if (warp < kb) {
+        for (int i = lane; i < nv; i += 32)
+            col[i] = B.H1[(int64_t)warp * nv + i] + B.H2[(int64_t)warp * nv + i];
+        for (int i = lane; i < kb; i += 32) col[nv + i] = i <= warp ? B.Rt[warp * kb + i] : 0.0;
+        __syncwarp();
+        // the earlier reflections, in order
+        for (int q = 0; q < j * kb; ++q) bg_reflect(B.hv + (int64_t)q * (B.k + 1), B.hbeta[q], col + q, kb, lane);
+    }
+    __syncthreads();
+    for (int a = 0; a < kb; ++a) {
+        const int q = j * kb + a;
+        double* hvq = B.hv + (int64_t)q * (B.k + 1);
+        if (warp == a) {
+            double* x = B.Hb + (int64_t)q * ldh + q;
+            double ss = 0.0;
+            for (int l = lane; l <= kb; l += 32) ss = fma(x[l], x[l], ss);
+            const double nrm = sqrt(warp_sum(ss));
+            const double x0 = x[0];
+            __syncwarp();
+            if (nrm == 0.0) {
+                for (int l = lane; l <= kb; l += 32) hvq[l] = 0.0;
+                if (lane == 0) B.hbeta[q] = 0.0;
+            } else {
+                const double alpha = x0 >= 0.0 ? -nrm : nrm;
+                double vv = 0.0;
+                for (int l = lane; l <= kb; l += 32) {
+                    const double vl = l == 0 ? x0 - alpha : x[l];
+                    hvq[l] = vl;
+                    vv = fma(vl, vl, vv);
+                }
+                vv = warp_sum(vv);
+                __syncwarp();
+                for (int l = lane; l <= kb; l += 32) x[l] = l == 0 ? alpha : 0.0;
+                if (lane == 0) B.hbeta[q] = 2.0 / vv;
+            }
+        }
+        __syncthreads();
+        if (warp < kb) {
+            const double beta = B.hbeta[q];
+            if (warp > a) bg_reflect(hvq, beta, B.Hb + (int64_t)(j * kb + warp) * ldh + q, kb, lane);
+            bg_reflect(hvq, beta, B.G + (int64_t)warp * ldh + q, kb, lane);
+        }
+        __syncthreads();
+    }
+    // least-squares residual of each column: G rows (j+1)kb .. (j+2)kb-1;
+    // a system that used up its iterations ends the cycle too
+    __shared__ int nconv, ncap;
+    if (threadIdx.x == 0) {
+        nconv = 0;
+        ncap = 0;
+    }
+    __syncthreads();
+    if (warp < kb) {
+        const double* g = B.G + (int64_t)warp * ldh + nv;
+        double e = 0.0;
+        for (int l = lane; l < kb; l += 32) e = fma(g[l], g[l], e);
+        e = warp_sum(e);
+        if (lane == 0) {
+            const int c = B.lact[1 + warp];
+            S.iters[c] += 1;
+            if (sqrt(e) < S.thr[c]) atomicAdd(&nconv, 1);
+            if (S.iters[c] >= cap[c]) atomicAdd(&ncap, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) B.flags[0] = nconv == kb || ncap > 0;
+}
+
+// Ys = Rtri^{-1} G_top, nt = (steps) * kb rows; warp c solves column c
+template <class T>
+__global__ void __launch_bounds__(32 * BG_KMAX) k_bg_backsolve(int nt, Bg<T> B)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kb = B.flags[2];
+    if (warp >= kb) return;
+    const int64_t ldh = B.ldh, ldy = (int64_t)B.m * B.k;
+    double* y = B.Ys + (int64_t)warp * ldy;
+    const double* g = B.G + (int64_t)warp * ldh;
+    for (int i = nt - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int q = i + 1 + lane; q < nt; q += 32) s = fma(B.Hb[(int64_t)q * ldh + i], y[q], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            const double d = B.Hb[(int64_t)i * ldh + i];
+            if (d == 0.0) {
+                atomicExch(&B.flags[1], 2);
+                y[i] = 0.0;
+            } else {
+                y[i] = (g[i] - s) / d;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// cycle start: true residual norms (partials of the listed systems), stop
+// tests, the active list and its identity list; flags[2] = kb
+template <class T>
+__global__ void k_bg_cycle(int k, int nch, const double* part, const int* __restrict__ cap, int first, Sys S,
+                           Bg<T> B)
+{
+    __shared__ int act[CTRL];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (first) {
+            S.iters[c] = 0;
+            S.status[c] = ST_MAXITER;
+            S.active[c] = 1;
+        }
+        act[c] = 0;
+        if (S.active[c]) {
+            const double r = sqrt(sum_chunks(part, 0, c, k, nch));
+            if (r < S.thr[c]) {
+                S.active[c] = 0;
+                S.status[c] = ST_OK;
+            } else if (S.iters[c] >= cap[c] || B.flags[1]) {
+                S.active[c] = 0;
+                S.status[c] = B.flags[1] ? ST_BREAKDOWN : ST_MAXITER;
+            } else {
+                act[c] = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        build_list(k, act, B.lact);
+        const int kb = B.lact[0];
+        B.lid[0] = kb;
+        for (int a = 0; a < kb; ++a) B.lid[1 + a] = a;
+        B.flags[2] = kb;
+        B.flags[0] = 0;
+    }
+}
+
+// V0[a] = R[lact[a]] and X[lact[a]] += T[a]
+template <class T>
+__global__ void k_bg_gather(int32_t n, int64_t ld, const int* __restrict__ lact, const T* __restrict__ R,
+                            T* __restrict__ V0)
+{
+    const int kb = lact[0];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)kb * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / n);
+        const int64_t r = e % n;
+        V0[(int64_t)a * ld + r] = R[(int64_t)lact[1 + a] * ld + r];
+    }
+}
+
+template <class T>
+__global__ void k_bg_scatter_add(int32_t n, int64_t ld, const int* __restrict__ lact, const T* __restrict__ Tv,
+                                 T* __restrict__ X)
+{
+    const int kb = lact[0];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)kb * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / n);
+        const int64_t r = e % n;
+        X[(int64_t)lact[1 + a] * ld + r] += Tv[(int64_t)a * ld + r];
+    }
+}
+
+// the kernels specialised on the block size: KB = the smallest of 4, 8, 12,
+// 16, 24, 32 that holds kb
+#define BG_DISPATCH(kb, F, T, ...)                               \
+    do {                                                         \
+        if ((kb) <= 4) F<T, 4>__VA_ARGS__;                       \
+        else if ((kb) <= 8) F<T, 8>__VA_ARGS__;                  \
+        else if ((kb) <= 12) F<T, 12>__VA_ARGS__;                \
+        else if ((kb) <= 16) F<T, 16>__VA_ARGS__;                \
+        else if ((kb) <= 24) F<T, 24>__VA_ARGS__;                \
+        else F<T, 32>__VA_ARGS__;                                \
+    } while (0)
+
+// P = V^T W (nv basis vectors from V, kb columns of W) into H (nv x kb)
+template <class T>
+void bg_gram(int32_t n, int64_t ld, const T* V, int nv, const T* W, int kb, double* part, double* H,
+             cudaStream_t st)
+{
+    const int nch = (int)(((int64_t)n + BG_CR - 1) / BG_CR);
+    const dim3 grid((unsigned)nch, (unsigned)((nv + BG_GV - 1) / BG_GV));
+    sai_count_grid(grid.x * grid.y);
+    BG_DISPATCH(kb, k_bg_gram, T, <<<grid, BG_GV * 32, 0, st>>>(n, ld, V, nv, W, kb, part));
+    k_bg_reduce<<<SAI_GRID(sai_div_up((int64_t)nv * kb, 256)), 256, 0, st>>>(nch, nv, kb, part, H);
+}
+
+unsigned bg_rows_grid(int32_t n)
+{
+    int64_t g = ((int64_t)n + BG_UT - 1) / BG_UT;
+    if (g > (int64_t)g_sms * 8) g = (int64_t)g_sms * 8;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+template <class T>
+void bg_update(int32_t n, int64_t ld, const T* V, int nv, const double* H, int ldhh, int kb, T* W, int overwrite,
+               cudaStream_t st)
+{
+    const unsigned g = bg_rows_grid(n);
+    sai_count_grid(g);
+    BG_DISPATCH(kb, k_bg_update, T, <<<g, BG_UT, 0, st>>>(n, ld, V, nv, H, ldhh, kb, W, overwrite));
+}
+
+// W = Q R: shifted Cholesky QR in three passes, R accumulated in B.Rt. The
+// Gram matrices sum BG_CR/32 products per lane and 5 shuffle levels in T,
+// then the chunks in FP64 (counted too when T is FP64).
+template <class T>
+void bg_qr(int32_t n, int64_t ld, T* W, int kb, const Bg<T>& B, cudaStream_t st)
+{
+    const unsigned g = bg_rows_grid(n);
+    const double unit = sizeof(T) == 4 ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    const double leff = BG_CR / 32 + 5 + (sizeof(T) == 8 ? ((int64_t)n + BG_CR - 1) / BG_CR : 1);
+    for (int pass = 0; pass < 3; ++pass) {
+        bg_gram<T>(n, ld, W, kb, W, kb, B.part, B.Gm, st);
+        k_bg_chol<<<SAI_GRID(1), 1024, 0, st>>>(kb, leff, unit, B.Gm, B.Rp, B.Rt, pass == 0, B.flags);
+        sai_count_grid(g);
+        BG_DISPATCH(kb, k_bg_trsm, T, <<<g, BG_UT, 0, st>>>(n, ld, W, kb, B.Rp));
+    }
+}
+
+// Block GMRES(m) over the k systems with finite thresholds (vectors in T,
+// the small matrices in FP64); system c stops at S.thr[c] or after cap[c]
+// block steps; S.iters counts the block steps each system took part in.
+template <class T>
+sai_status bgmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs, T* Xs, T* R, Bg<T>& B, Sys& S,
+                      const int* cap, double* pt2, const Dims& D, cudaStream_t st)
+{
+    const int32_t n = I.n;
+    const int64_t ld = I.ld;
+    const int ib = item_blocks(n > 0 ? n : 1, k);
+    const unsigned gg = bg_rows_grid(n) * 4;
+    k_gm_init<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bs, Xs, R, S.lall, pt2);
+    SAI_CUDA(cudaMemsetAsync(B.flags, 0, sizeof(int) * 4, st));
+    int h[3] = {0, 0, 0};
+    for (int first = 1;; first = 0) {
+        k_bg_cycle<T><<<SAI_GRID(1), CTRL, 0, st>>>(k, I.nch, pt2, cap, first, S, B);
+        SAI_CUDA(cudaMemcpyAsync(h, B.flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaStreamSynchronize(st));
+        const int kb = h[2];
+        if (kb == 0) break;
+        // V_0 R = the active residuals; G = [R; 0]
+        k_bg_gather<T><<<SAI_GRID(gg), 256, 0, st>>>(n, ld, B.lact, R, B.V);
+        bg_qr<T>(n, ld, B.V, kb, B, st);
+        SAI_CUDA(cudaMemsetAsync(B.G, 0, sizeof(double) * (size_t)B.ldh * B.k, st));
+        SAI_CUDA(cudaMemcpy2DAsync(B.G, sizeof(double) * B.ldh, B.Rt, sizeof(double) * kb, sizeof(double) * kb, kb,
+                                   cudaMemcpyDeviceToDevice, st));
+        int steps = 0;
+        for (int j = 0; j < m; ++j) {
+            const T* Vj = B.V + (int64_t)j * kb * ld;
+            T* Vn = B.V + (int64_t)(j + 1) * kb * ld;
+            const int nv = (j + 1) * kb;
+            {
+                ProfScope ps(D.site_spmm, st);
+                spmv<T, 0>(n, ld, A.M, kb, Vj, B.T1, nullptr, B.lid, st);
+            }
+            {
+                ProfScope ps(D.site_spmm, st);
+                spmv<T, 0>(n, ld, A.A, kb, B.T1, Vn, nullptr, B.lid, st);
+            }
+            for (int pass = 0; pass < 2; ++pass) {
+                double* H = pass ? B.H2 : B.H1;
+                {
+                    ProfScope ps(D.site_dots, st);
+                    bg_gram<T>(n, ld, B.V, nv, Vn, kb, B.part, H, st);
+                }
+                {
+                    ProfScope ps(D.site_upd, st);
+                    bg_update<T>(n, ld, B.V, nv, H, nv, kb, Vn, 0, st);
+                }
+            }
+            {
+                ProfScope ps(PROF_GM_STEP, st);
+                bg_qr<T>(n, ld, Vn, kb, B, st);
+                k_bg_lsq<T><<<SAI_GRID(1), 32 * BG_KMAX, 0, st>>>(j, B, S, cap);
+            }
+            SAI_CUDA(cudaGetLastError());
+            SAI_CUDA(cudaMemcpyAsync(h, B.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            steps = j + 1;
+            if (h[0] || h[1]) break;
+        }
+        // X[lact] += M (V Ys), R = B - A~ X
+        k_bg_backsolve<T><<<SAI_GRID(1), 32 * BG_KMAX, 0, st>>>(steps * kb, B);
+        bg_update<T>(n, ld, B.V, steps * kb, B.Ys, m * B.k, kb, B.Z, 1, st);
+        spmv<T, 0>(n, ld, A.M, kb, B.Z, B.T1, nullptr, B.lid, st);
+        k_bg_scatter_add<T><<<SAI_GRID(gg), 256, 0, st>>>(n, ld, B.lact, B.T1, Xs);
+        spmv<T, 1>(n, ld, A.A, k, Xs, R, Bs, B.lact, st);
+        k_norm2<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, R, B.lact, pt2);
+        SAI_CUDA(cudaGetLastError());
+    }
+    return SAI_OK;
+}
+
+template <class T>
+sai_status bg_alloc(int k, int m, int32_t n, int64_t ld, Buf& vb, Buf& hb, Buf& ib, Bg<T>& B, cudaStream_t st)
+{
+    B.m = m;
+    B.k = k;
+    B.ldh = (int64_t)(m + 1) * k;
+    const size_t blk = (size_t)ld * k;
+    // basis, two work blocks and the residual block R of the caller
+    SAI_TRY(vb.alloc(sizeof(T) * (blk * (size_t)(m + 1) + 3 * blk) + 64, st, true));
+    SAI_CUDA(cudaMemsetAsync(vb.p, 0, sizeof(T) * (blk * (size_t)(m + 1) + 3 * blk), st));
+    T* d = vb.as<T>();
+    B.V = d;
+    B.T1 = d + blk * (m + 1);
+    B.Z = B.T1 + blk;
+    B.R = B.Z + blk;
+    const int nch = (int)(((int64_t)(n > 0 ? n : 1) + BG_CR - 1) / BG_CR);
+    const size_t nvmax = (size_t)B.ldh;
+    const size_t hsz = (size_t)B.ldh * m * k + (size_t)m * k * (k + 1) + (size_t)m * k + (size_t)B.ldh * k +
+                       (size_t)m * k * k + 3 * (size_t)k * k + 2 * nvmax * k + (size_t)nch * nvmax * k;
+    SAI_TRY(hb.alloc(sizeof(double) * hsz, st, true));
+    SAI_CUDA(cudaMemsetAsync(hb.p, 0, sizeof(double) * hsz, st));
+    double* e = hb.as<double>();
+    B.Hb = e;
+    e += (size_t)B.ldh * m * k;
+    B.hv = e;
+    e += (size_t)m * k * (k + 1);
+    B.hbeta = e;
+    e += (size_t)m * k;
+    B.G = e;
+    e += (size_t)B.ldh * k;
+    B.Ys = e;
+    e += (size_t)m * k * k;
+    B.Rt = e;
+    B.Rp = e + k * k;
+    B.Gm = e + 2 * k * k;
+    e += 3 * (size_t)k * k;
+    B.H1 = e;
+    B.H2 = e + nvmax * k;
+    e += 2 * nvmax * k;
+    B.part = e;
+    SAI_TRY(ib.alloc(sizeof(int) * (2 * (size_t)(k + 1) + 4), st, true));
+    SAI_CUDA(cudaMemsetAsync(ib.p, 0, sizeof(int) * (2 * (size_t)(k + 1) + 4), st));
+    B.lact = ib.as<int>();
+    B.lid = B.lact + (k + 1);
+    B.flags = B.lid + (k + 1);
+    return SAI_OK;
+}
+
 }  // namespace
 
 sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t k, const double* B,
@@ -2309,13 +2866,17 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     const bool big_ok =
         (prm->method == SAI_BICGSTAB || prm->method == SAI_CGS || prm->method == SAI_BICG) && prm->precision == SAI_FP64;
     if (k > (big_ok ? KBIG : CTRL)) return SAI_INVALID_ARG;
-    if (prm->maxit < 0 || (prm->method == SAI_GMRES && (prm->restart < 1 || prm->restart >= GM_MAXM)))
+    if (prm->maxit < 0 || ((prm->method == SAI_GMRES || prm->method == SAI_BGMRES) &&
+                           (prm->restart < 1 || prm->restart >= GM_MAXM)))
         return SAI_INVALID_ARG;
-    if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES && prm->method != SAI_CGS && prm->method != SAI_BICG)
+    if (prm->method != SAI_BICGSTAB && prm->method != SAI_GMRES && prm->method != SAI_CGS && prm->method != SAI_BICG &&
+        prm->method != SAI_BGMRES)
         return SAI_INVALID_ARG;
+    if (prm->method == SAI_BGMRES && k > BG_KMAX) return SAI_INVALID_ARG;
     if (prm->precision != SAI_FP64 && prm->precision != SAI_FP32_REFINE64) return SAI_INVALID_ARG;
     if (prm->transpose != 0 && prm->transpose != 1) return SAI_INVALID_ARG;
-    if (prm->precision == SAI_FP32_REFINE64 && prm->method != SAI_GMRES) return SAI_NOT_IMPLEMENTED;
+    if (prm->precision == SAI_FP32_REFINE64 && prm->method != SAI_GMRES && prm->method != SAI_BGMRES)
+        return SAI_NOT_IMPLEMENTED;
     const int32_t n = h->n;
     if (n > 0 && (!B || !X)) return SAI_INVALID_ARG;
     if (g_sms == 0) {
@@ -2419,7 +2980,9 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
     k_fill_int<<<SAI_GRID(1), 256, 0, st>>>(k, cap, prm->maxit);
     SAI_CUDA(cudaGetLastError());
 
-    if (prm->method != SAI_GMRES || prm->precision == SAI_FP64) {
+    // sliced-ELL copies for the FP64 solvers; the refined forms build FP32
+    // ones in the same buffers and keep the CSR arrays for the FP64 residual
+    if (prm->precision == SAI_FP64) {
         Ops<double> S64 = A64;
         SAI_TRY(build_sell<double>(n, h->nnz_At, A64.A.rp, A64.A.ci, A64.A.v, sell[0], sell[1], sell[2], S64.A, st));
         SAI_TRY(build_sell<double>(n, P->nnz, A64.M.rp, A64.M.ci, A64.M.v, sell[3], sell[4], sell[5], S64.M, st));
@@ -2449,6 +3012,11 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
             T64.A.v = P->Mr_v.as<double>();
         }
         SAI_TRY(bicg_run(I, k, A64, T64, Bsd, Xsd, S, pt, fl, prm->maxit, D, st));
+    } else if (prm->method == SAI_BGMRES && prm->precision == SAI_FP64) {
+        Bg<double> Bgm;
+        Buf vb, hb, ibuf;
+        SAI_TRY(bg_alloc<double>(k, prm->restart, n, ld, vb, hb, ibuf, Bgm, st));
+        SAI_TRY(bgmres_run<double>(I, k, prm->restart, A64, Bsd, Xsd, Bgm.R, Bgm, S, cap, pt2, D, st));
     } else if (prm->precision == SAI_FP64) {
         Gm G;
         Buf hb, ibuf, vb, wb;
@@ -2463,8 +3031,13 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         Gm G;
         Buf hb, ibuf, vb, wb, a32, m32, r64b, v32b, irb, ird;
         GmWork<float> Wk;
-        SAI_TRY(gm_alloc(k, prm->restart, hb, ibuf, G, st));
-        SAI_TRY(gm_work_alloc<float>(blk, prm->restart, vb, wb, Wk, st));
+        Bg<float> Bgm;  // block GMRES inner solver
+        if (prm->method == SAI_BGMRES) {
+            SAI_TRY(bg_alloc<float>(k, prm->restart, n, ld, vb, hb, ibuf, Bgm, st));
+        } else {
+            SAI_TRY(gm_alloc(k, prm->restart, hb, ibuf, G, st));
+            SAI_TRY(gm_work_alloc<float>(blk, prm->restart, vb, wb, Wk, st));
+        }
         SAI_TRY(a32.alloc(sizeof(float) * (size_t)(h->nnz_At > 0 ? h->nnz_At : 1), st, true));
         SAI_TRY(m32.alloc(sizeof(float) * (size_t)(P->nnz > 0 ? P->nnz : 1), st, true));
         SAI_TRY(r64b.alloc(sizeof(double) * blk + 8, st, true));
@@ -2513,7 +3086,10 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
             SAI_CUDA(cudaStreamSynchronize(st));
             if (!hflag) break;
             k_ir_scale<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, r64, beta, done, r32, S.lall);
-            SAI_TRY(gmres_run<float>(I, k, prm->restart, A32, r32, d32, Wk, S, G, cap, pt, pt2, fl, D32, st));
+            if (prm->method == SAI_BGMRES)
+                SAI_TRY(bgmres_run<float>(I, k, prm->restart, A32, r32, d32, Bgm.R, Bgm, S, cap, pt2, D32, st));
+            else
+                SAI_TRY(gmres_run<float>(I, k, prm->restart, A32, r32, d32, Wk, S, G, cap, pt, pt2, fl, D32, st));
             k_ir_update<<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, Xsd, d32, beta, lir);
             k_ir_total<<<SAI_GRID(1), 32, 0, st>>>(k, lir, S.iters, tot);
             spmv<double, 1>(n, ld, A64.A, k, Xsd, r64, Bsd, lir, st);
