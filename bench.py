@@ -218,15 +218,16 @@ def measured_traffic(site):
     return None
 
 
-def roofline(prof, peaks):
+def roofline(prof, peaks, traffic=True):
     """Dominant profiled site (largest device time): achieved vs its binding peak;
-    every site's figures under "sites"."""
+    every site's figures under "sites". traffic=False when the site's kernels
+    are not the ones the traffic table measured (null traffic)."""
     sites = {k: v for k, v in prof["sites"].items() if v["launches"] > 0 and v["ms"] > 0}
     if not sites:
         return None
     name = max(sites, key=lambda k: sites[k]["ms"])
     r = site_roofline(name, sites[name], peaks)
-    r.update({"kernel": name, "traffic": measured_traffic(name),
+    r.update({"kernel": name, "traffic": measured_traffic(name) if traffic else None,
               "measured": "CUDA events on the first 16 launches of each site and every 7th after, "
                           "one profiled step after the timed steps",
               "sites": {k: dict(ms=round(v["ms"], 3), **{q: (round(x, 4) if isinstance(x, float) else x)
@@ -842,6 +843,110 @@ def run_zerodiag(args):
     return 0
 
 
+GOLDEN_BG = os.path.join(ROOT, "tests", "golden", "oracle_bgmres_m64_s10.json")
+
+
+def bgmres_oracle_sample(P):
+    """The oracle on a bounded sample of the bgmres64 step: split and SPAI
+    build of all n columns timed in full; the block GMRES timed for its first
+    10 block steps and scaled to the complete oracle block solve by the ratio
+    of that sample's time here to the one the oracle-only script
+    tests/golden/make_oracle_bgmres64.py recorded with the complete solve."""
+    import oracle as O
+    import scipy.sparse as sps
+    with open(GOLDEN_BG) as f:
+        gold = json.load(f)
+    t0 = time.perf_counter()
+    J, p, _ = O.detect(P.A)
+    At, U = O.split(P.A, J, p)
+    At = sps.csc_matrix(At)
+    M = sps.csc_matrix(O.spai(At, SPAI_KW["delta"], SPAI_KW["mn"], SPAI_KW["max_aug"])[0])
+    t_setup = time.perf_counter() - t0
+    s = len(J)
+    B = np.hstack([P.b[:, None], sps.csc_matrix(U).toarray()])
+    bn = np.linalg.norm(P.b)
+    thr = np.array([0.5 * 1e-10 * bn] + [1e-10 * bn / (2.0 * np.sqrt(s))] * s)
+    t0 = time.perf_counter()
+    O.block_gmres(At, M, B, thr, restart=50, maxit=gold["sample_steps"])
+    t_sample = time.perf_counter() - t0
+    est = t_setup + gold["krylov_seconds"] * t_sample / gold["sample_seconds"]
+    return {"value": P.n / est, "unit": UNIT, "cores": 1, "kind": "oracle", "est_step_s": est,
+            "sample": "split and SPAI build of all %d columns timed in full; the first %d block GMRES steps timed and "
+                      "the complete oracle block solve (%.0f s, %s block steps, rr %.2e, oracle-written golden file) "
+                      "scaled by that sample's time here against the golden file's"
+                      % (P.n, gold["sample_steps"], gold["krylov_seconds"], max(gold["block_steps"]),
+                         gold["report"]["rr"])}
+
+
+def run_bgmres(args):
+    """Procedure * with block GMRES(50) over the s+1 = 11 systems of the 64^3
+    system (SPAI(0.3, 5, 10), refined forms: FP32 QR + FP64 refinement in the
+    build, FP32 inner block solves refined in FP64), eps = 1e-10."""
+    torch, sai, dist, ws, rank, local = _gpu_setup()
+    P = W.convdiff3d_irregular(seed=W.SEED_BASE + 2 + rank)
+    A, n = P.A, P.n
+    dA = sai.CscMatrix.from_arrays(A.indptr, A.indices, A.data, n)
+    b = torch.as_tensor(P.b, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    kw = dict(SPAI_KW, **dict(KRYLOV_KW, krylov="bgmres"), **OPT_KW)
+
+    def step():
+        return sai.solve(dA, b, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sai.launch_count()
+    ms_step, out, _ = _timed_steps(torch, sai, dist, step, args.steps, flush, label="bench_timed")
+    launches = sai.launch_count() - l0
+    clk = clocks.stop()
+    _, _, prof = _timed_steps(torch, sai, dist, step, 1, flush, profile=True)
+    hA = [torch.as_tensor(a).pin_memory() for a in (A.indptr.astype(np.int64), A.indices.astype(np.int32),
+                                                    A.data.astype(np.float64), P.b)]
+    hx = torch.empty(n, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hA)
+    e2e_ms = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cp, ri, va, bb = (t.to("cuda", non_blocking=True) for t in hA)
+        x, _, _ = sai.solve(sai.CscMatrix(n, cp, ri, va), bb, **kw)
+        hx.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    x, iters, rep = out
+    peaks = load_peaks()
+    cfg = {k: v for k, v in workload_config(P).items() if k != "psai"}
+    cfg.update(workload="bgmres64: the 64^3 convection-diffusion system with ten 5% columns; SPAI(0.3,5,10) with FP32 "
+                        "QR + FP64 refinement, block GMRES(50) over the 11 systems, FP32 inner block solves refined "
+                        "in FP64 to 1e-10; b = A*ones", krylov=dict(KRYLOV_KW, krylov="bgmres"))
+    line = {
+        "metric": "SAI columns/sec of Procedure * with block GMRES(50) over the s+1 systems (64^3)",
+        "value": ws * n / (ms_step / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32", "data": "synthetic", "config": cfg,
+        "stage_ms": {k: rep[k] for k in ("ms_split", "ms_build", "ms_krylov", "ms_smw")},
+        "block_steps": iters, "rr": rep["rr"], "status_ok": rep["status"] == sai.SAI_OK,
+        "roofline": roofline(prof, peaks, traffic=False),
+        "e2e": {"value": ws * n / (float(np.mean(e2e_ms)) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(n * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = bgmres_oracle_sample(P)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -849,7 +954,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="convdiff3d64", choices=["convdiff3d64", "zipf", "batch256", "zerodiag64"])
+    ap.add_argument("--workload", default="convdiff3d64", choices=["convdiff3d64", "zipf", "batch256", "zerodiag64", "bgmres64"])
     ap.add_argument("--zipf-n", type=int, default=100000, help="order of the Zipf-count matrix (--workload zipf)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -860,6 +965,8 @@ def main():
         return run_batch(args)
     if args.workload == "zerodiag64":
         return run_zerodiag(args)
+    if args.workload == "bgmres64":
+        return run_bgmres(args)
     return run_ours(args)
 
 

@@ -2342,43 +2342,64 @@ struct Bg {
     int64_t ldh;
 };
 
+// basis vectors per warp of the Gram kernel: W's row, held in registers,
+// serves that many of them
+__host__ __device__ constexpr int bg_vb(int esz, int KB)
+{
+    return esz == 4 ? (KB <= 12 ? 4 : (KB <= 16 ? 2 : 1)) : (KB <= 8 ? 2 : 1);
+}
+
 template <class T, int KB>
 __global__ void __launch_bounds__(BG_GV * 32)
 k_bg_gram(int32_t n, int64_t ld, const T* __restrict__ V, int nv, const T* __restrict__ W, int kb,
           double* __restrict__ part)
 {
+    constexpr int VB = bg_vb(sizeof(T), KB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.y * BG_GV + warp;
-    if (b >= nv) return;
+    const int b0 = (blockIdx.y * BG_GV + warp) * VB;
+    if (b0 >= nv) return;
     const int64_t r0 = (int64_t)blockIdx.x * BG_CR;
     const int64_t r1 = r0 + BG_CR < n ? r0 + BG_CR : n;
-    T acc[KB];
+    T acc[VB][KB];
 #pragma unroll
-    for (int c = 0; c < KB; ++c) acc[c] = 0;
-    const T* v = V + (int64_t)b * ld;
+    for (int u = 0; u < VB; ++u)
+#pragma unroll
+        for (int c = 0; c < KB; ++c) acc[u][c] = 0;
     for (int64_t r = r0 + lane; r < r1; r += 32) {
-        const T x = v[r];
+        T w[KB];
 #pragma unroll
-        for (int c = 0; c < KB; ++c)
-            if (c < kb) acc[c] = fma(x, W[(int64_t)c * ld + r], acc[c]);
+        for (int c = 0; c < KB; ++c) w[c] = c < kb ? W[(int64_t)c * ld + r] : T(0);
+#pragma unroll
+        for (int u = 0; u < VB; ++u)
+            if (b0 + u < nv) {
+                const T x = V[(int64_t)(b0 + u) * ld + r];
+#pragma unroll
+                for (int c = 0; c < KB; ++c) acc[u][c] = fma(x, w[c], acc[u][c]);
+            }
     }
 #pragma unroll
-    for (int c = 0; c < KB; ++c)
-        if (c < kb) {
-            const T s = warp_sum_t(acc[c]);
-            if (lane == 0) part[((int64_t)blockIdx.x * nv + b) * kb + c] = (double)s;
-        }
+    for (int u = 0; u < VB; ++u)
+        if (b0 + u < nv)
+#pragma unroll
+            for (int c = 0; c < KB; ++c)
+                if (c < kb) {
+                    const T sum = warp_sum_t(acc[u][c]);
+                    if (lane == 0) part[((int64_t)blockIdx.x * nv + b0 + u) * kb + c] = (double)sum;
+                }
 }
 
-// H[c*nv + b] = sum over chunks (fixed order) of part[q][b][c]
+// H[c*nv + b] = the sum over chunks of part[q][b][c]: a warp per (b, c), lane
+// l takes chunks l, l+32, .. in order, then a fixed shuffle tree
 __global__ void k_bg_reduce(int nch, int nv, int kb, const double* __restrict__ part, double* __restrict__ H)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nv * kb) return;
-    const int b = t / kb, c = t % kb;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)nv * kb) return;
+    const int b = (int)(w / kb), c = (int)(w % kb);
     double s = 0.0;
-    for (int q = 0; q < nch; ++q) s += part[((int64_t)q * nv + b) * kb + c];
-    H[(int64_t)c * nv + b] = s;
+    for (int q = lane; q < nch; q += 32) s += part[((int64_t)q * nv + b) * kb + c];
+    s = warp_sum(s);
+    if (lane == 0) H[(int64_t)c * nv + b] = s;
 }
 
 // W -= V H (overwrite = 0) or W = V H (overwrite = 1); H: nv x kb, ld ldhh
@@ -2523,8 +2544,36 @@ __global__ void __launch_bounds__(32 * BG_KMAX) k_bg_lsq(int j, Bg<T> B, Sys S, 
             col[i] = B.H1[(int64_t)warp * nv + i] + B.H2[(int64_t)warp * nv + i];
         for (int i = lane; i < kb; i += 32) col[nv + i] = i <= warp ? B.Rt[warp * kb + i] : 0.0;
         __syncwarp();
-        // the earlier reflections, in order
-        for (int q = 0; q < j * kb; ++q) bg_reflect(B.hv + (int64_t)q * (B.k + 1), B.hbeta[q], col + q, kb, lane);
+        // the earlier reflections, in order. Reflection q touches rows
+        // q..q+kb, so for kb < 32 the kb+1 rows in play sit in the warp's
+        // registers (lane l: row q+l): after reflection q, row q is final and
+        // the window moves down one row; the next reflector and the row that
+        // enters are loaded ahead (neither depends on the reflections so far).
+        const int nq = j * kb;
+        if (kb < 32 && nq > 0) {
+            const int64_t hs = B.k + 1;
+            double x = lane <= kb ? col[lane] : 0.0;
+            double v = lane <= kb ? B.hv[lane] : 0.0;
+            double be = B.hbeta[0];
+            double in = lane == kb ? col[kb + 1] : 0.0;
+            for (int q = 0; q < nq; ++q) {
+                const bool more = q + 1 < nq;
+                const double vn = (more && lane <= kb) ? B.hv[(q + 1) * hs + lane] : 0.0;
+                const double bn = more ? B.hbeta[q + 1] : 0.0;
+                const double inn = (more && lane == kb) ? col[q + kb + 2] : 0.0;
+                const double d = warp_sum(v * x) * be;
+                x -= d * v;
+                if (lane == 0) col[q] = x;
+                const double down = __shfl_down_sync(SAI_FULL, x, 1);
+                x = lane < kb ? down : (lane == kb ? in : 0.0);
+                v = vn;
+                be = bn;
+                in = inn;
+            }
+            if (lane <= kb) col[nq + lane] = x;
+        } else {
+            for (int q = 0; q < nq; ++q) bg_reflect(B.hv + (int64_t)q * (B.k + 1), B.hbeta[q], col + q, kb, lane);
+        }
     }
     __syncthreads();
     for (int a = 0; a < kb; ++a) {
@@ -2678,6 +2727,15 @@ __global__ void k_bg_scatter_add(int32_t n, int64_t ld, const int* __restrict__ 
     }
 }
 
+// algorithmic work of one block-GMRES pass, added to a profile site (only
+// while a profile is open)
+__global__ void k_bg_work(int site, double bytes, double flops) { kwork_add(site, bytes, flops); }
+
+inline void bg_work(int site, double bytes, double flops, cudaStream_t st)
+{
+    if (sai_prof_on()) k_bg_work<<<SAI_GRID(1), 1, 0, st>>>(site, bytes, flops);
+}
+
 // the kernels specialised on the block size: KB = the smallest of 4, 8, 12,
 // 16, 24, 32 that holds kb
 #define BG_DISPATCH(kb, F, T, ...)                               \
@@ -2696,10 +2754,12 @@ void bg_gram(int32_t n, int64_t ld, const T* V, int nv, const T* W, int kb, doub
              cudaStream_t st)
 {
     const int nch = (int)(((int64_t)n + BG_CR - 1) / BG_CR);
-    const dim3 grid((unsigned)nch, (unsigned)((nv + BG_GV - 1) / BG_GV));
+    const int KBs = kb <= 4 ? 4 : kb <= 8 ? 8 : kb <= 12 ? 12 : kb <= 16 ? 16 : kb <= 24 ? 24 : 32;
+    const int per_block = BG_GV * bg_vb((int)sizeof(T), KBs);
+    const dim3 grid((unsigned)nch, (unsigned)((nv + per_block - 1) / per_block));
     sai_count_grid(grid.x * grid.y);
     BG_DISPATCH(kb, k_bg_gram, T, <<<grid, BG_GV * 32, 0, st>>>(n, ld, V, nv, W, kb, part));
-    k_bg_reduce<<<SAI_GRID(sai_div_up((int64_t)nv * kb, 256)), 256, 0, st>>>(nch, nv, kb, part, H);
+    k_bg_reduce<<<SAI_GRID(sai_div_up((int64_t)nv * kb * 32, 256)), 256, 0, st>>>(nch, nv, kb, part, H);
 }
 
 unsigned bg_rows_grid(int32_t n)
@@ -2774,6 +2834,9 @@ sai_status bgmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs
                 ProfScope ps(D.site_spmm, st);
                 spmv<T, 0>(n, ld, A.A, kb, B.T1, Vn, nullptr, B.lid, st);
             }
+            // SpMV: matrix values + column indices once, kb vectors in and out
+            bg_work(D.site_spmm, (D.esz + 4.0) * (D.nnzM + D.nnzA) + 4.0 * D.esz * D.n * kb,
+                    2.0 * (D.nnzM + D.nnzA) * kb, st);
             for (int pass = 0; pass < 2; ++pass) {
                 double* H = pass ? B.H2 : B.H1;
                 {
@@ -2784,6 +2847,9 @@ sai_status bgmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs
                     ProfScope ps(D.site_upd, st);
                     bg_update<T>(n, ld, B.V, nv, H, nv, kb, Vn, 0, st);
                 }
+                // Gram: the nv basis vectors and W once; update: V once, W in and out
+                bg_work(D.site_dots, D.esz * D.n * (nv + kb), 2.0 * D.n * nv * kb, st);
+                bg_work(D.site_upd, D.esz * D.n * (nv + 2.0 * kb), 2.0 * D.n * nv * kb, st);
             }
             {
                 ProfScope ps(PROF_GM_STEP, st);

@@ -19,6 +19,9 @@ rounding.
    oracle's FP64 answer, and at 64^3;
  - limits: more than 32 systems and restart 0 are refused.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -119,10 +122,15 @@ def test_refined_block_gmres_matches_oracle():
     np.testing.assert_allclose(x.cpu().numpy(), xo, rtol=0, atol=1e-6)
 
 
+GOLDEN_BG = os.path.join(os.path.dirname(__file__), "golden", "oracle_bgmres_m64_s10.json")
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_block_gmres_full_size_64cubed(precision):
     """The 64^3 benchmark system (n = 262144, 11 systems), SPAI(0.3, 5, 10),
-    block GMRES(50) in FP64 and in the refined form to eps = 1e-10."""
+    block GMRES(50) in FP64 and in the refined form to eps = 1e-10. The FP64
+    form's block steps per system against the oracle's complete block solve
+    (stored by the oracle-only tests/golden/make_oracle_bgmres64.py), +-1."""
     need_gpu()
     sai = lib()
     P = W.convdiff3d_irregular()
@@ -131,6 +139,11 @@ def test_block_gmres_full_size_64cubed(precision):
     assert rep["status"] == sai.SAI_OK and rep["s"] == 10
     assert rep["rr"] < 1e-10
     np.testing.assert_allclose(x.cpu().numpy(), np.ones(P.n), rtol=0, atol=1e-6)
+    if precision == 0:
+        with open(GOLDEN_BG) as f:
+            gold = json.load(f)
+        assert gold["status"] == O.OK and gold["report"]["rr"] < 1e-10
+        assert all(abs(a - b) <= 1 for a, b in zip(iters, gold["block_steps"])), (iters, gold["block_steps"])
 
 
 def test_block_gmres_limits():
