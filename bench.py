@@ -31,6 +31,16 @@ the metric's unit.
             one sai_solve_batched (per-matrix splits, one SPAI build with FP32
             QR + FP64 refinement, one batched FP64 BiCGStab to 1e-8, batched
             SMW); value = columns of M built per second of the whole batch.
+  zerodiag64  the 64^3 system with a seeded cycle over 5 % of its rows (zeros
+            on the diagonal): step = zero-diagonal repair (maximum
+            transversal, A(p,:)) -> split -> SPAI(0.3, 5, 10) -> GMRES(50)
+            refined to 1e-10 -> SMW -> rr; value = n / step time.
+  bgmres64  the 64^3 system: step = split -> SPAI(0.3, 5, 10) -> block
+            GMRES(50) over the 11 systems (FP32 inner block solves refined in
+            FP64) to 1e-10 -> SMW -> rr; value = n / step time.
+
+The default line also carries block_gmres_spai: one block GMRES(50) solve of
+its SPAI systems in the refined and the FP64 form (outside the timed steps).
 """
 import argparse
 import hashlib
