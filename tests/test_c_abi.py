@@ -30,8 +30,23 @@ def libpath():
 def test_header_declares_entry_points():
     names = _declared()
     for must in ("sai_split_create", "sai_build_spai", "sai_build_psai", "sai_krylov_solve", "sai_smw_recover",
-                 "sai_solve", "sai_rel_resid"):
+                 "sai_solve", "sai_rel_resid", "sai_solve_with", "sai_backward", "sai_solve_batched",
+                 "sai_precond_create", "sai_dmperm", "sai_permute_rows"):
         assert must in names
+
+
+def test_abi_structs_match_the_binding():
+    """The binding's ctypes mirrors have the header's field order and sizes
+    (the solve report, the split parameters and the method enum)."""
+    import ctypes as C
+    import paper_1211_6866_gb300 as sai
+    hdr = open(os.path.join(ROOT, "include", "saismw.h")).read()
+    assert "int32_t zero_diag;" in hdr and "int32_t moved;" in hdr
+    assert [f for f, _ in sai._SplitParams._fields_] == ["thresh_mult", "abs_tau", "ge", "p_keep", "keep_rule",
+                                                          "zero_diag"]
+    assert C.sizeof(sai._SplitParams) == 32
+    assert [f for f, _ in sai._SolveReport._fields_][-2:] == ["moved", "reserved"]
+    assert re.search(r"SAI_BGMRES\s*=\s*4", hdr) and sai.BGMRES == 4 and sai._METHOD["bgmres"] == 4
 
 
 def test_library_exports_every_declared_symbol(libpath):
