@@ -88,6 +88,19 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(dist, total, device="cuda"):
+    """The largest of the ranks' timed totals (all ranks get it), then a
+    barrier; the value itself without a process group."""
+    if not dist:
+        return total
+    import torch
+    t = torch.tensor([float(total)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total = float(t.item())
+    dist.barrier()
+    return total
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -380,11 +393,7 @@ def run_ours(args):
             nvtx(torch, None)
         prof = sai.profile_end() if profile else None
         total = float(np.sum(ms))
-        if dist:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-            dist.barrier()
+        total = max_over_ranks(dist, total)
         return total / nsteps, reps, prof
 
     clocks = ClockSampler(local)
@@ -528,11 +537,7 @@ def _timed_steps(torch, sai, dist, step, nsteps, flush, profile=False, label=Non
         nvtx(torch, None)
     prof = sai.profile_end() if profile else None
     total = float(np.sum(ms))
-    if dist:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-        dist.barrier()
+    total = max_over_ranks(dist, total)
     return total / nsteps, out, prof
 
 
