@@ -156,7 +156,7 @@ def test_repair_reports_structural_singularity():
     assert e.value.status == sai.SAI_SINGULAR
 
 
-def test_split_create_and_batched_reject_the_flag():
+def test_split_create_rejects_the_flag():
     need_gpu()
     sai = lib()
     P = W.convdiff2d_irregular(m=12, s=1, density=0.3)
