@@ -944,3 +944,32 @@ def test_procedure_with_block_gmres_meets_theorem2():
     x, it, rep = O.solve(P.A, P.b, krylov="bgmres", restart=30, eps=1e-8)
     assert rep["status"] == O.OK
     assert rep["rr"] < 1e-8 and rep["rr"] <= rep["bound"] / np.linalg.norm(P.b) * (1 + 1e-6)
+
+
+def test_oracle_backward_with_block_gmres():
+    """The adjoint pipeline with block GMRES(30) (all s+1 transposed systems
+    in one block): the Theorem 2 bound on ||g - A^T lambda||, agreement with
+    the dense adjoint, and block-step counts equal to a direct block solve of
+    the transposed systems at the thresholds taken from ||g||."""
+    P = W.convdiff2d_irregular()
+    A = O.as_csc(P.A)
+    eps = 1e-10
+    x = O.solve(A, P.b, krylov="bgmres", restart=30, eps=eps)[0]
+    g = np.random.default_rng(6).standard_normal(A.shape[0])
+    lam, gv, iters, rep = O.backward(A, x, g, krylov="bgmres", restart=30, eps=eps)
+    assert rep["status"] == O.OK and rep["s"] == 3
+    assert rep["rr"] <= eps * (1 + rep["c"]) / 2 * 1.05
+    lam_d, gv_d = O.backward_dense(A, x, g)
+    np.testing.assert_allclose(lam, lam_d, rtol=0, atol=1e-7 * np.abs(lam_d).max())
+    np.testing.assert_allclose(gv, gv_d, rtol=0, atol=1e-7 * np.abs(gv_d).max())
+    J, p, _ = O.detect(A)
+    At, U = O.split(A, J, p)
+    M = O.spai(At, 0.4, 5, 10)[0]
+    gn = np.linalg.norm(g)
+    s = len(J)
+    thr = [eps / 2 * gn] + [gn * eps / (2 * np.sqrt(s))] * s
+    R = np.zeros((A.shape[0], s + 1))
+    R[:, 0] = g
+    R[J, np.arange(1, s + 1)] = 1.0
+    _, it, st = O.block_gmres(sp.csc_matrix(At.T), sp.csc_matrix(M.T), R, thr, restart=30)
+    assert st == O.OK and list(it) == list(iters)
