@@ -361,6 +361,46 @@ def test_krylov_true_residual_meets_threshold(solver):
     np.testing.assert_allclose(y, 1.0, rtol=0, atol=1e-6)
 
 
+def _scipy_bicgstab_steps(A, M, b, j):
+    """scipy's BiCGStab (van der Vorst's recurrence, x0 = 0, shadow residual
+    r^ = b; its M is applied as a right preconditioner: p^ = M p, v = A p^,
+    x += alpha p^ + omega s^) run for exactly j iterations: no tolerance can
+    stop it early."""
+    import scipy.sparse.linalg as sla_
+    Mop = sla_.LinearOperator(A.shape, matvec=lambda v: M @ v, dtype=np.float64)
+    x, info = sla_.bicgstab(sp.csr_matrix(A), b, rtol=0.0, atol=0.0, maxiter=j, M=Mop)
+    assert info == j, info
+    return x
+
+
+@pytest.mark.parametrize("case", ["random40", "convdiff36"])
+def test_bicgstab_iterates_match_scipy_step_by_step(case):
+    """The oracle's BiCGStab iterate y_j after j = 1..6 iterations equals
+    scipy's on the same right-preconditioned system A~ M z = b, y = M z. A
+    wrong omega (the stabilising step) or beta (the direction update) changes
+    y_2 onwards, although both would still converge; the exact-preconditioner
+    pin never reaches omega (it stops at the half step)."""
+    if case == "random40":
+        At = sp.csc_matrix(_dominant(40, 4, seed=77))
+        M = O.spai(At, 0.3, 3, 2)[0]
+        b = np.random.default_rng(5).standard_normal(40)
+    else:
+        At = W.convdiff2d_irregular(m=6, s=0).A
+        M = O.spai(At, 0.2, 3, 2)[0]
+        b = At @ np.ones(At.shape[0])
+    Ms = sp.csc_matrix(M)
+    assert abs(Ms - Ms.T).max() > 1e-3 and abs(At - At.T).max() > 1e-3  # nonsymmetric operator
+    for j in range(1, 7):
+        y, it, st = O.bicgstab(At, M, b, 0.0, maxit=j)
+        assert st == O.MAXITER and it == j
+        x = _scipy_bicgstab_steps(At, Ms, b, j)
+        np.testing.assert_allclose(y, x, rtol=0, atol=1e-10 * np.abs(x).max())
+    # the iterates move: consecutive steps differ well above the tolerance
+    y1 = O.bicgstab(At, M, b, 0.0, maxit=1)[0]
+    y2 = O.bicgstab(At, M, b, 0.0, maxit=2)[0]
+    assert np.abs(y2 - y1).max() > 1e-6 * np.abs(y2).max()
+
+
 def test_krylov_maxit_status():
     A = W.convdiff2d_irregular(m=30, s=0).A
     I = sp.identity(A.shape[0], format="csc")
