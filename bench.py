@@ -190,7 +190,7 @@ def site_roofline(name, s, peaks):
     return r
 
 
-TRAFFIC_MD = os.path.join(ROOT, "profiles", "traffic_convdiff3d64_bench_step.md")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic_convdiff3d64.json")
 
 
 def source_digest(ref):
@@ -218,26 +218,34 @@ def source_digest(ref):
     return hashlib.sha256(text).hexdigest()[:16]
 
 
-def measured_traffic(site):
-    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum,
-    averaged over every launch of the site's kernel in one ncu capture of the
-    timed step) from the committed summary, or None when there is none or the
-    kernel's source has changed since (its sha256 prefix is recorded)."""
+def measured_traffic(site, algorithmic_bytes_per_launch, path=TRAFFIC_JSON):
+    """DRAM bytes per launch of the site's kernel, scaled to the bench's
+    average launch: the data file records dram__bytes_read.sum +
+    dram__bytes_write.sum of a few captured launches of one kernel (ncu -k
+    <kernel> -c <few>) next to those launches' algorithmic bytes; the
+    measured bytes per algorithmic byte times the bench's algorithmic bytes
+    per launch is the figure (the pass streams its vectors, so its traffic
+    grows with them). None when the file has no entry for the site or the
+    kernel's source has changed since the capture (its sha256 prefix is
+    recorded)."""
     try:
-        with open(TRAFFIC_MD) as f:
-            text = f.read()
-    except OSError:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
         return None
-    for line in text.splitlines():
-        parts = [q.strip().strip("`") for q in line.strip().strip("|").split("|")]
-        if len(parts) < 6 or parts[0] != site:
+    for e in data.get("kernels", []):
+        if e.get("site") != site:
             continue
         try:
-            if source_digest(parts[4]) != parts[5]:
+            if source_digest(e["source"]) != e["sha256_16"]:
                 return None
-            return float(parts[3])
-        except (OSError, ValueError):
+        except (OSError, ValueError, KeyError):
             return None
+        meas = sum(l["dram_bytes"] for l in e["launches"])
+        alg = sum(l["algorithmic_bytes"] for l in e["launches"])
+        if alg <= 0:
+            return None
+        return meas / alg * algorithmic_bytes_per_launch
     return None
 
 
@@ -250,7 +258,8 @@ def roofline(prof, peaks, traffic=True):
         return None
     name = max(sites, key=lambda k: sites[k]["ms"])
     r = site_roofline(name, sites[name], peaks)
-    r.update({"kernel": name, "traffic": measured_traffic(name) if traffic else None,
+    r.update({"kernel": name,
+              "traffic": measured_traffic(name, r["algorithmic_bytes_per_launch"]) if traffic else None,
               "measured": "CUDA events on the first 16 launches of each site and every 7th after, "
                           "one profiled step after the timed steps",
               "sites": {k: dict(ms=round(v["ms"], 3), **{q: (round(x, 4) if isinstance(x, float) else x)
@@ -962,6 +971,27 @@ def run_bgmres(args):
     return 0
 
 
+def run_probe(args):
+    """One Procedure * on the 64^3 system with the headline's refined forms
+    and the given SAI builder, with no autotuning, warm-up or timing: a short
+    program for ncu captures of single kernels (few launches precede the
+    first Krylov launches). Prints the solve's report, not a bench line."""
+    import torch
+    import paper_1211_6866_gb300 as sai
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
+    sai.load()
+    P = W.convdiff3d_irregular()
+    dA = sai.CscMatrix.from_arrays(P.A.indptr, P.A.indices, P.A.data, P.n)
+    b = torch.as_tensor(P.b, device="cuda")
+    kw = SPAI_KW if args.probe == "spai" else PSAI_KW
+    x, iters, rep = sai.solve(dA, b, **kw, **KRYLOV_KW, **OPT_KW)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": args.probe, "iters": iters, "rr": rep["rr"], "status": rep["status"],
+                      "nnz_M": rep["nnz_M"]}))
+    return 0 if rep["status"] == sai.SAI_OK and rep["rr"] < KRYLOV_KW["eps"] else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -971,7 +1001,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="convdiff3d64", choices=["convdiff3d64", "zipf", "batch256", "zerodiag64", "bgmres64"])
     ap.add_argument("--zipf-n", type=int, default=100000, help="order of the Zipf-count matrix (--workload zipf)")
+    ap.add_argument("--probe", choices=["spai", "psai"], default=None,
+                    help="run one untimed 64^3 solve with this SAI builder (for ncu captures) and exit")
     args = ap.parse_args()
+    if args.probe:
+        return run_probe(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "zipf":

@@ -309,7 +309,8 @@ sai_status sai_krylov_solve(sai_split h, sai_precond P, int32_t k, const double*
  * Gaussian elimination with partial pivoting on the s x s matrix (the
  * largest |pivot|, the first row on ties): one thread block for s <= 256, a
  * blocked right-looking LU (panels of 16 columns, FP64 tiles for the
- * trailing update) for larger s. SAI_SINGULAR on a zero pivot.
+ * trailing update) for larger s. SAI_SINGULAR on a zero pivot, after which
+ * x is not valid.
  * ---------------------------------------------------------------------- */
 sai_status sai_smw_recover(sai_split h, const double* Y, double* x, double* c_out, sai_stream_t stream);
 
@@ -322,10 +323,13 @@ sai_status sai_smw_recover(sai_split h, const double* Y, double* x, double* c_ou
  * (n, device output), c_out (host, may be NULL).
  * Scratch: a static device array of about 516 KB (s <= 256) that every
  * device loading the library holds until the process exits; s > 256 returns
- * SAI_INVALID_ARG. The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture. All calls share the array, so calls that overlap on the GPU (other
- * streams or threads) race: serialise them. Synchronises the stream. */
+ * SAI_INVALID_ARG. Every call looks up the array's device address in the
+ * current context (cudaGetSymbolAddress, which allocates nothing); the first
+ * call on a device may also load the library's module there, so make that
+ * first call before any stream capture. All calls share the array, so calls
+ * that overlap on the GPU (other streams or threads) race: serialise them.
+ * On SAI_SINGULAR (a zero pivot) x holds yhat, column 0 of Y, uncorrected.
+ * Synchronises the stream. */
 sai_status sai_smw_recover_noalloc(int32_t n, int32_t s, const int32_t* J, const double* Y, double* x,
                                    double* c_out, sai_stream_t stream);
 

@@ -2818,6 +2818,12 @@ sai_status bgmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs
         // V_0 R = the active residuals; G = [R; 0]
         k_bg_gather<T><<<SAI_GRID(gg), 256, 0, st>>>(n, ld, B.lact, R, B.V);
         bg_qr<T>(n, ld, B.V, kb, B, st);
+        // a breakdown in the QR of V_0 (the active residuals are numerically
+        // dependent): no step of this cycle is taken, X keeps its value and
+        // the next cycle start ends the active systems with BREAKDOWN
+        SAI_CUDA(cudaMemcpyAsync(h, B.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaStreamSynchronize(st));
+        if (h[1]) continue;
         SAI_CUDA(cudaMemsetAsync(B.G, 0, sizeof(double) * (size_t)B.ldh * B.k, st));
         SAI_CUDA(cudaMemcpy2DAsync(B.G, sizeof(double) * B.ldh, B.Rt, sizeof(double) * kb, sizeof(double) * kb, kb,
                                    cudaMemcpyDeviceToDevice, st));
@@ -2859,9 +2865,13 @@ sai_status bgmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs
             SAI_CUDA(cudaGetLastError());
             SAI_CUDA(cudaMemcpyAsync(h, B.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
             SAI_CUDA(cudaStreamSynchronize(st));
-            steps = j + 1;
+            // a breakdown in this step's QR leaves the step out: the first j
+            // block steps' rows of G and columns of the block Hessenberg
+            // matrix are final before step j's reflections
+            steps = h[1] ? j : j + 1;
             if (h[0] || h[1]) break;
         }
+        if (steps == 0) continue;
         // X[lact] += M (V Ys), R = B - A~ X
         k_bg_backsolve<T><<<SAI_GRID(1), 32 * BG_KMAX, 0, st>>>(steps * kb, B);
         bg_update<T>(n, ld, B.V, steps * kb, B.Ys, m * B.k, kb, B.Z, 1, st);

@@ -9,8 +9,6 @@
 // system is C = I + U^T What, g = U^T yhat (k_smw_gather_adj).
 #include <math.h>
 
-#include <mutex>
-
 #include "internal.h"
 
 namespace {
@@ -542,24 +540,15 @@ constexpr size_t NOALLOC_BYTES = NOALLOC_ERR_OFF + 256;
 
 static __device__ __align__(256) unsigned char g_smw_noalloc_scratch[NOALLOC_BYTES];
 
-constexpr int NOALLOC_MAX_DEV = 64;
-static unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEV];
-static std::mutex g_noalloc_mu;
-
-// Device address of the scratch array for the current device, looked up once
-// per device (the host-side symbol is only a stand-in, not a device address).
+// Device address of the scratch array in the current device's context (the
+// host-side symbol is only a stand-in, not a device address). Looked up on
+// every call: the lookup allocates nothing, and an address kept from an
+// earlier context (before a cudaDeviceReset, say) would no longer be valid.
 sai_status noalloc_scratch(unsigned char** out)
 {
-    int dev = 0;
-    SAI_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NOALLOC_MAX_DEV) return SAI_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        SAI_CUDA(cudaGetSymbolAddress(&p, g_smw_noalloc_scratch));
-        g_noalloc_ptr[dev] = (unsigned char*)p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    SAI_CUDA(cudaGetSymbolAddress(&p, g_smw_noalloc_scratch));
+    *out = (unsigned char*)p;
     return SAI_OK;
 }
 
@@ -578,9 +567,11 @@ extern "C" sai_status sai_smw_recover_noalloc(int32_t n, int32_t s, const int32_
     double* z = (double*)(base + NOALLOC_Z_OFF);
     double* cval = (double*)(base + NOALLOC_CV_OFF);
     int* err = (int*)(base + NOALLOC_ERR_OFF);
-    // the array keeps the previous call's contents: clear what must start at zero
+    // the array keeps the previous call's contents: clear what must start at
+    // zero; z too, so that a zero pivot (z left unwritten) gives x = yhat
     SAI_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     SAI_CUDA(cudaMemsetAsync(cval, 0, sizeof(double), st));
+    if (s > 0) SAI_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)s, st));
     if (s > 0) {
         k_smw_gather<<<SAI_GRID(sai_div_up((int64_t)s * s, 256)), 256, 0, st>>>(n, s, J, Y, C, g);
         k_lu_solve<<<SAI_GRID(1), 1024, 0, st>>>(s, C, g, z, cval, err);

@@ -1,7 +1,9 @@
 """Host logic of bench.py's roofline on CPU: the bound of a profiled site,
 the achieved rate and fraction, and the DRAM traffic of the committed ncu
-table, which is reported only while the kernel's source still has the
-recorded digest."""
+data file (measured bytes per algorithmic byte of a few captured launches),
+which is reported only while the kernel's source still has the recorded
+digest."""
+import json
 import os
 import sys
 
@@ -37,31 +39,37 @@ def test_roofline_picks_the_longest_site_and_can_drop_traffic():
     assert set(r["sites"]) == {"krylov_spmm_fp32", "gmres_update_fp32"}
 
 
-def test_traffic_only_while_the_digest_matches(tmp_path, monkeypatch):
+def _traffic_file(tmp_path, rel, dig):
+    data = {"kernels": [{"site": "site_a", "kernel": "k_a", "source": rel + "::k_a", "sha256_16": dig,
+                         "launches": [{"dram_bytes": 1.5e6, "algorithmic_bytes": 1.0e6},
+                                      {"dram_bytes": 3.0e6, "algorithmic_bytes": 2.0e6}]}]}
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(data))
+    return str(path)
+
+
+def test_traffic_only_while_the_digest_matches(tmp_path):
     src = tmp_path / "k.cu"
     src.write_text("__global__ void k_a(int n)\n{\n    (void)n;\n}\n__global__ void k_b(int n)\n{\n}\n")
     rel = os.path.relpath(str(src), ROOT)
-    dig = bench.source_digest(rel + "::k_a")
-    table = tmp_path / "traffic.md"
-    table.write_text("| site | kernel | launches | DRAM bytes per launch | source | sha256 |\n|---|---|---|---|---|---|\n"
-                     "| site_a | `k_a` | 3 | 1.5e+06 | `%s::k_a` | %s |\n" % (rel, dig))
-    monkeypatch.setattr(bench, "TRAFFIC_MD", str(table))
-    assert bench.measured_traffic("site_a") == 1.5e6
-    assert bench.measured_traffic("site_b") is None
+    path = _traffic_file(tmp_path, rel, bench.source_digest(rel + "::k_a"))
+    # 4.5 MB measured over 3 MB algorithmic: 1.5 measured bytes per algorithmic byte
+    assert abs(bench.measured_traffic("site_a", 4.0e6, path) - 6.0e6) < 1e-6
+    assert bench.measured_traffic("site_b", 4.0e6, path) is None
     # another kernel of the file changing leaves k_a's figure valid; k_a changing drops it
     src.write_text("__global__ void k_a(int n)\n{\n    (void)n;\n}\n__global__ void k_b(int n)\n{\n    n++;\n}\n")
-    assert bench.measured_traffic("site_a") == 1.5e6
+    assert abs(bench.measured_traffic("site_a", 4.0e6, path) - 6.0e6) < 1e-6
     src.write_text("__global__ void k_a(int n)\n{\n    n += 1;\n}\n")
-    assert bench.measured_traffic("site_a") is None
+    assert bench.measured_traffic("site_a", 4.0e6, path) is None
 
 
-def test_committed_traffic_table_names_existing_kernels():
-    """Every row of the committed table names a source and kernel that
-    exist (a renamed kernel would otherwise silently drop its figure)."""
-    rows = 0
-    for line in open(bench.TRAFFIC_MD).read().splitlines():
-        parts = [q.strip().strip("`") for q in line.strip().strip("|").split("|")]
-        if len(parts) >= 6 and "::" in parts[4] or (len(parts) >= 6 and parts[4].endswith(".cu")):
-            bench.source_digest(parts[4])
-            rows += 1
-    assert rows >= 5
+def test_committed_traffic_file_names_existing_kernels():
+    """Every entry of the committed traffic file names a source and kernel
+    that exist (a renamed kernel would otherwise silently drop its figure)
+    and carries launches with both byte counts."""
+    if not os.path.exists(bench.TRAFFIC_JSON):
+        return
+    data = json.load(open(bench.TRAFFIC_JSON))
+    for e in data["kernels"]:
+        bench.source_digest(e["source"])
+        assert e["launches"] and all(l["dram_bytes"] > 0 and l["algorithmic_bytes"] > 0 for l in e["launches"])

@@ -158,3 +158,30 @@ def test_block_gmres_limits():
     with pytest.raises(sai.SaiError) as e:
         sai.krylov_solve(sp_, Pc, torch.as_tensor(B, device="cuda"), thr, method=sai.BGMRES, restart=0)
     assert e.value.status == sai.SAI_INVALID_ARG
+
+
+def test_identical_right_hand_sides_keep_x_sound():
+    """Two identical right-hand sides make the first block numerically rank
+    deficient, so the shifted Cholesky QR may break down. Whatever happens,
+    each system ends with OK (and meets its threshold) or BREAKDOWN, and a
+    broken block step never enters X: every returned column's residual is at
+    most the starting one (x0 = 0) and the two columns agree."""
+    need_gpu()
+    sai = lib()
+    P = W.convdiff2d_irregular()
+    sp_, Pc, At, M, B, thr = _system(P)
+    B2 = np.stack([P.b, P.b], axis=1)
+    thr2 = [thr[0], thr[0]]
+    for fp in (0, 1):
+        X, iters, status, st = sai.krylov_solve(sp_, Pc, torch.as_tensor(B2, device="cuda"), thr2,
+                                                method=sai.BGMRES, restart=30, precision=fp)
+        X = X.cpu().numpy()
+        assert st in (sai.SAI_OK, sai.SAI_BREAKDOWN), st
+        for c in range(2):
+            r = np.linalg.norm(P.b - At @ X[:, c])
+            assert status[c] in (sai.SAI_OK, sai.SAI_BREAKDOWN), status
+            assert np.all(np.isfinite(X[:, c]))
+            assert r <= np.linalg.norm(P.b) * (1 + 1e-12)
+            if status[c] == sai.SAI_OK:
+                assert r < thr2[c] * 1.000001
+        np.testing.assert_allclose(X[:, 0], X[:, 1], rtol=0, atol=1e-6 * max(np.abs(X).max(), 1.0))

@@ -65,8 +65,10 @@ def test_noalloc_clears_error_state_between_calls():
     for i, j in enumerate(Jh):         # W(J,:) = -I makes I + V^T W = 0
         Ys[j, 1:] = 0.0
         Ys[j, 1 + i] = -1.0
-    st, _, _ = _call_noalloc(h.n, h.s, J, Ys)
+    st, xs, _ = _call_noalloc(h.n, h.s, J, Ys)
     assert st == sai.SAI_SINGULAR
+    # a zero pivot leaves the correction out: x is yhat (column 0 of Y)
+    np.testing.assert_array_equal(xs.cpu().numpy(), Ys[:, 0].cpu().numpy())
     x_ref, c_ref = sai.smw_recover(h, Y)
     st, x, c = _call_noalloc(h.n, h.s, J, Y)
     assert st == sai.SAI_OK
