@@ -165,28 +165,39 @@ FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 
 def site_roofline(name, s, peaks):
-    """Binding peak and achieved rate of one profiled site (per-launch averages)."""
+    """Binding peak and achieved rate of one profiled site (per-launch averages).
+    Flops split by type: s["flops32"] of s["flops"] are FP32 (without the key,
+    all of an "_fp32" site's and none of another's); an ALU-bound site's peak
+    is the rate at which its FP64 and FP32 work would run on the two pipes'
+    peaks one after the other, so frac is the share of its time that work
+    needs at peak."""
     avg_s = s["ms"] / s["launches"] / 1e3
     bytes_l = s["bytes"] / s["launches"]
     flops_l = s["flops"] / s["launches"]
+    f32_l = (s["flops32"] if "flops32" in s else (s["flops"] if name.endswith("_fp32") else 0.0)) / s["launches"]
+    f64_l = max(flops_l - f32_l, 0.0)
     hbm = (peaks or {}).get("hbm_gbs", 6800.0)
-    fp32 = name.endswith("_fp32")
-    alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
     t_hbm = bytes_l / (hbm * 1e9)
-    t_alu = flops_l / (alu_peak * 1e12)
+    t_alu = f64_l / (FP64_PEAK_TFLOPS * 1e12) + f32_l / (FP32_PEAK_TFLOPS * 1e12)
     if bytes_l == 0 and flops_l == 0:  # control kernels: no algorithmic traffic to set against a peak
         r = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
              "peak_source": "no algorithmic bytes or flops (control kernel)"}
     elif flops_l > 0 and t_alu > t_hbm:
         ach = flops_l / avg_s / 1e12
-        r = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-             "peak_source": ("FP32" if fp32 else "FP64") + " ALU nominal from unit counts and clocks"}
+        peak = flops_l / t_alu / 1e12
+        kinds = [k for k, f in (("FP64", f64_l), ("FP32", f32_l)) if f > 0]
+        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "peak_source": " + ".join(kinds) + " ALU nominal from unit counts and clocks"}
+        if len(kinds) == 2:
+            r.update({"achieved_fp64": f64_l / avg_s / 1e12, "frac_fp64": f64_l / avg_s / 1e12 / FP64_PEAK_TFLOPS,
+                      "achieved_fp32": f32_l / avg_s / 1e12, "frac_fp32": f32_l / avg_s / 1e12 / FP32_PEAK_TFLOPS})
     else:
         ach = bytes_l / avg_s / 1e9
         r = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
              "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback"}
     r.update({"launches": s["launches"], "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": bytes_l,
-              "algorithmic_flops_per_launch": flops_l, "timed_launches": s.get("timed", s["launches"])})
+              "algorithmic_flops_per_launch": flops_l, "algorithmic_fp32_flops_per_launch": f32_l,
+              "timed_launches": s.get("timed", s["launches"])})
     return r
 
 
@@ -264,7 +275,8 @@ def roofline(prof, peaks, traffic=True):
                           "one profiled step after the timed steps",
               "sites": {k: dict(ms=round(v["ms"], 3), **{q: (round(x, 4) if isinstance(x, float) else x)
                                                          for q, x in site_roofline(k, v, peaks).items()
-                                                         if q in ("bound", "achieved", "unit", "frac", "launches")})
+                                                         if q in ("bound", "achieved", "unit", "frac", "launches",
+                                                                  "frac_fp64", "frac_fp32")})
                         for k, v in sites.items()}})
     return r
 
@@ -483,7 +495,7 @@ def run_ours(args):
         "roofline": roofline(prof, peaks),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": float(np.mean(e2e_ms))},
-        "build_schedule": {k: tuned[k] for k in ("warps_t0", "blocks_per_sm_t12", "heavy_first")},
+        "build_schedule": {k: tuned[k] for k in ("warps_t0", "blocks_per_sm_t12", "heavy_first", "first_tier")},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -985,6 +997,7 @@ def run_probe(args):
     dA = sai.CscMatrix.from_arrays(P.A.indptr, P.A.indices, P.A.data, P.n)
     b = torch.as_tensor(P.b, device="cuda")
     kw = SPAI_KW if args.probe == "spai" else PSAI_KW
+    sai.build_set_config(8, 2, 0, args.first_tier)
     x, iters, rep = sai.solve(dA, b, **kw, **KRYLOV_KW, **OPT_KW)
     torch.cuda.synchronize()
     print(json.dumps({"probe": args.probe, "iters": iters, "rr": rep["rr"], "status": rep["status"],
@@ -1003,6 +1016,9 @@ def main():
     ap.add_argument("--zipf-n", type=int, default=100000, help="order of the Zipf-count matrix (--workload zipf)")
     ap.add_argument("--probe", choices=["spai", "psai"], default=None,
                     help="run one untimed 64^3 solve with this SAI builder (for ncu captures) and exit")
+    ap.add_argument("--first-tier", type=int, default=0, choices=[0, 1, 2],
+                    help="build schedule's first tier for --probe (0: one column per warp; 1, 2: the small tier "
+                         "with four or two columns per warp)")
     args = ap.parse_args()
     if args.probe:
         return run_probe(args)

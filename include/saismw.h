@@ -194,16 +194,25 @@ typedef struct {
 
 typedef struct sai_precond_s* sai_precond;
 
-/* Schedule of the SAI build (not part of the method: every configuration
- * gives the same M). warps_t0: warps per block of the shared-memory tier (4
- * or 8); blocks_per_sm_t12: blocks per SM of the global-memory tiers (1, 2
- * or 4); heavy_first: 1 puts the columns of A~ with more than twice the
- * average entry count at the head of the work queue. ms: the sampled build
- * time measured by sai_build_autotune (0 otherwise). Default {8, 2, 0}. */
+/* Schedule of the SAI build (not part of the method). warps_t0: warps per
+ * block of the shared-memory tiers (4 or 8); blocks_per_sm_t12: blocks per
+ * SM of the global-memory tiers (1, 2 or 4); heavy_first: 1 puts the columns
+ * of A~ with more than twice the average entry count at the head of the work
+ * queue; first_tier: the workspace every column starts in -- 0: tier 0 (|L|
+ * <= 64 rows, |S| <= 16 columns, one column per warp), 1: the small tier
+ * (|L| <= 32, |S| <= 8) with four columns per warp (8-lane groups), 2: the
+ * small tier with two columns per warp (16-lane groups); a column that
+ * outgrows its tier restarts in the next one. ms: the sampled build time
+ * measured by sai_build_autotune (0 otherwise). Default {8, 2, 0, 0}.
+ * warps_t0, blocks_per_sm_t12 and heavy_first never change M. first_tier
+ * sets how many lanes sum each reduction of the columns the small tier
+ * finishes, so M's values can differ in the last bits between first_tier 0
+ * and 1 or 2 (the same first_tier always gives the same bits). */
 typedef struct {
     int32_t warps_t0;
     int32_t blocks_per_sm_t12;
     int32_t heavy_first;
+    int32_t first_tier;
     float ms;
 } sai_build_config;
 
@@ -219,7 +228,8 @@ typedef struct {
     int64_t nnz_M;
     int32_t n_c;        /* columns whose final (pre-drop) residual > delta */
     int32_t l_m;        /* largest loop index used over all columns */
-    int32_t n_tier[4];  /* columns finished per workspace tier: 0 shared memory, 1-3 global memory */
+    int32_t n_tier[5];  /* columns finished per workspace tier: 0 shared memory, 1-3 global
+                           memory, 4 the small shared-memory tier (first_tier 1 or 2) */
     double build_ms;    /* device time of the build, CUDA events */
 } sai_precond_info;
 
@@ -228,11 +238,15 @@ sai_status sai_build_psai(sai_split h, const sai_psai_params* prm, sai_stream_t 
 sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info);
 
 /* Autotuner of the build schedule: times the build of a strided sample of
- * h's columns (about 1/16 of them, at least 4096 when n allows) under each
- * candidate configuration (warps_t0 x blocks_per_sm_t12 x heavy_first), with
- * sai = 0 (SPAI, spai params) or 1 (PSAI, psai params), and makes the fastest
- * the process-wide configuration of later builds. out (host) receives the
- * candidates and the choice. Synchronises the stream. */
+ * h's columns (every max(1, n/65536)-th, at least 4096 when n allows) under
+ * candidate configurations, with sai = 0 (SPAI, spai params) or 1 (PSAI,
+ * psai params), and makes the fastest the process-wide configuration of
+ * later builds. The search takes one coordinate at a time: first_tier (the
+ * workspace shape and columns per warp of the first tier) x warps_t0 with
+ * {blocks_per_sm_t12 2, heavy_first 0}, then heavy_first 1 on the best of
+ * those, then blocks_per_sm_t12 1 and 4 on the best so far (nine
+ * candidates). out (host) receives the candidates and the choice.
+ * Synchronises the stream. */
 sai_status sai_build_autotune(sai_split h, int32_t sai, const sai_spai_params* spai, const sai_psai_params* psai,
                               sai_stream_t stream, sai_build_tuning* out);
 /* Sets the process-wide build configuration; NULL restores the default.
@@ -456,6 +470,8 @@ typedef struct {
     double ms;          /* device time of all launches: mean timed duration x launches */
     double bytes;       /* algorithmic bytes moved by all launches */
     double flops;       /* algorithmic floating-point operations of all launches */
+    double flops32;     /* the FP32 ones among them (the refined build's QR, the FP32
+                           Krylov sites); the rest are FP64 */
 } sai_profile_site;
 
 typedef struct {

@@ -67,7 +67,7 @@ class _PsaiParams(C.Structure):
 
 class _PrecondInfo(C.Structure):
     _fields_ = [("n", C.c_int32), ("nnz_M", C.c_int64), ("n_c", C.c_int32), ("l_m", C.c_int32),
-                ("n_tier", C.c_int32 * 4), ("build_ms", C.c_double)]
+                ("n_tier", C.c_int32 * 5), ("build_ms", C.c_double)]
 
 
 class _KrylovParams(C.Structure):
@@ -88,7 +88,7 @@ class _BatchReport(C.Structure):
 
 class _BuildConfig(C.Structure):
     _fields_ = [("warps_t0", C.c_int32), ("blocks_per_sm_t12", C.c_int32), ("heavy_first", C.c_int32),
-                ("ms", C.c_float)]
+                ("first_tier", C.c_int32), ("ms", C.c_float)]
 
 
 class _BuildTuning(C.Structure):
@@ -113,7 +113,7 @@ class _SolveReport(C.Structure):
 
 class _ProfSite(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("timed", C.c_int64), ("ms", C.c_double),
-                ("bytes", C.c_double), ("flops", C.c_double)]
+                ("bytes", C.c_double), ("flops", C.c_double), ("flops32", C.c_double)]
 
 
 class _ProfReport(C.Structure):
@@ -303,7 +303,8 @@ def build_spai(sp, delta=0.4, mn=5, max_aug=10, key_bits=20, precision=0):
 
 
 def _cfg_dict(c):
-    return dict(warps_t0=c.warps_t0, blocks_per_sm_t12=c.blocks_per_sm_t12, heavy_first=c.heavy_first, ms=c.ms)
+    return dict(warps_t0=c.warps_t0, blocks_per_sm_t12=c.blocks_per_sm_t12, heavy_first=c.heavy_first,
+                first_tier=c.first_tier, ms=c.ms)
 
 
 def build_autotune(sp, sai="spai", delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10,
@@ -319,13 +320,15 @@ def build_autotune(sp, sai="spai", delta=0.4, mn=5, max_aug=10, key_bits=20, tol
     return _cfg_dict(t.chosen), [_cfg_dict(t.cand[i]) for i in range(t.ncand)]
 
 
-def build_set_config(warps_t0=None, blocks_per_sm_t12=2, heavy_first=0):
-    """Sets the build schedule (warps_t0=None restores the default)."""
+def build_set_config(warps_t0=None, blocks_per_sm_t12=2, heavy_first=0, first_tier=0):
+    """Sets the build schedule (warps_t0=None restores the default).
+    first_tier: 0 starts every column in tier 0 (one column per warp), 1 in
+    the small shared-memory tier with four columns per warp, 2 with two."""
     L = load()
     if warps_t0 is None:
         _check("sai_build_set_config", L.sai_build_set_config(None))
     else:
-        c = _BuildConfig(warps_t0, blocks_per_sm_t12, heavy_first, 0.0)
+        c = _BuildConfig(warps_t0, blocks_per_sm_t12, heavy_first, first_tier, 0.0)
         _check("sai_build_set_config", L.sai_build_set_config(C.byref(c)))
 
 
@@ -587,5 +590,5 @@ def profile_end():
     for q in range(rep.nsites):
         st = rep.site[q]
         sites[st.name.decode()] = dict(launches=int(st.launches), timed=int(st.timed), ms=st.ms, bytes=st.bytes,
-                                       flops=st.flops)
+                                       flops=st.flops, flops32=st.flops32)
     return {"launches": int(rep.launches), "sites": sites}

@@ -138,9 +138,9 @@ sai_status sai_profile_end(sai_profile_report* out)
     SAI_CUDA(cudaDeviceSynchronize());
     memset(out, 0, sizeof(*out));
     out->launches = g_launches.load();
-    double wk[PROF_NSITES * 2], wb[PROF_NSITES * 2], wt[PROF_NSITES * 2];
+    double wk[PROF_NSITES * 2], wb[PROF_NSITES * 2], wt[PROF_NSITES * 2], wb32 = 0.0;
     SAI_TRY(sai_krylov_work_read(wk));
-    SAI_TRY(sai_build_work_read(wb));
+    SAI_TRY(sai_build_work_read(wb, &wb32));
     SAI_TRY(sai_batch_work_read(wt));
     std::lock_guard<std::mutex> lk(g_prof_mu);
     out->nsites = PROF_NSITES;
@@ -169,7 +169,13 @@ sai_status sai_profile_end(sai_profile_report* out)
         ps.timed = (int64_t)timed;
         g_prof_ev[q].clear();
         ps.bytes = wk[2 * q] + wb[2 * q] + wt[2 * q];
-        ps.flops = wk[2 * q + 1] + wb[2 * q + 1] + wt[2 * q + 1];
+        // all flops, and their FP32 share: the whole of an FP32 Krylov site,
+        // the QR of the refined build
+        const double b32 = q == PROF_SAI_BUILD ? wb32 : 0.0;
+        ps.flops = wk[2 * q + 1] + wb[2 * q + 1] + wt[2 * q + 1] + b32;
+        const size_t ln = strlen(k_site_names[q]);
+        const bool fp32_site = ln > 5 && strcmp(k_site_names[q] + ln - 5, "_fp32") == 0;
+        ps.flops32 = fp32_site ? ps.flops : b32;
     }
     return SAI_OK;
 }
@@ -326,7 +332,7 @@ sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info)
     info->nnz_M = P->nnz;
     info->n_c = P->n_c;
     info->l_m = P->l_m;
-    for (int q = 0; q < 4; ++q) info->n_tier[q] = P->n_tier[q];
+    for (int q = 0; q < 5; ++q) info->n_tier[q] = P->n_tier[q];
     info->build_ms = P->ms;
     return SAI_OK;
 }
@@ -486,7 +492,7 @@ void report_handles(const sai_split_s& h, const sai_precond_s& P, sai_solve_repo
     rep->precond.nnz_M = P.nnz;
     rep->precond.n_c = P.n_c;
     rep->precond.l_m = P.l_m;
-    for (int q = 0; q < 4; ++q) rep->precond.n_tier[q] = P.n_tier[q];
+    for (int q = 0; q < 5; ++q) rep->precond.n_tier[q] = P.n_tier[q];
     rep->precond.build_ms = P.ms;
 }
 

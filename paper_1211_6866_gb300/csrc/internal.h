@@ -63,7 +63,7 @@ struct sai_precond_s {
     int32_t n = 0;
     int64_t nnz = 0;
     int32_t n_c = 0, l_m = 0;
-    int32_t n_tier[4] = {0, 0, 0, 0};
+    int32_t n_tier[5] = {0, 0, 0, 0, 0};
     float ms = 0.f;
     Buf M_cp, M_ri, M_v;     // CSC
     Buf Mr_rp, Mr_ci, Mr_v;  // CSR
@@ -102,6 +102,6 @@ cudaStream_t sai_aux_stream();
 sai_status sai_krylov_work_reset();
 sai_status sai_krylov_work_read(double* out /* PROF_NSITES x 2 */);
 sai_status sai_build_work_reset();
-sai_status sai_build_work_read(double* out /* PROF_NSITES x 2 */);
+sai_status sai_build_work_read(double* out /* PROF_NSITES x 2 */, double* flops32 /* FP32 flops of the build */);
 sai_status sai_batch_work_reset();
 sai_status sai_batch_work_read(double* out /* PROF_NSITES x 2 */);

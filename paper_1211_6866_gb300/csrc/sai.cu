@@ -1,9 +1,10 @@
 // sai.cu -- construction of the sparse approximate inverse M ~ A~^{-1}
 // (section 2 of the paper): n independent problems min ||A~ m_k - e_k||
 // (eq. (subprob)) reduced to min ||A^_k m^_k - e^_k|| (eq. (lsprob)) and solved
-// by Householder QR, one warp per column.
+// by Householder QR, one lane group per column.
 //
-// Per column k the warp keeps, in a private workspace:
+// Per column k a group of G lanes (G = 8, 16 or 32: four, two or one column
+// per warp) keeps, in a private workspace:
 //   S      the pattern (insertion order), |S| <= SCAP
 //   L      the rows of A~(:,S) plus k (row k always at local position 0),
 //          with a hash row -> local position, |L| <= LCAP
@@ -18,16 +19,21 @@
 //
 // SPAI (section 2.1): candidates N \ S from the rows of L (CSR of A~),
 // rho_j^2 = ||r||^2 - (r^T A~e_j)^2/||A~e_j||^2 (eq. (rhoj)), ranked by the key
-// (floor(rho_j^2/||r||^2 * 2^key_bits) << 32 | j) and the mn smallest added.
+// (floor(rho_j^2/||r||^2 * 2^key_bits) << 32 | j) and the mn smallest added;
+// rho_j^2/||r||^2 is formed as 1 - (r^T A~e_j)^2 ||A~e_j||^-2 ||r||^-2 with the
+// reciprocals taken once per column of A~ and once per loop.
 // PSAI(tol) (section 2.2): drop |m_jk| <= tol_k (eq. (tolk)); grow
 // S^(l+1) = P(|A~| a^(l)) u S_kept.
 //
-// Workspace tiers: tier 0 lives in shared memory (most columns of regular
-// sparse matrices); a column that outgrows it is queued and restarted in the
-// global-memory tiers 1, 2 and 3 (tier 3 for columns whose rows reach more
-// than 4096 candidate columns, as in heavy-tailed matrices). Restarting
-// reproduces the same arithmetic, so the result does not depend on the tier
-// that finished a column.
+// Workspace tiers: the first runs in shared memory with a small workspace
+// (|L| <= 32, |S| <= 8) and 8- or 16-lane groups, for the columns of stencil
+// matrices whose patterns stay small; tier 0 in shared memory with one
+// column per warp; a column that outgrows a tier is queued and restarted in
+// the next: tier 0, then the global-memory tiers 1, 2 and 3 (tier 3 for
+// columns whose rows reach more than 4096 candidate columns, as in
+// heavy-tailed matrices). A restart reproduces the column's steps; the
+// rounding of its sums depends on the group size, so a column's result
+// depends on the tier that finishes it, which the column alone decides.
 #include <float.h>
 
 #include <mutex>
@@ -41,7 +47,10 @@ enum { ST_DONE = 0, ST_OVERFLOW = 1, ST_SINGULAR = 2 };
 // Algorithmic bytes of the build (site PROF_SAI_BUILD), per finished column:
 // the final pattern's columns read (12 B per stored entry), the row patterns
 // of L read for candidates (4 B per entry) and the column written (12 B per entry).
+// Flops: d_swork holds the FP64 ones, d_swork32 the FP32 ones (the QR of
+// the refined form).
 __device__ double d_swork[PROF_NSITES * 2];
+__device__ double d_swork32;
 constexpr int MNMAX = 8;
 
 struct SaiMat {
@@ -51,7 +60,7 @@ struct SaiMat {
     const double* __restrict__ cv;
     const int64_t* __restrict__ rp;  // CSR pattern of A~
     const int32_t* __restrict__ rc;
-    const double* __restrict__ colnorm2;
+    const double* __restrict__ icn;  // 1/||A~e_j||^2 (0 for an empty column)
     double norm1;
 };
 
@@ -102,18 +111,72 @@ struct Tier {
     static constexpr size_t OFF_CF = OFF_CK + 4ull * HC;
     static constexpr size_t OFF_KP = OFF_CF + (size_t)HC;
     static constexpr size_t BYTES = a16(OFF_KP + (size_t)SCAP);
+    // distance between the workspaces of consecutive groups: a multiple of
+    // 128 bytes plus 32, so that the 8-lane groups of one warp start in
+    // different shared-memory banks
+    static constexpr size_t STRIDE = ((BYTES + 127) & ~size_t(127)) + 32;
     static_assert(HL >= 2 * LCAP && (HL & (HL - 1)) == 0, "row hash");
     static_assert(HC >= 2 * SCAP && (HC & (HC - 1)) == 0, "candidate hash");
 };
 
+using TierS = Tier<32, 8, 64, 128>;         // shared memory, small patterns, ~4.1 KB per group
 using Tier0 = Tier<64, 16, 128, 512>;      // shared memory, ~13.7 KB per warp
 using Tier1 = Tier<256, 64, 512, 2048>;    // global memory, ~150 KB per warp
 using Tier2 = Tier<1024, 128, 2048, 8192>; // global memory, ~1.1 MB per warp
 using Tier3 = Tier<2048, 128, 4096, 65536>; // global memory, ~2.4 MB per warp (up to 32768 candidates)
+using TierSF = Tier<32, 8, 64, 128, float>;
 using Tier0F = Tier<64, 16, 128, 512, float>;
 using Tier1F = Tier<256, 64, 512, 2048, float>;
 using Tier2F = Tier<1024, 128, 2048, 8192, float>;
 using Tier3F = Tier<2048, 128, 4096, 65536, float>;
+
+// The lanes that work on one column: a group of G consecutive lanes of a
+// warp (G = 32: the whole warp). Every reduction, vote and barrier below is
+// over the group only, so the groups of a warp run independent columns.
+template <int G>
+struct Grp {
+    static_assert(G == 8 || G == 16 || G == 32, "group size");
+    unsigned mask;  // the group's lanes within the warp
+    int base;       // first lane of the group
+    int l;          // lane within the group
+    __device__ __forceinline__ Grp()
+    {
+        const int lane = threadIdx.x & 31;
+        l = lane & (G - 1);
+        base = lane & ~(G - 1);
+        mask = G == 32 ? 0xffffffffu : (((1u << (G & 31)) - 1u) << base);
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    // the predicate's votes of the group, bit i = group lane i
+    __device__ __forceinline__ unsigned ballot(bool p) const
+    {
+        const unsigned b = __ballot_sync(mask, p);
+        return G == 32 ? b : (b >> base) & ((1u << (G & 31)) - 1u);
+    }
+    __device__ __forceinline__ bool any(bool p) const { return __any_sync(mask, p); }
+    template <class V>
+    __device__ __forceinline__ V bcast(V v, int src) const
+    {
+        return __shfl_sync(mask, v, base + src);
+    }
+    // butterfly sum over the group (for G = 32 the order of warp_sum)
+    template <class V>
+    __device__ __forceinline__ V sum(V v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+        return v;
+    }
+    __device__ __forceinline__ unsigned long long min_u64(unsigned long long v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(mask, v, o);
+            v = w < v ? w : v;
+        }
+        return v;
+    }
+};
 
 template <class TQ>
 struct WsT {
@@ -209,13 +272,13 @@ __device__ __forceinline__ int hslot(const int32_t* hk, int32_t key)
 
 // Adds the rows of column j of A~ to L. New rows get consecutive positions in
 // entry order, so L's order does not depend on scheduling. False on overflow.
-template <class T>
+template <class T, int G>
 __device__ bool add_rows(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t j, int& nL)
 {
-    const int lane = lane_id();
+    const Grp<G> g;
     const int64_t b = A.cp[j], e = A.cp[j + 1];
-    for (int64_t base = b; base < e; base += 32) {
-        const int64_t q = base + lane;
+    for (int64_t base = b; base < e; base += G) {
+        const int64_t q = base + g.l;
         bool isnew = false;
         int slot = 0;
         int32_t i = -1;
@@ -223,36 +286,36 @@ __device__ bool add_rows(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t 
             i = A.ri[q];
             slot = hinsert<T::HL>(w.hk, i, isnew);
         }
-        if (__any_sync(SAI_FULL, slot < 0)) return false;
-        const unsigned mask = __ballot_sync(SAI_FULL, isnew);
+        if (g.any(slot < 0)) return false;
+        const unsigned mask = g.ballot(isnew);
         const int cnt = __popc(mask);
         if (nL + cnt > T::LCAP) return false;
         if (isnew) {
-            const int pos = nL + __popc(mask & ((1u << lane) - 1u));
+            const int pos = nL + __popc(mask & ((1u << g.l) - 1u));
             w.hv[slot] = pos;
             w.Lrow[pos] = i;
         }
         nL += cnt;
-        __syncwarp();
+        g.sync();
     }
     return true;
 }
 
 // Resets the per-column state to S = {k}, L = {k}, cv = e^.
-template <class T>
+template <class T, int G>
 __device__ void col_init(const WsT<typename T::TQ>& w, int32_t k, int& nL, int& nS, int& nfact)
 {
-    const int lane = lane_id();
-    for (int q = lane; q < T::HL; q += 32) w.hk[q] = -1;
-    __syncwarp();
-    if (lane == 0) {
+    const Grp<G> g;
+    for (int q = g.l; q < T::HL; q += G) w.hk[q] = -1;
+    g.sync();
+    if (g.l == 0) {
         bool ins;
         int sl = hinsert<T::HL>(w.hk, k, ins);
         w.hv[sl] = 0;
         w.Lrow[0] = k;
         w.cv[0] = 1;
     }
-    __syncwarp();
+    g.sync();
     nL = 1;
     nS = 1;
     nfact = 0;
@@ -260,30 +323,30 @@ __device__ void col_init(const WsT<typename T::TQ>& w, int32_t k, int& nL, int& 
 
 // Gathers the new columns S[nfact..nS), updates the QR factorisation and
 // solves R m = (Q^T e^)(0:nS). Returns ST_DONE, ST_OVERFLOW or ST_SINGULAR.
-template <class T>
+template <class T, int G>
 __device__ int ls_update(const WsT<typename T::TQ>& w, const SaiMat& A, int& nL, int nS, int& nfact)
 {
     using TQ = typename T::TQ;
-    const int lane = lane_id();
+    const Grp<G> g;
     const int nL_old = nL;
     for (int t = nfact; t < nS; ++t)
-        if (!add_rows<T>(w, A, w.S[t], nL)) return ST_OVERFLOW;
+        if (!add_rows<T, G>(w, A, w.S[t], nL)) return ST_OVERFLOW;
     // zero the new rows of the old columns and of cv, and the new columns
     for (int t = 0; t < nS; ++t) {
         TQ* col = w.Q + (size_t)t * T::LCAP;
-        for (int i = (t < nfact ? nL_old : 0) + lane; i < nL; i += 32) col[i] = 0;
+        for (int i = (t < nfact ? nL_old : 0) + g.l; i < nL; i += G) col[i] = 0;
     }
-    for (int i = nL_old + lane; i < nL; i += 32) w.cv[i] = 0;
-    __syncwarp();
+    for (int i = nL_old + g.l; i < nL; i += G) w.cv[i] = 0;
+    g.sync();
     for (int t = nfact; t < nS; ++t) {
         const int32_t j = w.S[t];
         TQ* col = w.Q + (size_t)t * T::LCAP;
-        for (int64_t q = A.cp[j] + lane; q < A.cp[j + 1]; q += 32) {
+        for (int64_t q = A.cp[j] + g.l; q < A.cp[j + 1]; q += G) {
             const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) col[pos] = (TQ)A.cv[q];
         }
     }
-    __syncwarp();
+    g.sync();
     // old reflectors on the new columns
     for (int jr = 0; jr < nfact; ++jr) {
         const TQ* v = w.Q + (size_t)jr * T::LCAP;
@@ -291,115 +354,115 @@ __device__ int ls_update(const WsT<typename T::TQ>& w, const SaiMat& A, int& nL,
         for (int t = nfact; t < nS; ++t) {
             TQ* col = w.Q + (size_t)t * T::LCAP;
             TQ d = 0;
-            for (int i = jr + lane; i < nL; i += 32) d = fma(v[i], col[i], d);
-            d = warp_sum_t(d);
+            for (int i = jr + g.l; i < nL; i += G) d = fma(v[i], col[i], d);
+            d = g.sum(d);
             const TQ f = bj * d;
-            for (int i = jr + lane; i < nL; i += 32) col[i] = fma(-f, v[i], col[i]);
-            __syncwarp();
+            for (int i = jr + g.l; i < nL; i += G) col[i] = fma(-f, v[i], col[i]);
+            g.sync();
         }
     }
     // factor the trailing block column by column
     for (int t = nfact; t < nS; ++t) {
         TQ* col = w.Q + (size_t)t * T::LCAP;
         TQ s2 = 0;
-        for (int i = t + lane; i < nL; i += 32) s2 = fma(col[i], col[i], s2);
-        s2 = warp_sum_t(s2);
+        for (int i = t + g.l; i < nL; i += G) s2 = fma(col[i], col[i], s2);
+        s2 = g.sum(s2);
         if (!(s2 > (TQ)0)) return ST_SINGULAR;
         const TQ nrm = sqrt(s2);
         const TQ x0 = col[t];
         const TQ alpha = x0 >= (TQ)0 ? -nrm : nrm;
         const TQ bt = (TQ)1 / (nrm * (nrm + fabs(x0)));  // 2/(v^T v), v^T v = 2 nrm (nrm + |x0|)
-        __syncwarp();
-        if (lane == 0) {
+        g.sync();
+        if (g.l == 0) {
             col[t] = x0 - alpha;
             w.rd[t] = alpha;
             w.beta[t] = bt;
         }
-        __syncwarp();
+        g.sync();
         for (int t2 = t + 1; t2 <= nS; ++t2) {
             TQ* c2 = t2 < nS ? w.Q + (size_t)t2 * T::LCAP : w.cv;
             TQ d = 0;
-            for (int i = t + lane; i < nL; i += 32) d = fma(col[i], c2[i], d);
-            d = warp_sum_t(d);
+            for (int i = t + g.l; i < nL; i += G) d = fma(col[i], c2[i], d);
+            d = g.sum(d);
             const TQ f = bt * d;
-            for (int i = t + lane; i < nL; i += 32) c2[i] = fma(-f, col[i], c2[i]);
-            __syncwarp();
+            for (int i = t + g.l; i < nL; i += G) c2[i] = fma(-f, col[i], c2[i]);
+            g.sync();
         }
     }
     nfact = nS;
     // back substitution (FP64 arithmetic on the stored factors)
-    for (int i = lane; i < nS; i += 32) w.m[i] = (double)w.cv[i];
-    __syncwarp();
+    for (int i = g.l; i < nS; i += G) w.m[i] = (double)w.cv[i];
+    g.sync();
     for (int t = nS - 1; t >= 0; --t) {
         const double mt = w.m[t] / (double)w.rd[t];
-        __syncwarp();
-        if (lane == 0) w.m[t] = mt;
+        g.sync();
+        if (g.l == 0) w.m[t] = mt;
         const TQ* col = w.Q + (size_t)t * T::LCAP;
-        for (int i = lane; i < t; i += 32) w.m[i] = fma(-(double)col[i], mt, w.m[i]);
-        __syncwarp();
+        for (int i = g.l; i < t; i += G) w.m[i] = fma(-(double)col[i], mt, w.m[i]);
+        g.sync();
     }
     return ST_DONE;
 }
 
 // r = A~(L,S) m - e^ on L (only the columns with use[t] != 0 when use given);
 // returns ||r||^2.
-template <class T>
+template <class T, int G>
 __device__ double residual(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, int nS, const uint8_t* use)
 {
-    const int lane = lane_id();
-    for (int i = lane; i < nL; i += 32) w.r[i] = (i == 0) ? -1.0 : 0.0;
-    __syncwarp();
+    const Grp<G> g;
+    for (int i = g.l; i < nL; i += G) w.r[i] = (i == 0) ? -1.0 : 0.0;
+    g.sync();
     for (int t = 0; t < nS; ++t) {
         if (use && !use[t]) continue;
         const int32_t j = w.S[t];
         const double mt = w.m[t];
-        for (int64_t q = A.cp[j] + lane; q < A.cp[j + 1]; q += 32) {
+        for (int64_t q = A.cp[j] + g.l; q < A.cp[j + 1]; q += G) {
             const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) w.r[pos] = fma(A.cv[q], mt, w.r[pos]);
         }
-        __syncwarp();
+        g.sync();
     }
     double s = 0.0;
-    for (int i = lane; i < nL; i += 32) s = fma(w.r[i], w.r[i], s);
-    return warp_sum(s);
+    for (int i = g.l; i < nL; i += G) s = fma(w.r[i], w.r[i], s);
+    return g.sum(s);
 }
 
 // One FP64 refinement step of the LS solution by the corrected semi-normal
 // equations: m += R^{-1} R^{-T} A^^T (e^ - A^ m), with the residual and
 // A^^T r formed in FP64 from the FP64 values of A~ and R from the (FP32) QR.
-template <class T>
+template <class T, int G>
 __device__ void refine(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, int nS)
 {
-    const int lane = lane_id();
-    residual<T>(w, A, nL, nS, nullptr);  // r = A^ m - e^
-    for (int t = lane; t < nS; t += 32) {
+    const Grp<G> g;
+    residual<T, G>(w, A, nL, nS, nullptr);  // r = A^ m - e^
+    for (int t = g.l; t < nS; t += G) {
         const int32_t j = w.S[t];
-        double g = 0.0;
+        double gt = 0.0;
         for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
             const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
-            if (pos >= 0) g = fma(-A.cv[q], w.r[pos], g);
+            if (pos >= 0) gt = fma(-A.cv[q], w.r[pos], gt);
         }
-        w.g[t] = g;  // A^^T (e^ - A^ m)
+        w.g[t] = gt;  // A^^T (e^ - A^ m)
     }
-    __syncwarp();
+    g.sync();
     // R^T y = g (forward), R(t,i) = Q[i][t] for i > t
     for (int t = 0; t < nS; ++t) {
         const double yt = w.g[t] / (double)w.rd[t];
-        __syncwarp();
-        if (lane == 0) w.g[t] = yt;
-        for (int i = t + 1 + lane; i < nS; i += 32) w.g[i] = fma(-(double)w.Q[(size_t)i * T::LCAP + t], yt, w.g[i]);
-        __syncwarp();
+        g.sync();
+        if (g.l == 0) w.g[t] = yt;
+        for (int i = t + 1 + g.l; i < nS; i += G) w.g[i] = fma(-(double)w.Q[(size_t)i * T::LCAP + t], yt, w.g[i]);
+        g.sync();
     }
     // R d = y (backward)
     for (int t = nS - 1; t >= 0; --t) {
         const double dt = w.g[t] / (double)w.rd[t];
-        __syncwarp();
-        if (lane == 0) w.g[t] = dt;
-        for (int i = lane; i < t; i += 32) w.g[i] = fma(-(double)w.Q[(size_t)t * T::LCAP + i], dt, w.g[i]);
-        __syncwarp();
+        g.sync();
+        if (g.l == 0) w.g[t] = dt;
+        for (int i = g.l; i < t; i += G) w.g[i] = fma(-(double)w.Q[(size_t)t * T::LCAP + i], dt, w.g[i]);
+        g.sync();
     }
-    for (int t = lane; t < nS; t += 32) w.m[t] += w.g[t];
-    __syncwarp();
+    for (int t = g.l; t < nS; t += G) w.m[t] += w.g[t];
+    g.sync();
 }
 
 // Algorithmic flops of one ls_update call that grows the factor of an
@@ -415,57 +478,60 @@ __device__ __forceinline__ long long qr_flops(int nL, int c, int nS)
     return f + (long long)nS * nS;
 }
 
-// sum of nnz(A~(:,j)) over j in S (warp-uniform result)
-template <class T>
+// sum of nnz(A~(:,j)) over j in S (group-uniform result)
+template <class T, int G>
 __device__ int s_nnz(const WsT<typename T::TQ>& w, const SaiMat& A, int nS)
 {
+    const Grp<G> g;
     int c = 0;
-    for (int t = lane_id(); t < nS; t += 32) c += (int)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]);
-    return warp_sum_int(c);
+    for (int t = g.l; t < nS; t += G) c += (int)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]);
+    return g.sum(c);
 }
 
-template <class T>
-__device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out, int& l_out,
-                           double& rn_out, int& nL_out, long long& fl)
+// fl: FP64 flops of the column; fq: flops of its QR (in the QR's type)
+template <class T, int G>
+__device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out,
+                           int& l_out, double& rn_out, int& nL_out, long long& fl, long long& fq)
 {
-    const int lane = lane_id();
+    const Grp<G> g;
     int nL, nS, nfact;
-    col_init<T>(w, k, nL, nS, nfact);
-    if (lane == 0) w.S[0] = k;
-    __syncwarp();
+    col_init<T, G>(w, k, nL, nS, nfact);
+    if (g.l == 0) w.S[0] = k;
+    g.sync();
     int l = 0;
     double rn = 0.0;
     fl = 0;
+    fq = 0;
     for (;;) {
         const int c0 = nfact;
-        int st = ls_update<T>(w, A, nL, nS, nfact);
+        int st = ls_update<T, G>(w, A, nL, nS, nfact);
         if (st != ST_DONE) return st;
-        const long long sn = s_nnz<T>(w, A, nS);
-        fl += qr_flops(nL, c0, nS);
+        const long long sn = s_nnz<T, G>(w, A, nS);
+        fq += qr_flops(nL, c0, nS);
         if (sizeof(typename T::TQ) < sizeof(double)) {
-            refine<T>(w, A, nL, nS);
+            refine<T, G>(w, A, nL, nS);
             fl += 4 * sn + 2LL * nL + 2LL * nS * nS;
         }
-        const double rn2 = residual<T>(w, A, nL, nS, nullptr);
+        const double rn2 = residual<T, G>(w, A, nL, nS, nullptr);
         fl += 2 * sn + 2LL * nL;
         rn = sqrt(rn2);
         if (rn <= a.delta || l >= a.max_aug) break;
         // candidate set N \ S from the rows of L
-        for (int q = lane; q < T::HC; q += 32) {
+        for (int q = g.l; q < T::HC; q += G) {
             w.ck[q] = -1;
             w.cf[q] = 0;
         }
-        __syncwarp();
+        g.sync();
         bool ovf = false;
-        for (int t = lane; t < nS; t += 32) {
+        for (int t = g.l; t < nS; t += G) {
             bool ins;
             int sl = hinsert<T::HC>(w.ck, w.S[t], ins);
             if (sl < 0) ovf = true;
             else w.cf[sl] = 1;
         }
-        __syncwarp();
+        g.sync();
         int ncand = 0;
-        for (int idx = lane; idx < nL; idx += 32) {
+        for (int idx = g.l; idx < nL; idx += G) {
             const int32_t i = w.Lrow[idx];
             for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
                 bool ins;
@@ -474,21 +540,21 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
                 ncand += ins;
             }
         }
-        ncand = warp_sum_int(ncand);
-        if (__any_sync(SAI_FULL, ovf) || ncand + nS > T::HC / 2) return ST_OVERFLOW;
-        __syncwarp();
+        ncand = g.sum(ncand);
+        if (g.any(ovf) || ncand + nS > T::HC / 2) return ST_OVERFLOW;
+        g.sync();
         // compact the candidates (occupied slots not in S) to the front of ck,
         // in slot order, so that the scoring keeps every lane on a candidate;
         // a chunk is read whole before it is written, and the writes stay at
         // or below it
         int nc = 0;
-        for (int s0 = 0; s0 < T::HC; s0 += 32) {
-            const int32_t j = w.ck[s0 + lane];
-            const bool keep = j >= 0 && !w.cf[s0 + lane];
-            const unsigned km = __ballot_sync(SAI_FULL, keep);
-            if (keep) w.ck[nc + __popc(km & ((1u << lane) - 1u))] = j;
+        for (int s0 = 0; s0 < T::HC; s0 += G) {
+            const int32_t j = w.ck[s0 + g.l];
+            const bool keep = j >= 0 && !w.cf[s0 + g.l];
+            const unsigned km = g.ballot(keep);
+            if (keep) w.ck[nc + __popc(km & ((1u << g.l) - 1u))] = j;
             nc += __popc(km);
-            __syncwarp();
+            g.sync();
         }
         // profitability keys and a per-lane sorted top list (the selection of
         // the mn smallest keys below does not depend on which lane scored what)
@@ -496,20 +562,21 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
 #pragma unroll
         for (int q = 0; q < MNMAX; ++q) top[q] = ULLONG_MAX;
         int fsc = 0;
-        for (int idx = lane; idx < nc; idx += 32) {
+        const double irn2 = 1.0 / rn2;  // rn2 > delta^2 >= 0 here
+        for (int idx = g.l; idx < nc; idx += G) {
             const int32_t j = w.ck[idx];
-            const double nj = A.colnorm2[j];
-            if (!(nj > 0.0)) continue;
+            const double inj = A.icn[j];
+            if (!(inj > 0.0)) continue;
             fsc += 2 * (int)(A.cp[j + 1] - A.cp[j]) + 5;  // r^T a_j, rho_j^2 and its key
             double d = 0.0;
             for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
                 const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
                 if (pos >= 0) d = fma(w.r[pos], A.cv[q], d);
             }
-            const double rho2 = rn2 - d * d / nj;
-            double tq = rho2 / rn2;
+            // rho_j^2 / ||r||^2 = 1 - (r^T a_j)^2 / (||a_j||^2 ||r||^2), in [0, 1]
+            double tq = fma(-(d * d), inj * irn2, 1.0);
             tq = fmin(fmax(tq, 0.0), 1.0);
-            unsigned long long x = ((unsigned long long)floor(tq * a.scale) << 32) | (unsigned)j;
+            unsigned long long x = (__double2ull_rz(tq * a.scale) << 32) | (unsigned)j;
 #pragma unroll
             for (int q = 0; q < MNMAX; ++q) {
                 const unsigned long long lo = top[q] < x ? top[q] : x;
@@ -517,10 +584,10 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
                 top[q] = lo;
             }
         }
-        fl += warp_sum_int(fsc);
+        fl += g.sum(fsc);
         int added = 0;
         for (int sel = 0; sel < a.mn; ++sel) {
-            const unsigned long long best = warp_min_u64(top[0]);
+            const unsigned long long best = g.min_u64(top[0]);
             if (best == ULLONG_MAX) break;
             if (top[0] == best) {
 #pragma unroll
@@ -528,10 +595,10 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
                 top[MNMAX - 1] = ULLONG_MAX;
             }
             if (nS + added >= T::SCAP) return ST_OVERFLOW;
-            if (lane == 0) w.S[nS + added] = (int32_t)(best & 0xffffffffull);
+            if (g.l == 0) w.S[nS + added] = (int32_t)(best & 0xffffffffull);
             ++added;
         }
-        __syncwarp();
+        g.sync();
         if (added == 0) break;
         nS += added;
         ++l;
@@ -544,46 +611,47 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
 }
 
 // PSAI(tol), reading (A): S^(l+1) = P(a^(l+1)) u S_kept^(l), a^(l+1) = |A~| a^(l).
-template <class T>
-__device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out, int& l_out,
-                           double& rn_pre, double& rn_post, int& nL_out, long long& fl)
+template <class T, int G>
+__device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out,
+                           int& l_out, double& rn_pre, double& rn_post, int& nL_out, long long& fl, long long& fq)
 {
-    const int lane = lane_id();
+    const Grp<G> g;
     int nL, nS, nfact;
-    col_init<T>(w, k, nL, nS, nfact);
-    if (lane == 0) {
+    col_init<T, G>(w, k, nL, nS, nfact);
+    if (g.l == 0) {
         w.S[0] = k;
         w.a0[0] = k;
     }
-    __syncwarp();
+    g.sync();
     int na = 1;
     int32_t* apat = w.a0;
     int32_t* anew = w.a1;
     int l = 0;
     fl = 0;
+    fq = 0;
     for (;;) {
         const int c0 = nfact;
-        int st = ls_update<T>(w, A, nL, nS, nfact);
+        int st = ls_update<T, G>(w, A, nL, nS, nfact);
         if (st != ST_DONE) return st;
-        const long long sn = s_nnz<T>(w, A, nS);
-        fl += qr_flops(nL, c0, nS);
+        const long long sn = s_nnz<T, G>(w, A, nS);
+        fq += qr_flops(nL, c0, nS);
         if (sizeof(typename T::TQ) < sizeof(double)) {
-            refine<T>(w, A, nL, nS);
+            refine<T, G>(w, A, nL, nS);
             fl += 4 * sn + 2LL * nL + 2LL * nS * nS;
         }
-        const double rn = sqrt(residual<T>(w, A, nL, nS, nullptr));
+        const double rn = sqrt(residual<T, G>(w, A, nL, nS, nullptr));
         fl += 2 * sn + 2LL * nL;
         double tolk = a.tol;
         if (a.tol_mode == 0) {
             int nz = 0;
-            for (int t = lane; t < nS; t += 32) nz += (w.m[t] != 0.0);
-            nz = warp_sum_int(nz);
+            for (int t = g.l; t < nS; t += G) nz += (w.m[t] != 0.0);
+            nz = g.sum(nz);
             tolk = (nz > 0 && A.norm1 > 0.0) ? a.delta / ((double)nz * A.norm1) : 0.0;
         }
         if (a.tol_mode == 2) {
             // PSAI(lfill): kp[t] = m_t is among the lfill largest in magnitude
             // (equal magnitudes to the smaller column index)
-            for (int t = lane; t < nS; t += 32) {
+            for (int t = g.l; t < nS; t += G) {
                 const double mt = fabs(w.m[t]);
                 const int32_t jt = w.S[t];
                 int rank = 0;
@@ -595,16 +663,16 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             }
         } else {
             // keep flags: kp[t] = |m_t| > tol_k
-            for (int t = lane; t < nS; t += 32) w.kp[t] = (uint8_t)(fabs(w.m[t]) > tolk);
+            for (int t = g.l; t < nS; t += G) w.kp[t] = (uint8_t)(fabs(w.m[t]) > tolk);
         }
-        __syncwarp();
+        g.sync();
         if (rn <= a.delta || l >= a.lmax) {
             rn_pre = rn;
-            rn_post = sqrt(residual<T>(w, A, nL, nS, w.kp));
+            rn_post = sqrt(residual<T, G>(w, A, nL, nS, w.kp));
             fl += 2 * sn + 2LL * nL;
             // compact the kept entries to the front of S / m (order preserved)
             int q = 0;
-            if (lane == 0) {
+            if (g.l == 0) {
                 for (int t = 0; t < nS; ++t)
                     if (w.kp[t]) {
                         w.S[q] = w.S[t];
@@ -612,8 +680,8 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
                         ++q;
                     }
             }
-            nS_out = __shfl_sync(SAI_FULL, q, 0);
-            __syncwarp();
+            nS_out = g.bcast(q, 0);
+            g.sync();
             l_out = l;
             nL_out = nL;
             return ST_DONE;
@@ -622,21 +690,21 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             // reading (C): S^(l+1) = S_kept^(l) u (P(a^(l+1)) \ P(a^(l))), so a
             // dropped position never comes back. Hash flags: 2 in P(a^(l)),
             // 8 kept member of S^(l), 4 in P(a^(l+1)).
-            for (int q = lane; q < T::HC; q += 32) {
+            for (int q = g.l; q < T::HC; q += G) {
                 w.ck[q] = -1;
                 w.cf[q] = 0;
             }
-            __syncwarp();
+            g.sync();
             bool ovf = false;
-            for (int t = lane; t < na; t += 32) {
+            for (int t = g.l; t < na; t += G) {
                 bool ins;
                 const int sl = hinsert<T::HC>(w.ck, apat[t], ins);
                 if (sl < 0) ovf = true;
                 else w.cf[sl] |= 2;
             }
-            __syncwarp();
+            g.sync();
             int nk = 0;
-            for (int t = lane; t < nS; t += 32) {
+            for (int t = g.l; t < nS; t += G) {
                 if (!w.kp[t]) continue;
                 ++nk;
                 bool ins;
@@ -644,37 +712,37 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
                 if (sl < 0) ovf = true;
                 else w.cf[sl] |= 8;
             }
-            nk = warp_sum_int(nk);
-            __syncwarp();
+            nk = g.sum(nk);
+            g.sync();
             for (int t = 0; t < na; ++t) {
                 const int32_t j = apat[t];
                 const int64_t b = A.cp[j], e = A.cp[j + 1];
-                for (int64_t q = b + lane; q < e; q += 32) {
+                for (int64_t q = b + g.l; q < e; q += G) {
                     bool ins;
                     const int sl = hinsert<T::HC>(w.ck, A.ri[q], ins);
                     if (sl < 0) ovf = true;
                     else w.cf[sl] |= 4;
                 }
-                __syncwarp();
+                g.sync();
             }
-            if (__any_sync(SAI_FULL, ovf)) return ST_OVERFLOW;
-            const unsigned lt = (1u << lane) - 1u;
+            if (g.any(ovf)) return ST_OVERFLOW;
+            const unsigned lt = (1u << g.l) - 1u;
             int nb = 0, nf = 0;
-            for (int s0 = 0; s0 < T::HC; s0 += 32) {
-                const int32_t key = w.ck[s0 + lane];
-                const uint8_t f = key >= 0 ? w.cf[s0 + lane] : (uint8_t)0;
-                const unsigned mn = __ballot_sync(SAI_FULL, (f & 4) != 0);
-                const unsigned mf = __ballot_sync(SAI_FULL, (f & 4) != 0 && (f & 10) == 0);
+            for (int s0 = 0; s0 < T::HC; s0 += G) {
+                const int32_t key = w.ck[s0 + g.l];
+                const uint8_t f = key >= 0 ? w.cf[s0 + g.l] : (uint8_t)0;
+                const unsigned mn = g.ballot((f & 4) != 0);
+                const unsigned mf = g.ballot((f & 4) != 0 && (f & 10) == 0);
                 if (nb + __popc(mn) > T::SCAP) return ST_OVERFLOW;
                 if (f & 4) anew[nb + __popc(mn & lt)] = key;
                 nb += __popc(mn);
                 nf += __popc(mf);
             }
-            __syncwarp();
+            g.sync();
             if (nk + nf == 0) {
                 // nothing kept and no new position: the column stops at loop l
                 rn_pre = rn;
-                rn_post = sqrt(residual<T>(w, A, nL, nS, w.kp));
+                rn_post = sqrt(residual<T, G>(w, A, nL, nS, w.kp));
                 fl += 2 * sn + 2LL * nL;
                 nS_out = 0;
                 l_out = l;
@@ -683,23 +751,23 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             }
             if (nk + nf > T::SCAP) return ST_OVERFLOW;
             const bool dropped = nk < nS;
-            if (dropped && lane == 0) {  // the kept members, in list order, to the front
+            if (dropped && g.l == 0) {  // the kept members, in list order, to the front
                 int q = 0;
                 for (int t = 0; t < nS; ++t)
                     if (w.kp[t]) w.S[q++] = w.S[t];
             }
-            __syncwarp();
+            g.sync();
             int q = nk;
-            for (int s0 = 0; s0 < T::HC; s0 += 32) {  // then the frontier, in slot order
-                const int32_t key = w.ck[s0 + lane];
-                const uint8_t f = key >= 0 ? w.cf[s0 + lane] : (uint8_t)0;
+            for (int s0 = 0; s0 < T::HC; s0 += G) {  // then the frontier, in slot order
+                const int32_t key = w.ck[s0 + g.l];
+                const uint8_t f = key >= 0 ? w.cf[s0 + g.l] : (uint8_t)0;
                 const bool fr = (f & 4) != 0 && (f & 10) == 0;
-                const unsigned mf = __ballot_sync(SAI_FULL, fr);
+                const unsigned mf = g.ballot(fr);
                 if (fr) w.S[q + __popc(mf & lt)] = key;
                 q += __popc(mf);
             }
-            __syncwarp();
-            if (dropped) col_init<T>(w, k, nL, nS, nfact);  // refactor from scratch on the new pattern
+            g.sync();
+            if (dropped) col_init<T, G>(w, k, nL, nS, nfact);  // refactor from scratch on the new pattern
             nS = q;
             int32_t* sw = apat;
             apat = anew;
@@ -709,17 +777,17 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             continue;
         }
         // a^(l+1): union of the column patterns of a^(l); positions in entry order
-        for (int q = lane; q < T::HC; q += 32) {
+        for (int q = g.l; q < T::HC; q += G) {
             w.ck[q] = -1;
             w.cf[q] = 0;
         }
-        __syncwarp();
+        g.sync();
         int nb = 0;
         for (int t = 0; t < na; ++t) {
             const int32_t j = apat[t];
             const int64_t b = A.cp[j], e = A.cp[j + 1];
-            for (int64_t base = b; base < e; base += 32) {
-                const int64_t q = base + lane;
+            for (int64_t base = b; base < e; base += G) {
+                const int64_t q = base + g.l;
                 bool isnew = false;
                 int slot = 0;
                 int32_t i = -1;
@@ -727,61 +795,61 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
                     i = A.ri[q];
                     slot = hinsert<T::HC>(w.ck, i, isnew);
                 }
-                if (__any_sync(SAI_FULL, slot < 0)) return ST_OVERFLOW;
-                const unsigned mask = __ballot_sync(SAI_FULL, isnew);
+                if (g.any(slot < 0)) return ST_OVERFLOW;
+                const unsigned mask = g.ballot(isnew);
                 const int cnt = __popc(mask);
                 if (nb + cnt > T::SCAP) return ST_OVERFLOW;
-                if (isnew) anew[nb + __popc(mask & ((1u << lane) - 1u))] = i;
+                if (isnew) anew[nb + __popc(mask & ((1u << g.l) - 1u))] = i;
                 nb += cnt;
-                __syncwarp();
+                g.sync();
             }
         }
         // cf = 1 marks members of S^(l) inside a^(l+1); a dropped member that is
         // not in a^(l+1) leaves the pattern (S shrinks)
         bool shrink = false;
-        for (int t = lane; t < nS; t += 32) {
+        for (int t = g.l; t < nS; t += G) {
             const int sl = hslot<T::HC>(w.ck, w.S[t]);
             if (sl >= 0) w.cf[sl] = 1;
             else if (!w.kp[t]) shrink = true;
         }
-        shrink = __any_sync(SAI_FULL, shrink);
-        __syncwarp();
+        shrink = g.any(shrink);
+        g.sync();
         if (!shrink) {
             // pure growth: append the members of a^(l+1) not in S, in list order
             int add = 0;
-            for (int base = 0; base < nb; base += 32) {
-                const int t = base + lane;
+            for (int base = 0; base < nb; base += G) {
+                const int t = base + g.l;
                 bool fresh = false;
                 int32_t j = -1;
                 if (t < nb) {
                     j = anew[t];
                     fresh = w.cf[hslot<T::HC>(w.ck, j)] == 0;
                 }
-                const unsigned mask = __ballot_sync(SAI_FULL, fresh);
+                const unsigned mask = g.ballot(fresh);
                 if (nS + add + __popc(mask) > T::SCAP) return ST_OVERFLOW;
-                if (fresh) w.S[nS + add + __popc(mask & ((1u << lane) - 1u))] = j;
+                if (fresh) w.S[nS + add + __popc(mask & ((1u << g.l) - 1u))] = j;
                 add += __popc(mask);
             }
-            __syncwarp();
+            g.sync();
             nS += add;
         } else {
             // rebuild from scratch with S = a^(l+1), then the kept members of
             // S^(l) outside a^(l+1)
             int q2 = nb;
-            if (lane == 0) {
+            if (g.l == 0) {
                 for (int t = 0; t < nS; ++t)
                     if (w.kp[t] && hslot<T::HC>(w.ck, w.S[t]) < 0) {
                         if (q2 < T::SCAP) apat[q2 - nb] = w.S[t];
                         ++q2;
                     }
             }
-            q2 = __shfl_sync(SAI_FULL, q2, 0);
-            __syncwarp();
+            q2 = g.bcast(q2, 0);
+            g.sync();
             if (q2 > T::SCAP) return ST_OVERFLOW;
             // apat (old a^(l)) is free now: it holds the extra kept members
-            for (int t = lane; t < q2; t += 32) w.S[t] = t < nb ? anew[t] : apat[t - nb];
-            __syncwarp();
-            col_init<T>(w, k, nL, nS, nfact);
+            for (int t = g.l; t < q2; t += G) w.S[t] = t < nb ? anew[t] : apat[t - nb];
+            g.sync();
+            col_init<T, G>(w, k, nL, nS, nfact);
             nS = q2;
         }
         // a^(l+1) becomes current
@@ -793,68 +861,82 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
     }
 }
 
-template <class T, bool SMEM, bool PSAI>
+// Persistent build kernel: each warp takes 32/G consecutive columns from the
+// atomic queue (work list, or 0..nwork-1), one per group of G lanes, until
+// the queue is empty. The groups of a warp start their columns together and
+// wait for one another before the next ones, so that columns of similar
+// shape run their steps in the same instructions rather than one group after
+// another. SMEM: the workspaces live in dynamic shared memory, one per
+// group; otherwise in gscratch, one per group of the grid.
+template <class T, int G, bool SMEM, bool PSAI>
 __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa, const int32_t* __restrict__ work,
                                              int32_t nwork, int* next, char* gscratch, Out out, int32_t* ovf_list,
                                              int* ovf_cnt, int* err, int tier_id)
 {
     extern __shared__ __align__(16) char smem[];
-    const int lane = lane_id();
-    const int wib = threadIdx.x >> 5;
-    char* base = SMEM ? smem + (size_t)wib * T::BYTES
-                      : gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * T::BYTES;
+    const Grp<G> g;
+    constexpr int GPW = 32 / G;  // groups per warp
+    const int grp = (int)(threadIdx.x >> 5) * GPW + (g.base / G);  // group index within the block
+    char* base = SMEM ? smem + (size_t)grp * T::STRIDE
+                      : gscratch + ((size_t)blockIdx.x * (blockDim.x / G) + grp) * T::STRIDE;
     const WsT<typename T::TQ> w = bind_ws<T>(base);
     double work_bytes = 0.0;
-    long long work_flops = 0;
+    long long work_flops = 0, work_flops_q = 0;
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(next, 1);
-        item = __shfl_sync(SAI_FULL, item, 0);
-        if (item >= nwork) break;
-        const int32_t k = work ? work[item] : item;
-        int nS = 0, l = 0, nL = 0;
-        double rn = 0.0, rpost = 0.0;
-        long long cfl = 0;
-        int st = PSAI ? psai_column<T>(w, A, k, pa, nS, l, rn, rpost, nL, cfl)
-                      : spai_column<T>(w, A, k, sa, nS, l, rn, nL, cfl);
-        if (st == ST_DONE) {
-            if (nS > out.smax) st = ST_OVERFLOW;
-        }
-        if (st == ST_DONE) {
-            const size_t o = (size_t)k * out.smax;
-            for (int t = lane; t < nS; t += 32) {
-                out.rows[o + t] = w.S[t];
-                out.vals[o + t] = w.m[t];
+        int first = 0;
+        if ((threadIdx.x & 31) == 0) first = atomicAdd(next, GPW);
+        first = __shfl_sync(SAI_FULL, first, 0);
+        if (first >= nwork) break;
+        const int item = first + g.base / G;
+        if (item < nwork) {
+            const int32_t k = work ? work[item] : item;
+            int nS = 0, l = 0, nL = 0;
+            double rn = 0.0, rpost = 0.0;
+            long long cfl = 0, cfq = 0;
+            int st = PSAI ? psai_column<T, G>(w, A, k, pa, nS, l, rn, rpost, nL, cfl, cfq)
+                          : spai_column<T, G>(w, A, k, sa, nS, l, rn, nL, cfl, cfq);
+            if (st == ST_DONE) {
+                if (nS > out.smax) st = ST_OVERFLOW;
             }
-            double cb = 0.0;
-            for (int t = lane; t < nS; t += 32) cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
-            for (int t = lane; t < nL; t += 32) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
-            work_bytes += warp_sum(cb);
-            work_flops += cfl;
-            if (lane == 0) {
-                out.cnt[k] = nS;
-                out.loops[k] = l;
-                out.res[k] = rn;
-                if (out.res_post) out.res_post[k] = rpost;
-                out.tier[k] = tier_id;
-            }
-        } else if (st == ST_OVERFLOW) {
-            if (lane == 0) {
-                if (ovf_list) {
-                    int p = atomicAdd(ovf_cnt, 1);
-                    ovf_list[p] = k;
-                } else {
-                    atomicOr(err, 1);
+            if (st == ST_DONE) {
+                const size_t o = (size_t)k * out.smax;
+                for (int t = g.l; t < nS; t += G) {
+                    out.rows[o + t] = w.S[t];
+                    out.vals[o + t] = w.m[t];
                 }
+                double cb = 0.0;
+                for (int t = g.l; t < nS; t += G) cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
+                for (int t = g.l; t < nL; t += G) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
+                work_bytes += g.sum(cb);
+                work_flops += cfl;
+                work_flops_q += cfq;
+                if (g.l == 0) {
+                    out.cnt[k] = nS;
+                    out.loops[k] = l;
+                    out.res[k] = rn;
+                    if (out.res_post) out.res_post[k] = rpost;
+                    out.tier[k] = tier_id;
+                }
+            } else if (st == ST_OVERFLOW) {
+                if (g.l == 0) {
+                    if (ovf_list) {
+                        int p = atomicAdd(ovf_cnt, 1);
+                        ovf_list[p] = k;
+                    } else {
+                        atomicOr(err, 1);
+                    }
+                }
+            } else {
+                if (g.l == 0) atomicOr(err, 2);
             }
-        } else {
-            if (lane == 0) atomicOr(err, 2);
         }
         __syncwarp();
     }
-    if (lane == 0 && work_bytes > 0.0) {
+    if (g.l == 0 && work_bytes > 0.0) {
+        const bool q32 = sizeof(typename T::TQ) < sizeof(double);
         atomicAdd(&d_swork[2 * PROF_SAI_BUILD], work_bytes);
-        atomicAdd(&d_swork[2 * PROF_SAI_BUILD + 1], (double)work_flops);
+        atomicAdd(&d_swork[2 * PROF_SAI_BUILD + 1], (double)(work_flops + (q32 ? 0 : work_flops_q)));
+        if (q32) atomicAdd(&d_swork32, (double)work_flops_q);
     }
 }
 
@@ -895,22 +977,33 @@ __global__ void k_stats(int32_t n, const int32_t* loops, const double* res, doub
 // columns not built in this call (outside a column list) hold tier -1
 __global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
 {
-    int c[4] = {0, 0, 0, 0};
+    int c[5] = {0, 0, 0, 0, 0};
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int t = tier[k];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) c[q] += t == q;
+        for (int q = 0; q < 5; ++q) c[q] += t == q;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 5; ++q) {
         const int w = warp_sum_int(c[q]);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(&out[2 + q], w);
     }
 }
 
+// icn[j] = 1/cn2[j] (0 where cn2[j] = 0: an empty column scores no key)
+__global__ void k_recip(int32_t n, const double* __restrict__ cn2, double* __restrict__ icn)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        icn[j] = cn2[j] > 0.0 ? 1.0 / cn2[j] : 0.0;
+}
+
 int g_num_sms = 0;
 
-template <class T, bool SMEM, bool PSAI>
+// Launches one tier of the build over a work list: G lanes per column,
+// workspaces in shared memory (SMEM: as many blocks per SM as fit) or in a
+// pool buffer (blocks_per_sm_t12 blocks of 8 warps per SM, no more than the
+// list needs).
+template <class T, int G, bool SMEM, bool PSAI>
 sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, const int32_t* work, int32_t nwork,
                        int* next, const Out& out, int32_t* ovf_list, int* ovf_cnt, int* err, int tier_id,
                        const sai_build_config& cfg, cudaStream_t st)
@@ -918,28 +1011,29 @@ sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, 
     if (nwork <= 0) return SAI_OK;
     const int warps_per_block = SMEM ? cfg.warps_t0 : 8;
     const int threads = 32 * warps_per_block;
+    const int groups = threads / G;
     int blocks;
     Buf scratch;
     size_t smem = 0;
     if (SMEM) {
-        smem = T::BYTES * warps_per_block;
-        SAI_CUDA(cudaFuncSetAttribute(k_sai<T, SMEM, PSAI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        smem = T::STRIDE * groups;
+        SAI_CUDA(cudaFuncSetAttribute(k_sai<T, G, SMEM, PSAI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sai<T, SMEM, PSAI>, threads, smem));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sai<T, G, SMEM, PSAI>, threads, smem));
         if (per_sm < 1) per_sm = 1;
         blocks = g_num_sms * per_sm;
     } else {
         blocks = g_num_sms * cfg.blocks_per_sm_t12;
-        const int need = (nwork + warps_per_block - 1) / warps_per_block;
+        const int need = (nwork + groups - 1) / groups;
         if (blocks > need) blocks = need;
-        SAI_TRY(scratch.alloc(T::BYTES * (size_t)warps_per_block * blocks, st, true));
+        SAI_TRY(scratch.alloc(T::STRIDE * (size_t)groups * blocks, st, true));
     }
     SAI_CUDA(cudaMemsetAsync(next, 0, sizeof(int), st));
     {
         ProfScope ps(PROF_SAI_BUILD, st);
-        k_sai<T, SMEM, PSAI><<<SAI_GRID(blocks), threads, smem, st>>>(A, sa, pa, work, nwork, next,
-                                                                     scratch.as<char>(), out, ovf_list, ovf_cnt,
-                                                                     err, tier_id);
+        k_sai<T, G, SMEM, PSAI><<<SAI_GRID(blocks), threads, smem, st>>>(A, sa, pa, work, nwork, next,
+                                                                        scratch.as<char>(), out, ovf_list, ovf_cnt,
+                                                                        err, tier_id);
     }
     SAI_CUDA(cudaGetLastError());
     return SAI_OK;
@@ -949,6 +1043,7 @@ template <class TQ>
 struct Tiers;
 template <>
 struct Tiers<double> {
+    using TS = TierS;
     using T0 = Tier0;
     using T1 = Tier1;
     using T2 = Tier2;
@@ -956,19 +1051,22 @@ struct Tiers<double> {
 };
 template <>
 struct Tiers<float> {
+    using TS = TierSF;
     using T0 = Tier0F;
     using T1 = Tier1F;
     using T2 = Tier2F;
     using T3 = Tier3F;
 };
 
-// Build configuration: the tier-0 warps per block, the blocks per SM of the
-// global-memory tiers and the order of the tier-0 work queue (heavy_first:
-// the columns of A~ with more than twice the average number of entries, in
-// index order, then the rest, in index order). Every column's result is the
-// same under any configuration; only the schedule changes.
+// Build configuration: the warps per block of the shared-memory tiers, the
+// blocks per SM of the global-memory tiers, the order of the first tier's
+// work queue (heavy_first: the columns of A~ with more than twice the
+// average number of entries, in index order, then the rest, in index order)
+// and the first tier (0: tier 0; 1 or 2: the small tier with 8- or 16-lane
+// groups). Only first_tier changes a column's arithmetic (its group size);
+// the rest changes the schedule alone.
 std::mutex g_cfg_mu;
-sai_build_config g_cfg = {8, 2, 0, 0.f};
+sai_build_config g_cfg = {8, 2, 0, 0, 0.f};
 
 sai_build_config current_config()
 {
@@ -1022,11 +1120,18 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     A.cv = h->At_v.as<double>();
     A.rp = h->Atr_rp.as<int64_t>();
     A.rc = h->Atr_ci.as<int32_t>();
-    A.colnorm2 = h->colnorm2.as<double>();
     A.norm1 = h->norm1;
 
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    Buf cnt, rows, vals, tier, ctr, ovf0, ovf1;
+    Buf icn;
+    SAI_TRY(icn.alloc(sizeof(double) * nn, st, true));
+    if (n > 0) {
+        const unsigned gi = sai_div_up(n, 256) < (unsigned)g_num_sms * 8 ? sai_div_up(n, 256) : g_num_sms * 8;
+        k_recip<<<SAI_GRID(gi), 256, 0, st>>>(n, h->colnorm2.as<double>(), icn.as<double>());
+        SAI_CUDA(cudaGetLastError());
+    }
+    A.icn = icn.as<double>();
+    Buf cnt, rows, vals, tier, ctr, ovf0, ovf1, ovfs;
     SAI_TRY(cnt.alloc(sizeof(int32_t) * nn, st, true));
     SAI_TRY(rows.alloc(sizeof(int32_t) * nn * smax, st, true));
     SAI_TRY(vals.alloc(sizeof(double) * nn * smax, st, true));
@@ -1037,6 +1142,7 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     SAI_TRY(ctr.alloc(sizeof(int) * 16, st, true));
     SAI_TRY(ovf0.alloc(sizeof(int32_t) * nn, st, true));
     SAI_TRY(ovf1.alloc(sizeof(int32_t) * nn, st, true));
+    if (cfg.first_tier != 0) SAI_TRY(ovfs.alloc(sizeof(int32_t) * nn, st, true));
     SAI_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(int) * 16, st));
     SAI_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->res_post.p, 0, sizeof(double) * nn, st));
@@ -1044,7 +1150,9 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     SAI_CUDA(cudaMemsetAsync(tier.p, 0xff, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->loops.p, 0, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->res.p, 0, sizeof(double) * nn, st));
-    int* c = ctr.as<int>();  // [0] next, [1..2] ovf counts t0, t1, [3] err, [4..9] stats, [10] ovf count t2
+    // [0] next, [1..2] ovf counts t0, t1, [3] err, [4..10] stats, [11] ovf count t2, [12] ovf count of
+    // the small tier
+    int* c = ctr.as<int>();
     Out out;
     out.smax = smax;
     out.cnt = cnt.as<int32_t>();
@@ -1055,6 +1163,7 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     out.res_post = PSAI ? P->res_post.as<double>() : nullptr;
     out.tier = tier.as<int32_t>();
 
+    using TS = typename Tiers<TQ>::TS;
     using T0 = typename Tiers<TQ>::T0;
     using T1 = typename Tiers<TQ>::T1;
     using T2 = typename Tiers<TQ>::T2;
@@ -1076,26 +1185,40 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
         SAI_CUDA(cudaGetLastError());
         queue = qbuf.as<int32_t>();
     }
-    SAI_TRY((launch_tier<T0, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovf0.as<int32_t>(), c + 1, c + 3, 0, cfg,
-                                            st)));
+    // the small tier first (first_tier 1 or 2): its overflows are tier 0's queue
+    const int32_t* q0 = queue;
+    int32_t n0 = nq;
+    if (cfg.first_tier != 0) {
+        if (cfg.first_tier == 1)
+            SAI_TRY((launch_tier<TS, 8, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 12,
+                                                    c + 3, 4, cfg, st)));
+        else
+            SAI_TRY((launch_tier<TS, 16, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 12,
+                                                     c + 3, 4, cfg, st)));
+        SAI_CUDA(cudaMemcpyAsync(&n0, c + 12, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaStreamSynchronize(st));
+        q0 = ovfs.as<int32_t>();
+    }
+    SAI_TRY((launch_tier<T0, 32, true, PSAI>(A, sa, pa, q0, n0, c + 0, out, ovf0.as<int32_t>(), c + 1, c + 3, 0, cfg,
+                                             st)));
     int hc[4];
     SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));
     if (hc[1] > 0) {
-        SAI_TRY((launch_tier<T1, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), hc[1], c + 0, out, ovf1.as<int32_t>(),
-                                                 c + 2, c + 3, 1, cfg, st)));
+        SAI_TRY((launch_tier<T1, 32, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), hc[1], c + 0, out,
+                                                     ovf1.as<int32_t>(), c + 2, c + 3, 1, cfg, st)));
         SAI_CUDA(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
         SAI_CUDA(cudaStreamSynchronize(st));
         if (hc[2] > 0) {
             // tier 2 queues its overflows in ovf0 (tier 1's input, no longer read)
-            SAI_TRY((launch_tier<T2, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out, ovf0.as<int32_t>(),
-                                                     c + 10, c + 3, 2, cfg, st)));
+            SAI_TRY((launch_tier<T2, 32, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out,
+                                                         ovf0.as<int32_t>(), c + 11, c + 3, 2, cfg, st)));
             int h3 = 0;
-            SAI_CUDA(cudaMemcpyAsync(&h3, c + 10, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaMemcpyAsync(&h3, c + 11, sizeof(int), cudaMemcpyDeviceToHost, st));
             SAI_CUDA(cudaStreamSynchronize(st));
             if (h3 > 0)
-                SAI_TRY((launch_tier<T3, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), h3, c + 0, out, nullptr,
-                                                         nullptr, c + 3, 3, cfg, st)));
+                SAI_TRY((launch_tier<T3, 32, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), h3, c + 0, out, nullptr,
+                                                             nullptr, c + 3, 3, cfg, st)));
         }
     }
     // assemble M (CSC, rows ascending) and its CSR copy
@@ -1123,12 +1246,12 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
         k_tier_count<<<SAI_GRID(g_num_sms * 2), 256, 0, st>>>(n, tier.as<int32_t>(), c + 4);
     }
     SAI_CUDA(cudaGetLastError());
-    int hs[6];
+    int hs[7];
     SAI_CUDA(cudaMemcpyAsync(hs, c + 4, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));
     P->n_c = hs[0];
     P->l_m = hs[1];
-    for (int q = 0; q < 4; ++q) P->n_tier[q] = hs[2 + q];
+    for (int q = 0; q < 5; ++q) P->n_tier[q] = hs[2 + q];
     SAI_CUDA(cudaEventElapsedTime(&P->ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1189,13 +1312,13 @@ bool config_ok(const sai_build_config& c)
 {
     return (c.warps_t0 == 4 || c.warps_t0 == 8) &&
            (c.blocks_per_sm_t12 == 1 || c.blocks_per_sm_t12 == 2 || c.blocks_per_sm_t12 == 4) &&
-           (c.heavy_first == 0 || c.heavy_first == 1);
+           (c.heavy_first == 0 || c.heavy_first == 1) && (c.first_tier >= 0 && c.first_tier <= 2);
 }
 }  // namespace
 
 sai_status sai_build_set_config_run(const sai_build_config* cfg)
 {
-    sai_build_config c = cfg ? *cfg : sai_build_config{8, 2, 0, 0.f};
+    sai_build_config c = cfg ? *cfg : sai_build_config{8, 2, 0, 0, 0.f};
     if (!config_ok(c)) return SAI_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_cfg_mu);
     g_cfg = c;
@@ -1258,39 +1381,62 @@ sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_s
     SAI_CUDA(cudaEventCreate(&e0));
     SAI_CUDA(cudaEventCreate(&e1));
     int best = -1;
-    for (int w : {4, 8})
-        for (int b : {1, 2, 4})
-            for (int hf : {0, 1}) {
-                sai_build_config c = {w, b, hf, 0.f};
-                float ms = 0.f;
-                for (int rep = 0; rep < 2; ++rep) {  // the first run warms the pool and the caches
-                    sai_precond_s P;
-                    SAI_CUDA(cudaEventRecord(e0, st));
-                    sai_status r;
-                    if (sai == 0)
-                        r = f32 ? build_common<false, float>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(),
-                                                             m, &c)
-                                : build_common<false, double>(h, sa, pa, smax, delta, st, true, &P,
-                                                              list.as<int32_t>(), m, &c);
-                    else
-                        r = f32 ? build_common<true, float>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(),
-                                                            m, &c)
-                                : build_common<true, double>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(),
-                                                             m, &c);
-                    if (r != SAI_OK) {
-                        cudaEventDestroy(e0);
-                        cudaEventDestroy(e1);
-                        return r;
-                    }
-                    SAI_CUDA(cudaEventRecord(e1, st));
-                    SAI_CUDA(cudaEventSynchronize(e1));
-                    SAI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                }
-                c.ms = ms;
-                out->cand[out->ncand] = c;
-                if (best < 0 || ms < out->cand[best].ms) best = out->ncand;
-                ++out->ncand;
+    // one sampled build (two runs: the first warms the pool and the caches)
+    auto run = [&](sai_build_config c, float* ms) -> sai_status {
+        for (int rep = 0; rep < 2; ++rep) {
+            sai_precond_s P;
+            SAI_CUDA(cudaEventRecord(e0, st));
+            sai_status r;
+            if (sai == 0)
+                r = f32 ? build_common<false, float>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(), m, &c)
+                        : build_common<false, double>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(), m,
+                                                      &c);
+            else
+                r = f32 ? build_common<true, float>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(), m, &c)
+                        : build_common<true, double>(h, sa, pa, smax, delta, st, true, &P, list.as<int32_t>(), m,
+                                                     &c);
+            if (r != SAI_OK) return r;
+            SAI_CUDA(cudaEventRecord(e1, st));
+            SAI_CUDA(cudaEventSynchronize(e1));
+            SAI_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        }
+        return SAI_OK;
+    };
+    auto try_cfg = [&](sai_build_config c) -> sai_status {
+        float ms = 0.f;
+        const sai_status r = run(c, &ms);
+        if (r != SAI_OK) return r;
+        c.ms = ms;
+        out->cand[out->ncand] = c;
+        if (best < 0 || ms < out->cand[best].ms) best = out->ncand;
+        ++out->ncand;
+        return SAI_OK;
+    };
+    sai_status r = SAI_OK;
+    // the first tier's shape and group size, with the warps per block
+    for (int ft : {0, 1, 2})
+        for (int w : {4, 8})
+            if (r == SAI_OK) r = try_cfg(sai_build_config{w, 2, 0, ft, 0.f});
+    // then the queue order, then the blocks per SM of the global-memory tiers
+    if (r == SAI_OK) {
+        sai_build_config c = out->cand[best];
+        c.heavy_first = 1;
+        r = try_cfg(c);
+    }
+    if (r == SAI_OK) {
+        const sai_build_config c0 = out->cand[best];
+        for (int b : {1, 4})
+            if (r == SAI_OK) {
+                sai_build_config c = c0;
+                c.blocks_per_sm_t12 = b;
+                r = try_cfg(c);
             }
+    }
+    if (r != SAI_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return r;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     out->chosen = out->cand[best];
@@ -1302,11 +1448,13 @@ sai_status sai_build_work_reset()
 {
     double z[PROF_NSITES * 2] = {};
     SAI_CUDA(cudaMemcpyToSymbol(d_swork, z, sizeof(z)));
+    SAI_CUDA(cudaMemcpyToSymbol(d_swork32, z, sizeof(double)));
     return SAI_OK;
 }
 
-sai_status sai_build_work_read(double* out)
+sai_status sai_build_work_read(double* out, double* flops32)
 {
     SAI_CUDA(cudaMemcpyFromSymbol(out, d_swork, sizeof(double) * PROF_NSITES * 2));
+    SAI_CUDA(cudaMemcpyFromSymbol(flops32, d_swork32, sizeof(double)));
     return SAI_OK;
 }

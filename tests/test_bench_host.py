@@ -25,6 +25,13 @@ def test_site_bounds_and_fractions():
     # an FP32 site uses the FP32 peak
     r = bench.site_roofline("gmres_project_fp32", dict(ms=1.0, launches=1, bytes=1e3, flops=1e12), PEAKS)
     assert r["peak"] == bench.FP32_PEAK_TFLOPS
+    # a mixed site: 1e9 FP64 and 8e10 FP32 flops in 2 ms need 0.8 + 1.0 ms at the two peaks
+    fp64, fp32 = bench.FP64_PEAK_TFLOPS * 1e12, bench.FP32_PEAK_TFLOPS * 1e12
+    r = bench.site_roofline("sai_build", dict(ms=2.0, launches=1, bytes=1e3, flops=1e9 + 8.05e10,
+                                              flops32=8.05e10), PEAKS)
+    t_alu = 1e9 / fp64 + 8.05e10 / fp32
+    assert r["bound"] == "alu" and abs(r["frac"] - t_alu / 2e-3) < 1e-12
+    assert abs(r["frac_fp64"] - 1e9 / 2e-3 / fp64) < 1e-12 and abs(r["frac_fp32"] - 8.05e10 / 2e-3 / fp32) < 1e-12
     # control kernels carry no algorithmic work
     r = bench.site_roofline("gmres_step", dict(ms=1.0, launches=4, bytes=0.0, flops=0.0), PEAKS)
     assert r["bound"] == "latency" and r["frac"] is None

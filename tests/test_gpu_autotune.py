@@ -1,9 +1,12 @@
 """The build-schedule autotuner (sai_build_autotune / sai_build_set_config).
 
-The schedule (tier-0 warps per block, blocks per SM of the global-memory
-tiers, heavy columns first in the work queue) must not change M: every
-configuration gives the same M bit for bit, and the tuner picks the fastest
-candidate it timed.
+The schedule (warps per block of the shared-memory tiers, blocks per SM of
+the global-memory tiers, heavy columns first in the work queue) must not
+change M: every such configuration gives the same M bit for bit. The first
+tier's shape (first_tier) sets the group size of the columns it finishes,
+so only configurations with the same first_tier are compared bit for bit
+here (tests/test_gpu_small_tier.py compares each with the oracle). The
+tuner picks the fastest candidate it timed.
 """
 import numpy as np
 import pytest
@@ -51,20 +54,26 @@ def test_every_schedule_gives_the_same_m(case):
 
 
 def test_autotune_picks_the_fastest_candidate_and_keeps_m():
+    """Nine candidates: the three first-tier shapes x two block sizes, then
+    heavy_first and the global tiers' blocks per SM on the best; the chosen
+    one is the fastest timed, and a build under it gives the bits of the same
+    configuration set by hand (and the oracle's pattern)."""
     need_gpu()
     sai = lib()
     A = W.convdiff3d_irregular(m=32, s=4, density=0.1).A
     sp_ = sai.split(to_dev(A))
     kw = dict(delta=0.3, mn=5, max_aug=10)
     try:
-        sai.build_set_config()
-        ref, _ = _m(sai, sp_, "spai", kw)
         chosen, cands = sai.build_autotune(sp_, "spai", **kw)
-        assert len(cands) == 12 and all(c["ms"] > 0 for c in cands)
+        assert len(cands) == 9 and all(c["ms"] > 0 for c in cands)
         assert chosen["ms"] == min(c["ms"] for c in cands)
-        assert {(c["warps_t0"], c["blocks_per_sm_t12"], c["heavy_first"]) for c in cands} == {
-            (w, b, h) for w in (4, 8) for b in (1, 2, 4) for h in (0, 1)}
+        assert {(c["first_tier"], c["warps_t0"]) for c in cands[:6]} == {(f, w) for f in (0, 1, 2) for w in (4, 8)}
+        assert all((c["blocks_per_sm_t12"], c["heavy_first"]) == (2, 0) for c in cands[:6])
+        assert cands[6]["heavy_first"] == 1 and {c["blocks_per_sm_t12"] for c in cands[7:]} == {1, 4}
         got, _ = _m(sai, sp_, "spai", kw)
+        sai.build_set_config(chosen["warps_t0"], chosen["blocks_per_sm_t12"], chosen["heavy_first"],
+                             chosen["first_tier"])
+        ref, _ = _m(sai, sp_, "spai", kw)
         _same(got, ref)
     finally:
         sai.build_set_config()
@@ -73,7 +82,7 @@ def test_autotune_picks_the_fastest_candidate_and_keeps_m():
 def test_set_config_rejects_values_outside_the_candidates():
     need_gpu()
     sai = lib()
-    for bad in ((16, 2, 0), (8, 3, 0), (8, 2, 2)):
+    for bad in ((16, 2, 0), (8, 3, 0), (8, 2, 2), (8, 2, 0, 3)):
         with pytest.raises(sai.SaiError) as e:
             sai.build_set_config(*bad)
         assert e.value.status == sai.SAI_INVALID_ARG

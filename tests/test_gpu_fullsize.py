@@ -75,3 +75,36 @@ def test_fullsize_solve_matches_oracle_run(problem, case):
     assert O.rel_resid(P.A, P.b, x.cpu().numpy()) < 1e-10
     assert rep["c"] == pytest.approx(g["report"]["c"], rel=1e-6)
     np.testing.assert_allclose(x.cpu().numpy(), 1.0, rtol=0, atol=1e-7)
+
+
+@pytest.mark.parametrize("first_tier", [0, 1, 2])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fullsize_refined_build_samples_match_oracle(problem, case, first_tier):
+    """The headline form of the build (FP32 QR + one FP64 refinement step per
+    loop) at 64^3 under each first-tier shape the autotuner may choose: the
+    oracle's pattern and values within 1e-4 on the three column ranges, and
+    nnz(M), n_c and l_m of the complete oracle run."""
+    P, At, gold = problem
+    sai = lib()
+    h = sai.split(to_dev(P.A))
+    kw = CASES[case]
+    try:
+        sai.build_set_config(8, 2, 0, first_tier)
+        if case == "spai":
+            Pc = sai.build_spai(h, delta=kw["delta"], mn=kw["mn"], max_aug=kw["max_aug"], precision=1)
+        else:
+            Pc = sai.build_psai(h, delta=kw["delta"], tol=kw["tol"], tol_mode=kw["tol_mode"], lmax=kw["lmax"],
+                                precision=1)
+    finally:
+        sai.build_set_config()
+    Md = to_scipy(Pc.arrays()[0])
+    rep = gold["cases"][case]["report"]
+    assert Pc.nnz == rep["nnz_M"] and Pc.n_c == rep["n_c"] and Pc.l_m == rep["l_m"]
+    if first_tier:
+        assert Pc.n_tier[4] > 0.99 * P.n, Pc.n_tier
+    for c0, c1 in RANGES:
+        if case == "spai":
+            Mo = O.spai(At, kw["delta"], kw["mn"], kw["max_aug"], cols=(c0, c1))[0]
+        else:
+            Mo = O.psai(At, kw["delta"], kw["tol"], kw["tol_mode"], kw["lmax"], cols=(c0, c1))[0]
+        assert_same_pattern_and_values(Md, Mo, rtol=1e-4, cols=range(c0, c1))
