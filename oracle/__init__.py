@@ -39,13 +39,15 @@ class _PsaiParams(C.Structure):
 class _SolveParams(C.Structure):
     _fields_ = [("thresh_mult", C.c_double), ("abs_tau", C.c_double), ("sai", C.c_int32),
                 ("spai", _SpaiParams), ("psai", _PsaiParams), ("krylov", C.c_int32),
-                ("restart", C.c_int32), ("maxit", C.c_int32), ("eps", C.c_double)]
+                ("restart", C.c_int32), ("maxit", C.c_int32), ("eps", C.c_double), ("c_adapt", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class _SolveReport(C.Structure):
     _fields_ = [("s", C.c_int32), ("p", C.c_int32), ("tau", C.c_double), ("nnz_At", C.c_int64),
                 ("nnz_M", C.c_int64), ("n_c", C.c_int32), ("l_m", C.c_int32), ("iter_max", C.c_int32),
-                ("status", C.c_int32), ("c", C.c_double), ("rr", C.c_double), ("bound", C.c_double)]
+                ("status", C.c_int32), ("c", C.c_double), ("rr", C.c_double), ("bound", C.c_double),
+                ("c_first", C.c_double), ("c_rounds", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -276,14 +278,17 @@ def rel_resid(A, b, x):
 
 
 def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0,
-          abs_tau=-1.0, delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10):
-    """Procedure * end to end. Returns (x, iters[s+1], report dict)."""
+          abs_tau=-1.0, delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, c_adapt=0):
+    """Procedure * end to end. Returns (x, iters[s+1], report dict). c_adapt=1:
+    when the recovery's c exceeds 1, the u_j systems are continued to
+    eq. (stopU2) with that c and x is recovered again."""
     a = _In(A)
     n = a.shape[1]
     b = np.ascontiguousarray(b, dtype=np.float64)
     prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
-                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3, "bgmres": 4}[krylov], restart, maxit, eps)
+                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3, "bgmres": 4}[krylov], restart, maxit, eps,
+                       int(c_adapt), 0)
     x = np.zeros(n)
     iters = np.zeros(n + 1, np.int32)
     rep = _SolveReport()
@@ -364,7 +369,8 @@ def backward(A, x, g, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restar
     g = np.ascontiguousarray(g, dtype=np.float64)
     prm = _SolveParams(thresh_mult, abs_tau, 0 if sai == "spai" else 1,
                        _SpaiParams(delta, mn, max_aug, key_bits), _PsaiParams(delta, tol, tol_mode, lmax),
-                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3, "bgmres": 4}[krylov], restart, maxit, eps)
+                       {"bicgstab": 0, "gmres": 1, "cgs": 2, "bicg": 3, "bgmres": 4}[krylov], restart, maxit, eps,
+                       0, 0)
     lam = np.zeros(n)
     gv = np.zeros(a.nnz)
     iters = np.zeros(n + 1, np.int32)

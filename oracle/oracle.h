@@ -161,6 +161,9 @@ typedef struct {
     int32_t restart;
     int32_t maxit;
     double eps;
+    int32_t c_adapt;      /* 1: when SMW's c = ||z|| exceeds 1, continue the u_j systems to
+                             eq. (stopU2) with that c (times 1.05) and recover x again */
+    int32_t reserved;
 } orc_solve_params;
 
 typedef struct {
@@ -174,6 +177,9 @@ typedef struct {
     double c;             /* ||(I+V^T W)^{-1} V^T y|| */
     double rr;            /* ||b - A xhat|| / ||b|| */
     double bound;         /* ||r_y|| + c ||R_W||_F  (Theorem 2, eq. (rry)) */
+    double c_first;       /* c of the first recovery (c when no second round ran) */
+    int32_t c_rounds;     /* 1 when the u_j systems were continued with the measured c */
+    int32_t reserved;
 } orc_solve_report;
 
 /* Full Procedure *: split, build M, s+1 Krylov solves, SMW, rr.

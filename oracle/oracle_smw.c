@@ -1,7 +1,8 @@
 /* oracle_smw.c -- Sherman-Morrison-Woodbury recovery (Theorem 1, eqs.
  * (update1), (composi)), the true relative residual (eq. (rrnorm)) and the
  * whole of Procedure * with the stopping rules of Theorem 2, eqs. (stopb)
- * and (stopU2) with c = 1 (section 4).  Test infrastructure only. */
+ * and (stopU2) with c = 1 (section 4), optionally continued with the c the
+ * recovery measures.  Test infrastructure only. */
 #include "oracle_internal.h"
 #include <math.h>
 #include <stdlib.h>
@@ -144,6 +145,65 @@ int orc_solve(const orc_csc* A, const double* b, const orc_solve_params* prm,
             double* z = (double*)orc_xmalloc((size_t)(s > 0 ? s : 1) * sizeof(double));
             double c = 0.0;
             st = orc_smw(n, s, Y, Y + n, J, x_out, z, &c);
+            rep->c_first = c;
+            if (st == ORC_OK && prm->c_adapt && s > 0 && c > 1.0) {
+                /* Theorem 2 bounds ||b - A xhat|| by ||r_y|| + c ||R_W||_F; with
+                 * the c = 1 thresholds that exceeds eps ||b|| once c > 1. Reading
+                 * of eq. (stopU2): its c is the c the recovery measures, so the
+                 * u_j systems are continued from their iterates (a correction
+                 * solve A~ d = u_j - A~ w_j, w_j += d) to eps ||b|| / (2 sqrt(s)
+                 * 1.05 c) and x is recovered again. */
+                const double thr2 = prm->eps * bnorm / (2.0 * sqrt((double)s) * 1.05 * c);
+                double* D = (double*)orc_xcalloc((size_t)(s + 1) * (size_t)n, sizeof(double));
+                double* R = (double*)orc_xcalloc((size_t)(s + 1) * (size_t)n, sizeof(double));
+                double* th2 = (double*)orc_xmalloc((size_t)(s + 1) * sizeof(double));
+                int32_t* it2 = (int32_t*)orc_xcalloc((size_t)(s + 1), sizeof(int32_t));
+                th2[0] = 0.5 * prm->eps * bnorm;  /* system 0 has no correction: rhs 0 */
+                for (int32_t q = 1; q <= s; ++q) {
+                    double* rq = R + (size_t)q * n;
+                    for (int64_t t = U.col_ptr[q - 1]; t < U.col_ptr[q]; ++t) rq[U.row_idx[t]] = U.val[t];
+                    orc_csc_matvec(&At, Y + (size_t)q * n, tmp);
+                    for (int32_t i = 0; i < n; ++i) rq[i] -= tmp[i];
+                    th2[q] = thr2;
+                }
+                int ks2 = ORC_OK;
+                if (prm->krylov == 4) {
+                    ks2 = orc_block_gmres(&At, &M, s + 1, R, th2, prm->restart, prm->maxit, D, it2);
+                } else {
+                    for (int32_t q = 1; q <= s; ++q) {
+                        int kq;
+                        double* rq = R + (size_t)q * n;
+                        double* dq = D + (size_t)q * n;
+                        if (prm->krylov == 0) kq = orc_bicgstab(&At, &M, rq, thr2, prm->maxit, dq, &it2[q]);
+                        else if (prm->krylov == 2) kq = orc_cgs(&At, &M, rq, thr2, prm->maxit, dq, &it2[q]);
+                        else if (prm->krylov == 3) kq = orc_bicg(&At, &M, rq, thr2, prm->maxit, dq, &it2[q]);
+                        else kq = orc_gmres(&At, &M, rq, thr2, prm->restart, prm->maxit, dq, &it2[q]);
+                        if (kq != ORC_OK && ks2 == ORC_OK) ks2 = kq;
+                    }
+                }
+                if (ks2 != ORC_OK && rep->status == ORC_OK) rep->status = ks2;
+                rW2 = 0.0;
+                for (int32_t q = 1; q <= s; ++q) {
+                    double* wq = Y + (size_t)q * n;
+                    double* dq = D + (size_t)q * n;
+                    for (int32_t i = 0; i < n; ++i) wq[i] += dq[i];
+                    const int32_t itq = (iters_out ? iters_out[q] : 0) + it2[q];
+                    if (iters_out) iters_out[q] = itq;
+                    if (itq > rep->iter_max) rep->iter_max = itq;
+                    /* true residual of the continued w_q */
+                    double* rq = R + (size_t)q * n;
+                    for (int32_t i = 0; i < n; ++i) rq[i] = 0.0;
+                    for (int64_t t = U.col_ptr[q - 1]; t < U.col_ptr[q]; ++t) rq[U.row_idx[t]] = U.val[t];
+                    orc_csc_matvec(&At, wq, tmp);
+                    for (int32_t i = 0; i < n; ++i) rW2 += (rq[i] - tmp[i]) * (rq[i] - tmp[i]);
+                }
+                st = orc_smw(n, s, Y, Y + n, J, x_out, z, &c);
+                rep->c_rounds = 1;
+                free(D);
+                free(R);
+                free(th2);
+                free(it2);
+            }
             if (st == ORC_OK) {
                 rep->c = c;
                 rep->rr = orc_rel_resid(A, b, x_out);

@@ -1013,3 +1013,46 @@ def test_oracle_backward_with_block_gmres():
     R[J, np.arange(1, s + 1)] = 1.0
     _, it, st = O.block_gmres(sp.csc_matrix(At.T), sp.csc_matrix(M.T), R, thr, restart=30)
     assert st == O.OK and list(it) == list(iters)
+
+
+# ------------------------------------- eq. (stopU2) with the recovery's c
+
+def _batch_matrix(q):
+    """Matrix q of the 256-matrix batched workload (the random geometric-graph
+    systems), generated on its own."""
+    rng = np.random.default_rng(W.SEED_BASE + 3)
+    ns = rng.integers(1000, 50001, size=256)
+    return W.rgg_irregular(int(ns[q]), seed=(W.SEED_BASE + 3) * 1000 + q)
+
+
+def test_c_continuation_meets_eps_by_theorem2():
+    """Theorem 2 bounds ||b - A x|| by ||r_y|| + c ||R_W||_F. With eq. (stopU2)
+    at c = 1 that is eps ||b|| (1 + c) / 2, and matrix 10 of the batched
+    workload (c = sqrt(10): b = A 1 makes z = x(J) = 1) ends above eps. With
+    the u_j systems continued to the threshold with the measured c, the
+    residual (recomputed here with scipy) is below eps, below the report's
+    Theorem 2 bound, which is itself below eps ||b||; the continued systems
+    took more iterations and the b system none."""
+    P = _batch_matrix(10)
+    b = P.b
+    bn = np.linalg.norm(b)
+    x0, it0, r0 = O.solve(P.A, b, eps=1e-8)
+    assert r0["c"] > 1.0 and r0["c_rounds"] == 0
+    assert np.linalg.norm(b - P.A @ x0) / bn > 1e-8           # the c = 1 bound is not enough here
+    x1, it1, r1 = O.solve(P.A, b, eps=1e-8, c_adapt=1)
+    assert r1["c_rounds"] == 1 and r1["c_first"] == pytest.approx(r0["c"], rel=1e-12)
+    rr = np.linalg.norm(b - P.A @ x1) / bn
+    assert rr < 1e-8 and rr == pytest.approx(r1["rr"], rel=1e-6)
+    assert rr * bn <= r1["bound"] * (1 + 1e-9) and r1["bound"] <= 1e-8 * bn
+    assert it1[0] == it0[0] and all(a > c for a, c in zip(it1[1:], it0[1:]))
+    np.testing.assert_allclose(x1, 1.0, rtol=0, atol=1e-5)
+
+
+def test_c_continuation_is_idle_when_c_is_small():
+    """No second round when c <= 1: a matrix without irregular columns (s = 0,
+    c = 0) gives the same bits with and without the option."""
+    P = _batch_matrix(64)
+    x0, it0, r0 = O.solve(P.A, P.b, eps=1e-8)
+    x1, it1, r1 = O.solve(P.A, P.b, eps=1e-8, c_adapt=1)
+    assert r0["s"] == 0 and r1["c_rounds"] == 0
+    assert np.array_equal(x0, x1) and np.array_equal(it0, it1)
