@@ -305,18 +305,83 @@ def oracle_sample(P, krylov_iters=50):
     with open(GOLDEN) as f:
         gold = json.load(f)
     t_kry = 0.0
+    t_step = {}
     for M, case in ((Ms, "spai"), (Mp, "psai")):
         t0 = time.perf_counter()
         _, it, _ = O.gmres(At, M, P.b, 0.0, restart=50, maxit=krylov_iters)
         t_it = (time.perf_counter() - t0) / max(it, 1)
+        t_step[case] = t_it
         t_kry += t_it * sum(gold["cases"][case]["iters"])
     est = 2 * t_split + t_spai + t_psai + t_kry
     tot = sum(sum(c["iters"]) for c in gold["cases"].values())
-    sample = ("split, SPAI and PSAI builds of all %d columns timed in full; GMRES(50) timed for one %d-step cycle "
-              "per M and scaled to the %d inner steps of the complete oracle solves (oracle-written golden file)"
-              % (n, krylov_iters, tot))
+    sample = ("split, SPAI and PSAI builds of all %d columns timed in full; GMRES(50) extrapolated: timed for one "
+              "%d-step cycle per M and scaled to the %d inner steps of the complete oracle solves (oracle-written "
+              "golden file)" % (n, krylov_iters, tot))
     return {"est_step_s": est, "value": 2 * n / est, "t_split": t_split, "t_spai": t_spai, "t_psai": t_psai,
-            "t_krylov_est": t_kry, "cols_per_s_spai": n / t_spai, "cols_per_s_psai": n / t_psai, "sample": sample}
+            "t_krylov_est": t_kry, "cols_per_s_spai": n / t_spai, "cols_per_s_psai": n / t_psai, "sample": sample,
+            "t_step_spai": t_step["spai"], "t_step_psai": t_step["psai"]}
+
+
+_POOL_AT = None
+
+
+def _pool_init(indptr, indices, data, n):
+    """Worker start (spawned process): keep A~ for the column-range builds."""
+    global _POOL_AT
+    import scipy.sparse as sps
+    _POOL_AT = sps.csc_matrix((data, indices, indptr), shape=(n, n))
+
+
+def _pool_build(task):
+    """One column range of the oracle's SPAI or PSAI build; returns its seconds."""
+    import oracle as O
+    kind, c0, c1 = task
+    t0 = time.perf_counter()
+    if kind == "spai":
+        O.spai(_POOL_AT, SPAI_KW["delta"], SPAI_KW["mn"], SPAI_KW["max_aug"], cols=(c0, c1))
+    else:
+        O.psai(_POOL_AT, PSAI_KW["delta"], PSAI_KW["tol"], PSAI_KW["tol_mode"], PSAI_KW["lmax"], cols=(c0, c1))
+    return time.perf_counter() - t0
+
+
+def oracle_sample_all_cores(P, single):
+    """The same oracle on all host cores: its SPAI and PSAI builds split into
+    column ranges over a process pool (one process per core, started by
+    spawn; the oracle's columns are independent, so each range is the
+    unchanged oracle run on cols=(c0, c1)), timed in full as wall time; the
+    split as timed single-threaded; the s+1 GMRES solves one per core, each
+    system's time taken from the single-threaded sample's seconds per inner
+    step times the system's inner steps in the complete oracle run, the
+    longest system bounding the wall time (an extrapolation, like the
+    single-threaded figure's)."""
+    import multiprocessing as mp
+    import oracle as O
+    cores = os.cpu_count() or 1
+    J, p, _ = O.detect(P.A)
+    At, _ = O.split(P.A, J, p)
+    n = P.n
+    chunk = max(1, -(-n // (4 * cores)))
+    ctx = mp.get_context("spawn")
+    t_build = {}
+    with ctx.Pool(cores, initializer=_pool_init,
+                  initargs=(At.indptr.astype(np.int64), At.indices.astype(np.int32), At.data, n)) as pool:
+        pool.map(_pool_build, [("spai", 0, min(n, 64))] * cores)  # workers up and the oracle loaded
+        for kind in ("spai", "psai"):
+            t0 = time.perf_counter()
+            pool.map(_pool_build, [(kind, c0, min(n, c0 + chunk)) for c0 in range(0, n, chunk)])
+            t_build[kind] = time.perf_counter() - t0
+    with open(GOLDEN) as f:
+        gold = json.load(f)
+    t_kry = 0.0
+    for case in ("spai", "psai"):
+        t_kry += single["t_step_" + case] * max(gold["cases"][case]["iters"])
+    est = 2 * single["t_split"] + t_build["spai"] + t_build["psai"] + t_kry
+    return {"value": 2 * n / est, "unit": UNIT, "cores": cores, "kind": "oracle", "est_step_s": est,
+            "t_spai": t_build["spai"], "t_psai": t_build["psai"], "t_krylov_est": t_kry,
+            "sample": "SPAI and PSAI builds of all %d columns timed in full over %d spawned processes (column "
+                      "ranges of %d, the unchanged oracle per range); splits single-threaded; GMRES extrapolated: "
+                      "one system per core, the longest system's inner steps in the complete oracle run times the "
+                      "single-threaded seconds per step" % (n, cores, chunk)}
 
 
 def run_reference(args):
@@ -427,6 +492,7 @@ def run_ours(args):
     # (graph replay is off while a profile is open; kernel durations are the same)
     _, _, prof = timed(OPT_KW, 1, True)
     ms_plain, reps_plain, _ = timed(PLAIN_KW, max(1, min(args.steps, 3)), False)
+    _, _, prof_plain = timed(PLAIN_KW, 1, True)
     value = ws * 2 * n / (ms_step / 1e3)
     # the block Krylov alternative on the same SPAI systems: block GMRES(50)
     # in the refined and the plain FP64 form, one solve each after one warm-up
@@ -450,19 +516,25 @@ def run_ours(args):
     hx = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
     h2d = sum(t.numel() * t.element_size() for t in hA)
     d2h = sum(t.numel() * t.element_size() for t in hx)
-    e2e_ms = []
-    for _ in range(max(1, args.steps)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        cp, ri, va, bb = (t.to("cuda", non_blocking=True) for t in hA)
-        M = sai.CscMatrix(n, cp, ri, va)
-        for kw, xh in zip((SPAI_KW, PSAI_KW), hx):
-            x, _, _ = sai.solve(M, bb, **kw, **KRYLOV_KW, **OPT_KW)
-            xh.copy_(x, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = ws * 2 * n / (float(np.mean(e2e_ms)) / 1e3)
+
+    def e2e(form, nsteps):
+        e2e_ms = []
+        for _ in range(max(1, nsteps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cp, ri, va, bb = (t.to("cuda", non_blocking=True) for t in hA)
+            M = sai.CscMatrix(n, cp, ri, va)
+            for kw, xh in zip((SPAI_KW, PSAI_KW), hx):
+                x, _, _ = sai.solve(M, bb, **kw, **KRYLOV_KW, **form)
+                xh.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        return float(np.mean(e2e_ms))
+
+    e2e_mean = e2e(OPT_KW, args.steps)
+    e2e_val = ws * 2 * n / (e2e_mean / 1e3)
+    e2e_plain = e2e(PLAIN_KW, min(args.steps, 2))
 
     if rank != 0:
         if dist:
@@ -487,14 +559,22 @@ def run_ours(args):
         "form": "SAI build with FP32 Householder QR and one FP64 refinement step per loop (FP64 residuals, stop "
                 "tests and SPAI keys); s+1 GMRES(50) solves with FP32 inner iterations refined in FP64 (FP64 residual "
                 "b - A~x, correction and every stop test); SMW and rr FP64",
-        "plain_fp64": {"ms_per_step": ms_plain, "value": ws * 2 * n / (ms_plain / 1e3),
+        "plain_fp64": {"ms_per_step": ms_plain, "value": ws * 2 * n / (ms_plain / 1e3), "unit": UNIT,
+                       "dtype": "f64",
+                       "form": "SAI build with FP64 Householder QR; s+1 GMRES(50) solves in FP64; SMW and rr FP64 "
+                               "(the paper's precision)",
                        "iters": {k: r[1] for k, r in zip(("spai", "psai"), reps_plain[-1])},
-                       "rr": {k: r[2]["rr"] for k, r in zip(("spai", "psai"), reps_plain[-1])}},
+                       "rr": {k: r[2]["rr"] for k, r in zip(("spai", "psai"), reps_plain[-1])},
+                       "stage_ms": {k: {q: round(r[2][q], 3) for q in ("ms_split", "ms_build", "ms_krylov", "ms_smw")}
+                                    for k, r in zip(("spai", "psai"), reps_plain[-1])},
+                       "roofline": roofline(prof_plain, load_peaks(), traffic=False),
+                       "e2e": {"value": ws * 2 * n / (e2e_plain / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_plain}},
         "vs_plain_fp64": ms_plain / ms_step,
         "block_gmres_spai": blk,
         "roofline": roofline(prof, peaks),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(np.mean(e2e_ms))},
+                "ms_per_step": e2e_mean},
         "build_schedule": {k: tuned[k] for k in ("warps_t0", "blocks_per_sm_t12", "heavy_first", "first_tier")},
         "gpu_launches": launches,
         "clocks": clk,
@@ -502,7 +582,11 @@ def run_ours(args):
     if ws == 1 and not args.no_cpu_baseline:
         r = oracle_sample(P)
         line["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": r["sample"], "est_step_s": r["est_step_s"]}
+                                "sample": r["sample"], "est_step_s": r["est_step_s"],
+                                "build_columns_per_s": {"spai": r["cols_per_s_spai"], "psai": r["cols_per_s_psai"]}}
+        ra = oracle_sample_all_cores(P, r)
+        line["cpu_baseline_all_cores"] = dict(ra, build_columns_per_s={"spai": n / ra["t_spai"],
+                                                                      "psai": n / ra["t_psai"]})
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -513,7 +597,7 @@ def run_ours(args):
 ZIPF_SPAI = dict(delta=0.4, mn=5, max_aug=10)
 ZIPF_TAU = 200.0
 ZIPF_EPS = 1e-10
-BATCH_KW = dict(delta=0.4, mn=5, max_aug=10, eps=1e-8, sai_precision=1)
+BATCH_KW = dict(delta=0.4, mn=5, max_aug=10, eps=1e-8, sai_precision=1, c_adapt=1)
 
 
 def _gpu_setup():
@@ -705,6 +789,10 @@ def run_batch(args):
     def step():
         return sai.solve_batched(As, bs, **BATCH_KW)
 
+    # the build schedule (first tier's shape and group size, block sizes,
+    # queue order), autotuned once on the batch's stacked A~ outside the timing
+    tuned, _ = sai.build_autotune_batched(As, delta=BATCH_KW["delta"], mn=BATCH_KW["mn"], max_aug=BATCH_KW["max_aug"],
+                                          sai_precision=BATCH_KW["sai_precision"])
     for _ in range(args.warmup):
         step()
     clocks = ClockSampler(local)
@@ -745,7 +833,8 @@ def run_batch(args):
         "config": {"workload": "batch256: 256 random geometric-graph Laplacians (average degree 8), n ~ U[1k, 50k], "
                                "nonsymmetric perturbation U(-0.1,0.1)*deg, column dominance 1.05, s ~ U{1..20} "
                                "dense N(0,1) columns at 1-10%; SPAI(0.4,5,10) with FP32 QR + FP64 refinement, "
-                               "batched FP64 BiCGStab to 1e-8",
+                               "batched FP64 BiCGStab to 1e-8 (the whole loop one graph launch), u_j systems "
+                               "continued with the measured c where c > 1",
                    "matrices": len(Ps), "columns": ncols, "nnz": int(sum(P.A.nnz for P in Ps)),
                    "systems": rep["systems"], "l2": "flushed by a 256 MB write between timed steps"},
         "stage_ms": {k: rep[k] for k in rep if k.startswith("ms_")},
@@ -753,6 +842,8 @@ def run_batch(args):
         # Theorem 2 with c = ||z||: rr <= eps (1 + c) / 2 for every matrix
         "rr_within_theorem2_bound": all(r["rr"] <= BATCH_KW["eps"] * (1.0 + r["c"]) / 2.0 for r in per),
         "matrices_rr_above_eps": sum(r["rr"] >= BATCH_KW["eps"] for r in per),
+        "matrices_continued": sum(r["c_rounds"] for r in per),
+        "build_schedule": {k: tuned[k] for k in ("warps_t0", "blocks_per_sm_t12", "heavy_first", "first_tier")},
         "status_ok": all(r["status"] == sai.SAI_OK for r in per),
         "roofline": roofline(prof, peaks),
         "e2e": {"value": ws * ncols / (float(np.mean(e2e_ms)) / 1e3), "unit": "columns/s",
@@ -760,10 +851,31 @@ def run_batch(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_oracle_sample(Ps, ncols)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def batch_oracle_sample(Ps, ncols, sample=(0, 10, 79, 128, 200)):
+    """The oracle's Procedure * (same parameters, with the continuation) on a
+    sample of the batch's matrices, timed in full and scaled to the batch by
+    columns (the work per column is alike across these graphs)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    cols = 0
+    for q in sample:
+        P = Ps[q]
+        O.solve(P.A, P.b, krylov="bicgstab", eps=BATCH_KW["eps"], delta=BATCH_KW["delta"], mn=BATCH_KW["mn"],
+                max_aug=BATCH_KW["max_aug"], c_adapt=1)
+        cols += P.n
+    t = time.perf_counter() - t0
+    return {"value": cols / t, "unit": "columns/s", "cores": 1, "kind": "oracle", "est_step_s": t * ncols / cols,
+            "sample": "Procedure * (split, SPAI(0.4,5,10) in FP64, BiCGStab to 1e-8 with the continuation, SMW) of "
+                      "matrices %s (%d columns) timed in full and scaled to the batch's %d columns"
+                      % (list(sample), cols, ncols)}
 
 
 GOLDEN_ZD = os.path.join(ROOT, "tests", "golden", "oracle_zerodiag_m64_s10.json")

@@ -364,6 +364,12 @@ typedef struct {
     sai_psai_params psai;
     sai_krylov_params krylov;
     double eps;                   /* paper: 1e-8 */
+    int32_t c_adapt;              /* 0: c = 1 in eq. (stopU2) (the paper's setting). 1: when the
+                                     recovery's c = ||z|| exceeds 1, the u_j systems are continued
+                                     from their iterates to eps ||b|| / (2 sqrt(s) 1.05 c) and x is
+                                     recovered again, so that Theorem 2 bounds the residual by
+                                     eps ||b|| (one extra round at most) */
+    int32_t reserved;             /* 0 */
 } sai_solve_params;
 
 typedef struct {
@@ -376,7 +382,8 @@ typedef struct {
     double ms_split, ms_build, ms_krylov, ms_smw;  /* device time per step
                                      (ms_split includes the zero-diagonal repair) */
     int32_t moved;                /* zero_diag: columns j with p[j] != j (0: A kept) */
-    int32_t reserved;
+    int32_t c_rounds;             /* c_adapt: 1 when the u_j systems were continued (the
+                                     iteration counts include both rounds; c is the last one) */
 } sai_solve_report;
 
 /* iters (host, may be NULL): s+1 iteration counts in the order [b, u_1..u_s];
@@ -428,8 +435,10 @@ sai_status sai_backward(const sai_csc_view* A, sai_split h, sai_precond P, const
  * SAI launch (the block-diagonal A~ of the batch: every column's least-squares
  * problem only sees its own matrix); the sum(s_i + 1) Krylov systems of the
  * batch run together in one batched FP64 BiCGStab (each system on its own
- * matrix, with the Theorem 2 thresholds of its matrix); then SMW and rr per
- * matrix. Supported: SPAI, and PSAI with a fixed tolerance (tol_mode 1; the
+ * matrix, with the Theorem 2 thresholds of its matrix), the whole iteration
+ * loop as one CUDA graph launch (a conditional while node); then SMW and rr
+ * per matrix. prm->c_adapt = 1 continues, for each matrix whose c exceeds 1,
+ * its u_j systems with that c (as sai_solve does) in a second batched pass. Supported: SPAI, and PSAI with a fixed tolerance (tol_mode 1; the
  * tol_k of eq. (tolk) is per matrix and is not taken in a batch), both
  * precisions of the build; BiCGStab in FP64 (GMRES and the refined Krylov form
  * return SAI_NOT_IMPLEMENTED).
@@ -441,8 +450,10 @@ typedef struct {
     int32_t status;    /* worst Krylov status of the matrix's s+1 systems */
     int32_t iter_max;  /* max iterations over its s+1 systems */
     int32_t s, p;      /* irregular columns found, p = floor(nnz/n) */
-    double c;          /* ||(I + V^T What)^{-1} V^T yhat|| */
+    double c;          /* ||(I + V^T What)^{-1} V^T yhat|| (of the last recovery) */
     double rr;         /* ||b - A x|| / ||b|| */
+    int32_t c_rounds;  /* prm->c_adapt: 1 when this matrix's u_j systems were continued */
+    int32_t reserved;
 } sai_batch_item;
 
 typedef struct {
@@ -456,6 +467,22 @@ typedef struct {
 sai_status sai_solve_batched(int32_t nmat, const sai_csc_view* A, const double* const* b,
                              const sai_solve_params* prm, double* const* x, sai_batch_item* items,
                              sai_batch_report* rep, sai_stream_t stream);
+
+/* The SAI build of a batch alone (section 2 on each matrix's A~_i): each
+ * matrix split on its own (prm->split), the regular parts stacked as the
+ * block-diagonal A~ of the batch (matrix m's rows and columns start at the sum
+ * of the earlier orders), one build over all its columns (prm->sai with
+ * prm->spai or prm->psai; the same limits as sai_solve_batched). *out: the
+ * preconditioner of the stacked A~, owned by the caller (sai_precond_destroy);
+ * its diagonal blocks are the M_i that sai_solve_batched uses. */
+sai_status sai_build_batched(int32_t nmat, const sai_csc_view* A, const sai_solve_params* prm,
+                             sai_stream_t stream, sai_precond* out);
+/* The build-schedule autotuner (as sai_build_autotune) on the stacked A~ of a
+ * batch, split and stacked as sai_build_batched does; the fastest
+ * configuration becomes the process-wide one, so a later sai_solve_batched
+ * builds with it. Synchronises the stream. */
+sai_status sai_build_autotune_batched(int32_t nmat, const sai_csc_view* A, const sai_solve_params* prm,
+                                      sai_stream_t stream, sai_build_tuning* out);
 
 /* ----------------------------------------------------------------------
  * Diagnostics (not part of the paper's method): launch counting and the

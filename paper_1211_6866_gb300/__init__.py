@@ -77,7 +77,7 @@ class _KrylovParams(C.Structure):
 
 class _BatchItem(C.Structure):
     _fields_ = [("status", C.c_int32), ("iter_max", C.c_int32), ("s", C.c_int32), ("p", C.c_int32),
-                ("c", C.c_double), ("rr", C.c_double)]
+                ("c", C.c_double), ("rr", C.c_double), ("c_rounds", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _BatchReport(C.Structure):
@@ -102,13 +102,13 @@ class _StageParams(C.Structure):
 
 class _SolveParams(C.Structure):
     _fields_ = [("split", _SplitParams), ("sai", C.c_int32), ("spai", _SpaiParams), ("psai", _PsaiParams),
-                ("krylov", _KrylovParams), ("eps", C.c_double)]
+                ("krylov", _KrylovParams), ("eps", C.c_double), ("c_adapt", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _SolveReport(C.Structure):
     _fields_ = [("split", _SplitInfo), ("precond", _PrecondInfo), ("status", C.c_int32), ("iter_max", C.c_int32),
                 ("c", C.c_double), ("rr", C.c_double), ("ms_split", C.c_double), ("ms_build", C.c_double),
-                ("ms_krylov", C.c_double), ("ms_smw", C.c_double), ("moved", C.c_int32), ("reserved", C.c_int32)]
+                ("ms_krylov", C.c_double), ("ms_smw", C.c_double), ("moved", C.c_int32), ("c_rounds", C.c_int32)]
 
 
 class _ProfSite(C.Structure):
@@ -164,6 +164,9 @@ def load():
                                     C.POINTER(_BatchItem), C.POINTER(_BatchReport), vp]
     L.sai_build_autotune.argtypes = [vp, i32, C.POINTER(_SpaiParams), C.POINTER(_PsaiParams), vp,
                                      C.POINTER(_BuildTuning)]
+    L.sai_build_batched.argtypes = [i32, C.POINTER(_CscView), C.POINTER(_SolveParams), vp, C.POINTER(vp)]
+    L.sai_build_autotune_batched.argtypes = [i32, C.POINTER(_CscView), C.POINTER(_SolveParams), vp,
+                                             C.POINTER(_BuildTuning)]
     L.sai_build_set_config.argtypes = [C.POINTER(_BuildConfig)]
     L.sai_dmperm.argtypes = [C.POINTER(_CscView), dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp]
     L.sai_permute_rows.argtypes = [C.POINTER(_CscView), dp, dp, dp, dp, vp]
@@ -174,7 +177,8 @@ def load():
     for f in ("sai_profile_begin", "sai_profile_end", "sai_split_create", "sai_split_get_info", "sai_split_copy_out", "sai_build_spai", "sai_build_psai",
               "sai_precond_get_info", "sai_precond_copy_out", "sai_krylov_solve", "sai_smw_recover",
               "sai_rel_resid", "sai_solve", "sai_solve_with", "sai_backward", "sai_solve_batched",
-              "sai_build_autotune", "sai_build_set_config", "sai_dmperm", "sai_permute_rows"):
+              "sai_build_autotune", "sai_build_set_config", "sai_dmperm", "sai_permute_rows", "sai_build_batched",
+              "sai_build_autotune_batched"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -436,11 +440,13 @@ def permute_rows(A, p):
 
 def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, thresh_mult=10.0, abs_tau=-1.0,
           delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0, tol_mode=0, lmax=10, x=None, krylov_precision=0,
-          inner_tol=0.0, sai_precision=0, keep="nearest", lfill=0, growth="A", zero_diag=False):
+          inner_tol=0.0, sai_precision=0, keep="nearest", lfill=0, growth="A", zero_diag=False, c_adapt=0):
     """Procedure * on the device. krylov_precision=1 selects the FP32-inner /
     FP64-refined GMRES; sai_precision=1 the FP32 QR + FP64 refinement build;
     zero_diag=True first applies the zero-diagonal repair of section 5
-    (report["moved"] columns moved). Returns (x, iters list, report dict)."""
+    (report["moved"] columns moved); c_adapt=1 continues the u_j systems with
+    the measured c when the recovery's c exceeds 1 (report["c_rounds"]).
+    Returns (x, iters list, report dict)."""
     L = load()
     if x is None:
         x = torch.empty(A.n, dtype=torch.float64, device=b.device)
@@ -449,7 +455,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
                        _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill, _GROWTH[growth], 0),
                        _KrylovParams(_METHOD[krylov], restart, maxit, krylov_precision,
-                                     inner_tol, 0), eps)
+                                     inner_tol, 0), eps, int(c_adapt), 0)
     cap = A.n + 1
     iters = (C.c_int32 * cap)()
     rep = _SolveReport()
@@ -461,7 +467,7 @@ def solve(A, b, sai="spai", krylov="bicgstab", eps=1e-8, maxit=500, restart=50, 
                   nnz_M=rep.precond.nnz_M, n_c=rep.precond.n_c, l_m=rep.precond.l_m,
                   n_tier=list(rep.precond.n_tier), status=st, iter_max=rep.iter_max, c=rep.c, rr=rep.rr,
                   ms_split=rep.ms_split, ms_build=rep.ms_build, ms_krylov=rep.ms_krylov, ms_smw=rep.ms_smw,
-                  build_ms=rep.precond.build_ms, moved=rep.moved)
+                  build_ms=rep.precond.build_ms, moved=rep.moved, c_rounds=rep.c_rounds)
     return x, list(iters[: s + 1]), report
 
 
@@ -547,10 +553,11 @@ class SparseSolve(torch.autograd.Function):
 
 def solve_batched(As, bs, sai="spai", eps=1e-8, maxit=500, thresh_mult=10.0, abs_tau=-1.0, delta=0.4, mn=5,
                   max_aug=10, key_bits=20, tol=0.0, tol_mode=1, lmax=10, sai_precision=0, keep="nearest", lfill=0,
-                  growth="A"):
+                  growth="A", c_adapt=0):
     """Procedure * for a batch of independent matrices (lists of CscMatrix and
     device b vectors): one SAI build over all their columns, one batched
-    BiCGStab over all their s_i + 1 systems, SMW per matrix.
+    BiCGStab over all their s_i + 1 systems (one graph launch), SMW per matrix;
+    c_adapt=1 continues the u_j systems of every matrix whose c exceeds 1.
     Returns (xs list, per-matrix list of dicts, batch report dict)."""
     L = load()
     nmat = len(As)
@@ -558,18 +565,55 @@ def solve_batched(As, bs, sai="spai", eps=1e-8, maxit=500, thresh_mult=10.0, abs
     xs = [torch.empty(A.n, dtype=torch.float64, device=b.device) for A, b in zip(As, bs)]
     bp = (C.c_void_p * nmat)(*[_p(b.contiguous()).value for b in bs])
     xp = (C.c_void_p * nmat)(*[_p(x).value for x in xs])
-    prm = _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
-                       _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
-                       _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill, _GROWTH[growth], 0),
-                       _KrylovParams(BICGSTAB, 50, maxit, 0, 0.0, 0), eps)
+    prm = _batch_params(sai, eps, maxit, thresh_mult, abs_tau, delta, mn, max_aug, key_bits, tol, tol_mode, lmax,
+                        sai_precision, keep, lfill, growth, c_adapt)
     items = (_BatchItem * nmat)()
     rep = _BatchReport()
     st = _check("sai_solve_batched", L.sai_solve_batched(nmat, views, bp, C.byref(prm), xp, items, C.byref(rep),
                                                          _stream()), allow=(SAI_MAXITER, SAI_BREAKDOWN))
-    per = [dict(status=it.status, iter_max=it.iter_max, s=it.s, p=it.p, c=it.c, rr=it.rr) for it in items]
+    per = [dict(status=it.status, iter_max=it.iter_max, s=it.s, p=it.p, c=it.c, rr=it.rr, c_rounds=it.c_rounds)
+           for it in items]
     report = {f: getattr(rep, f) for f, _ in _BatchReport._fields_}
     report["status"] = st
     return xs, per, report
+
+
+def _batch_params(sai, eps, maxit, thresh_mult, abs_tau, delta, mn, max_aug, key_bits, tol, tol_mode, lmax,
+                  sai_precision, keep, lfill, growth, c_adapt):
+    return _SolveParams(_SplitParams(thresh_mult, abs_tau, 0, 0, _KEEP[keep], 0), 0 if sai == "spai" else 1,
+                        _SpaiParams(delta, mn, max_aug, key_bits, sai_precision),
+                        _PsaiParams(delta, tol, tol_mode, lmax, sai_precision, lfill, _GROWTH[growth], 0),
+                        _KrylovParams(BICGSTAB, 50, maxit, 0, 0.0, 0), eps, int(c_adapt), 0)
+
+
+def build_batched(As, sai="spai", thresh_mult=10.0, abs_tau=-1.0, delta=0.4, mn=5, max_aug=10, key_bits=20, tol=0.0,
+                  tol_mode=1, lmax=10, sai_precision=0, keep="nearest", lfill=0, growth="A"):
+    """The batch's SAI build alone: a Precond of the block-diagonal A~ of the
+    batch (matrix m's rows and columns start at the sum of the earlier
+    orders); its diagonal blocks are the M_i that solve_batched uses."""
+    L = load()
+    nmat = len(As)
+    views = (_CscView * nmat)(*[A.view() for A in As])
+    prm = _batch_params(sai, 1e-8, 500, thresh_mult, abs_tau, delta, mn, max_aug, key_bits, tol, tol_mode, lmax,
+                        sai_precision, keep, lfill, growth, 0)
+    h = C.c_void_p()
+    _check("sai_build_batched", L.sai_build_batched(nmat, views, C.byref(prm), _stream(), C.byref(h)))
+    return Precond(h.value)
+
+
+def build_autotune_batched(As, sai="spai", thresh_mult=10.0, abs_tau=-1.0, delta=0.4, mn=5, max_aug=10, key_bits=20,
+                           tol=0.0, tol_mode=1, lmax=10, sai_precision=0, keep="nearest", lfill=0, growth="A"):
+    """The build-schedule autotuner on the batch's stacked A~; the fastest
+    configuration becomes the process-wide one. Returns (chosen, candidates)."""
+    L = load()
+    nmat = len(As)
+    views = (_CscView * nmat)(*[A.view() for A in As])
+    prm = _batch_params(sai, 1e-8, 500, thresh_mult, abs_tau, delta, mn, max_aug, key_bits, tol, tol_mode, lmax,
+                        sai_precision, keep, lfill, growth, 0)
+    t = _BuildTuning()
+    _check("sai_build_autotune_batched", L.sai_build_autotune_batched(nmat, views, C.byref(prm), _stream(),
+                                                                      C.byref(t)))
+    return _cfg_dict(t.chosen), [_cfg_dict(t.cand[i]) for i in range(t.ncand)]
 
 
 def launch_count():

@@ -510,12 +510,13 @@ sai_status host_norm(int32_t n, const double* v, double* out, cudaStream_t st)
     return SAI_OK;
 }
 
-// The s+1 solves with the Theorem 2 thresholds (c = 1) of eqs. (stopb) and
-// (stopU2), taken from rnorm = ||b|| (or ||g|| for the adjoint solves).
-// Returns an error, or SAI_OK with *kst the worst system status.
+// The s+1 solves with the Theorem 2 thresholds of eqs. (stopb) and (stopU2),
+// taken from rnorm = ||b|| (or ||g|| for the adjoint solves), with c = cu in
+// eq. (stopU2) (1 unless a continuation round tightens it). Returns an
+// error, or SAI_OK with *kst the worst system status.
 sai_status stage_solves(const sai_split_s& h, const sai_precond_s& P, const double* B, double rnorm,
                         const sai_krylov_params& kp, double eps, double* Y, int32_t* iters, int32_t iters_cap,
-                        int32_t* imax, sai_status* kst, cudaStream_t st)
+                        int32_t* imax, sai_status* kst, cudaStream_t st, double cu = 1.0)
 {
     const int32_t s = h.s, k = s + 1;
     double* thr = (double*)malloc(sizeof(double) * k);
@@ -528,7 +529,7 @@ sai_status stage_solves(const sai_split_s& h, const sai_precond_s& P, const doub
         return SAI_OOM;
     }
     thr[0] = 0.5 * eps * rnorm;
-    for (int t = 1; t < k; ++t) thr[t] = eps * rnorm / (2.0 * sqrt((double)s));
+    for (int t = 1; t < k; ++t) thr[t] = eps * rnorm / (2.0 * sqrt((double)s) * cu);
     const sai_status r = sai_krylov_run(&h, &P, k, B, thr, &kp, Y, it, stt, st);
     if (r == SAI_OK || r == SAI_MAXITER || r == SAI_BREAKDOWN) {
         int m = 0;
@@ -545,12 +546,21 @@ sai_status stage_solves(const sai_split_s& h, const sai_precond_s& P, const doub
     return (r == SAI_OK || r == SAI_MAXITER || r == SAI_BREAKDOWN) ? SAI_OK : r;
 }
 
+// Y += D over n x k values
+__global__ void k_add_block(int64_t m, const double* __restrict__ D, double* __restrict__ Y)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        Y[i] += D[i];
+}
+
 // Steps 3-5 of Procedure * on the handles: B = [b, u_1..u_s], the solves,
-// SMW recovery, rr.
+// SMW recovery, rr. c_adapt: when the recovery's c exceeds 1, one more round
+// continues the u_j systems (correction solves A~ d = u_j - A~ w_j to the
+// eq. (stopU2) threshold with c = 1.05 c, w_j += d) and recovers x again.
 sai_status solve_steps(const sai_csc_view* A, const sai_split_s& h, const sai_precond_s& P, const double* b,
                        const sai_krylov_params& kp, double eps, double* x, int32_t* iters, int32_t iters_cap,
                        sai_solve_report* rep, cudaEvent_t e_solve, cudaEvent_t e_smw, cudaEvent_t e_end,
-                       cudaStream_t st)
+                       cudaStream_t st, int c_adapt = 0)
 {
     const int32_t n = h.n, s = h.s, k = s + 1;
     Buf Bb, Yb;
@@ -567,8 +577,37 @@ sai_status solve_steps(const sai_csc_view* A, const sai_split_s& h, const sai_pr
     int32_t imax = 0;
     sai_status kst = SAI_OK;
     SAI_TRY(stage_solves(h, P, Bb.as<double>(), bnorm, kp, eps, Yb.as<double>(), iters, iters_cap, &imax, &kst, st));
-    SAI_CUDA(cudaEventRecord(e_smw, st));
     double c = 0.0;
+    if (c_adapt && s > 0) {
+        SAI_TRY(sai_smw_run(&h, Yb.as<double>(), x, &c, st));
+        if (c > 1.0) {
+            // R = B - A~ Y; its column 0 is cleared (the y system is not continued)
+            Buf Rb, Db;
+            SAI_TRY(Rb.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+            SAI_TRY(Db.alloc(sizeof(double) * (size_t)n * k + 8, st, true));
+            SAI_TRY(sai_spmm(n, h.Atr_rp.as<int64_t>(), h.Atr_ci.as<int32_t>(), h.Atr_v.as<double>(), k,
+                             Yb.as<double>(), Rb.as<double>(), Bb.as<double>(), 1, st));
+            SAI_CUDA(cudaMemset2DAsync(Rb.p, sizeof(double) * (size_t)k, 0, sizeof(double), (size_t)n, st));
+            std::vector<int32_t> it2((size_t)k, 0);
+            int32_t imax2 = 0;
+            sai_status kst2 = SAI_OK;
+            SAI_TRY(stage_solves(h, P, Rb.as<double>(), bnorm, kp, eps, Db.as<double>(), it2.data(), k, &imax2, &kst2,
+                                 st, 1.05 * c));
+            const int64_t m = (int64_t)n * k;
+            k_add_block<<<SAI_GRID(sai_div_up(m, 256) < 4096u ? sai_div_up(m, 256) : 4096u), 256, 0, st>>>(
+                m, Db.as<double>(), Yb.as<double>());
+            SAI_CUDA(cudaGetLastError());
+            imax = 0;
+            for (int32_t t = 0; t < k; ++t) {
+                const int32_t tot = (iters && t < iters_cap ? iters[t] : 0) + it2[t];
+                if (iters && t < iters_cap) iters[t] = tot;
+                imax = tot > imax ? tot : imax;
+            }
+            if (kst == SAI_OK) kst = kst2;
+            rep->c_rounds = 1;
+        }
+    }
+    SAI_CUDA(cudaEventRecord(e_smw, st));
     SAI_TRY(sai_smw_run(&h, Yb.as<double>(), x, &c, st));
     SAI_CUDA(cudaEventRecord(e_end, st));
     double nn[2] = {0.0, 0.0};
@@ -591,7 +630,8 @@ float elapsed(cudaEvent_t a, cudaEvent_t b)
 sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_params* prm, double* x,
                       int32_t* iters, int32_t iters_cap, sai_solve_report* rep, cudaStream_t st)
 {
-    if (!A || !prm || !rep || (A->n > 0 && (!b || !x)) || (prm->split.zero_diag != 0 && prm->split.zero_diag != 1))
+    if (!A || !prm || !rep || (A->n > 0 && (!b || !x)) || (prm->split.zero_diag != 0 && prm->split.zero_diag != 1) ||
+        (prm->c_adapt != 0 && prm->c_adapt != 1))
         return SAI_INVALID_ARG;
     *rep = sai_solve_report{};
     Ev e0, e1, e2, e3, e4, e5;
@@ -627,8 +667,8 @@ sai_status solve_impl(const sai_csc_view* A, const double* b, const sai_solve_pa
     if (prm->sai == 0) SAI_TRY(sai_spai_build(&h, &prm->spai, st, true, &P));
     else SAI_TRY(sai_psai_build(&h, &prm->psai, st, true, &P));
     SAI_CUDA(cudaEventRecord(e2.e, st));
-    const sai_status r =
-        solve_steps(A, h, P, b, prm->krylov, prm->eps, x, iters, iters_cap, rep, e3.e, e4.e, e5.e, st);
+    const sai_status r = solve_steps(A, h, P, b, prm->krylov, prm->eps, x, iters, iters_cap, rep, e3.e, e4.e, e5.e,
+                                     st, prm->c_adapt);
     if (r != SAI_OK && r != SAI_MAXITER && r != SAI_BREAKDOWN) return r;
     rep->ms_split = elapsed(e0.e, e1.e);
     rep->ms_build = elapsed(e1.e, e2.e);

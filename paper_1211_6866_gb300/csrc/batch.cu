@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <memory>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -389,6 +390,61 @@ __global__ void k_b_any(int32_t nsys, const int* active, int* any)
     if (threadIdx.x == 0) *any = f;
 }
 
+// The condition of the while node that runs the whole batched loop: true
+// while a system is active and fewer than max_body bodies have run.
+// nbody counts the bodies (for the launch count), any mirrors the flag.
+__global__ void k_b_cond(int32_t nsys, const int* active, int* any, int* nbody, int max_body,
+                         cudaGraphConditionalHandle h)
+{
+    __shared__ int f;
+    if (threadIdx.x == 0) f = 0;
+    __syncthreads();
+    int a = 0;
+    for (int c = threadIdx.x; c < nsys; c += blockDim.x) a |= active[c];
+    if (a) f = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nb = *nbody + 1;
+        *nbody = nb;
+        *any = f;
+        cudaGraphSetConditional(h, (f && nb < max_body) ? 1u : 0u);
+    }
+}
+
+// R = B - R on the systems with sel set (R holds A~ X there)
+__global__ void __launch_bounds__(BR) k_b_resid(BSys Y, const double* __restrict__ B, const int* sel, double* R)
+{
+    const int lane = threadIdx.x & 31;
+    FOR_WARP_ITEMS(Y, q)
+    {
+        const int c = Y.it_sys[q];
+        if (!sel[c]) continue;
+        const int64_t o = Y.off[c], r0 = Y.it_r0[q], n = Y.len[c];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int64_t i = r0 + lane + 32 * t;
+            if (i < n) R[o + i] = B[o + i] - R[o + i];
+        }
+    }
+}
+
+// X += D on the systems with sel set
+__global__ void __launch_bounds__(BR) k_b_acc(BSys Y, const double* __restrict__ D, const int* sel, double* X)
+{
+    const int lane = threadIdx.x & 31;
+    FOR_WARP_ITEMS(Y, q)
+    {
+        const int c = Y.it_sys[q];
+        if (!sel[c]) continue;
+        const int64_t o = Y.off[c], r0 = Y.it_r0[q], n = Y.len[c];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int64_t i = r0 + lane + 32 * t;
+            if (i < n) X[o + i] += D[o + i];
+        }
+    }
+}
+
 // B = [b_i, u_i1 .. u_is] per matrix (U_i scattered into its systems)
 __global__ void k_b_rhs_b(int32_t n, const double* __restrict__ b, double* __restrict__ B)
 {
@@ -526,6 +582,58 @@ unsigned grid_for(int64_t work, int64_t cap)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// The block-diagonal A~ of a batch (CSC and CSR with row / column offsets,
+// ||a~_j||^2, the largest ||A~_i||_1) from the matrices' split handles;
+// R0[m] = first row of matrix m.
+sai_status stack_splits(int32_t nmat, const std::vector<std::unique_ptr<sai_split_s>>& hs, sai_split_s& bd,
+                        std::vector<int64_t>& R0, int64_t cap, cudaStream_t st)
+{
+    R0.assign(nmat + 1, 0);
+    std::vector<int64_t> Z0(nmat + 1, 0);
+    double norm1 = 0.0;
+    for (int32_t m = 0; m < nmat; ++m) {
+        R0[m + 1] = R0[m] + hs[m]->n;
+        Z0[m + 1] = Z0[m] + hs[m]->nnz_At;
+        norm1 = hs[m]->norm1 > norm1 ? hs[m]->norm1 : norm1;
+    }
+    const int64_t N = R0[nmat], NZ = Z0[nmat];
+    if (N > INT32_MAX - 1) return SAI_INVALID_ARG;
+    bd.n = (int32_t)N;
+    bd.nnz_At = NZ;
+    bd.norm1 = norm1;
+    SAI_TRY(bd.At_cp.alloc(sizeof(int64_t) * (size_t)(N + 1), st, true));
+    SAI_TRY(bd.At_ri.alloc(sizeof(int32_t) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.At_v.alloc(sizeof(double) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.Atr_rp.alloc(sizeof(int64_t) * (size_t)(N + 1), st, true));
+    SAI_TRY(bd.Atr_ci.alloc(sizeof(int32_t) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.Atr_v.alloc(sizeof(double) * (size_t)(NZ > 0 ? NZ : 1), st, true));
+    SAI_TRY(bd.colnorm2.alloc(sizeof(double) * (size_t)N, st, true));
+    for (int32_t m = 0; m < nmat; ++m) {
+        const sai_split_s& h = *hs[m];
+        const int64_t n = h.n, z = h.nnz_At;
+        const unsigned gz = grid_for(sai_div_up(z > n ? z : n, 256), cap);
+        k_b_add_i64<<<SAI_GRID(gz), 256, 0, st>>>(n, h.At_cp.as<int64_t>(), Z0[m], bd.At_cp.as<int64_t>() + R0[m]);
+        k_b_add_i64<<<SAI_GRID(gz), 256, 0, st>>>(n, h.Atr_rp.as<int64_t>(), Z0[m], bd.Atr_rp.as<int64_t>() + R0[m]);
+        if (z > 0) {
+            k_b_add_i32<<<SAI_GRID(gz), 256, 0, st>>>(z, h.At_ri.as<int32_t>(), (int32_t)R0[m],
+                                                      bd.At_ri.as<int32_t>() + Z0[m]);
+            k_b_add_i32<<<SAI_GRID(gz), 256, 0, st>>>(z, h.Atr_ci.as<int32_t>(), (int32_t)R0[m],
+                                                      bd.Atr_ci.as<int32_t>() + Z0[m]);
+            SAI_CUDA(cudaMemcpyAsync(bd.At_v.as<double>() + Z0[m], h.At_v.p, sizeof(double) * z,
+                                     cudaMemcpyDeviceToDevice, st));
+            SAI_CUDA(cudaMemcpyAsync(bd.Atr_v.as<double>() + Z0[m], h.Atr_v.p, sizeof(double) * z,
+                                     cudaMemcpyDeviceToDevice, st));
+        }
+        SAI_CUDA(cudaMemcpyAsync(bd.colnorm2.as<double>() + R0[m], h.colnorm2.p, sizeof(double) * n,
+                                 cudaMemcpyDeviceToDevice, st));
+    }
+    SAI_CUDA(cudaMemcpyAsync(bd.At_cp.as<int64_t>() + N, &Z0[nmat], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SAI_CUDA(cudaMemcpyAsync(bd.Atr_rp.as<int64_t>() + N, &Z0[nmat], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SAI_CUDA(cudaGetLastError());
+
+    return SAI_OK;
+}
+
 sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const* b, const sai_solve_params* prm,
                         double* const* x, sai_batch_item* items, sai_batch_report* rep, cudaStream_t st)
 {
@@ -616,48 +724,10 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     SAI_CUDA(cudaEventRecord(e1.e, st));
 
     // ---- the block-diagonal A~ of the batch (CSC and CSR), ||a~_j||^2
-    std::vector<int64_t> R0(nmat + 1, 0), Z0(nmat + 1, 0);
-    double norm1 = 0.0;
-    for (int32_t m = 0; m < nmat; ++m) {
-        R0[m + 1] = R0[m] + hs[m]->n;
-        Z0[m + 1] = Z0[m] + hs[m]->nnz_At;
-        norm1 = hs[m]->norm1 > norm1 ? hs[m]->norm1 : norm1;
-    }
-    const int64_t N = R0[nmat], NZ = Z0[nmat];
-    if (N > INT32_MAX - 1) return SAI_INVALID_ARG;
+    std::vector<int64_t> R0;
     sai_split_s bd;
-    bd.n = (int32_t)N;
-    bd.nnz_At = NZ;
-    bd.norm1 = norm1;
-    SAI_TRY(bd.At_cp.alloc(sizeof(int64_t) * (size_t)(N + 1), st, true));
-    SAI_TRY(bd.At_ri.alloc(sizeof(int32_t) * (size_t)(NZ > 0 ? NZ : 1), st, true));
-    SAI_TRY(bd.At_v.alloc(sizeof(double) * (size_t)(NZ > 0 ? NZ : 1), st, true));
-    SAI_TRY(bd.Atr_rp.alloc(sizeof(int64_t) * (size_t)(N + 1), st, true));
-    SAI_TRY(bd.Atr_ci.alloc(sizeof(int32_t) * (size_t)(NZ > 0 ? NZ : 1), st, true));
-    SAI_TRY(bd.Atr_v.alloc(sizeof(double) * (size_t)(NZ > 0 ? NZ : 1), st, true));
-    SAI_TRY(bd.colnorm2.alloc(sizeof(double) * (size_t)N, st, true));
-    for (int32_t m = 0; m < nmat; ++m) {
-        const sai_split_s& h = *hs[m];
-        const int64_t n = h.n, z = h.nnz_At;
-        const unsigned gz = grid_for(sai_div_up(z > n ? z : n, 256), cap);
-        k_b_add_i64<<<SAI_GRID(gz), 256, 0, st>>>(n, h.At_cp.as<int64_t>(), Z0[m], bd.At_cp.as<int64_t>() + R0[m]);
-        k_b_add_i64<<<SAI_GRID(gz), 256, 0, st>>>(n, h.Atr_rp.as<int64_t>(), Z0[m], bd.Atr_rp.as<int64_t>() + R0[m]);
-        if (z > 0) {
-            k_b_add_i32<<<SAI_GRID(gz), 256, 0, st>>>(z, h.At_ri.as<int32_t>(), (int32_t)R0[m],
-                                                      bd.At_ri.as<int32_t>() + Z0[m]);
-            k_b_add_i32<<<SAI_GRID(gz), 256, 0, st>>>(z, h.Atr_ci.as<int32_t>(), (int32_t)R0[m],
-                                                      bd.Atr_ci.as<int32_t>() + Z0[m]);
-            SAI_CUDA(cudaMemcpyAsync(bd.At_v.as<double>() + Z0[m], h.At_v.p, sizeof(double) * z,
-                                     cudaMemcpyDeviceToDevice, st));
-            SAI_CUDA(cudaMemcpyAsync(bd.Atr_v.as<double>() + Z0[m], h.Atr_v.p, sizeof(double) * z,
-                                     cudaMemcpyDeviceToDevice, st));
-        }
-        SAI_CUDA(cudaMemcpyAsync(bd.colnorm2.as<double>() + R0[m], h.colnorm2.p, sizeof(double) * n,
-                                 cudaMemcpyDeviceToDevice, st));
-    }
-    SAI_CUDA(cudaMemcpyAsync(bd.At_cp.as<int64_t>() + N, &Z0[nmat], sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    SAI_CUDA(cudaMemcpyAsync(bd.Atr_rp.as<int64_t>() + N, &Z0[nmat], sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    SAI_CUDA(cudaGetLastError());
+    SAI_TRY(stack_splits(nmat, hs, bd, R0, cap, st));
+    const int64_t N = R0[nmat];
 
     // ---- one SAI build for every column of the batch
     sai_precond_s P;
@@ -748,7 +818,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     double* sh = s + NV;
     double* t = sh + NV;
     SAI_TRY(bst.alloc(sizeof(double) * 6 * (size_t)nsys, st, true));
-    SAI_TRY(bsi.alloc(sizeof(int) * (5 * (size_t)nsys + 1), st, true));
+    SAI_TRY(bsi.alloc(sizeof(int) * (5 * (size_t)nsys + 2), st, true));
     SAI_TRY(part.alloc(sizeof(double) * 2 * (size_t)(nit > 0 ? nit : 1), st, true));
     SAI_TRY(misc.alloc(sizeof(double) * ((size_t)joff[nmat] + 2 * (size_t)nmat + 4), st, true));
     BState S;
@@ -766,7 +836,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     S.mode = ip + 3 * nsys;
     S.go = ip + 4 * nsys;
     int* any = ip + 5 * nsys;
-    SAI_CUDA(cudaMemsetAsync(ip, 0, sizeof(int) * (5 * (size_t)nsys + 1), st));
+    SAI_CUDA(cudaMemsetAsync(ip, 0, sizeof(int) * (5 * (size_t)nsys + 2), st));
 
     // right-hand sides and the Theorem 2 thresholds of each matrix
     std::vector<double> thr(nsys);
@@ -807,11 +877,10 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     const unsigned gs = sai_div_up((int64_t)nsys * 32, 256), gt = sai_div_up(nsys, 256);
     double* pt = part.as<double>();
     const int maxit = prm->krylov.maxit;
-    k_b_f0<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
-    SAI_CUDA(cudaGetLastError());
     BWork Wk;
     Wk.Arp = Ar;
     Wk.Mrp = Mr;
+    double* Xd = X;  // the iterates of the current pass
     // profile scopes act only while a profile is open, when no graph is captured
     auto iteration = [&](cudaStream_t q) {
         k_b_start<<<SAI_GRID(gt), 256, 0, q>>>(nsys, maxit, S);
@@ -852,68 +921,128 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
         k_b_f3<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S, Wk);
         {
             ProfScope ps(PROF_BICG_VEC, q);
-            k_b_xr<<<SAI_GRID(gw), BR, 0, q>>>(Y, X, r, rh, ph, sh, s, t, S, pt);
+            k_b_xr<<<SAI_GRID(gw), BR, 0, q>>>(Y, Xd, r, rh, ph, sh, s, t, S, pt);
         }
         k_b_f4<<<SAI_GRID(gs), 256, 0, q>>>(Y, pt, S);
     };
     constexpr int ITERS_PER_CHECK = 8, LAUNCHES = ITERS_PER_CHECK * 14 + 1;
-    // Groups of ITERS_PER_CHECK iterations (and the any-active test) run as one
-    // CUDA graph, captured once on a library stream ordered after the caller's;
-    // iterations past maxit change nothing (k_b_start retires those systems).
-    cudaStream_t q = st;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    if (!sai_prof_on()) {
-        cudaStream_t aux = sai_aux_stream();
-        if (aux) {
-            SAI_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
-            SAI_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
-            SAI_CUDA(cudaEventRecord(ev_in, st));
-            SAI_CUDA(cudaStreamWaitEvent(aux, ev_in, 0));
-            q = aux;
-            cudaGraph_t graph = nullptr;
-            SAI_CUDA(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
-            for (int k = 0; k < ITERS_PER_CHECK; ++k) iteration(q);
-            k_b_any<<<SAI_GRID(1), 1024, 0, q>>>(nsys, S.active, any);
-            cudaError_t e = cudaStreamEndCapture(q, &graph);
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            if (e != cudaSuccess) {
-                gexec = nullptr;
-                (void)cudaGetLastError();
+    int* nbody = any + 1;  // body runs of the while graph
+    // One pass of the batched BiCGStab from x = 0 on the right-hand sides
+    // Bsrc (thresholds in S.thr), iterates into Xdst. Without an open
+    // profile the whole loop is one CUDA graph launch: a conditional while
+    // node whose body runs ITERS_PER_CHECK iterations and then k_b_cond,
+    // which keeps the loop going while any system is active and fewer than
+    // maxit iterations have run. Where that graph cannot be built, groups of
+    // ITERS_PER_CHECK iterations run as a captured graph with one host check
+    // of the "any system active" flag per group. Both run on a library
+    // stream ordered after the caller's; iterations past maxit change nothing
+    // (k_b_start retires those systems).
+    auto run_pass = [&](const double* Bsrc, double* Xdst) -> sai_status {
+        Xd = Xdst;
+        k_b_init<<<SAI_GRID(gw), BR, 0, st>>>(Y, Bsrc, Xdst, r, rh, p, v, pt);
+        k_b_f0<<<SAI_GRID(gs), 256, 0, st>>>(Y, pt, S);
+        SAI_CUDA(cudaMemsetAsync(any, 0, sizeof(int) * 2, st));
+        SAI_CUDA(cudaGetLastError());
+        cudaStream_t q = st;
+        cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+        cudaGraphExec_t gexec = nullptr;
+        bool whole = false;  // gexec is the whole loop
+        const int max_body = (maxit + ITERS_PER_CHECK - 1) / ITERS_PER_CHECK;
+        if (!sai_prof_on()) {
+            cudaStream_t aux = sai_aux_stream();
+            if (aux) {
+                SAI_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+                SAI_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+                SAI_CUDA(cudaEventRecord(ev_in, st));
+                SAI_CUDA(cudaStreamWaitEvent(aux, ev_in, 0));
+                q = aux;
+                // the whole loop: a while node around the body
+                cudaGraph_t graph = nullptr;
+                cudaError_t e = max_body > 0 ? cudaGraphCreate(&graph, 0) : cudaErrorNotSupported;
+                cudaGraphConditionalHandle hnd = 0;
+                if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hnd, graph, 1, cudaGraphCondAssignDefault);
+                cudaGraph_t body = nullptr;
+                if (e == cudaSuccess) {
+                    cudaGraphNodeParams np = {};
+                    np.type = cudaGraphNodeTypeConditional;
+                    np.conditional.handle = hnd;
+                    np.conditional.type = cudaGraphCondTypeWhile;
+                    np.conditional.size = 1;
+                    cudaGraphNode_t node = nullptr;
+                    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+                    if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+                }
+                if (e == cudaSuccess)
+                    e = cudaStreamBeginCaptureToGraph(q, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int k = 0; k < ITERS_PER_CHECK; ++k) iteration(q);
+                    k_b_cond<<<SAI_GRID(1), 1024, 0, q>>>(nsys, S.active, any, nbody, max_body, hnd);
+                    cudaGraph_t cap_g = nullptr;
+                    e = cudaStreamEndCapture(q, &cap_g);
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e == cudaSuccess) {
+                    whole = true;
+                } else {
+                    gexec = nullptr;
+                    (void)cudaGetLastError();
+                    // groups of iterations with host checks
+                    graph = nullptr;
+                    SAI_CUDA(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
+                    for (int k = 0; k < ITERS_PER_CHECK; ++k) iteration(q);
+                    k_b_any<<<SAI_GRID(1), 1024, 0, q>>>(nsys, S.active, any);
+                    e = cudaStreamEndCapture(q, &graph);
+                    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+                    if (graph) cudaGraphDestroy(graph);
+                    if (e != cudaSuccess) {
+                        gexec = nullptr;
+                        (void)cudaGetLastError();
+                    }
+                }
+                sai_count_grid_add(-(long long)LAUNCHES);  // captured, not run: counted at replay
             }
-            sai_count_grid_add(-(long long)LAUNCHES);  // captured, not run: counted at replay
         }
-    }
-    int hflag = 0;
-    sai_status kst = SAI_OK;
-    for (int it = 0; it < maxit; it += ITERS_PER_CHECK) {
-        if (gexec) {
-            if (cudaGraphLaunch(gexec, q) != cudaSuccess) {
-                kst = SAI_CUDA_ERROR;
-                break;
+        sai_status kst = SAI_OK;
+        if (whole) {
+            if (cudaGraphLaunch(gexec, q) != cudaSuccess) kst = SAI_CUDA_ERROR;
+            int nb = 0;
+            if (kst == SAI_OK) {
+                SAI_CUDA(cudaMemcpyAsync(&nb, nbody, sizeof(int), cudaMemcpyDeviceToHost, q));
+                SAI_CUDA(cudaStreamSynchronize(q));
             }
-            sai_count_grid_add(LAUNCHES);
+            sai_count_grid_add((long long)nb * LAUNCHES);
         } else {
-            for (int k = 0; k < ITERS_PER_CHECK; ++k) iteration(q);
-            k_b_any<<<SAI_GRID(1), 1024, 0, q>>>(nsys, S.active, any);
+            int hflag = 0;
+            for (int it = 0; it < maxit; it += ITERS_PER_CHECK) {
+                if (gexec) {
+                    if (cudaGraphLaunch(gexec, q) != cudaSuccess) {
+                        kst = SAI_CUDA_ERROR;
+                        break;
+                    }
+                    sai_count_grid_add(LAUNCHES);
+                } else {
+                    for (int k = 0; k < ITERS_PER_CHECK; ++k) iteration(q);
+                    k_b_any<<<SAI_GRID(1), 1024, 0, q>>>(nsys, S.active, any);
+                }
+                SAI_CUDA(cudaGetLastError());
+                SAI_CUDA(cudaMemcpyAsync(&hflag, any, sizeof(int), cudaMemcpyDeviceToHost, q));
+                SAI_CUDA(cudaStreamSynchronize(q));
+                if (!hflag) break;
+            }
+        }
+        if (gexec) cudaGraphExecDestroy(gexec);
+        k_b_start<<<SAI_GRID(gt), 256, 0, q>>>(nsys, maxit, S);  // systems still running after maxit
+        if (ev_in) {
+            cudaEventRecord(ev_out, q);
+            cudaStreamWaitEvent(st, ev_out, 0);
+            cudaEventDestroy(ev_in);
+            cudaEventDestroy(ev_out);
         }
         SAI_CUDA(cudaGetLastError());
-        SAI_CUDA(cudaMemcpyAsync(&hflag, any, sizeof(int), cudaMemcpyDeviceToHost, q));
-        SAI_CUDA(cudaStreamSynchronize(q));
-        if (!hflag) break;
-    }
-    if (gexec) cudaGraphExecDestroy(gexec);
-    k_b_start<<<SAI_GRID(gt), 256, 0, q>>>(nsys, maxit, S);  // systems still running after maxit
-    if (ev_in) {
-        cudaEventRecord(ev_out, q);
-        cudaStreamWaitEvent(st, ev_out, 0);
-        cudaEventDestroy(ev_in);
-        cudaEventDestroy(ev_out);
-    }
-    SAI_CUDA(cudaGetLastError());
-    if (kst != SAI_OK) return kst;
-    SAI_CUDA(cudaEventRecord(e4.e, st));
+        return kst;
+    };
+    SAI_TRY(run_pass(Bv, X));
 
     // ---- SMW per matrix, x_m = yhat_m - What_m z_m, rr per matrix
     double* zcat = misc.as<double>();
@@ -922,20 +1051,78 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
     W.z = zcat;
     W.c = cvec;
     W.err = errv;
-    SAI_CUDA(cudaMemsetAsync(cvec, 0, sizeof(double) * nmat, st));
-    SAI_CUDA(cudaMemsetAsync(errv, 0, sizeof(int) * nmat, st));
     const size_t smw_smem = sizeof(double) * ((size_t)smax * smax + smax);
     if (smw_smem > 48 * 1024)
         SAI_CUDA(cudaFuncSetAttribute(k_b_smw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw_smem));
-    k_b_smw<<<SAI_GRID(nmat), 256, smw_smem, st>>>(W, X, smax);
+    auto smw_all = [&]() -> sai_status {
+        SAI_CUDA(cudaMemsetAsync(cvec, 0, sizeof(double) * nmat, st));
+        SAI_CUDA(cudaMemsetAsync(errv, 0, sizeof(int) * nmat, st));
+        k_b_smw<<<SAI_GRID(nmat), 256, smw_smem, st>>>(W, X, smax);
+        SAI_CUDA(cudaGetLastError());
+        return SAI_OK;
+    };
+    std::vector<int> it_h(nsys), st_h(nsys), err_h(nmat);
+    std::vector<double> c_h(nmat);
+    std::vector<int32_t> rounds(nmat, 0);
+    if (prm->c_adapt) {
+        // Theorem 2 with the measured c: a matrix whose c = ||z_m|| exceeds 1
+        // has its u_j systems continued from their iterates (correction
+        // solves A~ d = u_j - A~ w_j to eps ||b_m|| / (2 sqrt(s_m) 1.05 c_m),
+        // w_j += d) before the recovery
+        SAI_TRY(smw_all());
+        SAI_CUDA(cudaMemcpyAsync(c_h.data(), cvec, sizeof(double) * nmat, cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaMemcpyAsync(it_h.data(), S.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaMemcpyAsync(st_h.data(), S.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> sel(nsys, 0);
+        std::vector<double> thr2(thr);
+        bool any_sel = false;
+        for (int32_t m = 0; m < nmat; ++m)
+            if (hs[m]->s > 0 && c_h[m] > 1.0) {
+                rounds[m] = 1;
+                any_sel = true;
+                for (int32_t c = sys0[m] + 1; c < sys0[m + 1]; ++c) {
+                    sel[c] = 1;
+                    thr2[c] = thr[c] / (1.05 * c_h[m]);
+                }
+            }
+        if (any_sel) {
+            Buf extra;
+            SAI_TRY(extra.alloc(sizeof(double) * 2 * (size_t)NV + sizeof(int) * (size_t)nsys + 64, st, true));
+            double* R = extra.as<double>();
+            double* D = R + NV;
+            int* dsel = (int*)(D + NV);  // the continued systems
+            SAI_CUDA(cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+            SAI_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)NV, st));
+            k_b_spmv<<<SAI_GRID(gi), BR, 0, st>>>(Y, Ar, Ac, Av, X, R, dsel);
+            k_b_resid<<<SAI_GRID(gw), BR, 0, st>>>(Y, Bv, dsel, R);
+            SAI_CUDA(cudaGetLastError());
+            SAI_CUDA(cudaMemcpyAsync(S.thr, thr2.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st));
+            SAI_TRY(run_pass(R, D));
+            k_b_acc<<<SAI_GRID(gw), BR, 0, st>>>(Y, D, dsel, X);
+            SAI_CUDA(cudaGetLastError());
+            std::vector<int> it2(nsys), st2(nsys);
+            SAI_CUDA(cudaMemcpyAsync(it2.data(), S.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaMemcpyAsync(st2.data(), S.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaStreamSynchronize(st));
+            for (int32_t c = 0; c < nsys; ++c)
+                if (sel[c]) {
+                    it_h[c] += it2[c];
+                    if (st_h[c] == B_OK) st_h[c] = st2[c];
+                }
+            SAI_CUDA(cudaMemcpyAsync(S.iters, it_h.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+            SAI_CUDA(cudaMemcpyAsync(S.status, st_h.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+            SAI_CUDA(cudaStreamSynchronize(st));  // extra (and the host vectors) go out of scope
+        }
+    }
+    SAI_CUDA(cudaEventRecord(e4.e, st));
+    SAI_TRY(smw_all());
     for (int32_t m = 0; m < nmat; ++m)
         k_b_xhat<<<SAI_GRID(sai_div_up(hs[m]->n, 256)), 256, 0, st>>>(hs[m]->n, hs[m]->s, X + xoff[m], zcat + joff[m],
                                                                      x[m]);
     SAI_CUDA(cudaGetLastError());
     Ev e5;
     SAI_CUDA(cudaEventRecord(e5.e, st));
-    std::vector<int> it_h(nsys), st_h(nsys), err_h(nmat);
-    std::vector<double> c_h(nmat);
     SAI_CUDA(cudaMemcpyAsync(it_h.data(), S.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaMemcpyAsync(st_h.data(), S.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaMemcpyAsync(err_h.data(), errv, sizeof(int) * nmat, cudaMemcpyDeviceToHost, st));
@@ -948,6 +1135,7 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
         it.s = hs[m]->s;
         it.p = hs[m]->p;
         it.c = c_h[m];
+        it.c_rounds = rounds[m];
         for (int32_t c = sys0[m]; c < sys0[m + 1]; ++c) {
             if (it_h[c] > it.iter_max) it.iter_max = it_h[c];
             if (st_h[c] != B_OK && it.status == SAI_OK) it.status = st_h[c];
@@ -970,6 +1158,65 @@ sai_status batched_impl(int32_t nmat, const sai_csc_view* A, const double* const
 }
 
 }  // namespace
+
+namespace {
+
+// The matrices split one after another on st and stacked (for the build-only
+// entry points; sai_solve_batched splits on worker streams).
+sai_status split_and_stack(int32_t nmat, const sai_csc_view* A, const sai_solve_params* prm,
+                           std::vector<std::unique_ptr<sai_split_s>>& hs, sai_split_s& bd, cudaStream_t st)
+{
+    if (nmat < 1 || !A || !prm || prm->split.zero_diag != 0) return SAI_INVALID_ARG;
+    if (prm->sai == 1 && prm->psai.tol_mode == 0) return SAI_NOT_IMPLEMENTED;
+    int dev = 0, sms = 0;
+    SAI_CUDA(cudaGetDevice(&dev));
+    SAI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    hs.resize((size_t)nmat);
+    for (int32_t m = 0; m < nmat; ++m) {
+        if (A[m].n < 1) return SAI_INVALID_ARG;
+        hs[m].reset(new (std::nothrow) sai_split_s);
+        if (!hs[m]) return SAI_OOM;
+        SAI_TRY(sai_split_build(&A[m], &prm->split, st, true, hs[m].get()));
+    }
+    std::vector<int64_t> R0;
+    return stack_splits(nmat, hs, bd, R0, (int64_t)sms * 8, st);
+}
+
+}  // namespace
+
+extern "C" sai_status sai_build_batched(int32_t nmat, const sai_csc_view* A, const sai_solve_params* prm,
+                                        sai_stream_t stream, sai_precond* out)
+{
+    if (!out) return SAI_INVALID_ARG;
+    *out = nullptr;
+    sai_pool_init_once();
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<std::unique_ptr<sai_split_s>> hs;
+    sai_split_s bd;
+    SAI_TRY(split_and_stack(nmat, A, prm, hs, bd, st));
+    sai_precond_s* P = new (std::nothrow) sai_precond_s();
+    if (!P) return SAI_OOM;
+    const sai_status r = prm->sai == 0 ? sai_spai_build(&bd, &prm->spai, st, false, P)
+                                       : sai_psai_build(&bd, &prm->psai, st, false, P);
+    if (r != SAI_OK) {
+        delete P;
+        return r;
+    }
+    *out = P;
+    return SAI_OK;
+}
+
+extern "C" sai_status sai_build_autotune_batched(int32_t nmat, const sai_csc_view* A, const sai_solve_params* prm,
+                                                 sai_stream_t stream, sai_build_tuning* out)
+{
+    if (!out) return SAI_INVALID_ARG;
+    sai_pool_init_once();
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<std::unique_ptr<sai_split_s>> hs;
+    sai_split_s bd;
+    SAI_TRY(split_and_stack(nmat, A, prm, hs, bd, st));
+    return sai_build_autotune_run(&bd, prm->sai, &prm->spai, &prm->psai, st, out);
+}
 
 extern "C" sai_status sai_solve_batched(int32_t nmat, const sai_csc_view* A, const double* const* b,
                                         const sai_solve_params* prm, double* const* x, sai_batch_item* items,

@@ -45,7 +45,10 @@ def test_abi_structs_match_the_binding():
     assert [f for f, _ in sai._SplitParams._fields_] == ["thresh_mult", "abs_tau", "ge", "p_keep", "keep_rule",
                                                           "zero_diag"]
     assert C.sizeof(sai._SplitParams) == 32
-    assert [f for f, _ in sai._SolveReport._fields_][-2:] == ["moved", "reserved"]
+    assert [f for f, _ in sai._SolveReport._fields_][-2:] == ["moved", "c_rounds"]
+    assert [f for f, _ in sai._SolveParams._fields_][-3:] == ["eps", "c_adapt", "reserved"]
+    assert "int32_t c_adapt;" in hdr and "int32_t c_rounds;" in hdr
+    assert [f for f, _ in sai._BatchItem._fields_][-2:] == ["c_rounds", "reserved"]
     assert re.search(r"SAI_BGMRES\s*=\s*4", hdr) and sai.BGMRES == 4 and sai._METHOD["bgmres"] == 4
     # the build schedule: four int32 fields and the measured time; five tier counts
     assert "int32_t first_tier;" in hdr and "int32_t n_tier[5];" in hdr
