@@ -228,8 +228,11 @@ typedef struct {
     int64_t nnz_M;
     int32_t n_c;        /* columns whose final (pre-drop) residual > delta */
     int32_t l_m;        /* largest loop index used over all columns */
-    int32_t n_tier[5];  /* columns finished per workspace tier: 0 shared memory, 1-3 global
-                           memory, 4 the small shared-memory tier (first_tier 1 or 2) */
+    int32_t n_tier[6];  /* columns finished per workspace tier: 0 shared memory (|L| <= 64,
+                           |S| <= 16), 1-3 global memory (|L| <= 256 / 1024 / 2048, |S| <= 64 /
+                           128 / 128), 4 the small shared-memory tier (first_tier 1 or 2),
+                           5 the large-pattern tier (|L| <= 4096, |S| <= 2048, one warp per
+                           column and per SM) */
     double build_ms;    /* device time of the build, CUDA events */
 } sai_precond_info;
 

@@ -67,7 +67,7 @@ class _PsaiParams(C.Structure):
 
 class _PrecondInfo(C.Structure):
     _fields_ = [("n", C.c_int32), ("nnz_M", C.c_int64), ("n_c", C.c_int32), ("l_m", C.c_int32),
-                ("n_tier", C.c_int32 * 5), ("build_ms", C.c_double)]
+                ("n_tier", C.c_int32 * 6), ("build_ms", C.c_double)]
 
 
 class _KrylovParams(C.Structure):

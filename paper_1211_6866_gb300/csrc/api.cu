@@ -332,7 +332,7 @@ sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info)
     info->nnz_M = P->nnz;
     info->n_c = P->n_c;
     info->l_m = P->l_m;
-    for (int q = 0; q < 5; ++q) info->n_tier[q] = P->n_tier[q];
+    for (int q = 0; q < 6; ++q) info->n_tier[q] = P->n_tier[q];
     info->build_ms = P->ms;
     return SAI_OK;
 }
@@ -492,7 +492,7 @@ void report_handles(const sai_split_s& h, const sai_precond_s& P, sai_solve_repo
     rep->precond.nnz_M = P.nnz;
     rep->precond.n_c = P.n_c;
     rep->precond.l_m = P.l_m;
-    for (int q = 0; q < 5; ++q) rep->precond.n_tier[q] = P.n_tier[q];
+    for (int q = 0; q < 6; ++q) rep->precond.n_tier[q] = P.n_tier[q];
     rep->precond.build_ms = P.ms;
 }
 

@@ -63,7 +63,7 @@ struct sai_precond_s {
     int32_t n = 0;
     int64_t nnz = 0;
     int32_t n_c = 0, l_m = 0;
-    int32_t n_tier[5] = {0, 0, 0, 0, 0};
+    int32_t n_tier[6] = {0, 0, 0, 0, 0, 0};
     float ms = 0.f;
     Buf M_cp, M_ri, M_v;     // CSC
     Buf Mr_rp, Mr_ci, Mr_v;  // CSR

@@ -1639,13 +1639,19 @@ __device__ __forceinline__ void rebuild_list(int k, const int* mask, int* list)
 // the chunk partials, finishes column j-1 (Givens rotation, residual
 // estimate |g_j|, stop tests) and forms the coefficients of k_dc_update.
 // tiny: relative floor of alpha^2 below which u counts as lying in span(V).
+// The sums, alpha and d are FP64; the Givens rotations and the products
+// with Hbar run in T, the type of the basis (FP32 for the inner solves of
+// the refined GMRES, whose basis and inner products carry FP32 rounding
+// already): they are the serial chain of the step, and one FP64
+// instruction issues at 1/64 of the FP32 rate on this GPU.
+template <class T>
 __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const double* __restrict__ part,
                                                          const int* cap, Sys S, Gm G, Dims D, double tiny,
                                                          int* any_adv)
 {
     __shared__ double red[PS];
-    __shared__ double rc[GM_MAXM + 1];
-    __shared__ double csS[GM_MAXM], snS[GM_MAXM];
+    __shared__ T rc[GM_MAXM + 1];
+    __shared__ T csS[GM_MAXM], snS[GM_MAXM];
     __shared__ double sh[2];
     __shared__ int stop, mine;
     extern __shared__ double hsm[];  // columns q < j of Hbar (leading dimension m + 1)
@@ -1722,29 +1728,31 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
             for (int i = tid; i <= j; i += blockDim.x) {
                 const double v = i < j ? hpc[i] + red[2 * i] : al;
                 Huc[(size_t)(j - 1) * (m + 1) + i] = v;
-                rc[i] = v;
+                rc[i] = (T)v;
             }
             for (int i = tid; i < j - 1; i += blockDim.x) {
-                csS[i] = G.cs[(size_t)c * m + i];
-                snS[i] = G.sn[(size_t)c * m + i];
+                csS[i] = (T)G.cs[(size_t)c * m + i];
+                snS[i] = (T)G.sn[(size_t)c * m + i];
             }
             __syncthreads();
             if (tid == 0) {
+                T ri = rc[0];
                 for (int i = 0; i < j - 1; ++i) {
-                    const double a = rc[i], b = rc[i + 1];
-                    rc[i] = csS[i] * a + snS[i] * b;
-                    rc[i + 1] = -snS[i] * a + csS[i] * b;
+                    const T b = rc[i + 1];
+                    rc[i] = csS[i] * ri + snS[i] * b;
+                    ri = -snS[i] * ri + csS[i] * b;
                 }
-                const double a = rc[j - 1], b = rc[j];
-                const double den = sqrt(a * a + b * b);
-                const double cn = den == 0.0 ? 1.0 : a / den, sn = den == 0.0 ? 0.0 : b / den;
-                G.cs[(size_t)c * m + j - 1] = cn;
-                G.sn[(size_t)c * m + j - 1] = sn;
+                const T a = ri, b = rc[j];
+                const T den = sqrt(a * a + b * b);
+                const T cn = den == (T)0 ? (T)1 : a / den, sn = den == (T)0 ? (T)0 : b / den;
+                G.cs[(size_t)c * m + j - 1] = (double)cn;
+                G.sn[(size_t)c * m + j - 1] = (double)sn;
                 rc[j - 1] = cn * a + sn * b;
-                rc[j] = 0.0;
+                rc[j] = (T)0;
                 double* gc = G.g + (size_t)c * (m + 1);
-                gc[j] = -sn * gc[j - 1];
-                gc[j - 1] = cn * gc[j - 1];
+                const T gj1 = (T)gc[j - 1];
+                gc[j] = (double)(-sn * gj1);
+                gc[j - 1] = (double)(cn * gj1);
                 S.iters[c] += 1;
                 G.jd[c] = j;
                 if (fabs(gc[j]) < S.thr[c]) {
@@ -1755,7 +1763,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
                 }
             }
             __syncthreads();
-            for (int i = tid; i <= j; i += blockDim.x) Hc[(size_t)(j - 1) * (m + 1) + i] = rc[i];
+            for (int i = tid; i <= j; i += blockDim.x) Hc[(size_t)(j - 1) * (m + 1) + i] = (double)rc[i];
         } else if (tid == 0) {
             // v_0 = r0 / alpha: the right-hand side of the small problem is alpha e_1
             G.g[(size_t)c * (m + 1)] = al;
@@ -1776,18 +1784,18 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
             for (int e = tid; e < j * (m + 1); e += blockDim.x) hsm[e] = Huc[e];
             __syncthreads();
             for (int i = tid; i <= j; i += blockDim.x) {
-                double hs = 0.0;
+                T hs = 0;
                 int q = i > 0 ? i - 1 : 0;
                 for (; q + 8 <= j; q += 8) {
-                    double hv[8];
+                    T hv[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) hv[u] = hsm[(size_t)(q + u) * (m + 1) + i];
+                    for (int u = 0; u < 8; ++u) hv[u] = (T)hsm[(size_t)(q + u) * (m + 1) + i];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) hs = fma(hv[u], red[2 * (q + u)], hs);
+                    for (int u = 0; u < 8; ++u) hs = fma(hv[u], (T)red[2 * (q + u)], hs);
                 }
-                for (; q < j; ++q) hs = fma(hsm[(size_t)q * (m + 1) + i], red[2 * q], hs);
+                for (; q < j; ++q) hs = fma((T)hsm[(size_t)q * (m + 1) + i], (T)red[2 * q], hs);
                 const double cz = i < j ? red[2 * i + 1] : d;
-                hpc[i] = (cz - hs) / al;
+                hpc[i] = (cz - (double)hs) / al;
             }
             for (int i = tid; i < j; i += blockDim.x) {
                 G.sco[(size_t)c * (m + 1) + i] = red[2 * i];
@@ -2116,7 +2124,8 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
     }
     {
         ProfScope ps(PROF_GM_STEP, st);
-        k_dc_step<<<SAI_GRID(k * STEP_RB), STEP_THREADS, step_smem(G.m), st>>>(k, I.nch, pt, cap, S, G, D, tiny, fl);
+        k_dc_step<T><<<SAI_GRID(k * STEP_RB), STEP_THREADS, step_smem(G.m), st>>>(k, I.nch, pt, cap, S, G, D, tiny,
+                                                                              fl);
     }
     {
         ProfScope ps(D.site_upd, st);
@@ -2146,7 +2155,7 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
     // static shared memory counts against the same per-block limit)
     const size_t tri_smem = sizeof(double) * ((size_t)m * (m + 1) + m);
     SAI_CUDA(cudaFuncSetAttribute(k_dc_trisolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
-    SAI_CUDA(cudaFuncSetAttribute(k_dc_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem(m)));
+    SAI_CUDA(cudaFuncSetAttribute(k_dc_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem(m)));
     int hflag = 0;
     T* r = Wk.r;
     T* w = Wk.w;

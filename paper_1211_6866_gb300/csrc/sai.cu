@@ -86,6 +86,12 @@ struct Out {
     double* res;       // [n]
     double* res_post;  // [n] (PSAI)
     int32_t* tier;     // [n] tier that finished the column
+    // the large-pattern tier writes its columns to slots of its own (the
+    // column's index in that tier's work list): big_slot[k] >= 0 marks them
+    int32_t big_smax;  // slots per large column (0: not the large tier)
+    int32_t* big_slot; // [n], -1 for the other columns
+    int32_t* big_rows; // [work list length * big_smax]
+    double* big_vals;
 };
 
 constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -124,11 +130,13 @@ using Tier0 = Tier<64, 16, 128, 512>;      // shared memory, ~13.7 KB per warp
 using Tier1 = Tier<256, 64, 512, 2048>;    // global memory, ~150 KB per warp
 using Tier2 = Tier<1024, 128, 2048, 8192>; // global memory, ~1.1 MB per warp
 using Tier3 = Tier<2048, 128, 4096, 65536>; // global memory, ~2.4 MB per warp (up to 32768 candidates)
+using Tier4 = Tier<4096, 2048, 8192, 65536>; // global memory, ~68 MB per warp: the large-pattern tier
 using TierSF = Tier<32, 8, 64, 128, float>;
 using Tier0F = Tier<64, 16, 128, 512, float>;
 using Tier1F = Tier<256, 64, 512, 2048, float>;
 using Tier2F = Tier<1024, 128, 2048, 8192, float>;
 using Tier3F = Tier<2048, 128, 4096, 65536, float>;
+using Tier4F = Tier<4096, 2048, 8192, 65536, float>;
 
 // The lanes that work on one column: a group of G consecutive lanes of a
 // warp (G = 32: the whole warp). Every reduction, vote and barrier below is
@@ -895,15 +903,18 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
             long long cfl = 0, cfq = 0;
             int st = PSAI ? psai_column<T, G>(w, A, k, pa, nS, l, rn, rpost, nL, cfl, cfq)
                           : spai_column<T, G>(w, A, k, sa, nS, l, rn, nL, cfl, cfq);
+            const bool big = out.big_smax > 0;
             if (st == ST_DONE) {
-                if (nS > out.smax) st = ST_OVERFLOW;
+                if (nS > (big ? out.big_smax : out.smax)) st = ST_OVERFLOW;
             }
             if (st == ST_DONE) {
-                const size_t o = (size_t)k * out.smax;
+                int32_t* orow = big ? out.big_rows + (size_t)item * out.big_smax : out.rows + (size_t)k * out.smax;
+                double* oval = big ? out.big_vals + (size_t)item * out.big_smax : out.vals + (size_t)k * out.smax;
                 for (int t = g.l; t < nS; t += G) {
-                    out.rows[o + t] = w.S[t];
-                    out.vals[o + t] = w.m[t];
+                    orow[t] = w.S[t];
+                    oval[t] = w.m[t];
                 }
+                if (big && g.l == 0) out.big_slot[k] = item;
                 double cb = 0.0;
                 for (int t = g.l; t < nS; t += G) cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
                 for (int t = g.l; t < nL; t += G) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
@@ -940,21 +951,25 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
     }
 }
 
-// One warp per column: rank-sort the column's slots by row into CSC.
+// One warp per column: rank-sort the column's slots by row into CSC (the
+// large tier's columns from their own slots).
 __global__ void k_assemble(int32_t n, int32_t smax, const int32_t* cnt, const int32_t* rows, const double* vals,
-                           const int64_t* cp, int32_t* ri, double* v)
+                           const int64_t* cp, int32_t* ri, double* v, const int32_t* big_slot, int32_t big_smax,
+                           const int32_t* big_rows, const double* big_vals)
 {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= n) return;
     const int c = cnt[k];
-    const size_t o = (size_t)k * smax;
+    const int bs = big_slot ? big_slot[k] : -1;
+    const int32_t* rk = bs >= 0 ? big_rows + (size_t)bs * big_smax : rows + (size_t)k * smax;
+    const double* vk = bs >= 0 ? big_vals + (size_t)bs * big_smax : vals + (size_t)k * smax;
     for (int t = lane; t < c; t += 32) {
-        const int32_t r = rows[o + t];
+        const int32_t r = rk[t];
         int rank = 0;
-        for (int u = 0; u < c; ++u) rank += rows[o + u] < r;
+        for (int u = 0; u < c; ++u) rank += rk[u] < r;
         ri[cp[k] + rank] = r;
-        v[cp[k] + rank] = vals[o + t];
+        v[cp[k] + rank] = vk[t];
     }
 }
 
@@ -977,14 +992,14 @@ __global__ void k_stats(int32_t n, const int32_t* loops, const double* res, doub
 // columns not built in this call (outside a column list) hold tier -1
 __global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
 {
-    int c[5] = {0, 0, 0, 0, 0};
+    int c[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int t = tier[k];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) c[q] += t == q;
+        for (int q = 0; q < 6; ++q) c[q] += t == q;
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 6; ++q) {
         const int w = warp_sum_int(c[q]);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(&out[2 + q], w);
     }
@@ -1039,6 +1054,39 @@ sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, 
     return SAI_OK;
 }
 
+// The large-pattern tier: one warp per column and per block, as many as
+// the list needs up to one per SM, fewer when their workspaces (~68 MB
+// each in FP64) would take more than a quarter of the free device memory
+// (16 GB at most); the columns write to slots of their own.
+template <class T, bool PSAI>
+sai_status launch_big(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, const int32_t* work, int32_t nwork,
+                      int* next, Out out, int* err, cudaStream_t st, Buf& big_rows, Buf& big_vals)
+{
+    if (nwork <= 0) return SAI_OK;
+    size_t fr = 0, tot = 0;
+    SAI_CUDA(cudaMemGetInfo(&fr, &tot));
+    size_t budget = fr / 4;
+    if (budget > (size_t(16) << 30)) budget = size_t(16) << 30;
+    int64_t warps = nwork < g_num_sms ? nwork : g_num_sms;
+    const int64_t fit = (int64_t)(budget / T::STRIDE);
+    if (warps > fit) warps = fit > 0 ? fit : 1;
+    Buf scratch;
+    SAI_TRY(scratch.alloc(T::STRIDE * (size_t)warps, st, true));
+    SAI_TRY(big_rows.alloc(sizeof(int32_t) * (size_t)nwork * T::SCAP, st, true));
+    SAI_TRY(big_vals.alloc(sizeof(double) * (size_t)nwork * T::SCAP, st, true));
+    out.big_smax = T::SCAP;
+    out.big_rows = big_rows.as<int32_t>();
+    out.big_vals = big_vals.as<double>();
+    SAI_CUDA(cudaMemsetAsync(next, 0, sizeof(int), st));
+    {
+        ProfScope ps(PROF_SAI_BUILD, st);
+        k_sai<T, 32, false, PSAI><<<SAI_GRID(warps), 32, 0, st>>>(A, sa, pa, work, nwork, next, scratch.as<char>(), out,
+                                                                  nullptr, nullptr, err, 5);
+    }
+    SAI_CUDA(cudaGetLastError());
+    return SAI_OK;
+}
+
 template <class TQ>
 struct Tiers;
 template <>
@@ -1048,6 +1096,7 @@ struct Tiers<double> {
     using T1 = Tier1;
     using T2 = Tier2;
     using T3 = Tier3;
+    using T4 = Tier4;
 };
 template <>
 struct Tiers<float> {
@@ -1056,6 +1105,7 @@ struct Tiers<float> {
     using T1 = Tier1F;
     using T2 = Tier2F;
     using T3 = Tier3F;
+    using T4 = Tier4F;
 };
 
 // Build configuration: the warps per block of the shared-memory tiers, the
@@ -1131,7 +1181,8 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
         SAI_CUDA(cudaGetLastError());
     }
     A.icn = icn.as<double>();
-    Buf cnt, rows, vals, tier, ctr, ovf0, ovf1, ovfs;
+    Buf cnt, rows, vals, tier, ctr, ovf0, ovf1, ovfs, bslot, brows, bvals;
+    bool big_used = false;
     SAI_TRY(cnt.alloc(sizeof(int32_t) * nn, st, true));
     SAI_TRY(rows.alloc(sizeof(int32_t) * nn * smax, st, true));
     SAI_TRY(vals.alloc(sizeof(double) * nn * smax, st, true));
@@ -1150,8 +1201,8 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     SAI_CUDA(cudaMemsetAsync(tier.p, 0xff, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->loops.p, 0, sizeof(int32_t) * nn, st));
     SAI_CUDA(cudaMemsetAsync(P->res.p, 0, sizeof(double) * nn, st));
-    // [0] next, [1..2] ovf counts t0, t1, [3] err, [4..10] stats, [11] ovf count t2, [12] ovf count of
-    // the small tier
+    // [0] next, [1..2] ovf counts t0, t1, [3] err, [4..11] stats (n_c, l_m, columns per tier), [12] ovf
+    // count t2, [13] ovf count of the small tier, [14] ovf count t3
     int* c = ctr.as<int>();
     Out out;
     out.smax = smax;
@@ -1162,12 +1213,18 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     out.res = P->res.as<double>();
     out.res_post = PSAI ? P->res_post.as<double>() : nullptr;
     out.tier = tier.as<int32_t>();
+    SAI_TRY(bslot.alloc(sizeof(int32_t) * nn, st, true));
+    out.big_smax = 0;
+    out.big_slot = bslot.as<int32_t>();
+    out.big_rows = nullptr;
+    out.big_vals = nullptr;
 
     using TS = typename Tiers<TQ>::TS;
     using T0 = typename Tiers<TQ>::T0;
     using T1 = typename Tiers<TQ>::T1;
     using T2 = typename Tiers<TQ>::T2;
     using T3 = typename Tiers<TQ>::T3;
+    using T4 = typename Tiers<TQ>::T4;
     // tier-0 work queue: all columns (or the given list), optionally heavy ones first
     const int32_t nq = cols ? ncols : n;
     const int32_t* queue = cols;
@@ -1190,12 +1247,12 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     int32_t n0 = nq;
     if (cfg.first_tier != 0) {
         if (cfg.first_tier == 1)
-            SAI_TRY((launch_tier<TS, 8, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 12,
+            SAI_TRY((launch_tier<TS, 8, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 13,
                                                     c + 3, 4, cfg, st)));
         else
-            SAI_TRY((launch_tier<TS, 16, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 12,
+            SAI_TRY((launch_tier<TS, 16, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 13,
                                                      c + 3, 4, cfg, st)));
-        SAI_CUDA(cudaMemcpyAsync(&n0, c + 12, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SAI_CUDA(cudaMemcpyAsync(&n0, c + 13, sizeof(int), cudaMemcpyDeviceToHost, st));
         SAI_CUDA(cudaStreamSynchronize(st));
         q0 = ovfs.as<int32_t>();
     }
@@ -1212,13 +1269,24 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
         if (hc[2] > 0) {
             // tier 2 queues its overflows in ovf0 (tier 1's input, no longer read)
             SAI_TRY((launch_tier<T2, 32, false, PSAI>(A, sa, pa, ovf1.as<int32_t>(), hc[2], c + 0, out,
-                                                         ovf0.as<int32_t>(), c + 11, c + 3, 2, cfg, st)));
+                                                         ovf0.as<int32_t>(), c + 12, c + 3, 2, cfg, st)));
             int h3 = 0;
-            SAI_CUDA(cudaMemcpyAsync(&h3, c + 11, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SAI_CUDA(cudaMemcpyAsync(&h3, c + 12, sizeof(int), cudaMemcpyDeviceToHost, st));
             SAI_CUDA(cudaStreamSynchronize(st));
-            if (h3 > 0)
-                SAI_TRY((launch_tier<T3, 32, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), h3, c + 0, out, nullptr,
-                                                             nullptr, c + 3, 3, cfg, st)));
+            if (h3 > 0) {
+                // tier 3 queues its overflows in ovf1 (tier 2's input, no longer read)
+                SAI_TRY((launch_tier<T3, 32, false, PSAI>(A, sa, pa, ovf0.as<int32_t>(), h3, c + 0, out,
+                                                             ovf1.as<int32_t>(), c + 14, c + 3, 3, cfg, st)));
+                int h4 = 0;
+                SAI_CUDA(cudaMemcpyAsync(&h4, c + 14, sizeof(int), cudaMemcpyDeviceToHost, st));
+                SAI_CUDA(cudaStreamSynchronize(st));
+                if (h4 > 0) {
+                    SAI_CUDA(cudaMemsetAsync(bslot.p, 0xff, sizeof(int32_t) * nn, st));
+                    big_used = true;
+                    SAI_TRY((launch_big<T4, PSAI>(A, sa, pa, ovf1.as<int32_t>(), h4, c + 0, out, c + 3, st, brows,
+                                                  bvals)));
+                }
+            }
         }
     }
     // assemble M (CSC, rows ascending) and its CSR copy
@@ -1234,9 +1302,10 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     SAI_TRY(P->M_ri.alloc(sizeof(int32_t) * (size_t)(nnzM > 0 ? nnzM : 1), st, async));
     SAI_TRY(P->M_v.alloc(sizeof(double) * (size_t)(nnzM > 0 ? nnzM : 1), st, async));
     if (n > 0)
-        k_assemble<<<SAI_GRID(sai_div_up((int64_t)n * 32, 256)), 256, 0, st>>>(n, smax, cnt.as<int32_t>(), rows.as<int32_t>(),
-                                                                     vals.as<double>(), P->M_cp.as<int64_t>(),
-                                                                     P->M_ri.as<int32_t>(), P->M_v.as<double>());
+        k_assemble<<<SAI_GRID(sai_div_up((int64_t)n * 32, 256)), 256, 0, st>>>(
+            n, smax, cnt.as<int32_t>(), rows.as<int32_t>(), vals.as<double>(), P->M_cp.as<int64_t>(),
+            P->M_ri.as<int32_t>(), P->M_v.as<double>(), big_used ? bslot.as<int32_t>() : nullptr, T4::SCAP,
+            big_used ? brows.as<int32_t>() : nullptr, big_used ? bvals.as<double>() : nullptr);
     SAI_CUDA(cudaGetLastError());
     SAI_TRY(sai_csc_to_csr(n, n, nnzM, P->M_cp.as<int64_t>(), P->M_ri.as<int32_t>(), P->M_v.as<double>(), P->Mr_rp,
                            P->Mr_ci, P->Mr_v, st, async));
@@ -1246,12 +1315,12 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
         k_tier_count<<<SAI_GRID(g_num_sms * 2), 256, 0, st>>>(n, tier.as<int32_t>(), c + 4);
     }
     SAI_CUDA(cudaGetLastError());
-    int hs[7];
+    int hs[8];
     SAI_CUDA(cudaMemcpyAsync(hs, c + 4, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SAI_CUDA(cudaStreamSynchronize(st));
     P->n_c = hs[0];
     P->l_m = hs[1];
-    for (int q = 0; q < 5; ++q) P->n_tier[q] = hs[2 + q];
+    for (int q = 0; q < 6; ++q) P->n_tier[q] = hs[2 + q];
     SAI_CUDA(cudaEventElapsedTime(&P->ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -51,7 +51,7 @@ def test_abi_structs_match_the_binding():
     assert [f for f, _ in sai._BatchItem._fields_][-2:] == ["c_rounds", "reserved"]
     assert re.search(r"SAI_BGMRES\s*=\s*4", hdr) and sai.BGMRES == 4 and sai._METHOD["bgmres"] == 4
     # the build schedule: four int32 fields and the measured time; five tier counts
-    assert "int32_t first_tier;" in hdr and "int32_t n_tier[5];" in hdr
+    assert "int32_t first_tier;" in hdr and "int32_t n_tier[6];" in hdr
     assert [f for f, _ in sai._BuildConfig._fields_] == ["warps_t0", "blocks_per_sm_t12", "heavy_first",
                                                          "first_tier", "ms"]
     assert C.sizeof(sai._BuildConfig) == 20 and C.sizeof(sai._BuildTuning) == 20 + 8 + 12 * 20

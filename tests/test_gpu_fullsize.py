@@ -108,3 +108,23 @@ def test_fullsize_refined_build_samples_match_oracle(problem, case, first_tier):
         else:
             Mo = O.psai(At, kw["delta"], kw["tol"], kw["tol_mode"], kw["lmax"], cols=(c0, c1))[0]
         assert_same_pattern_and_values(Md, Mo, rtol=1e-4, cols=range(c0, c1))
+
+
+def test_fullsize_psai_paper_settings_sample_match_oracle(problem):
+    """PSAI with the paper's Table 5 settings at 64^3 (delta 0.1 here, tol_k of
+    eq. (tolk), l_max 10): the whole build runs without a pattern overflow
+    and three column ranges match the oracle (pattern bit for bit, values
+    within 1e-10, loops exact)."""
+    P, At, gold = problem
+    sai = lib()
+    h = sai.split(to_dev(P.A))
+    kw = dict(delta=0.1, tol=0.0, tol_mode=0, lmax=10)
+    Pc = sai.build_psai(h, **kw)
+    Md, loops_d, _, _ = Pc.arrays()
+    Md = to_scipy(Md)
+    loops_d = loops_d.cpu().numpy()
+    assert sum(Pc.n_tier) == P.n
+    for c0, c1 in RANGES:
+        Mo, loops_o, _, _ = O.psai(At, kw["delta"], kw["tol"], kw["tol_mode"], kw["lmax"], cols=(c0, c1))
+        assert_same_pattern_and_values(Md, Mo, cols=range(c0, c1))
+        assert np.array_equal(loops_d[c0:c1], loops_o[c0:c1])

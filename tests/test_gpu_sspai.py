@@ -10,10 +10,11 @@ directly. On the 2D workload (n = 2025, three columns with ~30% nonzeros):
    depends on the rounding order here), x within 1e-6, rr < eps, and
    about twice the iterations of the split method on the same system (the
    point of the split);
- - S-PSAI: the power pattern of a column of A spreads through the dense
-   columns to most of the matrix (the oracle's |S| reaches 1653 of 2025 at
-   l_max = 2), beyond the 128-entry column workspace, and the build returns
-   SAI_PATTERN_OVERFLOW.
+ - S-PSAI: the power pattern of a dense column spreads to most of the
+   matrix (the oracle's |S| reaches 2023 of 2025 with Table 5's settings),
+   beyond the 128-entry global-memory tiers: those columns finish in the
+   large-pattern tier, and M (FP64 and refined) and BiCGStab with it are
+   compared with the oracle.
 """
 import numpy as np
 import pytest
@@ -73,13 +74,52 @@ def test_sspai_solve_against_oracle_and_split_method(direct):
     assert 1.5 * max(it_split) < iters[0], (it_split, iters)
 
 
-def test_spsai_pattern_outgrows_the_workspace(direct):
+@pytest.fixture(scope="module")
+def spsai_oracle(direct):
+    """The oracle's S-PSAI of A with the settings of the paper's Table 5
+    (delta 0.4, tol_k of eq. (tolk), l_max 10) and with a fixed tolerance
+    1e-3 and l_max 2."""
+    P, At, _ = direct
+    return {"tolk": O.psai(At, 0.4, 0.0, 0, 10), "fixed": O.psai(At, 0.4, 1e-3, 1, 2)}
+
+
+@pytest.mark.parametrize("case", ["tolk", "fixed"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_spsai_builds_large_patterns(direct, spsai_oracle, case, precision):
+    """S-PSAI on A: the three dense columns' patterns spread to most of the
+    matrix (up to 2023 of 2025 entries at the third loop), beyond the
+    128-entry global-memory tiers; they finish in the large-pattern tier
+    (|L| <= 4096, |S| <= 2048) and M matches the oracle's (pattern bit for
+    bit, values within 1e-10 / 1e-4, loops exact)."""
     need_gpu()
     sai = lib()
     P, At, _ = direct
-    Mp = sp.csc_matrix(O.psai(At, 0.4, 1e-3, 1, 2)[0])
-    assert np.diff(Mp.indptr).max() > 128  # the oracle's pattern passes the workspace
+    Mo, loops_o, pre_o, post_o = spsai_oracle[case]
+    Mo = sp.csc_matrix(Mo)
+    assert np.diff(Mo.indptr).max() > 1000  # the oracle's pattern passes the 128-entry tiers
     sp_ = sai.split(to_dev(P.A), abs_tau=INF)
-    with pytest.raises(sai.SaiError) as e:
-        sai.build_psai(sp_, delta=0.4, tol=1e-3, tol_mode=1, lmax=2)
-    assert e.value.status == sai.SAI_PATTERN_OVERFLOW
+    kw = dict(delta=0.4, tol=0.0, tol_mode=0, lmax=10) if case == "tolk" else \
+        dict(delta=0.4, tol=1e-3, tol_mode=1, lmax=2)
+    Pc = sai.build_psai(sp_, precision=precision, **kw)
+    Md, loops_d, res_d, post_d = Pc.arrays()
+    assert_same_pattern_and_values(to_scipy(Md), Mo, rtol=1e-10 if precision == 0 else 1e-4)
+    assert np.array_equal(loops_d.cpu().numpy(), loops_o)
+    assert Pc.n_tier[5] == int((np.diff(Mo.indptr) > 128).sum()) > 0, Pc.n_tier
+    assert sum(Pc.n_tier) == P.n
+
+
+def test_spsai_solve_against_oracle(direct, spsai_oracle):
+    """BiCGStab with the S-PSAI preconditioner of Table 5's settings: the
+    oracle's iteration count within 5% (rounding-order dependent, as for
+    S-SPAI), x within 1e-6, rr < eps."""
+    need_gpu()
+    sai = lib()
+    P, At, _ = direct
+    Mo = sp.csc_matrix(spsai_oracle["tolk"][0])
+    x, iters, rep = sai.solve(to_dev(P.A), _dev(P.b), sai="psai", krylov="bicgstab", eps=1e-8, abs_tau=INF,
+                              delta=0.4, tol_mode=0, lmax=10)
+    yo, it_o, st_o = O.bicgstab(At, Mo, P.b, 0.5e-8 * np.linalg.norm(P.b))
+    assert rep["s"] == 0 and rep["status"] == sai.SAI_OK and st_o == O.OK
+    assert abs(iters[0] - it_o) <= max(1, 0.05 * it_o), (iters, it_o)
+    assert rep["rr"] < 1e-8
+    np.testing.assert_allclose(x.cpu().numpy(), yo, rtol=0, atol=1e-6)
