@@ -201,13 +201,14 @@ typedef struct sai_precond_s* sai_precond;
  * queue; first_tier: the workspace every column starts in -- 0: tier 0 (|L|
  * <= 64 rows, |S| <= 16 columns, one column per warp), 1: the small tier
  * (|L| <= 32, |S| <= 8) with four columns per warp (8-lane groups), 2: the
- * small tier with two columns per warp (16-lane groups); a column that
- * outgrows its tier restarts in the next one. ms: the sampled build time
+ * small tier with two columns per warp (16-lane groups), 3: the small tier
+ * with one column per lane (32 per warp, each lane running its column's
+ * steps alone); a column that outgrows its tier restarts in the next one. ms: the sampled build time
  * measured by sai_build_autotune (0 otherwise). Default {8, 2, 0, 0}.
  * warps_t0, blocks_per_sm_t12 and heavy_first never change M. first_tier
  * sets how many lanes sum each reduction of the columns the small tier
  * finishes, so M's values can differ in the last bits between first_tier 0
- * and 1 or 2 (the same first_tier always gives the same bits). */
+ * and 1, 2 or 3 (the same first_tier always gives the same bits). */
 typedef struct {
     int32_t warps_t0;
     int32_t blocks_per_sm_t12;
@@ -246,9 +247,9 @@ sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info);
  * psai params), and makes the fastest the process-wide configuration of
  * later builds. The search takes one coordinate at a time: first_tier (the
  * workspace shape and columns per warp of the first tier) x warps_t0 with
- * {blocks_per_sm_t12 2, heavy_first 0}, then heavy_first 1 on the best of
- * those, then blocks_per_sm_t12 1 and 4 on the best so far (nine
- * candidates). out (host) receives the candidates and the choice.
+ * {blocks_per_sm_t12 2, heavy_first 0} (first_tier 3 with warps_t0 8 only),
+ * then heavy_first 1 on the best of those, then blocks_per_sm_t12 1 and 4
+ * on the best so far (ten candidates). out (host) receives the candidates and the choice.
  * Synchronises the stream. */
 sai_status sai_build_autotune(sai_split h, int32_t sai, const sai_spai_params* spai, const sai_psai_params* psai,
                               sai_stream_t stream, sai_build_tuning* out);

@@ -327,7 +327,8 @@ def build_autotune(sp, sai="spai", delta=0.4, mn=5, max_aug=10, key_bits=20, tol
 def build_set_config(warps_t0=None, blocks_per_sm_t12=2, heavy_first=0, first_tier=0):
     """Sets the build schedule (warps_t0=None restores the default).
     first_tier: 0 starts every column in tier 0 (one column per warp), 1 in
-    the small shared-memory tier with four columns per warp, 2 with two."""
+    the small shared-memory tier with four columns per warp, 2 with two, 3
+    with one column per lane (32 per warp)."""
     L = load()
     if warps_t0 is None:
         _check("sai_build_set_config", L.sai_build_set_config(None))

@@ -1546,7 +1546,12 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __r
     const int ng = j > 0 ? (j + PD - 1) / PD : 1;  // groups of PD basis vectors
     const int cnt = list[0];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t it = blockIdx.x; it < (int64_t)cnt * I.nch * ng; it += gridDim.x) {
+    // each block takes a contiguous range of items: the groups of one
+    // (chunk, system) follow one another and read u and z from cache
+    const int64_t total = (int64_t)cnt * I.nch * ng;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t it_end = min(total, ((int64_t)blockIdx.x + 1) * per);
+    for (int64_t it = (int64_t)blockIdx.x * per; it < it_end; ++it) {
         const int g = (int)(it % ng);
         const int64_t rest = it / ng;
         const int c = list[1 + (int)(rest % cnt)];
@@ -1827,7 +1832,10 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
 }
 
 // v_j = (u - V s)/alpha and u <- (z - V c - d v_j)/alpha for the systems of
-// list; one pass over the rows, PJ basis vectors per register tile.
+// list; one pass over the rows, PJ basis vectors per register tile. Items
+// (system, chunk of CHUNK_U rows) run system-major, each warp over a
+// contiguous range of them: a warp streams consecutive rows of one system
+// and loads its coefficients again only when the system changes.
 template <class T>
 __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_update(Items I, T* __restrict__ u, const T* __restrict__ z,
                                                             Basis<T> Bv, Gm G, const int* list, const int* jdev)
@@ -1841,16 +1849,26 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_update(Items I, T* __restr
     const int m1 = G.m + 1;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = w0; it < (int64_t)cnt * I.nchu; it += nw) {
-        const int c = list[1 + (int)(it % cnt)];
-        const int q = (int)(it / cnt);
-        for (int i = lane; i < j; i += 32) {
-            hs[wid][i] = (T)G.sco[(size_t)c * m1 + i];
-            hc[wid][i] = (T)G.cco[(size_t)c * m1 + i];
+    const int64_t total = (int64_t)cnt * I.nchu;
+    const int64_t per = (total + nw - 1) / nw;
+    const int64_t it_end = min(total, (w0 + 1) * per);
+    int cur = -1, c = 0;
+    T ia = 0, dd = 0;
+    for (int64_t it = w0 * per; it < it_end; ++it) {
+        const int ci = (int)(it / I.nchu);
+        const int q = (int)(it - (int64_t)ci * I.nchu);
+        if (ci != cur) {
+            __syncwarp();
+            cur = ci;
+            c = list[1 + ci];
+            for (int i = lane; i < j; i += 32) {
+                hs[wid][i] = (T)G.sco[(size_t)c * m1 + i];
+                hc[wid][i] = (T)G.cco[(size_t)c * m1 + i];
+            }
+            ia = (T)(1.0 / G.alpha[c]);
+            dd = (T)G.dco[c];
+            __syncwarp();
         }
-        const T ia = (T)(1.0 / G.alpha[c]);
-        const T dd = (T)G.dco[c];
-        __syncwarp();
         const int64_t r0 = (int64_t)q * CHUNK_U, r1 = min((int64_t)I.n, r0 + CHUNK_U);
         const int64_t o = (int64_t)c * I.ld;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
@@ -1879,7 +1897,6 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_update(Items I, T* __restr
             *reinterpret_cast<VT*>(Vj + row) = v;
             *reinterpret_cast<VT*>(u + o + row) = un;
         }
-        __syncwarp();
     }
 }
 

@@ -869,6 +869,604 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
     }
 }
 
+// ---------------------------------------------------------------- lane tier
+// The small tier with one lane per column: a warp builds 32 columns at once,
+// each lane running its column's steps (the same steps as above) one after
+// another, so a warp instruction serves 32 columns and no step needs a
+// reduction across lanes. Each lane's workspace (|L| <= LT_L rows, |S| <=
+// LT_S columns, the row and candidate hash tables) lives in shared memory,
+// interleaved across the warp's lanes: element e of a lane's array sits at
+// word e * 32 + lane, so the 32 lanes touch 32 different banks. A column
+// that outgrows it is queued for tier 0, like the columns of the group form
+// of the small tier.
+constexpr int LT_L = 32, LT_S = 8, LT_HL = 64, LT_HC = 64;
+
+// A lane's view of an array interleaved across the warp: element e at p[32 e].
+template <class V>
+struct LA {
+    V* p;
+    __device__ __forceinline__ V& operator[](int e) const { return p[(size_t)e * 32]; }
+};
+
+template <class TQ>
+struct LaneLayout {
+    // per-lane sizes in bytes of each array; each region holds 32 lanes
+    static constexpr size_t Q = sizeof(TQ) * LT_L * LT_S, CV = sizeof(TQ) * LT_L, R = 8ull * LT_L, M = 8ull * LT_S,
+                            G = 8ull * LT_S, BETA = sizeof(TQ) * LT_S, RD = sizeof(TQ) * LT_S, LROW = 4ull * LT_L,
+                            HK = 4ull * LT_HL, HV = 1ull * LT_HL, S = 4ull * LT_S, A0 = 4ull * LT_S, A1 = 4ull * LT_S,
+                            CK = 4ull * LT_HC, CF = 1ull * LT_HC, KP = 4ull * LT_S;
+    static constexpr size_t OFF_Q = 0, OFF_CV = OFF_Q + 32 * Q, OFF_R = OFF_CV + 32 * CV, OFF_M = OFF_R + 32 * R,
+                            OFF_G = OFF_M + 32 * M, OFF_BETA = OFF_G + 32 * G, OFF_RD = OFF_BETA + 32 * BETA,
+                            OFF_LROW = OFF_RD + 32 * RD, OFF_HK = OFF_LROW + 32 * LROW, OFF_HV = OFF_HK + 32 * HK,
+                            OFF_S = OFF_HV + 32 * HV, OFF_A0 = OFF_S + 32 * S, OFF_A1 = OFF_A0 + 32 * A0,
+                            OFF_CK = OFF_A1 + 32 * A1, OFF_CF = OFF_CK + 32 * CK, OFF_KP = OFF_CF + 32 * CF;
+    static constexpr size_t WARP_BYTES = OFF_KP + 32 * KP;  // one warp's 32 workspaces
+};
+
+template <class TQ>
+struct LWs {
+    LA<TQ> Q, cv, beta, rd;
+    LA<double> r, m, g;
+    LA<int32_t> Lrow, hk, S, a0, a1, ck;
+    LA<uint8_t> hv, cf;  // row positions (< 32), candidate flags
+    LA<int32_t> kp;
+};
+
+template <class TQ>
+__device__ __forceinline__ LWs<TQ> bind_lane(char* wbase, int lane)
+{
+    using Lo = LaneLayout<TQ>;
+    LWs<TQ> w;
+    w.Q.p = (TQ*)(wbase + Lo::OFF_Q) + lane;
+    w.cv.p = (TQ*)(wbase + Lo::OFF_CV) + lane;
+    w.r.p = (double*)(wbase + Lo::OFF_R) + lane;
+    w.m.p = (double*)(wbase + Lo::OFF_M) + lane;
+    w.g.p = (double*)(wbase + Lo::OFF_G) + lane;
+    w.beta.p = (TQ*)(wbase + Lo::OFF_BETA) + lane;
+    w.rd.p = (TQ*)(wbase + Lo::OFF_RD) + lane;
+    w.Lrow.p = (int32_t*)(wbase + Lo::OFF_LROW) + lane;
+    w.hk.p = (int32_t*)(wbase + Lo::OFF_HK) + lane;
+    w.hv.p = (uint8_t*)(wbase + Lo::OFF_HV) + lane;
+    w.S.p = (int32_t*)(wbase + Lo::OFF_S) + lane;
+    w.a0.p = (int32_t*)(wbase + Lo::OFF_A0) + lane;
+    w.a1.p = (int32_t*)(wbase + Lo::OFF_A1) + lane;
+    w.ck.p = (int32_t*)(wbase + Lo::OFF_CK) + lane;
+    w.cf.p = (uint8_t*)(wbase + Lo::OFF_CF) + lane;
+    w.kp.p = (int32_t*)(wbase + Lo::OFF_KP) + lane;
+    return w;
+}
+
+// open-addressing tables of one lane (keys -1 = empty)
+template <int H>
+__device__ __forceinline__ int lh_find(const LA<int32_t>& hk, const LA<uint8_t>& hv, int32_t key)
+{
+    uint32_t s = hmix(key) & (H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+        const int32_t k = hk[s];
+        if (k == key) return hv[s];
+        if (k == -1) return -1;
+        s = (s + 1) & (H - 1);
+    }
+    return -1;
+}
+
+// slot of key, inserted if absent (ins set); -1 when the table is full
+template <int H>
+__device__ __forceinline__ int lh_insert(const LA<int32_t>& hk, int32_t key, bool& ins)
+{
+    uint32_t s = hmix(key) & (H - 1);
+    ins = false;
+    for (int probe = 0; probe < H; ++probe) {
+        const int32_t k = hk[s];
+        if (k == key) return (int)s;
+        if (k == -1) {
+            hk[s] = key;
+            ins = true;
+            return (int)s;
+        }
+        s = (s + 1) & (H - 1);
+    }
+    return -1;
+}
+
+template <int H>
+__device__ __forceinline__ int lh_slot(const LA<int32_t>& hk, int32_t key)
+{
+    uint32_t s = hmix(key) & (H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+        const int32_t k = hk[s];
+        if (k == key) return (int)s;
+        if (k == -1) return -1;
+        s = (s + 1) & (H - 1);
+    }
+    return -1;
+}
+
+template <class TQ>
+__device__ void lane_init(const LWs<TQ>& w, int32_t k, int& nL, int& nS, int& nfact)
+{
+    for (int q = 0; q < LT_HL; ++q) w.hk[q] = -1;
+    bool ins;
+    const int sl = lh_insert<LT_HL>(w.hk, k, ins);
+    w.hv[sl] = 0;
+    w.Lrow[0] = k;
+    w.cv[0] = 1;
+    nL = 1;
+    nS = 1;
+    nfact = 0;
+}
+
+// rows of column j of A~ into L, new rows at consecutive positions in entry order
+template <class TQ>
+__device__ bool lane_add_rows(const LWs<TQ>& w, const SaiMat& A, int32_t j, int& nL)
+{
+    for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+        const int32_t i = A.ri[q];
+        bool ins;
+        const int sl = lh_insert<LT_HL>(w.hk, i, ins);
+        if (sl < 0) return false;
+        if (ins) {
+            if (nL >= LT_L) return false;
+            w.hv[sl] = (uint8_t)nL;
+            w.Lrow[nL] = i;
+            ++nL;
+        }
+    }
+    return true;
+}
+
+// the steps of ls_update for one lane: gather the new columns, old
+// reflectors on them, Householder factorisation of the trailing block,
+// back substitution
+template <class TQ>
+__device__ int lane_ls_update(const LWs<TQ>& w, const SaiMat& A, int& nL, int nS, int& nfact)
+{
+    const int nL_old = nL;
+    for (int t = nfact; t < nS; ++t)
+        if (!lane_add_rows(w, A, w.S[t], nL)) return ST_OVERFLOW;
+    for (int t = 0; t < nS; ++t)
+        for (int i = t < nfact ? nL_old : 0; i < nL; ++i) w.Q[t * LT_L + i] = 0;
+    for (int i = nL_old; i < nL; ++i) w.cv[i] = 0;
+    for (int t = nfact; t < nS; ++t) {
+        const int32_t j = w.S[t];
+        for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+            const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
+            if (pos >= 0) w.Q[t * LT_L + pos] = (TQ)A.cv[q];
+        }
+    }
+    for (int jr = 0; jr < nfact; ++jr) {
+        const TQ bj = w.beta[jr];
+        for (int t = nfact; t < nS; ++t) {
+            TQ d = 0;
+            for (int i = jr; i < nL; ++i) d = fma(w.Q[jr * LT_L + i], w.Q[t * LT_L + i], d);
+            const TQ f = bj * d;
+            for (int i = jr; i < nL; ++i) w.Q[t * LT_L + i] = fma(-f, w.Q[jr * LT_L + i], w.Q[t * LT_L + i]);
+        }
+    }
+    for (int t = nfact; t < nS; ++t) {
+        TQ s2 = 0;
+        for (int i = t; i < nL; ++i) s2 = fma(w.Q[t * LT_L + i], w.Q[t * LT_L + i], s2);
+        if (!(s2 > (TQ)0)) return ST_SINGULAR;
+        const TQ nrm = sqrt(s2);
+        const TQ x0 = w.Q[t * LT_L + t];
+        const TQ alpha = x0 >= (TQ)0 ? -nrm : nrm;
+        const TQ bt = (TQ)1 / (nrm * (nrm + fabs(x0)));
+        w.Q[t * LT_L + t] = x0 - alpha;
+        w.rd[t] = alpha;
+        w.beta[t] = bt;
+        for (int t2 = t + 1; t2 <= nS; ++t2) {
+            TQ d = 0;
+            if (t2 < nS) {
+                for (int i = t; i < nL; ++i) d = fma(w.Q[t * LT_L + i], w.Q[t2 * LT_L + i], d);
+                const TQ f = bt * d;
+                for (int i = t; i < nL; ++i) w.Q[t2 * LT_L + i] = fma(-f, w.Q[t * LT_L + i], w.Q[t2 * LT_L + i]);
+            } else {
+                for (int i = t; i < nL; ++i) d = fma(w.Q[t * LT_L + i], w.cv[i], d);
+                const TQ f = bt * d;
+                for (int i = t; i < nL; ++i) w.cv[i] = fma(-f, w.Q[t * LT_L + i], w.cv[i]);
+            }
+        }
+    }
+    nfact = nS;
+    for (int i = 0; i < nS; ++i) w.m[i] = (double)w.cv[i];
+    for (int t = nS - 1; t >= 0; --t) {
+        const double mt = w.m[t] / (double)w.rd[t];
+        w.m[t] = mt;
+        for (int i = 0; i < t; ++i) w.m[i] = fma(-(double)w.Q[t * LT_L + i], mt, w.m[i]);
+    }
+    return ST_DONE;
+}
+
+template <class TQ>
+__device__ double lane_residual(const LWs<TQ>& w, const SaiMat& A, int nL, int nS, bool use_kp)
+{
+    for (int i = 0; i < nL; ++i) w.r[i] = i == 0 ? -1.0 : 0.0;
+    for (int t = 0; t < nS; ++t) {
+        if (use_kp && !w.kp[t]) continue;
+        const int32_t j = w.S[t];
+        const double mt = w.m[t];
+        for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+            const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
+            if (pos >= 0) w.r[pos] = fma(A.cv[q], mt, w.r[pos]);
+        }
+    }
+    double s = 0.0;
+    for (int i = 0; i < nL; ++i) s = fma(w.r[i], w.r[i], s);
+    return s;
+}
+
+template <class TQ>
+__device__ void lane_refine(const LWs<TQ>& w, const SaiMat& A, int nL, int nS)
+{
+    lane_residual(w, A, nL, nS, false);
+    for (int t = 0; t < nS; ++t) {
+        const int32_t j = w.S[t];
+        double gt = 0.0;
+        for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+            const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
+            if (pos >= 0) gt = fma(-A.cv[q], w.r[pos], gt);
+        }
+        w.g[t] = gt;
+    }
+    for (int t = 0; t < nS; ++t) {
+        const double yt = w.g[t] / (double)w.rd[t];
+        w.g[t] = yt;
+        for (int i = t + 1; i < nS; ++i) w.g[i] = fma(-(double)w.Q[i * LT_L + t], yt, w.g[i]);
+    }
+    for (int t = nS - 1; t >= 0; --t) {
+        const double dt = w.g[t] / (double)w.rd[t];
+        w.g[t] = dt;
+        for (int i = 0; i < t; ++i) w.g[i] = fma(-(double)w.Q[t * LT_L + i], dt, w.g[i]);
+    }
+    for (int t = 0; t < nS; ++t) w.m[t] += w.g[t];
+}
+
+template <class TQ>
+__device__ int lane_nnz(const LWs<TQ>& w, const SaiMat& A, int nS)
+{
+    int c = 0;
+    for (int t = 0; t < nS; ++t) c += (int)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]);
+    return c;
+}
+
+template <class TQ>
+__device__ int lane_spai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const SpaiArgs& a, int& nS_out, int& l_out,
+                         double& rn_out, int& nL_out, long long& fl, long long& fq)
+{
+    int nL, nS, nfact;
+    lane_init(w, k, nL, nS, nfact);
+    w.S[0] = k;
+    int l = 0;
+    double rn = 0.0;
+    fl = 0;
+    fq = 0;
+    for (;;) {
+        const int c0 = nfact;
+        const int st = lane_ls_update(w, A, nL, nS, nfact);
+        if (st != ST_DONE) return st;
+        const long long sn = lane_nnz(w, A, nS);
+        fq += qr_flops(nL, c0, nS);
+        if (sizeof(TQ) < sizeof(double)) {
+            lane_refine(w, A, nL, nS);
+            fl += 4 * sn + 2LL * nL + 2LL * nS * nS;
+        }
+        const double rn2 = lane_residual(w, A, nL, nS, false);
+        fl += 2 * sn + 2LL * nL;
+        rn = sqrt(rn2);
+        if (rn <= a.delta || l >= a.max_aug) break;
+        // candidates N \ S from the rows of L (cf = 1 marks members of S)
+        for (int q = 0; q < LT_HC; ++q) {
+            w.ck[q] = -1;
+            w.cf[q] = 0;
+        }
+        for (int t = 0; t < nS; ++t) {
+            bool ins;
+            const int sl = lh_insert<LT_HC>(w.ck, w.S[t], ins);
+            if (sl < 0) return ST_OVERFLOW;
+            w.cf[sl] = 1;
+        }
+        int ncand = 0;
+        for (int idx = 0; idx < nL; ++idx) {
+            const int32_t i = w.Lrow[idx];
+            for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+                bool ins;
+                if (lh_insert<LT_HC>(w.ck, A.rc[q], ins) < 0) return ST_OVERFLOW;
+                ncand += ins;
+            }
+        }
+        if (ncand + nS > LT_HC / 2) return ST_OVERFLOW;
+        // keys of the candidates; the mn smallest in a sorted list
+        unsigned long long top[MNMAX];
+#pragma unroll
+        for (int q = 0; q < MNMAX; ++q) top[q] = ULLONG_MAX;
+        const double irn2 = 1.0 / rn2;
+        for (int sl = 0; sl < LT_HC; ++sl) {
+            const int32_t j = w.ck[sl];
+            if (j < 0 || w.cf[sl]) continue;
+            const double inj = A.icn[j];
+            if (!(inj > 0.0)) continue;
+            fl += 2 * (A.cp[j + 1] - A.cp[j]) + 5;
+            double d = 0.0;
+            for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+                const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
+                if (pos >= 0) d = fma(w.r[pos], A.cv[q], d);
+            }
+            double tq = fma(-(d * d), inj * irn2, 1.0);
+            tq = fmin(fmax(tq, 0.0), 1.0);
+            unsigned long long x = (__double2ull_rz(tq * a.scale) << 32) | (unsigned)j;
+#pragma unroll
+            for (int q = 0; q < MNMAX; ++q) {
+                const unsigned long long lo = top[q] < x ? top[q] : x;
+                x = top[q] < x ? x : top[q];
+                top[q] = lo;
+            }
+        }
+        int added = 0;
+#pragma unroll
+        for (int q = 0; q < MNMAX; ++q) {
+            if (q >= a.mn || top[q] == ULLONG_MAX) break;
+            if (nS + added >= LT_S) return ST_OVERFLOW;
+            w.S[nS + added] = (int32_t)(top[q] & 0xffffffffull);
+            ++added;
+        }
+        if (added == 0) break;
+        nS += added;
+        ++l;
+    }
+    nS_out = nS;
+    l_out = l;
+    rn_out = rn;
+    nL_out = nL;
+    return ST_DONE;
+}
+
+// PSAI(tol) for one lane: reading (A) growth, S^(l+1) = P(a^(l+1)) u S_kept^(l),
+// and reading (C) (growth 1), as psai_column
+template <class TQ>
+__device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const PsaiArgs& a, int& nS_out, int& l_out,
+                         double& rn_pre, double& rn_post, int& nL_out, long long& fl, long long& fq)
+{
+    int nL, nS, nfact;
+    lane_init(w, k, nL, nS, nfact);
+    w.S[0] = k;
+    w.a0[0] = k;
+    int na = 1;
+    bool cur0 = true;  // a^(l) in a0 (else a1)
+    int l = 0;
+    fl = 0;
+    fq = 0;
+    for (;;) {
+        const LA<int32_t> apat = cur0 ? w.a0 : w.a1;
+        const LA<int32_t> anew = cur0 ? w.a1 : w.a0;
+        const int c0 = nfact;
+        const int st = lane_ls_update(w, A, nL, nS, nfact);
+        if (st != ST_DONE) return st;
+        const long long sn = lane_nnz(w, A, nS);
+        fq += qr_flops(nL, c0, nS);
+        if (sizeof(TQ) < sizeof(double)) {
+            lane_refine(w, A, nL, nS);
+            fl += 4 * sn + 2LL * nL + 2LL * nS * nS;
+        }
+        const double rn = sqrt(lane_residual(w, A, nL, nS, false));
+        fl += 2 * sn + 2LL * nL;
+        double tolk = a.tol;
+        if (a.tol_mode == 0) {
+            int nz = 0;
+            for (int t = 0; t < nS; ++t) nz += (w.m[t] != 0.0);
+            tolk = (nz > 0 && A.norm1 > 0.0) ? a.delta / ((double)nz * A.norm1) : 0.0;
+        }
+        if (a.tol_mode == 2) {
+            for (int t = 0; t < nS; ++t) {
+                const double mt = fabs(w.m[t]);
+                const int32_t jt = w.S[t];
+                int rank = 0;
+                for (int u = 0; u < nS; ++u) {
+                    const double mu = fabs(w.m[u]);
+                    rank += (mu > mt) || (mu == mt && w.S[u] < jt);
+                }
+                w.kp[t] = rank < a.lfill;
+            }
+        } else {
+            for (int t = 0; t < nS; ++t) w.kp[t] = fabs(w.m[t]) > tolk;
+        }
+        if (rn <= a.delta || l >= a.lmax) {
+            rn_pre = rn;
+            rn_post = sqrt(lane_residual(w, A, nL, nS, true));
+            fl += 2 * sn + 2LL * nL;
+            int q = 0;
+            for (int t = 0; t < nS; ++t)
+                if (w.kp[t]) {
+                    w.S[q] = w.S[t];
+                    w.m[q] = w.m[t];
+                    ++q;
+                }
+            nS_out = q;
+            l_out = l;
+            nL_out = nL;
+            return ST_DONE;
+        }
+        for (int q = 0; q < LT_HC; ++q) {
+            w.ck[q] = -1;
+            w.cf[q] = 0;
+        }
+        if (a.growth == 1) {
+            // reading (C): flags 2 in P(a^(l)), 8 kept member, 4 in P(a^(l+1))
+            for (int t = 0; t < na; ++t) {
+                bool ins;
+                const int sl = lh_insert<LT_HC>(w.ck, apat[t], ins);
+                if (sl < 0) return ST_OVERFLOW;
+                w.cf[sl] = (uint8_t)(w.cf[sl] | 2);
+            }
+            int nk = 0;
+            for (int t = 0; t < nS; ++t) {
+                if (!w.kp[t]) continue;
+                ++nk;
+                bool ins;
+                const int sl = lh_insert<LT_HC>(w.ck, w.S[t], ins);
+                if (sl < 0) return ST_OVERFLOW;
+                w.cf[sl] = (uint8_t)(w.cf[sl] | 8);
+            }
+            for (int t = 0; t < na; ++t) {
+                const int32_t j = apat[t];
+                for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+                    bool ins;
+                    const int sl = lh_insert<LT_HC>(w.ck, A.ri[q], ins);
+                    if (sl < 0) return ST_OVERFLOW;
+                    w.cf[sl] = (uint8_t)(w.cf[sl] | 4);
+                }
+            }
+            int nb = 0, nf = 0;
+            for (int sl = 0; sl < LT_HC; ++sl) {
+                const int32_t key = w.ck[sl];
+                const int f = key >= 0 ? w.cf[sl] : 0;
+                if (f & 4) {
+                    if (nb >= LT_S) return ST_OVERFLOW;
+                    anew[nb++] = key;
+                    if ((f & 10) == 0) ++nf;
+                }
+            }
+            if (nk + nf == 0) {
+                rn_pre = rn;
+                rn_post = sqrt(lane_residual(w, A, nL, nS, true));
+                fl += 2 * sn + 2LL * nL;
+                nS_out = 0;
+                l_out = l;
+                nL_out = nL;
+                return ST_DONE;
+            }
+            if (nk + nf > LT_S) return ST_OVERFLOW;
+            const bool dropped = nk < nS;
+            if (dropped) {
+                int q = 0;
+                for (int t = 0; t < nS; ++t)
+                    if (w.kp[t]) w.S[q++] = w.S[t];
+            }
+            int q = nk;
+            for (int sl = 0; sl < LT_HC; ++sl) {
+                const int32_t key = w.ck[sl];
+                const int f = key >= 0 ? w.cf[sl] : 0;
+                if ((f & 4) != 0 && (f & 10) == 0) w.S[q++] = key;
+            }
+            if (dropped) lane_init(w, k, nL, nS, nfact);
+            nS = q;
+            na = nb;
+            cur0 = !cur0;
+            ++l;
+            continue;
+        }
+        // a^(l+1): the rows of the columns of a^(l), in entry order
+        int nb = 0;
+        for (int t = 0; t < na; ++t) {
+            const int32_t j = apat[t];
+            for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
+                bool ins;
+                const int32_t i = A.ri[q];
+                const int sl = lh_insert<LT_HC>(w.ck, i, ins);
+                if (sl < 0) return ST_OVERFLOW;
+                if (ins) {
+                    if (nb >= LT_S) return ST_OVERFLOW;
+                    anew[nb++] = i;
+                }
+            }
+        }
+        bool shrink = false;
+        for (int t = 0; t < nS; ++t) {
+            const int sl = lh_slot<LT_HC>(w.ck, w.S[t]);
+            if (sl >= 0) w.cf[sl] = 1;
+            else if (!w.kp[t]) shrink = true;
+        }
+        if (!shrink) {
+            int add = 0;
+            for (int t = 0; t < nb; ++t) {
+                const int32_t j = anew[t];
+                if (w.cf[lh_slot<LT_HC>(w.ck, j)] == 0) {
+                    if (nS + add >= LT_S) return ST_OVERFLOW;
+                    w.S[nS + add] = j;
+                    ++add;
+                }
+            }
+            nS += add;
+        } else {
+            int q2 = nb;
+            for (int t = 0; t < nS; ++t)
+                if (w.kp[t] && lh_slot<LT_HC>(w.ck, w.S[t]) < 0) {
+                    if (q2 >= LT_S) return ST_OVERFLOW;
+                    apat[q2 - nb] = w.S[t];
+                    ++q2;
+                }
+            for (int t = 0; t < q2; ++t) w.S[t] = t < nb ? anew[t] : apat[t - nb];
+            lane_init(w, k, nL, nS, nfact);
+            nS = q2;
+        }
+        na = nb;
+        cur0 = !cur0;
+        ++l;
+    }
+}
+
+// Persistent lane-tier kernel: a warp takes 32 consecutive columns of the
+// queue, one per lane, and takes the next 32 when all of its lanes are done.
+template <class TQ, bool PSAI>
+__global__ void __launch_bounds__(64) k_sai_lane(SaiMat A, SpaiArgs sa, PsaiArgs pa, const int32_t* __restrict__ work,
+                                                  int32_t nwork, int* next, Out out, int32_t* ovf_list, int* ovf_cnt,
+                                                  int* err, int tier_id)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31;
+    char* wbase = smem + (size_t)(threadIdx.x >> 5) * LaneLayout<TQ>::WARP_BYTES;
+    const LWs<TQ> w = bind_lane<TQ>(wbase, lane);
+    double work_bytes = 0.0;
+    long long work_flops = 0, work_flops_q = 0;
+    for (;;) {
+        int first = 0;
+        if (lane == 0) first = atomicAdd(next, 32);
+        first = __shfl_sync(SAI_FULL, first, 0);
+        if (first >= nwork) break;
+        const int item = first + lane;
+        if (item < nwork) {
+            const int32_t k = work ? work[item] : item;
+            int nS = 0, l = 0, nL = 0;
+            double rn = 0.0, rpost = 0.0;
+            long long cfl = 0, cfq = 0;
+            int st = PSAI ? lane_psai(w, A, k, pa, nS, l, rn, rpost, nL, cfl, cfq)
+                          : lane_spai(w, A, k, sa, nS, l, rn, nL, cfl, cfq);
+            if (st == ST_DONE && nS > out.smax) st = ST_OVERFLOW;
+            if (st == ST_DONE) {
+                const size_t o = (size_t)k * out.smax;
+                double cb = 0.0;
+                for (int t = 0; t < nS; ++t) {
+                    out.rows[o + t] = w.S[t];
+                    out.vals[o + t] = w.m[t];
+                    cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
+                }
+                for (int t = 0; t < nL; ++t) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
+                work_bytes += cb;
+                work_flops += cfl;
+                work_flops_q += cfq;
+                out.cnt[k] = nS;
+                out.loops[k] = l;
+                out.res[k] = rn;
+                if (out.res_post) out.res_post[k] = rpost;
+                out.tier[k] = tier_id;
+            } else if (st == ST_OVERFLOW) {
+                if (ovf_list) ovf_list[atomicAdd(ovf_cnt, 1)] = k;
+                else atomicOr(err, 1);
+            } else {
+                atomicOr(err, 2);
+            }
+        }
+        __syncwarp();
+    }
+    work_bytes = warp_sum(work_bytes);
+    const double wf = warp_sum((double)work_flops), wq = warp_sum((double)work_flops_q);
+    if (lane == 0 && work_bytes > 0.0) {
+        const bool q32 = sizeof(TQ) < sizeof(double);
+        atomicAdd(&d_swork[2 * PROF_SAI_BUILD], work_bytes);
+        atomicAdd(&d_swork[2 * PROF_SAI_BUILD + 1], wf + (q32 ? 0.0 : wq));
+        if (q32) atomicAdd(&d_swork32, wq);
+    }
+}
+
 // Persistent build kernel: each warp takes 32/G consecutive columns from the
 // atomic queue (work list, or 0..nwork-1), one per group of G lanes, until
 // the queue is empty. The groups of a warp start their columns together and
@@ -1049,6 +1647,32 @@ sai_status launch_tier(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, 
         k_sai<T, G, SMEM, PSAI><<<SAI_GRID(blocks), threads, smem, st>>>(A, sa, pa, work, nwork, next,
                                                                         scratch.as<char>(), out, ovf_list, ovf_cnt,
                                                                         err, tier_id);
+    }
+    SAI_CUDA(cudaGetLastError());
+    return SAI_OK;
+}
+
+// The lane form of the small tier: one warp per block (its 32 workspaces
+// take the block's shared memory), as many blocks as fit on each SM, no more
+// than the list needs.
+template <class TQ, bool PSAI>
+sai_status launch_lane(const SaiMat& A, const SpaiArgs& sa, const PsaiArgs& pa, const int32_t* work, int32_t nwork,
+                       int* next, const Out& out, int32_t* ovf_list, int* ovf_cnt, int* err, cudaStream_t st)
+{
+    if (nwork <= 0) return SAI_OK;
+    const size_t smem = LaneLayout<TQ>::WARP_BYTES;
+    SAI_CUDA(cudaFuncSetAttribute(k_sai_lane<TQ, PSAI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sai_lane<TQ, PSAI>, 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)g_num_sms * per_sm;
+    const int64_t need = ((int64_t)nwork + 31) / 32;
+    if (blocks > need) blocks = need;
+    SAI_CUDA(cudaMemsetAsync(next, 0, sizeof(int), st));
+    {
+        ProfScope ps(PROF_SAI_BUILD, st);
+        k_sai_lane<TQ, PSAI><<<SAI_GRID(blocks), 32, smem, st>>>(A, sa, pa, work, nwork, next, out, ovf_list, ovf_cnt,
+                                                                 err, 4);
     }
     SAI_CUDA(cudaGetLastError());
     return SAI_OK;
@@ -1246,7 +1870,9 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
     const int32_t* q0 = queue;
     int32_t n0 = nq;
     if (cfg.first_tier != 0) {
-        if (cfg.first_tier == 1)
+        if (cfg.first_tier == 3)
+            SAI_TRY((launch_lane<TQ, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 13, c + 3, st)));
+        else if (cfg.first_tier == 1)
             SAI_TRY((launch_tier<TS, 8, true, PSAI>(A, sa, pa, queue, nq, c + 0, out, ovfs.as<int32_t>(), c + 13,
                                                     c + 3, 4, cfg, st)));
         else
@@ -1381,7 +2007,7 @@ bool config_ok(const sai_build_config& c)
 {
     return (c.warps_t0 == 4 || c.warps_t0 == 8) &&
            (c.blocks_per_sm_t12 == 1 || c.blocks_per_sm_t12 == 2 || c.blocks_per_sm_t12 == 4) &&
-           (c.heavy_first == 0 || c.heavy_first == 1) && (c.first_tier >= 0 && c.first_tier <= 2);
+           (c.heavy_first == 0 || c.heavy_first == 1) && (c.first_tier >= 0 && c.first_tier <= 3);
 }
 }  // namespace
 
@@ -1482,10 +2108,11 @@ sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_s
         return SAI_OK;
     };
     sai_status r = SAI_OK;
-    // the first tier's shape and group size, with the warps per block
-    for (int ft : {0, 1, 2})
+    // the first tier's shape and group size, with the warps per block of
+    // the shared-memory tiers (the lane form runs one warp per block)
+    for (int ft : {0, 1, 2, 3})
         for (int w : {4, 8})
-            if (r == SAI_OK) r = try_cfg(sai_build_config{w, 2, 0, ft, 0.f});
+            if (r == SAI_OK && (ft != 3 || w == 8)) r = try_cfg(sai_build_config{w, 2, 0, ft, 0.f});
     // then the queue order, then the blocks per SM of the global-memory tiers
     if (r == SAI_OK) {
         sai_build_config c = out->cand[best];
