@@ -1243,9 +1243,9 @@ def main():
     ap.add_argument("--zipf-n", type=int, default=100000, help="order of the Zipf-count matrix (--workload zipf)")
     ap.add_argument("--probe", choices=["spai", "psai"], default=None,
                     help="run one untimed 64^3 solve with this SAI builder (for ncu captures) and exit")
-    ap.add_argument("--first-tier", type=int, default=0, choices=[0, 1, 2],
-                    help="build schedule's first tier for --probe (0: one column per warp; 1, 2: the small tier "
-                         "with four or two columns per warp)")
+    ap.add_argument("--first-tier", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="build schedule's first tier for --probe (0: one column per warp; 1, 2, 3: the small tier "
+                         "with four or two columns per warp, or one per lane)")
     args = ap.parse_args()
     if args.probe:
         return run_probe(args)

@@ -879,7 +879,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
 // word e * 32 + lane, so the 32 lanes touch 32 different banks. A column
 // that outgrows it is queued for tier 0, like the columns of the group form
 // of the small tier.
-constexpr int LT_L = 32, LT_S = 8, LT_HL = 64, LT_HC = 64;
+constexpr int LT_L = 32, LT_S = 8, LT_HL = 64, LT_HC = 128;
 
 // A lane's view of an array interleaved across the warp: element e at p[32 e].
 template <class V>

@@ -54,7 +54,8 @@ def test_every_schedule_gives_the_same_m(case):
 
 
 def test_autotune_picks_the_fastest_candidate_and_keeps_m():
-    """Nine candidates: the three first-tier shapes x two block sizes, then
+    """Ten candidates: the four first-tier forms x two block sizes (the lane
+    form with one), then
     heavy_first and the global tiers' blocks per SM on the best; the chosen
     one is the fastest timed, and a build under it gives the bits of the same
     configuration set by hand (and the oracle's pattern)."""
@@ -65,11 +66,12 @@ def test_autotune_picks_the_fastest_candidate_and_keeps_m():
     kw = dict(delta=0.3, mn=5, max_aug=10)
     try:
         chosen, cands = sai.build_autotune(sp_, "spai", **kw)
-        assert len(cands) == 9 and all(c["ms"] > 0 for c in cands)
+        assert len(cands) == 10 and all(c["ms"] > 0 for c in cands)
         assert chosen["ms"] == min(c["ms"] for c in cands)
-        assert {(c["first_tier"], c["warps_t0"]) for c in cands[:6]} == {(f, w) for f in (0, 1, 2) for w in (4, 8)}
-        assert all((c["blocks_per_sm_t12"], c["heavy_first"]) == (2, 0) for c in cands[:6])
-        assert cands[6]["heavy_first"] == 1 and {c["blocks_per_sm_t12"] for c in cands[7:]} == {1, 4}
+        assert {(c["first_tier"], c["warps_t0"]) for c in cands[:7]} == \
+            {(f, w) for f in (0, 1, 2) for w in (4, 8)} | {(3, 8)}
+        assert all((c["blocks_per_sm_t12"], c["heavy_first"]) == (2, 0) for c in cands[:7])
+        assert cands[7]["heavy_first"] == 1 and {c["blocks_per_sm_t12"] for c in cands[8:]} == {1, 4}
         got, _ = _m(sai, sp_, "spai", kw)
         sai.build_set_config(chosen["warps_t0"], chosen["blocks_per_sm_t12"], chosen["heavy_first"],
                              chosen["first_tier"])
@@ -82,7 +84,7 @@ def test_autotune_picks_the_fastest_candidate_and_keeps_m():
 def test_set_config_rejects_values_outside_the_candidates():
     need_gpu()
     sai = lib()
-    for bad in ((16, 2, 0), (8, 3, 0), (8, 2, 2), (8, 2, 0, 3)):
+    for bad in ((16, 2, 0), (8, 3, 0), (8, 2, 2), (8, 2, 0, 4)):
         with pytest.raises(sai.SaiError) as e:
             sai.build_set_config(*bad)
         assert e.value.status == sai.SAI_INVALID_ARG

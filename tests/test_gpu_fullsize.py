@@ -77,7 +77,7 @@ def test_fullsize_solve_matches_oracle_run(problem, case):
     np.testing.assert_allclose(x.cpu().numpy(), 1.0, rtol=0, atol=1e-7)
 
 
-@pytest.mark.parametrize("first_tier", [0, 1, 2])
+@pytest.mark.parametrize("first_tier", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_fullsize_refined_build_samples_match_oracle(problem, case, first_tier):
     """The headline form of the build (FP32 QR + one FP64 refinement step per

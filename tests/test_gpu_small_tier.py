@@ -1,6 +1,6 @@
 """The small shared-memory tier of the SAI build (first_tier 1: four columns
-per warp in 8-lane groups; 2: two columns per warp in 16-lane groups)
-against the oracle, through the C ABI.
+per warp in 8-lane groups; 2: two columns per warp in 16-lane groups; 3: one
+column per lane, 32 per warp) against the oracle, through the C ABI.
 
 The tier holds |L| <= 32 rows and |S| <= 8 columns; a column that outgrows it
 restarts in tier 0. Bars as for the other tiers: the oracle's sparsity
@@ -61,7 +61,7 @@ def _oracle_build(At, kind, kw):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("first_tier", [1, 2])
+@pytest.mark.parametrize("first_tier", [1, 2, 3])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_small_tier_matches_oracle(case, first_tier, precision):
     sai = lib()
@@ -84,7 +84,7 @@ def test_small_tier_matches_oracle(case, first_tier, precision):
         assert sum(P.n_tier[:4]) > 0, P.n_tier  # columns that outgrew the tier restarted in tier 0 or later
 
 
-@pytest.mark.parametrize("first_tier", [1, 2])
+@pytest.mark.parametrize("first_tier", [1, 2, 3])
 def test_small_tier_bits_do_not_depend_on_the_rest_of_the_schedule(first_tier):
     sai = lib()
     A = W.convdiff2d_irregular().A
@@ -99,14 +99,15 @@ def test_small_tier_bits_do_not_depend_on_the_rest_of_the_schedule(first_tier):
         assert np.array_equal(got.data, ref.data)
 
 
-def test_procedure_star_with_the_small_tier():
+@pytest.mark.parametrize("first_tier", [1, 3])
+def test_procedure_star_with_the_small_tier(first_tier):
     """Procedure * on the 2D workload with the small tier: every system's
     BiCGStab iteration count within +-1 of the oracle's, rr < eps, x within
     1e-6 of the oracle's."""
     sai = lib()
     import torch
     P = W.convdiff2d_irregular()
-    sai.build_set_config(8, 2, 0, 1)
+    sai.build_set_config(8, 2, 0, first_tier)
     dA = to_dev(P.A)
     b = torch.as_tensor(P.b, device="cuda")
     x, iters, rep = sai.solve(dA, b, sai="spai", krylov="bicgstab", eps=1e-8, delta=0.4, mn=5, max_aug=10)
