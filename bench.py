@@ -448,9 +448,14 @@ def run_ours(args):
             out.append((x, iters, rep))
         return out
 
-    # the build schedule: autotuned once on this matrix (outside the timed region)
-    tuned, _ = sai.build_autotune(sai.split(dA), "spai", delta=SPAI_KW["delta"], mn=SPAI_KW["mn"],
+    # the build schedules of both builders: autotuned once on this matrix
+    # (outside the timed region)
+    sp0 = sai.split(dA)
+    tuned, _ = sai.build_autotune(sp0, "spai", delta=SPAI_KW["delta"], mn=SPAI_KW["mn"],
                                   max_aug=SPAI_KW["max_aug"], precision=OPT_KW["sai_precision"])
+    tuned_p, _ = sai.build_autotune(sp0, "psai", delta=PSAI_KW["delta"], tol=PSAI_KW["tol"],
+                                    tol_mode=PSAI_KW["tol_mode"], lmax=PSAI_KW["lmax"],
+                                    precision=OPT_KW["sai_precision"])
     for _ in range(args.warmup):
         step(OPT_KW)
     step(PLAIN_KW)
@@ -575,7 +580,8 @@ def run_ours(args):
         "roofline": roofline(prof, peaks),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_mean},
-        "build_schedule": {k: tuned[k] for k in ("warps_t0", "blocks_per_sm_t12", "heavy_first", "first_tier")},
+        "build_schedule": {b: {k: t[k] for k in ("warps_t0", "blocks_per_sm_t12", "heavy_first", "first_tier")}
+                           for b, t in (("spai", tuned), ("psai", tuned_p))},
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -245,16 +245,18 @@ sai_status sai_precond_get_info(sai_precond P, sai_precond_info* info);
  * h's columns (every max(1, n/65536)-th, at least 4096 when n allows) under
  * candidate configurations, with sai = 0 (SPAI, spai params) or 1 (PSAI,
  * psai params), and makes the fastest the process-wide configuration of
- * later builds. The search takes one coordinate at a time: first_tier (the
- * workspace shape and columns per warp of the first tier) x warps_t0 with
- * {blocks_per_sm_t12 2, heavy_first 0} (first_tier 3 with warps_t0 8 only),
- * then heavy_first 1 on the best of those, then blocks_per_sm_t12 1 and 4
- * on the best so far (ten candidates). out (host) receives the candidates and the choice.
+ * that builder's later builds (SPAI and PSAI keep one each). The search
+ * takes one coordinate at a time: first_tier (the workspace shape and
+ * columns per warp of the first tier) x warps_t0 with {blocks_per_sm_t12 2,
+ * heavy_first 0} (first_tier 3 with warps_t0 8 only), then heavy_first 1 on
+ * the best of those, then blocks_per_sm_t12 1 and 4 on the best so far (ten
+ * candidates). out (host) receives the candidates and the choice.
  * Synchronises the stream. */
 sai_status sai_build_autotune(sai_split h, int32_t sai, const sai_spai_params* spai, const sai_psai_params* psai,
                               sai_stream_t stream, sai_build_tuning* out);
-/* Sets the process-wide build configuration; NULL restores the default.
- * Returns SAI_INVALID_ARG for values outside the candidate ranges. */
+/* Sets the process-wide build configuration of both builders; NULL restores
+ * the default. Returns SAI_INVALID_ARG for values outside the candidate
+ * ranges. */
 sai_status sai_build_set_config(const sai_build_config* cfg);
 /* M as CSC (rows ascending per column): col_ptr n+1, row_idx/val nnz_M.
  * loops[n]: augmentation steps (SPAI) or last loop index (PSAI).

@@ -1528,15 +1528,20 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* 
 // those of Arnoldi with modified Gram-Schmidt (Sec. 4.3's GMRES).
 
 // Partials: slot 2i = v_i^T u, 2i+1 = v_i^T z (i < j), 2*GM_MAXM = u^T u,
-// 2*GM_MAXM+1 = u^T z, stored at part[((c*PS) + slot)*nch + q] for chunk q.
-// One block per item (chunk q, system, group g of PD basis vectors), g
-// fastest so the items of one chunk read its rows of u and z from cache; the
-// block's IT_WARPS warps take interleaved 16-byte row vectors of the chunk and
-// their sums are combined in warp order through shared memory.
+// 2*GM_MAXM+1 = u^T z, stored at part[((c*PS) + slot)*ndc + q] for chunk q
+// of DC_CHUNK rows. One block per item (chunk q, system, group g of PD
+// basis vectors), g fastest so the items of one chunk read its rows of u and
+// z from cache; the block's IT_WARPS warps take interleaved 16-byte row
+// vectors of the chunk and their sums are combined in warp order through
+// shared memory. Chunks of four reduction chunks leave the step kernel a
+// quarter of the partials to sum.
+constexpr int DC_CHUNK = 4 * CHUNK;  // rows per item of the fused dot kernel (one partial per item)
+inline int dc_chunks(int64_t n) { return (int)((n + DC_CHUNK - 1) / DC_CHUNK); }
+
 template <class T>
-__global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __restrict__ u, const T* __restrict__ z,
-                                                          Basis<T> Bv, const int* list, const int* jdev,
-                                                          double* __restrict__ part)
+__global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, int ndc, const T* __restrict__ u,
+                                                          const T* __restrict__ z, Basis<T> Bv, const int* list,
+                                                          const int* jdev, double* __restrict__ part)
 {
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
@@ -1548,7 +1553,7 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __r
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // each block takes a contiguous range of items: the groups of one
     // (chunk, system) follow one another and read u and z from cache
-    const int64_t total = (int64_t)cnt * I.nch * ng;
+    const int64_t total = (int64_t)cnt * ndc * ng;
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t it_end = min(total, ((int64_t)blockIdx.x + 1) * per);
     for (int64_t it = (int64_t)blockIdx.x * per; it < it_end; ++it) {
@@ -1558,7 +1563,7 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __r
         const int q = (int)(rest / cnt);
         const int i0 = g * PD;
         const int ni = min(PD, j - i0);
-        const int64_t r0 = (int64_t)q * CHUNK, r1 = min((int64_t)I.n, r0 + CHUNK);
+        const int64_t r0 = (int64_t)q * DC_CHUNK, r1 = min((int64_t)I.n, r0 + DC_CHUNK);
         const int64_t o = (int64_t)c * I.ld;
         const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
         const T* Vp = Bv.V + (int64_t)i0 * Bv.vs + o;
@@ -1609,7 +1614,7 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_dots(Items I, const T* __r
             double sum = 0.0;
 #pragma unroll
             for (int w = 0; w < IT_WARPS; ++w) sum += (double)red[w][widx];
-            part[((size_t)c * PS + slot) * I.nch + q] = sum;
+            part[((size_t)c * PS + slot) * ndc + q] = sum;
         }
         __syncthreads();
     }
@@ -2131,17 +2136,18 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
     }
     const int fp = sizeof(T) == 4;
     const int64_t pcap = (int64_t)g_sms * g_res_dots[fp], ucap = (int64_t)g_sms * g_res_upd[fp];
-    int64_t pb = (int64_t)I.nch * k * ((G.m - 1) / PD + 1);
+    const int ndc = dc_chunks(n);
+    int64_t pb = (int64_t)ndc * k * ((G.m - 1) / PD + 1);
     int64_t ub = ((int64_t)I.nchu * k + IT_WARPS - 1) / IT_WARPS;
     pb = pb < pcap ? pb : pcap;
     ub = ub < ucap ? ub : ucap;
     {
         ProfScope ps(D.site_dots, st);
-        k_dc_dots<T><<<SAI_GRID(pb), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G.ladv, G.jdev, pt);
+        k_dc_dots<T><<<SAI_GRID(pb), IT_WARPS * 32, 0, st>>>(I, ndc, Wk.r, Wk.z, Wk.B, G.ladv, G.jdev, pt);
     }
     {
         ProfScope ps(PROF_GM_STEP, st);
-        k_dc_step<T><<<SAI_GRID(k * STEP_RB), STEP_THREADS, step_smem(G.m), st>>>(k, I.nch, pt, cap, S, G, D, tiny,
+        k_dc_step<T><<<SAI_GRID(k * STEP_RB), STEP_THREADS, step_smem(G.m), st>>>(k, ndc, pt, cap, S, G, D, tiny,
                                                                               fl);
     }
     {

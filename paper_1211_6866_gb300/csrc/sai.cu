@@ -1737,15 +1737,16 @@ struct Tiers<float> {
 // work queue (heavy_first: the columns of A~ with more than twice the
 // average number of entries, in index order, then the rest, in index order)
 // and the first tier (0: tier 0; 1 or 2: the small tier with 8- or 16-lane
-// groups). Only first_tier changes a column's arithmetic (its group size);
-// the rest changes the schedule alone.
+// groups; 3: its lane form). Only first_tier changes a column's arithmetic
+// (its group size); the rest changes the schedule alone. SPAI and PSAI keep
+// a configuration each (their columns' shapes differ).
 std::mutex g_cfg_mu;
-sai_build_config g_cfg = {8, 2, 0, 0, 0.f};
+sai_build_config g_cfg[2] = {{8, 2, 0, 0, 0.f}, {8, 2, 0, 0, 0.f}};
 
-sai_build_config current_config()
+sai_build_config current_config(bool psai)
 {
     std::lock_guard<std::mutex> lk(g_cfg_mu);
-    return g_cfg;
+    return g_cfg[psai ? 1 : 0];
 }
 
 // heavy[i] = nnz(A~ e_{list_i}) > thr (list = nullptr: i itself)
@@ -1775,7 +1776,7 @@ sai_status build_common(const sai_split_s* h, const SpaiArgs& sa, const PsaiArgs
                         cudaStream_t st, bool async, sai_precond_s* P, const int32_t* cols = nullptr,
                         int32_t ncols = -1, const sai_build_config* cfgp = nullptr)
 {
-    const sai_build_config cfg = cfgp ? *cfgp : current_config();
+    const sai_build_config cfg = cfgp ? *cfgp : current_config(PSAI);
     if (g_num_sms == 0) {
         int dev = 0;
         SAI_CUDA(cudaGetDevice(&dev));
@@ -2011,14 +2012,20 @@ bool config_ok(const sai_build_config& c)
 }
 }  // namespace
 
-sai_status sai_build_set_config_run(const sai_build_config* cfg)
+namespace {
+// which: 0 SPAI, 1 PSAI, -1 both
+sai_status set_config(const sai_build_config* cfg, int which)
 {
     sai_build_config c = cfg ? *cfg : sai_build_config{8, 2, 0, 0, 0.f};
     if (!config_ok(c)) return SAI_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_cfg_mu);
-    g_cfg = c;
+    if (which != 1) g_cfg[0] = c;
+    if (which != 0) g_cfg[1] = c;
     return SAI_OK;
 }
+}  // namespace
+
+sai_status sai_build_set_config_run(const sai_build_config* cfg) { return set_config(cfg, -1); }
 
 sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_spai_params* sp,
                                   const sai_psai_params* pp, cudaStream_t st, sai_build_tuning* out)
@@ -2137,7 +2144,7 @@ sai_status sai_build_autotune_run(const sai_split_s* h, int32_t sai, const sai_s
     cudaEventDestroy(e1);
     out->chosen = out->cand[best];
     out->sample_columns = m;
-    return sai_build_set_config_run(&out->chosen);
+    return set_config(&out->chosen, sai);
 }
 
 sai_status sai_build_work_reset()
