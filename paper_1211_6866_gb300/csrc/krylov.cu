@@ -272,15 +272,24 @@ struct Mat {
 // supergroup of SELL_SG systems, supergroup-major, which keeps the gathers
 // in L2 and gives every SM enough warps; otherwise an item is a slice for
 // all listed systems.
+// The stop index, the list count and (without supergroups) the first pass's
+// list entries are requested together, and a slice's entries before the
+// stop test: the first slice of a warp waits for one round of loads less
+// than it would if each waited for the one before. The list holds at least
+// k + 1 entries; those past its count are loaded but not used.
 constexpr int SELL_SG = 16;
 template <class T, int MODE, bool GM>
 __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T> Am, const T* __restrict__ X,
                                                    T* __restrict__ Y, const T* __restrict__ B,
-                                                   const int* __restrict__ list, const int* __restrict__ jstop, int jmax)
+                                                   const int* __restrict__ list, int k, const int* __restrict__ jstop,
+                                                   int jmax)
 {
     constexpr int CT = SELL_CT, W = SELL_W;
-    if (jstop && *jstop >= jmax) return;  // the step needs no operator application
+    const int js = jstop ? *jstop : 0;
     const int cnt = list[0];
+    int l0[CT];
+#pragma unroll
+    for (int t = 0; t < CT; ++t) l0[t] = !GM && t < k ? list[1 + t] : 0;
     const int64_t nitems = GM ? (int64_t)((cnt + SELL_SG - 1) / SELL_SG) * Am.nslices : Am.nslices;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -301,10 +310,12 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
                 col[u] = q < e ? Am.sci[q] : 0;
                 a[u] = q < e ? Am.sv[q] : (T)0;
             }
+            if (jstop && js >= jmax) return;  // the step needs no operator application
             for (int g0 = gb; g0 < ge; g0 += CT) {
                 int64_t off[CT];
 #pragma unroll
-                for (int t = 0; t < CT; ++t) off[t] = g0 + t < ge ? (int64_t)list[1 + g0 + t] * ld : 0;
+                for (int t = 0; t < CT; ++t)
+                    off[t] = g0 + t < ge ? (int64_t)(!GM && g0 == 0 ? l0[t] : list[1 + g0 + t]) * ld : 0;
                 T acc[CT];
 #pragma unroll
                 for (int t = 0; t < CT; ++t) acc[t] = 0;
@@ -325,6 +336,7 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
                 }
             }
         } else {
+            if (jstop && js >= jmax) return;
             for (int g0 = gb; g0 < ge; g0 += CT) {
                 int64_t off[CT];
 #pragma unroll
@@ -404,8 +416,8 @@ void spmv(int32_t n, int64_t ld, const Mat<T>& A, int k, const T* X, T* Y, const
         const int64_t cap = (int64_t)g_sms * 8;
         if (g > cap) g = cap;
         if (g < 1) g = 1;
-        if (gm) k_spmv_sell<T, MODE, true><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, jstop, jmax);
-        else k_spmv_sell<T, MODE, false><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, jstop, jmax);
+        if (gm) k_spmv_sell<T, MODE, true><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, k, jstop, jmax);
+        else k_spmv_sell<T, MODE, false><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, k, jstop, jmax);
         return;
     }
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
@@ -1660,18 +1672,22 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
                                                          int* any_adv)
 {
     __shared__ double red[PS];
+    __shared__ double hpS[GM_MAXM + 1];
     __shared__ T rc[GM_MAXM + 1];
     __shared__ T csS[GM_MAXM], snS[GM_MAXM];
     __shared__ double sh[2];
+    __shared__ double gj1S, thrS;
+    __shared__ int itS, capS;
     __shared__ int stop, mine;
     extern __shared__ double hsm[];  // columns q < j of Hbar (leading dimension m + 1)
+    // the step index, the list count and this block's system are requested together
     const int j = *G.jdev;
     const int cnt = G.ladv[0];
     const int m = G.m;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
     const int sb = blockIdx.x / STEP_RB, rb = blockIdx.x % STEP_RB;
+    const int c = G.ladv[1 + sb];  // the list holds k + 1 entries (grid: k x STEP_RB blocks)
     if (sb < cnt) {
-        const int c = G.ladv[1 + sb];
         const int ns = 2 * j + 2;
         // the STEP_RB blocks of system c reduce its slots (one warp per slot,
         // eight independent loads in flight per lane, summed in a fixed order)
@@ -1705,10 +1721,28 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         __syncthreads();
     }
     if (sb < cnt && mine) {
-        const int c = G.ladv[1 + sb];
         const int ns = 2 * j + 2;
+        double* Huc = G.Hu + (size_t)c * m * (m + 1);
+        double* Hc = G.H + (size_t)c * m * (m + 1);
+        double* hpc = G.hp + (size_t)c * (m + 1);
+        double* gc = G.g + (size_t)c * (m + 1);
+        // one round of independent loads: the reduced sums, the first-pass
+        // coefficients of column j-1, the rotations so far, Hbar's final
+        // columns q < j-1 and the system's scalars
         const volatile double* gr = G.red + (size_t)c * PS;
         for (int t = tid; t < ns; t += blockDim.x) red[t] = gr[t];
+        for (int i = tid; i < j; i += blockDim.x) hpS[i] = hpc[i];
+        for (int i = tid; i < j - 1; i += blockDim.x) {
+            csS[i] = (T)G.cs[(size_t)c * m + i];
+            snS[i] = (T)G.sn[(size_t)c * m + i];
+        }
+        for (int e = tid; e < (j - 1) * (m + 1); e += blockDim.x) hsm[e] = Huc[e];
+        if (tid == 0) {
+            gj1S = j >= 1 ? gc[j - 1] : 0.0;
+            thrS = S.thr[c];
+            itS = S.iters[c];
+            capS = cap[c];
+        }
         __syncthreads();
         // red[2i] = s_i, red[2i+1] = c_i (i < j), red[2j] = u^T u, red[2j+1] = u^T z
         if (wid == 0) {
@@ -1730,19 +1764,13 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         }
         __syncthreads();
         const double al = sh[0], d = sh[1];
-        double* Huc = G.Hu + (size_t)c * m * (m + 1);
-        double* Hc = G.H + (size_t)c * m * (m + 1);
         if (j >= 1) {
             // column j-1: first-pass coefficients + s, subdiagonal alpha
-            const double* hpc = G.hp + (size_t)c * (m + 1);
             for (int i = tid; i <= j; i += blockDim.x) {
-                const double v = i < j ? hpc[i] + red[2 * i] : al;
+                const double v = i < j ? hpS[i] + red[2 * i] : al;
                 Huc[(size_t)(j - 1) * (m + 1) + i] = v;
+                hsm[(size_t)(j - 1) * (m + 1) + i] = v;
                 rc[i] = (T)v;
-            }
-            for (int i = tid; i < j - 1; i += blockDim.x) {
-                csS[i] = (T)G.cs[(size_t)c * m + i];
-                snS[i] = (T)G.sn[(size_t)c * m + i];
             }
             __syncthreads();
             if (tid == 0) {
@@ -1759,16 +1787,17 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
                 G.sn[(size_t)c * m + j - 1] = (double)sn;
                 rc[j - 1] = cn * a + sn * b;
                 rc[j] = (T)0;
-                double* gc = G.g + (size_t)c * (m + 1);
-                const T gj1 = (T)gc[j - 1];
-                gc[j] = (double)(-sn * gj1);
+                const T gj1 = (T)gj1S;
+                const double gj = (double)(-sn * gj1);
+                gc[j] = gj;
                 gc[j - 1] = (double)(cn * gj1);
-                S.iters[c] += 1;
+                const int it = itS + 1;
+                S.iters[c] = it;
                 G.jd[c] = j;
-                if (fabs(gc[j]) < S.thr[c]) {
+                if (fabs(gj) < thrS) {
                     G.conv[c] = 1;
                     stop = 1;
-                } else if (al == 0.0 || S.iters[c] >= cap[c] || j >= m) {
+                } else if (al == 0.0 || it >= capS || j >= m) {
                     stop = 1;  // breakdown, iteration cap, or the cycle is full: restart
                 }
             }
@@ -1776,7 +1805,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
             for (int i = tid; i <= j; i += blockDim.x) Hc[(size_t)(j - 1) * (m + 1) + i] = (double)rc[i];
         } else if (tid == 0) {
             // v_0 = r0 / alpha: the right-hand side of the small problem is alpha e_1
-            G.g[(size_t)c * (m + 1)] = al;
+            gc[0] = al;
             if (al == 0.0) {
                 G.conv[c] = 1;
                 stop = 1;
@@ -1785,14 +1814,9 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         __syncthreads();
         if (!stop) {
             // first-pass coefficients of column j and the update coefficients;
-            // (Hbar s)_i = sum_{q >= max(i-1,0)} Hbar(i,q) s_q over the final columns q < j,
-            // one thread per row i (adjacent rows of a column are adjacent in memory),
-            // q ascending, the column loads in batches of 8 ahead of their FMAs
-            double* hpc = G.hp + (size_t)c * (m + 1);
-            // Hbar's final columns to shared memory in one round of loads (column j-1
-            // was written above by this block)
-            for (int e = tid; e < j * (m + 1); e += blockDim.x) hsm[e] = Huc[e];
-            __syncthreads();
+            // (Hbar s)_i = sum_{q >= max(i-1,0)} Hbar(i,q) s_q over the final columns q < j
+            // (in shared memory), one thread per row i, q ascending, the column
+            // loads in batches of 8 ahead of their FMAs
             for (int i = tid; i <= j; i += blockDim.x) {
                 T hs = 0;
                 int q = i > 0 ? i - 1 : 0;
@@ -1819,20 +1843,31 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
             G.adv[c] = 0;
         }
     }
-    if (last_block_arrives(G.bcnt) && tid == 0) {
-        rebuild_list(k, G.adv, G.ladv);
-        const int ku = G.ladv[0];
-        if (cnt > 0) {
-            if (j < m) {
-                spmm_work(D, D.nnzM, cnt);
-                spmm_work(D, D.nnzA, cnt);
-            }
-            kwork_add(D.site_dots, D.esz * D.n * cnt * (j + 2), D.n * cnt * (4.0 * j + 4.0));
-            if (ku > 0) kwork_add(D.site_upd, D.esz * D.n * ku * (j + 4), D.n * ku * (4.0 * j + 6.0));
-            *G.jdev = j + 1;
+    if (last_block_arrives(G.bcnt) && wid == 0) {
+        // the list of systems that advance, 32 at a time by ballot
+        const volatile int* va = G.adv;
+        int ku = 0;
+        for (int c0 = 0; c0 < k; c0 += 32) {
+            const int q = c0 + lane;
+            const bool on = q < k && va[q] != 0;
+            const unsigned bal = __ballot_sync(SAI_FULL, on);
+            if (on) G.ladv[1 + ku + __popc(bal & ((1u << lane) - 1u))] = q;
+            ku += __popc(bal);
         }
-        *any_adv = ku > 0;
-        *G.bcnt = 0;
+        if (lane == 0) {
+            G.ladv[0] = ku;
+            if (cnt > 0) {
+                if (j < m) {
+                    spmm_work(D, D.nnzM, cnt);
+                    spmm_work(D, D.nnzA, cnt);
+                }
+                kwork_add(D.site_dots, D.esz * D.n * cnt * (j + 2), D.n * cnt * (4.0 * j + 4.0));
+                if (ku > 0) kwork_add(D.site_upd, D.esz * D.n * ku * (j + 4), D.n * ku * (4.0 * j + 6.0));
+                *G.jdev = j + 1;
+            }
+            *any_adv = ku > 0;
+            *G.bcnt = 0;
+        }
     }
 }
 
