@@ -1392,6 +1392,7 @@ constexpr int PD = 8;                    // basis vectors per pass of the fused 
 constexpr int PS = 2 * GM_MAXM + 2;      // partial slots per (system, chunk)
 constexpr int STEP_THREADS = 256;        // threads per block of the step kernel
 constexpr int STEP_RB = 8;               // blocks per system of the step kernel
+static_assert(STEP_THREADS > GM_MAXM && 2 * STEP_THREADS >= PS, "the step kernel's single-round loads");
 
 // Krylov basis: m+1 system-major blocks of k vectors in the value type T.
 template <class T>
@@ -1675,11 +1676,12 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
     __shared__ double hpS[GM_MAXM + 1];
     __shared__ T rc[GM_MAXM + 1];
     __shared__ T csS[GM_MAXM], snS[GM_MAXM];
-    __shared__ double sh[2];
+    __shared__ double sh[3];
+    __shared__ T rsT[GM_MAXM];
     __shared__ double gj1S, thrS;
     __shared__ int itS, capS;
     __shared__ int stop, mine;
-    extern __shared__ double hsm[];  // columns q < j of Hbar (leading dimension m + 1)
+    extern __shared__ double hsm[];  // columns q < j of Hbar in T (leading dimension m + 1)
     // the step index, the list count and this block's system are requested together
     const int j = *G.jdev;
     const int cnt = G.ladv[0];
@@ -1726,22 +1728,65 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         double* Hc = G.H + (size_t)c * m * (m + 1);
         double* hpc = G.hp + (size_t)c * (m + 1);
         double* gc = G.g + (size_t)c * (m + 1);
-        // one round of independent loads: the reduced sums, the first-pass
-        // coefficients of column j-1, the rotations so far, Hbar's final
-        // columns q < j-1 and the system's scalars
-        const volatile double* gr = G.red + (size_t)c * PS;
-        for (int t = tid; t < ns; t += blockDim.x) red[t] = gr[t];
-        for (int i = tid; i < j; i += blockDim.x) hpS[i] = hpc[i];
-        for (int i = tid; i < j - 1; i += blockDim.x) {
-            csS[i] = (T)G.cs[(size_t)c * m + i];
-            snS[i] = (T)G.sn[(size_t)c * m + i];
-        }
-        for (int e = tid; e < (j - 1) * (m + 1); e += blockDim.x) hsm[e] = Huc[e];
-        if (tid == 0) {
-            gj1S = j >= 1 ? gc[j - 1] : 0.0;
-            thrS = S.thr[c];
-            itS = S.iters[c];
-            capS = cap[c];
+        // one round of independent loads: the reduced sums (through L2: the
+        // other blocks of the system wrote them), the first-pass coefficients
+        // of column j-1, the rotations so far, Hbar's final columns q < j-1
+        // (converted to T for the products below) and the system's scalars;
+        // their stores to shared memory follow them all
+        const int ne = (j - 1) * (m + 1);
+        const int bd = (int)blockDim.x;
+        T* hsmT = reinterpret_cast<T*>(hsm);
+        {
+            double rv[2], hv[8];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int t = tid + u * bd;
+                rv[u] = t < ns ? __ldcg(G.red + (size_t)c * PS + t) : 0.0;
+            }
+            const double hpv = tid < j ? hpc[tid] : 0.0;
+            const double csv = tid < j - 1 ? G.cs[(size_t)c * m + tid] : 0.0;
+            const double snv = tid < j - 1 ? G.sn[(size_t)c * m + tid] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = tid + u * bd;
+                hv[u] = e < ne ? Huc[e] : 0.0;
+            }
+            double g1 = 0.0, th = 0.0;
+            int itv = 0, cpv = 0;
+            if (tid == 0) {
+                g1 = j >= 1 ? gc[j - 1] : 0.0;
+                th = S.thr[c];
+                itv = S.iters[c];
+                cpv = cap[c];
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (tid + u * bd < ns) red[tid + u * bd] = rv[u];
+            if (tid < j) hpS[tid] = hpv;
+            if (tid < j - 1) {
+                csS[tid] = (T)csv;
+                snS[tid] = (T)snv;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (tid + u * bd < ne) hsmT[tid + u * bd] = (T)hv[u];
+            if (tid == 0) {
+                gj1S = g1;
+                thrS = th;
+                itS = itv;
+                capS = cpv;
+            }
+            // the rest of the columns when m is large, eight loads in flight per thread
+            for (int e0 = tid + 8 * bd; e0 < ne; e0 += 8 * bd) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * bd;
+                    hv[u] = e < ne ? Huc[e] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e0 + u * bd < ne) hsmT[e0 + u * bd] = (T)hv[u];
+            }
         }
         __syncthreads();
         // red[2i] = s_i, red[2i+1] = c_i (i < j), red[2j] = u^T u, red[2j+1] = u^T z
@@ -1757,19 +1802,22 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
                 const double uu = red[2 * j], uz = red[2 * j + 1];
                 const double a2 = uu - ss;
                 const double al = a2 > tiny * uu ? sqrt(a2) : 0.0;
+                const double ial = al > 0.0 ? 1.0 / al : 0.0;
                 sh[0] = al;
-                sh[1] = al > 0.0 ? (uz - sc) / al : 0.0;
+                sh[1] = (uz - sc) * ial;
+                sh[2] = ial;
                 stop = 0;
             }
         }
         __syncthreads();
-        const double al = sh[0], d = sh[1];
+        const double al = sh[0], d = sh[1], ial = sh[2];
+        for (int i = tid; i < j; i += blockDim.x) rsT[i] = (T)red[2 * i];
         if (j >= 1) {
             // column j-1: first-pass coefficients + s, subdiagonal alpha
             for (int i = tid; i <= j; i += blockDim.x) {
                 const double v = i < j ? hpS[i] + red[2 * i] : al;
                 Huc[(size_t)(j - 1) * (m + 1) + i] = v;
-                hsm[(size_t)(j - 1) * (m + 1) + i] = v;
+                hsmT[(size_t)(j - 1) * (m + 1) + i] = (T)v;
                 rc[i] = (T)v;
             }
             __syncthreads();
@@ -1815,7 +1863,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
         if (!stop) {
             // first-pass coefficients of column j and the update coefficients;
             // (Hbar s)_i = sum_{q >= max(i-1,0)} Hbar(i,q) s_q over the final columns q < j
-            // (in shared memory), one thread per row i, q ascending, the column
+            // (in shared memory, in T), one thread per row i, q ascending, the column
             // loads in batches of 8 ahead of their FMAs
             for (int i = tid; i <= j; i += blockDim.x) {
                 T hs = 0;
@@ -1823,13 +1871,13 @@ __global__ void __launch_bounds__(STEP_THREADS) k_dc_step(int k, int nch, const 
                 for (; q + 8 <= j; q += 8) {
                     T hv[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) hv[u] = (T)hsm[(size_t)(q + u) * (m + 1) + i];
+                    for (int u = 0; u < 8; ++u) hv[u] = hsmT[(size_t)(q + u) * (m + 1) + i];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) hs = fma(hv[u], (T)red[2 * (q + u)], hs);
+                    for (int u = 0; u < 8; ++u) hs = fma(hv[u], rsT[q + u], hs);
                 }
-                for (; q < j; ++q) hs = fma((T)hsm[(size_t)q * (m + 1) + i], (T)red[2 * q], hs);
+                for (; q < j; ++q) hs = fma(hsmT[(size_t)q * (m + 1) + i], rsT[q], hs);
                 const double cz = i < j ? red[2 * i + 1] : d;
-                hpc[i] = (cz - (double)hs) / al;
+                hpc[i] = (cz - (double)hs) * ial;
             }
             for (int i = tid; i < j; i += blockDim.x) {
                 G.sco[(size_t)c * (m + 1) + i] = red[2 * i];
