@@ -36,12 +36,15 @@ constexpr int CHUNK_U = 256;   // rows per item of the GMRES update (no per-vect
 constexpr int TILE = 256;      // rows per SpMV item (one block)
 constexpr int PJ = 16;         // basis vectors per register-tiled projection pass
 constexpr int IT_WARPS = 4;    // warps per block of the item kernels (small blocks: finer occupancy)
+constexpr int UP_CWARPS = 4;   // consumer warps of the ring-fed GMRES update (plus one producer warp)
+constexpr int UP_VPS = 4;      // vector slices (2 KB each) per stage of its ring
+constexpr int UP_STAGES = 4;   // stages of its ring
 
 enum { ST_OK = 0, ST_MAXITER = 5, ST_BREAKDOWN = 6 };  // same values as sai_status
 
 int g_sms = 0;
 // resident blocks per SM of the GMRES dot / update kernels, [0] double, [1] float
-int g_res_dots[2] = {1, 1}, g_res_upd[2] = {1, 1};
+int g_res_dots[2] = {1, 1}, g_res_upd[2] = {1, 1}, g_res_ring[2] = {1, 1};
 
 // ---------------------------------------------------------------- accounting
 __device__ double d_kwork[PROF_NSITES * 2];
@@ -1988,6 +1991,227 @@ __global__ void __launch_bounds__(IT_WARPS * 32) k_dc_update(Items I, T* __restr
     }
 }
 
+// ---------------------------------------------------------------- bulk-copy ring
+// Shared-memory ring fed by the bulk-copy engine (cp.async.bulk, completion
+// counted in bytes on an mbarrier per stage): one producer thread issues the
+// copies of a block's segments in order, the consumer warps take them in the
+// same order and release each stage on a second mbarrier. Every wait polls a
+// bounded number of times; on running out it sets d_pipe_err and the block
+// stops (the host turns the flag into SAI_CUDA_ERROR).
+__device__ int d_pipe_err;
+constexpr uint32_t PIPE_POLLS = 1u << 21;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+// true once the phase of parity `par` has completed; false after PIPE_POLLS polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par)
+{
+    const uint32_t a = smem_u32(b);
+    for (uint32_t it = 0; it < PIPE_POLLS; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(par)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// bytes (a multiple of 16) from src (16-byte aligned) to dst (16-byte aligned shared memory)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(UP_CWARPS * 32) : "memory"); }
+
+// The GMRES update of k_dc_update with the basis streamed through the ring:
+// items are (system, chunk of 128 W rows) pairs, system-major, a contiguous
+// range per block; an item's vector slices are V_0 .. V_{j-1}, u and z (the
+// rows of its chunk, 2 KB each), UP_VPS of them per stage. Consumer thread t
+// owns rows t W + [0, W) of the chunk and forms v_j = (u - V s)/alpha and
+// u <- (z - V c - d v_j)/alpha with the same per-row operation order as
+// k_dc_update. The caller checks that V, u, z, the vector stride and ld give
+// 16-byte aligned slices.
+template <class T>
+__global__ void __launch_bounds__((UP_CWARPS + 1) * 32) k_dc_update_ring(Items I, T* __restrict__ u,
+                                                                       const T* __restrict__ z, Basis<T> Bv, Gm G,
+                                                                       const int* list, const int* jdev)
+{
+    using VT = typename Vec<T>::type;
+    constexpr int VW = Vec<T>::W;
+    constexpr int ROWS = UP_CWARPS * 32 * VW;  // rows per chunk
+    constexpr uint32_t SEGB = UP_CWARPS * 32 * 16;
+    constexpr uint32_t STB = SEGB * UP_VPS;
+    __shared__ alignas(128) unsigned char ring[UP_STAGES * STB];
+    __shared__ alignas(8) uint64_t full[UP_STAGES], empty[UP_STAGES];
+    __shared__ T hs[GM_MAXM], hc[GM_MAXM];
+    __shared__ T coef[2];
+    const int tid = threadIdx.x;
+    const int j = *jdev - 1;  // k_dc_step has advanced the index: write V_j
+    const int cnt = list[0];
+    const int64_t nch = ((int64_t)I.n + ROWS - 1) / ROWS;
+    const int64_t total = (int64_t)cnt * nch;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t it0 = (int64_t)blockIdx.x * per, it1 = min(total, it0 + per);
+    if (tid == 0) {
+        for (int s = 0; s < UP_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], UP_CWARPS);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int nseg = j + 2;  // vector slices per item
+    if (tid >= UP_CWARPS * 32) {
+        // producer: one thread
+        if (tid != UP_CWARPS * 32) return;
+        uint32_t seg = 0;  // stages filled
+        bool ok = true;
+        int pci = -1;
+        int64_t oc = 0;
+        for (int64_t it = it0; it < it1 && ok; ++it) {
+            const int ci = (int)(it / nch);
+            if (ci != pci) {
+                pci = ci;
+                oc = (int64_t)list[1 + ci] * I.ld;
+            }
+            const int64_t r0 = (it - (int64_t)ci * nch) * ROWS;
+            const int64_t r1 = min((int64_t)I.n, r0 + ROWS);
+            const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
+            const uint32_t bytes = (uint32_t)((r1v - r0) * (int64_t)sizeof(T));
+            const int64_t o = oc + r0;
+            for (int v0 = 0; v0 < nseg; v0 += UP_VPS, ++seg) {
+                const int nv = min(UP_VPS, nseg - v0);
+                const uint32_t st = seg % UP_STAGES, use = seg / UP_STAGES;
+                if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&full[st], bytes * (uint32_t)nv);
+                for (int t = 0; t < nv; ++t) {
+                    const int sg = v0 + t;
+                    const T* src = sg < j ? Bv.V + (int64_t)sg * Bv.vs + o : (sg == j ? u + o : z + o);
+                    bulk_g2s(ring + st * STB + t * SEGB, src, bytes, &full[st]);
+                }
+            }
+        }
+        if (!ok) {
+            atomicExch(&d_pipe_err, 1);
+            // the copies still in flight land before the block's shared memory goes away
+            const uint32_t s0 = seg > UP_STAGES ? seg - UP_STAGES : 0;
+            for (uint32_t q = s0; q < seg; ++q) (void)mbar_wait(&full[q % UP_STAGES], (q / UP_STAGES) & 1);
+        }
+        return;
+    }
+    // consumers: a thread whose wait runs out stops waiting and storing but
+    // keeps to the loop, so that every consumer reaches every named barrier
+    const int lane = tid & 31;
+    const int m1 = G.m + 1;
+    uint32_t seg = 0, seg_dead = 0;
+    bool dead = false;
+    int cur = -1, c = 0;
+    for (int64_t it = it0; it < it1; ++it) {
+        const int ci = (int)(it / nch);
+        const int64_t r0 = (it - (int64_t)ci * nch) * ROWS;
+        const int64_t r1 = min((int64_t)I.n, r0 + ROWS);
+        const int64_t r1v = min(I.ld, (r1 + VW - 1) / VW * VW);
+        if (ci != cur) {
+            consumer_sync();
+            cur = ci;
+            c = list[1 + ci];
+            for (int i = tid; i < j; i += UP_CWARPS * 32) {
+                hs[i] = (T)G.sco[(size_t)c * m1 + i];
+                hc[i] = (T)G.cco[(size_t)c * m1 + i];
+            }
+            if (tid == 0) {
+                coef[0] = (T)(1.0 / G.alpha[c]);
+                coef[1] = (T)G.dco[c];
+            }
+            consumer_sync();
+        }
+        VT a_s = Vec<T>::zero(), a_c = Vec<T>::zero(), uv = Vec<T>::zero(), zv = Vec<T>::zero();
+        for (int v0 = 0; v0 < nseg; v0 += UP_VPS, ++seg) {
+            const int nv = min(UP_VPS, nseg - v0);
+            const uint32_t st = seg % UP_STAGES, use = seg / UP_STAGES;
+            if (!dead && !mbar_wait(&full[st], use & 1)) {
+                dead = true;
+                seg_dead = seg;
+                atomicExch(&d_pipe_err, 1);
+            }
+            VT v[UP_VPS];
+#pragma unroll
+            for (int t = 0; t < UP_VPS; ++t)
+                if (t < nv) v[t] = reinterpret_cast<const VT*>(ring + st * STB + t * SEGB)[tid];
+            __syncwarp();
+            if (lane == 0 && !dead) mbar_arrive(&empty[st]);
+#pragma unroll
+            for (int t = 0; t < UP_VPS; ++t) {
+                const int sg = v0 + t;
+                if (sg < j) {
+                    a_s = Vec<T>::axpy(hs[sg], v[t], a_s);
+                    a_c = Vec<T>::axpy(hc[sg], v[t], a_c);
+                } else if (sg == j) {
+                    uv = v[t];
+                } else if (sg == j + 1) {
+                    zv = v[t];
+                }
+            }
+        }
+        const int64_t row = r0 + (int64_t)tid * VW;
+        if (!dead && row < r1v) {
+            const T ia = coef[0], dd = coef[1];
+            const int64_t o = (int64_t)c * I.ld;
+            const VT v = Vec<T>::scale(ia, Vec<T>::sub(uv, a_s));
+            const VT un = Vec<T>::scale(ia, Vec<T>::axpy(-dd, v, Vec<T>::sub(zv, a_c)));
+            *reinterpret_cast<VT*>(Bv.V + (int64_t)j * Bv.vs + o + row) = v;
+            *reinterpret_cast<VT*>(u + o + row) = un;
+        }
+    }
+    if (dead) {
+        // the producer runs at most UP_STAGES stages ahead: let any of its
+        // copies still in flight land (short, bounded polls)
+        for (uint32_t q = seg_dead; q < seg_dead + UP_STAGES; ++q) {
+            const uint32_t a = smem_u32(&full[q % UP_STAGES]);
+            for (int it = 0; it < 4096; ++it) {
+                uint32_t ok;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                    "selp.b32 %0, 1, 0, p;\n\t}"
+                    : "=r"(ok)
+                    : "r"(a), "r"((q / UP_STAGES) & 1)
+                    : "memory");
+                if (ok) break;
+            }
+        }
+    }
+}
+
 // y = R(0:jd,0:jd)^{-1} g(0:jd) per system of the cycle (R upper triangular),
 // by column-oriented back substitution from shared memory; grid = k blocks,
 // dynamic shared memory (m*(m+1) + m) doubles.
@@ -2202,6 +2426,14 @@ struct GmWork {  // device buffers of one GMRES engine
 // dynamic shared memory of k_dc_step: the final columns of Hbar, m x (m+1) doubles
 inline size_t step_smem(int m) { return sizeof(double) * (size_t)m * (size_t)(m + 1); }
 
+// the bulk copies of k_dc_update_ring need 16-byte aligned segments
+template <class T>
+bool ring_aligned(const Items& I, const GmWork<T>& Wk)
+{
+    const uintptr_t p = (uintptr_t)Wk.B.V | (uintptr_t)Wk.r | (uintptr_t)Wk.z;
+    return p % 16 == 0 && ((size_t)Wk.B.vs * sizeof(T)) % 16 == 0 && ((size_t)I.ld * sizeof(T)) % 16 == 0;
+}
+
 template <class T>
 void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, Sys& S, Gm& G, const int* cap,
                   double* pt, int* fl, const Dims& D, double tiny, cudaStream_t st)
@@ -2235,7 +2467,16 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
     }
     {
         ProfScope ps(D.site_upd, st);
-        k_dc_update<T><<<SAI_GRID(ub), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G, G.ladv, G.jdev);
+        if (ring_aligned(I, Wk)) {
+            const int64_t rows = (int64_t)UP_CWARPS * 32 * Vec<T>::W;
+            int64_t rb = ((int64_t)n + rows - 1) / rows * k;
+            const int64_t rcap = (int64_t)g_sms * g_res_ring[fp];
+            rb = rb < rcap ? rb : rcap;
+            k_dc_update_ring<T>
+                <<<SAI_GRID(rb), (UP_CWARPS + 1) * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G, G.ladv, G.jdev);
+        } else {
+            k_dc_update<T><<<SAI_GRID(ub), IT_WARPS * 32, 0, st>>>(I, Wk.r, Wk.z, Wk.B, G, G.ladv, G.jdev);
+        }
     }
 }
 
@@ -2336,6 +2577,17 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         SAI_CUDA(cudaGetLastError());
     }
     if (gexec) cudaGraphExecDestroy(gexec);
+    {
+        // a ring wait of k_dc_update_ring that ran out (the flag is cleared for the next call)
+        int perr = 0;
+        if (cudaMemcpyFromSymbolAsync(&perr, d_pipe_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess && perr != 0) {
+            const int zero = 0;
+            (void)cudaMemcpyToSymbolAsync(d_pipe_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+            (void)cudaStreamSynchronize(st);
+            if (status == SAI_OK) status = SAI_CUDA_ERROR;
+        }
+    }
     if (ev_in) {
         cudaEventRecord(ev_out, st);
         cudaStreamWaitEvent(caller, ev_out, 0);
@@ -3078,9 +3330,14 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_dots[1], k_dc_dots<float>, IT_WARPS * 32, 0));
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[0], k_dc_update<double>, IT_WARPS * 32, 0));
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[1], k_dc_update<float>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_ring[0], k_dc_update_ring<double>,
+                                                               (UP_CWARPS + 1) * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_ring[1], k_dc_update_ring<float>,
+                                                               (UP_CWARPS + 1) * 32, 0));
         for (int i = 0; i < 2; ++i) {
             if (g_res_dots[i] < 1) g_res_dots[i] = 1;
             if (g_res_upd[i] < 1) g_res_upd[i] = 1;
+            if (g_res_ring[i] < 1) g_res_ring[i] = 1;
         }
     }
     // leading dimension: n rounded up to 32, plus 32 so that the k system
