@@ -44,7 +44,7 @@ enum { ST_OK = 0, ST_MAXITER = 5, ST_BREAKDOWN = 6 };  // same values as sai_sta
 
 int g_sms = 0;
 // resident blocks per SM of the GMRES dot / update kernels, [0] double, [1] float
-int g_res_dots[2] = {1, 1}, g_res_upd[2] = {1, 1}, g_res_ring[2] = {1, 1};
+int g_res_dots[2] = {1, 1}, g_res_upd[2] = {1, 1}, g_res_ring[2] = {1, 1}, g_res_sellp[2] = {1, 1};
 
 // ---------------------------------------------------------------- accounting
 __device__ double d_kwork[PROF_NSITES * 2];
@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(TILE) k_spmv(int32_t n, int64_t ld, const int6
 constexpr int SELL_C = 32;
 constexpr int SELL_CT = 4;  // systems per pass of the sliced-ELL SpMV
 constexpr int SELL_W = 8;   // slice width held in registers
+constexpr int SELL_CTP = 4;  // systems per pass of the prefetching sliced-ELL SpMV
 
 // One matrix of an operator: CSR, plus a sliced-ELL copy when sp != nullptr.
 template <class T>
@@ -377,6 +378,158 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int32_t n, int64_t ld, Mat<T>
     }
 }
 
+// Sliced-ELL SpMV for few systems with the slice entries prefetched: each
+// warp walks its slices (grid stride; a contiguous range per block measured
+// slower) and, while it gathers for one slice, copies the next slice's
+// column indices and values into its own shared buffer with cp.async (16
+// bytes per copy; the entry arrays start on 128-byte slice boundaries), so
+// a slice waits only for its gathers. The
+// block keeps the list in shared memory when it has fewer than SELL_LS
+// entries. Slices wider than SELL_W are read from global memory as in
+// k_spmv_sell. A system's sum runs over its row's entries in order, padding
+// included, as in k_spmv_sell.
+constexpr int SP_WARPS = 4;
+constexpr int SELL_LS = 256;
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <class T, int MODE, int CT>
+__global__ void __launch_bounds__(SP_WARPS * 32) k_spmv_sellp(int32_t n, int64_t ld, Mat<T> Am, const T* __restrict__ X,
+                                                             T* __restrict__ Y, const T* __restrict__ B,
+                                                             const int* __restrict__ list, int k,
+                                                             const int* __restrict__ jstop, int jmax)
+{
+    constexpr int W = SELL_W, EB = SELL_W * SELL_C;
+    __shared__ alignas(16) int32_t scol[SP_WARPS][2][EB];
+    __shared__ alignas(16) T sval[SP_WARPS][2][EB];
+    __shared__ int ls[SELL_LS];
+    if (jstop && *jstop >= jmax) return;  // the step needs no operator application
+    const bool shl = k < SELL_LS;
+    if (shl)
+        for (int i = threadIdx.x; i <= k; i += blockDim.x) ls[i] = list[i];
+    __syncthreads();
+    const int* L = shl ? ls : list;
+    const int cnt = L[0];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nsl = Am.nslices;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // copies the entries [b, e) of a slice (a multiple of SELL_C, at most EB) into buffer bf
+    auto prefetch = [&](int bf, int64_t b, int64_t e) {
+        if (e - b <= EB) {
+            const int nq = (int)(e - b) / 4;  // 16-byte pieces of the column indices
+            for (int q = lane; q < nq; q += 32) cp_async16(&scol[wid][bf][4 * q], Am.sci + b + 4 * q);
+            constexpr int PV = 16 / (int)sizeof(T);
+            const int nv = (int)(e - b) / PV;
+            for (int q = lane; q < nv; q += 32) cp_async16(&sval[wid][bf][PV * q], Am.sv + b + PV * q);
+        }
+        cp_async_commit();
+    };
+    int64_t b = 0, e = 0, bn = 0, en = 0;
+    if (sl < nsl) {
+        b = Am.sp[sl];
+        e = Am.sp[sl + 1];
+    }
+    if (sl + nw < nsl) {
+        bn = Am.sp[sl + nw];
+        en = Am.sp[sl + nw + 1];
+    }
+    prefetch(0, b, e);
+    int bf = 0;
+    for (; sl < nsl; sl += nw) {
+        prefetch(bf ^ 1, bn, en);  // an empty group past the last slice
+        int64_t b2 = 0, e2 = 0;
+        if (sl + 2 * nw < nsl) {
+            b2 = Am.sp[sl + 2 * nw];
+            e2 = Am.sp[sl + 2 * nw + 1];
+        }
+        cp_async_wait<1>();
+        __syncwarp();
+        const int64_t row = sl * SELL_C + lane;
+        if (e - b <= EB) {
+            const int wc = (int)(e - b) / SELL_C;  // width of this slice
+            const int32_t* cs = scol[wid][bf];
+            const T* vs = sval[wid][bf];
+            for (int g0 = 0; g0 < cnt; g0 += CT) {
+                const T* xb[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) xb[t] = X + (int64_t)L[1 + (g0 + t < cnt ? g0 + t : g0)] * ld;
+                T acc[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) acc[t] = 0;
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    if (u < wc) {
+                        const int32_t cu = cs[u * SELL_C + lane];
+                        const T au = vs[u * SELL_C + lane];
+#pragma unroll
+                        for (int t = 0; t < CT; ++t)
+                            if (g0 + t < cnt) acc[t] = fma(au, xb[t][cu], acc[t]);
+                    }
+                }
+                if (row < n) {
+#pragma unroll
+                    for (int t = 0; t < CT; ++t) {
+                        if (g0 + t < cnt) {
+                            const int64_t off = (int64_t)L[1 + g0 + t] * ld;
+                            if (MODE == 0) Y[off + row] = acc[t];
+                            else if (MODE == 1) Y[off + row] = B[off + row] - acc[t];
+                            else Y[off + row] += acc[t];
+                        }
+                    }
+                }
+            }
+        } else {
+            for (int g0 = 0; g0 < cnt; g0 += CT) {
+                int64_t off[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) off[t] = g0 + t < cnt ? (int64_t)L[1 + g0 + t] * ld : 0;
+                T acc[CT];
+#pragma unroll
+                for (int t = 0; t < CT; ++t) acc[t] = 0;
+                for (int64_t q0 = b + lane; q0 < e; q0 += (int64_t)W * SELL_C) {
+                    int32_t col[W];
+                    T a[W];
+#pragma unroll
+                    for (int u = 0; u < W; ++u) {
+                        const int64_t q = q0 + (int64_t)u * SELL_C;
+                        col[u] = q < e ? Am.sci[q] : 0;
+                        a[u] = q < e ? Am.sv[q] : (T)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < W; ++u)
+#pragma unroll
+                        for (int t = 0; t < CT; ++t)
+                            if (g0 + t < cnt) acc[t] = fma(a[u], X[off[t] + col[u]], acc[t]);
+                }
+                if (row < n) {
+#pragma unroll
+                    for (int t = 0; t < CT; ++t) {
+                        if (g0 + t < cnt) {
+                            if (MODE == 0) Y[off[t] + row] = acc[t];
+                            else if (MODE == 1) Y[off[t] + row] = B[off[t] + row] - acc[t];
+                            else Y[off[t] + row] += acc[t];
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();  // every lane is done with buffer bf before it is refilled
+        b = bn;
+        e = en;
+        bn = b2;
+        en = e2;
+        bf ^= 1;
+    }
+    cp_async_wait<0>();  // no copy in flight when the warp exits
+}
+
 // slice widths (longest row of each slice) times SELL_C, one warp per slice
 __global__ void k_sell_width(int32_t n, const int64_t* __restrict__ rp, int64_t nslices, int64_t* __restrict__ cnt)
 {
@@ -408,6 +561,13 @@ __global__ void k_sell_fill(int32_t n, const int64_t* __restrict__ rp, const int
     }
 }
 
+// the cp.async copies of k_spmv_sellp need 16-byte aligned entry arrays
+template <class T>
+bool sell_aligned(const Mat<T>& A)
+{
+    return (((uintptr_t)A.sci | (uintptr_t)A.sv) % 16) == 0;
+}
+
 template <class T, int MODE>
 void spmv(int32_t n, int64_t ld, const Mat<T>& A, int k, const T* X, T* Y, const T* B, const int* list,
           cudaStream_t st, const int* jstop = nullptr, int jmax = 0)
@@ -419,8 +579,18 @@ void spmv(int32_t n, int64_t ld, const Mat<T>& A, int k, const T* X, T* Y, const
         const int64_t cap = (int64_t)g_sms * 8;
         if (g > cap) g = cap;
         if (g < 1) g = 1;
-        if (gm) k_spmv_sell<T, MODE, true><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, k, jstop, jmax);
-        else k_spmv_sell<T, MODE, false><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, k, jstop, jmax);
+        if (gm) {
+            k_spmv_sell<T, MODE, true><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, k, jstop, jmax);
+        } else if (sell_aligned(A)) {
+            int64_t gp = (A.nslices + SP_WARPS - 1) / SP_WARPS;
+            const int64_t pcap = (int64_t)g_sms * g_res_sellp[sizeof(T) == 4];
+            if (gp > pcap) gp = pcap;
+            if (gp < 1) gp = 1;
+            k_spmv_sellp<T, MODE, SELL_CTP>
+                <<<SAI_GRID(gp), SP_WARPS * 32, 0, st>>>(n, ld, A, X, Y, B, list, k, jstop, jmax);
+        } else {
+            k_spmv_sell<T, MODE, false><<<SAI_GRID(g), 256, 0, st>>>(n, ld, A, X, Y, B, list, k, jstop, jmax);
+        }
         return;
     }
     const int64_t tiles = ((int64_t)n + TILE - 1) / TILE;
@@ -3330,6 +3500,10 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_dots[1], k_dc_dots<float>, IT_WARPS * 32, 0));
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[0], k_dc_update<double>, IT_WARPS * 32, 0));
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_upd[1], k_dc_update<float>, IT_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_sellp[0], k_spmv_sellp<double, 0, SELL_CTP>,
+                                                               SP_WARPS * 32, 0));
+        SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_sellp[1], k_spmv_sellp<float, 0, SELL_CTP>,
+                                                               SP_WARPS * 32, 0));
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_ring[0], k_dc_update_ring<double>,
                                                                (UP_CWARPS + 1) * 32, 0));
         SAI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_res_ring[1], k_dc_update_ring<float>,
@@ -3338,6 +3512,7 @@ sai_status sai_krylov_run(const sai_split_s* h, const sai_precond_s* P, int32_t 
             if (g_res_dots[i] < 1) g_res_dots[i] = 1;
             if (g_res_upd[i] < 1) g_res_upd[i] = 1;
             if (g_res_ring[i] < 1) g_res_ring[i] = 1;
+            if (g_res_sellp[i] < 1) g_res_sellp[i] = 1;
         }
     }
     // leading dimension: n rounded up to 32, plus 32 so that the k system
