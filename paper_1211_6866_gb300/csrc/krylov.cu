@@ -1561,7 +1561,7 @@ struct Gm {
 };
 
 constexpr int GM_MAXM = 128;             // largest restart length
-constexpr int PD = 8;                    // basis vectors per pass of the fused dot kernel
+constexpr int PD = 4;                    // basis vectors per pass of the fused dot kernel
 constexpr int PS = 2 * GM_MAXM + 2;      // partial slots per (system, chunk)
 constexpr int STEP_THREADS = 256;        // threads per block of the step kernel
 constexpr int STEP_RB = 8;               // blocks per system of the step kernel
@@ -1721,7 +1721,7 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* 
 // vectors of the chunk and their sums are combined in warp order through
 // shared memory. Chunks of four reduction chunks leave the step kernel a
 // quarter of the partials to sum.
-constexpr int DC_CHUNK = 4 * CHUNK;  // rows per item of the fused dot kernel (one partial per item)
+constexpr int DC_CHUNK = 2 * CHUNK;  // rows per item of the fused dot kernel (one partial per item)
 inline int dc_chunks(int64_t n) { return (int)((n + DC_CHUNK - 1) / DC_CHUNK); }
 
 template <class T>
