@@ -389,20 +389,29 @@ def run_reference(args):
     if rank != 0:
         return 0
     P = W.convdiff3d_irregular()
-    times = []
+    walls, ests = [], []
     r = None
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         r = oracle_sample(P)
         if it >= args.warmup:
-            times.append(r["est_step_s"])
-    est = float(np.mean(times))
-    val = 2 * P.n / est
+            walls.append(time.perf_counter() - t0)
+            ests.append(r["est_step_s"])
+    # each step is the sampled step, measured as it ran: the value is its
+    # columns over its wall time (the GMRES part is one cycle per builder,
+    # not the full solves, so this favours the oracle); the extrapolation
+    # to the full step is reported beside it
+    wall = float(np.mean(walls))
+    val = 2 * P.n / wall
+    sample = ("one step = the oracle's split, SPAI and PSAI builds of all %d columns and one 50-step GMRES(50) "
+              "cycle per builder on the b system, timed as run (not the complete solves)" % P.n)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(P),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "full_step_extrapolated": {"ms": float(np.mean(ests)) * 1e3, "value": 2 * P.n / float(np.mean(ests)),
+                                       "how": r["sample"]},
             "oracle_build_columns_per_s": {"spai": r["cols_per_s_spai"], "psai": r["cols_per_s_psai"]}}
     print(json.dumps(line))
     return 0
