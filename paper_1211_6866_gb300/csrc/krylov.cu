@@ -37,7 +37,8 @@ constexpr int TILE = 256;      // rows per SpMV item (one block)
 constexpr int PJ = 16;         // basis vectors per register-tiled projection pass
 constexpr int IT_WARPS = 4;    // warps per block of the item kernels (small blocks: finer occupancy)
 constexpr int UP_CWARPS = 4;   // consumer warps of the ring-fed GMRES update (plus one producer warp)
-constexpr int UP_VPS = 4;      // vector slices (2 KB each) per stage of its ring
+constexpr int UP_PT = 2;       // 16-byte pieces per consumer thread of a vector slice (slices of 4 KB)
+constexpr int UP_VPS = 2;      // vector slices per stage of its ring
 constexpr int UP_STAGES = 4;   // stages of its ring
 
 enum { ST_OK = 0, ST_MAXITER = 5, ST_BREAKDOWN = 6 };  // same values as sai_status
@@ -2220,13 +2221,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(UP_CWARPS * 32) : "memory"); }
 
 // The GMRES update of k_dc_update with the basis streamed through the ring:
-// items are (system, chunk of 128 W rows) pairs, system-major, a contiguous
-// range per block; an item's vector slices are V_0 .. V_{j-1}, u and z (the
-// rows of its chunk, 2 KB each), UP_VPS of them per stage. Consumer thread t
-// owns rows t W + [0, W) of the chunk and forms v_j = (u - V s)/alpha and
-// u <- (z - V c - d v_j)/alpha with the same per-row operation order as
-// k_dc_update. The caller checks that V, u, z, the vector stride and ld give
-// 16-byte aligned slices.
+// items are (system, chunk of 128 UP_PT W rows) pairs, system-major, a
+// contiguous range per block; an item's vector slices are V_0 .. V_{j-1}, u
+// and z (the rows of its chunk, 4 KB each), UP_VPS of them per stage.
+// Consumer thread t owns rows (t + 128 p) W + [0, W), p < UP_PT, of the chunk
+// and forms v_j = (u - V s)/alpha and u <- (z - V c - d v_j)/alpha with the
+// same per-row operation order as k_dc_update. The caller checks that V, u,
+// z, the vector stride and ld give 16-byte aligned slices.
 template <class T>
 __global__ void __launch_bounds__((UP_CWARPS + 1) * 32) k_dc_update_ring(Items I, T* __restrict__ u,
                                                                        const T* __restrict__ z, Basis<T> Bv, Gm G,
@@ -2234,8 +2235,9 @@ __global__ void __launch_bounds__((UP_CWARPS + 1) * 32) k_dc_update_ring(Items I
 {
     using VT = typename Vec<T>::type;
     constexpr int VW = Vec<T>::W;
-    constexpr int ROWS = UP_CWARPS * 32 * VW;  // rows per chunk
-    constexpr uint32_t SEGB = UP_CWARPS * 32 * 16;
+    constexpr int NC = UP_CWARPS * 32;          // consumer threads
+    constexpr int ROWS = NC * VW * UP_PT;       // rows per chunk
+    constexpr uint32_t SEGB = NC * 16 * UP_PT;  // bytes per slice
     constexpr uint32_t STB = SEGB * UP_VPS;
     __shared__ alignas(128) unsigned char ring[UP_STAGES * STB];
     __shared__ alignas(8) uint64_t full[UP_STAGES], empty[UP_STAGES];
@@ -2324,7 +2326,9 @@ __global__ void __launch_bounds__((UP_CWARPS + 1) * 32) k_dc_update_ring(Items I
             }
             consumer_sync();
         }
-        VT a_s = Vec<T>::zero(), a_c = Vec<T>::zero(), uv = Vec<T>::zero(), zv = Vec<T>::zero();
+        VT a_s[UP_PT], a_c[UP_PT], uv[UP_PT], zv[UP_PT];
+#pragma unroll
+        for (int p = 0; p < UP_PT; ++p) a_s[p] = a_c[p] = uv[p] = zv[p] = Vec<T>::zero();
         for (int v0 = 0; v0 < nseg; v0 += UP_VPS, ++seg) {
             const int nv = min(UP_VPS, nseg - v0);
             const uint32_t st = seg % UP_STAGES, use = seg / UP_STAGES;
@@ -2333,33 +2337,43 @@ __global__ void __launch_bounds__((UP_CWARPS + 1) * 32) k_dc_update_ring(Items I
                 seg_dead = seg;
                 atomicExch(&d_pipe_err, 1);
             }
-            VT v[UP_VPS];
+            VT v[UP_VPS][UP_PT];
 #pragma unroll
             for (int t = 0; t < UP_VPS; ++t)
-                if (t < nv) v[t] = reinterpret_cast<const VT*>(ring + st * STB + t * SEGB)[tid];
+#pragma unroll
+                for (int p = 0; p < UP_PT; ++p)
+                    if (t < nv) v[t][p] = reinterpret_cast<const VT*>(ring + st * STB + t * SEGB)[tid + p * NC];
             __syncwarp();
             if (lane == 0 && !dead) mbar_arrive(&empty[st]);
 #pragma unroll
             for (int t = 0; t < UP_VPS; ++t) {
                 const int sg = v0 + t;
-                if (sg < j) {
-                    a_s = Vec<T>::axpy(hs[sg], v[t], a_s);
-                    a_c = Vec<T>::axpy(hc[sg], v[t], a_c);
-                } else if (sg == j) {
-                    uv = v[t];
-                } else if (sg == j + 1) {
-                    zv = v[t];
+#pragma unroll
+                for (int p = 0; p < UP_PT; ++p) {
+                    if (sg < j) {
+                        a_s[p] = Vec<T>::axpy(hs[sg], v[t][p], a_s[p]);
+                        a_c[p] = Vec<T>::axpy(hc[sg], v[t][p], a_c[p]);
+                    } else if (sg == j) {
+                        uv[p] = v[t][p];
+                    } else if (sg == j + 1) {
+                        zv[p] = v[t][p];
+                    }
                 }
             }
         }
-        const int64_t row = r0 + (int64_t)tid * VW;
-        if (!dead && row < r1v) {
+        if (!dead) {
             const T ia = coef[0], dd = coef[1];
             const int64_t o = (int64_t)c * I.ld;
-            const VT v = Vec<T>::scale(ia, Vec<T>::sub(uv, a_s));
-            const VT un = Vec<T>::scale(ia, Vec<T>::axpy(-dd, v, Vec<T>::sub(zv, a_c)));
-            *reinterpret_cast<VT*>(Bv.V + (int64_t)j * Bv.vs + o + row) = v;
-            *reinterpret_cast<VT*>(u + o + row) = un;
+#pragma unroll
+            for (int p = 0; p < UP_PT; ++p) {
+                const int64_t row = r0 + (int64_t)(tid + p * NC) * VW;
+                if (row < r1v) {
+                    const VT v = Vec<T>::scale(ia, Vec<T>::sub(uv[p], a_s[p]));
+                    const VT un = Vec<T>::scale(ia, Vec<T>::axpy(-dd, v, Vec<T>::sub(zv[p], a_c[p])));
+                    *reinterpret_cast<VT*>(Bv.V + (int64_t)j * Bv.vs + o + row) = v;
+                    *reinterpret_cast<VT*>(u + o + row) = un;
+                }
+            }
         }
     }
     if (dead) {
@@ -2638,7 +2652,7 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
     {
         ProfScope ps(D.site_upd, st);
         if (ring_aligned(I, Wk)) {
-            const int64_t rows = (int64_t)UP_CWARPS * 32 * Vec<T>::W;
+            const int64_t rows = (int64_t)UP_CWARPS * 32 * Vec<T>::W * UP_PT;
             int64_t rb = ((int64_t)n + rows - 1) / rows * k;
             const int64_t rcap = (int64_t)g_sms * g_res_ring[fp];
             rb = rb < rcap ? rb : rcap;
