@@ -39,7 +39,8 @@ typedef struct CUstream_st* sai_stream_t; /* a cudaStream_t; NULL = legacy defau
 typedef enum {
     SAI_OK = 0,
     SAI_INVALID_ARG = 1,       /* bad size, NULL pointer, unsorted rows, ... */
-    SAI_CUDA_ERROR = 2,        /* a CUDA runtime call failed */
+    SAI_CUDA_ERROR = 2,        /* a CUDA runtime call failed, or a bounded wait inside a
+                                  kernel (the GMRES update's copy ring) gave up */
     SAI_OOM = 3,               /* device allocation failed */
     SAI_PATTERN_OVERFLOW = 4,  /* an SAI column outgrew the largest workspace tier */
     SAI_MAXITER = 5,           /* a Krylov system hit maxit (iterates still returned) */
