@@ -241,7 +241,7 @@ template <int H>
 __device__ __forceinline__ int32_t hfind(const int32_t* hk, const int32_t* hv, int32_t key)
 {
     uint32_t s = hmix(key) & (H - 1);
-    #pragma unroll 1
+#pragma unroll 1
     for (int probe = 0; probe < H; ++probe) {
         int32_t k = hk[s];
         if (k == key) return hv[s];
@@ -257,7 +257,7 @@ __device__ __forceinline__ int hinsert(int32_t* hk, int32_t key, bool& inserted)
 {
     uint32_t s = hmix(key) & (H - 1);
     inserted = false;
-    #pragma unroll 1
+#pragma unroll 1
     for (int probe = 0; probe < H; ++probe) {
         int32_t k = *((volatile int32_t*)&hk[s]);
         if (k == key) return (int)s;
@@ -278,7 +278,7 @@ template <int H>
 __device__ __forceinline__ int hslot(const int32_t* hk, int32_t key)
 {
     uint32_t s = hmix(key) & (H - 1);
-    #pragma unroll 1
+#pragma unroll 1
     for (int probe = 0; probe < H; ++probe) {
         int32_t k = hk[s];
         if (k == key) return (int)s;
@@ -295,7 +295,7 @@ __device__ bool add_rows(const WsT<typename T::TQ>& w, const SaiMat& A, int32_t 
 {
     const Grp<G> g;
     const int64_t b = A.cp[j], e = A.cp[j + 1];
-    #pragma unroll 1
+#pragma unroll 1
     for (int64_t base = b; base < e; base += G) {
         const int64_t q = base + g.l;
         bool isnew = false;
@@ -325,7 +325,7 @@ template <class T, int G>
 __device__ void col_init(const WsT<typename T::TQ>& w, int32_t k, int& nL, int& nS, int& nfact)
 {
     const Grp<G> g;
-    #pragma unroll 1
+#pragma unroll 1
     for (int q = g.l; q < T::HL; q += G) w.hk[q] = -1;
     g.sync();
     if (g.l == 0) {
@@ -349,24 +349,24 @@ __device__ int ls_update(const WsT<typename T::TQ>& w, const SaiMat& A, int& nL,
     using TQ = typename T::TQ;
     const Grp<G> g;
     const int nL_old = nL;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nfact; t < nS; ++t)
         if (!add_rows<T, G>(w, A, w.S[t], nL)) return ST_OVERFLOW;
     // zero the new rows of the old columns and of cv, and the new columns
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) {
         TQ* col = w.Q + (size_t)t * T::LCAP;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = (t < nfact ? nL_old : 0) + g.l; i < nL; i += G) col[i] = 0;
     }
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = nL_old + g.l; i < nL; i += G) w.cv[i] = 0;
     g.sync();
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nfact; t < nS; ++t) {
         const int32_t j = w.S[t];
         TQ* col = w.Q + (size_t)t * T::LCAP;
-        #pragma unroll 1
+#pragma unroll 1
         for (int64_t q = A.cp[j] + g.l; q < A.cp[j + 1]; q += G) {
             const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) col[pos] = (TQ)A.cv[q];
@@ -374,29 +374,29 @@ __device__ int ls_update(const WsT<typename T::TQ>& w, const SaiMat& A, int& nL,
     }
     g.sync();
     // old reflectors on the new columns
-    #pragma unroll 1
+#pragma unroll 1
     for (int jr = 0; jr < nfact; ++jr) {
         const TQ* v = w.Q + (size_t)jr * T::LCAP;
         const TQ bj = w.beta[jr];
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = nfact; t < nS; ++t) {
             TQ* col = w.Q + (size_t)t * T::LCAP;
             TQ d = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int i = jr + g.l; i < nL; i += G) d = fma(v[i], col[i], d);
             d = g.sum(d);
             const TQ f = bj * d;
-            #pragma unroll 1
+#pragma unroll 1
             for (int i = jr + g.l; i < nL; i += G) col[i] = fma(-f, v[i], col[i]);
             g.sync();
         }
     }
     // factor the trailing block column by column
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nfact; t < nS; ++t) {
         TQ* col = w.Q + (size_t)t * T::LCAP;
         TQ s2 = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = t + g.l; i < nL; i += G) s2 = fma(col[i], col[i], s2);
         s2 = g.sum(s2);
         if (!(s2 > (TQ)0)) return ST_SINGULAR;
@@ -411,31 +411,31 @@ __device__ int ls_update(const WsT<typename T::TQ>& w, const SaiMat& A, int& nL,
             w.beta[t] = bt;
         }
         g.sync();
-        #pragma unroll 1
+#pragma unroll 1
         for (int t2 = t + 1; t2 <= nS; ++t2) {
             TQ* c2 = t2 < nS ? w.Q + (size_t)t2 * T::LCAP : w.cv;
             TQ d = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int i = t + g.l; i < nL; i += G) d = fma(col[i], c2[i], d);
             d = g.sum(d);
             const TQ f = bt * d;
-            #pragma unroll 1
+#pragma unroll 1
             for (int i = t + g.l; i < nL; i += G) c2[i] = fma(-f, col[i], c2[i]);
             g.sync();
         }
     }
     nfact = nS;
     // back substitution (FP64 arithmetic on the stored factors)
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = g.l; i < nS; i += G) w.m[i] = (double)w.cv[i];
     g.sync();
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nS - 1; t >= 0; --t) {
         const double mt = w.m[t] / (double)w.rd[t];
         g.sync();
         if (g.l == 0) w.m[t] = mt;
         const TQ* col = w.Q + (size_t)t * T::LCAP;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = g.l; i < t; i += G) w.m[i] = fma(-(double)col[i], mt, w.m[i]);
         g.sync();
     }
@@ -448,15 +448,15 @@ template <class T, int G>
 __device__ double residual(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, int nS, const uint8_t* use)
 {
     const Grp<G> g;
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = g.l; i < nL; i += G) w.r[i] = (i == 0) ? -1.0 : 0.0;
     g.sync();
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) {
         if (use && !use[t]) continue;
         const int32_t j = w.S[t];
         const double mt = w.m[t];
-        #pragma unroll 1
+#pragma unroll 1
         for (int64_t q = A.cp[j] + g.l; q < A.cp[j + 1]; q += G) {
             const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) w.r[pos] = fma(A.cv[q], mt, w.r[pos]);
@@ -464,7 +464,7 @@ __device__ double residual(const WsT<typename T::TQ>& w, const SaiMat& A, int nL
         g.sync();
     }
     double s = 0.0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = g.l; i < nL; i += G) s = fma(w.r[i], w.r[i], s);
     return g.sum(s);
 }
@@ -477,11 +477,11 @@ __device__ void refine(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, in
 {
     const Grp<G> g;
     residual<T, G>(w, A, nL, nS, nullptr);  // r = A^ m - e^
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = g.l; t < nS; t += G) {
         const int32_t j = w.S[t];
         double gt = 0.0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
             const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) gt = fma(-A.cv[q], w.r[pos], gt);
@@ -490,26 +490,26 @@ __device__ void refine(const WsT<typename T::TQ>& w, const SaiMat& A, int nL, in
     }
     g.sync();
     // R^T y = g (forward), R(t,i) = Q[i][t] for i > t
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) {
         const double yt = w.g[t] / (double)w.rd[t];
         g.sync();
         if (g.l == 0) w.g[t] = yt;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = t + 1 + g.l; i < nS; i += G) w.g[i] = fma(-(double)w.Q[(size_t)i * T::LCAP + t], yt, w.g[i]);
         g.sync();
     }
     // R d = y (backward)
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nS - 1; t >= 0; --t) {
         const double dt = w.g[t] / (double)w.rd[t];
         g.sync();
         if (g.l == 0) w.g[t] = dt;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = g.l; i < t; i += G) w.g[i] = fma(-(double)w.Q[(size_t)t * T::LCAP + i], dt, w.g[i]);
         g.sync();
     }
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = g.l; t < nS; t += G) w.m[t] += w.g[t];
     g.sync();
 }
@@ -523,7 +523,7 @@ __device__ __forceinline__ long long qr_flops(int nL, int c, int nS)
 {
     const long long q = nS - c;
     long long f = 4 * q * ((long long)c * nL - (long long)c * (c - 1) / 2);
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = c; t < nS; ++t) f += 2LL * (nL - t) + 4LL * (nS - t) * (nL - t);
     return f + (long long)nS * nS;
 }
@@ -534,7 +534,7 @@ __device__ int s_nnz(const WsT<typename T::TQ>& w, const SaiMat& A, int nS)
 {
     const Grp<G> g;
     int c = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = g.l; t < nS; t += G) c += (int)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]);
     return g.sum(c);
 }
@@ -553,7 +553,7 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
     double rn = 0.0;
     fl = 0;
     fq = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (;;) {
         const int c0 = nfact;
         int st = ls_update<T, G>(w, A, nL, nS, nfact);
@@ -569,14 +569,14 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         rn = sqrt(rn2);
         if (rn <= a.delta || l >= a.max_aug) break;
         // candidate set N \ S from the rows of L
-        #pragma unroll 1
+#pragma unroll 1
         for (int q = g.l; q < T::HC; q += G) {
             w.ck[q] = -1;
             w.cf[q] = 0;
         }
         g.sync();
         bool ovf = false;
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = g.l; t < nS; t += G) {
             bool ins;
             int sl = hinsert<T::HC>(w.ck, w.S[t], ins);
@@ -585,10 +585,10 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         }
         g.sync();
         int ncand = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int idx = g.l; idx < nL; idx += G) {
             const int32_t i = w.Lrow[idx];
-            #pragma unroll 1
+#pragma unroll 1
             for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
                 bool ins;
                 int sl = hinsert<T::HC>(w.ck, A.rc[q], ins);
@@ -604,7 +604,7 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         // a chunk is read whole before it is written, and the writes stay at
         // or below it
         int nc = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int s0 = 0; s0 < T::HC; s0 += G) {
             const int32_t j = w.ck[s0 + g.l];
             const bool keep = j >= 0 && !w.cf[s0 + g.l];
@@ -620,14 +620,14 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         for (int q = 0; q < MNMAX; ++q) top[q] = ULLONG_MAX;
         int fsc = 0;
         const double irn2 = 1.0 / rn2;  // rn2 > delta^2 >= 0 here
-        #pragma unroll 1
+#pragma unroll 1
         for (int idx = g.l; idx < nc; idx += G) {
             const int32_t j = w.ck[idx];
             const double inj = A.icn[j];
             if (!(inj > 0.0)) continue;
             fsc += 2 * (int)(A.cp[j + 1] - A.cp[j]) + 5;  // r^T a_j, rho_j^2 and its key
             double d = 0.0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
                 const int pos = hfind<T::HL>(w.hk, w.hv, A.ri[q]);
                 if (pos >= 0) d = fma(w.r[pos], A.cv[q], d);
@@ -645,7 +645,7 @@ __device__ int spai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         }
         fl += g.sum(fsc);
         int added = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int sel = 0; sel < a.mn; ++sel) {
             const unsigned long long best = g.min_u64(top[0]);
             if (best == ULLONG_MAX) break;
@@ -689,7 +689,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
     int l = 0;
     fl = 0;
     fq = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (;;) {
         const int c0 = nfact;
         int st = ls_update<T, G>(w, A, nL, nS, nfact);
@@ -705,7 +705,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         double tolk = a.tol;
         if (a.tol_mode == 0) {
             int nz = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = g.l; t < nS; t += G) nz += (w.m[t] != 0.0);
             nz = g.sum(nz);
             tolk = (nz > 0 && A.norm1 > 0.0) ? a.delta / ((double)nz * A.norm1) : 0.0;
@@ -713,12 +713,12 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         if (a.tol_mode == 2) {
             // PSAI(lfill): kp[t] = m_t is among the lfill largest in magnitude
             // (equal magnitudes to the smaller column index)
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = g.l; t < nS; t += G) {
                 const double mt = fabs(w.m[t]);
                 const int32_t jt = w.S[t];
                 int rank = 0;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int u = 0; u < nS; ++u) {
                     const double mu = fabs(w.m[u]);
                     rank += (mu > mt) || (mu == mt && w.S[u] < jt);
@@ -727,7 +727,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             }
         } else {
             // keep flags: kp[t] = |m_t| > tol_k
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = g.l; t < nS; t += G) w.kp[t] = (uint8_t)(fabs(w.m[t]) > tolk);
         }
         g.sync();
@@ -738,7 +738,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             // compact the kept entries to the front of S / m (order preserved)
             int q = 0;
             if (g.l == 0) {
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = 0; t < nS; ++t)
                     if (w.kp[t]) {
                         w.S[q] = w.S[t];
@@ -756,14 +756,14 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             // reading (C): S^(l+1) = S_kept^(l) u (P(a^(l+1)) \ P(a^(l))), so a
             // dropped position never comes back. Hash flags: 2 in P(a^(l)),
             // 8 kept member of S^(l), 4 in P(a^(l+1)).
-            #pragma unroll 1
+#pragma unroll 1
             for (int q = g.l; q < T::HC; q += G) {
                 w.ck[q] = -1;
                 w.cf[q] = 0;
             }
             g.sync();
             bool ovf = false;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = g.l; t < na; t += G) {
                 bool ins;
                 const int sl = hinsert<T::HC>(w.ck, apat[t], ins);
@@ -772,7 +772,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             }
             g.sync();
             int nk = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = g.l; t < nS; t += G) {
                 if (!w.kp[t]) continue;
                 ++nk;
@@ -783,11 +783,11 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             }
             nk = g.sum(nk);
             g.sync();
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < na; ++t) {
                 const int32_t j = apat[t];
                 const int64_t b = A.cp[j], e = A.cp[j + 1];
-                #pragma unroll 1
+#pragma unroll 1
                 for (int64_t q = b + g.l; q < e; q += G) {
                     bool ins;
                     const int sl = hinsert<T::HC>(w.ck, A.ri[q], ins);
@@ -799,7 +799,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             if (g.any(ovf)) return ST_OVERFLOW;
             const unsigned lt = (1u << g.l) - 1u;
             int nb = 0, nf = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int s0 = 0; s0 < T::HC; s0 += G) {
                 const int32_t key = w.ck[s0 + g.l];
                 const uint8_t f = key >= 0 ? w.cf[s0 + g.l] : (uint8_t)0;
@@ -825,13 +825,13 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             const bool dropped = nk < nS;
             if (dropped && g.l == 0) {  // the kept members, in list order, to the front
                 int q = 0;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = 0; t < nS; ++t)
                     if (w.kp[t]) w.S[q++] = w.S[t];
             }
             g.sync();
             int q = nk;
-            #pragma unroll 1
+#pragma unroll 1
             for (int s0 = 0; s0 < T::HC; s0 += G) {  // then the frontier, in slot order
                 const int32_t key = w.ck[s0 + g.l];
                 const uint8_t f = key >= 0 ? w.cf[s0 + g.l] : (uint8_t)0;
@@ -851,18 +851,18 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             continue;
         }
         // a^(l+1): union of the column patterns of a^(l); positions in entry order
-        #pragma unroll 1
+#pragma unroll 1
         for (int q = g.l; q < T::HC; q += G) {
             w.ck[q] = -1;
             w.cf[q] = 0;
         }
         g.sync();
         int nb = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = 0; t < na; ++t) {
             const int32_t j = apat[t];
             const int64_t b = A.cp[j], e = A.cp[j + 1];
-            #pragma unroll 1
+#pragma unroll 1
             for (int64_t base = b; base < e; base += G) {
                 const int64_t q = base + g.l;
                 bool isnew = false;
@@ -884,7 +884,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         // cf = 1 marks members of S^(l) inside a^(l+1); a dropped member that is
         // not in a^(l+1) leaves the pattern (S shrinks)
         bool shrink = false;
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = g.l; t < nS; t += G) {
             const int sl = hslot<T::HC>(w.ck, w.S[t]);
             if (sl >= 0) w.cf[sl] = 1;
@@ -895,7 +895,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
         if (!shrink) {
             // pure growth: append the members of a^(l+1) not in S, in list order
             int add = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int base = 0; base < nb; base += G) {
                 const int t = base + g.l;
                 bool fresh = false;
@@ -916,7 +916,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             // S^(l) outside a^(l+1)
             int q2 = nb;
             if (g.l == 0) {
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = 0; t < nS; ++t)
                     if (w.kp[t] && hslot<T::HC>(w.ck, w.S[t]) < 0) {
                         if (q2 < T::SCAP) apat[q2 - nb] = w.S[t];
@@ -927,7 +927,7 @@ __device__ int psai_column(const WsT<typename T::TQ>& w, const SaiMat& A, int32_
             g.sync();
             if (q2 > T::SCAP) return ST_OVERFLOW;
             // apat (old a^(l)) is free now: it holds the extra kept members
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = g.l; t < q2; t += G) w.S[t] = t < nb ? anew[t] : apat[t - nb];
             g.sync();
             col_init<T, G>(w, k, nL, nS, nfact);
@@ -1014,7 +1014,7 @@ template <int H>
 __device__ __forceinline__ int lh_find(const LA<int32_t>& hk, const LA<uint8_t>& hv, int32_t key)
 {
     uint32_t s = hmix(key) & (H - 1);
-    #pragma unroll 1
+#pragma unroll 1
     for (int probe = 0; probe < H; ++probe) {
         const int32_t k = hk[s];
         if (k == key) return hv[s];
@@ -1030,7 +1030,7 @@ __device__ __forceinline__ int lh_insert(const LA<int32_t>& hk, int32_t key, boo
 {
     uint32_t s = hmix(key) & (H - 1);
     ins = false;
-    #pragma unroll 1
+#pragma unroll 1
     for (int probe = 0; probe < H; ++probe) {
         const int32_t k = hk[s];
         if (k == key) return (int)s;
@@ -1048,7 +1048,7 @@ template <int H>
 __device__ __forceinline__ int lh_slot(const LA<int32_t>& hk, int32_t key)
 {
     uint32_t s = hmix(key) & (H - 1);
-    #pragma unroll 1
+#pragma unroll 1
     for (int probe = 0; probe < H; ++probe) {
         const int32_t k = hk[s];
         if (k == key) return (int)s;
@@ -1061,7 +1061,7 @@ __device__ __forceinline__ int lh_slot(const LA<int32_t>& hk, int32_t key)
 template <class TQ>
 __device__ void lane_init(const LWs<TQ>& w, int32_t k, int& nL, int& nS, int& nfact)
 {
-    #pragma unroll 1
+#pragma unroll 1
     for (int q = 0; q < LT_HL; ++q) w.hk[q] = -1;
     bool ins;
     const int sl = lh_insert<LT_HL>(w.hk, k, ins);
@@ -1077,7 +1077,7 @@ __device__ void lane_init(const LWs<TQ>& w, int32_t k, int& nL, int& nS, int& nf
 template <class TQ>
 __device__ bool lane_add_rows(const LWs<TQ>& w, const SaiMat& A, int32_t j, int& nL)
 {
-    #pragma unroll 1
+#pragma unroll 1
     for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
         const int32_t i = A.ri[q];
         bool ins;
@@ -1100,41 +1100,41 @@ template <class TQ>
 __device__ int lane_ls_update(const LWs<TQ>& w, const SaiMat& A, int& nL, int nS, int& nfact)
 {
     const int nL_old = nL;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nfact; t < nS; ++t)
         if (!lane_add_rows(w, A, w.S[t], nL)) return ST_OVERFLOW;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t)
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = t < nfact ? nL_old : 0; i < nL; ++i) w.Q[t * LT_L + i] = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = nL_old; i < nL; ++i) w.cv[i] = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nfact; t < nS; ++t) {
         const int32_t j = w.S[t];
-        #pragma unroll 1
+#pragma unroll 1
         for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
             const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) w.Q[t * LT_L + pos] = (TQ)A.cv[q];
         }
     }
-    #pragma unroll 1
+#pragma unroll 1
     for (int jr = 0; jr < nfact; ++jr) {
         const TQ bj = w.beta[jr];
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = nfact; t < nS; ++t) {
             TQ d = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int i = jr; i < nL; ++i) d = fma(w.Q[jr * LT_L + i], w.Q[t * LT_L + i], d);
             const TQ f = bj * d;
-            #pragma unroll 1
+#pragma unroll 1
             for (int i = jr; i < nL; ++i) w.Q[t * LT_L + i] = fma(-f, w.Q[jr * LT_L + i], w.Q[t * LT_L + i]);
         }
     }
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nfact; t < nS; ++t) {
         TQ s2 = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = t; i < nL; ++i) s2 = fma(w.Q[t * LT_L + i], w.Q[t * LT_L + i], s2);
         if (!(s2 > (TQ)0)) return ST_SINGULAR;
         const TQ nrm = sqrt(s2);
@@ -1144,32 +1144,32 @@ __device__ int lane_ls_update(const LWs<TQ>& w, const SaiMat& A, int& nL, int nS
         w.Q[t * LT_L + t] = x0 - alpha;
         w.rd[t] = alpha;
         w.beta[t] = bt;
-        #pragma unroll 1
+#pragma unroll 1
         for (int t2 = t + 1; t2 <= nS; ++t2) {
             TQ d = 0;
             if (t2 < nS) {
-                #pragma unroll 1
+#pragma unroll 1
                 for (int i = t; i < nL; ++i) d = fma(w.Q[t * LT_L + i], w.Q[t2 * LT_L + i], d);
                 const TQ f = bt * d;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int i = t; i < nL; ++i) w.Q[t2 * LT_L + i] = fma(-f, w.Q[t * LT_L + i], w.Q[t2 * LT_L + i]);
             } else {
-                #pragma unroll 1
+#pragma unroll 1
                 for (int i = t; i < nL; ++i) d = fma(w.Q[t * LT_L + i], w.cv[i], d);
                 const TQ f = bt * d;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int i = t; i < nL; ++i) w.cv[i] = fma(-f, w.Q[t * LT_L + i], w.cv[i]);
             }
         }
     }
     nfact = nS;
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = 0; i < nS; ++i) w.m[i] = (double)w.cv[i];
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nS - 1; t >= 0; --t) {
         const double mt = w.m[t] / (double)w.rd[t];
         w.m[t] = mt;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = 0; i < t; ++i) w.m[i] = fma(-(double)w.Q[t * LT_L + i], mt, w.m[i]);
     }
     return ST_DONE;
@@ -1178,21 +1178,21 @@ __device__ int lane_ls_update(const LWs<TQ>& w, const SaiMat& A, int& nL, int nS
 template <class TQ>
 __device__ double lane_residual(const LWs<TQ>& w, const SaiMat& A, int nL, int nS, bool use_kp)
 {
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = 0; i < nL; ++i) w.r[i] = i == 0 ? -1.0 : 0.0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) {
         if (use_kp && !w.kp[t]) continue;
         const int32_t j = w.S[t];
         const double mt = w.m[t];
-        #pragma unroll 1
+#pragma unroll 1
         for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
             const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) w.r[pos] = fma(A.cv[q], mt, w.r[pos]);
         }
     }
     double s = 0.0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int i = 0; i < nL; ++i) s = fma(w.r[i], w.r[i], s);
     return s;
 }
@@ -1201,32 +1201,32 @@ template <class TQ>
 __device__ void lane_refine(const LWs<TQ>& w, const SaiMat& A, int nL, int nS)
 {
     lane_residual(w, A, nL, nS, false);
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) {
         const int32_t j = w.S[t];
         double gt = 0.0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
             const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
             if (pos >= 0) gt = fma(-A.cv[q], w.r[pos], gt);
         }
         w.g[t] = gt;
     }
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) {
         const double yt = w.g[t] / (double)w.rd[t];
         w.g[t] = yt;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = t + 1; i < nS; ++i) w.g[i] = fma(-(double)w.Q[i * LT_L + t], yt, w.g[i]);
     }
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = nS - 1; t >= 0; --t) {
         const double dt = w.g[t] / (double)w.rd[t];
         w.g[t] = dt;
-        #pragma unroll 1
+#pragma unroll 1
         for (int i = 0; i < t; ++i) w.g[i] = fma(-(double)w.Q[t * LT_L + i], dt, w.g[i]);
     }
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) w.m[t] += w.g[t];
 }
 
@@ -1234,7 +1234,7 @@ template <class TQ>
 __device__ int lane_nnz(const LWs<TQ>& w, const SaiMat& A, int nS)
 {
     int c = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = 0; t < nS; ++t) c += (int)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]);
     return c;
 }
@@ -1250,7 +1250,7 @@ __device__ int lane_spai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Spa
     double rn = 0.0;
     fl = 0;
     fq = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (;;) {
         const int c0 = nfact;
         const int st = lane_ls_update(w, A, nL, nS, nfact);
@@ -1266,12 +1266,12 @@ __device__ int lane_spai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Spa
         rn = sqrt(rn2);
         if (rn <= a.delta || l >= a.max_aug) break;
         // candidates N \ S from the rows of L (cf = 1 marks members of S)
-        #pragma unroll 1
+#pragma unroll 1
         for (int q = 0; q < LT_HC; ++q) {
             w.ck[q] = -1;
             w.cf[q] = 0;
         }
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = 0; t < nS; ++t) {
             bool ins;
             const int sl = lh_insert<LT_HC>(w.ck, w.S[t], ins);
@@ -1279,10 +1279,10 @@ __device__ int lane_spai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Spa
             w.cf[sl] = 1;
         }
         int ncand = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int idx = 0; idx < nL; ++idx) {
             const int32_t i = w.Lrow[idx];
-            #pragma unroll 1
+#pragma unroll 1
             for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
                 bool ins;
                 if (lh_insert<LT_HC>(w.ck, A.rc[q], ins) < 0) return ST_OVERFLOW;
@@ -1295,7 +1295,7 @@ __device__ int lane_spai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Spa
 #pragma unroll
         for (int q = 0; q < MNMAX; ++q) top[q] = ULLONG_MAX;
         const double irn2 = 1.0 / rn2;
-        #pragma unroll 1
+#pragma unroll 1
         for (int sl = 0; sl < LT_HC; ++sl) {
             const int32_t j = w.ck[sl];
             if (j < 0 || w.cf[sl]) continue;
@@ -1303,7 +1303,7 @@ __device__ int lane_spai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Spa
             if (!(inj > 0.0)) continue;
             fl += 2 * (A.cp[j + 1] - A.cp[j]) + 5;
             double d = 0.0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
                 const int pos = lh_find<LT_HL>(w.hk, w.hv, A.ri[q]);
                 if (pos >= 0) d = fma(w.r[pos], A.cv[q], d);
@@ -1352,7 +1352,7 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
     int l = 0;
     fl = 0;
     fq = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (;;) {
         const LA<int32_t> apat = cur0 ? w.a0 : w.a1;
         const LA<int32_t> anew = cur0 ? w.a1 : w.a0;
@@ -1370,17 +1370,17 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
         double tolk = a.tol;
         if (a.tol_mode == 0) {
             int nz = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < nS; ++t) nz += (w.m[t] != 0.0);
             tolk = (nz > 0 && A.norm1 > 0.0) ? a.delta / ((double)nz * A.norm1) : 0.0;
         }
         if (a.tol_mode == 2) {
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < nS; ++t) {
                 const double mt = fabs(w.m[t]);
                 const int32_t jt = w.S[t];
                 int rank = 0;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int u = 0; u < nS; ++u) {
                     const double mu = fabs(w.m[u]);
                     rank += (mu > mt) || (mu == mt && w.S[u] < jt);
@@ -1388,7 +1388,7 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
                 w.kp[t] = rank < a.lfill;
             }
         } else {
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < nS; ++t) w.kp[t] = fabs(w.m[t]) > tolk;
         }
         if (rn <= a.delta || l >= a.lmax) {
@@ -1396,7 +1396,7 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
             rn_post = sqrt(lane_residual(w, A, nL, nS, true));
             fl += 2 * sn + 2LL * nL;
             int q = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < nS; ++t)
                 if (w.kp[t]) {
                     w.S[q] = w.S[t];
@@ -1408,14 +1408,14 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
             nL_out = nL;
             return ST_DONE;
         }
-        #pragma unroll 1
+#pragma unroll 1
         for (int q = 0; q < LT_HC; ++q) {
             w.ck[q] = -1;
             w.cf[q] = 0;
         }
         if (a.growth == 1) {
             // reading (C): flags 2 in P(a^(l)), 8 kept member, 4 in P(a^(l+1))
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < na; ++t) {
                 bool ins;
                 const int sl = lh_insert<LT_HC>(w.ck, apat[t], ins);
@@ -1423,7 +1423,7 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
                 w.cf[sl] = (uint8_t)(w.cf[sl] | 2);
             }
             int nk = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < nS; ++t) {
                 if (!w.kp[t]) continue;
                 ++nk;
@@ -1432,10 +1432,10 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
                 if (sl < 0) return ST_OVERFLOW;
                 w.cf[sl] = (uint8_t)(w.cf[sl] | 8);
             }
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < na; ++t) {
                 const int32_t j = apat[t];
-                #pragma unroll 1
+#pragma unroll 1
                 for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
                     bool ins;
                     const int sl = lh_insert<LT_HC>(w.ck, A.ri[q], ins);
@@ -1444,7 +1444,7 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
                 }
             }
             int nb = 0, nf = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int sl = 0; sl < LT_HC; ++sl) {
                 const int32_t key = w.ck[sl];
                 const int f = key >= 0 ? w.cf[sl] : 0;
@@ -1467,12 +1467,12 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
             const bool dropped = nk < nS;
             if (dropped) {
                 int q = 0;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = 0; t < nS; ++t)
                     if (w.kp[t]) w.S[q++] = w.S[t];
             }
             int q = nk;
-            #pragma unroll 1
+#pragma unroll 1
             for (int sl = 0; sl < LT_HC; ++sl) {
                 const int32_t key = w.ck[sl];
                 const int f = key >= 0 ? w.cf[sl] : 0;
@@ -1487,10 +1487,10 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
         }
         // a^(l+1): the rows of the columns of a^(l), in entry order
         int nb = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = 0; t < na; ++t) {
             const int32_t j = apat[t];
-            #pragma unroll 1
+#pragma unroll 1
             for (int64_t q = A.cp[j]; q < A.cp[j + 1]; ++q) {
                 bool ins;
                 const int32_t i = A.ri[q];
@@ -1503,7 +1503,7 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
             }
         }
         bool shrink = false;
-        #pragma unroll 1
+#pragma unroll 1
         for (int t = 0; t < nS; ++t) {
             const int sl = lh_slot<LT_HC>(w.ck, w.S[t]);
             if (sl >= 0) w.cf[sl] = 1;
@@ -1511,7 +1511,7 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
         }
         if (!shrink) {
             int add = 0;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < nb; ++t) {
                 const int32_t j = anew[t];
                 if (w.cf[lh_slot<LT_HC>(w.ck, j)] == 0) {
@@ -1523,14 +1523,14 @@ __device__ int lane_psai(const LWs<TQ>& w, const SaiMat& A, int32_t k, const Psa
             nS += add;
         } else {
             int q2 = nb;
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < nS; ++t)
                 if (w.kp[t] && lh_slot<LT_HC>(w.ck, w.S[t]) < 0) {
                     if (q2 >= LT_S) return ST_OVERFLOW;
                     apat[q2 - nb] = w.S[t];
                     ++q2;
                 }
-            #pragma unroll 1
+#pragma unroll 1
             for (int t = 0; t < q2; ++t) w.S[t] = t < nb ? anew[t] : apat[t - nb];
             lane_init(w, k, nL, nS, nfact);
             nS = q2;
@@ -1554,7 +1554,7 @@ __global__ void __launch_bounds__(64) k_sai_lane(SaiMat A, SpaiArgs sa, PsaiArgs
     const LWs<TQ> w = bind_lane<TQ>(wbase, lane);
     double work_bytes = 0.0;
     long long work_flops = 0, work_flops_q = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (;;) {
         int first = 0;
         if (lane == 0) first = atomicAdd(next, 32);
@@ -1572,13 +1572,13 @@ __global__ void __launch_bounds__(64) k_sai_lane(SaiMat A, SpaiArgs sa, PsaiArgs
             if (st == ST_DONE) {
                 const size_t o = (size_t)k * out.smax;
                 double cb = 0.0;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = 0; t < nS; ++t) {
                     out.rows[o + t] = w.S[t];
                     out.vals[o + t] = w.m[t];
                     cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
                 }
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = 0; t < nL; ++t) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
                 work_bytes += cb;
                 work_flops += cfl;
@@ -1628,7 +1628,7 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
     const WsT<typename T::TQ> w = bind_ws<T>(base);
     double work_bytes = 0.0;
     long long work_flops = 0, work_flops_q = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (;;) {
         int first = 0;
         if ((threadIdx.x & 31) == 0) first = atomicAdd(next, GPW);
@@ -1649,16 +1649,16 @@ __global__ void __launch_bounds__(256) k_sai(SaiMat A, SpaiArgs sa, PsaiArgs pa,
             if (st == ST_DONE) {
                 int32_t* orow = big ? out.big_rows + (size_t)item * out.big_smax : out.rows + (size_t)k * out.smax;
                 double* oval = big ? out.big_vals + (size_t)item * out.big_smax : out.vals + (size_t)k * out.smax;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = g.l; t < nS; t += G) {
                     orow[t] = w.S[t];
                     oval[t] = w.m[t];
                 }
                 if (big && g.l == 0) out.big_slot[k] = item;
                 double cb = 0.0;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = g.l; t < nS; t += G) cb += 12.0 * (double)(A.cp[w.S[t] + 1] - A.cp[w.S[t]]) + 12.0;
-                #pragma unroll 1
+#pragma unroll 1
                 for (int t = g.l; t < nL; t += G) cb += 4.0 * (double)(A.rp[w.Lrow[t] + 1] - A.rp[w.Lrow[t]]);
                 work_bytes += g.sum(cb);
                 work_flops += cfl;
@@ -1706,11 +1706,11 @@ __global__ void k_assemble(int32_t n, int32_t smax, const int32_t* cnt, const in
     const int bs = big_slot ? big_slot[k] : -1;
     const int32_t* rk = bs >= 0 ? big_rows + (size_t)bs * big_smax : rows + (size_t)k * smax;
     const double* vk = bs >= 0 ? big_vals + (size_t)bs * big_smax : vals + (size_t)k * smax;
-    #pragma unroll 1
+#pragma unroll 1
     for (int t = lane; t < c; t += 32) {
         const int32_t r = rk[t];
         int rank = 0;
-        #pragma unroll 1
+#pragma unroll 1
         for (int u = 0; u < c; ++u) rank += rk[u] < r;
         ri[cp[k] + rank] = r;
         v[cp[k] + rank] = vk[t];
@@ -1720,7 +1720,7 @@ __global__ void k_assemble(int32_t n, int32_t smax, const int32_t* cnt, const in
 __global__ void k_stats(int32_t n, const int32_t* loops, const double* res, double delta, int* out)
 {
     int nc = 0, lm = 0;
-    #pragma unroll 1
+#pragma unroll 1
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         nc += res[k] > delta;
         lm = max(lm, loops[k]);
@@ -1738,7 +1738,7 @@ __global__ void k_stats(int32_t n, const int32_t* loops, const double* res, doub
 __global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
 {
     int c[6] = {0, 0, 0, 0, 0, 0};
-    #pragma unroll 1
+#pragma unroll 1
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int t = tier[k];
 #pragma unroll
@@ -1754,7 +1754,7 @@ __global__ void k_tier_count(int32_t n, const int32_t* tier, int* out)
 // icn[j] = 1/cn2[j] (0 where cn2[j] = 0: an empty column scores no key)
 __global__ void k_recip(int32_t n, const double* __restrict__ cn2, double* __restrict__ icn)
 {
-    #pragma unroll 1
+#pragma unroll 1
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
         icn[j] = cn2[j] > 0.0 ? 1.0 / cn2[j] : 0.0;
 }
