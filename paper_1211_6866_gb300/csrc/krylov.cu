@@ -1559,7 +1559,6 @@ struct Gm {
     int* bcnt;         // arrival counter of the multi-block control kernels
     double* red;       // k x PS: a step's reduced partials per system
     int* scnt;         // k: per-system arrival counters of k_dc_step
-    int* nbody;        // 2: step groups run in this cycle / in all cycles (while-node form)
 };
 
 constexpr int GM_MAXM = 128;             // largest restart length
@@ -1687,7 +1686,6 @@ __global__ void k_gm_cycle_start(int k, int nch, const double* part, const int* 
         build_list(k, G.adv, G.ladv);
         *G.jdev = 0;
         *G.bcnt = 0;
-        G.nbody[0] = 0;
         *any_cyc = G.lcyc[0] > 0;
     }
 }
@@ -2667,20 +2665,8 @@ void arnoldi_step(const Items& I, int k, const Ops<T>& A, const GmWork<T>& Wk, S
     }
 }
 
-constexpr int GM_STEPS_PER_CHECK = 4;  // Arnoldi steps per graph body (or between host checks)
+constexpr int GM_STEPS_PER_CHECK = 4;  // Arnoldi steps between host checks (one graph)
 constexpr int GM_LAUNCHES_PER_STEP = 5;
-
-// The condition of the while node that runs a cycle's Arnoldi steps: true
-// while a system advances and fewer than max_body groups of steps have run
-// in this cycle; nbody[1] counts the groups of all cycles (for the launch
-// count).
-__global__ void k_gm_cond(const int* any_adv, int* nbody, int max_body, cudaGraphConditionalHandle h)
-{
-    const int nb = nbody[0] + 1;
-    nbody[0] = nb;
-    nbody[1] += 1;
-    cudaGraphSetConditional(h, (*any_adv != 0 && nb < max_body) ? 1u : 0u);
-}
 
 // Restarted GMRES on the systems with finite thresholds: X = 0 start,
 // per-system iteration caps, S.iters counts the inner steps of this call.
@@ -2721,62 +2707,22 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         }
     }
     cudaGraphExec_t gexec = nullptr;
-    bool whole = false;  // gexec runs all steps of a cycle (a while node around groups of steps)
-    const int max_body = (m + GM_STEPS_PER_CHECK) / GM_STEPS_PER_CHECK;  // steps 0..m
     if (use_graph && st != caller) {
         cudaStreamCaptureStatus cs;
         SAI_CUDA(cudaStreamIsCapturing(st, &cs));
         if (cs == cudaStreamCaptureStatusNone) {
-            SAI_CUDA(cudaMemsetAsync(G.nbody, 0, 2 * sizeof(int), st));
-            // a cycle's step loop as one graph: a while node whose body is a
-            // group of steps and k_gm_cond
             cudaGraph_t graph = nullptr;
-            cudaError_t e = cudaGraphCreate(&graph, 0);
-            cudaGraphConditionalHandle hnd = 0;
-            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hnd, graph, 1, cudaGraphCondAssignDefault);
-            cudaGraph_t body = nullptr;
-            if (e == cudaSuccess) {
-                cudaGraphNodeParams np = {};
-                np.type = cudaGraphNodeTypeConditional;
-                np.conditional.handle = hnd;
-                np.conditional.type = cudaGraphCondTypeWhile;
-                np.conditional.size = 1;
-                cudaGraphNode_t node = nullptr;
-                e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
-                if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
-            }
-            if (e == cudaSuccess)
-                e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                for (int q = 0; q < GM_STEPS_PER_CHECK; ++q)
-                    arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, fl, D, tiny, st);
-                k_gm_cond<<<SAI_GRID(1), 1, 0, st>>>(fl, G.nbody, max_body, hnd);
-                cudaGraph_t cg = nullptr;
-                e = cudaStreamEndCapture(st, &cg);
-            }
+            SAI_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            for (int q = 0; q < GM_STEPS_PER_CHECK; ++q) arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, fl, D, tiny, st);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
             if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
             if (graph) cudaGraphDestroy(graph);
-            if (e == cudaSuccess) {
-                whole = true;
-                sai_count_grid_add(-(long long)GM_STEPS_PER_CHECK * GM_LAUNCHES_PER_STEP - 1);
-            } else {
+            if (e != cudaSuccess) {
                 gexec = nullptr;
                 (void)cudaGetLastError();
-                // groups of steps with a host check after each
-                graph = nullptr;
-                SAI_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                for (int q = 0; q < GM_STEPS_PER_CHECK; ++q)
-                    arnoldi_step<T>(I, k, A, Wk, S, G, cap, pt, fl, D, tiny, st);
-                e = cudaStreamEndCapture(st, &graph);
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
-                if (graph) cudaGraphDestroy(graph);
-                if (e != cudaSuccess) {
-                    gexec = nullptr;
-                    (void)cudaGetLastError();
-                }
-                // the captured launches ran no kernel yet: count them at replay
-                sai_count_grid_add(-(long long)GM_STEPS_PER_CHECK * GM_LAUNCHES_PER_STEP);
             }
+            // the captured launches ran no kernel yet: count them at replay
+            sai_count_grid_add(-(long long)GM_STEPS_PER_CHECK * GM_LAUNCHES_PER_STEP);
         }
     }
     k_gm_init<T><<<SAI_GRID(ib), IT_WARPS * 32, 0, st>>>(I, k, Bs, Xs, r, S.lall, pt2);
@@ -2789,10 +2735,7 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         SAI_CUDA(cudaStreamSynchronize(st));
         if (!hflag) break;
         // steps 0..m: every system of the cycle stops by step m
-        if (whole) {
-            if (cudaGraphLaunch(gexec, st) != cudaSuccess) status = SAI_CUDA_ERROR;
-        }
-        for (int j0 = 0; !whole && j0 <= m; j0 += GM_STEPS_PER_CHECK) {
+        for (int j0 = 0; j0 <= m; j0 += GM_STEPS_PER_CHECK) {
             if (gexec) {
                 cudaError_t e = cudaGraphLaunch(gexec, st);
                 if (e != cudaSuccess) {
@@ -2819,13 +2762,6 @@ sai_status gmres_run(const Items& I, int k, int m, const Ops<T>& A, const T* Bs,
         SAI_CUDA(cudaGetLastError());
     }
     if (gexec) cudaGraphExecDestroy(gexec);
-    if (whole) {
-        // the groups of steps the while nodes ran, for the launch count
-        int nb[2] = {0, 0};
-        SAI_CUDA(cudaMemcpyAsync(nb, G.nbody, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        SAI_CUDA(cudaStreamSynchronize(st));
-        sai_count_grid_add((long long)nb[1] * (GM_STEPS_PER_CHECK * GM_LAUNCHES_PER_STEP + 1));
-    }
     {
         // a ring wait of k_dc_update_ring that ran out (the flag is cleared for the next call)
         int perr = 0;
@@ -2854,7 +2790,7 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
     const size_t km1 = (size_t)k * (m + 1);
     const size_t hsz = 2 * (size_t)k * (m + 1) * m + 2 * (size_t)k * m + 4 * km1 + (size_t)k * m + 2 * (size_t)k +
                        (size_t)k * PS;
-    const size_t isz = 6 * (size_t)k + 2 * (size_t)(k + 1) + 4;
+    const size_t isz = 6 * (size_t)k + 2 * (size_t)(k + 1) + 2;
     SAI_TRY(hb.alloc(sizeof(double) * hsz, st, true));
     SAI_TRY(ib.alloc(sizeof(int) * isz, st, true));
     SAI_CUDA(cudaMemsetAsync(hb.p, 0, sizeof(double) * hsz, st));
@@ -2892,7 +2828,6 @@ sai_status gm_alloc(int k, int m, Buf& hb, Buf& ib, Gm& G, cudaStream_t st)
     G.jdev = G.ladv + (k + 1);
     G.bcnt = G.jdev + 1;
     G.scnt = G.bcnt + 1;
-    G.nbody = G.scnt + k;
     return SAI_OK;
 }
 
